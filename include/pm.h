@@ -1,0 +1,221 @@
+/*
+ * pm.h -- C ABI of libpmgpu, a GB300 (sm_103a) implementation of the
+ * population fitness evaluation and genetic algorithm of AlBdaiwi &
+ * AboElFotoh, "A GPU-Based Genetic Algorithm for the P-Median Problem"
+ * (arXiv:1610.10061).
+ *
+ * Problem (Section 1, Eqs. 1-3): n clients, m facilities, an n x m matrix of
+ * non-negative distances d_ij and an integer 1 <= p < m; choose exactly p
+ * open facilities minimising the sum over clients of the distance to the
+ * nearest open facility.
+ *
+ * Conventions for every call:
+ *  - Every call returns a pm_status; nothing is thrown across the ABI.
+ *  - Facility ids are 0-based (the paper's Section 1 numbers them from 1).
+ *  - A population is `pop` bitsets of W = ceil(m/32) uint32 words each,
+ *    row-major (individual t occupies words [t*W, (t+1)*W)); facility j is
+ *    open in individual t iff bit (j & 31) of word t*W + (j >> 5) is set.
+ *    Bits at positions >= m must be 0.  This is the paper's chromosome of m
+ *    bits (Section 4.1), true = open.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Device
+ *    work is enqueued on it; a call that returns results in host memory
+ *    synchronises that stream before returning.
+ *  - The library never frees or retains caller buffers.  Objects it returns
+ *    (pm_instance, pm_ga) are owned by the caller and released with the
+ *    matching destroy call; they must not be used concurrently from two
+ *    streams.
+ *  - Pointers documented as "host or device" are classified with
+ *    cudaPointerGetAttributes: device (or managed) memory is used in place,
+ *    anything else is treated as host memory and staged through the
+ *    library's own device buffers (the call then synchronises `stream`).
+ *  - All device work runs in the library's own CUDA kernels; there is no CPU
+ *    fallback.  A failed CUDA call is reported as PM_ERR_CUDA.
+ */
+#ifndef PM_H
+#define PM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PM_API __attribute__((visibility("default")))
+#else
+#define PM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum pm_status {
+    PM_OK = 0,
+    PM_ERR_INVALID_ARG = 1,   /* a size, pointer or parameter is out of range */
+    PM_ERR_NEGATIVE_DIST = 2, /* some d_ij < 0 (the paper assumes d >= 0, Section 1) */
+    PM_ERR_UNSUPPORTED = 3,   /* m > 65535 (facility ids are stored as uint16) */
+    PM_ERR_MASK = 4,          /* checked evaluation: a bitset without exactly p open or with bits >= m */
+    PM_ERR_CUDA = 5,          /* a CUDA runtime call failed */
+    PM_ERR_OOM = 6,           /* device or host allocation failed */
+    PM_ERR_TIMEOUT = 7        /* a bounded device-side wait gave up */
+} pm_status;
+
+/* Human-readable name of a status code (static string, never NULL). */
+PM_API const char *pm_strerror(pm_status s);
+
+/* ------------------------------------------------------------------------
+ * Instances: the truncated ordering and increment tables.
+ * ------------------------------------------------------------------------ */
+
+typedef struct pm_instance pm_instance;
+
+/*
+ * pm_instance_create -- Section 2.1, Eq. 4 and the truncation argument after
+ * Eq. 6.  Copies d (n x m int32, row-major, host or device memory) to the
+ * device, checks d >= 0, and builds for each client i the ordering Pi'_i
+ * (facility ids sorted by ascending d_ij, equal distances by ascending id)
+ * and the increments Delta'_i (Delta'_i0 = smallest distance, then
+ * consecutive differences), both truncated to L = m - p + 1 columns.  The
+ * tables stay resident on `device` (Pi' uint16, Delta' int32, rows padded to
+ * a stride of round_up(L, 32) elements).
+ *   d       distance matrix; not retained.
+ *   n, m, p 1 <= n, 1 <= p < m <= 65535.
+ *   device  CUDA device ordinal; becomes the current device.
+ *   out     receives the new instance.
+ * Errors: PM_ERR_INVALID_ARG (sizes, NULL pointers), PM_ERR_UNSUPPORTED
+ * (m > 65535), PM_ERR_NEGATIVE_DIST, PM_ERR_OOM, PM_ERR_CUDA.  Synchronises
+ * `stream` (the distance check needs the device's answer).
+ */
+PM_API pm_status pm_instance_create(const int32_t *d, int64_t n, int64_t m, int64_t p, int device, void *stream,
+                             pm_instance **out);
+
+/* Release an instance and its device tables (NULL is accepted). */
+PM_API pm_status pm_instance_destroy(pm_instance *inst);
+
+/* Sizes of an instance: n, m, p, L = m-p+1, W = ceil(m/32) and the padded
+ * row stride of the device tables (elements).  Any output may be NULL. */
+PM_API pm_status pm_instance_info(const pm_instance *inst, int64_t *n, int64_t *m, int64_t *p, int64_t *L, int64_t *W,
+                           int64_t *row_stride);
+
+/*
+ * pm_instance_tables -- copy Pi' (uint16) and Delta' (int32) into caller
+ * buffers of n x L elements each (dense rows, no padding; host or device
+ * memory).  Section 2.1, Example 1 shows both tables for a 5 x 4 instance.
+ * Synchronises `stream`.
+ */
+PM_API pm_status pm_instance_tables(const pm_instance *inst, uint16_t *pi_out, int32_t *delta_out, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Population fitness evaluation (the hot path).
+ * ------------------------------------------------------------------------ */
+
+/*
+ * pm_eval_population -- Section 4.2 (function Fitness) and Eq. 6: for every
+ * individual t and client i, walk Delta'_i in the order of Pi'_i, adding each
+ * increment, and stop after the first rank whose facility is open in t; the
+ * cost of t is the int64 sum over clients.  It equals the p-median objective
+ * of Eqs. 1-3 for t's open set (Eq. 4 telescopes).
+ *   masks   pop x W bitsets (layout above), host or device memory.
+ *   pop     number of individuals, >= 0 (0 is a no-op).
+ *   costs   pop int64 results, host or device memory.
+ *   checked nonzero: first verify every bitset has exactly p open facilities
+ *           and no bits >= m, returning PM_ERR_MASK (costs untouched) if
+ *           not; this synchronises `stream`.  zero: bitsets are trusted; a
+ *           bitset with fewer than p open facilities may yield a meaningless
+ *           cost for that individual (never a fault).
+ * Asynchronous when masks and costs are device memory and checked == 0.
+ * Errors: PM_ERR_INVALID_ARG, PM_ERR_MASK, PM_ERR_OOM, PM_ERR_CUDA.
+ */
+PM_API pm_status pm_eval_population(pm_instance *inst, const uint32_t *masks, int64_t pop, int64_t *costs, int checked,
+                             void *stream);
+
+/* ------------------------------------------------------------------------
+ * The genetic algorithm (Sections 3.1, 3.2.2, 4.3-4.5) on the device.
+ * ------------------------------------------------------------------------ */
+
+typedef struct pm_ga_params {
+    int64_t deme;         /* D, the paper's NT: a power of two >= 2 dividing pop; 0 = min(pop, 256) */
+    int32_t xover_rounds; /* crossover rounds per generation; < 0 = lg D (Section 3.2.2, step 3) */
+    int32_t mut_tries;    /* mutation tries per generation; < 0 = lg D (Section 3.2.2, step 5) */
+    int64_t saturation;   /* S: stop when the best has not improved for S generations; 0 = off */
+    uint32_t stream_id;   /* fourth word of every random-number counter (independent runs) */
+    uint32_t reserved;    /* must be 0 */
+} pm_ga_params;
+
+typedef struct pm_ga pm_ga;
+
+/*
+ * pm_ga_create -- allocate a GA of `pop` individuals (pop/D demes, the
+ * paper's NB blocks of NT threads) on `inst`, seeded with `seed`.  No
+ * generation runs yet.  params may be NULL (all defaults).
+ * Random numbers: draw s of operation op for unit u in generation g is word
+ * (s & 3) of Philox4x32-10(counter = (g, u, op*2^16 + s/4, stream_id),
+ * key = (seed lo, seed hi)); U[0,N) = floor(u32 * N / 2^32).
+ * Errors: PM_ERR_INVALID_ARG, PM_ERR_OOM, PM_ERR_CUDA.
+ */
+PM_API pm_status pm_ga_create(pm_instance *inst, uint64_t seed, int64_t pop, const pm_ga_params *params, void *stream,
+                       pm_ga **out);
+
+/*
+ * pm_ga_step -- run up to `gens` more generations on the device (one CUDA
+ * graph launch; the loop is a conditional while-node, so the host is not
+ * involved between generations).  A generation is: a fresh random
+ * population (Floyd sampling) whose slot 0 of every deme receives that
+ * deme's best of the previous generation (migration, Section 4.5 variant
+ * (i)); evaluation; crossover rounds with butterfly partners t XOR
+ * (D >> (1 + r mod lg D)), children replacing parents only when strictly
+ * cheaper; mutation tries (circular or block shift, Section 4.4) on the
+ * individuals not yet improved, the first strictly cheaper mutant replacing
+ * the individual; deme best (lowest cost, then lowest index); global best
+ * and saturation count.  Stops early when saturation is reached.
+ *   trace  nullable; receives one int64 per generation actually run (the
+ *          global best cost after it), host or device memory, `gens`
+ *          entries of room.  A host trace synchronises `stream`.
+ * Errors: PM_ERR_INVALID_ARG, PM_ERR_OOM, PM_ERR_CUDA.
+ */
+PM_API pm_status pm_ga_step(pm_ga *ga, int64_t gens, int64_t *trace, void *stream);
+
+/*
+ * pm_ga_result -- synchronise `stream` and report the best solution so far.
+ * Any output may be NULL.  best_mask: W words (host or device memory);
+ * gens_run: generations run since creation; evals: fitness evaluations so
+ * far (failed crossovers produce no child and are not counted; mutation
+ * tries after an individual improved are not run and not counted).
+ */
+PM_API pm_status pm_ga_result(pm_ga *ga, int64_t *best_cost, uint32_t *best_mask, int64_t *gens_run, int64_t *evals,
+                       void *stream);
+
+/* pm_ga_population -- copy the population after the last generation: pop x W
+ * masks and pop costs (either may be NULL; host or device memory).
+ * Synchronises `stream`. */
+PM_API pm_status pm_ga_population(pm_ga *ga, uint32_t *masks, int64_t *costs, void *stream);
+
+/*
+ * pm_ga_save / pm_ga_load -- checkpoint and resume.  The state between
+ * generations is (seed, generation index, deme bests, global best,
+ * saturation count, evaluation count); the random numbers are keyed by the
+ * generation index, so a loaded GA continues exactly as the saved one would
+ * have.  pm_ga_save: if buf is NULL, *len receives the size needed;
+ * otherwise *len must be at least that size and receives the bytes written
+ * (host memory).  Synchronises `stream`.  pm_ga_load creates a new GA on
+ * `inst` (which must have the same n, m, p) from such a buffer.
+ */
+PM_API pm_status pm_ga_save(pm_ga *ga, void *buf, size_t *len, void *stream);
+PM_API pm_status pm_ga_load(pm_instance *inst, const void *buf, size_t len, void *stream, pm_ga **out);
+
+/* Release a GA and its device buffers (NULL is accepted). */
+PM_API pm_status pm_ga_destroy(pm_ga *ga);
+
+/*
+ * pm_ga_run -- convenience: create, run `gens` generations, report, destroy.
+ *   best_cost  receives the best cost; best_mask (W words, nullable, host or
+ *   device); gens_run, evals nullable; trace nullable (gens entries).
+ * Synchronises `stream`.
+ */
+PM_API pm_status pm_ga_run(pm_instance *inst, uint64_t seed, int64_t pop, int64_t gens, const pm_ga_params *params,
+                    int64_t *best_cost, uint32_t *best_mask, int64_t *gens_run, int64_t *evals, int64_t *trace,
+                    void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PM_H */

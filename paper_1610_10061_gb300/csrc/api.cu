@@ -1,0 +1,258 @@
+// C ABI: instances, population evaluation, status strings (include/pm.h).
+
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "pm_common.cuh"
+
+void pm_note_cuda_error(cudaError_t e, const char *what, const char *file, int line)
+{
+    static const bool verbose = std::getenv("PM_VERBOSE") != nullptr;
+    if (verbose)
+        std::fprintf(stderr, "libpmgpu: %s failed at %s:%d: %s\n", what, file, line, cudaGetErrorString(e));
+}
+
+pm_status pm_dbuf::reserve(size_t want)
+{
+    if (want <= bytes && ptr)
+        return PM_OK;
+    release();
+    size_t sz = want < 256 ? 256 : want;
+    cudaError_t e = cudaMalloc(&ptr, sz);
+    if (e != cudaSuccess) {
+        ptr = nullptr;
+        bytes = 0;
+        pm_note_cuda_error(e, "cudaMalloc", __FILE__, __LINE__);
+        return e == cudaErrorMemoryAllocation ? PM_ERR_OOM : PM_ERR_CUDA;
+    }
+    bytes = sz;
+    return PM_OK;
+}
+
+void pm_dbuf::release()
+{
+    if (ptr)
+        cudaFree(ptr);
+    ptr = nullptr;
+    bytes = 0;
+}
+
+bool pm_is_device_ptr(const void *p)
+{
+    if (!p)
+        return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+extern "C" const char *pm_strerror(pm_status s)
+{
+    switch (s) {
+    case PM_OK:
+        return "PM_OK";
+    case PM_ERR_INVALID_ARG:
+        return "PM_ERR_INVALID_ARG: argument out of range";
+    case PM_ERR_NEGATIVE_DIST:
+        return "PM_ERR_NEGATIVE_DIST: the distance matrix has a negative entry";
+    case PM_ERR_UNSUPPORTED:
+        return "PM_ERR_UNSUPPORTED: m exceeds 65535";
+    case PM_ERR_MASK:
+        return "PM_ERR_MASK: a bitset does not have exactly p open facilities";
+    case PM_ERR_CUDA:
+        return "PM_ERR_CUDA: a CUDA runtime call failed";
+    case PM_ERR_OOM:
+        return "PM_ERR_OOM: out of memory";
+    case PM_ERR_TIMEOUT:
+        return "PM_ERR_TIMEOUT: a bounded device wait gave up";
+    }
+    return "unknown pm_status";
+}
+
+static void destroy_instance(pm_instance *inst)
+{
+    if (!inst)
+        return;
+    cudaSetDevice(inst->device);
+    if (inst->pi)
+        cudaFree(inst->pi);
+    if (inst->delta)
+        cudaFree(inst->delta);
+    inst->stage_masks.release();
+    inst->stage_costs.release();
+    inst->partials.release();
+    inst->columns.release();
+    inst->flag.release();
+    inst->err.release();
+    delete inst;
+}
+
+static pm_status create_impl(const int32_t *d, int64_t n, int64_t m, int64_t p, int device, cudaStream_t stream,
+                             pm_instance *inst)
+{
+    PM_CUDA(cudaSetDevice(device));
+    inst->device = device;
+    inst->n = n;
+    inst->m = m;
+    inst->p = p;
+    inst->L = m - p + 1;
+    inst->W = pm_ceil_div(m, 32);
+    inst->stride = pm_round_up(inst->L, 32);
+    int v = 0;
+    PM_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device));
+    inst->sm_count = v;
+    PM_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+    inst->smem_optin = (size_t)v;
+    const size_t tab = (size_t)n * (size_t)inst->stride;
+    PM_CUDA(cudaMalloc(reinterpret_cast<void **>(&inst->pi), tab * sizeof(uint16_t)));
+    PM_CUDA(cudaMalloc(reinterpret_cast<void **>(&inst->delta), tab * sizeof(int32_t)));
+    PM_TRY(inst->err.reserve(256));
+    PM_CUDA(cudaMemsetAsync(inst->err.ptr, 0, 256, stream));
+    PM_TRY(pm_fitness_init(inst));
+    const int32_t *d_dev = d;
+    int32_t *tmp = nullptr;
+    if (!pm_is_device_ptr(d)) {
+        const size_t bytes = (size_t)n * (size_t)m * sizeof(int32_t);
+        PM_CUDA(cudaMallocAsync(reinterpret_cast<void **>(&tmp), bytes, stream));
+        cudaError_t e = cudaMemcpyAsync(tmp, d, bytes, cudaMemcpyHostToDevice, stream);
+        if (e != cudaSuccess) {
+            cudaFreeAsync(tmp, stream);
+            PM_CUDA(e);
+        }
+        d_dev = tmp;
+    }
+    pm_status st = pm_build_tables(inst, d_dev, stream);
+    if (tmp)
+        cudaFreeAsync(tmp, stream);
+    PM_TRY(st);
+    PM_CUDA(cudaStreamSynchronize(stream));
+    return PM_OK;
+}
+
+extern "C" pm_status pm_instance_create(const int32_t *d, int64_t n, int64_t m, int64_t p, int device, void *stream,
+                                        pm_instance **out)
+{
+    if (!out)
+        return PM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!d || n < 1 || m < 2 || p < 1 || p >= m || device < 0)
+        return PM_ERR_INVALID_ARG;
+    if (m > 65535)
+        return PM_ERR_UNSUPPORTED;
+    if (n > ((int64_t)1 << 40) / m)
+        return PM_ERR_INVALID_ARG;
+    pm_instance *inst = new (std::nothrow) pm_instance();
+    if (!inst)
+        return PM_ERR_OOM;
+    pm_status st = create_impl(d, n, m, p, device, static_cast<cudaStream_t>(stream), inst);
+    if (st != PM_OK) {
+        destroy_instance(inst);
+        return st;
+    }
+    *out = inst;
+    return PM_OK;
+}
+
+extern "C" pm_status pm_instance_destroy(pm_instance *inst)
+{
+    destroy_instance(inst);
+    return PM_OK;
+}
+
+extern "C" pm_status pm_instance_info(const pm_instance *inst, int64_t *n, int64_t *m, int64_t *p, int64_t *L,
+                                      int64_t *W, int64_t *row_stride)
+{
+    if (!inst)
+        return PM_ERR_INVALID_ARG;
+    if (n)
+        *n = inst->n;
+    if (m)
+        *m = inst->m;
+    if (p)
+        *p = inst->p;
+    if (L)
+        *L = inst->L;
+    if (W)
+        *W = inst->W;
+    if (row_stride)
+        *row_stride = inst->stride;
+    return PM_OK;
+}
+
+extern "C" pm_status pm_instance_tables(const pm_instance *inst, uint16_t *pi_out, int32_t *delta_out, void *stream)
+{
+    if (!inst || (!pi_out && !delta_out))
+        return PM_ERR_INVALID_ARG;
+    PM_CUDA(cudaSetDevice(inst->device));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (pi_out)
+        PM_CUDA(cudaMemcpy2DAsync(pi_out, inst->L * sizeof(uint16_t), inst->pi, inst->stride * sizeof(uint16_t),
+                                  inst->L * sizeof(uint16_t), inst->n, cudaMemcpyDefault, s));
+    if (delta_out)
+        PM_CUDA(cudaMemcpy2DAsync(delta_out, inst->L * sizeof(int32_t), inst->delta, inst->stride * sizeof(int32_t),
+                                  inst->L * sizeof(int32_t), inst->n, cudaMemcpyDefault, s));
+    PM_CUDA(cudaStreamSynchronize(s));
+    return PM_OK;
+}
+
+extern "C" pm_status pm_eval_population(pm_instance *inst, const uint32_t *masks, int64_t pop, int64_t *costs,
+                                        int checked, void *stream)
+{
+    if (!inst || pop < 0)
+        return PM_ERR_INVALID_ARG;
+    if (pop == 0)
+        return PM_OK;
+    if (!masks || !costs)
+        return PM_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> guard(inst->lock);
+    PM_CUDA(cudaSetDevice(inst->device));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t mask_bytes = (size_t)pop * (size_t)inst->W * sizeof(uint32_t);
+    const size_t cost_bytes = (size_t)pop * sizeof(int64_t);
+    const bool masks_dev = pm_is_device_ptr(masks);
+    const bool costs_dev = pm_is_device_ptr(costs);
+    const uint32_t *m_dev = masks;
+    int64_t *c_dev = costs;
+    if (!masks_dev) {
+        PM_TRY(inst->stage_masks.reserve(mask_bytes));
+        PM_CUDA(cudaMemcpyAsync(inst->stage_masks.ptr, masks, mask_bytes, cudaMemcpyHostToDevice, s));
+        m_dev = static_cast<const uint32_t *>(inst->stage_masks.ptr);
+    }
+    if (!costs_dev) {
+        PM_TRY(inst->stage_costs.reserve(cost_bytes));
+        c_dev = static_cast<int64_t *>(inst->stage_costs.ptr);
+    }
+    if (checked) {
+        PM_TRY(inst->flag.reserve(64));
+        int *flag = static_cast<int *>(inst->flag.ptr);
+        PM_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), s));
+        PM_TRY(pm_launch_mask_check(inst, m_dev, pop, flag, s));
+        int bad = 0;
+        PM_CUDA(cudaMemcpyAsync(&bad, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+        PM_CUDA(cudaStreamSynchronize(s));
+        if (bad)
+            return PM_ERR_MASK;
+    }
+    const pm_eval_plan plan = pm_plan_eval(inst, pop);
+    PM_TRY(inst->partials.reserve(pm_plan_partial_bytes(plan, pop)));
+    PM_TRY(inst->columns.reserve(std::max<size_t>(pm_plan_column_bytes(inst, plan), 256)));
+    pm_accept_args acc;
+    PM_TRY(pm_launch_eval(inst, plan, m_dev, pop, nullptr, c_dev, static_cast<int64_t *>(inst->partials.ptr),
+                          static_cast<uint32_t *>(inst->columns.ptr), static_cast<int *>(inst->err.ptr), acc, s));
+    if (!costs_dev || checked) {
+        if (!costs_dev)
+            PM_CUDA(cudaMemcpyAsync(costs, c_dev, cost_bytes, cudaMemcpyDeviceToHost, s));
+        int err = 0;
+        PM_CUDA(cudaMemcpyAsync(&err, inst->err.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+        PM_CUDA(cudaStreamSynchronize(s));
+        if (err)
+            return (pm_status)err;
+    }
+    return PM_OK;
+}

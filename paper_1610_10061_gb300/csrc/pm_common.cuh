@@ -1,0 +1,128 @@
+// Shared definitions of libpmgpu's translation units (device helpers, the
+// instance object and launch configuration).  Nothing here is visible at the
+// C ABI except through include/pm.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "pm.h"
+
+#define PM_FULL_MASK 0xffffffffu
+
+// Evaluate a CUDA runtime call; on failure return PM_ERR_CUDA (or OOM).
+#define PM_CUDA(call)                                                                                  \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess) {                                                                       \
+            pm_note_cuda_error(e_, #call, __FILE__, __LINE__);                                         \
+            return (e_ == cudaErrorMemoryAllocation) ? PM_ERR_OOM : PM_ERR_CUDA;                       \
+        }                                                                                              \
+    } while (0)
+
+#define PM_TRY(expr)                                                                                   \
+    do {                                                                                               \
+        pm_status s_ = (expr);                                                                         \
+        if (s_ != PM_OK)                                                                               \
+            return s_;                                                                                 \
+    } while (0)
+
+void pm_note_cuda_error(cudaError_t e, const char *what, const char *file, int line);
+
+// A device buffer owned by the library that grows on demand.
+struct pm_dbuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    pm_status reserve(size_t want);
+    void release();
+};
+
+// Scratch for one fitness launch configuration (partial sums per client split).
+struct pm_eval_plan {
+    int groups = 4;       // G: 32-individual groups per CTA
+    int warps = 16;       // warps per CTA
+    int splits = 1;       // CTAs per individual tile along the client axis
+    int64_t tiles = 0;    // ceil(pop / (32 G))
+};
+
+struct pm_instance {
+    int device = 0;
+    int64_t n = 0, m = 0, p = 0, L = 0, W = 0, stride = 0;
+    int32_t max_d = 0;
+    uint16_t *pi = nullptr;     // n x stride, Pi' (0-based facility ids)
+    int32_t *delta = nullptr;   // n x stride, Delta'
+    int sm_count = 0;
+    size_t smem_optin = 0;
+    // staging and scratch for pm_eval_population
+    pm_dbuf stage_masks, stage_costs, partials, columns, flag, err;
+    std::mutex lock;
+};
+
+// ---------------------------------------------------------------------------
+// Fitness evaluation (fitness.cu)
+// ---------------------------------------------------------------------------
+
+// Choose the tile configuration for `pop` individuals on `inst`.
+pm_eval_plan pm_plan_eval(const pm_instance *inst, int64_t pop);
+// Bytes of int64 partial sums the plan needs.
+size_t pm_plan_partial_bytes(const pm_eval_plan &plan, int64_t pop);
+
+// Epilogue applied after the per-individual sums are formed.
+//   mode 0: costs[t] = sum.
+//   mode 1 (accept): if active(t) and sum < cur_cost[t]: cur_cost[t] = sum,
+//           copy cand row t into cur row t, set improved[t] = 1.
+struct pm_accept_args {
+    int mode = 0;
+    int64_t *cur_cost = nullptr;
+    uint32_t *cur_masks = nullptr;
+    const uint32_t *cand_masks = nullptr;
+    uint8_t *improved = nullptr;
+};
+
+// Enqueue the scan over (masks, pop) -> partials -> sums (+ epilogue).
+// active: nullable, bit (t & 31) of word t >> 5 marks individual t as
+// evaluated; inactive individuals get no cost written.
+pm_status pm_launch_eval(const pm_instance *inst, const pm_eval_plan &plan, const uint32_t *masks, int64_t pop,
+                         const uint32_t *active, int64_t *costs, int64_t *partials, uint32_t *colT, int *err,
+                         const pm_accept_args &acc, cudaStream_t stream);
+// Bytes of the facility-major copy of the population the plan needs.
+size_t pm_plan_column_bytes(const pm_instance *inst, const pm_eval_plan &plan);
+// One-time per-process kernel attributes (dynamic shared memory opt-in).
+pm_status pm_fitness_init(const pm_instance *inst);
+
+// Checked mode: count bitsets with popcount != p or stray high bits into *flag.
+pm_status pm_launch_mask_check(const pm_instance *inst, const uint32_t *masks, int64_t pop, int *flag,
+                               cudaStream_t stream);
+
+// ---------------------------------------------------------------------------
+// Tables (tables.cu)
+// ---------------------------------------------------------------------------
+pm_status pm_build_tables(pm_instance *inst, const int32_t *d_dev, cudaStream_t stream);
+
+// ---------------------------------------------------------------------------
+// Small helpers
+// ---------------------------------------------------------------------------
+bool pm_is_device_ptr(const void *p);
+
+static inline int64_t pm_ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+static inline int64_t pm_round_up(int64_t a, int64_t b) { return pm_ceil_div(a, b) * b; }
+
+// 32 x 32 bit-matrix transpose across a warp: on entry lane l holds row l
+// (bit c = element (l, c)); on exit lane c holds column c (bit l = element
+// (l, c)).  Five butterfly exchanges.
+__device__ __forceinline__ uint32_t pm_transpose32(uint32_t x, int lane)
+{
+    const uint32_t masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const int j = 16 >> s;
+        const uint32_t m = masks[s];
+        const uint32_t y = __shfl_xor_sync(PM_FULL_MASK, x, j);
+        x = (lane & j) ? ((x & ~m) | ((y & ~m) >> j)) : ((x & m) | ((y & m) << j));
+    }
+    return x;
+}

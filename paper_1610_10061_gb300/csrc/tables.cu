@@ -1,0 +1,235 @@
+// Truncated ordering and increment tables (Section 2.1, Eq. 4 and the
+// truncation argument after Eq. 6), built on the device.
+//
+// For client i, Pi'_i lists the facility ids in ascending order of d_ij
+// (equal distances by ascending id) and Delta'_i holds the first distance
+// followed by consecutive differences; only the first L = m - p + 1 ranks
+// are kept.
+//
+// GB300 design: one CTA per row (grid-stride over rows), a stable LSD radix
+// sort of the row's distances with 8-bit digits.  The row starts in facility
+// order, so a stable sort on the distance alone yields the (distance, id)
+// order; only ceil(bits(max d) / 8) passes are needed.  Each pass:
+//   count   - every warp owns a contiguous segment of the row and walks it 32
+//             keys at a time; __match_any_sync groups equal digits, the lowest
+//             lane of each group adds the group size to the warp's histogram;
+//   offsets - per digit, the running count over warps, plus the exclusive
+//             scan over digits;
+//   scatter - the same walk; a key's destination is its warp's offset for
+//             that digit plus the number of equal-digit lanes below it, then
+//             the group leader advances the offset.
+// Keys (uint32) and ids (uint16) live in shared memory when the row fits
+// (12 bytes per element), else in a per-CTA global scratch slice.  The
+// epilogue writes Pi' and the differences Delta' into rows padded to a stride
+// of round_up(L, 32) elements (padding = 0).
+
+#include "pm_common.cuh"
+
+namespace {
+
+constexpr int kSortThreads = 512;
+constexpr int kSortWarps = kSortThreads / 32;
+
+__global__ void k_minmax(const int32_t *__restrict__ d, int64_t count, int *__restrict__ out)
+{
+    int lo = 0x7fffffff, hi = (int)0x80000000;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        const int v = __ldg(d + i);
+        lo = min(lo, v);
+        hi = max(hi, v);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(PM_FULL_MASK, lo, o));
+        hi = max(hi, __shfl_xor_sync(PM_FULL_MASK, hi, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(out + 0, lo);
+        atomicMax(out + 1, hi);
+    }
+}
+
+__global__ void k_minmax_init(int *out)
+{
+    out[0] = 0x7fffffff;
+    out[1] = (int)0x80000000;
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_tables(const int32_t *__restrict__ d, int64_t n, int32_t m,
+                                                         int32_t L, int64_t stride, int passes,
+                                                         uint16_t *__restrict__ pi, int32_t *__restrict__ delta,
+                                                         unsigned char *__restrict__ gscratch)
+{
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    __shared__ uint32_t whist[kSortWarps][256];
+    __shared__ uint32_t digit_base[256];
+    __shared__ uint32_t warp_tot[8];
+
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    unsigned char *buf = gscratch ? gscratch + (size_t)blockIdx.x * (size_t)m * 12 : sm_raw;
+    uint32_t *keysA = reinterpret_cast<uint32_t *>(buf);
+    uint32_t *keysB = keysA + m;
+    uint16_t *valsA = reinterpret_cast<uint16_t *>(keysB + m);
+    uint16_t *valsB = valsA + m;
+    const int seg = (((m + kSortWarps - 1) / kSortWarps) + 31) & ~31;
+    const int s_begin = warp * seg;
+    const int s_end = min(m, s_begin + seg);
+    const unsigned lt_mask = (1u << lane) - 1u;
+
+    for (int64_t row = blockIdx.x; row < n; row += gridDim.x) {
+        const int32_t *drow = d + row * (int64_t)m;
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+            keysA[i] = (uint32_t)__ldg(drow + i);
+            valsA[i] = (uint16_t)i;
+        }
+        __syncthreads();
+        uint32_t *kin = keysA, *kout = keysB;
+        uint16_t *vin = valsA, *vout = valsB;
+        for (int pass = 0; pass < passes; ++pass) {
+            const int shift = 8 * pass;
+            for (int i = threadIdx.x; i < kSortWarps * 256; i += blockDim.x)
+                (&whist[0][0])[i] = 0;
+            __syncthreads();
+            // count
+            for (int base = s_begin; base < s_end; base += 32) {
+                const int i = base + lane;
+                const bool valid = i < s_end;
+                const uint32_t dig = valid ? ((kin[i] >> shift) & 255u) : 256u;
+                const unsigned peers = __match_any_sync(PM_FULL_MASK, dig);
+                if (valid && lane == __ffs(peers) - 1)
+                    whist[warp][dig] += __popc(peers);
+                __syncwarp();
+            }
+            __syncthreads();
+            // offsets: per digit over warps, then exclusive scan over digits
+            if (threadIdx.x < 256) {
+                const int dg = threadIdx.x;
+                uint32_t run = 0;
+                for (int w = 0; w < kSortWarps; ++w) {
+                    const uint32_t c = whist[w][dg];
+                    whist[w][dg] = run;
+                    run += c;
+                }
+                // inclusive scan of run over the 256 digits: warp scan then warp totals
+                uint32_t x = run;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(PM_FULL_MASK, x, o);
+                    if (lane >= o)
+                        x += y;
+                }
+                if (lane == 31)
+                    warp_tot[warp] = x;
+                digit_base[dg] = x - run;  // exclusive within the warp
+            }
+            __syncthreads();
+            if (threadIdx.x < 256) {
+                const int dg = threadIdx.x;
+                uint32_t add = 0;
+                for (int w = 0; w < (dg >> 5); ++w)
+                    add += warp_tot[w];
+                const uint32_t b = digit_base[dg] + add;
+                for (int w = 0; w < kSortWarps; ++w)
+                    whist[w][dg] += b;
+            }
+            __syncthreads();
+            // scatter
+            for (int base = s_begin; base < s_end; base += 32) {
+                const int i = base + lane;
+                const bool valid = i < s_end;
+                uint32_t key = 0;
+                uint16_t val = 0;
+                if (valid) {
+                    key = kin[i];
+                    val = vin[i];
+                }
+                const uint32_t dig = valid ? ((key >> shift) & 255u) : 256u;
+                const unsigned peers = __match_any_sync(PM_FULL_MASK, dig);
+                if (valid) {
+                    const uint32_t pos = whist[warp][dig] + __popc(peers & lt_mask);
+                    kout[pos] = key;
+                    vout[pos] = val;
+                }
+                __syncwarp();
+                if (valid && lane == __ffs(peers) - 1)
+                    whist[warp][dig] += __popc(peers);
+                __syncwarp();
+            }
+            __syncthreads();
+            uint32_t *tk = kin;
+            kin = kout;
+            kout = tk;
+            uint16_t *tv = vin;
+            vin = vout;
+            vout = tv;
+        }
+        // epilogue: Pi' and Delta' (rank 0: the distance itself)
+        uint16_t *prow = pi + row * stride;
+        int32_t *qrow = delta + row * stride;
+        for (int r = threadIdx.x; r < stride; r += blockDim.x) {
+            if (r < L) {
+                prow[r] = vin[r];
+                qrow[r] = (int32_t)(kin[r] - (r > 0 ? kin[r - 1] : 0u));
+            } else {
+                prow[r] = 0;
+                qrow[r] = 0;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+static int bits_needed(uint32_t v)
+{
+    int b = 0;
+    while (v) {
+        ++b;
+        v >>= 1;
+    }
+    return b;
+}
+
+pm_status pm_build_tables(pm_instance *inst, const int32_t *d_dev, cudaStream_t stream)
+{
+    const int64_t count = inst->n * inst->m;
+    int *mm = nullptr;
+    PM_TRY(inst->flag.reserve(64));
+    mm = reinterpret_cast<int *>(inst->flag.ptr);
+    k_minmax_init<<<1, 1, 0, stream>>>(mm);
+    const int64_t blocks = std::min<int64_t>(pm_ceil_div(count, 256), (int64_t)inst->sm_count * 8);
+    k_minmax<<<(unsigned)blocks, 256, 0, stream>>>(d_dev, count, mm);
+    PM_CUDA(cudaGetLastError());
+    int host_mm[2];
+    PM_CUDA(cudaMemcpyAsync(host_mm, mm, sizeof(host_mm), cudaMemcpyDeviceToHost, stream));
+    PM_CUDA(cudaStreamSynchronize(stream));
+    if (host_mm[0] < 0)
+        return PM_ERR_NEGATIVE_DIST;
+    inst->max_d = host_mm[1];
+    const int passes = (bits_needed((uint32_t)host_mm[1]) + 7) / 8;
+
+    const size_t row_bytes = (size_t)inst->m * 12;
+    const size_t static_bytes = sizeof(uint32_t) * (kSortWarps * 256 + 256 + 8) + 1024;
+    const bool in_smem = row_bytes + static_bytes <= inst->smem_optin;
+    unsigned char *gscratch = nullptr;
+    int64_t grid;
+    size_t dyn = 0;
+    if (in_smem) {
+        dyn = row_bytes;
+        PM_CUDA(cudaFuncSetAttribute(k_tables, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+        const int64_t per_sm = std::max<int64_t>(1, std::min<int64_t>(4, (int64_t)(inst->smem_optin / (dyn + static_bytes))));
+        grid = std::min<int64_t>(inst->n, (int64_t)inst->sm_count * per_sm);
+    } else {
+        grid = std::min<int64_t>(inst->n, (int64_t)inst->sm_count);
+        PM_CUDA(cudaMallocAsync(reinterpret_cast<void **>(&gscratch), (size_t)grid * row_bytes, stream));
+    }
+    k_tables<<<(unsigned)grid, kSortThreads, dyn, stream>>>(d_dev, inst->n, (int32_t)inst->m, (int32_t)inst->L,
+                                                           inst->stride, passes, inst->pi, inst->delta, gscratch);
+    cudaError_t le = cudaGetLastError();
+    if (gscratch)
+        cudaFreeAsync(gscratch, stream);
+    PM_CUDA(le);
+    return PM_OK;
+}

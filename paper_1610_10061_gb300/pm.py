@@ -1,0 +1,288 @@
+"""Thin ctypes binding of libpmgpu (include/pm.h), same names as the C ABI.
+
+Only argument marshalling happens here; every step of the computation runs in
+the library's CUDA kernels.  Arrays may be numpy arrays (host memory) or torch
+CUDA tensors (device memory, used in place); torch supplies the stream
+(``torch.cuda.current_stream()``) when it is available.
+
+If ``libpmgpu.so`` is missing this module raises at import: there is no CPU
+fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libpmgpu.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is not built; run `python -m paper_1610_10061_gb300.build` "
+                      "(or __graft_entry__.build()) on a machine with nvcc")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+PM_OK = 0
+STATUS = {0: "PM_OK", 1: "PM_ERR_INVALID_ARG", 2: "PM_ERR_NEGATIVE_DIST", 3: "PM_ERR_UNSUPPORTED",
+          4: "PM_ERR_MASK", 5: "PM_ERR_CUDA", 6: "PM_ERR_OOM", 7: "PM_ERR_TIMEOUT"}
+
+
+class PMError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = int(status)
+        super().__init__(f"{where}: {pm_strerror(status)}")
+
+
+class pm_ga_params(ctypes.Structure):
+    _fields_ = [("deme", ctypes.c_int64), ("xover_rounds", ctypes.c_int32), ("mut_tries", ctypes.c_int32),
+                ("saturation", ctypes.c_int64), ("stream_id", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_PP = ctypes.POINTER(ctypes.c_void_p)
+_S = ctypes.c_int
+
+_SIGS = {
+    "pm_strerror": ([_S], ctypes.c_char_p),
+    "pm_instance_create": ([_P, _I64, _I64, _I64, ctypes.c_int, _P, _PP], _S),
+    "pm_instance_destroy": ([_P], _S),
+    "pm_instance_info": ([_P, _P, _P, _P, _P, _P, _P], _S),
+    "pm_instance_tables": ([_P, _P, _P, _P], _S),
+    "pm_eval_population": ([_P, _P, _I64, _P, ctypes.c_int, _P], _S),
+    "pm_ga_create": ([_P, ctypes.c_uint64, _I64, ctypes.POINTER(pm_ga_params), _P, _PP], _S),
+    "pm_ga_step": ([_P, _I64, _P, _P], _S),
+    "pm_ga_result": ([_P, _P, _P, _P, _P, _P], _S),
+    "pm_ga_population": ([_P, _P, _P, _P], _S),
+    "pm_ga_save": ([_P, _P, ctypes.POINTER(ctypes.c_size_t), _P], _S),
+    "pm_ga_load": ([_P, _P, ctypes.c_size_t, _P, _PP], _S),
+    "pm_ga_destroy": ([_P], _S),
+    "pm_ga_run": ([_P, ctypes.c_uint64, _I64, _I64, ctypes.POINTER(pm_ga_params), _P, _P, _P, _P, _P, _P], _S),
+}
+for _name, (_args, _res) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+
+def exported_symbols():
+    """Names this binding expects the library to export."""
+    return sorted(_SIGS)
+
+
+def pm_strerror(status: int) -> str:
+    return _lib.pm_strerror(int(status)).decode()
+
+
+def _check(status: int, where: str):
+    if status != PM_OK:
+        raise PMError(status, where)
+
+
+def _stream(stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    try:
+        import torch
+        if torch.cuda.is_available() and torch.cuda.is_initialized():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except Exception:
+        pass
+    return ctypes.c_void_p(0)
+
+
+def _addr(a):
+    """Address of a numpy array or a torch tensor (CPU or CUDA); None -> NULL."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return ctypes.c_void_p(a.ctypes.data)
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(a.data_ptr())
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+# --------------------------------------------------------------------------
+# Same-name wrappers of the C ABI (marshalling only)
+# --------------------------------------------------------------------------
+
+def pm_instance_create(d, n: int, m: int, p: int, device: int = 0, stream=None):
+    out = ctypes.c_void_p()
+    _check(_lib.pm_instance_create(_addr(d), n, m, p, device, _stream(stream), ctypes.byref(out)),
+           "pm_instance_create")
+    return out
+
+
+def pm_instance_destroy(inst):
+    _check(_lib.pm_instance_destroy(inst), "pm_instance_destroy")
+
+
+def pm_instance_info(inst):
+    vals = [ctypes.c_int64() for _ in range(6)]
+    _check(_lib.pm_instance_info(inst, *[ctypes.byref(v) for v in vals]), "pm_instance_info")
+    return dict(zip(["n", "m", "p", "L", "W", "stride"], [v.value for v in vals]))
+
+
+def pm_instance_tables(inst, pi_out, delta_out, stream=None):
+    _check(_lib.pm_instance_tables(inst, _addr(pi_out), _addr(delta_out), _stream(stream)), "pm_instance_tables")
+
+
+def pm_eval_population(inst, masks, pop: int, costs, checked: int = 0, stream=None):
+    _check(_lib.pm_eval_population(inst, _addr(masks), pop, _addr(costs), int(checked), _stream(stream)),
+           "pm_eval_population")
+
+
+def _params(deme=0, xover_rounds=-1, mut_tries=-1, saturation=0, stream_id=0):
+    return pm_ga_params(deme, xover_rounds, mut_tries, saturation, stream_id, 0)
+
+
+def pm_ga_create(inst, seed: int, pop: int, params: pm_ga_params | None = None, stream=None):
+    out = ctypes.c_void_p()
+    _check(_lib.pm_ga_create(inst, seed, pop, ctypes.byref(params) if params is not None else None,
+                             _stream(stream), ctypes.byref(out)), "pm_ga_create")
+    return out
+
+
+def pm_ga_step(ga, gens: int, trace=None, stream=None):
+    _check(_lib.pm_ga_step(ga, gens, _addr(trace), _stream(stream)), "pm_ga_step")
+
+
+def pm_ga_result(ga, best_mask=None, stream=None):
+    bc, gr, ev = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(_lib.pm_ga_result(ga, ctypes.byref(bc), _addr(best_mask), ctypes.byref(gr), ctypes.byref(ev),
+                             _stream(stream)), "pm_ga_result")
+    return bc.value, gr.value, ev.value
+
+
+def pm_ga_population(ga, masks, costs, stream=None):
+    _check(_lib.pm_ga_population(ga, _addr(masks), _addr(costs), _stream(stream)), "pm_ga_population")
+
+
+def pm_ga_save(ga, stream=None) -> bytes:
+    n = ctypes.c_size_t(0)
+    _check(_lib.pm_ga_save(ga, None, ctypes.byref(n), _stream(stream)), "pm_ga_save")
+    buf = ctypes.create_string_buffer(n.value)
+    _check(_lib.pm_ga_save(ga, buf, ctypes.byref(n), _stream(stream)), "pm_ga_save")
+    return buf.raw[: n.value]
+
+
+def pm_ga_load(inst, blob: bytes, stream=None):
+    out = ctypes.c_void_p()
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    _check(_lib.pm_ga_load(inst, buf, len(blob), _stream(stream), ctypes.byref(out)), "pm_ga_load")
+    return out
+
+
+def pm_ga_destroy(ga):
+    _check(_lib.pm_ga_destroy(ga), "pm_ga_destroy")
+
+
+def pm_ga_run(inst, seed: int, pop: int, gens: int, params: pm_ga_params | None = None, best_mask=None,
+              trace=None, stream=None):
+    bc, gr, ev = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(_lib.pm_ga_run(inst, seed, pop, gens, ctypes.byref(params) if params is not None else None,
+                          ctypes.byref(bc), _addr(best_mask), ctypes.byref(gr), ctypes.byref(ev), _addr(trace),
+                          _stream(stream)), "pm_ga_run")
+    return bc.value, gr.value, ev.value
+
+
+# --------------------------------------------------------------------------
+# Small object layer for Python callers
+# --------------------------------------------------------------------------
+
+class Instance:
+    """A p-median instance with its device-resident Pi'/Delta' tables."""
+
+    def __init__(self, d, p: int, device: int = 0, stream=None):
+        if isinstance(d, np.ndarray):
+            d = np.ascontiguousarray(d, dtype=np.int32)
+        n, m = int(d.shape[0]), int(d.shape[1])
+        self.handle = pm_instance_create(d, n, m, int(p), device, stream)
+        info = pm_instance_info(self.handle)
+        self.n, self.m, self.p, self.L, self.W, self.stride = (info[k] for k in ("n", "m", "p", "L", "W", "stride"))
+
+    def tables(self, stream=None):
+        pi = np.zeros((self.n, self.L), dtype=np.uint16)
+        de = np.zeros((self.n, self.L), dtype=np.int32)
+        pm_instance_tables(self.handle, pi, de, stream)
+        return pi, de
+
+    def eval(self, masks, costs=None, checked: bool = False, stream=None):
+        """Costs of a population; numpy in -> numpy out, CUDA tensor in -> CUDA tensor out."""
+        pop = int(masks.shape[0]) if masks.ndim == 2 else int(masks.shape[0] // self.W)
+        if costs is None:
+            if isinstance(masks, np.ndarray):
+                costs = np.zeros(pop, dtype=np.int64)
+            else:
+                import torch
+                costs = torch.empty(pop, dtype=torch.int64, device=masks.device)
+        pm_eval_population(self.handle, masks, pop, costs, int(checked), stream)
+        return costs
+
+    def close(self):
+        if self.handle:
+            pm_instance_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class GA:
+    """The device-resident genetic algorithm on an Instance."""
+
+    def __init__(self, inst: Instance, seed: int, pop: int, deme: int = 0, xover_rounds: int = -1,
+                 mut_tries: int = -1, saturation: int = 0, stream_id: int = 0, stream=None, _handle=None):
+        self.inst = inst
+        self.pop = int(pop)
+        self.handle = _handle if _handle is not None else pm_ga_create(
+            inst.handle, seed, pop, _params(deme, xover_rounds, mut_tries, saturation, stream_id), stream)
+
+    def step(self, gens: int, stream=None):
+        trace = np.zeros(max(int(gens), 1), dtype=np.int64)
+        before = self.result(stream)[1]
+        pm_ga_step(self.handle, int(gens), trace, stream)
+        ran = self.result(stream)[1] - before
+        return trace[:ran]
+
+    def result(self, stream=None):
+        mask = np.zeros(self.inst.W, dtype=np.uint32)
+        bc, gr, ev = pm_ga_result(self.handle, mask, stream)
+        return bc, gr, ev, mask
+
+    def population(self, stream=None):
+        masks = np.zeros((self.pop, self.inst.W), dtype=np.uint32)
+        costs = np.zeros(self.pop, dtype=np.int64)
+        pm_ga_population(self.handle, masks, costs, stream)
+        return masks, costs
+
+    def save(self, stream=None) -> bytes:
+        return pm_ga_save(self.handle, stream)
+
+    @classmethod
+    def load(cls, inst: Instance, blob: bytes, stream=None):
+        h = pm_ga_load(inst.handle, blob, stream)
+        import struct
+        P = struct.unpack_from("<q", blob, 8 + 4 + 4 + 8 * 3)[0]
+        return cls(inst, 0, P, _handle=h)
+
+    def close(self):
+        if self.handle:
+            pm_ga_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

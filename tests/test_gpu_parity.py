@@ -1,0 +1,263 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Tables and costs are integers, so the bar is bit-exact equality.  Cases span
+several tiles with ragged tails (m and pop not multiples of 32 or 128), the
+degenerate shapes (L = 2, p = 1, n = 1, all-equal distances, 31-bit
+distances), both fitness kernels (facility-major tiles and the row kernel for
+very large m) and, at the full workload sizes, sampled individuals checked by
+the direct evaluator.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1610_10061_gb300.inputs import (euclid_instance, graph_instance, masks_from_sets, paper_shape_instance,
+                                           random_masks, sets_from_masks)
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def pm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1610_10061_gb300 import build
+
+    build.build()
+    from paper_1610_10061_gb300 import pm as _pm
+
+    torch.cuda.set_device(0)
+    return _pm
+
+
+def to_dev(masks):
+    return torch.from_numpy(np.ascontiguousarray(masks).view(np.int32)).cuda()
+
+
+def _shapes():
+    rng = np.random.default_rng(0)
+    out = []
+    out.append(("n1", rng.integers(0, 50, size=(1, 2)).astype(np.int32), 1))
+    out.append(("ties", rng.integers(0, 3, size=(30, 70)).astype(np.int32), 9))
+    out.append(("allzero", np.zeros((9, 40), dtype=np.int32), 4))
+    out.append(("L2", rng.integers(0, 1000, size=(33, 65)).astype(np.int32), 64))
+    out.append(("p1", rng.integers(0, 1000, size=(40, 300)).astype(np.int32), 1))
+    out.append(("big31", rng.integers(0, 2**31 - 1, size=(20, 50)).astype(np.int32), 3))
+    out.append(("graph", graph_instance(100, 200, seed=0), 5))
+    out.append(("euclid", euclid_instance(700, seed=3)[:250], 17))
+    return out
+
+
+@pytest.mark.parametrize("name,d,p", _shapes(), ids=[s[0] for s in _shapes()])
+def test_tables_bit_exact(pm, name, d, p):
+    inst = pm.Instance(d, p)
+    pi, de = inst.tables()
+    opi, ode = oracle.tables(d, p)
+    np.testing.assert_array_equal(pi, opi)
+    np.testing.assert_array_equal(de, ode)
+    assert inst.L == d.shape[1] - p + 1 and inst.stride % 32 == 0
+    inst.close()
+
+
+def test_example1_through_the_abi(pm, example1):
+    C = np.array(example1["C"], dtype=np.int32)
+    inst = pm.Instance(C, 2)
+    pi, de = inst.tables()
+    np.testing.assert_array_equal(pi.astype(int) + 1, np.array(example1["PI_TRUNC"]))
+    np.testing.assert_array_equal(de, np.array(example1["DELTA_TRUNC"]))
+    import itertools
+
+    sets = list(itertools.combinations(range(4), 2))
+    costs = inst.eval(masks_from_sets(sets, 4), checked=True)
+    # the printed reduced polynomial of Example 1 evaluated at z = 1 - x
+    poly = {tuple(v - 1 for v in row[1:]): row[0] for row in example1["POLY"]}
+    expect = [sum(c for mono, c in poly.items() if not set(mono) & set(s)) for s in sets]
+    np.testing.assert_array_equal(costs, expect)
+
+
+@pytest.mark.parametrize("name,d,p", _shapes(), ids=[s[0] for s in _shapes()])
+@pytest.mark.parametrize("pop", [1, 31, 33, 129, 1000])
+def test_eval_bit_exact(pm, name, d, p, pop):
+    m = d.shape[1]
+    inst = pm.Instance(d, p)
+    masks = random_masks(pop, m, p, seed=pop + m)
+    expect = oracle.eval_direct(d, masks)
+    opi, ode = oracle.tables(d, p)
+    np.testing.assert_array_equal(expect, oracle.eval_scan(opi, ode, masks))
+    # host buffers (staged by the library)
+    np.testing.assert_array_equal(inst.eval(masks), expect)
+    # device buffers (used in place)
+    got = inst.eval(to_dev(masks))
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(got.cpu().numpy(), expect)
+    inst.close()
+
+
+def test_eval_empty_and_checked(pm):
+    d = graph_instance(60, 150, seed=2)
+    inst = pm.Instance(d, 6)
+    out = np.full(3, -7, dtype=np.int64)
+    pm.pm_eval_population(inst.handle, np.zeros((0, 2), dtype=np.uint32), 0, out)
+    assert (out == -7).all()
+    good = random_masks(40, 60, 6, seed=1)
+    np.testing.assert_array_equal(inst.eval(good, checked=True), oracle.eval_direct(d, good))
+    bad = good.copy()
+    bad[17, 0] ^= 1  # popcount p +- 1
+    with pytest.raises(pm.PMError) as e:
+        inst.eval(bad, checked=True)
+    assert e.value.status == 4
+    stray = good.copy()
+    keep = sets_from_masks(good[3:4], 60)[0][1:]  # p-1 open facilities ...
+    stray[3] = masks_from_sets([keep], 60)[0]
+    stray[3, 1] |= np.uint32(1) << np.uint32(31)  # ... plus bit 63, beyond m = 60
+    with pytest.raises(pm.PMError) as e:
+        inst.eval(stray, checked=True)
+    assert e.value.status == 4
+
+
+def test_negative_distance_rejected(pm):
+    d = np.ones((5, 6), dtype=np.int32)
+    d[3, 2] = -1
+    with pytest.raises(pm.PMError) as e:
+        pm.Instance(d, 2)
+    assert e.value.status == 2
+
+
+def test_device_distance_matrix(pm):
+    d = euclid_instance(300, seed=9)
+    dd = torch.from_numpy(d).cuda()
+    inst = pm.Instance(dd, 30)
+    opi, ode = oracle.tables(d, 30)
+    pi, de = inst.tables()
+    np.testing.assert_array_equal(pi, opi)
+    np.testing.assert_array_equal(de, ode)
+
+
+def test_row_kernel_for_very_large_m(pm):
+    """m = 60000: the facility-major tile exceeds shared memory, the row kernel runs; the sort uses global scratch."""
+    rng = np.random.default_rng(3)
+    m = 60000
+    d = rng.integers(0, 5000, size=(5, m)).astype(np.int32)
+    p = 40
+    inst = pm.Instance(d, p)
+    opi, ode = oracle.tables(d, p)
+    pi, de = inst.tables()
+    np.testing.assert_array_equal(pi, opi)
+    np.testing.assert_array_equal(de, ode)
+    masks = random_masks(70, m, p, seed=5)
+    np.testing.assert_array_equal(inst.eval(masks), oracle.eval_scan(opi, ode, masks))
+
+
+@pytest.mark.parametrize("p", [10, 100, 1000])
+def test_full_size_euclid10000_sampled(pm, p):
+    """n = m = 10000, pop 4096 (the fitness-throughput workload): sampled individuals and rows vs the oracle."""
+    d = paper_shape_instance(f"euclid10000_p{p}")["d"]
+    inst = pm.Instance(d, p)
+    masks = random_masks(4096, 10000, p, seed=p)
+    got = inst.eval(to_dev(masks))
+    torch.cuda.synchronize()
+    got = got.cpu().numpy()
+    rng = np.random.default_rng(p)
+    sample = rng.choice(4096, size=6, replace=False)
+    sample = np.concatenate([sample, [0, 4095]])
+    np.testing.assert_array_equal(got[sample], oracle.eval_direct(d, masks[sample]))
+    rows = rng.choice(10000, size=8, replace=False)
+    pi, de = inst.tables()
+    opi, ode = oracle.tables(d[rows], p)
+    np.testing.assert_array_equal(pi[rows], opi)
+    np.testing.assert_array_equal(de[rows], ode)
+    # property at full size: every cost is at least the sum of row minima
+    assert (got >= d.min(axis=1).astype(np.int64).sum()).all()
+
+
+# --------------------------------------------------------------------------
+# The GA: bit-exact trajectories
+# --------------------------------------------------------------------------
+
+def _ga_compare(pm, d, p, pop, gens, check_every=1, **kw):
+    inst = pm.Instance(d, p)
+    opi, ode = oracle.tables(d, p)
+    m = d.shape[1]
+    okw = dict(kw)
+    sid = okw.pop("stream_id", 0)
+    st, otrace, opops, ocosts = oracle.ga_run(opi, ode, m, p, seed=kw.get("seed", 0), P=pop, D=kw.get("deme") or None,
+                                              gens=gens, xover_rounds=kw.get("xover_rounds"),
+                                              mut_tries=kw.get("mut_tries"), saturation=kw.get("saturation", 0),
+                                              record=True, inst=sid)
+    ga = pm.GA(inst, seed=kw.get("seed", 0), pop=pop, deme=kw.get("deme") or 0,
+               xover_rounds=-1 if kw.get("xover_rounds") is None else kw["xover_rounds"],
+               mut_tries=-1 if kw.get("mut_tries") is None else kw["mut_tries"],
+               saturation=kw.get("saturation", 0), stream_id=sid)
+    done = 0
+    traces = []
+    while done < len(otrace):
+        k = min(check_every, len(otrace) - done)
+        traces.append(ga.step(k))
+        done += k
+        masks, costs = ga.population()
+        np.testing.assert_array_equal(masks, opops[done - 1], err_msg=f"population after generation {done}")
+        np.testing.assert_array_equal(costs, ocosts[done - 1], err_msg=f"costs after generation {done}")
+    np.testing.assert_array_equal(np.concatenate(traces), otrace)
+    bc, gr, ev, mask = ga.result()
+    assert bc == st.best_cost and ev == st.evals and gr == len(otrace)
+    np.testing.assert_array_equal(mask, st.best)
+    return ga, inst
+
+
+def test_ga_graph100_every_generation(pm):
+    w = paper_shape_instance("graph100")
+    _ga_compare(pm, w["d"], w["p"], 64, 40, check_every=1)
+
+
+def test_ga_graph100_full_run_reaches_brute_force_on_sub20(pm):
+    w = paper_shape_instance("graph100")
+    _ga_compare(pm, w["d"], w["p"], 64, 200, check_every=50)
+    s = paper_shape_instance("graph100_sub20")
+    best, _ = oracle.brute_force(s["d"], s["p"])
+    ga, _ = _ga_compare(pm, s["d"], s["p"], 64, 30, check_every=10)
+    assert ga.result()[0] == best
+
+
+def test_ga_graph900_first_generations(pm):
+    w = paper_shape_instance("graph900")
+    _ga_compare(pm, w["d"], w["p"], 1024, 2, check_every=1)
+
+
+@pytest.mark.parametrize("kw", [
+    dict(deme=16, seed=5),
+    dict(deme=2, seed=1),
+    dict(xover_rounds=0, mut_tries=3, seed=2),
+    dict(xover_rounds=7, mut_tries=0, deme=8, seed=3),
+    dict(stream_id=9, seed=4),
+])
+def test_ga_variants(pm, kw):
+    d = euclid_instance(77, seed=11)
+    _ga_compare(pm, d, 7, 128, 6, check_every=2, **kw)
+
+
+def test_ga_p1_and_saturation(pm):
+    d = graph_instance(45, 100, seed=4)
+    _ga_compare(pm, d, 1, 64, 5, check_every=5)
+    _ga_compare(pm, d, 3, 32, 300, check_every=300, deme=16, saturation=3)
+
+
+def test_ga_save_load_resume(pm):
+    d = graph_instance(100, 200, seed=0)
+    inst = pm.Instance(d, 5)
+    a = pm.GA(inst, seed=7, pop=64, deme=32)
+    ta = a.step(12)
+    b = pm.GA(inst, seed=7, pop=64, deme=32)
+    tb1 = b.step(5)
+    blob = b.save()
+    b.close()
+    c = pm.GA.load(inst, blob)
+    tb2 = c.step(7)
+    np.testing.assert_array_equal(np.concatenate([tb1, tb2]), ta)
+    ma, ca = a.population()
+    mc, cc = c.population()
+    np.testing.assert_array_equal(ma, mc)
+    np.testing.assert_array_equal(ca, cc)
+    assert a.result()[:3] == c.result()[:3]
