@@ -1,0 +1,421 @@
+#!/usr/bin/env python3
+"""GA fitness evaluations per second on one GB300 (or N, as independent replicas).
+
+A step is one generation of the device GA (population renewal with migration,
+evaluation, lg D crossover rounds and lg D mutation tries each followed by an
+evaluation with acceptance, deme bests, global best) on the workload
+``graph900``: a connected random graph with n = m = 900 nodes and 16200 edges
+(weights uniform in [1, 100]), all-pairs shortest-path distances, p = 90,
+population 1024 in demes of 256 -- the shape of the paper's OR-Library pmed40
+(Table 1), synthetic because the benchmark sets are not shipped.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
+Under torchrun each rank runs its own GA replica (stream id = rank): weak
+scaling with no collective on the data path.  Rank 0 prints one JSON line.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GA fitness evals/s"
+UNIT = "evals/s"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="graph900")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="ga", choices=["ga", "eval"],
+                    help="ga: GA generations (default); eval: one fitness evaluation pass of a random population")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(name):
+    from paper_1610_10061_gb300.inputs import paper_shape_instance
+
+    w = paper_shape_instance(name)
+    d, p, pop = w["d"], w["p"], w["pop"]
+    deme = min(pop, 256)
+    lg = deme.bit_length() - 1
+    desc = {
+        "graph900": "plain GA: connected random graph n=m=900, 16200 edges, weights U[1,100], APSP distances, "
+                    "p=90, pop 1024 in demes of 256",
+        "graph100": "plain GA: connected random graph n=m=100, 200 edges, weights U[1,100], APSP distances, "
+                    "p=5, pop 64 in one deme",
+    }.get(name, name)
+    return d, p, pop, deme, lg, desc
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            j = json.load(fh)
+        return float(j["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def fitness_source_hash():
+    h = hashlib.sha256()
+    for f in ("fitness.cu", "pm_common.cuh"):
+        with open(os.path.join(ROOT, "paper_1610_10061_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(name):
+    """DRAM bytes per launch of the scan kernel from the committed ncu summary, if it matches this source."""
+    path = os.path.join(ROOT, "profiles", f"fitness_scan_{name}.md")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as fh:
+        for line in fh:
+            if ":" in line and line.strip().startswith("- "):
+                k, v = line.strip()[2:].split(":", 1)
+                vals[k.strip()] = v.strip()
+    if vals.get("source_hash") != fitness_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(d, p, pop, deme, budget_s=12.0):
+    """The oracle GA (single-threaded C, as it stands) on a bounded number of generations of the same workload."""
+    import numpy as np
+
+    import oracle
+
+    m = d.shape[1]
+    pi, de = oracle.tables(d, p)
+    st = None
+    gens = 0
+    t0 = time.perf_counter()
+    while True:
+        st, _, _, _ = oracle.ga_run(pi, de, m, p, seed=0, P=pop, D=deme, gens=1, state=st)
+        gens += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": st.evals / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{gens} generations of the same GA (pop {pop}, demes of {deme}) on the same instance, "
+                      f"{st.evals} evaluations in {dt:.1f} s, single-threaded C oracle (gcc -O2)"}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+
+    d, p, pop, deme, lg, desc = workload(args.workload)
+    m = d.shape[1]
+    pi, de = oracle.tables(d, p)
+    st = None
+    for _ in range(args.warmup):
+        st, _, _, _ = oracle.ga_run(pi, de, m, p, seed=0, P=pop, D=deme, gens=1, state=st)
+    e0 = st.evals if st else 0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        st, _, _, _ = oracle.ga_run(pi, de, m, p, seed=0, P=pop, D=deme, gens=1, state=st)
+    dt = time.perf_counter() - t0
+    evals = st.evals - e0
+    value = evals / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / max(args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": args.workload, "description": desc, "n": int(d.shape[0]), "m": m, "p": p,
+                   "pop": pop, "deme": deme, "step": "one GA generation", "parallelism": "none (host CPU)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1,
+                         "sample": f"{args.steps} generations timed after {args.warmup} warm-up generations, "
+                                   "single-threaded C oracle (gcc -O2)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_1610_10061_gb300 import build
+
+    if rank == 0:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_1610_10061_gb300 import pm
+    from paper_1610_10061_gb300.inputs import random_masks
+
+    d, p, pop, deme, lg, desc = workload(args.workload)
+    n, m = d.shape
+    stream = torch.cuda.current_stream()
+    inst = pm.Instance(d, p, device=local, stream=stream.cuda_stream)
+    ga = pm.GA(inst, seed=0, pop=pop, deme=deme, stream_id=rank, stream=stream.cuda_stream)
+    info = ga.info()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+
+    for _ in range(args.warmup):
+        pm.pm_ga_step(ga.handle, 1, None, stream.cuda_stream)
+    torch.cuda.synchronize()
+    _, g0, e0 = pm.pm_ga_result(ga.handle, None, stream.cuda_stream)
+
+    clocks = Clocks(local)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for k in range(args.steps):
+        flush.zero_()  # L2 flush between timed steps (outside the events)
+        starts[k].record(stream)
+        pm.pm_ga_step(ga.handle, 1, None, stream.cuda_stream)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = float(sum(step_ms))
+    best, g1, e1 = pm.pm_ga_result(ga.handle, None, stream.cuda_stream)
+    evals = e1 - e0
+    assert g1 - g0 == args.steps
+    tot_evals, max_ms = evals, total_ms
+    if world > 1:
+        t = torch.tensor([float(evals), total_ms], dtype=torch.float64, device="cuda")
+        ev_t = t[:1].clone()
+        ms_t = t[1:].clone()
+        torch.distributed.all_reduce(ev_t, op=torch.distributed.ReduceOp.SUM)
+        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
+        tot_evals, max_ms = float(ev_t.item()), float(ms_t.item())
+    value = tot_evals / (max_ms / 1000.0)
+
+    # ---- roofline of the dominant kernel: the fitness evaluation at the same shape, timed alone ----
+    masks = random_masks(pop, m, p, seed=123)
+    dmask = torch.from_numpy(masks.view(np.int32)).cuda()
+    dcost = torch.empty(pop, dtype=torch.int64, device="cuda")
+    for _ in range(3):
+        pm.pm_eval_population(inst.handle, dmask, pop, dcost, 0, stream.cuda_stream)
+    reps = 30
+    es = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+    ee = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+    for k in range(reps):
+        flush.zero_()
+        es[k].record(stream)
+        pm.pm_eval_population(inst.handle, dmask, pop, dcost, 0, stream.cuda_stream)
+        ee[k].record(stream)
+    torch.cuda.synchronize()
+    eval_ms = statistics.mean(a.elapsed_time(b) for a, b in zip(es, ee))
+    W = (m + 31) // 32
+    ek = (m + 1) / (p + 1)  # mean ranks scanned per client for a uniform random p-subset
+    bytes_per_eval = n * ek * 6 + W * 4 + 8
+    alg_bytes = pop * bytes_per_eval
+    peak, peak_kind = measured_peaks()
+    achieved = alg_bytes / (eval_ms / 1000.0) / 1e9
+    traffic = profiled_traffic(args.workload)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": "fitness evaluation (transpose + column scan + split reduction)",
+                "peak_source": f"{peak_kind} burst copy bandwidth",
+                "launch_ms": eval_ms, "alg_bytes_per_launch": alg_bytes,
+                "note": "algorithmic bytes = pop * (n*(m+1)/(p+1)*6 + 4W + 8): the Pi'/Delta' prefix each "
+                        "evaluation scans; the tables are L2-resident at this size"}
+
+    # ---- end to end through the C ABI with host buffers ----
+    e2e = None
+    if rank == 0 or True:
+        dh = torch.from_numpy(d).pin_memory()
+        best_mask = torch.zeros(W, dtype=torch.int32).pin_memory()
+        trace = torch.zeros(args.steps, dtype=torch.int64).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = pm.pm_instance_create(dh, n, m, p, local, stream.cuda_stream)
+        bc, gr, ev = pm.pm_ga_run(h, 0, pop, args.steps, pm._params(deme=deme, stream_id=rank), best_mask, trace,
+                                  stream.cuda_stream)
+        pm.pm_instance_destroy(h)
+        t1 = time.perf_counter()
+        e2e = {"value": ev / (t1 - t0), "unit": UNIT,
+               "h2d_bytes_per_step": n * m * 4 / args.steps,
+               "d2h_bytes_per_step": (W * 4 + 8 * 3) / args.steps + 8,
+               "note": f"pm_instance_create from pinned host d + pm_ga_run({args.steps} generations) with host "
+                       "best mask and trace; copies amortised over the steps of one job"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(d, p, pop, deme)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": args.workload, "description": desc, "n": int(n), "m": int(m), "p": int(p),
+                       "pop": pop, "deme": deme, "xover_rounds": info["xover_rounds"],
+                       "mut_tries": info["mut_tries"], "step": "one GA generation (one pm_ga_step graph launch)",
+                       "l2": "flushed between timed steps (512 MiB write outside the events)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "evals": int(tot_evals), "best_cost": int(best),
+            "gpu_launches": int((info["kernels_per_generation"] + info["kernels_per_step_call"]) * args.steps),
+            "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_eval_mode(args):
+    """One evaluation pass of `pop` uniformly random p-subsets per step (the fitness-throughput workload)."""
+    import numpy as np
+    import torch
+
+    from paper_1610_10061_gb300 import build
+
+    build.build()
+    from paper_1610_10061_gb300 import pm
+    from paper_1610_10061_gb300.inputs import paper_shape_instance, random_masks
+
+    w = paper_shape_instance(args.workload)
+    d, p, pop = w["d"], w["p"], w["pop"]
+    n, m = d.shape
+    W = (m + 31) // 32
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    inst = pm.Instance(d, p, stream=stream.cuda_stream)
+    masks = random_masks(pop, m, p, seed=123)
+    dmask = torch.from_numpy(masks.view(np.int32)).cuda()
+    dcost = torch.empty(pop, dtype=torch.int64, device="cuda")
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        pm.pm_eval_population(inst.handle, dmask, pop, dcost, 0, stream.cuda_stream)
+    es = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ee = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = Clocks(0)
+    torch.cuda.synchronize()
+    clocks.start()
+    for k in range(args.steps):
+        flush.zero_()
+        es[k].record(stream)
+        pm.pm_eval_population(inst.handle, dmask, pop, dcost, 0, stream.cuda_stream)
+        ee[k].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = [a.elapsed_time(b) for a, b in zip(es, ee)]
+    mean_ms = statistics.mean(ms)
+    ek = (m + 1) / (p + 1)
+    alg_bytes = pop * (n * ek * 6 + W * 4 + 8)
+    peak, peak_kind = measured_peaks()
+    achieved = alg_bytes / (mean_ms / 1000) / 1e9
+    line = {"metric": "fitness evals/s (one evaluation pass)", "value": pop / (mean_ms / 1000), "unit": UNIT,
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_ms,
+            "ms_min": min(ms), "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "n": int(n), "m": int(m), "p": int(p), "pop": pop,
+                       "step": "pm_eval_population of a uniform random population (device buffers)",
+                       "l2": "flushed between timed steps"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": profiled_traffic(args.workload),
+                         "alg_bytes_per_launch": alg_bytes, "peak_source": f"{peak_kind} burst copy bandwidth"},
+            "gpu_launches": 3 * args.steps, "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    elif args.mode == "eval":
+        run_eval_mode(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

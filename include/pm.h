@@ -205,6 +205,15 @@ PM_API pm_status pm_ga_load(pm_instance *inst, const void *buf, size_t len, void
 PM_API pm_status pm_ga_destroy(pm_ga *ga);
 
 /*
+ * pm_ga_info -- the resolved parameters of a GA (any output may be NULL):
+ * pop, deme size D, crossover rounds, mutation tries, and the number of
+ * library kernels one generation launches (the graph body), plus the number
+ * launched once per pm_ga_step call (outside the body).  No device work.
+ */
+PM_API pm_status pm_ga_info(const pm_ga *ga, int64_t *pop, int64_t *deme, int32_t *xover_rounds, int32_t *mut_tries,
+                            int64_t *kernels_per_generation, int64_t *kernels_per_step_call);
+
+/*
  * pm_ga_run -- convenience: create, run `gens` generations, report, destroy.
  *   best_cost  receives the best cost; best_mask (W words, nullable, host or
  *   device); gens_run, evals nullable; trace nullable (gens entries).

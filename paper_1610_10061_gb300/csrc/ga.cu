@@ -788,6 +788,28 @@ extern "C" pm_status pm_ga_load(pm_instance *inst, const void *buf, size_t len, 
     return PM_OK;
 }
 
+extern "C" pm_status pm_ga_info(const pm_ga *ga, int64_t *pop, int64_t *deme, int32_t *xover_rounds,
+                                int32_t *mut_tries, int64_t *kernels_per_generation, int64_t *kernels_per_step_call)
+{
+    if (!ga)
+        return PM_ERR_INVALID_ARG;
+    const int64_t per_eval = pm_plan_kernels(ga->plan);
+    const int64_t rounds = ga->inst->p / 2 > 0 ? ga->R : 0;
+    if (pop)
+        *pop = ga->P;
+    if (deme)
+        *deme = ga->D;
+    if (xover_rounds)
+        *xover_rounds = ga->R;
+    if (mut_tries)
+        *mut_tries = ga->Q;
+    if (kernels_per_generation)
+        *kernels_per_generation = 1 + per_eval + rounds * (1 + per_eval) + ga->Q * (1 + per_eval) + 2;
+    if (kernels_per_step_call)
+        *kernels_per_step_call = 2;  // k_ga_begin and the gate
+    return PM_OK;
+}
+
 extern "C" pm_status pm_ga_destroy(pm_ga *ga)
 {
     ga_free(ga);

@@ -68,6 +68,8 @@ struct pm_instance {
 
 // Choose the tile configuration for `pop` individuals on `inst`.
 pm_eval_plan pm_plan_eval(const pm_instance *inst, int64_t pop);
+// Kernels one evaluation launches under the plan.
+static inline int64_t pm_plan_kernels(const pm_eval_plan &plan) { return plan.groups ? 3 : 2; }
 // Bytes of int64 partial sums the plan needs.
 size_t pm_plan_partial_bytes(const pm_eval_plan &plan, int64_t pop);
 

@@ -60,6 +60,7 @@ _SIGS = {
     "pm_ga_save": ([_P, _P, ctypes.POINTER(ctypes.c_size_t), _P], _S),
     "pm_ga_load": ([_P, _P, ctypes.c_size_t, _P, _PP], _S),
     "pm_ga_destroy": ([_P], _S),
+    "pm_ga_info": ([_P, _P, _P, _P, _P, _P, _P], _S),
     "pm_ga_run": ([_P, ctypes.c_uint64, _I64, _I64, ctypes.POINTER(pm_ga_params), _P, _P, _P, _P, _P, _P], _S),
 }
 for _name, (_args, _res) in _SIGS.items():
@@ -180,6 +181,15 @@ def pm_ga_load(inst, blob: bytes, stream=None):
     return out
 
 
+def pm_ga_info(ga):
+    pop, deme, kg, ks = (ctypes.c_int64() for _ in range(4))
+    xr, mt = ctypes.c_int32(), ctypes.c_int32()
+    _check(_lib.pm_ga_info(ga, ctypes.byref(pop), ctypes.byref(deme), ctypes.byref(xr), ctypes.byref(mt),
+                           ctypes.byref(kg), ctypes.byref(ks)), "pm_ga_info")
+    return dict(pop=pop.value, deme=deme.value, xover_rounds=xr.value, mut_tries=mt.value,
+                kernels_per_generation=kg.value, kernels_per_step_call=ks.value)
+
+
 def pm_ga_destroy(ga):
     _check(_lib.pm_ga_destroy(ga), "pm_ga_destroy")
 
@@ -268,6 +278,9 @@ class GA:
 
     def save(self, stream=None) -> bytes:
         return pm_ga_save(self.handle, stream)
+
+    def info(self):
+        return pm_ga_info(self.handle)
 
     @classmethod
     def load(cls, inst: Instance, blob: bytes, stream=None):
