@@ -127,6 +127,35 @@ PM_API pm_status pm_instance_tables(const pm_instance *inst, uint16_t *pi_out, i
 PM_API pm_status pm_eval_population(pm_instance *inst, const uint32_t *masks, int64_t pop, int64_t *costs, int checked,
                              void *stream);
 
+/*
+ * pm_eval_population_noalloc -- the same evaluation as pm_eval_population,
+ * for callers that cannot allocate device memory.  The paper has no
+ * counterpart; this entry point exists for the library's users.
+ *
+ * Some callers may not call cudaMalloc at the time they evaluate: a serving
+ * process whose framework has already reserved nearly all device memory for
+ * its own pool, a real-time loop that must not hit the allocator's locks and
+ * implicit synchronisation, or a component that owns no memory budget of its
+ * own.  This call allocates nothing: its scratch (the facility-major copy of
+ * the population and the per-split partial sums) lives in one fixed
+ * 8 MiB array compiled into the library, which every GPU that loads the
+ * library keeps for the life of the process.
+ *   masks, costs  device memory only (PM_ERR_INVALID_ARG for host pointers);
+ *                 layouts as for pm_eval_population.
+ *   pop           >= 0; the scratch needed is about pop * W * 4 bytes plus
+ *                 8 bytes per individual per client split; if it exceeds the
+ *                 8 MiB array the call returns PM_ERR_INVALID_ARG and launches
+ *                 nothing.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  All
+ * calls share the one array and each call overwrites it, so calls whose work
+ * overlaps on the GPU (different streams, or different instances at the same
+ * time) race and must be serialised by the caller.  Asynchronous on
+ * `stream`.  Errors: PM_ERR_INVALID_ARG, PM_ERR_CUDA.
+ */
+PM_API pm_status pm_eval_population_noalloc(pm_instance *inst, const uint32_t *masks, int64_t pop, int64_t *costs,
+                                            void *stream);
+
 /* ------------------------------------------------------------------------
  * The genetic algorithm (Sections 3.1, 3.2.2, 4.3-4.5) on the device.
  * ------------------------------------------------------------------------ */

@@ -482,3 +482,64 @@ pm_status pm_launch_mask_check(const pm_instance *inst, const uint32_t *masks, i
     PM_CUDA(cudaGetLastError());
     return PM_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Evaluation that allocates nothing (no counterpart in the paper): the
+// scratch of pm_launch_eval lives in a fixed array compiled into the library.
+// Layout inside the array: [0, 256) error word, then the facility-major
+// population copy, then the partial sums, each 256-byte aligned.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr size_t kNoAllocScratchBytes = size_t(8) << 20;  // 8 MiB per GPU
+constexpr int kNoAllocMaxDevices = 64;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on `device` (which must be current);
+// looked up once per device.
+pm_status noalloc_scratch(int device, unsigned char **out)
+{
+    if (device < 0 || device >= kNoAllocMaxDevices)
+        return PM_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> guard(g_noalloc_mu);
+    if (!g_noalloc_addr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || p == nullptr) {
+            pm_note_cuda_error(e, "cudaGetSymbolAddress(g_noalloc_scratch)", __FILE__, __LINE__);
+            return PM_ERR_CUDA;
+        }
+        g_noalloc_addr[device] = p;
+    }
+    *out = static_cast<unsigned char *>(g_noalloc_addr[device]);
+    return PM_OK;
+}
+}  // namespace
+
+extern "C" pm_status pm_eval_population_noalloc(pm_instance *inst, const uint32_t *masks, int64_t pop, int64_t *costs,
+                                                void *stream)
+{
+    if (!inst || pop < 0)
+        return PM_ERR_INVALID_ARG;
+    if (pop == 0)
+        return PM_OK;
+    if (!masks || !costs || !pm_is_device_ptr(masks) || !pm_is_device_ptr(costs))
+        return PM_ERR_INVALID_ARG;
+    const pm_eval_plan plan = pm_plan_eval(inst, pop);
+    const size_t cols = (size_t)pm_round_up((int64_t)pm_plan_column_bytes(inst, plan), 256);
+    const size_t part = (size_t)pm_round_up((int64_t)pm_plan_partial_bytes(plan, pop), 256);
+    if (256 + cols + part > kNoAllocScratchBytes)
+        return PM_ERR_INVALID_ARG;
+    PM_CUDA(cudaSetDevice(inst->device));
+    unsigned char *base = nullptr;
+    PM_TRY(noalloc_scratch(inst->device, &base));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int *err = reinterpret_cast<int *>(base);
+    uint32_t *colT = reinterpret_cast<uint32_t *>(base + 256);
+    int64_t *partials = reinterpret_cast<int64_t *>(base + 256 + cols);
+    // the array keeps the previous call's contents: the error word must start at zero
+    PM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+    pm_accept_args acc;
+    return pm_launch_eval(inst, plan, masks, pop, nullptr, costs, partials, colT, err, acc, s);
+}

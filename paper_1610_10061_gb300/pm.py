@@ -53,6 +53,7 @@ _SIGS = {
     "pm_instance_info": ([_P, _P, _P, _P, _P, _P, _P], _S),
     "pm_instance_tables": ([_P, _P, _P, _P], _S),
     "pm_eval_population": ([_P, _P, _I64, _P, ctypes.c_int, _P], _S),
+    "pm_eval_population_noalloc": ([_P, _P, _I64, _P, _P], _S),
     "pm_ga_create": ([_P, ctypes.c_uint64, _I64, ctypes.POINTER(pm_ga_params), _P, _PP], _S),
     "pm_ga_step": ([_P, _I64, _P, _P], _S),
     "pm_ga_result": ([_P, _P, _P, _P, _P, _P], _S),
@@ -138,6 +139,11 @@ def pm_instance_tables(inst, pi_out, delta_out, stream=None):
 def pm_eval_population(inst, masks, pop: int, costs, checked: int = 0, stream=None):
     _check(_lib.pm_eval_population(inst, _addr(masks), pop, _addr(costs), int(checked), _stream(stream)),
            "pm_eval_population")
+
+
+def pm_eval_population_noalloc(inst, masks, pop: int, costs, stream=None):
+    _check(_lib.pm_eval_population_noalloc(inst, _addr(masks), pop, _addr(costs), _stream(stream)),
+           "pm_eval_population_noalloc")
 
 
 def _params(deme=0, xover_rounds=-1, mut_tries=-1, saturation=0, stream_id=0):
