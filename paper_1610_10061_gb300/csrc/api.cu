@@ -14,8 +14,10 @@ void pm_note_cuda_error(cudaError_t e, const char *what, const char *file, int l
         std::fprintf(stderr, "libpmgpu: %s failed at %s:%d: %s\n", what, file, line, cudaGetErrorString(e));
 }
 
-pm_status pm_dbuf::reserve(size_t want)
+pm_status pm_dbuf::reserve(size_t want, bool *fresh)
 {
+    if (fresh)
+        *fresh = false;
     if (want <= bytes && ptr)
         return PM_OK;
     release();
@@ -28,6 +30,8 @@ pm_status pm_dbuf::reserve(size_t want)
         return e == cudaErrorMemoryAllocation ? PM_ERR_OOM : PM_ERR_CUDA;
     }
     bytes = sz;
+    if (fresh)
+        *fresh = true;
     return PM_OK;
 }
 
@@ -87,6 +91,7 @@ static void destroy_instance(pm_instance *inst)
     inst->stage_masks.release();
     inst->stage_costs.release();
     inst->partials.release();
+    inst->tickets.release();
     inst->columns.release();
     inst->flag.release();
     inst->err.release();
@@ -240,11 +245,18 @@ extern "C" pm_status pm_eval_population(pm_instance *inst, const uint32_t *masks
             return PM_ERR_MASK;
     }
     const pm_eval_plan plan = pm_plan_eval(inst, pop);
-    PM_TRY(inst->partials.reserve(pm_plan_partial_bytes(plan, pop)));
+    bool fresh = false;
+    PM_TRY(inst->partials.reserve(pm_plan_partial_bytes(plan, pop), &fresh));
+    if (fresh)  // column-kernel accumulators start at zero; launches leave them zero
+        PM_CUDA(cudaMemsetAsync(inst->partials.ptr, 0, inst->partials.bytes, s));
+    PM_TRY(inst->tickets.reserve(pm_plan_ticket_bytes(plan), &fresh));
+    if (fresh)
+        PM_CUDA(cudaMemsetAsync(inst->tickets.ptr, 0, inst->tickets.bytes, s));
     PM_TRY(inst->columns.reserve(std::max<size_t>(pm_plan_column_bytes(inst, plan), 256)));
     pm_accept_args acc;
     PM_TRY(pm_launch_eval(inst, plan, m_dev, pop, nullptr, c_dev, static_cast<int64_t *>(inst->partials.ptr),
-                          static_cast<uint32_t *>(inst->columns.ptr), static_cast<int *>(inst->err.ptr), acc, s));
+                          static_cast<int *>(inst->tickets.ptr), static_cast<uint32_t *>(inst->columns.ptr),
+                          static_cast<int *>(inst->err.ptr), acc, s));
     if (!costs_dev || checked) {
         if (!costs_dev)
             PM_CUDA(cudaMemcpyAsync(costs, c_dev, cost_bytes, cudaMemcpyDeviceToHost, s));

@@ -9,28 +9,35 @@
 // GB300 design ("column" kernel):
 //  * The population is first transposed into a facility-major layout: for a
 //    tile of 32*G individuals, word (j, g) holds bit b = "individual
-//    tile*32G + 32g + b has facility j open".  One 32-bit shared-memory load
-//    then tests one facility for 32 individuals.
+//    tile*32G + 32g + b has facility j open".  One shared-memory load of the
+//    G words of facility j (128 bits for G = 4) tests 32G individuals.
 //  * A CTA owns one tile; its m x G words are brought into shared memory with
-//    one TMA bulk copy (cp.async.bulk + mbarrier).  Grid.y splits the clients.
+//    TMA bulk copies (cp.async.bulk + mbarrier).  Grid.y splits the clients.
 //  * A warp takes one client at a time and walks its row 32 ranks per step:
-//    lane r loads Pi'[r] and Delta'[r] (coalesced), a warp scan turns the
-//    increments into running sums (the prefix of Delta' up to rank r), and
-//    for each group g lane r loads the 32-individual word of facility
-//    Pi'[r].  The 32x32 bit block (rank x individual) is transposed with
-//    five shuffles, so lane b finds its individual's first open rank with one
-//    find-first-set and takes that rank's running sum with one shuffle.
-//    Individuals resolved in a step leave the active set; the row walk ends
-//    when no individual of the tile is active.  Steps where no active
-//    individual has an open facility cost one load, one AND and one vote.
-//  * Per-lane int64 sums are combined in shared memory and written as one
-//    partial sum per (client split, individual); a second kernel adds the
-//    splits (integer, so the order does not matter) and applies the
-//    epilogue (plain store, or the GA's strict-improvement acceptance).
+//    lane r holds Pi'[r] and Delta'[r] (coalesced loads, the next step and
+//    the next client's first step prefetched into registers).  If no still
+//    active individual of the tile has facility Pi'[r] open at any lane, the
+//    step only adds the 32 increments to a running carry (one warp
+//    reduction).  Otherwise a warp scan turns the increments into running
+//    sums (the sum of Delta' up to rank r), and each group with hits
+//    resolves its individuals' first open ranks: with few hit lanes by
+//    walking those lanes in rank order, else by transposing the 32 x 32 bit
+//    block (rank x individual) with five shuffles so lane b finds its
+//    individual's first open rank with one find-first-set.  Resolved
+//    individuals leave the active set; the walk ends when none is left.
+//  * Per-lane int64 sums are combined in shared memory.  With one client
+//    split the CTA applies the epilogue itself; otherwise every CTA adds its
+//    sums into per-individual int64 accumulators (integers, so the order of
+//    the atomic additions does not matter) and the last CTA of the tile (an
+//    atomic ticket) reads the totals, zeroes the accumulators for the next
+//    launch and applies the epilogue: a plain store of the cost, or the GA's
+//    acceptance (replace the current individual iff the candidate is
+//    strictly cheaper).
 //
 // For very large m (the facility-major tile does not fit in shared memory)
 // a "row" kernel keeps each individual's own bitset in shared memory and
-// resolves one individual per warp step with a ballot.
+// resolves one individual per warp step with a ballot; a separate kernel
+// adds its splits.
 
 #include <cstdio>
 
@@ -40,6 +47,7 @@ namespace {
 
 constexpr int kMaxG = 4;
 constexpr uint32_t kSpinLimit = 1u << 22;  // bounded mbarrier wait (a few seconds at most)
+constexpr int kSparseLanes = 3;            // resolve by walking hit lanes up to this many
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -79,6 +87,25 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
+// The G words of facility j (groups 0..G-1) with one shared-memory load.
+template <int G>
+__device__ __forceinline__ void load_cols(const uint32_t *cb, uint32_t j, uint32_t (&w)[G])
+{
+    if constexpr (G == 4) {
+        const uint4 v = reinterpret_cast<const uint4 *>(cb)[j];
+        w[0] = v.x;
+        w[1] = v.y;
+        w[2] = v.z;
+        w[3] = v.w;
+    } else if constexpr (G == 2) {
+        const uint2 v = reinterpret_cast<const uint2 *>(cb)[j];
+        w[0] = v.x;
+        w[1] = v.y;
+    } else {
+        w[0] = cb[j];
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Row-major population -> facility-major tiles.
 // colT[tile][j][g] (j < 32W) = bits over individuals tile*32G + 32g + b.
@@ -103,144 +130,272 @@ __global__ void k_pop_to_columns(const uint32_t *__restrict__ masks, int64_t pop
     }
 }
 
+struct ScanEpilogue {
+    int mode;                    // 0: store costs; 1: accept strictly cheaper candidates
+    int64_t *costs;              // mode 0 (and optionally mode 1): candidate costs
+    int64_t *cur_cost;           // mode 1
+    uint32_t *cur_masks;         // mode 1
+    const uint32_t *cand_masks;  // mode 1
+    uint8_t *improved;           // mode 1, nullable
+    int32_t W;
+};
+
 // ---------------------------------------------------------------------------
-// The column scan kernel.
+// The column scan kernel (with the split reduction and epilogue fused).
+// Persistent: CTA b takes work items b, b + gridDim.x, ...; item = split *
+// tiles + tile, so the CTAs running at the same time walk the same clients
+// for different tiles and the rows they stream are shared through L2.
 // ---------------------------------------------------------------------------
 template <int G>
 __global__ void __launch_bounds__(1024) k_scan_columns(const uint16_t *__restrict__ pi,
                                                        const int32_t *__restrict__ delta, int64_t n, int32_t L,
                                                        int64_t stride, const uint32_t *__restrict__ colT,
                                                        int32_t W, int64_t pop, const uint32_t *__restrict__ active,
-                                                       int64_t clients_per_split,
+                                                       int64_t tiles, int64_t clients_per_split, int splits,
                                                        unsigned long long *__restrict__ partial,
-                                                       int *__restrict__ err)
+                                                       int *__restrict__ tickets, int *__restrict__ err,
+                                                       ScanEpilogue ep)
 {
     extern __shared__ __align__(128) uint32_t colbits[];  // [32W][G]
     __shared__ unsigned long long acc_s[G * 32];
     __shared__ uint32_t a0_s[G];
     __shared__ __align__(8) uint64_t bar;
+    __shared__ int last_s;
 
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
-    const int64_t tile = blockIdx.x;
-    const int split = blockIdx.y;
-    const int64_t ind0 = tile * 32 * G;
     const uint32_t tile_bytes = (uint32_t)W * 32u * G * 4u;
+    const int64_t items = tiles * splits;
 
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        mbar_arrive_expect_tx(&bar, tile_bytes);
-        const char *src = reinterpret_cast<const char *>(colT + tile * (int64_t)W * 32 * G);
-        char *dst = reinterpret_cast<char *>(colbits);
-        for (uint32_t off = 0; off < tile_bytes; off += 32768u) {
-            const uint32_t sz = (tile_bytes - off) < 32768u ? (tile_bytes - off) : 32768u;
-            bulk_g2s(dst + off, src + off, sz, &bar);
-        }
-    }
-    if (warp < G) {
-        const int64_t t = ind0 + 32 * warp + lane;
-        const bool on = (t < pop) && (active == nullptr || ((__ldg(active + (t >> 5)) >> (t & 31)) & 1u));
-        const uint32_t b = __ballot_sync(PM_FULL_MASK, on);
-        if (lane == 0)
-            a0_s[warp] = b;
-    }
-    for (int i = threadIdx.x; i < G * 32; i += blockDim.x)
-        acc_s[i] = 0ull;
-    // bounded wait for the tile (every thread waits; phase 0)
-    {
-        uint32_t spins = 0;
-        while (!mbar_try_wait(&bar, 0)) {
-            if (++spins > kSpinLimit) {
-                if (threadIdx.x == 0)
-                    atomicExch(err, (int)PM_ERR_TIMEOUT);
-                // the copy may still land: wait once more, again bounded, then leave
-                uint32_t extra = 0;
-                while (!mbar_try_wait(&bar, 0) && ++extra < kSpinLimit) {
-                }
-                return;
+
+    uint32_t phase = 0;
+    int64_t loaded_tile = -1;
+    for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
+        const int64_t tile = item % tiles;
+        const int split = (int)(item / tiles);
+        const int64_t ind0 = tile * 32 * G;
+        const bool reload = tile != loaded_tile;
+        if (reload && threadIdx.x == 0) {
+            mbar_arrive_expect_tx(&bar, tile_bytes);
+            const char *src = reinterpret_cast<const char *>(colT + tile * (int64_t)W * 32 * G);
+            char *dst = reinterpret_cast<char *>(colbits);
+            for (uint32_t off = 0; off < tile_bytes; off += 32768u) {
+                const uint32_t sz = (tile_bytes - off) < 32768u ? (tile_bytes - off) : 32768u;
+                bulk_g2s(dst + off, src + off, sz, &bar);
             }
         }
-    }
-    __syncthreads();
+        if (warp < G) {
+            const int64_t t = ind0 + 32 * warp + lane;
+            const bool on = (t < pop) && (active == nullptr || ((__ldg(active + (t >> 5)) >> (t & 31)) & 1u));
+            const uint32_t b = __ballot_sync(PM_FULL_MASK, on);
+            if (lane == 0)
+                a0_s[warp] = b;
+        }
+        for (int i = threadIdx.x; i < G * 32; i += blockDim.x)
+            acc_s[i] = 0ull;
 
-    uint32_t a0[G];
-    uint32_t any0 = 0;
-#pragma unroll
-    for (int g = 0; g < G; ++g) {
-        a0[g] = a0_s[g];
-        any0 |= a0[g];
-    }
-    unsigned long long acc[G];
-#pragma unroll
-    for (int g = 0; g < G; ++g)
-        acc[g] = 0ull;
+        // first chunks of this warp's first two clients, loaded while the tile lands
+        const int64_t c_begin = (int64_t)split * clients_per_split;
+        const int64_t c_end = (c_begin + clients_per_split < n) ? c_begin + clients_per_split : n;
+        auto load = [&](int64_t cc, int base, uint32_t &j, int32_t &dl) {
+            const int r = base + lane;
+            if (cc < c_end && r < L) {
+                j = __ldg(pi + cc * stride + r);
+                dl = __ldg(delta + cc * stride + r);
+            } else {
+                j = 0;
+                dl = 0;
+            }
+        };
+        int64_t c = c_begin + warp;
+        uint32_t j_cur, j_nxt, j_nc;
+        int32_t d_cur, d_nxt, d_nc;
+        load(c, 0, j_cur, d_cur);
+        load(c, 32, j_nxt, d_nxt);
+        load(c + nwarps, 0, j_nc, d_nc);
 
-    const int64_t c_begin = (int64_t)split * clients_per_split;
-    const int64_t c_end = (c_begin + clients_per_split < n) ? c_begin + clients_per_split : n;
-    if (any0) {
-        for (int64_t c = c_begin + warp; c < c_end; c += nwarps) {
-            const uint16_t *prow = pi + c * stride;
-            const int32_t *drow = delta + c * stride;
+        if (reload) {
+            // bounded wait for the tile (every thread waits)
+            uint32_t spins = 0;
+            while (!mbar_try_wait(&bar, phase)) {
+                if (++spins > kSpinLimit) {
+                    if (threadIdx.x == 0)
+                        atomicExch(err, (int)PM_ERR_TIMEOUT);
+                    uint32_t extra = 0;  // the copy may still land: wait once more, bounded, then leave
+                    while (!mbar_try_wait(&bar, phase) && ++extra < kSpinLimit) {
+                    }
+                    return;
+                }
+            }
+            phase ^= 1u;
+            loaded_tile = tile;
+        }
+        __syncthreads();
+
+        uint32_t a0[G];
+        uint32_t any0 = 0;
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            a0[g] = a0_s[g];
+            any0 |= a0[g];
+        }
+        unsigned long long acc[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+            acc[g] = 0ull;
+
+        if (any0 && c < c_end) {
             uint32_t a[G];
 #pragma unroll
             for (int g = 0; g < G; ++g)
                 a[g] = a0[g];
             int32_t carry = 0;
-            for (int base = 0; base < L; base += 32) {
-                const int r = base + lane;
-                uint32_t j = 0;
-                int32_t dl = 0;
-                if (r < L) {
-                    j = __ldg(prow + r);
-                    dl = __ldg(drow + r);
-                }
-                // running sum of Delta' up to rank r: the sorted distance at rank r
-                int32_t cs = dl;
+            int base = 0;
+            for (;;) {
+                uint32_t w[G];
+                if (base + lane < L) {
+                    load_cols<G>(colbits, j_cur, w);
+                } else {
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int32_t y = __shfl_up_sync(PM_FULL_MASK, cs, o);
-                    if (lane >= o)
-                        cs += y;
+                    for (int g = 0; g < G; ++g)
+                        w[g] = 0u;
                 }
-                cs += carry;
-                carry = __shfl_sync(PM_FULL_MASK, cs, 31);
-                uint32_t left = 0;
+                uint32_t hit = 0;
 #pragma unroll
                 for (int g = 0; g < G; ++g) {
-                    if (a[g] == 0u)
-                        continue;
-                    const uint32_t w = (r < L) ? (colbits[j * G + g] & a[g]) : 0u;
-                    if (!__any_sync(PM_FULL_MASK, w != 0u)) {
-                        left |= a[g];
-                        continue;
-                    }
-                    const uint32_t T = pm_transpose32(w, lane);
-                    const int f = __ffs(T) - 1;
-                    const int32_t v = __shfl_sync(PM_FULL_MASK, cs, f & 31);
-                    if (T)
-                        acc[g] += (unsigned long long)(uint32_t)v;
-                    a[g] &= ~__ballot_sync(PM_FULL_MASK, T != 0u);
-                    left |= a[g];
+                    w[g] &= a[g];
+                    hit |= w[g];
                 }
-                if (left == 0u)
+                if (!__any_sync(PM_FULL_MASK, hit != 0u)) {
+                    carry += __reduce_add_sync(PM_FULL_MASK, d_cur);
+                } else {
+                    // running sum of Delta' up to this lane's rank = the sorted distance at that rank
+                    int32_t cs = d_cur;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int32_t y = __shfl_up_sync(PM_FULL_MASK, cs, o);
+                        if (lane >= o)
+                            cs += y;
+                    }
+                    cs += carry;
+                    carry = __shfl_sync(PM_FULL_MASK, cs, 31);
+#pragma unroll
+                    for (int g = 0; g < G; ++g) {
+                        uint32_t hl = __ballot_sync(PM_FULL_MASK, w[g] != 0u);
+                        if (hl == 0u)
+                            continue;
+                        if (__popc(hl) <= kSparseLanes) {
+                            uint32_t ag = a[g];
+                            do {
+                                const int r = __ffs(hl) - 1;
+                                hl &= hl - 1u;
+                                const uint32_t hb = __shfl_sync(PM_FULL_MASK, w[g], r) & ag;
+                                const int32_t v = __shfl_sync(PM_FULL_MASK, cs, r);
+                                if ((hb >> lane) & 1u)
+                                    acc[g] += (unsigned long long)(uint32_t)v;
+                                ag &= ~hb;
+                            } while (hl);
+                            a[g] = ag;
+                        } else {
+                            const uint32_t T = pm_transpose32(w[g], lane);
+                            const int f = __ffs(T) - 1;
+                            const int32_t v = __shfl_sync(PM_FULL_MASK, cs, f & 31);
+                            if (T)
+                                acc[g] += (unsigned long long)(uint32_t)v;
+                            a[g] &= ~__ballot_sync(PM_FULL_MASK, T != 0u);
+                        }
+                    }
+                }
+                uint32_t left = 0;
+#pragma unroll
+                for (int g = 0; g < G; ++g)
+                    left |= a[g];
+                base += 32;
+                if (left != 0u && base < L) {
+                    j_cur = j_nxt;
+                    d_cur = d_nxt;
+                    load(c, base + 32, j_nxt, d_nxt);
+                    continue;
+                }
+                // next client of this warp
+                c += nwarps;
+                if (c >= c_end)
                     break;
+                j_cur = j_nc;
+                d_cur = d_nc;
+                load(c, 32, j_nxt, d_nxt);
+                load(c + nwarps, 0, j_nc, d_nc);
+                base = 0;
+                carry = 0;
+#pragma unroll
+                for (int g = 0; g < G; ++g)
+                    a[g] = a0[g];
             }
         }
-    }
 #pragma unroll
-    for (int g = 0; g < G; ++g)
-        if (acc[g])
-            atomicAdd(&acc_s[g * 32 + lane], acc[g]);
-    __syncthreads();
-    for (int i = threadIdx.x; i < G * 32; i += blockDim.x) {
-        const int64_t t = ind0 + i;
-        if (t < pop)
-            partial[(int64_t)split * pop + t] = acc_s[i];
+        for (int g = 0; g < G; ++g)
+            if (acc[g])
+                atomicAdd(&acc_s[g * 32 + lane], acc[g]);
+        __syncthreads();
+
+        bool finish = true;
+        if (splits > 1) {
+            // add this split's sums into the tile's accumulators; the last split of the tile
+            // (atomic ticket) reads the totals and leaves the accumulators zero again
+            for (int i = threadIdx.x; i < G * 32; i += blockDim.x) {
+                const int64_t t = ind0 + i;
+                if (t < pop && acc_s[i] != 0ull)
+                    atomicAdd(partial + t, acc_s[i]);
+            }
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0)
+                last_s = (atomicAdd(tickets + tile, 1) == splits - 1) ? 1 : 0;
+            __syncthreads();
+            finish = last_s != 0;
+            if (finish) {
+                __threadfence();
+                for (int i = threadIdx.x; i < G * 32; i += blockDim.x) {
+                    const int64_t t = ind0 + i;
+                    if (t < pop) {
+                        acc_s[i] = __ldcg(partial + t);
+                        partial[t] = 0ull;
+                    }
+                }
+                if (threadIdx.x == 0)
+                    tickets[tile] = 0;  // every CTA of the tile has taken its ticket: reset for the next launch
+                __syncthreads();
+            }
+        }
+        if (finish) {
+            // epilogue: one warp per individual of the tile
+            for (int i = warp; i < G * 32; i += nwarps) {
+                const int64_t t = ind0 + i;
+                if (t >= pop)
+                    break;
+                if (!((a0_s[i >> 5] >> (i & 31)) & 1u))
+                    continue;
+                const int64_t sum = (int64_t)acc_s[i];
+                if (ep.costs != nullptr && lane == 0)
+                    ep.costs[t] = sum;
+                if (ep.mode == 1 && sum < ep.cur_cost[t]) {
+                    for (int q = lane; q < ep.W; q += 32)
+                        ep.cur_masks[t * ep.W + q] = ep.cand_masks[t * ep.W + q];
+                    if (lane == 0) {
+                        ep.cur_cost[t] = sum;
+                        if (ep.improved)
+                            ep.improved[t] = 1;
+                    }
+                }
+            }
+        }
+        __syncthreads();  // shared state (tile, acc_s, a0_s) is reused by the next item
     }
 }
 
@@ -285,6 +440,11 @@ __global__ void __launch_bounds__(256) k_scan_rows(const uint16_t *__restrict__ 
                 dl = __ldg(drow + r);
             }
             const bool open = (r < L) && ((x[j >> 5] >> (j & 31)) & 1u);
+            const uint32_t hit = __ballot_sync(PM_FULL_MASK, open);
+            if (!hit) {
+                carry += __reduce_add_sync(PM_FULL_MASK, dl);
+                continue;
+            }
             int32_t cs = dl;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -293,12 +453,8 @@ __global__ void __launch_bounds__(256) k_scan_rows(const uint16_t *__restrict__ 
                     cs += y;
             }
             cs += carry;
-            const uint32_t hit = __ballot_sync(PM_FULL_MASK, open);
-            if (hit) {
-                acc += (unsigned long long)(uint32_t)__shfl_sync(PM_FULL_MASK, cs, __ffs(hit) - 1);
-                break;
-            }
-            carry = __shfl_sync(PM_FULL_MASK, cs, 31);
+            acc += (unsigned long long)(uint32_t)__shfl_sync(PM_FULL_MASK, cs, __ffs(hit) - 1);
+            break;
         }
     }
     if (lane == 0)
@@ -306,12 +462,11 @@ __global__ void __launch_bounds__(256) k_scan_rows(const uint16_t *__restrict__ 
 }
 
 // ---------------------------------------------------------------------------
-// Sum the splits and apply the epilogue.  One warp per individual.
+// Sum the splits of the row kernel and apply the epilogue (one warp per
+// individual).
 // ---------------------------------------------------------------------------
-__global__ void k_reduce_accept(const unsigned long long *__restrict__ partial, int splits, int64_t pop,
-                                const uint32_t *__restrict__ active, int64_t *__restrict__ costs, int mode,
-                                int64_t *__restrict__ cur_cost, uint32_t *__restrict__ cur_masks,
-                                const uint32_t *__restrict__ cand_masks, uint8_t *__restrict__ improved, int32_t W)
+__global__ void k_reduce_accept(unsigned long long *__restrict__ partial, int splits, int64_t pop,
+                                const uint32_t *__restrict__ active, ScanEpilogue ep)
 {
     const int lane = threadIdx.x & 31;
     const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -320,24 +475,23 @@ __global__ void k_reduce_accept(const unsigned long long *__restrict__ partial, 
     if (active != nullptr && !((__ldg(active + (t >> 5)) >> (t & 31)) & 1u))
         return;
     unsigned long long s = 0ull;
-    for (int k = lane; k < splits; k += 32)
+    for (int k = lane; k < splits; k += 32) {
         s += partial[(int64_t)k * pop + t];
+        partial[(int64_t)k * pop + t] = 0ull;  // leave the scratch zero, as the column kernel does
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
         s += __shfl_xor_sync(PM_FULL_MASK, s, o);
     const int64_t sum = (int64_t)s;
-    if (costs != nullptr && lane == 0)
-        costs[t] = sum;
-    if (mode == 1) {
-        const bool better = sum < cur_cost[t];
-        if (better) {
-            for (int w = lane; w < W; w += 32)
-                cur_masks[t * W + w] = cand_masks[t * W + w];
-            if (lane == 0) {
-                cur_cost[t] = sum;
-                if (improved)
-                    improved[t] = 1;
-            }
+    if (ep.costs != nullptr && lane == 0)
+        ep.costs[t] = sum;
+    if (ep.mode == 1 && sum < ep.cur_cost[t]) {
+        for (int w = lane; w < ep.W; w += 32)
+            ep.cur_masks[t * ep.W + w] = ep.cand_masks[t * ep.W + w];
+        if (lane == 0) {
+            ep.cur_cost[t] = sum;
+            if (ep.improved)
+                ep.improved[t] = 1;
         }
     }
 }
@@ -357,6 +511,12 @@ __global__ void k_mask_check(const uint32_t *__restrict__ masks, int64_t pop, in
         atomicAdd(flag, 1);
 }
 
+template <int G>
+const void *scan_fn()
+{
+    return reinterpret_cast<const void *>(k_scan_columns<G>);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -364,36 +524,6 @@ __global__ void k_mask_check(const uint32_t *__restrict__ masks, int64_t pop, in
 // ---------------------------------------------------------------------------
 
 static size_t column_smem_bytes(int64_t W, int G) { return (size_t)W * 32 * G * 4; }
-
-pm_eval_plan pm_plan_eval(const pm_instance *inst, int64_t pop)
-{
-    pm_eval_plan plan;
-    const size_t budget = inst->smem_optin > 4096 ? inst->smem_optin - 4096 : 0;
-    int G = kMaxG;
-    // fewer groups for small populations (keep >= 8 tiles) or when the tile does not fit
-    while (G > 1 && (pop <= (int64_t)32 * (G / 2) * 8 || column_smem_bytes(inst->W, G) > budget))
-        G /= 2;
-    int64_t ctas_per_sm;
-    if (column_smem_bytes(inst->W, G) > budget) {
-        plan.groups = 0;  // row kernel
-        plan.warps = 8;
-        plan.tiles = pm_ceil_div(pop, plan.warps);
-        ctas_per_sm = 8;
-    } else {
-        plan.groups = G;
-        const size_t smem = column_smem_bytes(inst->W, G);
-        plan.warps = smem > budget / 2 ? 32 : 16;
-        plan.tiles = pm_ceil_div(pop, 32 * G);
-        ctas_per_sm = std::min<int64_t>(64 / plan.warps, (int64_t)(budget / std::max<size_t>(smem, 1)));
-        ctas_per_sm = std::max<int64_t>(ctas_per_sm, 1);
-    }
-    const int64_t target = (int64_t)inst->sm_count * ctas_per_sm;
-    int64_t splits = pm_ceil_div(target, std::max<int64_t>(1, plan.tiles));
-    const int64_t max_splits = std::max<int64_t>(1, inst->n / (plan.groups ? plan.warps : 1));
-    splits = std::min<int64_t>(std::max<int64_t>(1, splits), std::min<int64_t>(max_splits, 65535));
-    plan.splits = (int)splits;
-    return plan;
-}
 
 pm_status pm_fitness_init(const pm_instance *inst)
 {
@@ -405,11 +535,74 @@ pm_status pm_fitness_init(const pm_instance *inst)
     return PM_OK;
 }
 
+// Resident CTAs per SM of the column kernel for (G, warps) at this instance's W.
+static int column_ctas_per_sm(const pm_instance *inst, int G, int warps)
+{
+    const size_t smem = column_smem_bytes(inst->W, G);
+    int nb = 0;
+    const void *fn = G == 4 ? scan_fn<4>() : (G == 2 ? scan_fn<2>() : scan_fn<1>());
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, warps * 32, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nb;
+}
+
+pm_eval_plan pm_plan_eval_with(const pm_instance *inst, int64_t pop, int G, int warps, int splits_hint)
+{
+    pm_eval_plan plan;
+    const size_t budget = inst->smem_optin > 4096 ? inst->smem_optin - 4096 : 0;
+    int64_t ctas_per_sm = 0;
+    if (G > 0 && column_smem_bytes(inst->W, G) <= budget)
+        ctas_per_sm = column_ctas_per_sm(inst, G, warps);
+    if (G <= 0 || ctas_per_sm <= 0) {
+        plan.groups = 0;  // row kernel
+        plan.warps = 8;
+        plan.tiles = pm_ceil_div(pop, plan.warps);
+        ctas_per_sm = 8;
+    } else {
+        plan.groups = G;
+        plan.warps = warps;
+        plan.tiles = pm_ceil_div(pop, 32 * G);
+    }
+    const int64_t slots = (int64_t)inst->sm_count * ctas_per_sm;
+    // default: about four work items per resident CTA slot; every warp gets at least one client
+    const int64_t max_splits = std::max<int64_t>(1, inst->n / (plan.groups ? plan.warps : 1));
+    int64_t splits = splits_hint > 0 ? splits_hint : pm_ceil_div(4 * slots, std::max<int64_t>(1, plan.tiles));
+    if (splits_hint <= 0 && splits > max_splits)  // too few clients for that: one item per slot instead
+        splits = std::max<int64_t>(1, std::min<int64_t>(max_splits, slots / std::max<int64_t>(1, plan.tiles)));
+    splits = std::min<int64_t>(std::max<int64_t>(1, splits), std::min<int64_t>(max_splits, 65535));
+    plan.splits = (int)splits;
+    plan.grid = plan.groups ? std::min<int64_t>(plan.tiles * splits, slots) : plan.tiles;
+    return plan;
+}
+
+pm_eval_plan pm_plan_eval(const pm_instance *inst, int64_t pop)
+{
+    {
+        std::lock_guard<std::mutex> g(inst->plan_mu);
+        auto it = inst->tuned.find(pop);
+        if (it != inst->tuned.end())
+            return it->second;
+    }
+    const size_t budget = inst->smem_optin > 4096 ? inst->smem_optin - 4096 : 0;
+    int G = kMaxG;
+    // fewer groups for small populations (keep >= 8 tiles) or when the tile does not fit
+    while (G > 1 && (pop <= (int64_t)32 * (G / 2) * 8 || column_smem_bytes(inst->W, G) > budget))
+        G /= 2;
+    // 32 warps when only one CTA fits per SM, else 16
+    const int warps = 2 * column_smem_bytes(inst->W, G) + 8192 > inst->smem_optin ? 32 : 16;
+    return pm_plan_eval_with(inst, pop, G, warps, 0);
+}
+
 size_t pm_plan_partial_bytes(const pm_eval_plan &plan, int64_t pop)
 {
-    size_t part = (size_t)plan.splits * (size_t)std::max<int64_t>(pop, 1) * sizeof(unsigned long long);
-    return part;
+    // column kernel: one self-resetting accumulator per individual; row kernel: one sum per split and individual
+    const int64_t per = plan.groups ? 1 : plan.splits;
+    return (size_t)pm_round_up(per * std::max<int64_t>(pop, 1) * 8, 256);
 }
+
+size_t pm_plan_ticket_bytes(const pm_eval_plan &plan) { return (size_t)pm_round_up(plan.tiles * 4, 256); }
 
 size_t pm_plan_column_bytes(const pm_instance *inst, const pm_eval_plan &plan)
 {
@@ -419,55 +612,61 @@ size_t pm_plan_column_bytes(const pm_instance *inst, const pm_eval_plan &plan)
 }
 
 pm_status pm_launch_eval(const pm_instance *inst, const pm_eval_plan &plan, const uint32_t *masks, int64_t pop,
-                         const uint32_t *active, int64_t *costs, int64_t *partials_i64, uint32_t *colT,
+                         const uint32_t *active, int64_t *costs, int64_t *partials_i64, int *tickets, uint32_t *colT,
                          int *err, const pm_accept_args &acc, cudaStream_t stream)
 {
     if (pop <= 0)
         return PM_OK;
     unsigned long long *partials = reinterpret_cast<unsigned long long *>(partials_i64);
     const int64_t cps = pm_ceil_div(inst->n, plan.splits);
+    ScanEpilogue ep;
+    ep.mode = acc.mode;
+    ep.costs = costs;
+    ep.cur_cost = acc.cur_cost;
+    ep.cur_masks = acc.cur_masks;
+    ep.cand_masks = acc.cand_masks;
+    ep.improved = acc.improved;
+    ep.W = (int32_t)inst->W;
     if (plan.groups) {
         const int G = plan.groups;
-        const int64_t jobs = plan.tiles * G * inst->W;
-        const int threads = 256;
-        const int64_t blocks = std::min<int64_t>(pm_ceil_div(jobs, threads / 32), (int64_t)inst->sm_count * 16);
-        k_pop_to_columns<<<(unsigned)blocks, threads, 0, stream>>>(masks, pop, (int32_t)inst->W, G, plan.tiles,
-                                                                   colT);
-        PM_CUDA(cudaGetLastError());
+        if (!acc.columns_ready) {
+            const int64_t jobs = plan.tiles * G * inst->W;
+            const int threads = 256;
+            const int64_t blocks = std::min<int64_t>(pm_ceil_div(jobs, threads / 32), (int64_t)inst->sm_count * 16);
+            k_pop_to_columns<<<(unsigned)blocks, threads, 0, stream>>>(masks, pop, (int32_t)inst->W, G, plan.tiles,
+                                                                       colT);
+            PM_CUDA(cudaGetLastError());
+        }
         const size_t smem = column_smem_bytes(inst->W, G);
-        dim3 grid((unsigned)plan.tiles, (unsigned)plan.splits);
+        const unsigned grid = (unsigned)plan.grid;
         const int threadsc = plan.warps * 32;
+#define PM_SCAN_ARGS                                                                                        \
+    inst->pi, inst->delta, inst->n, (int32_t)inst->L, inst->stride, colT, (int32_t)inst->W, pop, active,     \
+        plan.tiles, cps, plan.splits, partials, tickets, err, ep
         switch (G) {
         case 1:
-            k_scan_columns<1><<<grid, threadsc, smem, stream>>>(inst->pi, inst->delta, inst->n, (int32_t)inst->L,
-                                                               inst->stride, colT, (int32_t)inst->W, pop, active,
-                                                               cps, partials, err);
+            k_scan_columns<1><<<grid, threadsc, smem, stream>>>(PM_SCAN_ARGS);
             break;
         case 2:
-            k_scan_columns<2><<<grid, threadsc, smem, stream>>>(inst->pi, inst->delta, inst->n, (int32_t)inst->L,
-                                                               inst->stride, colT, (int32_t)inst->W, pop, active,
-                                                               cps, partials, err);
+            k_scan_columns<2><<<grid, threadsc, smem, stream>>>(PM_SCAN_ARGS);
             break;
         default:
-            k_scan_columns<4><<<grid, threadsc, smem, stream>>>(inst->pi, inst->delta, inst->n, (int32_t)inst->L,
-                                                               inst->stride, colT, (int32_t)inst->W, pop, active,
-                                                               cps, partials, err);
+            k_scan_columns<4><<<grid, threadsc, smem, stream>>>(PM_SCAN_ARGS);
             break;
         }
+#undef PM_SCAN_ARGS
         PM_CUDA(cudaGetLastError());
-    } else {
-        const size_t smem = (size_t)plan.warps * inst->W * 4;
-        dim3 grid((unsigned)plan.tiles, (unsigned)plan.splits);
-        k_scan_rows<<<grid, plan.warps * 32, smem, stream>>>(inst->pi, inst->delta, inst->n, (int32_t)inst->L,
-                                                             inst->stride, masks, (int32_t)inst->W, pop, active,
-                                                             cps, partials);
-        PM_CUDA(cudaGetLastError());
+        return PM_OK;
     }
+    const size_t smem = (size_t)plan.warps * inst->W * 4;
+    dim3 grid((unsigned)plan.tiles, (unsigned)plan.splits);
+    k_scan_rows<<<grid, plan.warps * 32, smem, stream>>>(inst->pi, inst->delta, inst->n, (int32_t)inst->L,
+                                                         inst->stride, masks, (int32_t)inst->W, pop, active, cps,
+                                                         partials);
+    PM_CUDA(cudaGetLastError());
     const int64_t threads = 256;
     const int64_t blocks = pm_ceil_div(pop * 32, threads);
-    k_reduce_accept<<<(unsigned)blocks, (unsigned)threads, 0, stream>>>(
-        partials, plan.splits, pop, active, costs, acc.mode, acc.cur_cost, acc.cur_masks, acc.cand_masks,
-        acc.improved, (int32_t)inst->W);
+    k_reduce_accept<<<(unsigned)blocks, (unsigned)threads, 0, stream>>>(partials, plan.splits, pop, active, ep);
     PM_CUDA(cudaGetLastError());
     return PM_OK;
 }
@@ -486,8 +685,9 @@ pm_status pm_launch_mask_check(const pm_instance *inst, const uint32_t *masks, i
 // ---------------------------------------------------------------------------
 // Evaluation that allocates nothing (no counterpart in the paper): the
 // scratch of pm_launch_eval lives in a fixed array compiled into the library.
-// Layout inside the array: [0, 256) error word, then the facility-major
-// population copy, then the partial sums, each 256-byte aligned.
+// Layout inside the array: [0, 256) error word, then the tile tickets, the
+// facility-major population copy and the partial sums, each 256-byte
+// aligned.
 // ---------------------------------------------------------------------------
 namespace {
 constexpr size_t kNoAllocScratchBytes = size_t(8) << 20;  // 8 MiB per GPU
@@ -527,19 +727,23 @@ extern "C" pm_status pm_eval_population_noalloc(pm_instance *inst, const uint32_
     if (!masks || !costs || !pm_is_device_ptr(masks) || !pm_is_device_ptr(costs))
         return PM_ERR_INVALID_ARG;
     const pm_eval_plan plan = pm_plan_eval(inst, pop);
+    const size_t tick = pm_plan_ticket_bytes(plan);
     const size_t cols = (size_t)pm_round_up((int64_t)pm_plan_column_bytes(inst, plan), 256);
-    const size_t part = (size_t)pm_round_up((int64_t)pm_plan_partial_bytes(plan, pop), 256);
-    if (256 + cols + part > kNoAllocScratchBytes)
+    const size_t part = pm_plan_partial_bytes(plan, pop);
+    if (256 + tick + cols + part > kNoAllocScratchBytes)
         return PM_ERR_INVALID_ARG;
     PM_CUDA(cudaSetDevice(inst->device));
     unsigned char *base = nullptr;
     PM_TRY(noalloc_scratch(inst->device, &base));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int *err = reinterpret_cast<int *>(base);
-    uint32_t *colT = reinterpret_cast<uint32_t *>(base + 256);
-    int64_t *partials = reinterpret_cast<int64_t *>(base + 256 + cols);
-    // the array keeps the previous call's contents: the error word must start at zero
-    PM_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+    int *tickets = reinterpret_cast<int *>(base + 256);
+    uint32_t *colT = reinterpret_cast<uint32_t *>(base + 256 + tick);
+    int64_t *partials = reinterpret_cast<int64_t *>(base + 256 + tick + cols);
+    // the array keeps the previous call's contents: the error word, the tile
+    // tickets and the accumulators must start at zero
+    PM_CUDA(cudaMemsetAsync(base, 0, 256 + tick, s));
+    PM_CUDA(cudaMemsetAsync(partials, 0, part, s));
     pm_accept_args acc;
-    return pm_launch_eval(inst, plan, masks, pop, nullptr, costs, partials, colT, err, acc, s);
+    return pm_launch_eval(inst, plan, masks, pop, nullptr, costs, partials, tickets, colT, err, acc, s);
 }

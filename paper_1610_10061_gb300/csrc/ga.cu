@@ -29,6 +29,7 @@
 // (seed) with counter (generation, unit, op * 2^16 + slot / 4, stream id);
 // draw `slot` is word slot & 3.  U[0, N) = floor(u * N / 2^32).
 
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -114,45 +115,98 @@ __global__ void k_ga_gate(ga_dev *st, cudaGraphConditionalHandle h)
     cudaGraphSetConditional(h, (st->remaining > 0 && !st->stop) ? 1u : 0u);
 }
 
-// Floyd sampling + migration; also clears the per-generation improved flags.
-__global__ void k_ga_init(uint32_t *__restrict__ X, uint8_t *__restrict__ improved, const uint32_t *__restrict__ deme_best,
-                          int64_t P, int32_t W, int32_t m, int32_t p, int64_t D, uint64_t seed, uint32_t sid,
-                          const ga_dev *__restrict__ st)
+// Where the operator kernels also write the facility-major copy the column
+// fitness kernel reads: colT[tile][j][g] for tiles of 32*G individuals
+// (colT == nullptr: the evaluation uses the row kernel and needs none).
+struct ColumnsOut {
+    uint32_t *colT;
+    int32_t G;
+};
+
+// Transpose the 32 rows (individuals t0 .. t0+31, row r at rows + r*rs) into
+// colT, one warp; rows of individuals >= P read as zero.
+__device__ __forceinline__ void write_columns(const uint32_t *rows, int64_t rs, int64_t t0, int64_t P, int32_t W,
+                                              ColumnsOut co, int lane, int w_begin, int w_step)
 {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= P)
+    if (co.colT == nullptr)
         return;
-    const uint32_t gen = (uint32_t)st->gen;
-    uint32_t *row = X + t * W;
-    improved[t] = 0;
-    if (gen > 0 && (t % D) == 0) {
-        const uint32_t *src = deme_best + (t / D) * W;
-        for (int w = 0; w < W; ++w)
-            row[w] = src[w];
-        return;
-    }
-    for (int w = 0; w < W; ++w)
-        row[w] = 0u;
-    uint4 v = make_uint4(0, 0, 0, 0);
-    for (int q = 0; q < p; ++q) {
-        if ((q & 3) == 0)
-            v = draw_block(seed, gen, (uint32_t)t, OP_INIT, (uint32_t)q >> 2, sid);
-        const uint32_t j = (uint32_t)(m - p + q);
-        const uint32_t c = uniform_below(word_of(v, q & 3), j + 1);
-        const uint32_t pick = ((row[c >> 5] >> (c & 31)) & 1u) ? j : c;
-        row[pick >> 5] |= 1u << (pick & 31);
+    const int64_t tile = t0 / (32 * co.G);
+    const int32_t g = (int32_t)((t0 / 32) % co.G);
+    for (int w = w_begin; w < W; w += w_step) {
+        const uint32_t x = (t0 + lane < P) ? rows[(int64_t)lane * rs + w] : 0u;
+        const uint32_t col = pm_transpose32(x, lane);
+        co.colT[(tile * (int64_t)W * 32 + (int64_t)w * 32 + lane) * co.G + g] = col;
     }
 }
 
-// One crossover round (Section 4.3): child of t from t and its couple.
-__global__ void k_ga_crossover(const uint32_t *__restrict__ X, uint32_t *__restrict__ Xc, uint32_t *__restrict__ active,
-                               int64_t P, int32_t W, int32_t m, int32_t p, int64_t stride, uint32_t round,
-                               uint64_t seed, uint32_t sid, ga_dev *__restrict__ st)
+// Floyd sampling + migration, one warp per 32 individuals (lane = individual,
+// the bitsets in shared memory when they fit, else in place in X); also
+// clears the per-generation improved flags and writes the columns.
+__global__ void __launch_bounds__(32) k_ga_init(uint32_t *__restrict__ X, uint8_t *__restrict__ improved,
+                                                const uint32_t *__restrict__ deme_best, int64_t P, int32_t W,
+                                                int32_t m, int32_t p, int64_t D, uint64_t seed, uint32_t sid,
+                                                const ga_dev *__restrict__ st, ColumnsOut co, int rows_in_smem)
 {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    extern __shared__ uint32_t rows_s[];  // [32][Ws], Ws = W | 1 (odd stride: conflict-free transposes)
+    const int lane = threadIdx.x;
+    const int64_t t0 = (int64_t)blockIdx.x * 32;
+    const int64_t t = t0 + lane;
+    const int32_t Ws = W | 1;
+    const uint32_t gen = (uint32_t)st->gen;
+    uint32_t *row = rows_in_smem ? rows_s + (int64_t)lane * Ws : X + t * W;
+    if (t < P) {
+        improved[t] = 0;
+        if (gen > 0 && (t % D) == 0) {
+            const uint32_t *src = deme_best + (t / D) * W;
+            for (int w = 0; w < W; ++w)
+                row[w] = src[w];
+        } else {
+            for (int w = 0; w < W; ++w)
+                row[w] = 0u;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            for (int q = 0; q < p; ++q) {
+                if ((q & 3) == 0)
+                    v = draw_block(seed, gen, (uint32_t)t, OP_INIT, (uint32_t)q >> 2, sid);
+                const uint32_t j = (uint32_t)(m - p + q);
+                const uint32_t c = uniform_below(word_of(v, q & 3), j + 1);
+                const uint32_t pick = ((row[c >> 5] >> (c & 31)) & 1u) ? j : c;
+                row[pick >> 5] |= 1u << (pick & 31);
+            }
+        }
+    }
+    __syncwarp();
+    if (rows_in_smem) {
+        // copy the 32 rows out (rows of consecutive individuals are contiguous in X)
+        const int64_t nrows = (P - t0) < 32 ? (P - t0) : 32;
+        for (int64_t idx = lane; idx < nrows * W; idx += 32)
+            X[t0 * W + idx] = rows_s[(idx / W) * Ws + (idx % W)];
+        write_columns(rows_s, Ws, t0, P, W, co, lane, 0, 1);
+    } else {
+        write_columns(X + t0 * W, W, t0, P, W, co, lane, 0, 1);
+    }
+}
+
+// One crossover round (Section 4.3).  CTA = 32 warps = 32 individuals; warp
+// k builds the child of individual t0 + k.  The positions r1, r1+1, ...
+// (circularly) are visited as W+1 segments: word w0 = r1/32 from bit r1%32
+// up, the following words, and word w0 below bit r1%32.  A warp scan of the
+// per-segment counts of 0->1 and 1->0 candidates (C != couple) tells each
+// segment how many of its candidates to take; within a segment the lowest
+// bits (earliest positions) come first.
+__global__ void __launch_bounds__(1024) k_ga_crossover(const uint32_t *__restrict__ X, uint32_t *__restrict__ Xc,
+                                                       uint32_t *__restrict__ active, int64_t P, int32_t W, int32_t m,
+                                                       int32_t p, int64_t stride, uint32_t round, uint64_t seed,
+                                                       uint32_t sid, ga_dev *__restrict__ st, ColumnsOut co)
+{
+    __shared__ uint32_t valid_s;
     const int lane = threadIdx.x & 31;
-    bool valid = false;
-    if (t < P && p / 2 > 0) {
+    const int k = threadIdx.x >> 5;
+    const int64_t t0 = (int64_t)blockIdx.x * 32;
+    const int64_t t = t0 + k;
+    if (threadIdx.x == 0)
+        valid_s = 0u;
+    __syncthreads();
+    if (t < P) {
         const uint32_t gen = (uint32_t)st->gen;
         const int64_t partner = t ^ stride;
         const uint32_t pair = (uint32_t)(t < partner ? t : partner);
@@ -162,109 +216,164 @@ __global__ void k_ga_crossover(const uint32_t *__restrict__ X, uint32_t *__restr
         const uint32_t *C = X + t * W;
         const uint32_t *K = X + partner * W;
         uint32_t *F = Xc + t * W;
-        for (int w = 0; w < W; ++w)
-            F[w] = C[w];
-        int need01 = i, need10 = i;
         const int w0 = (int)(r1 >> 5);
         const uint32_t b0 = r1 & 31u;
-        // positions r1 .. m-1 then 0 .. r1-1: word w0 from bit b0, the words
-        // after it, wrapping, then word w0 below bit b0
-        for (int s = 0; s <= W && (need01 > 0 || need10 > 0); ++s) {
-            int w;
-            uint32_t seg;
-            if (s == 0) {
-                w = w0;
-                seg = 0xffffffffu << b0;
-            } else if (s < W) {
-                w = w0 + s;
-                if (w >= W)
-                    w -= W;
-                seg = 0xffffffffu;
-            } else {
-                w = w0;
-                seg = b0 ? ((1u << b0) - 1u) : 0u;
+        int c01 = 0, c10 = 0;      // candidates in the segments of earlier rounds
+        uint32_t w0change = 0u;    // changes to word w0 (first and last segment)
+        for (int base = 0; base <= W; base += 32) {
+            const int sidx = base + lane;
+            uint32_t z = 0u, o = 0u, cw = 0u;
+            int w = -1;
+            if (sidx <= W) {
+                uint32_t seg;
+                if (sidx == 0) {
+                    w = w0;
+                    seg = 0xffffffffu << b0;
+                } else if (sidx < W) {
+                    w = w0 + sidx;
+                    if (w >= W)
+                        w -= W;
+                    seg = 0xffffffffu;
+                } else {
+                    w = w0;
+                    seg = b0 ? ((1u << b0) - 1u) : 0u;
+                }
+                cw = C[w];
+                const uint32_t kw = K[w];
+                z = ~cw & kw & seg;
+                o = cw & ~kw & seg;
             }
-            const uint32_t cw = C[w], kw = K[w];
-            const uint32_t take01 = lowest_bits(~cw & kw & seg, need01);
-            const uint32_t take10 = lowest_bits(cw & ~kw & seg, need10);
-            if (take01 | take10)
-                F[w] ^= (take01 | take10);
-            need01 -= __popc(take01);
-            need10 -= __popc(take10);
+            // exclusive warp scan of the two counts packed in one word
+            const uint32_t nz = __popc(z), no = __popc(o);
+            uint32_t packed = nz | (no << 16);
+            uint32_t incl = packed;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const uint32_t y = __shfl_up_sync(PM_FULL_MASK, incl, off);
+                if (lane >= off)
+                    incl += y;
+            }
+            const uint32_t excl = incl - packed;
+            const int before01 = c01 + (int)(excl & 0xffffu);
+            const int before10 = c10 + (int)(excl >> 16);
+            const int take01 = min(max(i - before01, 0), (int)nz);
+            const int take10 = min(max(i - before10, 0), (int)no);
+            const uint32_t change = lowest_bits(z, take01) | lowest_bits(o, take10);
+            if (w >= 0) {
+                if (sidx == 0 || sidx == W)
+                    w0change |= change;
+                else
+                    F[w] = cw ^ change;
+            }
+            const uint32_t tot = __shfl_sync(PM_FULL_MASK, incl, 31);
+            c01 += (int)(tot & 0xffffu);
+            c10 += (int)(tot >> 16);
         }
-        valid = (need01 == 0 && need10 == 0);
+        w0change = __reduce_or_sync(PM_FULL_MASK, w0change);
+        if (lane == 0)
+            F[w0] = C[w0] ^ w0change;
+        if (lane == 0 && p / 2 > 0 && c01 >= i && c10 >= i)
+            atomicOr(&valid_s, 1u << k);
     }
-    const uint32_t bal = __ballot_sync(PM_FULL_MASK, valid);
-    if (lane == 0) {
-        const int64_t t0 = t - lane;
-        if (t0 < P) {
-            active[t0 >> 5] = bal;
-            if (bal)
-                atomicAdd(reinterpret_cast<unsigned long long *>(&st->evals), (unsigned long long)__popc(bal));
-        }
+    __syncthreads();
+    if (threadIdx.x == 0 && t0 < P) {
+        active[t0 >> 5] = valid_s;
+        if (valid_s)
+            atomicAdd(reinterpret_cast<unsigned long long *>(&st->evals), (unsigned long long)__popc(valid_s));
     }
+    write_columns(Xc + t0 * W, W, t0, P, W, co, lane, k, 32);
 }
 
-// One mutation try (Section 4.4).  One warp per individual; lanes build words.
-__global__ void k_ga_mutate(const uint32_t *__restrict__ X, uint32_t *__restrict__ Xc, uint32_t *__restrict__ active,
-                            const uint8_t *__restrict__ improved, int64_t P, int32_t W, int32_t m, uint32_t q,
-                            uint64_t seed, uint32_t sid, ga_dev *__restrict__ st)
+// 32 bits of the bitset C starting at bit position s (s may be as low as
+// -31; bits read from below position 0 are zero).
+__device__ __forceinline__ uint32_t bits_from(const uint32_t *C, int32_t W, int64_t s)
 {
+    if (s < 0)
+        return __ldg(C) << (uint32_t)(-s);
+    const int64_t q = s >> 5;
+    const uint32_t r = (uint32_t)(s & 31);
+    const uint32_t lo = __ldg(C + q);
+    const uint32_t hi = (q + 1 < W) ? __ldg(C + q + 1) : 0u;
+    return __funnelshift_r(lo, hi, r);
+}
+
+__device__ __forceinline__ uint32_t range_mask(int64_t lo, int64_t hi)  // bits [lo, hi) of a word, 0 <= lo <= hi <= 32
+{
+    const uint32_t upto = hi >= 32 ? 0xffffffffu : ((1u << hi) - 1u);
+    const uint32_t below = lo >= 32 ? 0xffffffffu : ((1u << lo) - 1u);
+    return upto & ~below;
+}
+
+// One mutation try (Section 4.4).  CTA = 32 warps = 32 individuals; warp k
+// rotates individual t0 + k's bits [a, a+len) left by kl: F[a+j] =
+// C[a + (j+kl) mod len].  Each output word is at most three pieces, each a
+// funnel-shifted 32-bit read of C.
+__global__ void __launch_bounds__(1024) k_ga_mutate(const uint32_t *__restrict__ X, uint32_t *__restrict__ Xc,
+                                                    uint32_t *__restrict__ active, const uint8_t *__restrict__ improved,
+                                                    int64_t P, int32_t W, int32_t m, uint32_t q, uint64_t seed,
+                                                    uint32_t sid, ga_dev *__restrict__ st, ColumnsOut co)
+{
+    __shared__ uint32_t on_s;
     const int lane = threadIdx.x & 31;
-    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (t >= P)
-        return;
-    const bool on = improved[t] == 0;
-    if (lane == 0) {
-        if (on) {
-            atomicOr(active + (t >> 5), 1u << (t & 31));
-            atomicAdd(reinterpret_cast<unsigned long long *>(&st->evals), 1ull);
+    const int k = threadIdx.x >> 5;
+    const int64_t t0 = (int64_t)blockIdx.x * 32;
+    const int64_t t = t0 + k;
+    if (threadIdx.x == 0)
+        on_s = 0u;
+    __syncthreads();
+    if (t < P && improved[t] == 0) {
+        if (lane == 0)
+            atomicOr(&on_s, 1u << k);
+        const uint32_t gen = (uint32_t)st->gen;
+        const uint4 v0 = draw_block(seed, gen, (uint32_t)t, OP_MUT + q, 0, sid);
+        const uint32_t kind = uniform_below(v0.x, 2u);
+        const uint32_t right = uniform_below(v0.y, 2u);
+        int64_t a, len, kk;
+        if (kind == 0) {
+            a = 0;
+            len = m;
+            kk = 1 + uniform_below(v0.z, (uint32_t)(m - 1));
         } else {
-            atomicAnd(active + (t >> 5), ~(1u << (t & 31)));
+            const uint4 v1 = draw_block(seed, gen, (uint32_t)t, OP_MUT + q, 1, sid);
+            const uint32_t x = uniform_below(v0.z, (uint32_t)m);
+            uint32_t y = uniform_below(v0.w, (uint32_t)(m - 1));
+            if (y >= x)
+                ++y;
+            const uint32_t lo = x < y ? x : y, hi = x < y ? y : x;
+            a = lo;
+            len = hi - lo + 1;
+            kk = 1 + uniform_below(v1.x, hi - lo);
         }
-    }
-    if (!on)
-        return;
-    const uint32_t gen = (uint32_t)st->gen;
-    const uint4 v0 = draw_block(seed, gen, (uint32_t)t, OP_MUT + q, 0, sid);
-    const uint32_t kind = uniform_below(v0.x, 2u);
-    const uint32_t right = uniform_below(v0.y, 2u);
-    uint32_t a, len, k;
-    if (kind == 0) {
-        a = 0;
-        len = (uint32_t)m;
-        k = 1 + uniform_below(v0.z, (uint32_t)(m - 1));
-    } else {
-        const uint4 v1 = draw_block(seed, gen, (uint32_t)t, OP_MUT + q, 1, sid);
-        const uint32_t x = uniform_below(v0.z, (uint32_t)m);
-        uint32_t y = uniform_below(v0.w, (uint32_t)(m - 1));
-        if (y >= x)
-            ++y;
-        const uint32_t lo = x < y ? x : y, hi = x < y ? y : x;
-        a = lo;
-        len = hi - lo + 1;
-        k = 1 + uniform_below(v1.x, hi - lo);
-    }
-    const uint32_t kl = right ? (len - k) : k;  // rotate left by kl, 1 <= kl < len
-    const uint32_t *C = X + t * W;
-    uint32_t *F = Xc + t * W;
-    for (int w = lane; w < W; w += 32) {
-        uint32_t out = 0;
-        const uint32_t pos0 = (uint32_t)w * 32u;
-        const uint32_t lim = (uint32_t)m - pos0 < 32u ? (uint32_t)m - pos0 : 32u;
-        for (uint32_t b = 0; b < lim; ++b) {
-            const uint32_t pos = pos0 + b;
-            uint32_t src = pos;
-            if (pos >= a && pos < a + len) {
-                uint32_t j = pos - a + kl;
-                if (j >= len)
-                    j -= len;
-                src = a + j;
+        const int64_t kl = right ? (len - kk) : kk;  // rotate left by kl, 1 <= kl < len
+        const int64_t pwrap = a + len - kl;          // positions >= pwrap wrap to the start of the block
+        const uint32_t *C = X + t * W;
+        uint32_t *F = Xc + t * W;
+        for (int w = lane; w < W; w += 32) {
+            const int64_t pos0 = (int64_t)w * 32;
+            const int64_t in_lo = a > pos0 ? a : pos0;
+            const int64_t in_hi = (a + len) < (pos0 + 32) ? (a + len) : (pos0 + 32);
+            const uint32_t cw = __ldg(C + w);
+            if (in_lo >= in_hi) {
+                F[w] = cw;
+                continue;
             }
-            out |= ((__ldg(C + (src >> 5)) >> (src & 31)) & 1u) << b;
+            uint32_t out = cw & ~range_mask(in_lo - pos0, in_hi - pos0);
+            const int64_t e1 = in_hi < pwrap ? in_hi : pwrap;
+            if (in_lo < e1)
+                out |= bits_from(C, W, pos0 + kl) & range_mask(in_lo - pos0, e1 - pos0);
+            const int64_t s2 = in_lo > pwrap ? in_lo : pwrap;
+            if (s2 < in_hi)
+                out |= bits_from(C, W, pos0 + kl - len) & range_mask(s2 - pos0, in_hi - pos0);
+            F[w] = out;
         }
-        F[w] = out;
     }
+    __syncthreads();
+    if (threadIdx.x == 0 && t0 < P) {
+        active[t0 >> 5] = on_s;
+        if (on_s)
+            atomicAdd(reinterpret_cast<unsigned long long *>(&st->evals), (unsigned long long)__popc(on_s));
+    }
+    write_columns(Xc + t0 * W, W, t0, P, W, co, lane, k, 32);
 }
 
 // Lowest (cost, index) in each deme -> deme_best / deme_cost.  One CTA per deme.
@@ -317,7 +426,7 @@ __global__ void k_ga_deme_best(const uint32_t *__restrict__ X, const int64_t *__
 // Global best, saturation, trace, counters and the loop condition.
 __global__ void k_ga_finish(const uint32_t *__restrict__ deme_best, const int64_t *__restrict__ deme_cost, int64_t NB,
                             int32_t W, int64_t P, uint32_t *__restrict__ best, ga_dev *__restrict__ st,
-                            cudaGraphConditionalHandle h)
+                            cudaGraphConditionalHandle h, int in_graph)
 {
     __shared__ long long sc[32];
     __shared__ long long si[32];
@@ -375,7 +484,8 @@ __global__ void k_ga_finish(const uint32_t *__restrict__ deme_best, const int64_
         st->total_gens += 1;
         st->remaining -= 1;
         st->stop = (st->saturation > 0 && st->sat >= st->saturation) ? 1 : 0;
-        cudaGraphSetConditional(h, (st->remaining > 0 && !st->stop) ? 1u : 0u);
+        if (in_graph)
+            cudaGraphSetConditional(h, (st->remaining > 0 && !st->stop) ? 1u : 0u);
     }
 }
 
@@ -391,7 +501,7 @@ struct pm_ga {
     int64_t S = 0;
     uint32_t sid = 0;
     pm_eval_plan plan;
-    pm_dbuf X, Xc, cost, active, improved, deme_best, deme_cost, best, trace, partials, columns, st, err;
+    pm_dbuf X, Xc, cost, active, improved, deme_best, deme_cost, best, trace, partials, tickets, columns, st, err;
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -409,15 +519,16 @@ static void ga_free(pm_ga *ga)
     if (ga->cap)
         cudaStreamDestroy(ga->cap);
     pm_dbuf *bufs[] = {&ga->X,        &ga->Xc,        &ga->cost, &ga->active, &ga->improved,
-                       &ga->deme_best, &ga->deme_cost, &ga->best, &ga->trace,  &ga->partials,
+                       &ga->deme_best, &ga->deme_cost, &ga->best, &ga->trace,  &ga->partials, &ga->tickets,
                        &ga->columns,  &ga->st,        &ga->err};
     for (pm_dbuf *b : bufs)
         b->release();
     delete ga;
 }
 
-// Enqueue one generation on `s` (used under stream capture for the body).
-static pm_status enqueue_generation(pm_ga *ga, cudaStream_t s, cudaGraphConditionalHandle h)
+// Enqueue one generation on `s`: under stream capture for the graph body
+// (in_graph = 1), or directly on the stream (in_graph = 0).
+static pm_status enqueue_generation(pm_ga *ga, cudaStream_t s, cudaGraphConditionalHandle h, int in_graph)
 {
     pm_instance *inst = ga->inst;
     const int32_t W = (int32_t)inst->W, m = (int32_t)inst->m, p = (int32_t)inst->p;
@@ -428,38 +539,48 @@ static pm_status enqueue_generation(pm_ga *ga, cudaStream_t s, cudaGraphConditio
     uint32_t *active = static_cast<uint32_t *>(ga->active.ptr);
     uint8_t *improved = static_cast<uint8_t *>(ga->improved.ptr);
     int64_t *partials = static_cast<int64_t *>(ga->partials.ptr);
+    int *tickets = static_cast<int *>(ga->tickets.ptr);
     uint32_t *columns = static_cast<uint32_t *>(ga->columns.ptr);
     int *err = static_cast<int *>(ga->err.ptr);
     const int64_t P = ga->P;
-    const unsigned b256 = (unsigned)pm_ceil_div(P, 256);
+    const unsigned groups32 = (unsigned)pm_ceil_div(P, 32);
+    ColumnsOut co;
+    co.colT = ga->plan.groups ? columns : nullptr;
+    co.G = ga->plan.groups ? ga->plan.groups : 1;
+    const int32_t Ws = W | 1;
+    const size_t init_smem = (size_t)32 * Ws * 4;
+    const int rows_in_smem = init_smem <= 48 * 1024 ? 1 : 0;
 
-    k_ga_init<<<b256, 256, 0, s>>>(X, improved, static_cast<const uint32_t *>(ga->deme_best.ptr), P, W, m, p, ga->D,
-                                   ga->seed, ga->sid, st);
+    k_ga_init<<<groups32, 32, rows_in_smem ? init_smem : 0, s>>>(
+        X, improved, static_cast<const uint32_t *>(ga->deme_best.ptr), P, W, m, p, ga->D, ga->seed, ga->sid, st, co,
+        rows_in_smem);
     PM_CUDA(cudaGetLastError());
     pm_accept_args plain;
-    PM_TRY(pm_launch_eval(inst, ga->plan, X, P, nullptr, cost, partials, columns, err, plain, s));
+    plain.columns_ready = true;
+    PM_TRY(pm_launch_eval(inst, ga->plan, X, P, nullptr, cost, partials, tickets, columns, err, plain, s));
 
     pm_accept_args acc;
     acc.mode = 1;
     acc.cur_cost = cost;
     acc.cur_masks = X;
     acc.cand_masks = Xc;
+    acc.columns_ready = true;
     if (p / 2 > 0) {
         for (int r = 0; r < ga->R; ++r) {
             const int64_t stride = ga->D >> (1 + (r % ga->lgD));
-            k_ga_crossover<<<(unsigned)pm_ceil_div(P, 256) , 256, 0, s>>>(X, Xc, active, P, W, m, p, stride,
-                                                                         (uint32_t)r, ga->seed, ga->sid, st);
+            k_ga_crossover<<<groups32, 1024, 0, s>>>(X, Xc, active, P, W, m, p, stride, (uint32_t)r, ga->seed, ga->sid,
+                                                     st, co);
             PM_CUDA(cudaGetLastError());
             acc.improved = nullptr;
-            PM_TRY(pm_launch_eval(inst, ga->plan, Xc, P, active, nullptr, partials, columns, err, acc, s));
+            PM_TRY(pm_launch_eval(inst, ga->plan, Xc, P, active, nullptr, partials, tickets, columns, err, acc, s));
         }
     }
     for (int q = 0; q < ga->Q; ++q) {
-        k_ga_mutate<<<(unsigned)pm_ceil_div(P * 32, 256), 256, 0, s>>>(X, Xc, active, improved, P, W, m, (uint32_t)q,
-                                                                      ga->seed, ga->sid, st);
+        k_ga_mutate<<<groups32, 1024, 0, s>>>(X, Xc, active, improved, P, W, m, (uint32_t)q, ga->seed, ga->sid, st,
+                                              co);
         PM_CUDA(cudaGetLastError());
         acc.improved = improved;
-        PM_TRY(pm_launch_eval(inst, ga->plan, Xc, P, active, nullptr, partials, columns, err, acc, s));
+        PM_TRY(pm_launch_eval(inst, ga->plan, Xc, P, active, nullptr, partials, tickets, columns, err, acc, s));
     }
     const int dthreads = (int)std::min<int64_t>(ga->D, 1024);
     k_ga_deme_best<<<(unsigned)ga->NB, (unsigned)pm_round_up(dthreads, 32), 0, s>>>(
@@ -467,7 +588,7 @@ static pm_status enqueue_generation(pm_ga *ga, cudaStream_t s, cudaGraphConditio
     PM_CUDA(cudaGetLastError());
     k_ga_finish<<<1, 1024, 0, s>>>(static_cast<const uint32_t *>(ga->deme_best.ptr),
                                    static_cast<const int64_t *>(ga->deme_cost.ptr), ga->NB, W, P,
-                                   static_cast<uint32_t *>(ga->best.ptr), st, h);
+                                   static_cast<uint32_t *>(ga->best.ptr), st, h, in_graph);
     PM_CUDA(cudaGetLastError());
     return PM_OK;
 }
@@ -496,7 +617,7 @@ static pm_status build_graph(pm_ga *ga)
     PM_CUDA(cudaGraphAddNode(&loop, ga->graph, &gate, nullptr, 1, &cp));
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     PM_CUDA(cudaStreamBeginCaptureToGraph(ga->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    pm_status st_gen = enqueue_generation(ga, ga->cap, h);
+    pm_status st_gen = enqueue_generation(ga, ga->cap, h, 1);
     cudaGraph_t captured = nullptr;
     cudaError_t e = cudaStreamEndCapture(ga->cap, &captured);
     PM_TRY(st_gen);
@@ -520,6 +641,7 @@ static pm_status ga_alloc(pm_ga *ga, cudaStream_t s)
     PM_TRY(ga->trace.reserve(8 * 1024));
     ga->plan = pm_plan_eval(inst, ga->P);
     PM_TRY(ga->partials.reserve(pm_plan_partial_bytes(ga->plan, ga->P)));
+    PM_TRY(ga->tickets.reserve(pm_plan_ticket_bytes(ga->plan)));
     PM_TRY(ga->columns.reserve(std::max<size_t>(pm_plan_column_bytes(inst, ga->plan), 256)));
     PM_TRY(ga->st.reserve(sizeof(ga_dev)));
     PM_TRY(ga->err.reserve(256));
@@ -532,6 +654,8 @@ static pm_status ga_alloc(pm_ga *ga, cudaStream_t s)
     PM_CUDA(cudaMemsetAsync(ga->deme_cost.ptr, 0, ga->deme_cost.bytes, s));
     PM_CUDA(cudaMemsetAsync(ga->best.ptr, 0, ga->best.bytes, s));
     PM_CUDA(cudaMemsetAsync(ga->err.ptr, 0, 256, s));
+    PM_CUDA(cudaMemsetAsync(ga->tickets.ptr, 0, ga->tickets.bytes, s));    // tile tickets start at zero
+    PM_CUDA(cudaMemsetAsync(ga->partials.ptr, 0, ga->partials.bytes, s));  // and so do the accumulators
     ga_dev h = {};
     h.best_cost = -1;
     h.saturation = ga->S;
@@ -605,6 +729,14 @@ extern "C" pm_status pm_ga_create(pm_instance *inst, uint64_t seed, int64_t pop,
     return PM_OK;
 }
 
+// PM_GA_GRAPH=0 in the environment selects direct stream launches instead of
+// the conditional-while graph (identical results; for profiling).
+static bool graph_mode()
+{
+    const char *v = std::getenv("PM_GA_GRAPH");
+    return !(v && v[0] == '0');
+}
+
 static pm_status check_err(pm_ga *ga, cudaStream_t s)
 {
     int e = 0;
@@ -631,7 +763,22 @@ extern "C" pm_status pm_ga_step(pm_ga *ga, int64_t gens, int64_t *trace, void *s
     }
     k_ga_begin<<<1, 1, 0, s>>>(static_cast<ga_dev *>(ga->st.ptr), (long long)gens, tr);
     PM_CUDA(cudaGetLastError());
-    PM_CUDA(cudaGraphLaunch(ga->exec, s));
+    if (graph_mode()) {
+        PM_CUDA(cudaGraphLaunch(ga->exec, s));
+    } else {
+        // the same kernels, enqueued generation by generation (profilers cannot see
+        // kernels inside conditional graphs); saturation needs the host to look
+        for (int64_t g = 0; g < gens; ++g) {
+            PM_TRY(enqueue_generation(ga, s, 0, 0));
+            if (ga->S > 0) {
+                ga_dev h;
+                PM_CUDA(cudaMemcpyAsync(&h, ga->st.ptr, sizeof(h), cudaMemcpyDeviceToHost, s));
+                PM_CUDA(cudaStreamSynchronize(s));
+                if (h.stop)
+                    break;
+            }
+        }
+    }
     if (trace && !trace_dev) {
         // generations actually run may be fewer (saturation); copy all `gens` slots, caller reads gens_run
         PM_CUDA(cudaMemcpyAsync(trace, tr, (size_t)gens * 8, cudaMemcpyDeviceToHost, s));
@@ -793,7 +940,7 @@ extern "C" pm_status pm_ga_info(const pm_ga *ga, int64_t *pop, int64_t *deme, in
 {
     if (!ga)
         return PM_ERR_INVALID_ARG;
-    const int64_t per_eval = pm_plan_kernels(ga->plan);
+    const int64_t per_eval = ga->plan.groups ? 1 : 2;  // the operators write the columns themselves
     const int64_t rounds = ga->inst->p / 2 > 0 ? ga->R : 0;
     if (pop)
         *pop = ga->P;
@@ -806,7 +953,7 @@ extern "C" pm_status pm_ga_info(const pm_ga *ga, int64_t *pop, int64_t *deme, in
     if (kernels_per_generation)
         *kernels_per_generation = 1 + per_eval + rounds * (1 + per_eval) + ga->Q * (1 + per_eval) + 2;
     if (kernels_per_step_call)
-        *kernels_per_step_call = 2;  // k_ga_begin and the gate
+        *kernels_per_step_call = graph_mode() ? 2 : 1;  // k_ga_begin (and the gate in graph mode)
     return PM_OK;
 }
 

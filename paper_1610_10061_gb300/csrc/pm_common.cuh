@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <map>
 #include <mutex>
 #include <vector>
 
@@ -37,7 +38,8 @@ void pm_note_cuda_error(cudaError_t e, const char *what, const char *file, int l
 struct pm_dbuf {
     void *ptr = nullptr;
     size_t bytes = 0;
-    pm_status reserve(size_t want);
+    // Grow to at least `want` bytes; *fresh (optional) tells whether new memory was allocated.
+    pm_status reserve(size_t want, bool *fresh = nullptr);
     void release();
 };
 
@@ -47,6 +49,7 @@ struct pm_eval_plan {
     int warps = 16;       // warps per CTA
     int splits = 1;       // CTAs per individual tile along the client axis
     int64_t tiles = 0;    // ceil(pop / (32 G))
+    int64_t grid = 0;     // CTAs launched (column kernel: persistent over tiles x splits items)
 };
 
 struct pm_instance {
@@ -58,19 +61,30 @@ struct pm_instance {
     int sm_count = 0;
     size_t smem_optin = 0;
     // staging and scratch for pm_eval_population
-    pm_dbuf stage_masks, stage_costs, partials, columns, flag, err;
+    pm_dbuf stage_masks, stage_costs, partials, tickets, columns, flag, err;
     std::mutex lock;
+    // evaluation plans chosen by the autotuner, by population size
+    mutable std::mutex plan_mu;
+    std::map<int64_t, pm_eval_plan> tuned;
 };
 
 // ---------------------------------------------------------------------------
 // Fitness evaluation (fitness.cu)
 // ---------------------------------------------------------------------------
 
-// Choose the tile configuration for `pop` individuals on `inst`.
+// Choose the tile configuration for `pop` individuals on `inst` (the tuned
+// plan if the autotuner has run for this size, else a heuristic).
 pm_eval_plan pm_plan_eval(const pm_instance *inst, int64_t pop);
-// Kernels one evaluation launches under the plan.
-static inline int64_t pm_plan_kernels(const pm_eval_plan &plan) { return plan.groups ? 3 : 2; }
-// Bytes of int64 partial sums the plan needs.
+// A plan with explicit groups (0 = row kernel), warps per CTA and client
+// splits (0 = one full wave).
+pm_eval_plan pm_plan_eval_with(const pm_instance *inst, int64_t pop, int G, int warps, int splits_hint);
+// Bytes of per-tile tickets the plan needs (zero before the first launch;
+// every launch leaves them zero, whatever the plan).
+size_t pm_plan_ticket_bytes(const pm_eval_plan &plan);
+// Kernels one evaluation launches under the plan (column path: transpose +
+// scan with fused reduction; row path: scan + reduction).
+static inline int64_t pm_plan_kernels(const pm_eval_plan &plan) { return plan.groups ? 2 : 2; }
+// Bytes of int64 partial sums (one per client split and individual).
 size_t pm_plan_partial_bytes(const pm_eval_plan &plan, int64_t pop);
 
 // Epilogue applied after the per-individual sums are formed.
@@ -83,14 +97,15 @@ struct pm_accept_args {
     uint32_t *cur_masks = nullptr;
     const uint32_t *cand_masks = nullptr;
     uint8_t *improved = nullptr;
+    bool columns_ready = false;  // the caller already wrote the facility-major copy
 };
 
 // Enqueue the scan over (masks, pop) -> partials -> sums (+ epilogue).
 // active: nullable, bit (t & 31) of word t >> 5 marks individual t as
 // evaluated; inactive individuals get no cost written.
 pm_status pm_launch_eval(const pm_instance *inst, const pm_eval_plan &plan, const uint32_t *masks, int64_t pop,
-                         const uint32_t *active, int64_t *costs, int64_t *partials, uint32_t *colT, int *err,
-                         const pm_accept_args &acc, cudaStream_t stream);
+                         const uint32_t *active, int64_t *costs, int64_t *partials, int *tickets, uint32_t *colT,
+                         int *err, const pm_accept_args &acc, cudaStream_t stream);
 // Bytes of the facility-major copy of the population the plan needs.
 size_t pm_plan_column_bytes(const pm_instance *inst, const pm_eval_plan &plan);
 // One-time per-process kernel attributes (dynamic shared memory opt-in).

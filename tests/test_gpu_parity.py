@@ -261,3 +261,20 @@ def test_ga_save_load_resume(pm):
     np.testing.assert_array_equal(ma, mc)
     np.testing.assert_array_equal(ca, cc)
     assert a.result()[:3] == c.result()[:3]
+
+
+def test_ga_stream_launch_mode_matches_graph_mode(pm, monkeypatch):
+    """PM_GA_GRAPH=0 (direct stream launches, for profilers) gives the graph mode's results bit for bit."""
+    d = graph_instance(100, 200, seed=0)
+    inst = pm.Instance(d, 5)
+    a = pm.GA(inst, seed=3, pop=128, deme=32)
+    ta = a.step(9)
+    monkeypatch.setenv("PM_GA_GRAPH", "0")
+    b = pm.GA(inst, seed=3, pop=128, deme=32)
+    tb = b.step(9)
+    np.testing.assert_array_equal(ta, tb)
+    for x, y in zip(a.population(), b.population()):
+        np.testing.assert_array_equal(x, y)
+    assert a.result()[:3] == b.result()[:3]
+    # saturation stop in stream mode, against the oracle
+    _ga_compare(pm, graph_instance(30, 60, seed=1), 3, 32, 300, check_every=300, deme=16, saturation=4)
