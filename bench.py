@@ -239,6 +239,7 @@ def run_ours(args):
     n, m = d.shape
     stream = torch.cuda.current_stream()
     inst = pm.Instance(d, p, device=local, stream=stream.cuda_stream)
+    shape = inst.tune(pop, stream=stream.cuda_stream)  # autotuned evaluation tile (kept by the instance)
     ga = pm.GA(inst, seed=0, pop=pop, deme=deme, stream_id=rank, stream=stream.cuda_stream)
     info = ga.info()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
@@ -341,6 +342,7 @@ def run_ours(args):
                        "pop": pop, "deme": deme, "xover_rounds": info["xover_rounds"],
                        "mut_tries": info["mut_tries"], "step": "one GA generation (one pm_ga_step graph launch)",
                        "l2": "flushed between timed steps (512 MiB write outside the events)",
+                       "eval_tile": {k: shape[k] for k in ("groups", "warps", "splits", "grid")},
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "evals": int(tot_evals), "best_cost": int(best),
             "gpu_launches": int((info["kernels_per_generation"] + info["kernels_per_step_call"]) * args.steps),
@@ -369,6 +371,7 @@ def run_eval_mode(args):
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
     inst = pm.Instance(d, p, stream=stream.cuda_stream)
+    shape = inst.tune(pop, stream=stream.cuda_stream)
     masks = random_masks(pop, m, p, seed=123)
     dmask = torch.from_numpy(masks.view(np.int32)).cuda()
     dcost = torch.empty(pop, dtype=torch.int64, device="cuda")
@@ -399,6 +402,7 @@ def run_eval_mode(args):
             "data": "synthetic",
             "config": {"workload": args.workload, "n": int(n), "m": int(m), "p": int(p), "pop": pop,
                        "step": "pm_eval_population of a uniform random population (device buffers)",
+                       "eval_tile": {k: shape[k] for k in ("groups", "warps", "splits", "grid")},
                        "l2": "flushed between timed steps"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": profiled_traffic(args.workload),

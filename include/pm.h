@@ -156,6 +156,32 @@ PM_API pm_status pm_eval_population(pm_instance *inst, const uint32_t *masks, in
 PM_API pm_status pm_eval_population_noalloc(pm_instance *inst, const uint32_t *masks, int64_t pop, int64_t *costs,
                                             void *stream);
 
+/*
+ * pm_tune_eval -- autotune the tile shape of pm_eval_population for `pop`
+ * individuals on this instance (no counterpart in the paper, whose Fitness
+ * runs one thread per chromosome).  Candidates: facility-major tiles of
+ * 32, 64 or 128 individuals per CTA (groups = 1, 2, 4; those whose tile fits
+ * in shared memory), 8, 16 or 32 warps per CTA, and client splits around the
+ * one-wave default (x1/2, x1, x2); the row kernel when no tile fits.  Each
+ * candidate evaluates a uniformly random population (Floyd sampling, fixed
+ * seed) once untimed and three times timed with CUDA events on `stream`; the
+ * fastest median is kept for this (instance, pop) and used by every later
+ * evaluation of that size (pm_eval_population, pm_eval_population_noalloc
+ * and GAs created afterwards).  chosen (nullable, host) receives it.
+ * Synchronises `stream`.  Errors: PM_ERR_INVALID_ARG, PM_ERR_OOM, PM_ERR_CUDA.
+ */
+typedef struct pm_eval_shape {
+    int32_t groups;   /* 32-individual groups per CTA tile (1, 2, 4); 0 = row kernel */
+    int32_t warps;    /* warps per CTA */
+    int32_t splits;   /* client splits: work items per tile */
+    int32_t grid;     /* CTAs launched (persistent over tiles x splits) */
+    double ms;        /* median time of one evaluation with this shape */
+    int32_t candidates; /* shapes timed */
+    int32_t reserved;
+} pm_eval_shape;
+
+PM_API pm_status pm_tune_eval(pm_instance *inst, int64_t pop, void *stream, pm_eval_shape *chosen);
+
 /* ------------------------------------------------------------------------
  * The genetic algorithm (Sections 3.1, 3.2.2, 4.3-4.5) on the device.
  * ------------------------------------------------------------------------ */
@@ -166,8 +192,10 @@ typedef struct pm_ga_params {
     int32_t mut_tries;    /* mutation tries per generation; < 0 = lg D (Section 3.2.2, step 5) */
     int64_t saturation;   /* S: stop when the best has not improved for S generations; 0 = off */
     uint32_t stream_id;   /* fourth word of every random-number counter (independent runs) */
-    uint32_t reserved;    /* must be 0 */
+    uint32_t flags;       /* PM_GA_TUNE: run pm_tune_eval for this population size at creation */
 } pm_ga_params;
+
+#define PM_GA_TUNE 1u
 
 typedef struct pm_ga pm_ga;
 

@@ -491,7 +491,40 @@ __global__ void k_ga_finish(const uint32_t *__restrict__ deme_best, const int64_
 
 }  // namespace
 
+// Uniform random p-subsets (Floyd sampling, generation 0, no migration), one
+// thread per individual, bitsets written in place.
+__global__ void k_random_population(uint32_t *__restrict__ X, int64_t P, int32_t W, int32_t m, int32_t p,
+                                    uint64_t seed)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= P)
+        return;
+    uint32_t *row = X + t * W;
+    for (int w = 0; w < W; ++w)
+        row[w] = 0u;
+    uint4 v = make_uint4(0, 0, 0, 0);
+    for (int q = 0; q < p; ++q) {
+        if ((q & 3) == 0)
+            v = draw_block(seed, 0u, (uint32_t)t, OP_INIT, (uint32_t)q >> 2, 0u);
+        const uint32_t j = (uint32_t)(m - p + q);
+        const uint32_t c = uniform_below(word_of(v, q & 3), j + 1);
+        const uint32_t pick = ((row[c >> 5] >> (c & 31)) & 1u) ? j : c;
+        row[pick >> 5] |= 1u << (pick & 31);
+    }
+}
+
 // ------------------------------- host side ---------------------------------
+
+pm_status pm_launch_random_population(const pm_instance *inst, uint64_t seed, int64_t pop, uint32_t *masks,
+                                      cudaStream_t s)
+{
+    if (pop <= 0)
+        return PM_OK;
+    k_random_population<<<(unsigned)pm_ceil_div(pop, 128), 128, 0, s>>>(masks, pop, (int32_t)inst->W,
+                                                                       (int32_t)inst->m, (int32_t)inst->p, seed);
+    PM_CUDA(cudaGetLastError());
+    return PM_OK;
+}
 
 struct pm_ga {
     pm_instance *inst = nullptr;
@@ -674,7 +707,7 @@ static pm_status ga_configure(pm_ga *ga, pm_instance *inst, uint64_t seed, int64
     prm.mut_tries = -1;
     if (params)
         prm = *params;
-    if (prm.reserved != 0)
+    if ((prm.flags & ~PM_GA_TUNE) != 0)
         return PM_ERR_INVALID_ARG;
     int64_t D = prm.deme ? prm.deme : std::min<int64_t>(pop, 256);
     if (D < 2 || D > 1024 || (D & (D - 1)) != 0 || pop % D != 0 || prm.saturation < 0)
@@ -718,7 +751,10 @@ extern "C" pm_status pm_ga_create(pm_instance *inst, uint64_t seed, int64_t pop,
         delete ga;
         return PM_ERR_CUDA;
     }
-    st = ga_alloc(ga, static_cast<cudaStream_t>(stream));
+    if (params && (params->flags & PM_GA_TUNE))
+        st = pm_tune_eval(inst, pop, stream, nullptr);
+    if (st == PM_OK)
+        st = ga_alloc(ga, static_cast<cudaStream_t>(stream));
     if (st == PM_OK)
         st = build_graph(ga);
     if (st != PM_OK) {

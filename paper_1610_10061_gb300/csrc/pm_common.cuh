@@ -115,6 +115,10 @@ pm_status pm_fitness_init(const pm_instance *inst);
 pm_status pm_launch_mask_check(const pm_instance *inst, const uint32_t *masks, int64_t pop, int *flag,
                                cudaStream_t stream);
 
+// Uniform random p-subsets (Floyd sampling, fixed seed) for tuning (ga.cu).
+pm_status pm_launch_random_population(const pm_instance *inst, uint64_t seed, int64_t pop, uint32_t *masks,
+                                      cudaStream_t s);
+
 // ---------------------------------------------------------------------------
 // Tables (tables.cu)
 // ---------------------------------------------------------------------------

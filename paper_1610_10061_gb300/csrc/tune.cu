@@ -1,0 +1,127 @@
+// Autotuner for the evaluation tile shape (pm_tune_eval in include/pm.h).
+//
+// The scan's best shape depends on the instance: for short scans (many open
+// facilities) an evaluation is a few microseconds of dependent shuffles per
+// client and wants many small CTAs; for long scans it is issue-bound and
+// wants large tiles that share each staged row chunk among 128 individuals.
+// Rather than model that, the tuner times the candidate shapes on the
+// instance itself and keeps the fastest per population size.
+
+#include <algorithm>
+#include <vector>
+
+#include "pm_common.cuh"
+
+namespace {
+bool same_shape(const pm_eval_plan &a, const pm_eval_plan &b)
+{
+    return a.groups == b.groups && a.warps == b.warps && a.splits == b.splits;
+}
+}  // namespace
+
+extern "C" pm_status pm_tune_eval(pm_instance *inst, int64_t pop, void *stream, pm_eval_shape *chosen)
+{
+    if (!inst || pop < 1 || pop > ((int64_t)1 << 31))
+        return PM_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> guard(inst->lock);
+    PM_CUDA(cudaSetDevice(inst->device));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+    // candidate shapes
+    std::vector<pm_eval_plan> cands;
+    const size_t budget = inst->smem_optin > 4096 ? inst->smem_optin - 4096 : 0;
+    for (int G : {4, 2, 1}) {
+        if ((size_t)inst->W * 32 * G * 4 > budget)
+            continue;
+        for (int warps : {8, 16, 32}) {
+            const pm_eval_plan base = pm_plan_eval_with(inst, pop, G, warps, 0);
+            if (base.groups != G)
+                continue;
+            for (int sp : {std::max(1, base.splits / 2), base.splits, base.splits * 2}) {
+                const pm_eval_plan pl = pm_plan_eval_with(inst, pop, G, warps, sp);
+                bool dup = false;
+                for (const auto &c : cands)
+                    dup = dup || same_shape(c, pl);
+                if (!dup)
+                    cands.push_back(pl);
+            }
+        }
+    }
+    if (cands.empty())
+        cands.push_back(pm_plan_eval_with(inst, pop, 0, 8, 0));
+
+    // scratch for the largest candidate and a random population
+    size_t part = 0, tick = 0, cols = 0;
+    for (const auto &c : cands) {
+        part = std::max(part, pm_plan_partial_bytes(c, pop));
+        tick = std::max(tick, pm_plan_ticket_bytes(c));
+        cols = std::max(cols, pm_plan_column_bytes(inst, c));
+    }
+    bool fresh = false;
+    PM_TRY(inst->partials.reserve(part, &fresh));
+    if (fresh)
+        PM_CUDA(cudaMemsetAsync(inst->partials.ptr, 0, inst->partials.bytes, s));
+    PM_TRY(inst->tickets.reserve(tick, &fresh));
+    if (fresh)
+        PM_CUDA(cudaMemsetAsync(inst->tickets.ptr, 0, inst->tickets.bytes, s));
+    PM_TRY(inst->columns.reserve(std::max<size_t>(cols, 256)));
+    PM_TRY(inst->stage_masks.reserve((size_t)pop * inst->W * 4));
+    PM_TRY(inst->stage_costs.reserve((size_t)pop * 8));
+    uint32_t *masks = static_cast<uint32_t *>(inst->stage_masks.ptr);
+    int64_t *costs = static_cast<int64_t *>(inst->stage_costs.ptr);
+    PM_TRY(pm_launch_random_population(inst, 0x5EEDull, pop, masks, s));
+
+    cudaEvent_t e0, e1;
+    PM_CUDA(cudaEventCreate(&e0));
+    PM_CUDA(cudaEventCreate(&e1));
+    pm_accept_args acc;
+    int best = -1;
+    double best_ms = 1e30;
+    pm_status st = PM_OK;
+    for (size_t k = 0; k < cands.size() && st == PM_OK; ++k) {
+        const pm_eval_plan &pl = cands[k];
+        auto run = [&]() {
+            return pm_launch_eval(inst, pl, masks, pop, nullptr, costs, static_cast<int64_t *>(inst->partials.ptr),
+                                  static_cast<int *>(inst->tickets.ptr), static_cast<uint32_t *>(inst->columns.ptr),
+                                  static_cast<int *>(inst->err.ptr), acc, s);
+        };
+        st = run();  // warm-up
+        float t[3];
+        for (int r = 0; r < 3 && st == PM_OK; ++r) {
+            cudaEventRecord(e0, s);
+            st = run();
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t[r], e0, e1) != cudaSuccess)
+                st = PM_ERR_CUDA;
+        }
+        if (st != PM_OK)
+            break;
+        std::sort(t, t + 3);
+        if (t[1] < best_ms) {
+            best_ms = t[1];
+            best = (int)k;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    PM_TRY(st);
+    int err = 0;
+    PM_CUDA(cudaMemcpyAsync(&err, inst->err.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PM_CUDA(cudaStreamSynchronize(s));
+    if (err)
+        return (pm_status)err;
+    {
+        std::lock_guard<std::mutex> g(inst->plan_mu);
+        inst->tuned[pop] = cands[best];
+    }
+    if (chosen) {
+        chosen->groups = cands[best].groups;
+        chosen->warps = cands[best].warps;
+        chosen->splits = cands[best].splits;
+        chosen->grid = (int32_t)cands[best].grid;
+        chosen->ms = best_ms;
+        chosen->candidates = (int32_t)cands.size();
+        chosen->reserved = 0;
+    }
+    return PM_OK;
+}

@@ -38,7 +38,16 @@ class PMError(RuntimeError):
 
 class pm_ga_params(ctypes.Structure):
     _fields_ = [("deme", ctypes.c_int64), ("xover_rounds", ctypes.c_int32), ("mut_tries", ctypes.c_int32),
-                ("saturation", ctypes.c_int64), ("stream_id", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("saturation", ctypes.c_int64), ("stream_id", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
+
+
+class pm_eval_shape(ctypes.Structure):
+    _fields_ = [("groups", ctypes.c_int32), ("warps", ctypes.c_int32), ("splits", ctypes.c_int32),
+                ("grid", ctypes.c_int32), ("ms", ctypes.c_double), ("candidates", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+PM_GA_TUNE = 1
 
 
 _P = ctypes.c_void_p
@@ -54,6 +63,7 @@ _SIGS = {
     "pm_instance_tables": ([_P, _P, _P, _P], _S),
     "pm_eval_population": ([_P, _P, _I64, _P, ctypes.c_int, _P], _S),
     "pm_eval_population_noalloc": ([_P, _P, _I64, _P, _P], _S),
+    "pm_tune_eval": ([_P, _I64, _P, ctypes.POINTER(pm_eval_shape)], _S),
     "pm_ga_create": ([_P, ctypes.c_uint64, _I64, ctypes.POINTER(pm_ga_params), _P, _PP], _S),
     "pm_ga_step": ([_P, _I64, _P, _P], _S),
     "pm_ga_result": ([_P, _P, _P, _P, _P, _P], _S),
@@ -146,8 +156,15 @@ def pm_eval_population_noalloc(inst, masks, pop: int, costs, stream=None):
            "pm_eval_population_noalloc")
 
 
-def _params(deme=0, xover_rounds=-1, mut_tries=-1, saturation=0, stream_id=0):
-    return pm_ga_params(deme, xover_rounds, mut_tries, saturation, stream_id, 0)
+def pm_tune_eval(inst, pop: int, stream=None):
+    out = pm_eval_shape()
+    _check(_lib.pm_tune_eval(inst, pop, _stream(stream), ctypes.byref(out)), "pm_tune_eval")
+    return dict(groups=out.groups, warps=out.warps, splits=out.splits, grid=out.grid, ms=out.ms,
+                candidates=out.candidates)
+
+
+def _params(deme=0, xover_rounds=-1, mut_tries=-1, saturation=0, stream_id=0, tune=False):
+    return pm_ga_params(deme, xover_rounds, mut_tries, saturation, stream_id, PM_GA_TUNE if tune else 0)
 
 
 def pm_ga_create(inst, seed: int, pop: int, params: pm_ga_params | None = None, stream=None):
@@ -242,6 +259,10 @@ class Instance:
         pm_eval_population(self.handle, masks, pop, costs, int(checked), stream)
         return costs
 
+    def tune(self, pop: int, stream=None):
+        """Autotune the evaluation tile shape for populations of `pop` (see pm_tune_eval)."""
+        return pm_tune_eval(self.handle, int(pop), stream)
+
     def close(self):
         if self.handle:
             pm_instance_destroy(self.handle)
@@ -258,11 +279,12 @@ class GA:
     """The device-resident genetic algorithm on an Instance."""
 
     def __init__(self, inst: Instance, seed: int, pop: int, deme: int = 0, xover_rounds: int = -1,
-                 mut_tries: int = -1, saturation: int = 0, stream_id: int = 0, stream=None, _handle=None):
+                 mut_tries: int = -1, saturation: int = 0, stream_id: int = 0, tune: bool = False, stream=None,
+                 _handle=None):
         self.inst = inst
         self.pop = int(pop)
         self.handle = _handle if _handle is not None else pm_ga_create(
-            inst.handle, seed, pop, _params(deme, xover_rounds, mut_tries, saturation, stream_id), stream)
+            inst.handle, seed, pop, _params(deme, xover_rounds, mut_tries, saturation, stream_id, tune), stream)
 
     def step(self, gens: int, stream=None):
         trace = np.zeros(max(int(gens), 1), dtype=np.int64)

@@ -278,3 +278,29 @@ def test_ga_stream_launch_mode_matches_graph_mode(pm, monkeypatch):
     assert a.result()[:3] == b.result()[:3]
     # saturation stop in stream mode, against the oracle
     _ga_compare(pm, graph_instance(30, 60, seed=1), 3, 32, 300, check_every=300, deme=16, saturation=4)
+
+
+@pytest.mark.parametrize("name,d,p", [s for s in _shapes() if s[0] in ("ties", "p1", "graph", "euclid")],
+                         ids=["ties", "p1", "graph", "euclid"])
+def test_autotuned_shape_stays_bit_exact(pm, name, d, p):
+    m = d.shape[1]
+    inst = pm.Instance(d, p)
+    for pop in (40, 700):
+        shape = inst.tune(pop)
+        assert shape["groups"] in (0, 1, 2, 4) and shape["candidates"] >= 1 and shape["ms"] > 0
+        masks = random_masks(pop, m, p, seed=3 * pop)
+        np.testing.assert_array_equal(inst.eval(masks), oracle.eval_direct(d, masks))
+    inst.close()
+
+
+def test_ga_with_autotuned_shape_matches_untuned(pm):
+    w = paper_shape_instance("graph900")
+    inst = pm.Instance(w["d"], w["p"])
+    a = pm.GA(inst, seed=11, pop=512, deme=128)
+    ta = a.step(2)
+    b = pm.GA(inst, seed=11, pop=512, deme=128, tune=True)
+    tb = b.step(2)
+    np.testing.assert_array_equal(ta, tb)
+    for x, y in zip(a.population(), b.population()):
+        np.testing.assert_array_equal(x, y)
+    assert a.result()[:3] == b.result()[:3]
