@@ -225,13 +225,16 @@ PM_API pm_status pm_ga_create(pm_instance *inst, uint64_t seed, int64_t pop, con
  * and saturation count.  Stops early when saturation is reached.
  *   trace  nullable; receives one int64 per generation actually run (the
  *          global best cost after it), host or device memory, `gens`
- *          entries of room.  A host trace synchronises `stream`.
+ *          entries of room per instance (a batched GA writes instance k's
+ *          trace at [k * gens, (k+1) * gens)).  A host trace synchronises
+ *          `stream`.
  * Errors: PM_ERR_INVALID_ARG, PM_ERR_OOM, PM_ERR_CUDA.
  */
 PM_API pm_status pm_ga_step(pm_ga *ga, int64_t gens, int64_t *trace, void *stream);
 
 /*
- * pm_ga_result -- synchronise `stream` and report the best solution so far.
+ * pm_ga_result -- synchronise `stream` and report the best solution so far
+ * (of instance 0 for a batched GA; see pm_ga_instance_result).
  * Any output may be NULL.  best_mask: W words (host or device memory);
  * gens_run: generations run since creation; evals: fitness evaluations so
  * far (failed crossovers produce no child and are not counted; mutation
@@ -241,9 +244,16 @@ PM_API pm_status pm_ga_result(pm_ga *ga, int64_t *best_cost, uint32_t *best_mask
                        void *stream);
 
 /* pm_ga_population -- copy the population after the last generation: pop x W
- * masks and pop costs (either may be NULL; host or device memory).
- * Synchronises `stream`. */
+ * masks and pop costs (either may be NULL; host or device memory); instance
+ * 0 of a batched GA.  Synchronises `stream`. */
 PM_API pm_status pm_ga_population(pm_ga *ga, uint32_t *masks, int64_t *costs, void *stream);
+
+/* pm_ga_instance_result / pm_ga_instance_population -- the same for instance
+ * k (0 <= k < number of instances) of a GA made by pm_batch_ga_create
+ * (k = 0 for any GA).  Synchronise `stream`. */
+PM_API pm_status pm_ga_instance_result(pm_ga *ga, int64_t k, int64_t *best_cost, uint32_t *best_mask,
+                                       int64_t *gens_run, int64_t *evals, void *stream);
+PM_API pm_status pm_ga_instance_population(pm_ga *ga, int64_t k, uint32_t *masks, int64_t *costs, void *stream);
 
 /*
  * pm_ga_save / pm_ga_load -- checkpoint and resume.  The state between
@@ -279,6 +289,61 @@ PM_API pm_status pm_ga_info(const pm_ga *ga, int64_t *pop, int64_t *deme, int32_
 PM_API pm_status pm_ga_run(pm_instance *inst, uint64_t seed, int64_t pop, int64_t gens, const pm_ga_params *params,
                     int64_t *best_cost, uint32_t *best_mask, int64_t *gens_run, int64_t *evals, int64_t *trace,
                     void *stream);
+
+/* ------------------------------------------------------------------------
+ * Batches: many instances of uneven (n, m, p) in one launch (no counterpart
+ * in the paper, which solves one instance per run).
+ * ------------------------------------------------------------------------ */
+
+typedef struct pm_batch pm_batch;
+
+/*
+ * pm_batch_create -- group k instances (same device) for batched
+ * evaluation and GAs.  The batch refers to the instances; the caller keeps
+ * them alive until pm_batch_destroy.  Every instance's facility-major tile
+ * must fit in shared memory (m up to about 56000), else PM_ERR_UNSUPPORTED.
+ */
+PM_API pm_status pm_batch_create(pm_instance *const *insts, int64_t k, pm_batch **out);
+PM_API pm_status pm_batch_destroy(pm_batch *b);
+
+/*
+ * pm_batch_eval -- Section 4.2 for every individual of every instance in
+ * one persistent launch (plus one transpose launch).  Instance j evaluates
+ * pops[j] bitsets of W_j = ceil(m_j/32) words; masks holds the instances'
+ * populations back to back (instance 0's pops[0] rows, then instance 1's,
+ * ...), costs receives sum(pops) int64 values in the same order.  masks and
+ * costs must be device memory; pops is host memory.  Work items (instance,
+ * tile of 32G individuals, client split) are sized by an estimate of each
+ * instance's scan work so that uneven instances share the GPU evenly.
+ * Asynchronous.  Errors: PM_ERR_INVALID_ARG, PM_ERR_OOM, PM_ERR_CUDA.
+ */
+PM_API pm_status pm_batch_eval(pm_batch *b, const uint32_t *masks, const int64_t *pops, int64_t *costs,
+                               void *stream);
+
+/*
+ * pm_batch_tune -- autotune the batched launch for these population sizes:
+ * groups per tile (1, 2, 4), warps per CTA (16, 32) and work items per
+ * resident CTA (2, 4, 8), each timed (median of three, CUDA events) on
+ * uniformly random populations.  The fastest is used by later pm_batch_eval
+ * calls with the same sizes and by batched GAs.  chosen->splits reports the
+ * items per CTA.  Synchronises `stream`.
+ */
+PM_API pm_status pm_batch_tune(pm_batch *b, const int64_t *pops, void *stream, pm_eval_shape *chosen);
+
+/*
+ * pm_batch_ga_create -- one GA per instance of the batch, all with `pop`
+ * individuals and the same params, run together: every generation is the
+ * same sequence of kernels as pm_ga_create's, each launch covering all
+ * instances.  Instance k draws its random numbers with stream id
+ * params->stream_id + k, so its trajectory equals that of pm_ga_create on
+ * the instance alone with that stream id.  An instance that reaches its
+ * saturation limit stops while the others go on.  Use pm_ga_step,
+ * pm_ga_instance_result, pm_ga_instance_population, pm_ga_info and
+ * pm_ga_destroy on the result.  All instances must have p >= 2, or all
+ * p = 1 (PM_ERR_UNSUPPORTED otherwise).  PM_GA_TUNE runs pm_batch_tune.
+ */
+PM_API pm_status pm_batch_ga_create(pm_batch *b, uint64_t seed, int64_t pop, const pm_ga_params *params, void *stream,
+                                    pm_ga **out);
 
 #ifdef __cplusplus
 }

@@ -106,27 +106,47 @@ __device__ __forceinline__ void load_cols(const uint32_t *cb, uint32_t j, uint32
     }
 }
 
+// Largest k in [0, K) with base(k) <= x (bases ascending, base(0) = 0).
+template <typename F>
+__device__ __forceinline__ int find_prob(int K, int64_t x, F base)
+{
+    int lo = 0, hi = K - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (base(mid) <= x)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
 // ---------------------------------------------------------------------------
-// Row-major population -> facility-major tiles.
-// colT[tile][j][g] (j < 32W) = bits over individuals tile*32G + 32g + b.
-// One warp per (tile, g, w); grid-stride over those jobs.
+// Row-major population -> facility-major tiles, for every instance of the
+// launch.  colT[col_base + (tile*32W + j)*G + g] (j < 32W) = bits over
+// individuals tile*32G + 32g + b of that instance.  One warp per (instance,
+// tile, g, w) job; grid-stride over the jobs.
 // ---------------------------------------------------------------------------
-__global__ void k_pop_to_columns(const uint32_t *__restrict__ masks, int64_t pop, int32_t W, int32_t G,
-                                 int64_t tiles, uint32_t *__restrict__ colT)
+__global__ void k_pop_to_columns(const uint32_t *__restrict__ masks, const pm_prob *__restrict__ probs, int K,
+                                 pm_prob one, int64_t jobs, int32_t G, uint32_t *__restrict__ colT)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
-    const int64_t jobs = tiles * G * W;
     for (int64_t job = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); job < jobs;
          job += warps_total) {
-        const int32_t w = (int32_t)(job % W);
-        const int64_t tg = job / W;
+        const pm_prob *pr = &one;
+        if (K > 1)
+            pr = probs + find_prob(K, job, [&](int k) { return probs[k].job_base; });
+        const int64_t lj = job - pr->job_base;
+        const int32_t W = pr->W;
+        const int32_t w = (int32_t)(lj % W);
+        const int64_t tg = lj / W;
         const int32_t g = (int32_t)(tg % G);
         const int64_t tile = tg / G;
         const int64_t t = tile * 32 * G + 32 * g + lane;
-        const uint32_t x = (t < pop) ? __ldg(masks + t * W + w) : 0u;
+        const uint32_t x = (t < pr->pop) ? __ldg(masks + pr->word_base + t * W + w) : 0u;
         const uint32_t col = pm_transpose32(x, lane);
-        colT[(tile * (int64_t)W * 32 + (int64_t)w * 32 + lane) * G + g] = col;
+        colT[pr->col_base + (tile * (int64_t)W * 32 + (int64_t)w * 32 + lane) * G + g] = col;
     }
 }
 
@@ -137,22 +157,20 @@ struct ScanEpilogue {
     uint32_t *cur_masks;         // mode 1
     const uint32_t *cand_masks;  // mode 1
     uint8_t *improved;           // mode 1, nullable
-    int32_t W;
 };
 
 // ---------------------------------------------------------------------------
-// The column scan kernel (with the split reduction and epilogue fused).
-// Persistent: CTA b takes work items b, b + gridDim.x, ...; item = split *
-// tiles + tile, so the CTAs running at the same time walk the same clients
-// for different tiles and the rows they stream are shared through L2.
+// The column scan kernel (with the split reduction and epilogue fused), over
+// every instance of the launch.  Persistent: CTA b takes work items b, b +
+// gridDim.x, ...; within an instance item = split * tiles + tile, so the CTAs
+// running at the same time walk the same clients for different tiles and
+// the rows they stream are shared through L2.
 // ---------------------------------------------------------------------------
 template <int G>
-__global__ void __launch_bounds__(1024) k_scan_columns(const uint16_t *__restrict__ pi,
-                                                       const int32_t *__restrict__ delta, int64_t n, int32_t L,
-                                                       int64_t stride, const uint32_t *__restrict__ colT,
-                                                       int32_t W, int64_t pop, const uint32_t *__restrict__ active,
-                                                       int64_t tiles, int64_t clients_per_split, int splits,
-                                                       unsigned long long *__restrict__ partial,
+__global__ void __launch_bounds__(1024) k_scan_columns(const pm_prob *__restrict__ probs, int K, pm_prob one,
+                                                       int64_t items, const uint32_t *__restrict__ colT,
+                                                       const uint32_t *__restrict__ active,
+                                                       unsigned long long *__restrict__ accum,
                                                        int *__restrict__ tickets, int *__restrict__ err,
                                                        ScanEpilogue ep)
 {
@@ -161,12 +179,11 @@ __global__ void __launch_bounds__(1024) k_scan_columns(const uint16_t *__restric
     __shared__ uint32_t a0_s[G];
     __shared__ __align__(8) uint64_t bar;
     __shared__ int last_s;
+    __shared__ pm_prob pr_s;
 
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
-    const uint32_t tile_bytes = (uint32_t)W * 32u * G * 4u;
-    const int64_t items = tiles * splits;
 
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
@@ -175,15 +192,26 @@ __global__ void __launch_bounds__(1024) k_scan_columns(const uint16_t *__restric
     __syncthreads();
 
     uint32_t phase = 0;
-    int64_t loaded_tile = -1;
+    int64_t loaded_tile = -1;  // global tile index of the tile in shared memory
     for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
-        const int64_t tile = item % tiles;
-        const int split = (int)(item / tiles);
-        const int64_t ind0 = tile * 32 * G;
-        const bool reload = tile != loaded_tile;
+        if (threadIdx.x == 0)
+            pr_s = (K > 1) ? probs[find_prob(K, item, [&](int k) { return probs[k].item_base; })] : one;
+        __syncthreads();
+        const pm_prob &pr = pr_s;
+        const int64_t li = item - pr.item_base;
+        const int64_t tile = li % pr.tiles;
+        const int64_t split = li / pr.tiles;
+        const int64_t gtile = pr.tile_base + tile;
+        const int64_t ind0 = tile * 32 * G;  // first individual of the tile, within the instance
+        const int32_t W = pr.W, L = pr.L;
+        const int64_t pop = pr.pop, stride = pr.stride;
+        const uint16_t *__restrict__ pi = pr.pi;
+        const int32_t *__restrict__ delta = pr.delta;
+        const bool reload = gtile != loaded_tile;
         if (reload && threadIdx.x == 0) {
+            const uint32_t tile_bytes = (uint32_t)W * 32u * G * 4u;
             mbar_arrive_expect_tx(&bar, tile_bytes);
-            const char *src = reinterpret_cast<const char *>(colT + tile * (int64_t)W * 32 * G);
+            const char *src = reinterpret_cast<const char *>(colT + pr.col_base + tile * (int64_t)W * 32 * G);
             char *dst = reinterpret_cast<char *>(colbits);
             for (uint32_t off = 0; off < tile_bytes; off += 32768u) {
                 const uint32_t sz = (tile_bytes - off) < 32768u ? (tile_bytes - off) : 32768u;
@@ -192,7 +220,8 @@ __global__ void __launch_bounds__(1024) k_scan_columns(const uint16_t *__restric
         }
         if (warp < G) {
             const int64_t t = ind0 + 32 * warp + lane;
-            const bool on = (t < pop) && (active == nullptr || ((__ldg(active + (t >> 5)) >> (t & 31)) & 1u));
+            const int64_t tg = pr.ind_base + t;
+            const bool on = (t < pop) && (active == nullptr || ((__ldg(active + (tg >> 5)) >> (tg & 31)) & 1u));
             const uint32_t b = __ballot_sync(PM_FULL_MASK, on);
             if (lane == 0)
                 a0_s[warp] = b;
@@ -201,8 +230,8 @@ __global__ void __launch_bounds__(1024) k_scan_columns(const uint16_t *__restric
             acc_s[i] = 0ull;
 
         // first chunks of this warp's first two clients, loaded while the tile lands
-        const int64_t c_begin = (int64_t)split * clients_per_split;
-        const int64_t c_end = (c_begin + clients_per_split < n) ? c_begin + clients_per_split : n;
+        const int64_t c_begin = split * pr.cps;
+        const int64_t c_end = (c_begin + pr.cps < pr.n) ? c_begin + pr.cps : pr.n;
         auto load = [&](int64_t cc, int base, uint32_t &j, int32_t &dl) {
             const int r = base + lane;
             if (cc < c_end && r < L) {
@@ -234,7 +263,7 @@ __global__ void __launch_bounds__(1024) k_scan_columns(const uint16_t *__restric
                 }
             }
             phase ^= 1u;
-            loaded_tile = tile;
+            loaded_tile = gtile;
         }
         __syncthreads();
 
@@ -345,18 +374,18 @@ __global__ void __launch_bounds__(1024) k_scan_columns(const uint16_t *__restric
         __syncthreads();
 
         bool finish = true;
-        if (splits > 1) {
-            // add this split's sums into the tile's accumulators; the last split of the tile
+        if (pr.splits > 1) {
+            // add this split's sums into the instance's accumulators; the last split of the tile
             // (atomic ticket) reads the totals and leaves the accumulators zero again
             for (int i = threadIdx.x; i < G * 32; i += blockDim.x) {
                 const int64_t t = ind0 + i;
                 if (t < pop && acc_s[i] != 0ull)
-                    atomicAdd(partial + t, acc_s[i]);
+                    atomicAdd(accum + pr.ind_base + t, acc_s[i]);
             }
             __threadfence();
             __syncthreads();
             if (threadIdx.x == 0)
-                last_s = (atomicAdd(tickets + tile, 1) == splits - 1) ? 1 : 0;
+                last_s = (atomicAdd(tickets + gtile, 1) == (int)pr.splits - 1) ? 1 : 0;
             __syncthreads();
             finish = last_s != 0;
             if (finish) {
@@ -364,12 +393,12 @@ __global__ void __launch_bounds__(1024) k_scan_columns(const uint16_t *__restric
                 for (int i = threadIdx.x; i < G * 32; i += blockDim.x) {
                     const int64_t t = ind0 + i;
                     if (t < pop) {
-                        acc_s[i] = __ldcg(partial + t);
-                        partial[t] = 0ull;
+                        acc_s[i] = __ldcg(accum + pr.ind_base + t);
+                        accum[pr.ind_base + t] = 0ull;
                     }
                 }
                 if (threadIdx.x == 0)
-                    tickets[tile] = 0;  // every CTA of the tile has taken its ticket: reset for the next launch
+                    tickets[gtile] = 0;  // every CTA of the tile has taken its ticket: reset for the next launch
                 __syncthreads();
             }
         }
@@ -383,19 +412,20 @@ __global__ void __launch_bounds__(1024) k_scan_columns(const uint16_t *__restric
                     continue;
                 const int64_t sum = (int64_t)acc_s[i];
                 if (ep.costs != nullptr && lane == 0)
-                    ep.costs[t] = sum;
-                if (ep.mode == 1 && sum < ep.cur_cost[t]) {
-                    for (int q = lane; q < ep.W; q += 32)
-                        ep.cur_masks[t * ep.W + q] = ep.cand_masks[t * ep.W + q];
+                    ep.costs[pr.out_base + t] = sum;
+                if (ep.mode == 1 && sum < ep.cur_cost[pr.ind_base + t]) {
+                    const int64_t row = pr.word_base + t * W;
+                    for (int q = lane; q < W; q += 32)
+                        ep.cur_masks[row + q] = ep.cand_masks[row + q];
                     if (lane == 0) {
-                        ep.cur_cost[t] = sum;
+                        ep.cur_cost[pr.ind_base + t] = sum;
                         if (ep.improved)
-                            ep.improved[t] = 1;
+                            ep.improved[pr.ind_base + t] = 1;
                     }
                 }
             }
         }
-        __syncthreads();  // shared state (tile, acc_s, a0_s) is reused by the next item
+        __syncthreads();  // shared state (tile, acc_s, a0_s, pr_s) is reused by the next item
     }
 }
 
@@ -466,7 +496,7 @@ __global__ void __launch_bounds__(256) k_scan_rows(const uint16_t *__restrict__ 
 // individual).
 // ---------------------------------------------------------------------------
 __global__ void k_reduce_accept(unsigned long long *__restrict__ partial, int splits, int64_t pop,
-                                const uint32_t *__restrict__ active, ScanEpilogue ep)
+                                const uint32_t *__restrict__ active, ScanEpilogue ep, int32_t W)
 {
     const int lane = threadIdx.x & 31;
     const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -486,8 +516,8 @@ __global__ void k_reduce_accept(unsigned long long *__restrict__ partial, int sp
     if (ep.costs != nullptr && lane == 0)
         ep.costs[t] = sum;
     if (ep.mode == 1 && sum < ep.cur_cost[t]) {
-        for (int w = lane; w < ep.W; w += 32)
-            ep.cur_masks[t * ep.W + w] = ep.cand_masks[t * ep.W + w];
+        for (int w = lane; w < W; w += 32)
+            ep.cur_masks[t * W + w] = ep.cand_masks[t * W + w];
         if (lane == 0) {
             ep.cur_cost[t] = sum;
             if (ep.improved)
@@ -611,14 +641,31 @@ size_t pm_plan_column_bytes(const pm_instance *inst, const pm_eval_plan &plan)
     return (size_t)plan.tiles * column_smem_bytes(inst->W, plan.groups);
 }
 
-pm_status pm_launch_eval(const pm_instance *inst, const pm_eval_plan &plan, const uint32_t *masks, int64_t pop,
-                         const uint32_t *active, int64_t *costs, int64_t *partials_i64, int *tickets, uint32_t *colT,
-                         int *err, const pm_accept_args &acc, cudaStream_t stream)
+pm_prob pm_single_prob(const pm_instance *inst, const pm_eval_plan &plan, int64_t pop)
 {
-    if (pop <= 0)
+    pm_prob pr{};
+    pr.pi = inst->pi;
+    pr.delta = inst->delta;
+    pr.n = inst->n;
+    pr.stride = inst->stride;
+    pr.L = (int32_t)inst->L;
+    pr.W = (int32_t)inst->W;
+    pr.m = (int32_t)inst->m;
+    pr.p = (int32_t)inst->p;
+    pr.pop = pop;
+    pr.tiles = plan.tiles;
+    pr.splits = plan.splits;
+    pr.cps = pm_ceil_div(inst->n, plan.splits);
+    return pr;  // every base 0
+}
+
+// Enqueue the transpose (unless the caller wrote the columns) and the column
+// scan of a launch; smem = the tile bytes of the launch's widest instance.
+pm_status pm_launch_scan(const pm_scan_launch &L, const pm_accept_args &acc, int64_t *costs, size_t smem,
+                         cudaStream_t stream)
+{
+    if (L.items <= 0)
         return PM_OK;
-    unsigned long long *partials = reinterpret_cast<unsigned long long *>(partials_i64);
-    const int64_t cps = pm_ceil_div(inst->n, plan.splits);
     ScanEpilogue ep;
     ep.mode = acc.mode;
     ep.costs = costs;
@@ -626,38 +673,66 @@ pm_status pm_launch_eval(const pm_instance *inst, const pm_eval_plan &plan, cons
     ep.cur_masks = acc.cur_masks;
     ep.cand_masks = acc.cand_masks;
     ep.improved = acc.improved;
-    ep.W = (int32_t)inst->W;
-    if (plan.groups) {
-        const int G = plan.groups;
-        if (!acc.columns_ready) {
-            const int64_t jobs = plan.tiles * G * inst->W;
-            const int threads = 256;
-            const int64_t blocks = std::min<int64_t>(pm_ceil_div(jobs, threads / 32), (int64_t)inst->sm_count * 16);
-            k_pop_to_columns<<<(unsigned)blocks, threads, 0, stream>>>(masks, pop, (int32_t)inst->W, G, plan.tiles,
-                                                                       colT);
-            PM_CUDA(cudaGetLastError());
-        }
-        const size_t smem = column_smem_bytes(inst->W, G);
-        const unsigned grid = (unsigned)plan.grid;
-        const int threadsc = plan.warps * 32;
-#define PM_SCAN_ARGS                                                                                        \
-    inst->pi, inst->delta, inst->n, (int32_t)inst->L, inst->stride, colT, (int32_t)inst->W, pop, active,     \
-        plan.tiles, cps, plan.splits, partials, tickets, err, ep
-        switch (G) {
-        case 1:
-            k_scan_columns<1><<<grid, threadsc, smem, stream>>>(PM_SCAN_ARGS);
-            break;
-        case 2:
-            k_scan_columns<2><<<grid, threadsc, smem, stream>>>(PM_SCAN_ARGS);
-            break;
-        default:
-            k_scan_columns<4><<<grid, threadsc, smem, stream>>>(PM_SCAN_ARGS);
-            break;
-        }
-#undef PM_SCAN_ARGS
+    const int G = L.groups;
+    if (!acc.columns_ready) {
+        const int threads = 256;
+        const int64_t blocks = std::min<int64_t>(pm_ceil_div(L.jobs, threads / 32), (int64_t)2048);
+        k_pop_to_columns<<<(unsigned)blocks, threads, 0, stream>>>(L.masks, L.probs_dev, L.K, L.one, L.jobs, G,
+                                                                   L.colT);
         PM_CUDA(cudaGetLastError());
-        return PM_OK;
     }
+    const unsigned grid = (unsigned)L.grid;
+    const int threads = L.warps * 32;
+    unsigned long long *accum = reinterpret_cast<unsigned long long *>(L.accum);
+#define PM_SCAN_ARGS L.probs_dev, L.K, L.one, L.items, L.colT, L.active, accum, L.tickets, L.err, ep
+    switch (G) {
+    case 1:
+        k_scan_columns<1><<<grid, threads, smem, stream>>>(PM_SCAN_ARGS);
+        break;
+    case 2:
+        k_scan_columns<2><<<grid, threads, smem, stream>>>(PM_SCAN_ARGS);
+        break;
+    default:
+        k_scan_columns<4><<<grid, threads, smem, stream>>>(PM_SCAN_ARGS);
+        break;
+    }
+#undef PM_SCAN_ARGS
+    PM_CUDA(cudaGetLastError());
+    return PM_OK;
+}
+
+pm_status pm_launch_eval(const pm_instance *inst, const pm_eval_plan &plan, const uint32_t *masks, int64_t pop,
+                         const uint32_t *active, int64_t *costs, int64_t *partials_i64, int *tickets, uint32_t *colT,
+                         int *err, const pm_accept_args &acc, cudaStream_t stream)
+{
+    if (pop <= 0)
+        return PM_OK;
+    unsigned long long *partials = reinterpret_cast<unsigned long long *>(partials_i64);
+    if (plan.groups) {
+        pm_scan_launch L;
+        L.groups = plan.groups;
+        L.warps = plan.warps;
+        L.grid = plan.grid;
+        L.K = 1;
+        L.one = pm_single_prob(inst, plan, pop);
+        L.items = plan.tiles * plan.splits;
+        L.jobs = plan.tiles * plan.groups * inst->W;
+        L.masks = masks;
+        L.colT = colT;
+        L.active = active;
+        L.accum = partials_i64;
+        L.tickets = tickets;
+        L.err = err;
+        return pm_launch_scan(L, acc, costs, column_smem_bytes(inst->W, plan.groups), stream);
+    }
+    ScanEpilogue ep;
+    ep.mode = acc.mode;
+    ep.costs = costs;
+    ep.cur_cost = acc.cur_cost;
+    ep.cur_masks = acc.cur_masks;
+    ep.cand_masks = acc.cand_masks;
+    ep.improved = acc.improved;
+    const int64_t cps = pm_ceil_div(inst->n, plan.splits);
     const size_t smem = (size_t)plan.warps * inst->W * 4;
     dim3 grid((unsigned)plan.tiles, (unsigned)plan.splits);
     k_scan_rows<<<grid, plan.warps * 32, smem, stream>>>(inst->pi, inst->delta, inst->n, (int32_t)inst->L,
@@ -666,7 +741,8 @@ pm_status pm_launch_eval(const pm_instance *inst, const pm_eval_plan &plan, cons
     PM_CUDA(cudaGetLastError());
     const int64_t threads = 256;
     const int64_t blocks = pm_ceil_div(pop * 32, threads);
-    k_reduce_accept<<<(unsigned)blocks, (unsigned)threads, 0, stream>>>(partials, plan.splits, pop, active, ep);
+    k_reduce_accept<<<(unsigned)blocks, (unsigned)threads, 0, stream>>>(partials, plan.splits, pop, active, ep,
+                                                                        (int32_t)inst->W);
     PM_CUDA(cudaGetLastError());
     return PM_OK;
 }

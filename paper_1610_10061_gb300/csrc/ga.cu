@@ -1,5 +1,6 @@
 // The genetic algorithm of Sections 3.1, 3.2.2 and 4.3-4.5, run entirely on
-// the device.
+// the device, for one instance or for a batch of instances at once (every
+// kernel below covers all instances of the GA in one launch).
 //
 // One generation (the paper's Evolve call plus the host's population
 // renewal and migration):
@@ -8,26 +9,30 @@
 //                    a 64-bit rank cannot index C(m,p) for the sizes used
 //                    here); for generation g > 0 slot 0 of every deme gets that
 //                    deme's best of generation g-1 (Section 4.5, variant (i)).
-//   evaluate         the fitness kernels (Section 4.2).
+//   evaluate         the column scan (fitness.cu, Section 4.2).
 //   crossover r      k_ga_crossover builds every child (butterfly partner
 //                    t XOR (D >> (1 + r mod lg D)), Section 3.2.2 step 3), the
-//                    children are evaluated, and the reduction kernel replaces
-//                    a parent by its child iff strictly cheaper.  Children are
-//                    built from the population as it was when the round
-//                    started (the acceptance runs after all are built).
+//                    scan evaluates the children and replaces a parent by its
+//                    child iff strictly cheaper.  Children are built from the
+//                    population as it was when the round started.
 //   mutation q       k_ga_mutate rotates the whole bitset or a block of it
 //                    (Section 4.4) for individuals not yet improved in this
 //                    generation; the first strictly cheaper mutant replaces
 //                    the individual (Section 3.2.2 step 5).
 //   k_ga_deme_best   lowest (cost, index) per deme (Section 3.2.2 step 7).
-//   k_ga_finish      global best (strict improvement), saturation counter,
-//                    trace, generation counters, loop condition.
-// The loop is one CUDA graph: a gate kernel and a conditional while-node
-// whose body is one generation; the body's last kernel sets the condition.
+//   k_ga_finish      per instance: global best (strict improvement),
+//                    saturation counter, trace, counters; the last instance
+//                    to finish sets the loop condition.
+// The operators also write the facility-major copy of their output that the
+// scan reads, so no evaluation needs a separate transpose.  The loop is one
+// CUDA graph: a gate kernel and a conditional while-node whose body is one
+// generation.  An instance that reached its saturation limit stops: its
+// kernels do nothing while the others go on.
 //
 // Random numbers: Philox4x32-10 (Salmon et al., SC'11), stateless, keyed by
 // (seed) with counter (generation, unit, op * 2^16 + slot / 4, stream id);
-// draw `slot` is word slot & 3.  U[0, N) = floor(u * N / 2^32).
+// draw `slot` is word slot & 3.  U[0, N) = floor(u * N / 2^32).  Instance k
+// of a batch uses stream id (base + k).
 
 #include <cstdlib>
 #include <cstring>
@@ -36,24 +41,46 @@
 
 #include "pm_common.cuh"
 
+// batch.cu
+pm_status pm_batch_ga_plan(pm_batch *b, int64_t pop, pm_multi_plan &out);
+const std::vector<const pm_instance *> &pm_batch_instances(const pm_batch *b);
+
 namespace {
 
 constexpr uint32_t OP_INIT = 0x001u;
 constexpr uint32_t OP_XOVER = 0x100u;
 constexpr uint32_t OP_MUT = 0x200u;
 
-struct ga_dev {
+struct ga_dev {            // per instance
     long long gen;         // index of the next generation
-    long long remaining;   // generations left in the current step
     long long best_cost;   // -1 until the first generation finishes
     long long sat;         // generations since the best last improved
     long long evals;       // fitness evaluations so far
-    long long step_gens;   // generations run in the current step
     long long total_gens;  // generations run since creation
     long long saturation;  // S (0 = off)
-    long long *trace;      // device trace of the current step
-    int stop;
+    long long *trace;      // this instance's trace for the current step
+    int stop;              // saturation reached
     int pad;
+};
+
+struct ga_glob {
+    long long remaining;  // generations left in the current step
+    long long step_gens;  // generations run in the current step
+    int alive;            // instances not stopped
+    int done;             // k_ga_finish tickets
+};
+
+struct ga_prob {  // per instance layout of the GA arrays
+    int64_t pop, D, NB;
+    int32_t W, m, p, lgD;
+    int64_t ind_base;    // cost, improved, active bits (multiple of 32)
+    int64_t word_base;   // X, Xc rows
+    int64_t grp_base;    // first 32-individual group
+    int64_t deme_base;   // deme_cost index
+    int64_t dword_base;  // deme_best rows
+    int64_t best_base;   // best bitset
+    int64_t col_base;    // facility-major tiles
+    uint32_t sid, pad;
 };
 
 // ----------------------------- Philox4x32-10 --------------------------------
@@ -101,125 +128,177 @@ __device__ __forceinline__ uint32_t lowest_bits(uint32_t x, int k)
     return r;
 }
 
-// ------------------------------- kernels -----------------------------------
-
-__global__ void k_ga_begin(ga_dev *st, long long gens, long long *trace)
+// Largest k with base(k) <= x.
+template <typename F>
+__device__ __forceinline__ int find_k(int K, int64_t x, F base)
 {
-    st->remaining = gens;
-    st->step_gens = 0;
-    st->trace = trace;
+    int lo = 0, hi = K - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (base(mid) <= x)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
 }
 
-__global__ void k_ga_gate(ga_dev *st, cudaGraphConditionalHandle h)
+// The instance owning 32-individual group `grp` (by value).
+__device__ __forceinline__ ga_prob prob_of_group(const ga_prob *gps, int K, const ga_prob &one, int64_t grp, int &k)
 {
-    cudaGraphSetConditional(h, (st->remaining > 0 && !st->stop) ? 1u : 0u);
+    if (K == 1) {
+        k = 0;
+        return one;
+    }
+    k = find_k(K, grp, [&](int i) { return gps[i].grp_base; });
+    return gps[k];
 }
 
-// Where the operator kernels also write the facility-major copy the column
-// fitness kernel reads: colT[tile][j][g] for tiles of 32*G individuals
+// Where the operator kernels write the facility-major copy the scan reads
 // (colT == nullptr: the evaluation uses the row kernel and needs none).
 struct ColumnsOut {
     uint32_t *colT;
     int32_t G;
 };
 
-// Transpose the 32 rows (individuals t0 .. t0+31, row r at rows + r*rs) into
-// colT, one warp; rows of individuals >= P read as zero.
-__device__ __forceinline__ void write_columns(const uint32_t *rows, int64_t rs, int64_t t0, int64_t P, int32_t W,
+// Transpose 32 rows (individuals t0 .. t0+31 of one instance, row r at
+// rows + r*rs) into that instance's tiles; rows of individuals >= pop read
+// as zero.  One warp, words w_begin, w_begin + w_step, ...
+__device__ __forceinline__ void write_columns(const uint32_t *rows, int64_t rs, int64_t t0, const ga_prob &gp,
                                               ColumnsOut co, int lane, int w_begin, int w_step)
 {
     if (co.colT == nullptr)
         return;
+    const int32_t W = gp.W;
     const int64_t tile = t0 / (32 * co.G);
     const int32_t g = (int32_t)((t0 / 32) % co.G);
     for (int w = w_begin; w < W; w += w_step) {
-        const uint32_t x = (t0 + lane < P) ? rows[(int64_t)lane * rs + w] : 0u;
+        const uint32_t x = (t0 + lane < gp.pop) ? rows[(int64_t)lane * rs + w] : 0u;
         const uint32_t col = pm_transpose32(x, lane);
-        co.colT[(tile * (int64_t)W * 32 + (int64_t)w * 32 + lane) * co.G + g] = col;
+        co.colT[gp.col_base + (tile * (int64_t)W * 32 + (int64_t)w * 32 + lane) * co.G + g] = col;
     }
+}
+
+// ------------------------------- kernels -----------------------------------
+
+__global__ void k_ga_begin(ga_glob *glob, ga_dev *st, int K, long long gens, long long *trace)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < K)
+        st[k].trace = trace ? trace + (long long)k * gens : nullptr;
+    if (k == 0) {
+        glob->remaining = gens;
+        glob->step_gens = 0;
+    }
+}
+
+__global__ void k_ga_gate(const ga_glob *glob, cudaGraphConditionalHandle h)
+{
+    cudaGraphSetConditional(h, (glob->remaining > 0 && glob->alive > 0) ? 1u : 0u);
 }
 
 // Floyd sampling + migration, one warp per 32 individuals (lane = individual,
 // the bitsets in shared memory when they fit, else in place in X); also
-// clears the per-generation improved flags and writes the columns.
-__global__ void __launch_bounds__(32) k_ga_init(uint32_t *__restrict__ X, uint8_t *__restrict__ improved,
-                                                const uint32_t *__restrict__ deme_best, int64_t P, int32_t W,
-                                                int32_t m, int32_t p, int64_t D, uint64_t seed, uint32_t sid,
-                                                const ga_dev *__restrict__ st, ColumnsOut co, int rows_in_smem)
+// clears the improved flags, sets the active bits and writes the columns.
+__global__ void __launch_bounds__(32) k_ga_init(const ga_prob *__restrict__ gps, int K, ga_prob one,
+                                                uint32_t *__restrict__ X, uint8_t *__restrict__ improved,
+                                                uint32_t *__restrict__ active, const uint32_t *__restrict__ deme_best,
+                                                uint64_t seed, const ga_dev *__restrict__ st, ColumnsOut co,
+                                                int rows_in_smem)
 {
     extern __shared__ uint32_t rows_s[];  // [32][Ws], Ws = W | 1 (odd stride: conflict-free transposes)
+    int k;
+    const ga_prob gp = prob_of_group(gps, K, one, blockIdx.x, k);
     const int lane = threadIdx.x;
-    const int64_t t0 = (int64_t)blockIdx.x * 32;
+    const int64_t t0 = (blockIdx.x - gp.grp_base) * 32;
     const int64_t t = t0 + lane;
-    const int32_t Ws = W | 1;
-    const uint32_t gen = (uint32_t)st->gen;
-    uint32_t *row = rows_in_smem ? rows_s + (int64_t)lane * Ws : X + t * W;
-    if (t < P) {
-        improved[t] = 0;
-        if (gen > 0 && (t % D) == 0) {
-            const uint32_t *src = deme_best + (t / D) * W;
+    const int32_t W = gp.W, Ws = W | 1;
+    if (st[k].stop) {
+        if (lane == 0)
+            active[(gp.ind_base + t0) >> 5] = 0u;
+        return;
+    }
+    const uint32_t gen = (uint32_t)st[k].gen;
+    uint32_t *row = rows_in_smem ? rows_s + (int64_t)lane * Ws : X + gp.word_base + t * W;
+    if (t < gp.pop) {
+        improved[gp.ind_base + t] = 0;
+        if (gen > 0 && (t % gp.D) == 0) {
+            const uint32_t *src = deme_best + gp.dword_base + (t / gp.D) * W;
             for (int w = 0; w < W; ++w)
                 row[w] = src[w];
         } else {
             for (int w = 0; w < W; ++w)
                 row[w] = 0u;
             uint4 v = make_uint4(0, 0, 0, 0);
-            for (int q = 0; q < p; ++q) {
+            for (int q = 0; q < gp.p; ++q) {
                 if ((q & 3) == 0)
-                    v = draw_block(seed, gen, (uint32_t)t, OP_INIT, (uint32_t)q >> 2, sid);
-                const uint32_t j = (uint32_t)(m - p + q);
+                    v = draw_block(seed, gen, (uint32_t)t, OP_INIT, (uint32_t)q >> 2, gp.sid);
+                const uint32_t j = (uint32_t)(gp.m - gp.p + q);
                 const uint32_t c = uniform_below(word_of(v, q & 3), j + 1);
                 const uint32_t pick = ((row[c >> 5] >> (c & 31)) & 1u) ? j : c;
                 row[pick >> 5] |= 1u << (pick & 31);
             }
         }
     }
+    const uint32_t on = __ballot_sync(PM_FULL_MASK, t < gp.pop);
+    if (lane == 0)
+        active[(gp.ind_base + t0) >> 5] = on;
     __syncwarp();
     if (rows_in_smem) {
         // copy the 32 rows out (rows of consecutive individuals are contiguous in X)
-        const int64_t nrows = (P - t0) < 32 ? (P - t0) : 32;
+        const int64_t nrows = (gp.pop - t0) < 32 ? (gp.pop - t0) : 32;
         for (int64_t idx = lane; idx < nrows * W; idx += 32)
-            X[t0 * W + idx] = rows_s[(idx / W) * Ws + (idx % W)];
-        write_columns(rows_s, Ws, t0, P, W, co, lane, 0, 1);
+            X[gp.word_base + t0 * W + idx] = rows_s[(idx / W) * Ws + (idx % W)];
+        write_columns(rows_s, Ws, t0, gp, co, lane, 0, 1);
     } else {
-        write_columns(X + t0 * W, W, t0, P, W, co, lane, 0, 1);
+        write_columns(X + gp.word_base + t0 * W, W, t0, gp, co, lane, 0, 1);
     }
 }
 
 // One crossover round (Section 4.3).  CTA = 32 warps = 32 individuals; warp
-// k builds the child of individual t0 + k.  The positions r1, r1+1, ...
+// j builds the child of individual t0 + j.  The positions r1, r1+1, ...
 // (circularly) are visited as W+1 segments: word w0 = r1/32 from bit r1%32
 // up, the following words, and word w0 below bit r1%32.  A warp scan of the
 // per-segment counts of 0->1 and 1->0 candidates (C != couple) tells each
 // segment how many of its candidates to take; within a segment the lowest
 // bits (earliest positions) come first.
-__global__ void __launch_bounds__(1024) k_ga_crossover(const uint32_t *__restrict__ X, uint32_t *__restrict__ Xc,
-                                                       uint32_t *__restrict__ active, int64_t P, int32_t W, int32_t m,
-                                                       int32_t p, int64_t stride, uint32_t round, uint64_t seed,
-                                                       uint32_t sid, ga_dev *__restrict__ st, ColumnsOut co)
+__global__ void __launch_bounds__(1024) k_ga_crossover(const ga_prob *__restrict__ gps, int K, ga_prob one,
+                                                       const uint32_t *__restrict__ X, uint32_t *__restrict__ Xc,
+                                                       uint32_t *__restrict__ active, uint32_t round, uint64_t seed,
+                                                       ga_dev *__restrict__ st, ColumnsOut co)
 {
     __shared__ uint32_t valid_s;
+    int k;
+    const ga_prob gp = prob_of_group(gps, K, one, blockIdx.x, k);
     const int lane = threadIdx.x & 31;
-    const int k = threadIdx.x >> 5;
-    const int64_t t0 = (int64_t)blockIdx.x * 32;
-    const int64_t t = t0 + k;
+    const int j = threadIdx.x >> 5;
+    const int64_t t0 = (blockIdx.x - gp.grp_base) * 32;
+    const int64_t t = t0 + j;
+    const int32_t W = gp.W;
+    if (st[k].stop) {
+        if (threadIdx.x == 0)
+            active[(gp.ind_base + t0) >> 5] = 0u;
+        return;
+    }
     if (threadIdx.x == 0)
         valid_s = 0u;
     __syncthreads();
-    if (t < P) {
-        const uint32_t gen = (uint32_t)st->gen;
+    const int p = gp.p;
+    if (t < gp.pop) {
+        const uint32_t gen = (uint32_t)st[k].gen;
+        const int64_t stride = gp.D >> (1 + ((int)round % gp.lgD));
         const int64_t partner = t ^ stride;
         const uint32_t pair = (uint32_t)(t < partner ? t : partner);
-        const uint4 v = draw_block(seed, gen, pair, OP_XOVER + round, 0, sid);
-        const uint32_t r1 = uniform_below(v.x, (uint32_t)m);
+        const uint4 v = draw_block(seed, gen, pair, OP_XOVER + round, 0, gp.sid);
+        const uint32_t r1 = uniform_below(v.x, (uint32_t)gp.m);
         const int i = 1 + (int)uniform_below(v.y, (uint32_t)(p / 2));
-        const uint32_t *C = X + t * W;
-        const uint32_t *K = X + partner * W;
-        uint32_t *F = Xc + t * W;
+        const uint32_t *C = X + gp.word_base + t * W;
+        const uint32_t *Kp = X + gp.word_base + partner * W;
+        uint32_t *F = Xc + gp.word_base + t * W;
         const int w0 = (int)(r1 >> 5);
         const uint32_t b0 = r1 & 31u;
-        int c01 = 0, c10 = 0;      // candidates in the segments of earlier rounds
-        uint32_t w0change = 0u;    // changes to word w0 (first and last segment)
+        int c01 = 0, c10 = 0;    // candidates in the segments of earlier rounds
+        uint32_t w0change = 0u;  // changes to word w0 (first and last segment)
         for (int base = 0; base <= W; base += 32) {
             const int sidx = base + lane;
             uint32_t z = 0u, o = 0u, cw = 0u;
@@ -239,13 +318,13 @@ __global__ void __launch_bounds__(1024) k_ga_crossover(const uint32_t *__restric
                     seg = b0 ? ((1u << b0) - 1u) : 0u;
                 }
                 cw = C[w];
-                const uint32_t kw = K[w];
+                const uint32_t kw = Kp[w];
                 z = ~cw & kw & seg;
                 o = cw & ~kw & seg;
             }
             // exclusive warp scan of the two counts packed in one word
             const uint32_t nz = __popc(z), no = __popc(o);
-            uint32_t packed = nz | (no << 16);
+            const uint32_t packed = nz | (no << 16);
             uint32_t incl = packed;
 #pragma unroll
             for (int off = 1; off < 32; off <<= 1) {
@@ -273,15 +352,15 @@ __global__ void __launch_bounds__(1024) k_ga_crossover(const uint32_t *__restric
         if (lane == 0)
             F[w0] = C[w0] ^ w0change;
         if (lane == 0 && p / 2 > 0 && c01 >= i && c10 >= i)
-            atomicOr(&valid_s, 1u << k);
+            atomicOr(&valid_s, 1u << j);
     }
     __syncthreads();
-    if (threadIdx.x == 0 && t0 < P) {
-        active[t0 >> 5] = valid_s;
+    if (threadIdx.x == 0) {
+        active[(gp.ind_base + t0) >> 5] = valid_s;
         if (valid_s)
-            atomicAdd(reinterpret_cast<unsigned long long *>(&st->evals), (unsigned long long)__popc(valid_s));
+            atomicAdd(reinterpret_cast<unsigned long long *>(&st[k].evals), (unsigned long long)__popc(valid_s));
     }
-    write_columns(Xc + t0 * W, W, t0, P, W, co, lane, k, 32);
+    write_columns(Xc + gp.word_base + t0 * W, W, t0, gp, co, lane, j, 32);
 }
 
 // 32 bits of the bitset C starting at bit position s (s may be as low as
@@ -304,28 +383,37 @@ __device__ __forceinline__ uint32_t range_mask(int64_t lo, int64_t hi)  // bits 
     return upto & ~below;
 }
 
-// One mutation try (Section 4.4).  CTA = 32 warps = 32 individuals; warp k
-// rotates individual t0 + k's bits [a, a+len) left by kl: F[a+j] =
-// C[a + (j+kl) mod len].  Each output word is at most three pieces, each a
+// One mutation try (Section 4.4).  CTA = 32 warps = 32 individuals; warp j
+// rotates individual t0 + j's bits [a, a+len) left by kl: F[a+i] =
+// C[a + (i+kl) mod len].  Each output word is at most three pieces, each a
 // funnel-shifted 32-bit read of C.
-__global__ void __launch_bounds__(1024) k_ga_mutate(const uint32_t *__restrict__ X, uint32_t *__restrict__ Xc,
-                                                    uint32_t *__restrict__ active, const uint8_t *__restrict__ improved,
-                                                    int64_t P, int32_t W, int32_t m, uint32_t q, uint64_t seed,
-                                                    uint32_t sid, ga_dev *__restrict__ st, ColumnsOut co)
+__global__ void __launch_bounds__(1024) k_ga_mutate(const ga_prob *__restrict__ gps, int K, ga_prob one,
+                                                    const uint32_t *__restrict__ X, uint32_t *__restrict__ Xc,
+                                                    uint32_t *__restrict__ active,
+                                                    const uint8_t *__restrict__ improved, uint32_t q, uint64_t seed,
+                                                    ga_dev *__restrict__ st, ColumnsOut co)
 {
     __shared__ uint32_t on_s;
+    int k;
+    const ga_prob gp = prob_of_group(gps, K, one, blockIdx.x, k);
     const int lane = threadIdx.x & 31;
-    const int k = threadIdx.x >> 5;
-    const int64_t t0 = (int64_t)blockIdx.x * 32;
-    const int64_t t = t0 + k;
+    const int j = threadIdx.x >> 5;
+    const int64_t t0 = (blockIdx.x - gp.grp_base) * 32;
+    const int64_t t = t0 + j;
+    const int32_t W = gp.W, m = gp.m;
+    if (st[k].stop) {
+        if (threadIdx.x == 0)
+            active[(gp.ind_base + t0) >> 5] = 0u;
+        return;
+    }
     if (threadIdx.x == 0)
         on_s = 0u;
     __syncthreads();
-    if (t < P && improved[t] == 0) {
+    if (t < gp.pop && improved[gp.ind_base + t] == 0) {
         if (lane == 0)
-            atomicOr(&on_s, 1u << k);
-        const uint32_t gen = (uint32_t)st->gen;
-        const uint4 v0 = draw_block(seed, gen, (uint32_t)t, OP_MUT + q, 0, sid);
+            atomicOr(&on_s, 1u << j);
+        const uint32_t gen = (uint32_t)st[k].gen;
+        const uint4 v0 = draw_block(seed, gen, (uint32_t)t, OP_MUT + q, 0, gp.sid);
         const uint32_t kind = uniform_below(v0.x, 2u);
         const uint32_t right = uniform_below(v0.y, 2u);
         int64_t a, len, kk;
@@ -334,7 +422,7 @@ __global__ void __launch_bounds__(1024) k_ga_mutate(const uint32_t *__restrict__
             len = m;
             kk = 1 + uniform_below(v0.z, (uint32_t)(m - 1));
         } else {
-            const uint4 v1 = draw_block(seed, gen, (uint32_t)t, OP_MUT + q, 1, sid);
+            const uint4 v1 = draw_block(seed, gen, (uint32_t)t, OP_MUT + q, 1, gp.sid);
             const uint32_t x = uniform_below(v0.z, (uint32_t)m);
             uint32_t y = uniform_below(v0.w, (uint32_t)(m - 1));
             if (y >= x)
@@ -346,8 +434,8 @@ __global__ void __launch_bounds__(1024) k_ga_mutate(const uint32_t *__restrict__
         }
         const int64_t kl = right ? (len - kk) : kk;  // rotate left by kl, 1 <= kl < len
         const int64_t pwrap = a + len - kl;          // positions >= pwrap wrap to the start of the block
-        const uint32_t *C = X + t * W;
-        uint32_t *F = Xc + t * W;
+        const uint32_t *C = X + gp.word_base + t * W;
+        uint32_t *F = Xc + gp.word_base + t * W;
         for (int w = lane; w < W; w += 32) {
             const int64_t pos0 = (int64_t)w * 32;
             const int64_t in_lo = a > pos0 ? a : pos0;
@@ -368,26 +456,36 @@ __global__ void __launch_bounds__(1024) k_ga_mutate(const uint32_t *__restrict__
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0 && t0 < P) {
-        active[t0 >> 5] = on_s;
+    if (threadIdx.x == 0) {
+        active[(gp.ind_base + t0) >> 5] = on_s;
         if (on_s)
-            atomicAdd(reinterpret_cast<unsigned long long *>(&st->evals), (unsigned long long)__popc(on_s));
+            atomicAdd(reinterpret_cast<unsigned long long *>(&st[k].evals), (unsigned long long)__popc(on_s));
     }
-    write_columns(Xc + t0 * W, W, t0, P, W, co, lane, k, 32);
+    write_columns(Xc + gp.word_base + t0 * W, W, t0, gp, co, lane, j, 32);
 }
 
 // Lowest (cost, index) in each deme -> deme_best / deme_cost.  One CTA per deme.
-__global__ void k_ga_deme_best(const uint32_t *__restrict__ X, const int64_t *__restrict__ cost, int64_t D, int32_t W,
-                               uint32_t *__restrict__ deme_best, int64_t *__restrict__ deme_cost)
+__global__ void k_ga_deme_best(const ga_prob *__restrict__ gps, int K, ga_prob one, const uint32_t *__restrict__ X,
+                               const int64_t *__restrict__ cost, uint32_t *__restrict__ deme_best,
+                               int64_t *__restrict__ deme_cost, const ga_dev *__restrict__ st)
 {
     __shared__ long long sc[32];
     __shared__ long long si[32];
     __shared__ long long win;
-    const int64_t b = blockIdx.x;
+    int k = 0;
+    ga_prob gp = one;
+    if (K > 1) {
+        k = find_k(K, blockIdx.x, [&](int i) { return gps[i].deme_base; });
+        gp = gps[k];
+    }
+    if (st[k].stop)
+        return;
+    const int64_t b = blockIdx.x - gp.deme_base;
+    const int32_t W = gp.W;
     long long bc = 0x7fffffffffffffffLL, bi = 0x7fffffffffffffffLL;
-    for (int64_t k = threadIdx.x; k < D; k += blockDim.x) {
-        const int64_t t = b * D + k;
-        const long long c = cost[t];
+    for (int64_t i = threadIdx.x; i < gp.D; i += blockDim.x) {
+        const int64_t t = b * gp.D + i;
+        const long long c = cost[gp.ind_base + t];
         if (c < bc || (c == bc && t < bi)) {
             bc = c;
             bi = t;
@@ -415,81 +513,111 @@ __global__ void k_ga_deme_best(const uint32_t *__restrict__ X, const int64_t *__
                 bi = si[w];
             }
         win = bi;
-        deme_cost[b] = bc;
+        deme_cost[gp.deme_base + b] = bc;
     }
     __syncthreads();
     const int64_t tw = win;
     for (int w = threadIdx.x; w < W; w += blockDim.x)
-        deme_best[b * W + w] = X[tw * W + w];
+        deme_best[gp.dword_base + b * W + w] = X[gp.word_base + tw * W + w];
 }
 
-// Global best, saturation, trace, counters and the loop condition.
-__global__ void k_ga_finish(const uint32_t *__restrict__ deme_best, const int64_t *__restrict__ deme_cost, int64_t NB,
-                            int32_t W, int64_t P, uint32_t *__restrict__ best, ga_dev *__restrict__ st,
+// Per instance (one CTA each): global best, saturation, trace, counters.  The
+// last CTA (ticket) advances the step and sets the loop condition.
+__global__ void k_ga_finish(const ga_prob *__restrict__ gps, int K, ga_prob one,
+                            const uint32_t *__restrict__ deme_best, const int64_t *__restrict__ deme_cost,
+                            uint32_t *__restrict__ best, ga_dev *__restrict__ st, ga_glob *__restrict__ glob,
                             cudaGraphConditionalHandle h, int in_graph)
 {
     __shared__ long long sc[32];
     __shared__ long long si[32];
     __shared__ int improve;
     __shared__ long long winner;
-    long long bc = 0x7fffffffffffffffLL, bi = 0x7fffffffffffffffLL;
-    for (int64_t b = threadIdx.x; b < NB; b += blockDim.x) {
-        const long long c = deme_cost[b];
-        if (c < bc || (c == bc && b < bi)) {
-            bc = c;
-            bi = b;
-        }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const long long oc = __shfl_xor_sync(PM_FULL_MASK, bc, o);
-        const long long oi = __shfl_xor_sync(PM_FULL_MASK, bi, o);
-        if (oc < bc || (oc == bc && oi < bi)) {
-            bc = oc;
-            bi = oi;
-        }
-    }
+    __shared__ int last;
+    __shared__ int alive_s[32];
+    const int k = blockIdx.x;
+    const ga_prob gp = K > 1 ? gps[k] : one;
+    ga_dev &s = st[k];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    if (lane == 0) {
-        sc[warp] = bc;
-        si[warp] = bi;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int w = 1; w < nw; ++w)
-            if (sc[w] < bc || (sc[w] == bc && si[w] < bi)) {
-                bc = sc[w];
-                bi = si[w];
+    if (!s.stop) {
+        long long bc = 0x7fffffffffffffffLL, bi = 0x7fffffffffffffffLL;
+        for (int64_t b = threadIdx.x; b < gp.NB; b += blockDim.x) {
+            const long long c = deme_cost[gp.deme_base + b];
+            if (c < bc || (c == bc && b < bi)) {
+                bc = c;
+                bi = b;
             }
-        const bool better = st->best_cost < 0 || bc < st->best_cost;
-        improve = better ? 1 : 0;
-        winner = bi;
-        if (better) {
-            st->best_cost = bc;
-            st->sat = 0;
-        } else {
-            st->sat += 1;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const long long oc = __shfl_xor_sync(PM_FULL_MASK, bc, o);
+            const long long oi = __shfl_xor_sync(PM_FULL_MASK, bi, o);
+            if (oc < bc || (oc == bc && oi < bi)) {
+                bc = oc;
+                bi = oi;
+            }
+        }
+        if (lane == 0) {
+            sc[warp] = bc;
+            si[warp] = bi;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < nw; ++w)
+                if (sc[w] < bc || (sc[w] == bc && si[w] < bi)) {
+                    bc = sc[w];
+                    bi = si[w];
+                }
+            const bool better = s.best_cost < 0 || bc < s.best_cost;
+            improve = better ? 1 : 0;
+            winner = bi;
+            if (better) {
+                s.best_cost = bc;
+                s.sat = 0;
+            } else {
+                s.sat += 1;
+            }
+        }
+        __syncthreads();
+        if (improve)
+            for (int w = threadIdx.x; w < gp.W; w += blockDim.x)
+                best[gp.best_base + w] = deme_best[gp.dword_base + winner * gp.W + w];
+        if (threadIdx.x == 0) {
+            if (s.trace)
+                s.trace[glob->step_gens] = s.best_cost;
+            s.evals += gp.pop;
+            s.gen += 1;
+            s.total_gens += 1;
+            s.stop = (s.saturation > 0 && s.sat >= s.saturation) ? 1 : 0;
         }
     }
     __syncthreads();
-    if (improve)
-        for (int w = threadIdx.x; w < W; w += blockDim.x)
-            best[w] = deme_best[winner * W + w];
     if (threadIdx.x == 0) {
-        if (st->trace)
-            st->trace[st->step_gens] = st->best_cost;
-        st->evals += P;
-        st->gen += 1;
-        st->step_gens += 1;
-        st->total_gens += 1;
-        st->remaining -= 1;
-        st->stop = (st->saturation > 0 && st->sat >= st->saturation) ? 1 : 0;
+        __threadfence();
+        last = (atomicAdd(&glob->done, 1) == K - 1) ? 1 : 0;
+    }
+    __syncthreads();
+    if (!last)
+        return;
+    __threadfence();
+    int alive = 0;
+    for (int i = threadIdx.x; i < K; i += blockDim.x)
+        alive += (*(volatile int *)&st[i].stop) ? 0 : 1;
+    alive = __reduce_add_sync(PM_FULL_MASK, alive);
+    if (lane == 0)
+        alive_s[warp] = alive;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int a = 0;
+        for (int w = 0; w < nw; ++w)
+            a += alive_s[w];
+        glob->alive = a;
+        glob->done = 0;
+        glob->step_gens += 1;
+        glob->remaining -= 1;
         if (in_graph)
-            cudaGraphSetConditional(h, (st->remaining > 0 && !st->stop) ? 1u : 0u);
+            cudaGraphSetConditional(h, (glob->remaining > 0 && a > 0) ? 1u : 0u);
     }
 }
-
-}  // namespace
 
 // Uniform random p-subsets (Floyd sampling, generation 0, no migration), one
 // thread per individual, bitsets written in place.
@@ -513,6 +641,8 @@ __global__ void k_random_population(uint32_t *__restrict__ X, int64_t P, int32_t
     }
 }
 
+}  // namespace
+
 // ------------------------------- host side ---------------------------------
 
 pm_status pm_launch_random_population(const pm_instance *inst, uint64_t seed, int64_t pop, uint32_t *masks,
@@ -527,14 +657,20 @@ pm_status pm_launch_random_population(const pm_instance *inst, uint64_t seed, in
 }
 
 struct pm_ga {
-    pm_instance *inst = nullptr;
+    std::vector<pm_instance *> insts;
+    int K = 1;
     uint64_t seed = 0;
     int64_t P = 0, D = 0, NB = 0;
     int lgD = 0, R = 0, Q = 0;
     int64_t S = 0;
     uint32_t sid = 0;
-    pm_eval_plan plan;
-    pm_dbuf X, Xc, cost, active, improved, deme_best, deme_cost, best, trace, partials, tickets, columns, st, err;
+    bool single_row = false;  // one instance whose evaluation uses the row kernel
+    pm_eval_plan single;      // K == 1: the single-instance plan
+    pm_multi_plan plan;       // the scan plan over all instances
+    std::vector<ga_prob> gps;
+    int64_t groups_total = 0, demes_total = 0, dwords_total = 0, best_total = 0, Wmax = 0;
+    pm_dbuf X, Xc, cost, active, improved, deme_best, deme_cost, best, trace, accum, tickets, columns, st, glob, err,
+        probs, gprobs;
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -544,53 +680,79 @@ static void ga_free(pm_ga *ga)
 {
     if (!ga)
         return;
-    cudaSetDevice(ga->inst->device);
+    if (!ga->insts.empty())
+        cudaSetDevice(ga->insts[0]->device);
     if (ga->exec)
         cudaGraphExecDestroy(ga->exec);
     if (ga->graph)
         cudaGraphDestroy(ga->graph);
     if (ga->cap)
         cudaStreamDestroy(ga->cap);
-    pm_dbuf *bufs[] = {&ga->X,        &ga->Xc,        &ga->cost, &ga->active, &ga->improved,
-                       &ga->deme_best, &ga->deme_cost, &ga->best, &ga->trace,  &ga->partials, &ga->tickets,
-                       &ga->columns,  &ga->st,        &ga->err};
+    pm_dbuf *bufs[] = {&ga->X,         &ga->Xc,   &ga->cost,  &ga->active, &ga->improved, &ga->deme_best,
+                       &ga->deme_cost, &ga->best, &ga->trace, &ga->accum,  &ga->tickets,  &ga->columns,
+                       &ga->st,        &ga->glob, &ga->err,   &ga->probs,  &ga->gprobs};
     for (pm_dbuf *b : bufs)
         b->release();
     delete ga;
+}
+
+// PM_GA_GRAPH=0 in the environment selects direct stream launches instead of
+// the conditional-while graph (identical results; for profiling).
+static bool graph_mode()
+{
+    const char *v = std::getenv("PM_GA_GRAPH");
+    return !(v && v[0] == '0');
+}
+
+static pm_status ga_eval(pm_ga *ga, const uint32_t *masks, int64_t *costs, const pm_accept_args &acc,
+                         cudaStream_t s)
+{
+    int64_t *accum = static_cast<int64_t *>(ga->accum.ptr);
+    int *tickets = static_cast<int *>(ga->tickets.ptr);
+    uint32_t *columns = static_cast<uint32_t *>(ga->columns.ptr);
+    int *err = static_cast<int *>(ga->err.ptr);
+    const uint32_t *active = static_cast<const uint32_t *>(ga->active.ptr);
+    if (ga->single_row)
+        return pm_launch_eval(ga->insts[0], ga->single, masks, ga->P, active, costs, accum, tickets, columns, err, acc,
+                              s);
+    pm_scan_launch L;
+    pm_scan_launch_from(ga->plan, static_cast<const pm_prob *>(ga->probs.ptr), L);
+    L.masks = masks;
+    L.colT = columns;
+    L.active = active;
+    L.accum = accum;
+    L.tickets = tickets;
+    L.err = err;
+    return pm_launch_scan(L, acc, costs, ga->plan.smem, s);
 }
 
 // Enqueue one generation on `s`: under stream capture for the graph body
 // (in_graph = 1), or directly on the stream (in_graph = 0).
 static pm_status enqueue_generation(pm_ga *ga, cudaStream_t s, cudaGraphConditionalHandle h, int in_graph)
 {
-    pm_instance *inst = ga->inst;
-    const int32_t W = (int32_t)inst->W, m = (int32_t)inst->m, p = (int32_t)inst->p;
+    const ga_prob *gps = static_cast<const ga_prob *>(ga->gprobs.ptr);
+    const ga_prob one = ga->gps[0];
+    const int K = ga->K;
     ga_dev *st = static_cast<ga_dev *>(ga->st.ptr);
     uint32_t *X = static_cast<uint32_t *>(ga->X.ptr);
     uint32_t *Xc = static_cast<uint32_t *>(ga->Xc.ptr);
     int64_t *cost = static_cast<int64_t *>(ga->cost.ptr);
     uint32_t *active = static_cast<uint32_t *>(ga->active.ptr);
     uint8_t *improved = static_cast<uint8_t *>(ga->improved.ptr);
-    int64_t *partials = static_cast<int64_t *>(ga->partials.ptr);
-    int *tickets = static_cast<int *>(ga->tickets.ptr);
-    uint32_t *columns = static_cast<uint32_t *>(ga->columns.ptr);
-    int *err = static_cast<int *>(ga->err.ptr);
-    const int64_t P = ga->P;
-    const unsigned groups32 = (unsigned)pm_ceil_div(P, 32);
     ColumnsOut co;
-    co.colT = ga->plan.groups ? columns : nullptr;
-    co.G = ga->plan.groups ? ga->plan.groups : 1;
-    const int32_t Ws = W | 1;
-    const size_t init_smem = (size_t)32 * Ws * 4;
+    co.colT = ga->single_row ? nullptr : static_cast<uint32_t *>(ga->columns.ptr);
+    co.G = ga->single_row ? 1 : ga->plan.groups;
+    const unsigned groups = (unsigned)ga->groups_total;
+    const size_t init_smem = (size_t)32 * (ga->Wmax | 1) * 4;
     const int rows_in_smem = init_smem <= 48 * 1024 ? 1 : 0;
 
-    k_ga_init<<<groups32, 32, rows_in_smem ? init_smem : 0, s>>>(
-        X, improved, static_cast<const uint32_t *>(ga->deme_best.ptr), P, W, m, p, ga->D, ga->seed, ga->sid, st, co,
-        rows_in_smem);
+    k_ga_init<<<groups, 32, rows_in_smem ? init_smem : 0, s>>>(gps, K, one, X, improved, active,
+                                                               static_cast<const uint32_t *>(ga->deme_best.ptr),
+                                                               ga->seed, st, co, rows_in_smem);
     PM_CUDA(cudaGetLastError());
     pm_accept_args plain;
     plain.columns_ready = true;
-    PM_TRY(pm_launch_eval(inst, ga->plan, X, P, nullptr, cost, partials, tickets, columns, err, plain, s));
+    PM_TRY(ga_eval(ga, X, cost, plain, s));
 
     pm_accept_args acc;
     acc.mode = 1;
@@ -598,30 +760,29 @@ static pm_status enqueue_generation(pm_ga *ga, cudaStream_t s, cudaGraphConditio
     acc.cur_masks = X;
     acc.cand_masks = Xc;
     acc.columns_ready = true;
-    if (p / 2 > 0) {
+    if (ga->gps[0].p / 2 > 0) {  // p = 1: no crossover (a batch has p >= 2 everywhere or p = 1 everywhere)
         for (int r = 0; r < ga->R; ++r) {
-            const int64_t stride = ga->D >> (1 + (r % ga->lgD));
-            k_ga_crossover<<<groups32, 1024, 0, s>>>(X, Xc, active, P, W, m, p, stride, (uint32_t)r, ga->seed, ga->sid,
-                                                     st, co);
+            k_ga_crossover<<<groups, 1024, 0, s>>>(gps, K, one, X, Xc, active, (uint32_t)r, ga->seed, st, co);
             PM_CUDA(cudaGetLastError());
             acc.improved = nullptr;
-            PM_TRY(pm_launch_eval(inst, ga->plan, Xc, P, active, nullptr, partials, tickets, columns, err, acc, s));
+            PM_TRY(ga_eval(ga, Xc, nullptr, acc, s));
         }
     }
     for (int q = 0; q < ga->Q; ++q) {
-        k_ga_mutate<<<groups32, 1024, 0, s>>>(X, Xc, active, improved, P, W, m, (uint32_t)q, ga->seed, ga->sid, st,
-                                              co);
+        k_ga_mutate<<<groups, 1024, 0, s>>>(gps, K, one, X, Xc, active, improved, (uint32_t)q, ga->seed, st, co);
         PM_CUDA(cudaGetLastError());
         acc.improved = improved;
-        PM_TRY(pm_launch_eval(inst, ga->plan, Xc, P, active, nullptr, partials, tickets, columns, err, acc, s));
+        PM_TRY(ga_eval(ga, Xc, nullptr, acc, s));
     }
-    const int dthreads = (int)std::min<int64_t>(ga->D, 1024);
-    k_ga_deme_best<<<(unsigned)ga->NB, (unsigned)pm_round_up(dthreads, 32), 0, s>>>(
-        X, cost, ga->D, W, static_cast<uint32_t *>(ga->deme_best.ptr), static_cast<int64_t *>(ga->deme_cost.ptr));
+    const int dthreads = (int)pm_round_up(std::min<int64_t>(ga->D, 1024), 32);
+    k_ga_deme_best<<<(unsigned)ga->demes_total, (unsigned)dthreads, 0, s>>>(
+        gps, K, one, X, cost, static_cast<uint32_t *>(ga->deme_best.ptr), static_cast<int64_t *>(ga->deme_cost.ptr),
+        st);
     PM_CUDA(cudaGetLastError());
-    k_ga_finish<<<1, 1024, 0, s>>>(static_cast<const uint32_t *>(ga->deme_best.ptr),
-                                   static_cast<const int64_t *>(ga->deme_cost.ptr), ga->NB, W, P,
-                                   static_cast<uint32_t *>(ga->best.ptr), st, h, in_graph);
+    k_ga_finish<<<(unsigned)K, 256, 0, s>>>(gps, K, one, static_cast<const uint32_t *>(ga->deme_best.ptr),
+                                            static_cast<const int64_t *>(ga->deme_cost.ptr),
+                                            static_cast<uint32_t *>(ga->best.ptr), st,
+                                            static_cast<ga_glob *>(ga->glob.ptr), h, in_graph);
     PM_CUDA(cudaGetLastError());
     return PM_OK;
 }
@@ -632,8 +793,8 @@ static pm_status build_graph(pm_ga *ga)
     cudaGraphConditionalHandle h;
     PM_CUDA(cudaGraphConditionalHandleCreate(&h, ga->graph, 0, cudaGraphCondAssignDefault));
     // gate: sets the condition from the step's generation budget
-    ga_dev *st = static_cast<ga_dev *>(ga->st.ptr);
-    void *gate_args[] = {&st, &h};
+    ga_glob *glob = static_cast<ga_glob *>(ga->glob.ptr);
+    void *gate_args[] = {&glob, &h};
     cudaKernelNodeParams kp = {};
     kp.func = reinterpret_cast<void *>(k_ga_gate);
     kp.gridDim = dim3(1);
@@ -659,48 +820,87 @@ static pm_status build_graph(pm_ga *ga)
     return PM_OK;
 }
 
+// Layout of the GA arrays over the instances, the scan plan and the buffers.
 static pm_status ga_alloc(pm_ga *ga, cudaStream_t s)
 {
-    pm_instance *inst = ga->inst;
-    const size_t W = (size_t)inst->W, P = (size_t)ga->P;
-    PM_TRY(ga->X.reserve(P * W * 4));
-    PM_TRY(ga->Xc.reserve(P * W * 4));
-    PM_TRY(ga->cost.reserve(P * 8));
-    PM_TRY(ga->active.reserve(pm_ceil_div((int64_t)P, 32) * 4));
-    PM_TRY(ga->improved.reserve(P));
-    PM_TRY(ga->deme_best.reserve((size_t)ga->NB * W * 4));
-    PM_TRY(ga->deme_cost.reserve((size_t)ga->NB * 8));
-    PM_TRY(ga->best.reserve(W * 4));
+    const int K = ga->K;
+    ga->gps.resize(K);
+    int64_t grp = 0, deme = 0, dwords = 0, bestw = 0, Wmax = 0;
+    for (int k = 0; k < K; ++k) {
+        const pm_instance *in = ga->insts[k];
+        const pm_prob &pr = ga->plan.probs[k];
+        ga_prob &gp = ga->gps[k];
+        gp = ga_prob{};
+        gp.pop = ga->P;
+        gp.D = ga->D;
+        gp.NB = ga->NB;
+        gp.W = (int32_t)in->W;
+        gp.m = (int32_t)in->m;
+        gp.p = (int32_t)in->p;
+        gp.lgD = ga->lgD;
+        gp.ind_base = pr.ind_base;
+        gp.word_base = pr.word_base;
+        gp.col_base = pr.col_base;
+        gp.grp_base = grp;
+        gp.deme_base = deme;
+        gp.dword_base = dwords;
+        gp.best_base = bestw;
+        gp.sid = ga->sid + (uint32_t)k;
+        grp += pm_ceil_div(ga->P, 32);
+        deme += ga->NB;
+        dwords += ga->NB * in->W;
+        bestw += in->W;
+        Wmax = std::max<int64_t>(Wmax, in->W);
+    }
+    ga->groups_total = grp;
+    ga->demes_total = deme;
+    ga->dwords_total = dwords;
+    ga->best_total = bestw;
+    ga->Wmax = Wmax;
+    const size_t words = (size_t)ga->plan.words_total, inds = (size_t)ga->plan.ind_total;
+    PM_TRY(ga->X.reserve(words * 4));
+    PM_TRY(ga->Xc.reserve(words * 4));
+    PM_TRY(ga->cost.reserve(inds * 8));
+    PM_TRY(ga->active.reserve(inds / 8 + 4));
+    PM_TRY(ga->improved.reserve(inds));
+    PM_TRY(ga->deme_best.reserve((size_t)dwords * 4));
+    PM_TRY(ga->deme_cost.reserve((size_t)deme * 8));
+    PM_TRY(ga->best.reserve((size_t)bestw * 4));
     PM_TRY(ga->trace.reserve(8 * 1024));
-    ga->plan = pm_plan_eval(inst, ga->P);
-    PM_TRY(ga->partials.reserve(pm_plan_partial_bytes(ga->plan, ga->P)));
-    PM_TRY(ga->tickets.reserve(pm_plan_ticket_bytes(ga->plan)));
-    PM_TRY(ga->columns.reserve(std::max<size_t>(pm_plan_column_bytes(inst, ga->plan), 256)));
-    PM_TRY(ga->st.reserve(sizeof(ga_dev)));
+    const size_t acc_bytes = ga->single_row ? pm_plan_partial_bytes(ga->single, ga->P) : inds * 8;
+    const size_t tick_bytes = (size_t)pm_round_up(std::max<int64_t>(ga->plan.tiles_total, 1) * 4, 256);
+    PM_TRY(ga->accum.reserve(acc_bytes));
+    PM_TRY(ga->tickets.reserve(tick_bytes));
+    PM_TRY(ga->columns.reserve(std::max<size_t>((size_t)ga->plan.cols_total * 4, 256)));
+    PM_TRY(ga->st.reserve(sizeof(ga_dev) * K));
+    PM_TRY(ga->glob.reserve(sizeof(ga_glob)));
     PM_TRY(ga->err.reserve(256));
-    PM_CUDA(cudaMemsetAsync(ga->X.ptr, 0, P * W * 4, s));
-    PM_CUDA(cudaMemsetAsync(ga->Xc.ptr, 0, P * W * 4, s));
-    PM_CUDA(cudaMemsetAsync(ga->cost.ptr, 0, P * 8, s));
-    PM_CUDA(cudaMemsetAsync(ga->active.ptr, 0, ga->active.bytes, s));
-    PM_CUDA(cudaMemsetAsync(ga->improved.ptr, 0, P, s));
-    PM_CUDA(cudaMemsetAsync(ga->deme_best.ptr, 0, ga->deme_best.bytes, s));
-    PM_CUDA(cudaMemsetAsync(ga->deme_cost.ptr, 0, ga->deme_cost.bytes, s));
-    PM_CUDA(cudaMemsetAsync(ga->best.ptr, 0, ga->best.bytes, s));
-    PM_CUDA(cudaMemsetAsync(ga->err.ptr, 0, 256, s));
-    PM_CUDA(cudaMemsetAsync(ga->tickets.ptr, 0, ga->tickets.bytes, s));    // tile tickets start at zero
-    PM_CUDA(cudaMemsetAsync(ga->partials.ptr, 0, ga->partials.bytes, s));  // and so do the accumulators
-    ga_dev h = {};
-    h.best_cost = -1;
-    h.saturation = ga->S;
-    PM_CUDA(cudaMemcpyAsync(ga->st.ptr, &h, sizeof(h), cudaMemcpyHostToDevice, s));
+    PM_TRY(ga->probs.reserve(sizeof(pm_prob) * K));
+    PM_TRY(ga->gprobs.reserve(sizeof(ga_prob) * K));
+    pm_dbuf *zero[] = {&ga->X,         &ga->Xc,        &ga->cost, &ga->active,  &ga->improved, &ga->deme_best,
+                       &ga->deme_cost, &ga->best,      &ga->accum, &ga->tickets, &ga->err};
+    for (pm_dbuf *b : zero)
+        PM_CUDA(cudaMemsetAsync(b->ptr, 0, b->bytes, s));  // accumulators and tickets start at zero
+    std::vector<ga_dev> h(K);
+    for (int k = 0; k < K; ++k) {
+        h[k] = ga_dev{};
+        h[k].best_cost = -1;
+        h[k].saturation = ga->S;
+    }
+    ga_glob g = {};
+    g.alive = K;
+    PM_CUDA(cudaMemcpyAsync(ga->st.ptr, h.data(), sizeof(ga_dev) * K, cudaMemcpyHostToDevice, s));
+    PM_CUDA(cudaMemcpyAsync(ga->glob.ptr, &g, sizeof(g), cudaMemcpyHostToDevice, s));
+    PM_CUDA(cudaMemcpyAsync(ga->probs.ptr, ga->plan.probs.data(), sizeof(pm_prob) * K, cudaMemcpyHostToDevice, s));
+    PM_CUDA(cudaMemcpyAsync(ga->gprobs.ptr, ga->gps.data(), sizeof(ga_prob) * K, cudaMemcpyHostToDevice, s));
     PM_CUDA(cudaStreamSynchronize(s));
     PM_CUDA(cudaStreamCreateWithFlags(&ga->cap, cudaStreamNonBlocking));
     return PM_OK;
 }
 
-static pm_status ga_configure(pm_ga *ga, pm_instance *inst, uint64_t seed, int64_t pop, const pm_ga_params *params)
+static pm_status ga_configure(pm_ga *ga, int64_t pop, uint64_t seed, const pm_ga_params *params)
 {
-    if (!inst || pop < 2)
+    if (pop < 2)
         return PM_ERR_INVALID_ARG;
     pm_ga_params prm = {};
     prm.xover_rounds = -1;
@@ -717,7 +917,6 @@ static pm_status ga_configure(pm_ga *ga, pm_instance *inst, uint64_t seed, int64
     int lg = 0;
     while ((int64_t(1) << lg) < D)
         ++lg;
-    ga->inst = inst;
     ga->seed = seed;
     ga->P = pop;
     ga->D = D;
@@ -732,31 +931,36 @@ static pm_status ga_configure(pm_ga *ga, pm_instance *inst, uint64_t seed, int64
     return PM_OK;
 }
 
+static pm_status ga_create_common(pm_ga *ga, cudaStream_t s)
+{
+    pm_status st = ga_alloc(ga, s);
+    if (st == PM_OK)
+        st = build_graph(ga);
+    return st;
+}
+
 extern "C" pm_status pm_ga_create(pm_instance *inst, uint64_t seed, int64_t pop, const pm_ga_params *params,
                                   void *stream, pm_ga **out)
 {
-    if (!out)
+    if (!out || !inst)
         return PM_ERR_INVALID_ARG;
     *out = nullptr;
     pm_ga *ga = new (std::nothrow) pm_ga();
     if (!ga)
         return PM_ERR_OOM;
-    pm_status st = ga_configure(ga, inst, seed, pop, params);
-    if (st != PM_OK) {
-        delete ga;
-        return st;
-    }
-    cudaError_t e = cudaSetDevice(inst->device);
-    if (e != cudaSuccess) {
-        delete ga;
-        return PM_ERR_CUDA;
-    }
-    if (params && (params->flags & PM_GA_TUNE))
+    ga->insts.push_back(inst);
+    ga->K = 1;
+    pm_status st = ga_configure(ga, pop, seed, params);
+    if (st == PM_OK && cudaSetDevice(inst->device) != cudaSuccess)
+        st = PM_ERR_CUDA;
+    if (st == PM_OK && params && (params->flags & PM_GA_TUNE))
         st = pm_tune_eval(inst, pop, stream, nullptr);
-    if (st == PM_OK)
-        st = ga_alloc(ga, static_cast<cudaStream_t>(stream));
-    if (st == PM_OK)
-        st = build_graph(ga);
+    if (st == PM_OK) {
+        ga->single = pm_plan_eval(inst, pop);
+        ga->single_row = ga->single.groups == 0;
+        ga->plan = pm_plan_from_single(inst, ga->single, pop);
+        st = ga_create_common(ga, static_cast<cudaStream_t>(stream));
+    }
     if (st != PM_OK) {
         ga_free(ga);
         return st;
@@ -765,12 +969,43 @@ extern "C" pm_status pm_ga_create(pm_instance *inst, uint64_t seed, int64_t pop,
     return PM_OK;
 }
 
-// PM_GA_GRAPH=0 in the environment selects direct stream launches instead of
-// the conditional-while graph (identical results; for profiling).
-static bool graph_mode()
+extern "C" pm_status pm_batch_ga_create(pm_batch *b, uint64_t seed, int64_t pop, const pm_ga_params *params,
+                                        void *stream, pm_ga **out)
 {
-    const char *v = std::getenv("PM_GA_GRAPH");
-    return !(v && v[0] == '0');
+    if (!out || !b)
+        return PM_ERR_INVALID_ARG;
+    *out = nullptr;
+    const auto &insts = pm_batch_instances(b);
+    pm_ga *ga = new (std::nothrow) pm_ga();
+    if (!ga)
+        return PM_ERR_OOM;
+    for (const pm_instance *in : insts)
+        ga->insts.push_back(const_cast<pm_instance *>(in));
+    ga->K = (int)insts.size();
+    pm_status st = ga_configure(ga, pop, seed, params);
+    // crossover runs for all instances or for none: p = 1 mixed with p >= 2 is not supported
+    if (st == PM_OK) {
+        const bool any1 = std::any_of(insts.begin(), insts.end(), [](const pm_instance *in) { return in->p < 2; });
+        const bool all1 = std::all_of(insts.begin(), insts.end(), [](const pm_instance *in) { return in->p < 2; });
+        if (any1 && !all1)
+            st = PM_ERR_UNSUPPORTED;
+    }
+    if (st == PM_OK && cudaSetDevice(insts[0]->device) != cudaSuccess)
+        st = PM_ERR_CUDA;
+    if (st == PM_OK && params && (params->flags & PM_GA_TUNE)) {
+        std::vector<int64_t> pops(insts.size(), pop);
+        st = pm_batch_tune(b, pops.data(), stream, nullptr);
+    }
+    if (st == PM_OK)
+        st = pm_batch_ga_plan(b, pop, ga->plan);
+    if (st == PM_OK)
+        st = ga_create_common(ga, static_cast<cudaStream_t>(stream));
+    if (st != PM_OK) {
+        ga_free(ga);
+        return st;
+    }
+    *out = ga;
+    return PM_OK;
 }
 
 static pm_status check_err(pm_ga *ga, cudaStream_t s)
@@ -788,16 +1023,19 @@ extern "C" pm_status pm_ga_step(pm_ga *ga, int64_t gens, int64_t *trace, void *s
     if (gens == 0)
         return PM_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    PM_CUDA(cudaSetDevice(ga->inst->device));
+    PM_CUDA(cudaSetDevice(ga->insts[0]->device));
     const bool trace_dev = trace && pm_is_device_ptr(trace);
     long long *tr = nullptr;
+    const size_t tbytes = (size_t)gens * ga->K * 8;
     if (trace_dev) {
         tr = reinterpret_cast<long long *>(trace);
     } else if (trace) {
-        PM_TRY(ga->trace.reserve((size_t)gens * 8));
+        PM_TRY(ga->trace.reserve(tbytes));
         tr = static_cast<long long *>(ga->trace.ptr);
     }
-    k_ga_begin<<<1, 1, 0, s>>>(static_cast<ga_dev *>(ga->st.ptr), (long long)gens, tr);
+    k_ga_begin<<<(unsigned)pm_ceil_div(ga->K, 256), 256, 0, s>>>(static_cast<ga_glob *>(ga->glob.ptr),
+                                                                static_cast<ga_dev *>(ga->st.ptr), ga->K,
+                                                                (long long)gens, tr);
     PM_CUDA(cudaGetLastError());
     if (graph_mode()) {
         PM_CUDA(cudaGraphLaunch(ga->exec, s));
@@ -807,33 +1045,34 @@ extern "C" pm_status pm_ga_step(pm_ga *ga, int64_t gens, int64_t *trace, void *s
         for (int64_t g = 0; g < gens; ++g) {
             PM_TRY(enqueue_generation(ga, s, 0, 0));
             if (ga->S > 0) {
-                ga_dev h;
-                PM_CUDA(cudaMemcpyAsync(&h, ga->st.ptr, sizeof(h), cudaMemcpyDeviceToHost, s));
+                ga_glob h;
+                PM_CUDA(cudaMemcpyAsync(&h, ga->glob.ptr, sizeof(h), cudaMemcpyDeviceToHost, s));
                 PM_CUDA(cudaStreamSynchronize(s));
-                if (h.stop)
+                if (h.alive == 0)
                     break;
             }
         }
     }
     if (trace && !trace_dev) {
-        // generations actually run may be fewer (saturation); copy all `gens` slots, caller reads gens_run
-        PM_CUDA(cudaMemcpyAsync(trace, tr, (size_t)gens * 8, cudaMemcpyDeviceToHost, s));
+        // generations actually run may be fewer (saturation); copy all slots, the caller reads gens_run
+        PM_CUDA(cudaMemcpyAsync(trace, tr, tbytes, cudaMemcpyDeviceToHost, s));
         return check_err(ga, s);
     }
     return PM_OK;
 }
 
-extern "C" pm_status pm_ga_result(pm_ga *ga, int64_t *best_cost, uint32_t *best_mask, int64_t *gens_run,
-                                  int64_t *evals, void *stream)
+extern "C" pm_status pm_ga_instance_result(pm_ga *ga, int64_t k, int64_t *best_cost, uint32_t *best_mask,
+                                           int64_t *gens_run, int64_t *evals, void *stream)
 {
-    if (!ga)
+    if (!ga || k < 0 || k >= ga->K)
         return PM_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    PM_CUDA(cudaSetDevice(ga->inst->device));
+    PM_CUDA(cudaSetDevice(ga->insts[0]->device));
     ga_dev h;
-    PM_CUDA(cudaMemcpyAsync(&h, ga->st.ptr, sizeof(h), cudaMemcpyDeviceToHost, s));
+    PM_CUDA(cudaMemcpyAsync(&h, static_cast<ga_dev *>(ga->st.ptr) + k, sizeof(h), cudaMemcpyDeviceToHost, s));
     if (best_mask)
-        PM_CUDA(cudaMemcpyAsync(best_mask, ga->best.ptr, (size_t)ga->inst->W * 4, cudaMemcpyDefault, s));
+        PM_CUDA(cudaMemcpyAsync(best_mask, static_cast<uint32_t *>(ga->best.ptr) + ga->gps[k].best_base,
+                                (size_t)ga->gps[k].W * 4, cudaMemcpyDefault, s));
     PM_TRY(check_err(ga, s));
     if (best_cost)
         *best_cost = h.best_cost;
@@ -844,17 +1083,31 @@ extern "C" pm_status pm_ga_result(pm_ga *ga, int64_t *best_cost, uint32_t *best_
     return PM_OK;
 }
 
-extern "C" pm_status pm_ga_population(pm_ga *ga, uint32_t *masks, int64_t *costs, void *stream)
+extern "C" pm_status pm_ga_result(pm_ga *ga, int64_t *best_cost, uint32_t *best_mask, int64_t *gens_run,
+                                  int64_t *evals, void *stream)
 {
-    if (!ga)
+    return pm_ga_instance_result(ga, 0, best_cost, best_mask, gens_run, evals, stream);
+}
+
+extern "C" pm_status pm_ga_instance_population(pm_ga *ga, int64_t k, uint32_t *masks, int64_t *costs, void *stream)
+{
+    if (!ga || k < 0 || k >= ga->K)
         return PM_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    PM_CUDA(cudaSetDevice(ga->inst->device));
+    PM_CUDA(cudaSetDevice(ga->insts[0]->device));
+    const ga_prob &gp = ga->gps[k];
     if (masks)
-        PM_CUDA(cudaMemcpyAsync(masks, ga->X.ptr, (size_t)ga->P * ga->inst->W * 4, cudaMemcpyDefault, s));
+        PM_CUDA(cudaMemcpyAsync(masks, static_cast<uint32_t *>(ga->X.ptr) + gp.word_base, (size_t)ga->P * gp.W * 4,
+                                cudaMemcpyDefault, s));
     if (costs)
-        PM_CUDA(cudaMemcpyAsync(costs, ga->cost.ptr, (size_t)ga->P * 8, cudaMemcpyDefault, s));
+        PM_CUDA(cudaMemcpyAsync(costs, static_cast<int64_t *>(ga->cost.ptr) + gp.ind_base, (size_t)ga->P * 8,
+                                cudaMemcpyDefault, s));
     return check_err(ga, s);
+}
+
+extern "C" pm_status pm_ga_population(pm_ga *ga, uint32_t *masks, int64_t *costs, void *stream)
+{
+    return pm_ga_instance_population(ga, 0, masks, costs, stream);
 }
 
 // ------------------------------ checkpoints --------------------------------
@@ -872,14 +1125,14 @@ struct ga_header {
 
 static size_t ga_blob_size(const pm_ga *ga)
 {
-    const size_t W = (size_t)ga->inst->W;
+    const size_t W = (size_t)ga->insts[0]->W;
     return sizeof(ga_header) + (size_t)ga->NB * W * 4 + (size_t)ga->NB * 8 + W * 4 + (size_t)ga->P * W * 4 +
            (size_t)ga->P * 8;
 }
 
 extern "C" pm_status pm_ga_save(pm_ga *ga, void *buf, size_t *len, void *stream)
 {
-    if (!ga || !len)
+    if (!ga || !len || ga->K != 1)
         return PM_ERR_INVALID_ARG;
     const size_t need = ga_blob_size(ga);
     if (!buf) {
@@ -889,21 +1142,22 @@ extern "C" pm_status pm_ga_save(pm_ga *ga, void *buf, size_t *len, void *stream)
     if (*len < need)
         return PM_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    PM_CUDA(cudaSetDevice(ga->inst->device));
+    const pm_instance *inst = ga->insts[0];
+    PM_CUDA(cudaSetDevice(inst->device));
     ga_header h = {};
-    std::memcpy(h.magic, "PMGASAV1", 8);
-    h.version = 1;
+    std::memcpy(h.magic, "PMGASAV2", 8);
+    h.version = 2;
     h.sid = ga->sid;
-    h.n = ga->inst->n;
-    h.m = ga->inst->m;
-    h.p = ga->inst->p;
+    h.n = inst->n;
+    h.m = inst->m;
+    h.p = inst->p;
     h.P = ga->P;
     h.D = ga->D;
     h.R = ga->R;
     h.Q = ga->Q;
     h.S = ga->S;
     h.seed = ga->seed;
-    const size_t W = (size_t)ga->inst->W;
+    const size_t W = (size_t)inst->W;
     char *b = static_cast<char *>(buf) + sizeof(ga_header);
     PM_CUDA(cudaMemcpyAsync(&h.state, ga->st.ptr, sizeof(ga_dev), cudaMemcpyDeviceToHost, s));
     PM_CUDA(cudaMemcpyAsync(b, ga->deme_best.ptr, (size_t)ga->NB * W * 4, cudaMemcpyDeviceToHost, s));
@@ -929,7 +1183,7 @@ extern "C" pm_status pm_ga_load(pm_instance *inst, const void *buf, size_t len, 
     *out = nullptr;
     ga_header h;
     std::memcpy(&h, buf, sizeof(h));
-    if (std::memcmp(h.magic, "PMGASAV1", 8) != 0 || h.version != 1 || h.n != inst->n || h.m != inst->m ||
+    if (std::memcmp(h.magic, "PMGASAV2", 8) != 0 || h.version != 2 || h.n != inst->n || h.m != inst->m ||
         h.p != inst->p)
         return PM_ERR_INVALID_ARG;
     pm_ga_params prm = {};
@@ -949,10 +1203,11 @@ extern "C" pm_status pm_ga_load(pm_instance *inst, const void *buf, size_t len, 
     const char *b = static_cast<const char *>(buf) + sizeof(ga_header);
     ga_dev state = h.state;
     state.trace = nullptr;
-    state.remaining = 0;
-    state.step_gens = 0;
+    ga_glob g = {};
+    g.alive = state.stop ? 0 : 1;
     cudaError_t e = cudaSuccess;
     e = e ? e : cudaMemcpyAsync(ga->st.ptr, &state, sizeof(ga_dev), cudaMemcpyHostToDevice, s);
+    e = e ? e : cudaMemcpyAsync(ga->glob.ptr, &g, sizeof(g), cudaMemcpyHostToDevice, s);
     e = e ? e : cudaMemcpyAsync(ga->deme_best.ptr, b, (size_t)ga->NB * W * 4, cudaMemcpyHostToDevice, s);
     b += (size_t)ga->NB * W * 4;
     e = e ? e : cudaMemcpyAsync(ga->deme_cost.ptr, b, (size_t)ga->NB * 8, cudaMemcpyHostToDevice, s);
@@ -976,8 +1231,8 @@ extern "C" pm_status pm_ga_info(const pm_ga *ga, int64_t *pop, int64_t *deme, in
 {
     if (!ga)
         return PM_ERR_INVALID_ARG;
-    const int64_t per_eval = ga->plan.groups ? 1 : 2;  // the operators write the columns themselves
-    const int64_t rounds = ga->inst->p / 2 > 0 ? ga->R : 0;
+    const int64_t per_eval = ga->single_row ? 2 : 1;  // column path: the operators write the columns themselves
+    const int64_t rounds = ga->gps[0].p / 2 > 0 ? ga->R : 0;
     if (pop)
         *pop = ga->P;
     if (deme)

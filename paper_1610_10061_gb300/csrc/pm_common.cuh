@@ -52,6 +52,27 @@ struct pm_eval_plan {
     int64_t grid = 0;     // CTAs launched (column kernel: persistent over tiles x splits items)
 };
 
+// One instance inside an evaluation launch (host and device).  Individuals
+// of the launch are numbered globally: instance k owns [ind_base, ind_base +
+// pop), ind_base a multiple of 32; its bitset rows start at word word_base;
+// its facility-major tiles at word col_base.  Work items (tile, split) of
+// instance k are item_base .. item_base + tiles * splits - 1 (split-major).
+struct pm_prob {
+    const uint16_t *pi;
+    const int32_t *delta;
+    int64_t n, stride;
+    int32_t L, W, m, p;
+    int64_t pop;
+    int64_t ind_base;   // accumulators, active bits, GA per-individual arrays
+    int64_t out_base;   // caller's cost array
+    int64_t word_base;  // bitset rows
+    int64_t col_base;   // facility-major tiles
+    int64_t tiles, tile_base;
+    int64_t splits, cps;  // client splits and clients per split
+    int64_t item_base;
+    int64_t job_base;     // transpose jobs (tiles * G * W per instance)
+};
+
 struct pm_instance {
     int device = 0;
     int64_t n = 0, m = 0, p = 0, L = 0, W = 0, stride = 0;
@@ -100,6 +121,26 @@ struct pm_accept_args {
     bool columns_ready = false;  // the caller already wrote the facility-major copy
 };
 
+// A scan launch over one or more instances.
+struct pm_scan_launch {
+    int groups = 4, warps = 16;
+    int64_t grid = 0;
+    int K = 1;
+    const pm_prob *probs_dev = nullptr;  // K > 1: device table
+    pm_prob one{};                       // K == 1: passed by value
+    int64_t items = 0, jobs = 0;
+    const uint32_t *masks = nullptr;     // rows, for the transpose (when !columns_ready)
+    uint32_t *colT = nullptr;
+    const uint32_t *active = nullptr;    // bit per global individual, nullable
+    int64_t *accum = nullptr;            // one int64 per global individual, zero at rest
+    int *tickets = nullptr;              // one per global tile, zero at rest
+    int *err = nullptr;
+};
+pm_status pm_launch_scan(const pm_scan_launch &L, const pm_accept_args &acc, int64_t *costs, size_t smem,
+                         cudaStream_t stream);
+// The single-instance launch of `plan` (K = 1, all bases 0).
+pm_prob pm_single_prob(const pm_instance *inst, const pm_eval_plan &plan, int64_t pop);
+
 // Enqueue the scan over (masks, pop) -> partials -> sums (+ epilogue).
 // active: nullable, bit (t & 31) of word t >> 5 marks individual t as
 // evaluated; inactive individuals get no cost written.
@@ -118,6 +159,24 @@ pm_status pm_launch_mask_check(const pm_instance *inst, const uint32_t *masks, i
 // Uniform random p-subsets (Floyd sampling, fixed seed) for tuning (ga.cu).
 pm_status pm_launch_random_population(const pm_instance *inst, uint64_t seed, int64_t pop, uint32_t *masks,
                                       cudaStream_t s);
+
+// A scan plan over several instances (batch.cu): one tile shape for all,
+// per-instance splits, global numbering of individuals, rows, tiles.
+struct pm_multi_plan {
+    int groups = 4, warps = 16;
+    int64_t grid = 0, items = 0, jobs = 0;
+    int64_t tiles_total = 0, ind_total = 0, words_total = 0, cols_total = 0;
+    size_t smem = 0;  // tile bytes of the widest instance
+    std::vector<pm_prob> probs;
+};
+// Plan for `insts` with pops[k] individuals each; items_per_slot work items per
+// resident CTA (splits apportioned by an estimate of each instance's scan work).
+pm_status pm_plan_multi(const std::vector<const pm_instance *> &insts, const std::vector<int64_t> &pops, int G,
+                        int warps, int items_per_slot, pm_multi_plan &out);
+// The same layout for one instance under a single-instance plan.
+pm_multi_plan pm_plan_from_single(const pm_instance *inst, const pm_eval_plan &plan, int64_t pop);
+// Fill L from a multi plan (probs_dev: the plan's table on the device, or null when K == 1).
+void pm_scan_launch_from(const pm_multi_plan &mp, const pm_prob *probs_dev, pm_scan_launch &L);
 
 // ---------------------------------------------------------------------------
 // Tables (tables.cu)

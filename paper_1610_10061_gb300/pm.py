@@ -72,6 +72,13 @@ _SIGS = {
     "pm_ga_load": ([_P, _P, ctypes.c_size_t, _P, _PP], _S),
     "pm_ga_destroy": ([_P], _S),
     "pm_ga_info": ([_P, _P, _P, _P, _P, _P, _P], _S),
+    "pm_ga_instance_result": ([_P, _I64, _P, _P, _P, _P, _P], _S),
+    "pm_ga_instance_population": ([_P, _I64, _P, _P, _P], _S),
+    "pm_batch_create": ([_P, _I64, _PP], _S),
+    "pm_batch_destroy": ([_P], _S),
+    "pm_batch_eval": ([_P, _P, _P, _P, _P], _S),
+    "pm_batch_tune": ([_P, _P, _P, ctypes.POINTER(pm_eval_shape)], _S),
+    "pm_batch_ga_create": ([_P, ctypes.c_uint64, _I64, ctypes.POINTER(pm_ga_params), _P, _PP], _S),
     "pm_ga_run": ([_P, ctypes.c_uint64, _I64, _I64, ctypes.POINTER(pm_ga_params), _P, _P, _P, _P, _P, _P], _S),
 }
 for _name, (_args, _res) in _SIGS.items():
@@ -213,6 +220,49 @@ def pm_ga_info(ga):
                 kernels_per_generation=kg.value, kernels_per_step_call=ks.value)
 
 
+def pm_ga_instance_result(ga, k: int, best_mask=None, stream=None):
+    bc, gr, ev = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(_lib.pm_ga_instance_result(ga, k, ctypes.byref(bc), _addr(best_mask), ctypes.byref(gr), ctypes.byref(ev),
+                                      _stream(stream)), "pm_ga_instance_result")
+    return bc.value, gr.value, ev.value
+
+
+def pm_ga_instance_population(ga, k: int, masks, costs, stream=None):
+    _check(_lib.pm_ga_instance_population(ga, k, _addr(masks), _addr(costs), _stream(stream)),
+           "pm_ga_instance_population")
+
+
+def pm_batch_create(inst_handles):
+    arr = (ctypes.c_void_p * len(inst_handles))(*[h.value for h in inst_handles])
+    out = ctypes.c_void_p()
+    _check(_lib.pm_batch_create(arr, len(inst_handles), ctypes.byref(out)), "pm_batch_create")
+    return out
+
+
+def pm_batch_destroy(b):
+    _check(_lib.pm_batch_destroy(b), "pm_batch_destroy")
+
+
+def pm_batch_eval(b, masks, pops, costs, stream=None):
+    pv = np.ascontiguousarray(pops, dtype=np.int64)
+    _check(_lib.pm_batch_eval(b, _addr(masks), _addr(pv), _addr(costs), _stream(stream)), "pm_batch_eval")
+
+
+def pm_batch_tune(b, pops, stream=None):
+    pv = np.ascontiguousarray(pops, dtype=np.int64)
+    out = pm_eval_shape()
+    _check(_lib.pm_batch_tune(b, _addr(pv), _stream(stream), ctypes.byref(out)), "pm_batch_tune")
+    return dict(groups=out.groups, warps=out.warps, items_per_cta=out.splits, grid=out.grid, ms=out.ms,
+                candidates=out.candidates)
+
+
+def pm_batch_ga_create(b, seed: int, pop: int, params: pm_ga_params | None = None, stream=None):
+    out = ctypes.c_void_p()
+    _check(_lib.pm_batch_ga_create(b, seed, pop, ctypes.byref(params) if params is not None else None,
+                                   _stream(stream), ctypes.byref(out)), "pm_batch_ga_create")
+    return out
+
+
 def pm_ga_destroy(ga):
     _check(_lib.pm_ga_destroy(ga), "pm_ga_destroy")
 
@@ -316,6 +366,85 @@ class GA:
         import struct
         P = struct.unpack_from("<q", blob, 8 + 4 + 4 + 8 * 3)[0]
         return cls(inst, 0, P, _handle=h)
+
+    def close(self):
+        if self.handle:
+            pm_ga_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Several instances evaluated (and evolved) together in single launches."""
+
+    def __init__(self, instances):
+        self.instances = list(instances)
+        self.handle = pm_batch_create([i.handle for i in self.instances])
+
+    def eval(self, masks, pops, costs=None, stream=None):
+        """masks: device tensor of the populations back to back; returns a device tensor of sum(pops) costs."""
+        import torch
+
+        if costs is None:
+            costs = torch.empty(int(sum(pops)), dtype=torch.int64, device=masks.device)
+        pm_batch_eval(self.handle, masks, pops, costs, stream)
+        return costs
+
+    def tune(self, pops, stream=None):
+        return pm_batch_tune(self.handle, pops, stream)
+
+    def ga(self, seed: int, pop: int, deme: int = 0, xover_rounds: int = -1, mut_tries: int = -1,
+           saturation: int = 0, stream_id: int = 0, tune: bool = False, stream=None):
+        h = pm_batch_ga_create(self.handle, seed, pop,
+                               _params(deme, xover_rounds, mut_tries, saturation, stream_id, tune), stream)
+        return BatchGA(self, pop, h)
+
+    def close(self):
+        if self.handle:
+            pm_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BatchGA:
+    """A GA per instance of a Batch, stepped together."""
+
+    def __init__(self, batch: Batch, pop: int, handle):
+        self.batch = batch
+        self.pop = int(pop)
+        self.handle = handle
+        self.K = len(batch.instances)
+
+    def step(self, gens: int, stream=None):
+        """Run `gens` generations; returns a (K, gens) trace (entries past an instance's stop are unspecified)."""
+        trace = np.zeros((self.K, max(int(gens), 1)), dtype=np.int64)
+        pm_ga_step(self.handle, int(gens), trace, stream)
+        return trace[:, :int(gens)]
+
+    def result(self, k: int, stream=None):
+        mask = np.zeros(self.batch.instances[k].W, dtype=np.uint32)
+        bc, gr, ev = pm_ga_instance_result(self.handle, k, mask, stream)
+        return bc, gr, ev, mask
+
+    def population(self, k: int, stream=None):
+        W = self.batch.instances[k].W
+        masks = np.zeros((self.pop, W), dtype=np.uint32)
+        costs = np.zeros(self.pop, dtype=np.int64)
+        pm_ga_instance_population(self.handle, k, masks, costs, stream)
+        return masks, costs
+
+    def info(self):
+        return pm_ga_info(self.handle)
 
     def close(self):
         if self.handle:
