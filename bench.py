@@ -411,10 +411,75 @@ def run_eval_mode(args):
     print(json.dumps(line), flush=True)
 
 
+def run_batched(args):
+    """256 uneven instances evolved together: one launch per kernel of a generation covers them all."""
+    import numpy as np
+
+    from paper_1610_10061_gb300.inputs import batched_instances
+
+    count = int(args.workload[len("batched"):] or 256)
+    t0 = time.perf_counter()
+    data = batched_instances(count, seed=3, workers=max(1, (os.cpu_count() or 2) - 1))
+    gen_s = time.perf_counter() - t0
+    import torch
+
+    from paper_1610_10061_gb300 import build
+
+    build.build()
+    from paper_1610_10061_gb300 import pm
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    insts = [pm.Instance(d, p, stream=stream.cuda_stream) for d, p in data]
+    tables_s = time.perf_counter() - t0
+    batch = pm.Batch(insts)
+    pop = 256
+    shape = batch.tune([pop] * count, stream=stream.cuda_stream)
+    ga = batch.ga(seed=0, pop=pop, deme=256, stream=stream.cuda_stream)
+    info = ga.info()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        pm.pm_ga_step(ga.handle, 1, None, stream.cuda_stream)
+    torch.cuda.synchronize()
+    e0 = sum(pm.pm_ga_instance_result(ga.handle, k, None, stream.cuda_stream)[2] for k in range(count))
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = Clocks(0)
+    clocks.start()
+    for k in range(args.steps):
+        flush.zero_()
+        starts[k].record(stream)
+        pm.pm_ga_step(ga.handle, 1, None, stream.cuda_stream)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+    e1 = sum(pm.pm_ga_instance_result(ga.handle, k, None, stream.cuda_stream)[2] for k in range(count))
+    n_sizes = [d.shape[0] for d, _ in data]
+    tables_bytes = sum(d.shape[0] * (((d.shape[1] - p + 1) + 31) // 32 * 32) * 6 for d, p in data)
+    line = {"metric": METRIC, "value": (e1 - e0) / (ms / 1000), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": f"batched{count}: {count} instances, n=m log-uniform [100,5000] "
+                                   f"(min {min(n_sizes)}, max {max(n_sizes)}), p U[5,n/10], half graph (4n edges, "
+                                   "APSP) half Euclidean; pop 256 each in one deme; one launch per kernel per "
+                                   "generation covers all instances",
+                       "tables_bytes": tables_bytes, "eval_tile": shape, "generate_s": gen_s,
+                       "tables_build_s": tables_s, "step": "one generation of every instance's GA",
+                       "l2": "flushed between timed steps"},
+            "evals": int(e1 - e0),
+            "gpu_launches": int((info["kernels_per_generation"] + info["kernels_per_step_call"]) * args.steps),
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload.startswith("batched"):
+        run_batched(args)
     elif args.mode == "eval":
         run_eval_mode(args)
     else:

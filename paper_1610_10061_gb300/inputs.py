@@ -192,24 +192,36 @@ def paper_shape_instance(name: str) -> dict:
     raise KeyError(name)
 
 
-def batched_instances(count: int, seed: int, nmin: int = 100, nmax: int = 5000):
+def _batched_one(spec):
+    k, n, p, sub = spec
+    if k % 2 == 0:
+        d = graph_instance(n, min(4 * n, n * (n - 1) // 2), seed=sub)
+    else:
+        d = euclid_instance(n, seed=sub)
+    return d, p
+
+
+def batched_instances(count: int, seed: int, nmin: int = 100, nmax: int = 5000, workers: int = 1):
     """Uneven instances for batched evaluation.
 
     n = m log-uniform in [nmin, nmax]; p uniform in [5, n/10]; even entries are
     graph instances (4n edges, weights [1,100], shortest paths), odd entries
-    Euclidean.  Returns a list of (d, p).
+    Euclidean.  Returns a list of (d, p).  workers > 1 builds them in a pool of
+    spawned processes (call it before any CUDA work in the calling process).
     """
     rng = np.random.default_rng(seed)
-    out = []
+    specs = []
     for k in range(int(count)):
         n = int(round(math.exp(rng.uniform(math.log(nmin), math.log(nmax)))))
         n = max(nmin, min(nmax, n))
         p = int(rng.integers(5, max(6, n // 10) + 1))
         p = min(p, n - 1)
         sub = int(rng.integers(0, 2**31 - 1))
-        if k % 2 == 0:
-            d = graph_instance(n, min(4 * n, n * (n - 1) // 2), seed=sub)
-        else:
-            d = euclid_instance(n, seed=sub)
-        out.append((d, p))
-    return out
+        specs.append((k, n, p, sub))
+    if workers <= 1:
+        return [_batched_one(s) for s in specs]
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+
+    with ProcessPoolExecutor(max_workers=int(workers), mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_batched_one, specs, chunksize=1))
