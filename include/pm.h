@@ -193,11 +193,15 @@ typedef struct pm_ga_params {
     int64_t saturation;   /* S: stop when the best has not improved for S generations; 0 = off */
     uint32_t stream_id;   /* fourth word of every random-number counter (independent runs) */
     uint32_t flags;       /* PM_GA_TUNE: run pm_tune_eval for this population size at creation */
+    struct pm_model *model;  /* learned swap proposal (see pm_model_create); NULL = the paper's GA only */
+    int32_t candidates;      /* learned try: closed facilities (by gain) paired with every open one; <= 0: 4 */
+    int32_t reserved;        /* must be 0 */
 } pm_ga_params;
 
 #define PM_GA_TUNE 1u
 
 typedef struct pm_ga pm_ga;
+typedef struct pm_model pm_model;
 
 /*
  * pm_ga_create -- allocate a GA of `pop` individuals (pop/D demes, the
@@ -289,6 +293,85 @@ PM_API pm_status pm_ga_info(const pm_ga *ga, int64_t *pop, int64_t *deme, int32_
 PM_API pm_status pm_ga_run(pm_instance *inst, uint64_t seed, int64_t pop, int64_t gens, const pm_ga_params *params,
                     int64_t *best_cost, uint32_t *best_mask, int64_t *gens_run, int64_t *evals, int64_t *trace,
                     void *stream);
+
+/* ------------------------------------------------------------------------
+ * The learned swap proposal (no counterpart in the paper).  A small
+ * perceptron (16 -> 128 -> 128 -> 1, ReLU; BF16 weights and activations on
+ * the tensor cores, FP32 accumulation and master weights) scores swap moves
+ * (close open facility j, open closed facility k) from exact first-order
+ * statistics of the individual; a GA given a model (pm_ga_params.model)
+ * adds one learned mutation try per generation before the shift tries: each
+ * individual takes its best-scored swap among `candidates` x p candidates,
+ * and the child is evaluated exactly and kept only if strictly cheaper, like
+ * every other mutant.  The model never decides a cost.
+ * ------------------------------------------------------------------------ */
+
+/* Number of model parameters (FP32): W1 [16][128], b1 [128], W2 [128][128],
+ * b2 [128], w3 [128], b3 [1], in that order, row = input unit. */
+PM_API int64_t pm_model_num_params(void);
+
+/* Create a model on `device` with a seeded He-style initialisation. */
+PM_API pm_status pm_model_create(int device, uint64_t seed, pm_model **out);
+PM_API pm_status pm_model_destroy(pm_model *model);
+
+/* Set / get the FP32 master parameters (host or device, pm_model_num_params
+ * floats).  Setting resets the Adam moments.  Synchronise `stream`. */
+PM_API pm_status pm_model_set_params(pm_model *model, const float *params, void *stream);
+PM_API pm_status pm_model_get_params(pm_model *model, float *params, void *stream);
+
+/* Predictions y (rows FP32, device) for inputs x (rows x 16 BF16 bit patterns,
+ * device).  Asynchronous. */
+PM_API pm_status pm_model_forward(pm_model *model, const uint16_t *x, int64_t rows, float *y, void *stream);
+
+/* Mean squared error of the predictions against targets t (rows FP32,
+ * device) and its gradients (pm_model_num_params FP32, host or device,
+ * nullable).  Synchronises `stream`. */
+PM_API pm_status pm_model_grad(pm_model *model, const uint16_t *x, const float *t, int64_t rows, float *grads,
+                               float *loss, void *stream);
+
+/* One Adam step (Kingma & Ba 2015: beta1 0.9, beta2 0.999, eps 1e-8) on the
+ * batch (x, t) with learning rate lr; *loss (nullable) receives the batch's
+ * mean squared error before the step (then the call synchronises). */
+PM_API pm_status pm_model_train_step(pm_model *model, const uint16_t *x, const float *t, int64_t rows, float lr,
+                                     float *loss, void *stream);
+
+/*
+ * pm_swap_stats -- per individual and facility (pop x m arrays, device):
+ * gain[k] = the cost saved by opening closed facility k alone, cap[k] = the
+ * clients it would take, loss[j] = the cost added by closing open facility j
+ * alone (second-nearest minus nearest over j's clients, second-nearest taken
+ * within the truncated table), assign[j] = the clients j serves.  From the
+ * same scan over Pi'/Delta' as the fitness (Section 4.2), continued to the
+ * second open rank.  Asynchronous.
+ */
+PM_API pm_status pm_swap_stats(pm_instance *inst, const uint32_t *masks, int64_t pop, int64_t *gain, int32_t *cap,
+                               int64_t *loss, int32_t *assign, void *stream);
+
+/*
+ * pm_move_features -- the model's input rows (16 BF16 each; 8 features then
+ * zeros) for given moves: moves[(t*C + c)*2 + 0] = j (open, to close),
+ * [.. + 1] = k (closed, to open), C moves per individual; costs[t] the
+ * individual's cost.  Features, with Z = max(cost/p, 1): loss_j/Z, gain_k/Z,
+ * assign_j/(n/p), cap_k/(n/p), (loss_j-gain_k)/Z, log1p(loss_j/Z),
+ * log1p(gain_k/Z), p/m.  All device memory.  Asynchronous.
+ */
+PM_API pm_status pm_move_features(pm_instance *inst, const int64_t *gain, const int32_t *cap, const int64_t *loss,
+                                  const int32_t *assign, const int64_t *costs, const int32_t *moves, int64_t pop,
+                                  int64_t C, uint16_t *x, void *stream);
+
+/*
+ * pm_log_moves -- training tuples (individual, move, exact cost change) for
+ * the `pop` individuals in masks (device; costs[t] their exact costs):
+ * `per` moves each, j uniform among the open facilities and k, with
+ * probability 3/4, among the 4 closed facilities of largest gain, else
+ * uniform among the closed ones (Philox4x32-10 keyed by seed).  Writes the
+ * moves (pop x per x 2 int32), their feature rows x (pop x per x 16 BF16)
+ * and targets t (pop x per FP32) = (exact cost after the swap - cost) / Z,
+ * the swapped bitsets evaluated by the fitness kernels.  All device memory.
+ * Allocates stream-ordered scratch.  Asynchronous.
+ */
+PM_API pm_status pm_log_moves(pm_instance *inst, const uint32_t *masks, const int64_t *costs, int64_t pop, int64_t per,
+                              uint64_t seed, uint16_t *x, float *t, int32_t *moves, void *stream);
 
 /* ------------------------------------------------------------------------
  * Batches: many instances of uneven (n, m, p) in one launch (no counterpart

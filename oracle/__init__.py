@@ -76,6 +76,7 @@ def _load():
     lib.oracle_mutation_params.restype = None
     lib.oracle_crossover_params.argtypes = [U64, U32, U32, U32, U32, I64, I64, P, P]
     lib.oracle_crossover_params.restype = None
+    lib.oracle_swap_stats.argtypes = [P, P, I64, I64, I64, P, I64, I64, P, P, P, P]
     lib.oracle_ga_run.argtypes = [P, P, I64, I64, I64, U64, U32, I64, I64, ctypes.c_int32, ctypes.c_int32,
                                   I64, I64, P, P, P, P, P, P, P, P]
     _lib = lib
@@ -298,3 +299,23 @@ def ga_run(pi, delta, m: int, p: int, seed: int, P: int, D: int | None = None, g
     if record:
         pops, costs = pops[:k], costs[:k]
     return st, trace, pops, costs
+
+
+# --------------------------------------------------------------------------
+# Swap statistics and move features (the learned swap proposal; not in the paper)
+# --------------------------------------------------------------------------
+
+def swap_stats(pi, delta, m: int, masks):
+    """(gain, cap, loss, assign), each (P, m): see oracle_swap_stats in pm_oracle.c."""
+    pi = np.ascontiguousarray(pi, dtype=np.uint16)
+    delta = np.ascontiguousarray(delta, dtype=np.int32)
+    masks = np.ascontiguousarray(masks, dtype=np.uint32)
+    n, L = pi.shape
+    P, W = masks.shape
+    gain = np.zeros((P, m), dtype=np.int64)
+    cap = np.zeros((P, m), dtype=np.int32)
+    loss = np.zeros((P, m), dtype=np.int64)
+    assign = np.zeros((P, m), dtype=np.int32)
+    _check(_load().oracle_swap_stats(_ptr(pi), _ptr(delta), n, L, m, _ptr(masks), W, P, _ptr(gain), _ptr(cap),
+                                     _ptr(loss), _ptr(assign)), "swap_stats")
+    return gain, cap, loss, assign

@@ -1,0 +1,154 @@
+"""Oracle of the learned swap proposal (no counterpart in the paper) -- test infrastructure.
+
+* ``move_features``: the 8 features of a swap move (close open facility j,
+  open closed facility k) of one individual, from its swap statistics
+  (``oracle.swap_stats``), and the regression target (exact cost change of the
+  swap / Z, Z = max(cost / p, 1)).
+* A 3-layer perceptron F(16, the 8 features zero-padded) -> 128 -> 128 -> 1
+  with ReLU, its mean-squared-error gradients and the Adam update (Kingma &
+  Ba, "Adam: A Method for Stochastic Optimization", ICLR 2015: beta1 = 0.9,
+  beta2 = 0.999, eps = 1e-8, bias-corrected moments).
+
+Arithmetic is float64.  ``bf16=True`` reproduces where the CUDA path rounds to
+bfloat16 (inputs, weight copies, the hidden activations and their gradients
+that feed tensor-core products); everything else is exact float64, so the
+CUDA path (float32 accumulation) must agree within a tolerance.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+F_IN = 8      # features per move
+F_PAD = 16    # padded input width (one k-step of a 16-bit tensor-core product)
+HIDDEN = 128
+
+BETA1, BETA2, EPS = 0.9, 0.999, 1e-8
+
+
+def bf16_round(x):
+    """Round to the nearest bfloat16 (ties to even), returned as float64."""
+    f = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+    u = f.view(np.uint32).astype(np.uint64)
+    bias = 0x7FFF + ((u >> 16) & 1)
+    r = ((u + bias) & 0xFFFF0000).astype(np.uint32)
+    return r.view(np.float32).astype(np.float64)
+
+
+def _r(x, bf16):
+    return bf16_round(x) if bf16 else np.asarray(x, dtype=np.float64)
+
+
+# --------------------------------------------------------------------------
+# Move features
+# --------------------------------------------------------------------------
+
+def move_features(gain, cap, loss, assign, cost, n, m, p, j, k):
+    """Feature vector (length 8) of closing j and opening k, from one individual's swap statistics."""
+    Z = max(float(cost) / p, 1.0)
+    per = n / p
+    lj, gk = float(loss[j]), float(gain[k])
+    return np.array([
+        lj / Z,
+        gk / Z,
+        assign[j] / per,
+        cap[k] / per,
+        (lj - gk) / Z,
+        np.log1p(lj / Z),
+        np.log1p(gk / Z),
+        p / m,
+    ], dtype=np.float64)
+
+
+def move_target(cost_before, cost_after, p):
+    """Regression target: the exact cost change of the swap divided by Z."""
+    Z = max(float(cost_before) / p, 1.0)
+    return (float(cost_after) - float(cost_before)) / Z
+
+
+# --------------------------------------------------------------------------
+# The perceptron
+# --------------------------------------------------------------------------
+
+def init_params(seed=0):
+    """He-style initialisation (fixed seed); float64 master weights."""
+    rng = np.random.default_rng(seed)
+    return {
+        "W1": rng.normal(0, np.sqrt(2.0 / F_IN), size=(F_PAD, HIDDEN)),
+        "b1": np.zeros(HIDDEN),
+        "W2": rng.normal(0, np.sqrt(2.0 / HIDDEN), size=(HIDDEN, HIDDEN)),
+        "b2": np.zeros(HIDDEN),
+        "w3": rng.normal(0, np.sqrt(1.0 / HIDDEN), size=(HIDDEN,)),
+        "b3": np.zeros(1),
+    }
+
+
+def forward(params, X, bf16=False):
+    """y (B,) and the cache for backward.  X is (B, 16)."""
+    x = _r(X, bf16)
+    W1, W2, w3 = _r(params["W1"], bf16), _r(params["W2"], bf16), _r(params["w3"], bf16)
+    z1 = x @ W1 + params["b1"]
+    h1 = _r(np.maximum(z1, 0.0), bf16)
+    z2 = h1 @ W2 + params["b2"]
+    h2 = _r(np.maximum(z2, 0.0), bf16)
+    y = h2 @ w3 + params["b3"][0]
+    return y, (x, h1, h2, W1, W2, w3)
+
+
+def loss_and_grads(params, X, t, bf16=False):
+    """Mean squared error and its gradients with respect to every parameter."""
+    y, (x, h1, h2, W1, W2, w3) = forward(params, X, bf16)
+    B = X.shape[0]
+    r = y - np.asarray(t, dtype=np.float64)
+    loss = float(np.mean(r * r))
+    dy = 2.0 * r / B
+    g = {"b3": np.array([dy.sum()]), "w3": h2.T @ dy}
+    dh2 = np.outer(dy, w3) * (h2 > 0)
+    dh2 = _r(dh2, bf16)
+    g["b2"] = dh2.sum(axis=0)
+    g["W2"] = h1.T @ dh2
+    dh1 = (dh2 @ W2.T) * (h1 > 0)
+    dh1 = _r(dh1, bf16)
+    g["b1"] = dh1.sum(axis=0)
+    g["W1"] = x.T @ dh1
+    return loss, g
+
+
+def adam_init(params):
+    return {"t": 0, "m": {k: np.zeros_like(v) for k, v in params.items()},
+            "v": {k: np.zeros_like(v) for k, v in params.items()}}
+
+
+def adam_step(params, grads, state, lr):
+    """One Adam update in place (Kingma & Ba 2015, Algorithm 1)."""
+    state["t"] += 1
+    t = state["t"]
+    for k in params:
+        g = grads[k]
+        state["m"][k] = BETA1 * state["m"][k] + (1 - BETA1) * g
+        state["v"][k] = BETA2 * state["v"][k] + (1 - BETA2) * g * g
+        mhat = state["m"][k] / (1 - BETA1 ** t)
+        vhat = state["v"][k] / (1 - BETA2 ** t)
+        params[k] = params[k] - lr * mhat / (np.sqrt(vhat) + EPS)
+    return params
+
+
+def flatten(params):
+    """Parameters in the library's flat order: W1 (16x128), b1, W2 (128x128), b2, w3, b3."""
+    return np.concatenate([params["W1"].ravel(), params["b1"], params["W2"].ravel(), params["b2"], params["w3"],
+                           params["b3"]])
+
+
+def unflatten(v):
+    v = np.asarray(v, dtype=np.float64)
+    o = 0
+    out = {}
+    for name, shape in (("W1", (F_PAD, HIDDEN)), ("b1", (HIDDEN,)), ("W2", (HIDDEN, HIDDEN)), ("b2", (HIDDEN,)),
+                        ("w3", (HIDDEN,)), ("b3", (1,))):
+        size = int(np.prod(shape))
+        out[name] = v[o:o + size].reshape(shape).copy()
+        o += size
+    return out
+
+
+N_PARAMS = F_PAD * HIDDEN + HIDDEN + HIDDEN * HIDDEN + HIDDEN + HIDDEN + 1

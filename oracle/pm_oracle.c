@@ -510,3 +510,67 @@ done:
     free(enhanced);
     return err;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Swap statistics of an individual (features of the learned swap proposal;  */
+/* no counterpart in the paper).  For client i let r1 be the first rank whose */
+/* facility is open (its facility f1, its distance D1 = the running sum of   */
+/* Delta up to r1) and r2 the second such rank (distance D2; if no second    */
+/* open facility lies within the L columns, D2 = the running sum up to the  */
+/* last column).  Then, per facility (arrays of m entries per individual):  */
+/*   gain[k]   = sum over clients i and ranks s < r1 with Pi[i][s] = k of   */
+/*               D1 - (running sum up to s)   (what opening k alone saves)  */
+/*   cap[k]    = number of such (i, s)        (clients k would capture)     */
+/*   loss[j]   = sum over clients with f1 = j of D2 - D1                    */
+/*               (what closing j alone costs)                               */
+/*   assign[j] = number of clients with f1 = j                              */
+/* ------------------------------------------------------------------------ */
+
+int oracle_swap_stats(const uint16_t *pi, const int32_t *delta, int64_t n, int64_t L, int64_t m, const uint32_t *masks,
+                      int64_t W, int64_t P, int64_t *gain, int32_t *cap, int64_t *loss, int32_t *assign)
+{
+    for (int64_t t = 0; t < P; ++t) {
+        const uint32_t *x = masks + t * W;
+        int64_t *g = gain + t * m;
+        int32_t *c = cap + t * m;
+        int64_t *l = loss + t * m;
+        int32_t *a = assign + t * m;
+        for (int64_t j = 0; j < m; ++j) {
+            g[j] = 0;
+            c[j] = 0;
+            l[j] = 0;
+            a[j] = 0;
+        }
+        for (int64_t i = 0; i < n; ++i) {
+            const uint16_t *prow = pi + i * L;
+            const int32_t *drow = delta + i * L;
+            int64_t r1 = -1, r2 = -1, run = 0, d1 = 0, d2 = 0;
+            for (int64_t s = 0; s < L; ++s) {
+                run += drow[s];
+                if (bit_get(x, prow[s])) {
+                    if (r1 < 0) {
+                        r1 = s;
+                        d1 = run;
+                    } else {
+                        r2 = s;
+                        d2 = run;
+                        break;
+                    }
+                }
+            }
+            if (r1 < 0)
+                return OR_ERR_NO_OPEN;
+            if (r2 < 0)
+                d2 = run; /* no second open facility within the table: the last column's distance */
+            int64_t run2 = 0;
+            for (int64_t s = 0; s < r1; ++s) {
+                run2 += drow[s];
+                g[prow[s]] += d1 - run2;
+                c[prow[s]] += 1;
+            }
+            l[prow[r1]] += d2 - d1;
+            a[prow[r1]] += 1;
+        }
+    }
+    return OR_OK;
+}

@@ -43,6 +43,14 @@
 
 // batch.cu
 pm_status pm_batch_ga_plan(pm_batch *b, int64_t pop, pm_multi_plan &out);
+// learn.cu
+pm_status pm_learn_prepare(const pm_instance *inst);
+pm_status pm_launch_swap_stats(const pm_instance *inst, const uint32_t *masks, int64_t pop, int64_t *gain,
+                               int32_t *cap, int64_t *loss, int32_t *assign, cudaStream_t s);
+pm_status pm_launch_candidates(const pm_instance *inst, const uint32_t *masks, int64_t pop, const int64_t *gain,
+                               const int32_t *cap, const int64_t *loss, const int32_t *assign, const int64_t *costs,
+                               int T, int32_t *moves, uint16_t *x, cudaStream_t s);
+pm_status pm_model_forward_dev(pm_model *md, const void *x_dev, int64_t rows, float *y_dev, cudaStream_t s);
 const std::vector<const pm_instance *> &pm_batch_instances(const pm_batch *b);
 
 namespace {
@@ -619,6 +627,79 @@ __global__ void k_ga_finish(const ga_prob *__restrict__ gps, int K, ga_prob one,
     }
 }
 
+// The learned mutation try: individual t0 + j (warp j of the CTA) takes the
+// candidate swap with the lowest predicted cost change (ties: lowest
+// candidate index; a NaN score never wins) -- close moves[.][0], open
+// moves[.][1] -- into Xc, unless it already improved in this generation.
+__global__ void __launch_bounds__(1024) k_ga_learned_pick(const ga_prob *__restrict__ gps, int K, ga_prob one,
+                                                          const uint32_t *__restrict__ X, uint32_t *__restrict__ Xc,
+                                                          uint32_t *__restrict__ active,
+                                                          const uint8_t *__restrict__ improved,
+                                                          const float *__restrict__ scores,
+                                                          const int32_t *__restrict__ moves, int64_t C,
+                                                          ga_dev *__restrict__ st, ColumnsOut co)
+{
+    __shared__ uint32_t on_s;
+    int k;
+    const ga_prob gp = prob_of_group(gps, K, one, blockIdx.x, k);
+    const int lane = threadIdx.x & 31;
+    const int j = threadIdx.x >> 5;
+    const int64_t t0 = (blockIdx.x - gp.grp_base) * 32;
+    const int64_t t = t0 + j;
+    const int32_t W = gp.W;
+    if (st[k].stop) {
+        if (threadIdx.x == 0)
+            active[(gp.ind_base + t0) >> 5] = 0u;
+        return;
+    }
+    if (threadIdx.x == 0)
+        on_s = 0u;
+    __syncthreads();
+    if (t < gp.pop && improved[gp.ind_base + t] == 0) {
+        float bs = __int_as_float(0x7f800000);  // +inf
+        int64_t bc = C;
+        const float *sc = scores + t * C;
+        for (int64_t c = lane; c < C; c += 32) {
+            const float v = sc[c];
+            if (v < bs) {  // NaN compares false
+                bs = v;
+                bc = c;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ov = __shfl_xor_sync(PM_FULL_MASK, bs, o);
+            const int64_t oc = __shfl_xor_sync(PM_FULL_MASK, bc, o);
+            if (ov < bs || (ov == bs && oc < bc)) {
+                bs = ov;
+                bc = oc;
+            }
+        }
+        if (bc < C) {
+            const int32_t jc = moves[(t * C + bc) * 2], ko = moves[(t * C + bc) * 2 + 1];
+            const uint32_t *src = X + gp.word_base + t * W;
+            uint32_t *dst = Xc + gp.word_base + t * W;
+            for (int w = lane; w < W; w += 32) {
+                uint32_t v = src[w];
+                if (w == (jc >> 5))
+                    v &= ~(1u << (jc & 31));
+                if (w == (ko >> 5))
+                    v |= 1u << (ko & 31);
+                dst[w] = v;
+            }
+            if (lane == 0)
+                atomicOr(&on_s, 1u << j);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        active[(gp.ind_base + t0) >> 5] = on_s;
+        if (on_s)
+            atomicAdd(reinterpret_cast<unsigned long long *>(&st[k].evals), (unsigned long long)__popc(on_s));
+    }
+    write_columns(Xc + gp.word_base + t0 * W, W, t0, gp, co, lane, j, 32);
+}
+
 // Uniform random p-subsets (Floyd sampling, generation 0, no migration), one
 // thread per individual, bitsets written in place.
 __global__ void k_random_population(uint32_t *__restrict__ X, int64_t P, int32_t W, int32_t m, int32_t p,
@@ -671,6 +752,10 @@ struct pm_ga {
     int64_t groups_total = 0, demes_total = 0, dwords_total = 0, best_total = 0, Wmax = 0;
     pm_dbuf X, Xc, cost, active, improved, deme_best, deme_cost, best, trace, accum, tickets, columns, st, glob, err,
         probs, gprobs;
+    // learned swap proposal (single-instance GAs)
+    pm_model *model = nullptr;
+    int T = 4;
+    pm_dbuf s_gain, s_cap, s_loss, s_assign, moves, xfeat, scores;
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -690,7 +775,8 @@ static void ga_free(pm_ga *ga)
         cudaStreamDestroy(ga->cap);
     pm_dbuf *bufs[] = {&ga->X,         &ga->Xc,   &ga->cost,  &ga->active, &ga->improved, &ga->deme_best,
                        &ga->deme_cost, &ga->best, &ga->trace, &ga->accum,  &ga->tickets,  &ga->columns,
-                       &ga->st,        &ga->glob, &ga->err,   &ga->probs,  &ga->gprobs};
+                       &ga->st,        &ga->glob, &ga->err,   &ga->probs,  &ga->gprobs,
+                       &ga->s_gain,    &ga->s_cap, &ga->s_loss, &ga->s_assign, &ga->moves, &ga->xfeat, &ga->scores};
     for (pm_dbuf *b : bufs)
         b->release();
     delete ga;
@@ -767,6 +853,23 @@ static pm_status enqueue_generation(pm_ga *ga, cudaStream_t s, cudaGraphConditio
             acc.improved = nullptr;
             PM_TRY(ga_eval(ga, Xc, nullptr, acc, s));
         }
+    }
+    if (ga->model) {
+        // learned try: swap statistics -> candidate moves -> scores -> best swap -> exact evaluation
+        const pm_instance *inst = ga->insts[0];
+        int64_t *gain = static_cast<int64_t *>(ga->s_gain.ptr), *loss = static_cast<int64_t *>(ga->s_loss.ptr);
+        int32_t *capc = static_cast<int32_t *>(ga->s_cap.ptr), *asg = static_cast<int32_t *>(ga->s_assign.ptr);
+        int32_t *moves = static_cast<int32_t *>(ga->moves.ptr);
+        const int64_t C = inst->p * ga->T;
+        PM_TRY(pm_launch_swap_stats(inst, X, ga->P, gain, capc, loss, asg, s));
+        PM_TRY(pm_launch_candidates(inst, X, ga->P, gain, capc, loss, asg, cost, ga->T, moves,
+                                    static_cast<uint16_t *>(ga->xfeat.ptr), s));
+        PM_TRY(pm_model_forward_dev(ga->model, ga->xfeat.ptr, ga->P * C, static_cast<float *>(ga->scores.ptr), s));
+        k_ga_learned_pick<<<groups, 1024, 0, s>>>(gps, K, one, X, Xc, active, improved,
+                                                  static_cast<const float *>(ga->scores.ptr), moves, C, st, co);
+        PM_CUDA(cudaGetLastError());
+        acc.improved = improved;
+        PM_TRY(ga_eval(ga, Xc, nullptr, acc, s));
     }
     for (int q = 0; q < ga->Q; ++q) {
         k_ga_mutate<<<groups, 1024, 0, s>>>(gps, K, one, X, Xc, active, improved, (uint32_t)q, ga->seed, st, co);
@@ -907,7 +1010,11 @@ static pm_status ga_configure(pm_ga *ga, int64_t pop, uint64_t seed, const pm_ga
     prm.mut_tries = -1;
     if (params)
         prm = *params;
-    if ((prm.flags & ~PM_GA_TUNE) != 0)
+    if ((prm.flags & ~PM_GA_TUNE) != 0 || prm.reserved != 0)
+        return PM_ERR_INVALID_ARG;
+    ga->model = prm.model;
+    ga->T = prm.candidates > 0 ? prm.candidates : 4;
+    if (ga->T > 8)
         return PM_ERR_INVALID_ARG;
     int64_t D = prm.deme ? prm.deme : std::min<int64_t>(pop, 256);
     if (D < 2 || D > 1024 || (D & (D - 1)) != 0 || pop % D != 0 || prm.saturation < 0)
@@ -955,6 +1062,17 @@ extern "C" pm_status pm_ga_create(pm_instance *inst, uint64_t seed, int64_t pop,
         st = PM_ERR_CUDA;
     if (st == PM_OK && params && (params->flags & PM_GA_TUNE))
         st = pm_tune_eval(inst, pop, stream, nullptr);
+    if (st == PM_OK && ga->model) {
+        const size_t Pm = (size_t)pop * inst->m, C = (size_t)inst->p * ga->T;
+        st = pm_learn_prepare(inst);
+        if (st == PM_OK) st = ga->s_gain.reserve(Pm * 8);
+        if (st == PM_OK) st = ga->s_loss.reserve(Pm * 8);
+        if (st == PM_OK) st = ga->s_cap.reserve(Pm * 4);
+        if (st == PM_OK) st = ga->s_assign.reserve(Pm * 4);
+        if (st == PM_OK) st = ga->moves.reserve((size_t)pop * C * 8);
+        if (st == PM_OK) st = ga->xfeat.reserve((size_t)pop * C * 32);
+        if (st == PM_OK) st = ga->scores.reserve((size_t)pop * C * 4);
+    }
     if (st == PM_OK) {
         ga->single = pm_plan_eval(inst, pop);
         ga->single_row = ga->single.groups == 0;
@@ -983,6 +1101,8 @@ extern "C" pm_status pm_batch_ga_create(pm_batch *b, uint64_t seed, int64_t pop,
         ga->insts.push_back(const_cast<pm_instance *>(in));
     ga->K = (int)insts.size();
     pm_status st = ga_configure(ga, pop, seed, params);
+    if (st == PM_OK && ga->model)
+        st = PM_ERR_UNSUPPORTED;  // the learned try is for single-instance GAs
     // crossover runs for all instances or for none: p = 1 mixed with p >= 2 is not supported
     if (st == PM_OK) {
         const bool any1 = std::any_of(insts.begin(), insts.end(), [](const pm_instance *in) { return in->p < 2; });
@@ -1132,7 +1252,7 @@ static size_t ga_blob_size(const pm_ga *ga)
 
 extern "C" pm_status pm_ga_save(pm_ga *ga, void *buf, size_t *len, void *stream)
 {
-    if (!ga || !len || ga->K != 1)
+    if (!ga || !len || ga->K != 1 || ga->model)
         return PM_ERR_INVALID_ARG;
     const size_t need = ga_blob_size(ga);
     if (!buf) {
@@ -1242,7 +1362,8 @@ extern "C" pm_status pm_ga_info(const pm_ga *ga, int64_t *pop, int64_t *deme, in
     if (mut_tries)
         *mut_tries = ga->Q;
     if (kernels_per_generation)
-        *kernels_per_generation = 1 + per_eval + rounds * (1 + per_eval) + ga->Q * (1 + per_eval) + 2;
+        *kernels_per_generation = 1 + per_eval + rounds * (1 + per_eval) + ga->Q * (1 + per_eval) + 2 +
+                                  (ga->model ? 4 + per_eval : 0);
     if (kernels_per_step_call)
         *kernels_per_step_call = graph_mode() ? 2 : 1;  // k_ga_begin (and the gate in graph mode)
     return PM_OK;

@@ -1,0 +1,1223 @@
+// The learned swap proposal (no counterpart in the paper): swap statistics
+// from an extended scan, move features, a small perceptron on the tensor
+// cores (BF16 weights and activations, FP32 accumulation) with hand-written
+// forward, backward and Adam kernels, and the GA's learned mutation try.
+//
+// Swap statistics of an individual (per facility, m entries each): for
+// client i with first open rank r1 (distance D1) and second open rank r2
+// (distance D2; the last column's distance if none within the table):
+//   gain[k]  += D1 - d(i, k)   for every facility k ranked before r1 by i
+//   cap[k]   += 1              for the same facilities
+//   loss[f1] += D2 - D1        (f1 = the facility at r1)
+//   assign[f1] += 1
+// gain[k] is exactly what opening k alone saves and loss[j] what closing j
+// alone costs; the perceptron predicts the exact cost change of the swap
+// (close j, open k) from these first-order quantities.
+//
+// Features of a move (8, zero-padded to 16 for one tensor-core k-step), Z =
+// max(cost / p, 1):  loss_j/Z, gain_k/Z, assign_j/(n/p), cap_k/(n/p),
+// (loss_j - gain_k)/Z, log1p(loss_j/Z), log1p(gain_k/Z), p/m.
+//
+// Perceptron: x(16) -> 128 (ReLU) -> 128 (ReLU) -> 1, y = prediction of the
+// cost change / Z.  Parameters, flat FP32 masters: W1 [16][128], b1 [128],
+// W2 [128][128], b2 [128], w3 [128], b3 [1] (row = input unit); BF16
+// copies of W1, W2, w3 feed mma.sync.m16n8k16.  Hidden activations are
+// rounded to BF16 after the ReLU; gradients of the hidden layers are rounded
+// to BF16 before they enter a tensor-core product.  One CTA handles 64 rows:
+// forward, and in training the whole backward pass, with the weight
+// gradients of its rows added atomically into an FP32 gradient buffer; then
+// one Adam kernel updates the masters and refreshes the BF16 copies.
+
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "pm_common.cuh"
+
+namespace {
+
+constexpr int kIn = 16;       // padded input width
+constexpr int kFeat = 8;      // real features
+constexpr int kHid = 128;     // hidden width
+constexpr int kRows = 64;     // rows per CTA
+constexpr int kLdH = kHid + 8;   // padded row stride (bf16) of 128-wide tiles: conflict-free fragments
+constexpr int kLdX = kIn + 8;    // padded row stride of 16-wide tiles
+constexpr int kLdR = kRows + 8;  // padded stride of transposed (feature-major) 64-row tiles
+constexpr int kParams = kIn * kHid + kHid + kHid * kHid + kHid + kHid + 1;
+constexpr int kOffW1 = 0, kOffB1 = kIn * kHid, kOffW2 = kOffB1 + kHid, kOffB2 = kOffW2 + kHid * kHid,
+              kOffW3 = kOffB2 + kHid, kOffB3 = kOffW3 + kHid;
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2])
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ uint32_t ld32(const __nv_bfloat16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
+
+// A fragment (16 x 16, row-major source A[r][k], stride lda) at (r0, k0).
+__device__ __forceinline__ void frag_a(uint32_t (&a)[4], const __nv_bfloat16 *A, int lda, int r0, int k0, int lane)
+{
+    const int g = lane >> 2, c = lane & 3;
+    a[0] = ld32(A + (r0 + g) * lda + k0 + 2 * c);
+    a[1] = ld32(A + (r0 + g + 8) * lda + k0 + 2 * c);
+    a[2] = ld32(A + (r0 + g) * lda + k0 + 8 + 2 * c);
+    a[3] = ld32(A + (r0 + g + 8) * lda + k0 + 8 + 2 * c);
+}
+
+// B fragment (16 x 8) from a source stored n-major with k contiguous: B[n][k], stride ldb.
+__device__ __forceinline__ void frag_b(uint32_t (&b)[2], const __nv_bfloat16 *B, int ldb, int n0, int k0, int lane)
+{
+    const int g = lane >> 2, c = lane & 3;
+    b[0] = ld32(B + (n0 + g) * ldb + k0 + 2 * c);
+    b[1] = ld32(B + (n0 + g) * ldb + k0 + 8 + 2 * c);
+}
+
+struct MlpSmem {
+    __nv_bfloat16 X[kRows * kLdX];     // inputs [r][f]
+    __nv_bfloat16 W1T[kHid * kLdX];    // W1 as [out][in]
+    __nv_bfloat16 W2T[kHid * kLdH];    // W2 as [out][in] (forward B operand)
+    __nv_bfloat16 H1[kRows * kLdH];    // [r][unit]
+    float b1[kHid], b2[kHid], w3[kHid];
+    float y[kRows];
+};
+
+struct MlpTrainSmem {
+    __nv_bfloat16 W2[kHid * kLdH];      // W2 as [in][out] (backward B operand of dH1 = dH2 W2^T)
+    __nv_bfloat16 H2[kRows * kLdH];     // [r][unit]
+    __nv_bfloat16 XT[kIn * kLdR];       // [f][r]
+    __nv_bfloat16 H1T[kHid * kLdR];     // [unit][r]
+    __nv_bfloat16 dH2[kRows * kLdH];    // [r][unit]
+    __nv_bfloat16 dH2T[kHid * kLdR];    // [unit][r]
+    __nv_bfloat16 dH1T[kHid * kLdR];    // [unit][r]
+    float dy[kRows];
+};
+
+// Forward (and in TRAIN mode, backward) for rows [row0, row0 + 64).  4 warps.
+//   X: rows x 16 bf16; Wb: bf16 copies (W1 [16][128], W2 [128][128], w3 [128]);
+//   P: fp32 masters (biases read from here); y: rows fp32 predictions.
+//   TRAIN: t targets, inv_batch = 1/B; grads fp32 (atomic adds), loss (atomic add of sum of squares).
+template <bool TRAIN>
+__global__ void __launch_bounds__(128) k_mlp(const __nv_bfloat16 *__restrict__ X, int64_t rows,
+                                             const __nv_bfloat16 *__restrict__ W1b,
+                                             const __nv_bfloat16 *__restrict__ W2b,
+                                             const __nv_bfloat16 *__restrict__ w3b, const float *__restrict__ P,
+                                             float *__restrict__ y_out, const float *__restrict__ t, float inv_batch,
+                                             float *__restrict__ grads, float *__restrict__ loss)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    MlpSmem &S = *reinterpret_cast<MlpSmem *>(smem_raw);
+    MlpTrainSmem &T = *reinterpret_cast<MlpTrainSmem *>(smem_raw + ((sizeof(MlpSmem) + 15) & ~size_t(15)));
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int g = lane >> 2, c = lane & 3;
+    const int64_t row0 = (int64_t)blockIdx.x * kRows;
+
+    // ---- stage weights and inputs ----
+    for (int i = tid; i < kIn * kHid; i += blockDim.x) {  // W1 [in][out] -> W1T [out][in]
+        const int in = i / kHid, out = i % kHid;
+        S.W1T[out * kLdX + in] = W1b[i];
+    }
+    for (int i = tid; i < kHid * kHid; i += blockDim.x) {  // W2 [in][out]
+        const int in = i / kHid, out = i % kHid;
+        S.W2T[out * kLdH + in] = W2b[i];
+        if (TRAIN)
+            T.W2[in * kLdH + out] = W2b[i];
+    }
+    for (int i = tid; i < kHid; i += blockDim.x) {
+        S.b1[i] = P[kOffB1 + i];
+        S.b2[i] = P[kOffB2 + i];
+        S.w3[i] = __bfloat162float(w3b[i]);
+    }
+    for (int i = tid; i < kRows * kIn; i += blockDim.x) {
+        const int r = i / kIn, f = i % kIn;
+        const __nv_bfloat16 v = (row0 + r < rows) ? X[(row0 + r) * kIn + f] : __float2bfloat16(0.0f);
+        S.X[r * kLdX + f] = v;
+        if (TRAIN)
+            T.XT[f * kLdR + r] = v;
+    }
+    __syncthreads();
+
+    const int r0 = warp * 16;  // this warp's 16 rows
+    // ---- layer 1: H1 = relu(X W1 + b1) ----
+    {
+        uint32_t a[4];
+        frag_a(a, S.X, kLdX, r0, 0, lane);
+#pragma unroll
+        for (int nt = 0; nt < kHid / 8; ++nt) {
+            float d[4] = {0.f, 0.f, 0.f, 0.f};
+            uint32_t b[2];
+            frag_b(b, S.W1T, kLdX, nt * 8, 0, lane);
+            mma_bf16(d, a, b);
+            const int col = nt * 8 + 2 * c;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int r = r0 + g + 8 * h;
+                const float v0 = fmaxf(d[2 * h] + S.b1[col], 0.f), v1 = fmaxf(d[2 * h + 1] + S.b1[col + 1], 0.f);
+                const __nv_bfloat16 q0 = __float2bfloat16(v0), q1 = __float2bfloat16(v1);
+                S.H1[r * kLdH + col] = q0;
+                S.H1[r * kLdH + col + 1] = q1;
+                if (TRAIN) {
+                    T.H1T[col * kLdR + r] = q0;
+                    T.H1T[(col + 1) * kLdR + r] = q1;
+                }
+            }
+        }
+    }
+    __syncwarp();
+    // ---- layer 2 + 3: H2 = relu(H1 W2 + b2), y = H2 w3 + b3 ----
+    {
+        float acc[kHid / 8][4];
+#pragma unroll
+        for (int nt = 0; nt < kHid / 8; ++nt)
+            acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+#pragma unroll
+        for (int ks = 0; ks < kHid / 16; ++ks) {
+            uint32_t a[4];
+            frag_a(a, S.H1, kLdH, r0, ks * 16, lane);
+#pragma unroll
+            for (int nt = 0; nt < kHid / 8; ++nt) {
+                uint32_t b[2];
+                frag_b(b, S.W2T, kLdH, nt * 8, ks * 16, lane);
+                mma_bf16(acc[nt], a, b);
+            }
+        }
+        float ysum[2] = {0.f, 0.f};
+#pragma unroll
+        for (int nt = 0; nt < kHid / 8; ++nt) {
+            const int col = nt * 8 + 2 * c;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int r = r0 + g + 8 * h;
+                const __nv_bfloat16 q0 = __float2bfloat16(fmaxf(acc[nt][2 * h] + S.b2[col], 0.f));
+                const __nv_bfloat16 q1 = __float2bfloat16(fmaxf(acc[nt][2 * h + 1] + S.b2[col + 1], 0.f));
+                ysum[h] += __bfloat162float(q0) * S.w3[col] + __bfloat162float(q1) * S.w3[col + 1];
+                if (TRAIN) {
+                    T.H2[r * kLdH + col] = q0;
+                    T.H2[r * kLdH + col + 1] = q1;
+                }
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            ysum[h] += __shfl_xor_sync(PM_FULL_MASK, ysum[h], 1);
+            ysum[h] += __shfl_xor_sync(PM_FULL_MASK, ysum[h], 2);
+        }
+        if (c == 0) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int r = r0 + g + 8 * h;
+                const float yv = ysum[h] + P[kOffB3];
+                S.y[r] = yv;
+                if (row0 + r < rows)
+                    y_out[row0 + r] = yv;
+            }
+        }
+    }
+    if (!TRAIN)
+        return;
+
+    // ================= backward (mean squared error) =================
+    __syncthreads();
+    if (tid < kRows) {
+        const int r = tid;
+        float dy = 0.f, sq = 0.f;
+        if (row0 + r < rows) {
+            const float e = S.y[r] - t[row0 + r];
+            dy = 2.f * e * inv_batch;
+            sq = e * e;
+        }
+        T.dy[r] = dy;
+        // loss: sum of squares (the host divides by B)
+        sq += __shfl_xor_sync(PM_FULL_MASK, sq, 16);
+        sq += __shfl_xor_sync(PM_FULL_MASK, sq, 8);
+        sq += __shfl_xor_sync(PM_FULL_MASK, sq, 4);
+        sq += __shfl_xor_sync(PM_FULL_MASK, sq, 2);
+        sq += __shfl_xor_sync(PM_FULL_MASK, sq, 1);
+        if ((tid & 31) == 0)
+            atomicAdd(loss, sq);
+        float db3 = dy;
+        db3 += __shfl_xor_sync(PM_FULL_MASK, db3, 16);
+        db3 += __shfl_xor_sync(PM_FULL_MASK, db3, 8);
+        db3 += __shfl_xor_sync(PM_FULL_MASK, db3, 4);
+        db3 += __shfl_xor_sync(PM_FULL_MASK, db3, 2);
+        db3 += __shfl_xor_sync(PM_FULL_MASK, db3, 1);
+        if ((tid & 31) == 0)
+            atomicAdd(grads + kOffB3, db3);
+    }
+    __syncthreads();
+    // dw3[u] = sum_r h2[r][u] dy[r];  dH2[r][u] = bf16(dy[r] w3[u] [h2 > 0]);  db2[u] = sum_r dH2[r][u]
+    for (int u = tid; u < kHid; u += blockDim.x) {
+        float dw = 0.f, db = 0.f;
+        for (int r = 0; r < kRows; ++r) {
+            const float h2 = __bfloat162float(T.H2[r * kLdH + u]);
+            const float dyr = T.dy[r];
+            dw += h2 * dyr;
+            const __nv_bfloat16 q = __float2bfloat16(h2 > 0.f ? dyr * S.w3[u] : 0.f);
+            T.dH2[r * kLdH + u] = q;
+            T.dH2T[u * kLdR + r] = q;
+            db += __bfloat162float(q);
+        }
+        atomicAdd(grads + kOffW3 + u, dw);
+        atomicAdd(grads + kOffB2 + u, db);
+    }
+    __syncthreads();
+    // dH1 = bf16((dH2 W2^T) [h1 > 0]); warp w: rows r0..r0+15, all 128 units
+    {
+        float acc[kHid / 8][4];
+#pragma unroll
+        for (int nt = 0; nt < kHid / 8; ++nt)
+            acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+#pragma unroll
+        for (int ks = 0; ks < kHid / 16; ++ks) {
+            uint32_t a[4];
+            frag_a(a, T.dH2, kLdH, r0, ks * 16, lane);
+#pragma unroll
+            for (int nt = 0; nt < kHid / 8; ++nt) {
+                uint32_t b[2];
+                frag_b(b, T.W2, kLdH, nt * 8, ks * 16, lane);  // B[k = out][n = in] = W2[in][out]
+                mma_bf16(acc[nt], a, b);
+            }
+        }
+#pragma unroll
+        for (int nt = 0; nt < kHid / 8; ++nt) {
+            const int col = nt * 8 + 2 * c;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int r = r0 + g + 8 * h;
+                const bool on0 = __bfloat162float(S.H1[r * kLdH + col]) > 0.f;
+                const bool on1 = __bfloat162float(S.H1[r * kLdH + col + 1]) > 0.f;
+                T.dH1T[col * kLdR + r] = __float2bfloat16(on0 ? acc[nt][2 * h] : 0.f);
+                T.dH1T[(col + 1) * kLdR + r] = __float2bfloat16(on1 ? acc[nt][2 * h + 1] : 0.f);
+            }
+        }
+    }
+    __syncthreads();
+    // db1[u] = sum_r dH1[r][u]
+    for (int u = tid; u < kHid; u += blockDim.x) {
+        float db = 0.f;
+        for (int r = 0; r < kRows; ++r)
+            db += __bfloat162float(T.dH1T[u * kLdR + r]);
+        atomicAdd(grads + kOffB1 + u, db);
+    }
+    // dW2 = H1^T dH2 (128 x 128, k = the 64 rows); warp w: output rows 32w .. 32w+31, in two halves of 64 cols
+#pragma unroll 1
+    for (int half = 0; half < 2; ++half) {
+        float acc[2][8][4];
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt)
+                acc[mt][nt][0] = acc[mt][nt][1] = acc[mt][nt][2] = acc[mt][nt][3] = 0.f;
+#pragma unroll
+        for (int ks = 0; ks < kRows / 16; ++ks) {
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                uint32_t a[4];
+                frag_a(a, T.H1T, kLdR, warp * 32 + mt * 16, ks * 16, lane);
+#pragma unroll
+                for (int nt = 0; nt < 8; ++nt) {
+                    uint32_t b[2];
+                    frag_b(b, T.dH2T, kLdR, half * 64 + nt * 8, ks * 16, lane);
+                    mma_bf16(acc[mt][nt], a, b);
+                }
+            }
+        }
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt) {
+                const int col = half * 64 + nt * 8 + 2 * c;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int in = warp * 32 + mt * 16 + g + 8 * h;
+                    atomicAdd(grads + kOffW2 + in * kHid + col, acc[mt][nt][2 * h]);
+                    atomicAdd(grads + kOffW2 + in * kHid + col + 1, acc[mt][nt][2 * h + 1]);
+                }
+            }
+    }
+    // dW1 = X^T dH1 (16 x 128, k = the 64 rows); warp w: units 32w .. 32w+31
+    {
+        float acc[4][4];
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+            acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+#pragma unroll
+        for (int ks = 0; ks < kRows / 16; ++ks) {
+            uint32_t a[4];
+            frag_a(a, T.XT, kLdR, 0, ks * 16, lane);
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+                uint32_t b[2];
+                frag_b(b, T.dH1T, kLdR, warp * 32 + nt * 8, ks * 16, lane);
+                mma_bf16(acc[nt], a, b);
+            }
+        }
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+            const int col = warp * 32 + nt * 8 + 2 * c;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int in = g + 8 * h;
+                atomicAdd(grads + kOffW1 + in * kHid + col, acc[nt][2 * h]);
+                atomicAdd(grads + kOffW1 + in * kHid + col + 1, acc[nt][2 * h + 1]);
+            }
+        }
+    }
+}
+
+// Adam (Kingma & Ba 2015, Algorithm 1) on the FP32 masters; refreshes the BF16 copies.
+__global__ void k_adam(float *__restrict__ P, float *__restrict__ M, float *__restrict__ V,
+                       const float *__restrict__ G, int n, float lr, float bc1, float bc2,
+                       __nv_bfloat16 *__restrict__ W1b, __nv_bfloat16 *__restrict__ W2b,
+                       __nv_bfloat16 *__restrict__ w3b)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    const float g = G[i];
+    const float m = 0.9f * M[i] + 0.1f * g;
+    const float v = 0.999f * V[i] + 0.001f * g * g;
+    M[i] = m;
+    V[i] = v;
+    const float mhat = m / bc1, vhat = v / bc2;
+    const float w = P[i] - lr * mhat / (sqrtf(vhat) + 1e-8f);
+    P[i] = w;
+    if (i < kOffB1)
+        W1b[i - kOffW1] = __float2bfloat16(w);
+    else if (i >= kOffW2 && i < kOffB2)
+        W2b[i - kOffW2] = __float2bfloat16(w);
+    else if (i >= kOffW3 && i < kOffB3)
+        w3b[i - kOffW3] = __float2bfloat16(w);
+}
+
+__global__ void k_refresh_bf16(const float *__restrict__ P, __nv_bfloat16 *__restrict__ W1b,
+                               __nv_bfloat16 *__restrict__ W2b, __nv_bfloat16 *__restrict__ w3b)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < kIn * kHid)
+        W1b[i] = __float2bfloat16(P[kOffW1 + i]);
+    if (i < kHid * kHid)
+        W2b[i] = __float2bfloat16(P[kOffW2 + i]);
+    if (i < kHid)
+        w3b[i] = __float2bfloat16(P[kOffW3 + i]);
+}
+
+// ---------------------------------------------------------------------------
+// Swap statistics: one CTA per individual; accumulators in shared memory when
+// they fit (else in the output arrays, zeroed by the caller).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(512) k_swap_stats(const uint16_t *__restrict__ pi, const int32_t *__restrict__ delta,
+                                                    int64_t n, int32_t L, int64_t stride, int32_t W, int32_t m,
+                                                    const uint32_t *__restrict__ masks, int64_t pop,
+                                                    unsigned long long *__restrict__ gain, int *__restrict__ cap,
+                                                    unsigned long long *__restrict__ loss, int *__restrict__ assign,
+                                                    int in_smem)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int64_t t = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    uint32_t *bits = reinterpret_cast<uint32_t *>(sm);
+    const size_t off = ((size_t)W * 4 + 15) & ~size_t(15);
+    unsigned long long *G, *Lo;
+    int *C, *A;
+    if (in_smem) {
+        G = reinterpret_cast<unsigned long long *>(sm + off);
+        Lo = G + m;
+        C = reinterpret_cast<int *>(Lo + m);
+        A = C + m;
+        for (int j = threadIdx.x; j < m; j += blockDim.x) {
+            G[j] = 0ull;
+            Lo[j] = 0ull;
+            C[j] = 0;
+            A[j] = 0;
+        }
+    } else {
+        G = gain + t * m;
+        Lo = loss + t * m;
+        C = cap + t * m;
+        A = assign + t * m;
+    }
+    for (int w = threadIdx.x; w < W; w += blockDim.x)
+        bits[w] = masks[t * W + w];
+    __syncthreads();
+    for (int64_t i = warp; i < n; i += nwarps) {
+        const uint16_t *prow = pi + i * stride;
+        const int32_t *drow = delta + i * stride;
+        // pass 1: first and second open ranks and their distances
+        int32_t carry = 0, d1 = 0, d2 = 0;
+        int r1 = -1, found = 0;
+        for (int base = 0; base < L && found < 2; base += 32) {
+            const int r = base + lane;
+            uint32_t j = 0;
+            int32_t dl = 0;
+            if (r < L) {
+                j = __ldg(prow + r);
+                dl = __ldg(drow + r);
+            }
+            const bool open = (r < L) && ((bits[j >> 5] >> (j & 31)) & 1u);
+            int32_t cs = dl;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t y = __shfl_up_sync(PM_FULL_MASK, cs, o);
+                if (lane >= o)
+                    cs += y;
+            }
+            cs += carry;
+            uint32_t bal = __ballot_sync(PM_FULL_MASK, open);
+            if (found == 0 && bal) {
+                const int f = __ffs(bal) - 1;
+                d1 = __shfl_sync(PM_FULL_MASK, cs, f);
+                r1 = base + f;
+                found = 1;
+                bal &= bal - 1u;
+            }
+            if (found == 1 && bal) {
+                d2 = __shfl_sync(PM_FULL_MASK, cs, __ffs(bal) - 1);
+                found = 2;
+            }
+            carry = __shfl_sync(PM_FULL_MASK, cs, 31);
+        }
+        if (found == 0)
+            continue;  // fewer than p open facilities: no statistics for this client
+        if (found == 1)
+            d2 = carry;  // no second open facility within the table
+        if (lane == 0) {
+            const uint32_t f1 = __ldg(prow + r1);
+            atomicAdd(Lo + f1, (unsigned long long)(uint32_t)(d2 - d1));
+            atomicAdd(A + f1, 1);
+        }
+        // pass 2: every facility ranked before r1 gains D1 - d(i, k)
+        carry = 0;
+        for (int base = 0; base < r1; base += 32) {
+            const int r = base + lane;
+            uint32_t j = 0;
+            int32_t dl = 0;
+            if (r < r1) {
+                j = __ldg(prow + r);
+                dl = __ldg(drow + r);
+            }
+            int32_t cs = dl;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t y = __shfl_up_sync(PM_FULL_MASK, cs, o);
+                if (lane >= o)
+                    cs += y;
+            }
+            cs += carry;
+            if (r < r1) {
+                atomicAdd(G + j, (unsigned long long)(uint32_t)(d1 - cs));
+                atomicAdd(C + j, 1);
+            }
+            carry = __shfl_sync(PM_FULL_MASK, cs, 31);
+        }
+    }
+    if (in_smem) {
+        __syncthreads();
+        for (int j = threadIdx.x; j < m; j += blockDim.x) {
+            gain[t * m + j] = G[j];
+            loss[t * m + j] = Lo[j];
+            cap[t * m + j] = C[j];
+            assign[t * m + j] = A[j];
+        }
+    }
+}
+
+__device__ __forceinline__ void move_feature_row(__nv_bfloat16 *out, float lj, float gk, float aj, float ck, float Z,
+                                                 float per, float pm_ratio, float ldiff)
+{
+    float f[kFeat];
+    f[0] = lj / Z;
+    f[1] = gk / Z;
+    f[2] = aj / per;
+    f[3] = ck / per;
+    f[4] = ldiff / Z;
+    f[5] = log1pf(f[0]);
+    f[6] = log1pf(f[1]);
+    f[7] = pm_ratio;
+#pragma unroll
+    for (int q = 0; q < kFeat; ++q)
+        out[q] = __float2bfloat16(f[q]);
+#pragma unroll
+    for (int q = kFeat; q < kIn; ++q)
+        out[q] = __float2bfloat16(0.f);
+}
+
+// Features of given moves: moves[(t*C + c)*2 + {0,1}] = (j closed, k opened).
+__global__ void k_move_features(const unsigned long long *__restrict__ gain, const int *__restrict__ cap,
+                                const unsigned long long *__restrict__ loss, const int *__restrict__ assign,
+                                const int64_t *__restrict__ costs, const int32_t *__restrict__ moves, int64_t pop,
+                                int64_t C, int32_t m, int64_t n, int32_t p, __nv_bfloat16 *__restrict__ X)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= pop * C)
+        return;
+    const int64_t t = idx / C;
+    const int32_t j = min(max(moves[idx * 2], 0), m - 1), k = min(max(moves[idx * 2 + 1], 0), m - 1);
+    const float Z = fmaxf((float)costs[t] / (float)p, 1.f);
+    const unsigned long long lj = loss[t * m + j], gk = gain[t * m + k];
+    move_feature_row(X + idx * kIn, (float)lj, (float)gk, (float)assign[t * m + j], (float)cap[t * m + k], Z,
+                     (float)n / (float)p, (float)p / (float)m, (float)((long long)lj - (long long)gk));
+}
+
+// Candidate moves of the learned try, one CTA per individual: the T closed
+// facilities with the largest gain (ties: lower id), each paired with every
+// open facility: C = p * T rows (j = the a-th open facility, k = the b-th
+// best, row a * T + b).
+__global__ void __launch_bounds__(256) k_candidates(const uint32_t *__restrict__ masks, int32_t W, int32_t m,
+                                                    int32_t p, int64_t n, const unsigned long long *__restrict__ gain,
+                                                    const int *__restrict__ cap,
+                                                    const unsigned long long *__restrict__ loss,
+                                                    const int *__restrict__ assign, const int64_t *__restrict__ costs,
+                                                    int T, int32_t *__restrict__ moves, __nv_bfloat16 *__restrict__ X)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    int32_t *open_s = reinterpret_cast<int32_t *>(sm);  // p entries
+    for (int i = threadIdx.x; i < p; i += blockDim.x)
+        open_s[i] = 0;  // a bitset with fewer than p open facilities still yields valid ids
+    __syncthreads();
+    __shared__ unsigned long long top_g[8];
+    __shared__ int32_t top_k[8];
+    __shared__ int32_t nopen;
+    const int64_t t = blockIdx.x;
+    const uint32_t *x = masks + t * W;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // open facilities in ascending order (warp 0)
+    if (warp == 0) {
+        int cnt = 0;
+        for (int base = 0; base < W; base += 32) {
+            const int w = base + lane;
+            const uint32_t word = w < W ? x[w] : 0u;
+            const int pc = __popc(word);
+            int incl = pc;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(PM_FULL_MASK, incl, o);
+                if (lane >= o)
+                    incl += y;
+            }
+            int pos = cnt + incl - pc;
+            uint32_t rest = word;
+            while (rest) {
+                const int b = __ffs(rest) - 1;
+                rest &= rest - 1u;
+                if (pos < p)
+                    open_s[pos] = w * 32 + b;
+                ++pos;
+            }
+            cnt += __shfl_sync(PM_FULL_MASK, incl, 31);
+        }
+        if (lane == 0)
+            nopen = cnt < p ? cnt : p;
+    }
+    // top-T closed facilities by gain: T rounds of a block-wide (gain desc, id asc) arg-max
+    __shared__ unsigned long long red_g[8];
+    __shared__ int32_t red_k[8];
+    for (int b = 0; b < T; ++b) {
+        unsigned long long bg = 0ull;
+        int32_t bk = 0x7fffffff;
+        bool have = false;
+        for (int k = tid; k < m; k += blockDim.x) {
+            if ((x[k >> 5] >> (k & 31)) & 1u)
+                continue;
+            bool taken = false;
+            for (int q = 0; q < b; ++q)
+                taken = taken || (top_k[q] == k);
+            if (taken)
+                continue;
+            const unsigned long long gk = gain[t * m + k];
+            if (!have || gk > bg || (gk == bg && k < bk)) {
+                bg = gk;
+                bk = k;
+                have = true;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long og = __shfl_xor_sync(PM_FULL_MASK, bg, o);
+            const int32_t ok = __shfl_xor_sync(PM_FULL_MASK, bk, o);
+            if (ok != 0x7fffffff && (bk == 0x7fffffff || og > bg || (og == bg && ok < bk))) {
+                bg = og;
+                bk = ok;
+            }
+        }
+        if (lane == 0) {
+            red_g[warp] = bg;
+            red_k[warp] = bk;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            unsigned long long g0 = red_g[0];
+            int32_t k0 = red_k[0];
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+                if (red_k[w] != 0x7fffffff && (k0 == 0x7fffffff || red_g[w] > g0 || (red_g[w] == g0 && red_k[w] < k0))) {
+                    g0 = red_g[w];
+                    k0 = red_k[w];
+                }
+            if (k0 == 0x7fffffff)  // fewer than T closed facilities: repeat the previous one
+                k0 = b > 0 ? top_k[b - 1] : 0;
+            top_g[b] = g0;
+            top_k[b] = k0;
+        }
+        __syncthreads();
+    }
+    const float Z = fmaxf((float)costs[t] / (float)p, 1.f);
+    const float per = (float)n / (float)p, ratio = (float)p / (float)m;
+    const int64_t C = (int64_t)p * T;
+    for (int64_t row = tid; row < C; row += blockDim.x) {
+        const int a = (int)(row / T), b = (int)(row % T);
+        const int32_t j = open_s[a < nopen ? a : 0], k = top_k[b];
+        const int64_t idx = t * C + row;
+        moves[idx * 2] = j;
+        moves[idx * 2 + 1] = k;
+        const unsigned long long lj = loss[t * m + j], gk = gain[t * m + k];
+        move_feature_row(X + idx * kIn, (float)lj, (float)gk, (float)assign[t * m + j], (float)cap[t * m + k], Z, per,
+                         ratio, (float)((long long)lj - (long long)gk));
+    }
+}
+
+// Philox4x32-10 (Salmon et al., SC'11) for sampling training moves.
+__device__ __forceinline__ uint4 philox_draw(uint64_t seed, uint32_t a, uint32_t b, uint32_t c)
+{
+    uint4 x = make_uint4(a, b, c, 0x4C45524Eu);
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        if (round) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * x.x, hi0 = __umulhi(0xD2511F53u, x.x);
+        const uint32_t lo1 = 0xCD9E8D57u * x.z, hi1 = __umulhi(0xCD9E8D57u, x.z);
+        x = make_uint4(hi1 ^ x.y ^ k0, lo1, hi0 ^ x.w ^ k1, lo0);
+    }
+    return x;
+}
+
+__device__ __forceinline__ uint32_t below(uint32_t u, uint32_t N) { return (uint32_t)(((unsigned long long)u * N) >> 32); }
+
+// Training moves, one CTA per individual: j uniform among the open
+// facilities; k among the 4 largest-gain closed facilities with probability
+// 3/4 (the learned try's candidates), else uniform among the closed ones.
+__global__ void __launch_bounds__(256) k_sample_moves(const uint32_t *__restrict__ masks, int32_t W, int32_t m,
+                                                      int32_t p, const unsigned long long *__restrict__ gain,
+                                                      int64_t per, uint64_t seed, int32_t *__restrict__ moves)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    int32_t *open_s = reinterpret_cast<int32_t *>(sm);
+    for (int i = threadIdx.x; i < p; i += blockDim.x)
+        open_s[i] = 0;  // a bitset with fewer than p open facilities still yields valid ids
+    __syncthreads();
+    __shared__ int32_t top_k[4];
+    __shared__ unsigned long long red_g[8];
+    __shared__ int32_t red_k[8];
+    const int64_t t = blockIdx.x;
+    const uint32_t *x = masks + t * W;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (warp == 0) {
+        int cnt = 0;
+        for (int base = 0; base < W; base += 32) {
+            const int w = base + lane;
+            const uint32_t word = w < W ? x[w] : 0u;
+            const int pc = __popc(word);
+            int incl = pc;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(PM_FULL_MASK, incl, o);
+                if (lane >= o)
+                    incl += y;
+            }
+            int pos = cnt + incl - pc;
+            uint32_t rest = word;
+            while (rest) {
+                const int b = __ffs(rest) - 1;
+                rest &= rest - 1u;
+                if (pos < p)
+                    open_s[pos] = w * 32 + b;
+                ++pos;
+            }
+            cnt += __shfl_sync(PM_FULL_MASK, incl, 31);
+        }
+    }
+    for (int b = 0; b < 4; ++b) {
+        unsigned long long bg = 0ull;
+        int32_t bk = 0x7fffffff;
+        for (int k = tid; k < m; k += blockDim.x) {
+            if ((x[k >> 5] >> (k & 31)) & 1u)
+                continue;
+            bool taken = false;
+            for (int q = 0; q < b; ++q)
+                taken = taken || (top_k[q] == k);
+            if (taken)
+                continue;
+            const unsigned long long gk = gain[t * m + k];
+            if (bk == 0x7fffffff || gk > bg || (gk == bg && k < bk)) {
+                bg = gk;
+                bk = k;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long og = __shfl_xor_sync(PM_FULL_MASK, bg, o);
+            const int32_t ok = __shfl_xor_sync(PM_FULL_MASK, bk, o);
+            if (ok != 0x7fffffff && (bk == 0x7fffffff || og > bg || (og == bg && ok < bk))) {
+                bg = og;
+                bk = ok;
+            }
+        }
+        if (lane == 0) {
+            red_g[warp] = bg;
+            red_k[warp] = bk;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            unsigned long long g0 = red_g[0];
+            int32_t k0 = red_k[0];
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+                if (red_k[w] != 0x7fffffff && (k0 == 0x7fffffff || red_g[w] > g0 || (red_g[w] == g0 && red_k[w] < k0))) {
+                    g0 = red_g[w];
+                    k0 = red_k[w];
+                }
+            top_k[b] = k0 == 0x7fffffff ? (b > 0 ? top_k[b - 1] : 0) : k0;
+        }
+        __syncthreads();
+    }
+    for (int64_t q = tid; q < per; q += blockDim.x) {
+        const uint4 v = philox_draw(seed, (uint32_t)t, (uint32_t)q, 0u);
+        const int32_t j = open_s[below(v.x, (uint32_t)p)];
+        int32_t k = top_k[below(v.y, 4u)];
+        if (below(v.z, 4u) == 3u) {  // uniform closed facility (bounded rejection)
+            uint32_t u = v.w;
+            for (int tries = 0; tries < 64; ++tries) {
+                const int32_t c = (int32_t)below(u, (uint32_t)m);
+                if (!((x[c >> 5] >> (c & 31)) & 1u)) {
+                    k = c;
+                    break;
+                }
+                u = philox_draw(seed, (uint32_t)t, (uint32_t)q, (uint32_t)(tries + 1)).x;
+            }
+        }
+        moves[(t * per + q) * 2] = j;
+        moves[(t * per + q) * 2 + 1] = k;
+    }
+}
+
+// Swapped bitsets: row (t * per + q) = individual t with moves[..][0] closed and moves[..][1] opened.
+__global__ void k_apply_moves(const uint32_t *__restrict__ masks, int32_t W, int64_t pop, int64_t per,
+                              const int32_t *__restrict__ moves, uint32_t *__restrict__ out)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= pop * per * W)
+        return;
+    const int64_t row = idx / W;
+    const int32_t w = (int32_t)(idx % W);
+    const int64_t t = row / per;
+    uint32_t v = masks[t * W + w];
+    const int32_t j = moves[row * 2], k = moves[row * 2 + 1];
+    if ((j >> 5) == w)
+        v &= ~(1u << (j & 31));
+    if ((k >> 5) == w)
+        v |= 1u << (k & 31);
+    out[idx] = v;
+}
+
+__global__ void k_targets(const int64_t *__restrict__ before, const int64_t *__restrict__ after, int64_t pop,
+                          int64_t per, int32_t p, float *__restrict__ t_out)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= pop * per)
+        return;
+    const int64_t t = idx / per;
+    const float Z = fmaxf((float)before[t] / (float)p, 1.f);
+    t_out[idx] = (float)(after[idx] - before[t]) / Z;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Host side: the model object
+// ---------------------------------------------------------------------------
+
+pm_status pm_learn_prepare(const pm_instance *inst);
+
+struct pm_model {
+    int device = 0;
+    pm_dbuf P, M, V, G, W1b, W2b, w3b, loss;
+    int64_t step = 0;
+    std::mutex lock;
+};
+
+static size_t mlp_smem(bool train)
+{
+    size_t s = (sizeof(MlpSmem) + 15) & ~size_t(15);
+    if (train)
+        s += sizeof(MlpTrainSmem);
+    return s;
+}
+
+static pm_status mlp_init_attrs()
+{
+    PM_CUDA(cudaFuncSetAttribute(k_mlp<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp_smem(false)));
+    PM_CUDA(cudaFuncSetAttribute(k_mlp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp_smem(true)));
+    return PM_OK;
+}
+
+static pm_status model_refresh(pm_model *md, cudaStream_t s)
+{
+    k_refresh_bf16<<<(kHid * kHid + 255) / 256, 256, 0, s>>>(
+        static_cast<const float *>(md->P.ptr), static_cast<__nv_bfloat16 *>(md->W1b.ptr),
+        static_cast<__nv_bfloat16 *>(md->W2b.ptr), static_cast<__nv_bfloat16 *>(md->w3b.ptr));
+    PM_CUDA(cudaGetLastError());
+    return PM_OK;
+}
+
+extern "C" pm_status pm_model_create(int device, uint64_t seed, pm_model **out)
+{
+    if (!out || device < 0)
+        return PM_ERR_INVALID_ARG;
+    *out = nullptr;
+    PM_CUDA(cudaSetDevice(device));
+    pm_model *md = new (std::nothrow) pm_model();
+    if (!md)
+        return PM_ERR_OOM;
+    md->device = device;
+    pm_status st = PM_OK;
+    pm_dbuf *bufs[] = {&md->P, &md->M, &md->V, &md->G};
+    for (pm_dbuf *b : bufs)
+        if (st == PM_OK)
+            st = b->reserve(kParams * sizeof(float));
+    if (st == PM_OK)
+        st = md->W1b.reserve(kIn * kHid * 2);
+    if (st == PM_OK)
+        st = md->W2b.reserve(kHid * kHid * 2);
+    if (st == PM_OK)
+        st = md->w3b.reserve(kHid * 2);
+    if (st == PM_OK)
+        st = md->loss.reserve(256);
+    if (st == PM_OK)
+        st = mlp_init_attrs();
+    if (st != PM_OK) {
+        pm_model_destroy(md);
+        return st;
+    }
+    // He-style initialisation from a seeded host generator (splitmix64 + Box-Muller)
+    std::vector<float> h(kParams, 0.f);
+    uint64_t z = seed ^ 0x9E3779B97F4A7C15ull;
+    auto next = [&]() {
+        z += 0x9E3779B97F4A7C15ull;
+        uint64_t r = z;
+        r = (r ^ (r >> 30)) * 0xBF58476D1CE4E5B9ull;
+        r = (r ^ (r >> 27)) * 0x94D049BB133111EBull;
+        return r ^ (r >> 31);
+    };
+    auto normal = [&]() {
+        const double u1 = ((next() >> 11) + 1.0) / 9007199254740993.0, u2 = (next() >> 11) / 9007199254740992.0;
+        return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+    };
+    for (int i = 0; i < kFeat; ++i)  // rows of the padded inputs stay zero
+        for (int o = 0; o < kHid; ++o)
+            h[kOffW1 + i * kHid + o] = (float)(normal() * std::sqrt(2.0 / kFeat));
+    for (int i = 0; i < kHid * kHid; ++i)
+        h[kOffW2 + i] = (float)(normal() * std::sqrt(2.0 / kHid));
+    for (int i = 0; i < kHid; ++i)
+        h[kOffW3 + i] = (float)(normal() * std::sqrt(1.0 / kHid));
+    st = pm_model_set_params(md, h.data(), nullptr);
+    if (st != PM_OK) {
+        pm_model_destroy(md);
+        return st;
+    }
+    *out = md;
+    return PM_OK;
+}
+
+extern "C" pm_status pm_model_destroy(pm_model *md)
+{
+    if (!md)
+        return PM_OK;
+    cudaSetDevice(md->device);
+    pm_dbuf *bufs[] = {&md->P, &md->M, &md->V, &md->G, &md->W1b, &md->W2b, &md->w3b, &md->loss};
+    for (pm_dbuf *b : bufs)
+        b->release();
+    delete md;
+    return PM_OK;
+}
+
+extern "C" int64_t pm_model_num_params(void) { return kParams; }
+
+extern "C" pm_status pm_model_set_params(pm_model *md, const float *params, void *stream)
+{
+    if (!md || !params)
+        return PM_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> g(md->lock);
+    PM_CUDA(cudaSetDevice(md->device));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    PM_CUDA(cudaMemcpyAsync(md->P.ptr, params, kParams * sizeof(float), cudaMemcpyDefault, s));
+    PM_CUDA(cudaMemsetAsync(md->M.ptr, 0, kParams * sizeof(float), s));
+    PM_CUDA(cudaMemsetAsync(md->V.ptr, 0, kParams * sizeof(float), s));
+    md->step = 0;
+    PM_TRY(model_refresh(md, s));
+    PM_CUDA(cudaStreamSynchronize(s));
+    return PM_OK;
+}
+
+extern "C" pm_status pm_model_get_params(pm_model *md, float *params, void *stream)
+{
+    if (!md || !params)
+        return PM_ERR_INVALID_ARG;
+    PM_CUDA(cudaSetDevice(md->device));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    PM_CUDA(cudaMemcpyAsync(params, md->P.ptr, kParams * sizeof(float), cudaMemcpyDefault, s));
+    PM_CUDA(cudaStreamSynchronize(s));
+    return PM_OK;
+}
+
+static pm_status mlp_launch(pm_model *md, bool train, const void *x, int64_t rows, float *y, const float *t,
+                            float inv_batch, cudaStream_t s)
+{
+    const unsigned grid = (unsigned)pm_ceil_div(rows, kRows);
+    const __nv_bfloat16 *X = static_cast<const __nv_bfloat16 *>(x);
+    const __nv_bfloat16 *W1b = static_cast<const __nv_bfloat16 *>(md->W1b.ptr);
+    const __nv_bfloat16 *W2b = static_cast<const __nv_bfloat16 *>(md->W2b.ptr);
+    const __nv_bfloat16 *w3b = static_cast<const __nv_bfloat16 *>(md->w3b.ptr);
+    const float *P = static_cast<const float *>(md->P.ptr);
+    if (train)
+        k_mlp<true><<<grid, 128, mlp_smem(true), s>>>(X, rows, W1b, W2b, w3b, P, y, t, inv_batch,
+                                                      static_cast<float *>(md->G.ptr),
+                                                      static_cast<float *>(md->loss.ptr));
+    else
+        k_mlp<false><<<grid, 128, mlp_smem(false), s>>>(X, rows, W1b, W2b, w3b, P, y, nullptr, 0.f, nullptr,
+                                                        nullptr);
+    PM_CUDA(cudaGetLastError());
+    return PM_OK;
+}
+
+pm_status pm_model_forward_dev(pm_model *md, const void *x_dev, int64_t rows, float *y_dev, cudaStream_t s)
+{
+    if (rows <= 0)
+        return PM_OK;
+    return mlp_launch(md, false, x_dev, rows, y_dev, nullptr, 0.f, s);
+}
+
+extern "C" pm_status pm_model_forward(pm_model *md, const uint16_t *x, int64_t rows, float *y, void *stream)
+{
+    if (!md || !x || !y || rows < 0)
+        return PM_ERR_INVALID_ARG;
+    if (!pm_is_device_ptr(x) || !pm_is_device_ptr(y))
+        return PM_ERR_INVALID_ARG;
+    PM_CUDA(cudaSetDevice(md->device));
+    return pm_model_forward_dev(md, x, rows, y, static_cast<cudaStream_t>(stream));
+}
+
+// Gradients of the mean squared error (into md->G) and the loss; returns the
+// mean squared error in *loss_out (synchronises).
+static pm_status model_grad(pm_model *md, const uint16_t *x, const float *t, int64_t rows, float *loss_out,
+                            cudaStream_t s)
+{
+    PM_TRY(md->loss.reserve(256));
+    PM_CUDA(cudaMemsetAsync(md->G.ptr, 0, kParams * sizeof(float), s));
+    PM_CUDA(cudaMemsetAsync(md->loss.ptr, 0, sizeof(float), s));
+    // predictions go to a scratch area behind the loss word
+    pm_dbuf &yb = md->loss;
+    PM_TRY(yb.reserve(256 + (size_t)rows * 4));
+    PM_CUDA(cudaMemsetAsync(yb.ptr, 0, sizeof(float), s));
+    float *y = reinterpret_cast<float *>(static_cast<char *>(yb.ptr) + 256);
+    PM_TRY(mlp_launch(md, true, x, rows, y, t, 1.0f / (float)rows, s));
+    if (loss_out) {
+        float sq = 0.f;
+        PM_CUDA(cudaMemcpyAsync(&sq, yb.ptr, sizeof(float), cudaMemcpyDeviceToHost, s));
+        PM_CUDA(cudaStreamSynchronize(s));
+        *loss_out = sq / (float)rows;
+    }
+    return PM_OK;
+}
+
+extern "C" pm_status pm_model_grad(pm_model *md, const uint16_t *x, const float *t, int64_t rows, float *grads,
+                                   float *loss, void *stream)
+{
+    if (!md || !x || !t || rows < 1)
+        return PM_ERR_INVALID_ARG;
+    if (!pm_is_device_ptr(x) || !pm_is_device_ptr(t))
+        return PM_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> g(md->lock);
+    PM_CUDA(cudaSetDevice(md->device));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    PM_TRY(model_grad(md, x, t, rows, loss, s));
+    if (grads)
+        PM_CUDA(cudaMemcpyAsync(grads, md->G.ptr, kParams * sizeof(float), cudaMemcpyDefault, s));
+    PM_CUDA(cudaStreamSynchronize(s));
+    return PM_OK;
+}
+
+extern "C" pm_status pm_model_train_step(pm_model *md, const uint16_t *x, const float *t, int64_t rows, float lr,
+                                         float *loss, void *stream)
+{
+    if (!md || !x || !t || rows < 1 || !(lr > 0.f))
+        return PM_ERR_INVALID_ARG;
+    if (!pm_is_device_ptr(x) || !pm_is_device_ptr(t))
+        return PM_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> g(md->lock);
+    PM_CUDA(cudaSetDevice(md->device));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    PM_TRY(model_grad(md, x, t, rows, loss, s));
+    md->step += 1;
+    const float bc1 = 1.f - std::pow(0.9f, (float)md->step), bc2 = 1.f - std::pow(0.999f, (float)md->step);
+    k_adam<<<(kParams + 255) / 256, 256, 0, s>>>(
+        static_cast<float *>(md->P.ptr), static_cast<float *>(md->M.ptr), static_cast<float *>(md->V.ptr),
+        static_cast<const float *>(md->G.ptr), kParams, lr, bc1, bc2, static_cast<__nv_bfloat16 *>(md->W1b.ptr),
+        static_cast<__nv_bfloat16 *>(md->W2b.ptr), static_cast<__nv_bfloat16 *>(md->w3b.ptr));
+    PM_CUDA(cudaGetLastError());
+    if (loss)
+        PM_CUDA(cudaStreamSynchronize(s));
+    return PM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Swap statistics, move features, logging of training tuples
+// ---------------------------------------------------------------------------
+
+pm_status pm_launch_swap_stats(const pm_instance *inst, const uint32_t *masks, int64_t pop, int64_t *gain,
+                               int32_t *cap, int64_t *loss, int32_t *assign, cudaStream_t s)
+{
+    if (pop <= 0)
+        return PM_OK;
+    const size_t bits = (size_t)pm_round_up(inst->W * 4, 16);
+    const size_t acc = (size_t)inst->m * 24;
+    const bool in_smem = bits + acc + 1024 <= inst->smem_optin;
+    const size_t smem = in_smem ? bits + acc : bits;
+    if (!in_smem) {
+        PM_CUDA(cudaMemsetAsync(gain, 0, (size_t)pop * inst->m * 8, s));
+        PM_CUDA(cudaMemsetAsync(loss, 0, (size_t)pop * inst->m * 8, s));
+        PM_CUDA(cudaMemsetAsync(cap, 0, (size_t)pop * inst->m * 4, s));
+        PM_CUDA(cudaMemsetAsync(assign, 0, (size_t)pop * inst->m * 4, s));
+    }
+    k_swap_stats<<<(unsigned)pop, 512, smem, s>>>(inst->pi, inst->delta, inst->n, (int32_t)inst->L, inst->stride,
+                                                  (int32_t)inst->W, (int32_t)inst->m, masks, pop,
+                                                  reinterpret_cast<unsigned long long *>(gain), cap,
+                                                  reinterpret_cast<unsigned long long *>(loss), assign,
+                                                  in_smem ? 1 : 0);
+    PM_CUDA(cudaGetLastError());
+    return PM_OK;
+}
+
+extern "C" pm_status pm_swap_stats(pm_instance *inst, const uint32_t *masks, int64_t pop, int64_t *gain, int32_t *cap,
+                                   int64_t *loss, int32_t *assign, void *stream)
+{
+    if (!inst || pop < 0 || !masks || !gain || !cap || !loss || !assign)
+        return PM_ERR_INVALID_ARG;
+    const void *ptrs[] = {masks, gain, cap, loss, assign};
+    for (const void *p : ptrs)
+        if (!pm_is_device_ptr(p))
+            return PM_ERR_INVALID_ARG;
+    PM_CUDA(cudaSetDevice(inst->device));
+    PM_TRY(pm_learn_prepare(inst));
+    return pm_launch_swap_stats(inst, masks, pop, gain, cap, loss, assign, static_cast<cudaStream_t>(stream));
+}
+
+pm_status pm_launch_move_features(const pm_instance *inst, const int64_t *gain, const int32_t *cap, const int64_t *loss,
+                                  const int32_t *assign, const int64_t *costs, const int32_t *moves, int64_t pop,
+                                  int64_t C, uint16_t *x, cudaStream_t s)
+{
+    const int64_t rows = pop * C;
+    if (rows <= 0)
+        return PM_OK;
+    k_move_features<<<(unsigned)pm_ceil_div(rows, 256), 256, 0, s>>>(
+        reinterpret_cast<const unsigned long long *>(gain), cap, reinterpret_cast<const unsigned long long *>(loss),
+        assign, costs, moves, pop, C, (int32_t)inst->m, inst->n, (int32_t)inst->p,
+        reinterpret_cast<__nv_bfloat16 *>(x));
+    PM_CUDA(cudaGetLastError());
+    return PM_OK;
+}
+
+extern "C" pm_status pm_move_features(pm_instance *inst, const int64_t *gain, const int32_t *cap, const int64_t *loss,
+                                      const int32_t *assign, const int64_t *costs, const int32_t *moves, int64_t pop,
+                                      int64_t C, uint16_t *x, void *stream)
+{
+    if (!inst || pop < 0 || C < 0)
+        return PM_ERR_INVALID_ARG;
+    const void *ptrs[] = {gain, cap, loss, assign, costs, moves, x};
+    for (const void *p : ptrs)
+        if (!pm_is_device_ptr(p))
+            return PM_ERR_INVALID_ARG;
+    PM_CUDA(cudaSetDevice(inst->device));
+    return pm_launch_move_features(inst, gain, cap, loss, assign, costs, moves, pop, C, x,
+                                   static_cast<cudaStream_t>(stream));
+}
+
+pm_status pm_launch_candidates(const pm_instance *inst, const uint32_t *masks, int64_t pop, const int64_t *gain,
+                               const int32_t *cap, const int64_t *loss, const int32_t *assign, const int64_t *costs,
+                               int T, int32_t *moves, uint16_t *x, cudaStream_t s)
+{
+    if (pop <= 0)
+        return PM_OK;
+    const size_t smem = (size_t)pm_round_up(inst->p * 4, 16);
+    k_candidates<<<(unsigned)pop, 256, smem, s>>>(masks, (int32_t)inst->W, (int32_t)inst->m, (int32_t)inst->p, inst->n,
+                                                  reinterpret_cast<const unsigned long long *>(gain), cap,
+                                                  reinterpret_cast<const unsigned long long *>(loss), assign, costs, T,
+                                                  moves, reinterpret_cast<__nv_bfloat16 *>(x));
+    PM_CUDA(cudaGetLastError());
+    return PM_OK;
+}
+
+int pm_mlp_in_width() { return kIn; }
+
+// Kernel attributes of the learned path for this instance (call outside stream capture).
+pm_status pm_learn_prepare(const pm_instance *inst)
+{
+    const int cap = (int)(inst->smem_optin > 1024 ? inst->smem_optin - 1024 : inst->smem_optin);
+    PM_CUDA(cudaFuncSetAttribute(k_swap_stats, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+    PM_CUDA(cudaFuncSetAttribute(k_candidates, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+    return mlp_init_attrs();
+}
+
+extern "C" pm_status pm_log_moves(pm_instance *inst, const uint32_t *masks, const int64_t *costs, int64_t pop,
+                                  int64_t per, uint64_t seed, uint16_t *x, float *t, int32_t *moves, void *stream)
+{
+    if (!inst || pop < 1 || per < 1 || !masks || !costs || !x || !t || !moves)
+        return PM_ERR_INVALID_ARG;
+    const void *ptrs[] = {masks, costs, x, t, moves};
+    for (const void *ptr : ptrs)
+        if (!pm_is_device_ptr(ptr))
+            return PM_ERR_INVALID_ARG;
+    PM_CUDA(cudaSetDevice(inst->device));
+    PM_TRY(pm_learn_prepare(inst));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t Pm = (size_t)pop * inst->m, rows = (size_t)pop * per;
+    char *buf = nullptr;
+    const size_t bytes = Pm * 24 + rows * inst->W * 4 + rows * 8 + 1024;
+    PM_CUDA(cudaMallocAsync(reinterpret_cast<void **>(&buf), bytes, s));
+    int64_t *gain = reinterpret_cast<int64_t *>(buf);
+    int64_t *loss = gain + Pm;
+    int32_t *cap = reinterpret_cast<int32_t *>(loss + Pm);
+    int32_t *asg = cap + Pm;
+    uint32_t *swapped = reinterpret_cast<uint32_t *>(asg + Pm);
+    int64_t *after = reinterpret_cast<int64_t *>(swapped + rows * inst->W + (rows * inst->W & 1));
+    pm_status st = pm_launch_swap_stats(inst, masks, pop, gain, cap, loss, asg, s);
+    if (st == PM_OK) {
+        const size_t smem = (size_t)pm_round_up(inst->p * 4, 16);
+        cudaFuncSetAttribute(k_sample_moves, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_sample_moves<<<(unsigned)pop, 256, smem, s>>>(masks, (int32_t)inst->W, (int32_t)inst->m, (int32_t)inst->p,
+                                                        reinterpret_cast<const unsigned long long *>(gain), per, seed,
+                                                        moves);
+        st = cudaGetLastError() == cudaSuccess ? PM_OK : PM_ERR_CUDA;
+    }
+    if (st == PM_OK)
+        st = pm_launch_move_features(inst, gain, cap, loss, asg, costs, moves, pop, per, x, s);
+    if (st == PM_OK) {
+        const int64_t n = (int64_t)rows * inst->W;
+        k_apply_moves<<<(unsigned)pm_ceil_div(n, 256), 256, 0, s>>>(masks, (int32_t)inst->W, pop, per, moves, swapped);
+        st = cudaGetLastError() == cudaSuccess ? PM_OK : PM_ERR_CUDA;
+    }
+    if (st == PM_OK)
+        st = pm_eval_population(inst, swapped, (int64_t)rows, after, 0, stream);
+    if (st == PM_OK) {
+        k_targets<<<(unsigned)pm_ceil_div((int64_t)rows, 256), 256, 0, s>>>(costs, after, pop, per, (int32_t)inst->p, t);
+        st = cudaGetLastError() == cudaSuccess ? PM_OK : PM_ERR_CUDA;
+    }
+    cudaFreeAsync(buf, s);
+    return st;
+}

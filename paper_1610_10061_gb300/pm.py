@@ -38,7 +38,8 @@ class PMError(RuntimeError):
 
 class pm_ga_params(ctypes.Structure):
     _fields_ = [("deme", ctypes.c_int64), ("xover_rounds", ctypes.c_int32), ("mut_tries", ctypes.c_int32),
-                ("saturation", ctypes.c_int64), ("stream_id", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
+                ("saturation", ctypes.c_int64), ("stream_id", ctypes.c_uint32), ("flags", ctypes.c_uint32),
+                ("model", ctypes.c_void_p), ("candidates", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class pm_eval_shape(ctypes.Structure):
@@ -79,6 +80,17 @@ _SIGS = {
     "pm_batch_eval": ([_P, _P, _P, _P, _P], _S),
     "pm_batch_tune": ([_P, _P, _P, ctypes.POINTER(pm_eval_shape)], _S),
     "pm_batch_ga_create": ([_P, ctypes.c_uint64, _I64, ctypes.POINTER(pm_ga_params), _P, _PP], _S),
+    "pm_model_num_params": ([], ctypes.c_int64),
+    "pm_model_create": ([ctypes.c_int, ctypes.c_uint64, _PP], _S),
+    "pm_model_destroy": ([_P], _S),
+    "pm_model_set_params": ([_P, _P, _P], _S),
+    "pm_model_get_params": ([_P, _P, _P], _S),
+    "pm_model_forward": ([_P, _P, _I64, _P, _P], _S),
+    "pm_model_grad": ([_P, _P, _P, _I64, _P, _P, _P], _S),
+    "pm_model_train_step": ([_P, _P, _P, _I64, ctypes.c_float, _P, _P], _S),
+    "pm_swap_stats": ([_P, _P, _I64, _P, _P, _P, _P, _P], _S),
+    "pm_move_features": ([_P, _P, _P, _P, _P, _P, _P, _I64, _I64, _P, _P], _S),
+    "pm_log_moves": ([_P, _P, _P, _I64, _I64, ctypes.c_uint64, _P, _P, _P, _P], _S),
     "pm_ga_run": ([_P, ctypes.c_uint64, _I64, _I64, ctypes.POINTER(pm_ga_params), _P, _P, _P, _P, _P, _P], _S),
 }
 for _name, (_args, _res) in _SIGS.items():
@@ -170,8 +182,123 @@ def pm_tune_eval(inst, pop: int, stream=None):
                 candidates=out.candidates)
 
 
-def _params(deme=0, xover_rounds=-1, mut_tries=-1, saturation=0, stream_id=0, tune=False):
-    return pm_ga_params(deme, xover_rounds, mut_tries, saturation, stream_id, PM_GA_TUNE if tune else 0)
+def _params(deme=0, xover_rounds=-1, mut_tries=-1, saturation=0, stream_id=0, tune=False, model=None,
+            candidates=0):
+    mh = model.handle if isinstance(model, Model) else model
+    return pm_ga_params(deme, xover_rounds, mut_tries, saturation, stream_id, PM_GA_TUNE if tune else 0,
+                        mh if mh is not None else None, candidates, 0)
+
+
+# ----- learned swap proposal -----
+
+def pm_model_num_params() -> int:
+    return int(_lib.pm_model_num_params())
+
+
+def pm_model_create(device: int = 0, seed: int = 0):
+    out = ctypes.c_void_p()
+    _check(_lib.pm_model_create(device, seed, ctypes.byref(out)), "pm_model_create")
+    return out
+
+
+def pm_model_destroy(md):
+    _check(_lib.pm_model_destroy(md), "pm_model_destroy")
+
+
+def pm_model_set_params(md, params, stream=None):
+    _check(_lib.pm_model_set_params(md, _addr(params), _stream(stream)), "pm_model_set_params")
+
+
+def pm_model_get_params(md, params, stream=None):
+    _check(_lib.pm_model_get_params(md, _addr(params), _stream(stream)), "pm_model_get_params")
+
+
+def pm_model_forward(md, x, rows: int, y, stream=None):
+    _check(_lib.pm_model_forward(md, _addr(x), rows, _addr(y), _stream(stream)), "pm_model_forward")
+
+
+def pm_model_grad(md, x, t, rows: int, grads=None, stream=None) -> float:
+    loss = ctypes.c_float()
+    _check(_lib.pm_model_grad(md, _addr(x), _addr(t), rows, _addr(grads), ctypes.byref(loss), _stream(stream)),
+           "pm_model_grad")
+    return loss.value
+
+
+def pm_model_train_step(md, x, t, rows: int, lr: float, want_loss: bool = False, stream=None):
+    loss = ctypes.c_float()
+    _check(_lib.pm_model_train_step(md, _addr(x), _addr(t), rows, lr, ctypes.byref(loss) if want_loss else None,
+                                    _stream(stream)), "pm_model_train_step")
+    return loss.value if want_loss else None
+
+
+def pm_swap_stats(inst, masks, pop: int, gain, cap, loss, assign, stream=None):
+    _check(_lib.pm_swap_stats(inst, _addr(masks), pop, _addr(gain), _addr(cap), _addr(loss), _addr(assign),
+                              _stream(stream)), "pm_swap_stats")
+
+
+def pm_move_features(inst, gain, cap, loss, assign, costs, moves, pop: int, C: int, x, stream=None):
+    _check(_lib.pm_move_features(inst, _addr(gain), _addr(cap), _addr(loss), _addr(assign), _addr(costs),
+                                 _addr(moves), pop, C, _addr(x), _stream(stream)), "pm_move_features")
+
+
+def pm_log_moves(inst, masks, costs, pop: int, per: int, seed: int, x, t, moves, stream=None):
+    _check(_lib.pm_log_moves(inst, _addr(masks), _addr(costs), pop, per, seed, _addr(x), _addr(t), _addr(moves),
+                             _stream(stream)), "pm_log_moves")
+
+
+class Model:
+    """The swap-scoring perceptron (16 -> 128 -> 128 -> 1) on the device."""
+
+    def __init__(self, device: int = 0, seed: int = 0):
+        self.handle = pm_model_create(device, seed)
+        self.n_params = pm_model_num_params()
+
+    def params(self):
+        out = np.zeros(self.n_params, dtype=np.float32)
+        pm_model_get_params(self.handle, out)
+        return out
+
+    def set_params(self, params):
+        pm_model_set_params(self.handle, np.ascontiguousarray(params, dtype=np.float32))
+
+    def forward(self, x, stream=None):
+        import torch
+        y = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
+        pm_model_forward(self.handle, x, x.shape[0], y, stream)
+        return y
+
+    def grad(self, x, t):
+        g = np.zeros(self.n_params, dtype=np.float32)
+        loss = pm_model_grad(self.handle, x, t, x.shape[0], g)
+        return loss, g
+
+    def train(self, x, t, epochs: int = 3, batch: int = 4096, lr: float = 1e-3, seed: int = 0, stream=None):
+        """Adam on (x, t) (device tensors) in shuffled mini-batches; returns the mean loss per epoch."""
+        import torch
+        rows = x.shape[0]
+        gen = torch.Generator(device="cpu").manual_seed(seed)
+        losses = []
+        for _ in range(epochs):
+            perm = torch.randperm(rows, generator=gen).to(x.device)
+            xs, ts = x[perm].contiguous(), t[perm].contiguous()
+            tot, nb = 0.0, 0
+            for b0 in range(0, rows, batch):
+                nrow = min(batch, rows - b0)
+                tot += pm_model_train_step(self.handle, xs[b0:b0 + nrow], ts[b0:b0 + nrow], nrow, lr, True, stream)
+                nb += 1
+            losses.append(tot / max(nb, 1))
+        return losses
+
+    def close(self):
+        if self.handle:
+            pm_model_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def pm_ga_create(inst, seed: int, pop: int, params: pm_ga_params | None = None, stream=None):
@@ -329,12 +456,14 @@ class GA:
     """The device-resident genetic algorithm on an Instance."""
 
     def __init__(self, inst: Instance, seed: int, pop: int, deme: int = 0, xover_rounds: int = -1,
-                 mut_tries: int = -1, saturation: int = 0, stream_id: int = 0, tune: bool = False, stream=None,
-                 _handle=None):
+                 mut_tries: int = -1, saturation: int = 0, stream_id: int = 0, tune: bool = False, model=None,
+                 candidates: int = 0, stream=None, _handle=None):
         self.inst = inst
         self.pop = int(pop)
+        self.model = model
         self.handle = _handle if _handle is not None else pm_ga_create(
-            inst.handle, seed, pop, _params(deme, xover_rounds, mut_tries, saturation, stream_id, tune), stream)
+            inst.handle, seed, pop,
+            _params(deme, xover_rounds, mut_tries, saturation, stream_id, tune, model, candidates), stream)
 
     def step(self, gens: int, stream=None):
         trace = np.zeros(max(int(gens), 1), dtype=np.int64)

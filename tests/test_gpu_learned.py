@@ -1,0 +1,255 @@
+"""The learned swap proposal on the GPU against its oracle.
+
+Swap statistics are integers (bit-exact).  Features, the perceptron's
+predictions and gradients are compared within the tolerance of BF16 operands
+with FP32 accumulation (relative 2e-2, absolute 1e-3 of the tensor's scale);
+Adam, applied to the GPU's own gradients, within FP32 rounding.  The learned
+GA is checked for exactness (every reported cost equals the direct evaluator
+of its bitset) and for what the trained model gains.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp
+from paper_1610_10061_gb300.inputs import (euclid_instance, gmm_instance, graph_instance, masks_from_sets,
+                                           random_masks, sets_from_masks)
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def pm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1610_10061_gb300 import build
+
+    build.build()
+    from paper_1610_10061_gb300 import pm as _pm
+
+    torch.cuda.set_device(0)
+    return _pm
+
+
+def dev32(a):
+    return torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).cuda()
+
+
+def _stats_gpu(pm, inst, masks):
+    P, m = masks.shape[0], inst.m
+    dm = dev32(masks)
+    g = torch.zeros((P, m), dtype=torch.int64, device="cuda")
+    c = torch.zeros((P, m), dtype=torch.int32, device="cuda")
+    lo = torch.zeros((P, m), dtype=torch.int64, device="cuda")
+    a = torch.zeros((P, m), dtype=torch.int32, device="cuda")
+    pm.pm_swap_stats(inst.handle, dm, P, g, c, lo, a)
+    torch.cuda.synchronize()
+    return g, c, lo, a
+
+
+@pytest.mark.parametrize("case", ["graph", "euclid", "ties", "gmm", "wide"])
+def test_swap_stats_bit_exact(pm, case):
+    rng = np.random.default_rng(1)
+    if case == "graph":
+        d, p = graph_instance(100, 200, seed=0), 5
+    elif case == "euclid":
+        d, p = euclid_instance(300, seed=1), 30
+    elif case == "ties":
+        d, p = rng.integers(0, 4, size=(60, 90)).astype(np.int32), 7
+    elif case == "gmm":
+        d, p = gmm_instance(400, seed=2), 40
+    else:  # m large enough for the global-memory accumulators
+        d, p = rng.integers(0, 3000, size=(40, 10000)).astype(np.int32), 60
+    inst = pm.Instance(d, p)
+    masks = random_masks(37, d.shape[1], p, seed=3)
+    got = [x.cpu().numpy() for x in _stats_gpu(pm, inst, masks)]
+    pi, de = oracle.tables(d, p)
+    want = oracle.swap_stats(pi, de, d.shape[1], masks)
+    for gx, wx in zip(got, want):
+        np.testing.assert_array_equal(gx, wx)
+
+
+def _bf16_close(got, ref):
+    tol = np.abs(ref) / 128 + 1e-6
+    assert (np.abs(got - ref) <= tol).all(), np.max(np.abs(got - ref) - tol)
+
+
+def test_move_features_match_oracle(pm):
+    d, p = gmm_instance(300, seed=5), 20
+    inst = pm.Instance(d, p)
+    P, C = 16, 9
+    masks = random_masks(P, 300, p, seed=6)
+    costs = oracle.eval_direct(d, masks)
+    rng = np.random.default_rng(0)
+    moves = np.zeros((P, C, 2), dtype=np.int32)
+    sets = sets_from_masks(masks, 300)
+    for t in range(P):
+        closed = [k for k in range(300) if k not in sets[t]]
+        for c in range(C):
+            moves[t, c] = (rng.choice(sets[t]), rng.choice(closed))
+    g, ca, lo, a = _stats_gpu(pm, inst, masks)
+    x = torch.zeros((P * C, 16), dtype=torch.bfloat16, device="cuda")
+    pm.pm_move_features(inst.handle, g, ca, lo, a, torch.from_numpy(costs).cuda(), torch.from_numpy(moves).cuda(),
+                        P, C, x)
+    got = x.float().cpu().numpy()
+    pi, de = oracle.tables(d, p)
+    G, CA, LO, A = oracle.swap_stats(pi, de, 300, masks)
+    for t in range(P):
+        for c in range(C):
+            j, k = moves[t, c]
+            ref = mlp.move_features(G[t], CA[t], LO[t], A[t], costs[t], 300, 300, p, j, k)
+            _bf16_close(got[t * C + c, :8], ref)
+            assert (got[t * C + c, 8:] == 0).all()
+
+
+def _random_batch(rows, seed):
+    rng = np.random.default_rng(seed)
+    X = np.zeros((rows, 16))
+    X[:, :8] = rng.normal(0, 1, size=(rows, 8))
+    X = mlp.bf16_round(X)
+    t = rng.normal(0, 1, size=rows)
+    return X, t
+
+
+def _scale_close(got, ref, rtol=2e-2, atol=1e-3):
+    scale = max(1.0, float(np.max(np.abs(ref))))
+    np.testing.assert_allclose(got, ref, rtol=rtol, atol=atol * scale)
+
+
+@pytest.mark.parametrize("rows", [64, 1000, 4096])
+def test_mlp_forward_and_gradients(pm, rows):
+    model = pm.Model(seed=1)
+    params = mlp.init_params(seed=rows)
+    for k in ("b1", "b2", "b3"):
+        params[k] = np.random.default_rng(rows).normal(0, 0.1, size=params[k].shape)
+    model.set_params(mlp.flatten(params).astype(np.float32))
+    p32 = mlp.unflatten(model.params().astype(np.float64))  # the float32 masters the GPU holds
+    X, t = _random_batch(rows, rows)
+    xd = torch.from_numpy(X.astype(np.float32)).to(torch.bfloat16).cuda()
+    td = torch.from_numpy(t.astype(np.float32)).cuda()
+    y = model.forward(xd).cpu().numpy()
+    yref, _ = mlp.forward(p32, X, bf16=True)
+    _scale_close(y, yref)
+    loss, g = model.grad(xd, td)
+    lref, gref = mlp.loss_and_grads(p32, X, t, bf16=True)
+    assert loss == pytest.approx(lref, rel=2e-2)
+    G = mlp.unflatten(g.astype(np.float64))
+    for name in ("W1", "b1", "W2", "b2", "w3", "b3"):
+        _scale_close(G[name], gref[name])
+
+
+def test_adam_step_matches_oracle(pm):
+    model = pm.Model(seed=2)
+    X, t = _random_batch(512, 9)
+    xd = torch.from_numpy(X.astype(np.float32)).to(torch.bfloat16).cuda()
+    td = torch.from_numpy(t.astype(np.float32)).cuda()
+    p = mlp.unflatten(model.params().astype(np.float64))
+    state = mlp.adam_init(p)
+    for step in range(3):
+        _, g = model.grad(xd, td)
+        pm.pm_model_train_step(model.handle, xd, td, 512, 1e-3)
+        p = mlp.adam_step(p, mlp.unflatten(g.astype(np.float64)), state, lr=1e-3)
+        got = mlp.unflatten(model.params().astype(np.float64))
+        for name in p:
+            np.testing.assert_allclose(got[name], p[name], rtol=1e-5, atol=1e-7)
+
+
+def _log(pm, inst, masks, costs, per, seed):
+    P = masks.shape[0]
+    x = torch.zeros((P * per, 16), dtype=torch.bfloat16, device="cuda")
+    tt = torch.zeros(P * per, dtype=torch.float32, device="cuda")
+    mv = torch.zeros((P * per, 2), dtype=torch.int32, device="cuda")
+    pm.pm_log_moves(inst.handle, dev32(masks), torch.from_numpy(costs).cuda(), P, per, seed, x, tt, mv)
+    torch.cuda.synchronize()
+    return x, tt, mv
+
+
+def test_log_moves_targets_are_exact(pm):
+    d, p = euclid_instance(200, seed=4), 12
+    inst = pm.Instance(d, p)
+    masks = random_masks(20, 200, p, seed=8)
+    costs = oracle.eval_direct(d, masks)
+    x, tt, mv = _log(pm, inst, masks, costs, 16, seed=3)
+    mv = mv.cpu().numpy().reshape(20, 16, 2)
+    tt = tt.cpu().numpy().reshape(20, 16)
+    sets = sets_from_masks(masks, 200)
+    pi, de = oracle.tables(d, p)
+    G, CA, LO, A = oracle.swap_stats(pi, de, 200, masks)
+    top_share = 0
+    for t in range(20):
+        top4 = [k for k in np.argsort(-G[t], kind="stable") if k not in sets[t]][:4]
+        for q in range(16):
+            j, k = mv[t, q]
+            assert j in sets[t] and k not in sets[t]
+            top_share += k in top4
+            after = oracle.eval_direct(d, masks_from_sets([sorted([s for s in sets[t] if s != j] + [k])], 200))[0]
+            assert tt[t, q] == pytest.approx(mlp.move_target(costs[t], after, p), rel=1e-6, abs=1e-6)
+    assert top_share >= 0.6 * 20 * 16
+
+
+def _train_model(pm, d, p, seed=0, gens=6, per=64, epochs=8):
+    """Log tuples from plain-GA populations and train a model on them (all on the GPU)."""
+    inst = pm.Instance(d, p)
+    ga = pm.GA(inst, seed=seed + 100, pop=256, deme=64)
+    xs, ts = [], []
+    for g in range(gens):
+        ga.step(1)
+        masks, costs = ga.population()
+        x, tt, _ = _log(pm, inst, masks, costs, per, seed=seed * 1000 + g)
+        xs.append(x)
+        ts.append(tt)
+    X = torch.cat(xs)
+    T = torch.cat(ts)
+    model = pm.Model(seed=seed)
+    losses = model.train(X, T, epochs=epochs, batch=2048, lr=2e-3, seed=seed)
+    return inst, model, losses
+
+
+def _spearman(a, b):
+    ra = np.argsort(np.argsort(a))
+    rb = np.argsort(np.argsort(b))
+    return float(np.corrcoef(ra, rb)[0, 1])
+
+
+def test_training_lowers_the_loss_and_ranks_moves(pm):
+    d, p = gmm_instance(500, seed=7), 25
+    inst, model, losses = _train_model(pm, d, p)
+    assert losses[-1] < 0.5 * losses[0]
+    # held-out tuples from another population: the trained model ranks moves far better than an untrained one
+    masks = random_masks(128, 500, p, seed=99)
+    costs = oracle.eval_direct(d, masks)
+    x, tt, _ = _log(pm, inst, masks, costs, 32, seed=12345)
+    truth = tt.cpu().numpy()
+    yt = model.forward(x).cpu().numpy()
+    yu = pm.Model(seed=123).forward(x).cpu().numpy()
+    mse_t, mse_u = float(np.mean((yt - truth) ** 2)), float(np.mean((yu - truth) ** 2))
+    assert mse_t < 0.25 * mse_u, (mse_t, mse_u)
+    assert _spearman(yt, truth) > 0.95
+    # top-1 regret per individual: true change of the chosen move minus the best true change among its 32 moves
+    def regret(y):
+        yy, tt_ = y.reshape(128, 32), truth.reshape(128, 32)
+        return float(np.mean(tt_[np.arange(128), np.argmin(yy, axis=1)] - tt_.min(axis=1)))
+    assert regret(yt) <= regret(yu), (regret(yt), regret(yu))
+
+
+def test_learned_ga_is_exact_and_gains(pm):
+    d, p = gmm_instance(500, seed=7), 25
+    inst, model, _ = _train_model(pm, d, p, seed=1)
+    G = 8
+    plain = pm.GA(inst, seed=5, pop=256, deme=64)
+    tp = plain.step(G)
+    learned = pm.GA(inst, seed=5, pop=256, deme=64, model=model)
+    tl = learned.step(G)
+    masks, costs = learned.population()
+    np.testing.assert_array_equal(costs, oracle.eval_direct(d, masks))
+    assert all(len(s) == p for s in sets_from_masks(masks, 500))
+    bc, gr, ev, best = learned.result()
+    assert bc == oracle.eval_direct(d, best[None])[0] and gr == G
+    assert (np.diff(tl) <= 0).all()
+    # what the trained proposal gains: a better best after the same generations, reached earlier
+    assert tl[-1] < tp[-1]
+    first = int(np.argmax(tl <= tp[-1]))
+    assert tl[first] <= tp[-1] and first < G - 1

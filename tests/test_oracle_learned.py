@@ -1,0 +1,117 @@
+"""Pins for the oracle of the learned swap proposal (no GPU).
+
+Swap statistics are tied to exact identities of the p-median objective
+(opening one facility alone changes the cost by -gain, closing one alone by
++loss), to brute-force counts and to the direct evaluator; bf16 rounding to
+torch's conversion (a library routine); the perceptron's gradients to finite
+differences; Adam to a two-step example worked by hand from Kingma & Ba's
+Algorithm 1.
+"""
+
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp
+from paper_1610_10061_gb300.inputs import euclid_instance, graph_instance, masks_from_sets, random_masks, sets_from_masks
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_swap_stats_identities(seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(3, 30))
+    m = int(rng.integers(4, 40))
+    p = int(rng.integers(2, m))
+    d = rng.integers(0, [4, 50, 1000][seed % 3], size=(n, m)).astype(np.int32)
+    pif, def_ = oracle.tables(d, full=True)
+    masks = random_masks(12, m, p, seed=seed)
+    gain, cap, loss, assign = oracle.swap_stats(pif, def_, m, masks)
+    base = oracle.eval_direct(d, masks)
+    for t, s in enumerate(sets_from_masks(masks, m)):
+        closed = [k for k in range(m) if k not in s]
+        opened = masks_from_sets([sorted(s + [k]) for k in closed], m)
+        np.testing.assert_array_equal(oracle.eval_direct(d, opened), base[t] - gain[t, closed])
+        shut = masks_from_sets([[x for x in s if x != j] for j in s], m)
+        np.testing.assert_array_equal(oracle.eval_direct(d, shut), base[t] + loss[t, s])
+        assert assign[t].sum() == n and (assign[t, closed] == 0).all() and (loss[t, closed] == 0).all()
+        assert (gain[t, s] == 0).all() and (cap[t, s] == 0).all()
+        # cap[k] = number of clients that rank k ahead of their nearest open facility
+        order = np.argsort(d, axis=1, kind="stable")
+        rank = np.argsort(order, axis=1)
+        r1 = np.array([min(rank[i, x] for x in s) for i in range(n)])
+        for k in closed:
+            assert cap[t, k] == int((rank[:, k] < r1).sum())
+
+
+def test_swap_stats_truncated_tables_agree():
+    d = graph_instance(70, 200, seed=9)
+    for p in (3, 12):
+        pi, de = oracle.tables(d, p)
+        pif, def_ = oracle.tables(d, full=True)
+        masks = random_masks(40, 70, p, seed=p)
+        a = oracle.swap_stats(pi, de, 70, masks)
+        b = oracle.swap_stats(pif, def_, 70, masks)
+        for x, y in zip(a, b):
+            np.testing.assert_array_equal(x, y)
+
+
+def test_bf16_rounding_matches_torch():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(0)
+    x = np.concatenate([rng.normal(0, 10, 5000), rng.normal(0, 1e-3, 1000), [0.0, 1.0, -1.0, 1 + 2**-8, 1 + 3 * 2**-9,
+                                                                            65504.0, 1e-30]])
+    ref = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(mlp.bf16_round(x), ref)
+    assert mlp.bf16_round(1 + 2**-8) == 1.0               # tie -> even
+    assert mlp.bf16_round(1 + 3 * 2**-9) == 1 + 2**-7
+
+
+def test_backward_matches_finite_differences():
+    rng = np.random.default_rng(1)
+    params = mlp.init_params(3)
+    X = np.zeros((20, mlp.F_PAD))
+    X[:, :mlp.F_IN] = rng.normal(size=(20, mlp.F_IN))
+    t = rng.normal(size=20)
+    _, g = mlp.loss_and_grads(params, X, t)
+    eps = 1e-6
+    for name in params:
+        flat = params[name].reshape(-1)
+        for idx in rng.choice(flat.size, size=min(6, flat.size), replace=False):
+            old = flat[idx]
+            flat[idx] = old + eps
+            lp, _ = mlp.loss_and_grads(params, X, t)
+            flat[idx] = old - eps
+            lm, _ = mlp.loss_and_grads(params, X, t)
+            flat[idx] = old
+            num = (lp - lm) / (2 * eps)
+            assert abs(num - g[name].reshape(-1)[idx]) <= 1e-6 * max(1.0, abs(num)), (name, idx)
+
+
+def test_adam_two_steps_by_hand():
+    params = {"w": np.array([1.0])}
+    state = mlp.adam_init(params)
+    mlp.adam_step(params, {"w": np.array([0.5])}, state, lr=0.1)
+    assert params["w"][0] == pytest.approx(0.900000002, abs=1e-15)
+    mlp.adam_step(params, {"w": np.array([-0.25])}, state, lr=0.1)
+    assert params["w"][0] == pytest.approx(0.8733662987078463, abs=1e-15)
+
+
+def test_move_features_and_target():
+    d = euclid_instance(50, seed=2)
+    p = 5
+    pif, def_ = oracle.tables(d, full=True)
+    masks = random_masks(3, 50, p, seed=4)
+    gain, cap, loss, assign = oracle.swap_stats(pif, def_, 50, masks)
+    cost = oracle.eval_direct(d, masks)
+    s = sets_from_masks(masks[:1], 50)[0]
+    j, k = s[0], next(x for x in range(50) if x not in s)
+    f = mlp.move_features(gain[0], cap[0], loss[0], assign[0], cost[0], 50, 50, p, j, k)
+    Z = cost[0] / p
+    assert f.shape == (8,) and f[0] == pytest.approx(loss[0, j] / Z) and f[1] == pytest.approx(gain[0, k] / Z)
+    after = oracle.eval_direct(d, masks_from_sets([sorted([x for x in s if x != j] + [k])], 50))[0]
+    assert mlp.move_target(cost[0], after, p) == pytest.approx((after - cost[0]) / Z)
+    # first-order estimate loss - gain bounds the exact change from above (closing j can only lose less
+    # once k is open, opening k can only gain more once j is closed... or equal)
+    assert after - cost[0] <= loss[0, j] - 0 and after - cost[0] >= -gain[0, k]
