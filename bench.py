@@ -474,10 +474,114 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def run_learned(args):
+    """Time-to-target of the GA with the learned swap proposal against the plain GA (same GB300).
+
+    Workload gmm5000_p{50,500}: clustered Euclidean n = m = 5000 (50 Gaussian components, sigma 0.02), pop 1024
+    in demes of 256.  The model is trained on tuples (individual, move, exact cost change) logged from plain-GA
+    populations of a separate run (seed 1000).  Target = the best cost the plain GA (seed 0) reaches in
+    `--steps` generations; each arm's time-to-target is the summed CUDA-event time of its generations up to the
+    first one whose best cost is at or below the target (seeds 0..4, medians; training time reported apart).
+    """
+    import numpy as np
+    import torch
+
+    from paper_1610_10061_gb300 import build
+    from paper_1610_10061_gb300.inputs import paper_shape_instance
+
+    build.build()
+    from paper_1610_10061_gb300 import pm
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    name = args.workload.split("learned_", 1)[1]
+    w = paper_shape_instance(name)
+    d, p, pop = w["d"], w["p"], w["pop"]
+    n, m = d.shape
+    inst = pm.Instance(d, p, stream=stream.cuda_stream)
+    inst.tune(pop, stream=stream.cuda_stream)
+    budget = args.steps
+
+    # ---- log ~1M training tuples from plain-GA populations (a separate run) and train ----
+    t0 = time.perf_counter()
+    per = 64
+    log_gens = max(1, (1 << 20) // (pop * per))
+    ga = pm.GA(inst, seed=1000, pop=pop, deme=256, stream=stream.cuda_stream)
+    xs, ts = [], []
+    costs_dev = torch.empty(pop, dtype=torch.int64, device="cuda")
+    masks_dev = torch.empty((pop, inst.W), dtype=torch.int32, device="cuda")
+    for g in range(log_gens):
+        pm.pm_ga_step(ga.handle, 1, None, stream.cuda_stream)
+        pm.pm_ga_population(ga.handle, masks_dev, costs_dev, stream.cuda_stream)
+        x = torch.empty((pop * per, 16), dtype=torch.bfloat16, device="cuda")
+        tt = torch.empty(pop * per, dtype=torch.float32, device="cuda")
+        mv = torch.empty((pop * per, 2), dtype=torch.int32, device="cuda")
+        pm.pm_log_moves(inst.handle, masks_dev, costs_dev, pop, per, 77 + g, x, tt, mv, stream.cuda_stream)
+        xs.append(x)
+        ts.append(tt)
+    X, T = torch.cat(xs), torch.cat(ts)
+    torch.cuda.synchronize()
+    log_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    model = pm.Model(seed=0)
+    losses = model.train(X, T, epochs=6, batch=4096, lr=2e-3, seed=0, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+
+    def run(seed, use_model, gens):
+        g = pm.GA(inst, seed=seed, pop=pop, deme=256, model=model if use_model else None,
+                  stream=stream.cuda_stream)
+        ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(gens)]
+        ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(gens)]
+        tr = torch.empty(gens, dtype=torch.int64, device="cuda")
+        for k in range(gens):
+            ev_s[k].record(stream)
+            pm.pm_ga_step(g.handle, 1, tr[k:k + 1], stream.cuda_stream)
+            ev_e[k].record(stream)
+        torch.cuda.synchronize()
+        ms = np.array([a.elapsed_time(b) for a, b in zip(ev_s, ev_e)])
+        _, _, evals = pm.pm_ga_result(g.handle, None, stream.cuda_stream)
+        g.close()
+        return tr.cpu().numpy(), np.cumsum(ms) / 1000.0, evals
+
+    ptrace0, _, _ = run(0, False, budget)
+    target = int(ptrace0[-1])
+    res = {"plain": [], "learned": []}
+    for seed in range(5):
+        for arm in ("plain", "learned"):
+            tr, cum, evals = run(seed, arm == "learned", budget)
+            hit = np.nonzero(tr <= target)[0]
+            res[arm].append({"seed": seed, "time_s": float(cum[hit[0]]) if hit.size else None,
+                             "gens": int(hit[0] + 1) if hit.size else None, "final": int(tr[-1]),
+                             "ms_per_gen": float(cum[-1] / budget * 1000.0), "evals": int(evals)})
+
+    def med(arm, key):
+        vals = [r[key] for r in res[arm] if r[key] is not None]
+        return float(np.median(vals)) if len(vals) == len(res[arm]) else None
+
+    lt, pt = med("learned", "time_s"), med("plain", "time_s")
+    line = {"metric": "time-to-target cost, learned vs plain GA", "value": lt, "unit": "s",
+            "higher_is_better": False, "n_gpus": 1, "steps": budget, "warmup": 0, "vs_baseline": None,
+            "dtype": "int64 (costs); bf16/fp32 (model)", "data": "synthetic",
+            "config": {"workload": f"{name}: clustered Euclidean n=m={n}, 50 components sigma 0.02, p={p}, "
+                                   f"pop {pop} in demes of 256; target = plain GA (seed 0) best after {budget} "
+                                   "generations; seeds 0-4, medians",
+                       "target": target, "train_tuples": int(X.shape[0]), "train_epochs": 6,
+                       "train_loss_first_last": [losses[0], losses[-1]], "log_s": log_s, "train_s": train_s},
+            "plain_time_s": pt, "learned_time_s": lt,
+            "speedup": (pt / lt) if (pt and lt) else None,
+            "plain_gens": med("plain", "gens"), "learned_gens": med("learned", "gens"),
+            "plain_ms_per_gen": med("plain", "ms_per_gen"), "learned_ms_per_gen": med("learned", "ms_per_gen"),
+            "runs": res}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload.startswith("learned_"):
+        run_learned(args)
     elif args.workload.startswith("batched"):
         run_batched(args)
     elif args.mode == "eval":
