@@ -159,6 +159,19 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def combine_ranks(evals, ms, device="cpu"):
+    """Whole-job totals across ranks: evaluations summed, time the maximum over ranks."""
+    import torch
+    import torch.distributed as dist
+
+    ev_t = torch.tensor([float(evals)], dtype=torch.float64, device=device)
+    ms_t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(ev_t, op=dist.ReduceOp.SUM)
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    return float(ev_t.item()), float(ms_t.item())
+
+
 def cpu_baseline(d, p, pop, deme, budget_s=12.0):
     """The oracle GA (single-threaded C, as it stands) on a bounded number of generations of the same workload."""
     import numpy as np
@@ -270,14 +283,7 @@ def run_ours(args):
     best, g1, e1 = pm.pm_ga_result(ga.handle, None, stream.cuda_stream)
     evals = e1 - e0
     assert g1 - g0 == args.steps
-    tot_evals, max_ms = evals, total_ms
-    if world > 1:
-        t = torch.tensor([float(evals), total_ms], dtype=torch.float64, device="cuda")
-        ev_t = t[:1].clone()
-        ms_t = t[1:].clone()
-        torch.distributed.all_reduce(ev_t, op=torch.distributed.ReduceOp.SUM)
-        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
-        tot_evals, max_ms = float(ev_t.item()), float(ms_t.item())
+    tot_evals, max_ms = combine_ranks(evals, total_ms, device="cuda")
     value = tot_evals / (max_ms / 1000.0)
 
     # ---- roofline of the dominant kernel: the fitness evaluation at the same shape, timed alone ----
