@@ -182,6 +182,15 @@ typedef struct pm_eval_shape {
 
 PM_API pm_status pm_tune_eval(pm_instance *inst, int64_t pop, void *stream, pm_eval_shape *chosen);
 
+/*
+ * pm_selftest_bounded_wait -- failure-detection self-test (no counterpart in
+ * the paper).  Launches one CTA that waits on an mbarrier nothing will
+ * complete, with the bounded-poll exit every wait in this library uses; the
+ * call returns the status the kernel recorded, PM_ERR_TIMEOUT when the bound
+ * works, and leaves the context usable.  Synchronises `stream`.
+ */
+PM_API pm_status pm_selftest_bounded_wait(int device, void *stream);
+
 /* ------------------------------------------------------------------------
  * The genetic algorithm (Sections 3.1, 3.2.2, 4.3-4.5) on the device.
  * ------------------------------------------------------------------------ */

@@ -541,6 +541,27 @@ __global__ void k_mask_check(const uint32_t *__restrict__ masks, int64_t pop, in
         atomicAdd(flag, 1);
 }
 
+// Self-test of the bounded wait: an mbarrier that nothing arrives on (a flag
+// nothing sets).  The wait gives up after `limit` polls, records
+// PM_ERR_TIMEOUT and returns -- the same exit the scan kernel takes.
+__global__ void k_wait_selftest(int *__restrict__ err, uint32_t limit)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    uint32_t spins = 0;
+    while (!mbar_try_wait(&bar, 0)) {
+        if (++spins > limit) {
+            if (threadIdx.x == 0)
+                atomicExch(err, (int)PM_ERR_TIMEOUT);
+            return;
+        }
+    }
+}
+
 template <int G>
 const void *scan_fn()
 {
@@ -822,4 +843,27 @@ extern "C" pm_status pm_eval_population_noalloc(pm_instance *inst, const uint32_
     PM_CUDA(cudaMemsetAsync(partials, 0, part, s));
     pm_accept_args acc;
     return pm_launch_eval(inst, plan, masks, pop, nullptr, costs, partials, tickets, colT, err, acc, s);
+}
+
+extern "C" pm_status pm_selftest_bounded_wait(int device, void *stream)
+{
+    if (device < 0)
+        return PM_ERR_INVALID_ARG;
+    PM_CUDA(cudaSetDevice(device));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int *err = nullptr;
+    PM_CUDA(cudaMallocAsync(reinterpret_cast<void **>(&err), sizeof(int), s));
+    cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), s);
+    if (e == cudaSuccess) {
+        k_wait_selftest<<<1, 32, 0, s>>>(err, 1u << 14);
+        e = cudaGetLastError();
+    }
+    int h = 0;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(err, s);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s);
+    PM_CUDA(e);
+    return (pm_status)h;
 }

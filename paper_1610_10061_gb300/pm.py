@@ -64,6 +64,7 @@ _SIGS = {
     "pm_instance_tables": ([_P, _P, _P, _P], _S),
     "pm_eval_population": ([_P, _P, _I64, _P, ctypes.c_int, _P], _S),
     "pm_eval_population_noalloc": ([_P, _P, _I64, _P, _P], _S),
+    "pm_selftest_bounded_wait": ([ctypes.c_int, _P], _S),
     "pm_tune_eval": ([_P, _I64, _P, ctypes.POINTER(pm_eval_shape)], _S),
     "pm_ga_create": ([_P, ctypes.c_uint64, _I64, ctypes.POINTER(pm_ga_params), _P, _PP], _S),
     "pm_ga_step": ([_P, _I64, _P, _P], _S),
@@ -175,6 +176,11 @@ def pm_eval_population_noalloc(inst, masks, pop: int, costs, stream=None):
            "pm_eval_population_noalloc")
 
 
+def pm_selftest_bounded_wait(device: int = 0, stream=None) -> int:
+    """Status recorded by a kernel whose wait can never complete (PM_ERR_TIMEOUT = 7 when the bound works)."""
+    return int(_lib.pm_selftest_bounded_wait(device, _stream(stream)))
+
+
 def pm_tune_eval(inst, pop: int, stream=None):
     out = pm_eval_shape()
     _check(_lib.pm_tune_eval(inst, pop, _stream(stream), ctypes.byref(out)), "pm_tune_eval")
@@ -273,7 +279,7 @@ class Model:
         return loss, g
 
     def train(self, x, t, epochs: int = 3, batch: int = 4096, lr: float = 1e-3, seed: int = 0, stream=None):
-        """Adam on (x, t) (device tensors) in shuffled mini-batches; returns the mean loss per epoch."""
+        """Adam on (x, t) (device tensors) in shuffled mini-batches; returns each epoch's last batch loss."""
         import torch
         rows = x.shape[0]
         gen = torch.Generator(device="cpu").manual_seed(seed)
@@ -281,12 +287,12 @@ class Model:
         for _ in range(epochs):
             perm = torch.randperm(rows, generator=gen).to(x.device)
             xs, ts = x[perm].contiguous(), t[perm].contiguous()
-            tot, nb = 0.0, 0
+            last = None
             for b0 in range(0, rows, batch):
                 nrow = min(batch, rows - b0)
-                tot += pm_model_train_step(self.handle, xs[b0:b0 + nrow], ts[b0:b0 + nrow], nrow, lr, True, stream)
-                nb += 1
-            losses.append(tot / max(nb, 1))
+                final = b0 + batch >= rows  # read the loss (a synchronisation) once per epoch
+                last = pm_model_train_step(self.handle, xs[b0:b0 + nrow], ts[b0:b0 + nrow], nrow, lr, final, stream)
+            losses.append(last)
         return losses
 
     def close(self):

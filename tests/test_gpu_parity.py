@@ -304,3 +304,12 @@ def test_ga_with_autotuned_shape_matches_untuned(pm):
     for x, y in zip(a.population(), b.population()):
         np.testing.assert_array_equal(x, y)
     assert a.result()[:3] == b.result()[:3]
+
+
+def test_bounded_wait_times_out_and_context_survives(pm):
+    """A wait on a flag nothing sets gives up with PM_ERR_TIMEOUT; the next evaluation still works."""
+    assert pm.pm_selftest_bounded_wait(0) == 7
+    d = graph_instance(50, 120, seed=3)
+    inst = pm.Instance(d, 4)
+    masks = random_masks(40, 50, 4, seed=2)
+    np.testing.assert_array_equal(inst.eval(masks), oracle.eval_direct(d, masks))
