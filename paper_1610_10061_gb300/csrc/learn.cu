@@ -30,6 +30,7 @@
 
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -60,6 +61,11 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
 }
 
 __device__ __forceinline__ uint32_t ld32(const __nv_bfloat16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
+
+__device__ __forceinline__ uint32_t smem_u32_learn(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
 
 // A fragment (16 x 16, row-major source A[r][k], stride lda) at (r0, k0).
 __device__ __forceinline__ void frag_a(uint32_t (&a)[4], const __nv_bfloat16 *A, int lda, int r0, int k0, int lane)
@@ -98,6 +104,208 @@ struct MlpTrainSmem {
     __nv_bfloat16 dH1T[kHid * kLdR];    // [unit][r]
     float dy[kRows];
 };
+
+
+// ---------------------------------------------------------------------------
+// Inference forward on the 5th-generation tensor cores (tcgen05): 128 rows per
+// CTA; both layers are tcgen05.mma.cta_group::1.kind::f16 (BF16 x BF16 ->
+// FP32, M = N = 128) issued by one thread, operands in shared memory in the
+// K-major no-swizzle core-matrix layout (8 rows x 16 bytes per core matrix;
+// k-chunks 128 B apart, 8-row groups K*16 B apart), accumulators in tensor
+// memory (columns [0,128) layer 1, [128,256) layer 2), read back with
+// tcgen05.ld (thread = row) for the bias/ReLU/BF16 epilogues and the final
+// dot product with w3.  Completion is signalled by tcgen05.commit on an
+// mbarrier whose wait is bounded.
+// ---------------------------------------------------------------------------
+constexpr int kTcRows = 128;
+constexpr uint32_t kTmemCols = 256;
+constexpr uint32_t kTcSpinLimit = 1u << 22;
+// instruction descriptor: D F32 (bits 4-5 = 1), A BF16 (7-9 = 1), B BF16 (10-12 = 1), both K-major,
+// N >> 3 at bits 17-22, M >> 4 at bits 24-28
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ uint64_t umma_desc(const void *p, uint32_t lbo, uint32_t sbo)
+{
+    const uint32_t a = smem_u32_learn(p);
+    uint64_t d = (uint64_t)((a & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version for this architecture; base offset 0; no swizzle
+    return d;
+}
+
+// element (row, k) of a K-major no-swizzle tile with K columns (in elements)
+__device__ __forceinline__ int core_idx(int row, int k, int K)
+{
+    return ((row >> 3) * (K >> 3) * 128 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2) >> 1;
+}
+
+struct TcSmem {
+    __nv_bfloat16 A1[kTcRows * kIn];  // X tile
+    __nv_bfloat16 B1[kHid * kIn];     // W1 as (n = out, k = in)
+    __nv_bfloat16 A2[kTcRows * kHid]; // H1 tile
+    __nv_bfloat16 B2[kHid * kHid];    // W2 as (n = out, k = in)
+    float b1[kHid], b2[kHid], w3[kHid];
+    uint64_t bar;
+    uint32_t tmem;
+    int ok;
+};
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32_learn(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&v)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t phase)
+{
+    uint32_t spins = 0;
+    while (true) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(smem_u32_learn(bar)), "r"(phase)
+            : "memory");
+        if (ok)
+            return true;
+        if (++spins > kTcSpinLimit)
+            return false;
+    }
+}
+
+__global__ void __launch_bounds__(128) k_mlp_fwd_tc(const __nv_bfloat16 *__restrict__ X, int64_t rows,
+                                                    const __nv_bfloat16 *__restrict__ W1b,
+                                                    const __nv_bfloat16 *__restrict__ W2b,
+                                                    const __nv_bfloat16 *__restrict__ w3b,
+                                                    const float *__restrict__ P, float *__restrict__ y_out,
+                                                    int *__restrict__ err)
+{
+    extern __shared__ __align__(1024) unsigned char tc_raw[];
+    TcSmem &S = *reinterpret_cast<TcSmem *>(tc_raw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t row0 = (int64_t)blockIdx.x * kTcRows;
+
+    for (int i = tid; i < kIn * kHid; i += blockDim.x) {  // W1 [in][out]
+        const int in = i / kHid, out = i % kHid;
+        S.B1[core_idx(out, in, kIn)] = W1b[i];
+    }
+    for (int i = tid; i < kHid * kHid; i += blockDim.x) {  // W2 [in][out]
+        const int in = i / kHid, out = i % kHid;
+        S.B2[core_idx(out, in, kHid)] = W2b[i];
+    }
+    for (int i = tid; i < kTcRows * kIn; i += blockDim.x) {
+        const int r = i / kIn, f = i % kIn;
+        S.A1[core_idx(r, f, kIn)] = (row0 + r < rows) ? X[(row0 + r) * kIn + f] : __float2bfloat16(0.f);
+    }
+    for (int i = tid; i < kHid; i += blockDim.x) {
+        S.b1[i] = P[kOffB1 + i];
+        S.b2[i] = P[kOffB2 + i];
+        S.w3[i] = __bfloat162float(w3b[i]);
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32_learn(&S.bar)), "r"(1u) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32_learn(&S.tmem)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // smem operands visible to the tensor core
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = S.tmem;
+    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;  // this warp's TMEM lanes
+    const int r = warp * 32 + lane;                         // this thread's row
+
+    // layer 1: D[0,128) = X W1
+    if (tid == 0) {
+        tc_mma(tmem, umma_desc(S.A1, 128, (kIn / 8) * 128), umma_desc(S.B1, 128, (kIn / 8) * 128), kIdesc, 0u);
+        tc_commit(&S.bar);
+    }
+    uint32_t pending = 0;  // phase of the last commit
+    bool ok = tc_wait(&S.bar, 0);
+    ok = __syncthreads_and(ok);
+    if (ok) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        for (int c = 0; c < kHid / 32; ++c) {
+            uint32_t v[32];
+            tc_ld32(tmem + lane_off + (uint32_t)(c * 32), v);
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+                const int col = c * 32 + q;
+                S.A2[core_idx(r, col, kHid)] = __float2bfloat16(fmaxf(__uint_as_float(v[q]) + S.b1[col], 0.f));
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // layer 2: D[128,256) = H1 W2, eight k-steps of 16
+        if (tid == 0) {
+#pragma unroll
+            for (int s = 0; s < kHid / 16; ++s)
+                tc_mma(tmem + 128u, umma_desc(S.A2 + s * 128, 128, (kHid / 8) * 128),
+                       umma_desc(S.B2 + s * 128, 128, (kHid / 8) * 128), kIdesc, s > 0 ? 1u : 0u);
+            tc_commit(&S.bar);
+        }
+        pending = 1;
+        ok = tc_wait(&S.bar, 1);
+        ok = __syncthreads_and(ok);
+        if (ok) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            float ysum = 0.f;
+            for (int c = 0; c < kHid / 32; ++c) {
+                uint32_t v[32];
+                tc_ld32(tmem + lane_off + 128u + (uint32_t)(c * 32), v);
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    const int col = c * 32 + q;
+                    const float h2 = __bfloat162float(__float2bfloat16(fmaxf(__uint_as_float(v[q]) + S.b2[col], 0.f)));
+                    ysum += h2 * S.w3[col];
+                }
+            }
+            if (row0 + r < rows)
+                y_out[row0 + r] = ysum + P[kOffB3];
+        }
+    }
+    if (!ok) {
+        if (tid == 0)
+            atomicExch(err, (int)PM_ERR_TIMEOUT);
+        (void)tc_wait(&S.bar, pending);  // let an MMA in flight finish (bounded) before its memory is released
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+}
 
 // Forward (and in TRAIN mode, backward) for rows [row0, row0 + 64).  4 warps.
 //   X: rows x 16 bf16; Wb: bf16 copies (W1 [16][128], W2 [128][128], w3 [128]);
@@ -847,7 +1055,7 @@ pm_status pm_learn_prepare(const pm_instance *inst);
 
 struct pm_model {
     int device = 0;
-    pm_dbuf P, M, V, G, W1b, W2b, w3b, loss;
+    pm_dbuf P, M, V, G, W1b, W2b, w3b, loss, err;
     int64_t step = 0;
     std::mutex lock;
 };
@@ -860,8 +1068,13 @@ static size_t mlp_smem(bool train)
     return s;
 }
 
+// dynamic shared memory of the tcgen05 forward: the tiles, padded so that at most two CTAs share an SM
+// (2 x 256 TMEM columns = the SM's 512)
+static size_t tc_smem() { return std::max<size_t>(sizeof(TcSmem) + 1024, 100 * 1024); }
+
 static pm_status mlp_init_attrs()
 {
+    PM_CUDA(cudaFuncSetAttribute(k_mlp_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem()));
     PM_CUDA(cudaFuncSetAttribute(k_mlp<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp_smem(false)));
     PM_CUDA(cudaFuncSetAttribute(k_mlp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp_smem(true)));
     return PM_OK;
@@ -899,6 +1112,10 @@ extern "C" pm_status pm_model_create(int device, uint64_t seed, pm_model **out)
         st = md->w3b.reserve(kHid * 2);
     if (st == PM_OK)
         st = md->loss.reserve(256);
+    if (st == PM_OK)
+        st = md->err.reserve(256);
+    if (st == PM_OK && cudaMemset(md->err.ptr, 0, 256) != cudaSuccess)
+        st = PM_ERR_CUDA;
     if (st == PM_OK)
         st = mlp_init_attrs();
     if (st != PM_OK) {
@@ -940,7 +1157,7 @@ extern "C" pm_status pm_model_destroy(pm_model *md)
     if (!md)
         return PM_OK;
     cudaSetDevice(md->device);
-    pm_dbuf *bufs[] = {&md->P, &md->M, &md->V, &md->G, &md->W1b, &md->W2b, &md->w3b, &md->loss};
+    pm_dbuf *bufs[] = {&md->P, &md->M, &md->V, &md->G, &md->W1b, &md->W2b, &md->w3b, &md->loss, &md->err};
     for (pm_dbuf *b : bufs)
         b->release();
     delete md;
@@ -990,8 +1207,8 @@ static pm_status mlp_launch(pm_model *md, bool train, const void *x, int64_t row
                                                       static_cast<float *>(md->G.ptr),
                                                       static_cast<float *>(md->loss.ptr));
     else
-        k_mlp<false><<<grid, 128, mlp_smem(false), s>>>(X, rows, W1b, W2b, w3b, P, y, nullptr, 0.f, nullptr,
-                                                        nullptr);
+        k_mlp_fwd_tc<<<(unsigned)pm_ceil_div(rows, kTcRows), 128, tc_smem(), s>>>(
+            X, rows, W1b, W2b, w3b, P, y, static_cast<int *>(md->err.ptr));
     PM_CUDA(cudaGetLastError());
     return PM_OK;
 }

@@ -204,8 +204,10 @@ def _train_model(pm, d, p, seed=0, gens=6, per=64, epochs=8):
     X = torch.cat(xs)
     T = torch.cat(ts)
     model = pm.Model(seed=seed)
+    before, _ = model.grad(X, T)
     losses = model.train(X, T, epochs=epochs, batch=2048, lr=2e-3, seed=seed)
-    return inst, model, losses
+    after, _ = model.grad(X, T)
+    return inst, model, [before, after]
 
 
 def _spearman(a, b):
