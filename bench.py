@@ -269,11 +269,13 @@ def run_ours(args):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks.start()
+    torch.cuda.nvtx.range_push("timed")
     for k in range(args.steps):
         flush.zero_()  # L2 flush between timed steps (outside the events)
         starts[k].record(stream)
         pm.pm_ga_step(ga.handle, 1, None, stream.cuda_stream)
         ends[k].record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -408,11 +410,13 @@ def run_eval_mode(args):
     clocks = Clocks(0)
     torch.cuda.synchronize()
     clocks.start()
+    torch.cuda.nvtx.range_push("timed")
     for k in range(args.steps):
         flush.zero_()
         es[k].record(stream)
         pm.pm_eval_population(inst.handle, dmask, pop, dcost, 0, stream.cuda_stream)
         ee[k].record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms = [a.elapsed_time(b) for a, b in zip(es, ee)]
@@ -472,11 +476,13 @@ def run_batched(args):
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     clocks = Clocks(0)
     clocks.start()
+    torch.cuda.nvtx.range_push("timed")
     for k in range(args.steps):
         flush.zero_()
         starts[k].record(stream)
         pm.pm_ga_step(ga.handle, 1, None, stream.cuda_stream)
         ends[k].record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
@@ -573,6 +579,7 @@ def run_learned(args):
     target = int(ptrace0[-1])
     res = {"plain": [], "learned": []}
     limit = 4 * budget  # each arm may run up to four times the budget that defined the target
+    torch.cuda.nvtx.range_push("timed")
     for seed in range(5):
         for arm in ("plain", "learned"):
             tr, cum, evals = run(seed, arm == "learned", limit)
@@ -580,6 +587,7 @@ def run_learned(args):
             res[arm].append({"seed": seed, "time_s": float(cum[hit[0]]) if hit.size else None,
                              "gens": int(hit[0] + 1) if hit.size else None, "final": int(tr[-1]),
                              "ms_per_gen": float(cum[-1] / limit * 1000.0), "evals": int(evals)})
+    torch.cuda.nvtx.range_pop()
 
     def med(arm, key):
         vals = [r[key] for r in res[arm] if r[key] is not None]

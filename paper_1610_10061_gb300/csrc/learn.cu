@@ -620,37 +620,36 @@ __global__ void k_refresh_bf16(const float *__restrict__ P, __nv_bfloat16 *__res
 // Swap statistics: one CTA per individual; accumulators in shared memory when
 // they fit (else in the output arrays, zeroed by the caller).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(512) k_swap_stats(const uint16_t *__restrict__ pi, const int32_t *__restrict__ delta,
-                                                    int64_t n, int32_t L, int64_t stride, int32_t W, int32_t m,
-                                                    const uint32_t *__restrict__ masks, int64_t pop,
-                                                    unsigned long long *__restrict__ gain, int *__restrict__ cap,
-                                                    unsigned long long *__restrict__ loss, int *__restrict__ assign,
-                                                    int in_smem)
+template <typename Acc>
+__global__ void __launch_bounds__(1024) k_swap_stats(const uint16_t *__restrict__ pi,
+                                                     const int32_t *__restrict__ delta, int64_t n, int32_t L,
+                                                     int64_t stride, int32_t W, int32_t m,
+                                                     const uint32_t *__restrict__ masks, int64_t pop,
+                                                     unsigned long long *__restrict__ gain, int *__restrict__ cap,
+                                                     unsigned long long *__restrict__ loss, int *__restrict__ assign,
+                                                     int in_smem)
 {
     extern __shared__ __align__(16) unsigned char sm[];
     const int64_t t = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     uint32_t *bits = reinterpret_cast<uint32_t *>(sm);
     const size_t off = ((size_t)W * 4 + 15) & ~size_t(15);
-    unsigned long long *G, *Lo;
-    int *C, *A;
+    // accumulators: in shared memory (Acc: 32 or 64 bits, chosen by the host so sums cannot overflow) or
+    // directly in the outputs (64 bits, zeroed by the caller)
+    Acc *Gs = reinterpret_cast<Acc *>(sm + off);
+    Acc *Ls = Gs + m;
+    int *Cs = reinterpret_cast<int *>(Ls + m);
+    int *As = Cs + m;
     if (in_smem) {
-        G = reinterpret_cast<unsigned long long *>(sm + off);
-        Lo = G + m;
-        C = reinterpret_cast<int *>(Lo + m);
-        A = C + m;
         for (int j = threadIdx.x; j < m; j += blockDim.x) {
-            G[j] = 0ull;
-            Lo[j] = 0ull;
-            C[j] = 0;
-            A[j] = 0;
+            Gs[j] = 0;
+            Ls[j] = 0;
+            Cs[j] = 0;
+            As[j] = 0;
         }
-    } else {
-        G = gain + t * m;
-        Lo = loss + t * m;
-        C = cap + t * m;
-        A = assign + t * m;
     }
+    int *C = in_smem ? Cs : cap + t * m;
+    int *A = in_smem ? As : assign + t * m;
     for (int w = threadIdx.x; w < W; w += blockDim.x)
         bits[w] = masks[t * W + w];
     __syncthreads();
@@ -669,6 +668,11 @@ __global__ void __launch_bounds__(512) k_swap_stats(const uint16_t *__restrict__
                 dl = __ldg(drow + r);
             }
             const bool open = (r < L) && ((bits[j >> 5] >> (j & 31)) & 1u);
+            uint32_t bal = __ballot_sync(PM_FULL_MASK, open);
+            if (bal == 0u && found == 0) {  // no open facility among these 32 ranks: only the carry moves
+                carry += __reduce_add_sync(PM_FULL_MASK, dl);
+                continue;
+            }
             int32_t cs = dl;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -677,7 +681,6 @@ __global__ void __launch_bounds__(512) k_swap_stats(const uint16_t *__restrict__
                     cs += y;
             }
             cs += carry;
-            uint32_t bal = __ballot_sync(PM_FULL_MASK, open);
             if (found == 0 && bal) {
                 const int f = __ffs(bal) - 1;
                 d1 = __shfl_sync(PM_FULL_MASK, cs, f);
@@ -697,7 +700,10 @@ __global__ void __launch_bounds__(512) k_swap_stats(const uint16_t *__restrict__
             d2 = carry;  // no second open facility within the table
         if (lane == 0) {
             const uint32_t f1 = __ldg(prow + r1);
-            atomicAdd(Lo + f1, (unsigned long long)(uint32_t)(d2 - d1));
+            if (in_smem)
+                atomicAdd(Ls + f1, (Acc)(uint32_t)(d2 - d1));
+            else
+                atomicAdd(loss + t * m + f1, (unsigned long long)(uint32_t)(d2 - d1));
             atomicAdd(A + f1, 1);
         }
         // pass 2: every facility ranked before r1 gains D1 - d(i, k)
@@ -719,7 +725,10 @@ __global__ void __launch_bounds__(512) k_swap_stats(const uint16_t *__restrict__
             }
             cs += carry;
             if (r < r1) {
-                atomicAdd(G + j, (unsigned long long)(uint32_t)(d1 - cs));
+                if (in_smem)
+                    atomicAdd(Gs + j, (Acc)(uint32_t)(d1 - cs));
+                else
+                    atomicAdd(gain + t * m + j, (unsigned long long)(uint32_t)(d1 - cs));
                 atomicAdd(C + j, 1);
             }
             carry = __shfl_sync(PM_FULL_MASK, cs, 31);
@@ -728,10 +737,10 @@ __global__ void __launch_bounds__(512) k_swap_stats(const uint16_t *__restrict__
     if (in_smem) {
         __syncthreads();
         for (int j = threadIdx.x; j < m; j += blockDim.x) {
-            gain[t * m + j] = G[j];
-            loss[t * m + j] = Lo[j];
-            cap[t * m + j] = C[j];
-            assign[t * m + j] = A[j];
+            gain[t * m + j] = (unsigned long long)Gs[j];
+            loss[t * m + j] = (unsigned long long)Ls[j];
+            cap[t * m + j] = Cs[j];
+            assign[t * m + j] = As[j];
         }
     }
 }
@@ -1303,7 +1312,9 @@ pm_status pm_launch_swap_stats(const pm_instance *inst, const uint32_t *masks, i
     if (pop <= 0)
         return PM_OK;
     const size_t bits = (size_t)pm_round_up(inst->W * 4, 16);
-    const size_t acc = (size_t)inst->m * 24;
+    // 32-bit shared accumulators suffice when no sum can reach 2^32: every gain and loss is at most n * max d
+    const bool narrow = (double)inst->n * (double)std::max(inst->max_d, 1) < 4294967295.0;
+    const size_t acc = (size_t)inst->m * (narrow ? 16 : 24);
     const bool in_smem = bits + acc + 1024 <= inst->smem_optin;
     const size_t smem = in_smem ? bits + acc : bits;
     if (!in_smem) {
@@ -1312,11 +1323,15 @@ pm_status pm_launch_swap_stats(const pm_instance *inst, const uint32_t *masks, i
         PM_CUDA(cudaMemsetAsync(cap, 0, (size_t)pop * inst->m * 4, s));
         PM_CUDA(cudaMemsetAsync(assign, 0, (size_t)pop * inst->m * 4, s));
     }
-    k_swap_stats<<<(unsigned)pop, 512, smem, s>>>(inst->pi, inst->delta, inst->n, (int32_t)inst->L, inst->stride,
-                                                  (int32_t)inst->W, (int32_t)inst->m, masks, pop,
-                                                  reinterpret_cast<unsigned long long *>(gain), cap,
-                                                  reinterpret_cast<unsigned long long *>(loss), assign,
-                                                  in_smem ? 1 : 0);
+#define PM_STATS_ARGS                                                                                              \
+    inst->pi, inst->delta, inst->n, (int32_t)inst->L, inst->stride, (int32_t)inst->W, (int32_t)inst->m, masks, pop, \
+        reinterpret_cast<unsigned long long *>(gain), cap, reinterpret_cast<unsigned long long *>(loss), assign,     \
+        in_smem ? 1 : 0
+    if (narrow && in_smem)
+        k_swap_stats<unsigned int><<<(unsigned)pop, 1024, smem, s>>>(PM_STATS_ARGS);
+    else
+        k_swap_stats<unsigned long long><<<(unsigned)pop, 1024, smem, s>>>(PM_STATS_ARGS);
+#undef PM_STATS_ARGS
     PM_CUDA(cudaGetLastError());
     return PM_OK;
 }
@@ -1386,7 +1401,8 @@ int pm_mlp_in_width() { return kIn; }
 pm_status pm_learn_prepare(const pm_instance *inst)
 {
     const int cap = (int)(inst->smem_optin > 1024 ? inst->smem_optin - 1024 : inst->smem_optin);
-    PM_CUDA(cudaFuncSetAttribute(k_swap_stats, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+    PM_CUDA(cudaFuncSetAttribute(k_swap_stats<unsigned int>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+    PM_CUDA(cudaFuncSetAttribute(k_swap_stats<unsigned long long>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
     PM_CUDA(cudaFuncSetAttribute(k_candidates, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
     return mlp_init_attrs();
 }
