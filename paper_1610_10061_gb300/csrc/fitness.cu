@@ -130,6 +130,7 @@ __device__ __forceinline__ int find_prob(int K, int64_t x, F base)
 __global__ void k_pop_to_columns(const uint32_t *__restrict__ masks, const pm_prob *__restrict__ probs, int K,
                                  pm_prob one, int64_t jobs, int32_t G, uint32_t *__restrict__ colT)
 {
+    pm_grid_dependency_wait();
     const int lane = threadIdx.x & 31;
     const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t job = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); job < jobs;
@@ -174,6 +175,7 @@ __global__ void __launch_bounds__(1024) k_scan_columns(const pm_prob *__restrict
                                                        int *__restrict__ tickets, int *__restrict__ err,
                                                        ScanEpilogue ep)
 {
+    pm_grid_dependency_wait();
     extern __shared__ __align__(128) uint32_t colbits[];  // [32W][G]
     __shared__ unsigned long long acc_s[G * 32];
     __shared__ uint32_t a0_s[G];
@@ -440,6 +442,7 @@ __global__ void __launch_bounds__(256) k_scan_rows(const uint16_t *__restrict__ 
                                                    const uint32_t *__restrict__ active, int64_t clients_per_split,
                                                    unsigned long long *__restrict__ partial)
 {
+    pm_grid_dependency_wait();
     extern __shared__ __align__(16) uint32_t rowbits[];  // [warps][W]
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -498,6 +501,7 @@ __global__ void __launch_bounds__(256) k_scan_rows(const uint16_t *__restrict__ 
 __global__ void k_reduce_accept(unsigned long long *__restrict__ partial, int splits, int64_t pop,
                                 const uint32_t *__restrict__ active, ScanEpilogue ep, int32_t W)
 {
+    pm_grid_dependency_wait();
     const int lane = threadIdx.x & 31;
     const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (t >= pop)
@@ -698,9 +702,8 @@ pm_status pm_launch_scan(const pm_scan_launch &L, const pm_accept_args &acc, int
     if (!acc.columns_ready) {
         const int threads = 256;
         const int64_t blocks = std::min<int64_t>(pm_ceil_div(L.jobs, threads / 32), (int64_t)2048);
-        k_pop_to_columns<<<(unsigned)blocks, threads, 0, stream>>>(L.masks, L.probs_dev, L.K, L.one, L.jobs, G,
-                                                                   L.colT);
-        PM_CUDA(cudaGetLastError());
+        PM_CUDA(pm_launch(k_pop_to_columns, (unsigned)blocks, threads, 0, stream, L.masks, L.probs_dev, L.K, L.one,
+                          L.jobs, G, L.colT));
     }
     const unsigned grid = (unsigned)L.grid;
     const int threads = L.warps * 32;
@@ -708,17 +711,16 @@ pm_status pm_launch_scan(const pm_scan_launch &L, const pm_accept_args &acc, int
 #define PM_SCAN_ARGS L.probs_dev, L.K, L.one, L.items, L.colT, L.active, accum, L.tickets, L.err, ep
     switch (G) {
     case 1:
-        k_scan_columns<1><<<grid, threads, smem, stream>>>(PM_SCAN_ARGS);
+        PM_CUDA(pm_launch(k_scan_columns<1>, grid, threads, smem, stream, PM_SCAN_ARGS));
         break;
     case 2:
-        k_scan_columns<2><<<grid, threads, smem, stream>>>(PM_SCAN_ARGS);
+        PM_CUDA(pm_launch(k_scan_columns<2>, grid, threads, smem, stream, PM_SCAN_ARGS));
         break;
     default:
-        k_scan_columns<4><<<grid, threads, smem, stream>>>(PM_SCAN_ARGS);
+        PM_CUDA(pm_launch(k_scan_columns<4>, grid, threads, smem, stream, PM_SCAN_ARGS));
         break;
     }
 #undef PM_SCAN_ARGS
-    PM_CUDA(cudaGetLastError());
     return PM_OK;
 }
 
@@ -756,15 +758,12 @@ pm_status pm_launch_eval(const pm_instance *inst, const pm_eval_plan &plan, cons
     const int64_t cps = pm_ceil_div(inst->n, plan.splits);
     const size_t smem = (size_t)plan.warps * inst->W * 4;
     dim3 grid((unsigned)plan.tiles, (unsigned)plan.splits);
-    k_scan_rows<<<grid, plan.warps * 32, smem, stream>>>(inst->pi, inst->delta, inst->n, (int32_t)inst->L,
-                                                         inst->stride, masks, (int32_t)inst->W, pop, active, cps,
-                                                         partials);
-    PM_CUDA(cudaGetLastError());
+    PM_CUDA(pm_launch(k_scan_rows, grid, plan.warps * 32, smem, stream, inst->pi, inst->delta, inst->n,
+                      (int32_t)inst->L, inst->stride, masks, (int32_t)inst->W, pop, active, cps, partials));
     const int64_t threads = 256;
     const int64_t blocks = pm_ceil_div(pop * 32, threads);
-    k_reduce_accept<<<(unsigned)blocks, (unsigned)threads, 0, stream>>>(partials, plan.splits, pop, active, ep,
-                                                                        (int32_t)inst->W);
-    PM_CUDA(cudaGetLastError());
+    PM_CUDA(pm_launch(k_reduce_accept, (unsigned)blocks, (unsigned)threads, 0, stream, partials, plan.splits, pop,
+                      active, ep, (int32_t)inst->W));
     return PM_OK;
 }
 

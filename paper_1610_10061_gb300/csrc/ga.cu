@@ -214,6 +214,7 @@ __global__ void __launch_bounds__(32) k_ga_init(const ga_prob *__restrict__ gps,
                                                 uint64_t seed, const ga_dev *__restrict__ st, ColumnsOut co,
                                                 int rows_in_smem)
 {
+    pm_grid_dependency_wait();
     extern __shared__ uint32_t rows_s[];  // [32][Ws], Ws = W | 1 (odd stride: conflict-free transposes)
     int k;
     const ga_prob gp = prob_of_group(gps, K, one, blockIdx.x, k);
@@ -275,6 +276,7 @@ __global__ void __launch_bounds__(1024) k_ga_crossover(const ga_prob *__restrict
                                                        uint32_t *__restrict__ active, uint32_t round, uint64_t seed,
                                                        ga_dev *__restrict__ st, ColumnsOut co)
 {
+    pm_grid_dependency_wait();
     __shared__ uint32_t valid_s;
     int k;
     const ga_prob gp = prob_of_group(gps, K, one, blockIdx.x, k);
@@ -401,6 +403,7 @@ __global__ void __launch_bounds__(1024) k_ga_mutate(const ga_prob *__restrict__ 
                                                     const uint8_t *__restrict__ improved, uint32_t q, uint64_t seed,
                                                     ga_dev *__restrict__ st, ColumnsOut co)
 {
+    pm_grid_dependency_wait();
     __shared__ uint32_t on_s;
     int k;
     const ga_prob gp = prob_of_group(gps, K, one, blockIdx.x, k);
@@ -477,6 +480,7 @@ __global__ void k_ga_deme_best(const ga_prob *__restrict__ gps, int K, ga_prob o
                                const int64_t *__restrict__ cost, uint32_t *__restrict__ deme_best,
                                int64_t *__restrict__ deme_cost, const ga_dev *__restrict__ st)
 {
+    pm_grid_dependency_wait();
     __shared__ long long sc[32];
     __shared__ long long si[32];
     __shared__ long long win;
@@ -536,6 +540,7 @@ __global__ void k_ga_finish(const ga_prob *__restrict__ gps, int K, ga_prob one,
                             uint32_t *__restrict__ best, ga_dev *__restrict__ st, ga_glob *__restrict__ glob,
                             cudaGraphConditionalHandle h, int in_graph)
 {
+    pm_grid_dependency_wait();
     __shared__ long long sc[32];
     __shared__ long long si[32];
     __shared__ int improve;
@@ -639,6 +644,7 @@ __global__ void __launch_bounds__(1024) k_ga_learned_pick(const ga_prob *__restr
                                                           const int32_t *__restrict__ moves, int64_t C,
                                                           ga_dev *__restrict__ st, ColumnsOut co)
 {
+    pm_grid_dependency_wait();
     __shared__ uint32_t on_s;
     int k;
     const ga_prob gp = prob_of_group(gps, K, one, blockIdx.x, k);
@@ -832,10 +838,8 @@ static pm_status enqueue_generation(pm_ga *ga, cudaStream_t s, cudaGraphConditio
     const size_t init_smem = (size_t)32 * (ga->Wmax | 1) * 4;
     const int rows_in_smem = init_smem <= 48 * 1024 ? 1 : 0;
 
-    k_ga_init<<<groups, 32, rows_in_smem ? init_smem : 0, s>>>(gps, K, one, X, improved, active,
-                                                               static_cast<const uint32_t *>(ga->deme_best.ptr),
-                                                               ga->seed, st, co, rows_in_smem);
-    PM_CUDA(cudaGetLastError());
+    PM_CUDA(pm_launch(k_ga_init, groups, 32, rows_in_smem ? init_smem : 0, s, gps, K, one, X, improved, active,
+                      static_cast<const uint32_t *>(ga->deme_best.ptr), ga->seed, st, co, rows_in_smem));
     pm_accept_args plain;
     plain.columns_ready = true;
     PM_TRY(ga_eval(ga, X, cost, plain, s));
@@ -848,8 +852,8 @@ static pm_status enqueue_generation(pm_ga *ga, cudaStream_t s, cudaGraphConditio
     acc.columns_ready = true;
     if (ga->gps[0].p / 2 > 0) {  // p = 1: no crossover (a batch has p >= 2 everywhere or p = 1 everywhere)
         for (int r = 0; r < ga->R; ++r) {
-            k_ga_crossover<<<groups, 1024, 0, s>>>(gps, K, one, X, Xc, active, (uint32_t)r, ga->seed, st, co);
-            PM_CUDA(cudaGetLastError());
+            PM_CUDA(pm_launch(k_ga_crossover, groups, 1024, 0, s, gps, K, one, X, Xc, active, (uint32_t)r, ga->seed,
+                              st, co));
             acc.improved = nullptr;
             PM_TRY(ga_eval(ga, Xc, nullptr, acc, s));
         }
@@ -865,28 +869,24 @@ static pm_status enqueue_generation(pm_ga *ga, cudaStream_t s, cudaGraphConditio
         PM_TRY(pm_launch_candidates(inst, X, ga->P, gain, capc, loss, asg, cost, ga->T, moves,
                                     static_cast<uint16_t *>(ga->xfeat.ptr), s));
         PM_TRY(pm_model_forward_dev(ga->model, ga->xfeat.ptr, ga->P * C, static_cast<float *>(ga->scores.ptr), s));
-        k_ga_learned_pick<<<groups, 1024, 0, s>>>(gps, K, one, X, Xc, active, improved,
-                                                  static_cast<const float *>(ga->scores.ptr), moves, C, st, co);
-        PM_CUDA(cudaGetLastError());
+        PM_CUDA(pm_launch(k_ga_learned_pick, groups, 1024, 0, s, gps, K, one, X, Xc, active, improved,
+                          static_cast<const float *>(ga->scores.ptr), moves, C, st, co));
         acc.improved = improved;
         PM_TRY(ga_eval(ga, Xc, nullptr, acc, s));
     }
     for (int q = 0; q < ga->Q; ++q) {
-        k_ga_mutate<<<groups, 1024, 0, s>>>(gps, K, one, X, Xc, active, improved, (uint32_t)q, ga->seed, st, co);
-        PM_CUDA(cudaGetLastError());
+        PM_CUDA(pm_launch(k_ga_mutate, groups, 1024, 0, s, gps, K, one, X, Xc, active, improved, (uint32_t)q,
+                          ga->seed, st, co));
         acc.improved = improved;
         PM_TRY(ga_eval(ga, Xc, nullptr, acc, s));
     }
     const int dthreads = (int)pm_round_up(std::min<int64_t>(ga->D, 1024), 32);
-    k_ga_deme_best<<<(unsigned)ga->demes_total, (unsigned)dthreads, 0, s>>>(
-        gps, K, one, X, cost, static_cast<uint32_t *>(ga->deme_best.ptr), static_cast<int64_t *>(ga->deme_cost.ptr),
-        st);
-    PM_CUDA(cudaGetLastError());
-    k_ga_finish<<<(unsigned)K, 256, 0, s>>>(gps, K, one, static_cast<const uint32_t *>(ga->deme_best.ptr),
-                                            static_cast<const int64_t *>(ga->deme_cost.ptr),
-                                            static_cast<uint32_t *>(ga->best.ptr), st,
-                                            static_cast<ga_glob *>(ga->glob.ptr), h, in_graph);
-    PM_CUDA(cudaGetLastError());
+    PM_CUDA(pm_launch(k_ga_deme_best, (unsigned)ga->demes_total, (unsigned)dthreads, 0, s, gps, K, one, X, cost,
+                      static_cast<uint32_t *>(ga->deme_best.ptr), static_cast<int64_t *>(ga->deme_cost.ptr), st));
+    PM_CUDA(pm_launch(k_ga_finish, (unsigned)K, 256, 0, s, gps, K, one,
+                      static_cast<const uint32_t *>(ga->deme_best.ptr),
+                      static_cast<const int64_t *>(ga->deme_cost.ptr), static_cast<uint32_t *>(ga->best.ptr), st,
+                      static_cast<ga_glob *>(ga->glob.ptr), h, in_graph));
     return PM_OK;
 }
 

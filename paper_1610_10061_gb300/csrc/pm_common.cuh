@@ -5,6 +5,8 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <cstdlib>
+#include <utility>
 
 #include <algorithm>
 #include <map>
@@ -72,6 +74,43 @@ struct pm_prob {
     int64_t item_base;
     int64_t job_base;     // transpose jobs (tiles * G * W per instance)
 };
+
+// Programmatic dependent launch.  Kernels of the GA generation and of the
+// evaluation are launched with programmatic stream serialisation, so the next
+// kernel of the stream is scheduled while the current one still runs; every
+// such kernel first waits for the completion (and memory) of the grid before
+// it, then lets its own successor be scheduled.  Without the launch attribute
+// the wait returns at once.  PM_PDL=0 in the environment turns the attribute off.
+__device__ __forceinline__ void pm_grid_dependency_wait()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+inline bool pm_pdl_enabled()
+{
+    static const bool on = [] {
+        const char *e = std::getenv("PM_PDL");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t pm_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pm_pdl_enabled() ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 struct pm_instance {
     int device = 0;
