@@ -183,6 +183,18 @@ typedef struct pm_eval_shape {
 PM_API pm_status pm_tune_eval(pm_instance *inst, int64_t pop, void *stream, pm_eval_shape *chosen);
 
 /*
+ * pm_set_eval_shape -- use `shape` (groups, warps, splits; grid, ms,
+ * candidates and reserved are ignored) for evaluations of `pop` individuals on inst
+ * and for GAs created afterwards, in place of the heuristic or a tuned
+ * shape (no counterpart in the paper: it pins a launch shape for
+ * reproducible timing and tests).  groups 0 selects the row kernel; splits 0
+ * the default split count.  The costs do not depend on the shape.  Errors:
+ * PM_ERR_INVALID_ARG (bad values), PM_ERR_UNSUPPORTED (the shape does not
+ * fit this instance's shared-memory budget).
+ */
+PM_API pm_status pm_set_eval_shape(pm_instance *inst, int64_t pop, const pm_eval_shape *shape);
+
+/*
  * pm_selftest_bounded_wait -- failure-detection self-test (no counterpart in
  * the paper).  Launches one CTA that waits on an mbarrier nothing will
  * complete, with the bounded-poll exit every wait in this library uses; the

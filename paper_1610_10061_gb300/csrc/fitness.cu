@@ -151,6 +151,107 @@ __global__ void k_pop_to_columns(const uint32_t *__restrict__ masks, const pm_pr
     }
 }
 
+// One warp's walk over the clients c, c + step, ... (< c_end) of one tile:
+// the tile's facility-major bits are in colbits, a0[g] marks its active
+// individuals; every resolved individual's distance is added to acc[g] at
+// the lane of the individual.  load(cc, base, j, dl) yields rank base + lane
+// of client cc (Pi' and Delta', zeros past the row or past c_end); the
+// caller passes the first two steps of client c and the first step of client
+// c + step already loaded.
+template <int G, typename Ld>
+__device__ __forceinline__ void scan_clients(const uint32_t *__restrict__ colbits, const uint32_t (&a0)[G], int64_t c,
+                                             int64_t c_end, int step, int32_t L, int lane, Ld &load,
+                                             uint32_t j_cur, int32_t d_cur, uint32_t j_nxt, int32_t d_nxt,
+                                             uint32_t j_nc, int32_t d_nc, unsigned long long (&acc)[G])
+{
+    uint32_t a[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+        a[g] = a0[g];
+    int32_t carry = 0;
+    int base = 0;
+    for (;;) {
+        uint32_t w[G];
+        if (base + lane < L) {
+            load_cols<G>(colbits, j_cur, w);
+        } else {
+#pragma unroll
+            for (int g = 0; g < G; ++g)
+                w[g] = 0u;
+        }
+        uint32_t hit = 0;
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            w[g] &= a[g];
+            hit |= w[g];
+        }
+        if (!__any_sync(PM_FULL_MASK, hit != 0u)) {
+            carry += __reduce_add_sync(PM_FULL_MASK, d_cur);
+        } else {
+            // running sum of Delta' up to this lane's rank = the sorted distance at that rank
+            int32_t cs = d_cur;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t y = __shfl_up_sync(PM_FULL_MASK, cs, o);
+                if (lane >= o)
+                    cs += y;
+            }
+            cs += carry;
+            carry = __shfl_sync(PM_FULL_MASK, cs, 31);
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                uint32_t hl = __ballot_sync(PM_FULL_MASK, w[g] != 0u);
+                if (hl == 0u)
+                    continue;
+                if (__popc(hl) <= kSparseLanes) {
+                    uint32_t ag = a[g];
+                    do {
+                        const int r = __ffs(hl) - 1;
+                        hl &= hl - 1u;
+                        const uint32_t hb = __shfl_sync(PM_FULL_MASK, w[g], r) & ag;
+                        const int32_t v = __shfl_sync(PM_FULL_MASK, cs, r);
+                        if ((hb >> lane) & 1u)
+                            acc[g] += (unsigned long long)(uint32_t)v;
+                        ag &= ~hb;
+                    } while (hl);
+                    a[g] = ag;
+                } else {
+                    const uint32_t T = pm_transpose32(w[g], lane);
+                    const int f = __ffs(T) - 1;
+                    const int32_t v = __shfl_sync(PM_FULL_MASK, cs, f & 31);
+                    if (T)
+                        acc[g] += (unsigned long long)(uint32_t)v;
+                    a[g] &= ~__ballot_sync(PM_FULL_MASK, T != 0u);
+                }
+            }
+        }
+        uint32_t left = 0;
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+            left |= a[g];
+        base += 32;
+        if (left != 0u && base < L) {
+            j_cur = j_nxt;
+            d_cur = d_nxt;
+            load(c, base + 32, j_nxt, d_nxt);
+            continue;
+        }
+        // next client of this warp
+        c += step;
+        if (c >= c_end)
+            break;
+        j_cur = j_nc;
+        d_cur = d_nc;
+        load(c, 32, j_nxt, d_nxt);
+        load(c + step, 0, j_nc, d_nc);
+        base = 0;
+        carry = 0;
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+            a[g] = a0[g];
+    }
+}
+
 struct ScanEpilogue {
     int mode;                    // 0: store costs; 1: accept strictly cheaper candidates
     int64_t *costs;              // mode 0 (and optionally mode 1): candidate costs
@@ -159,6 +260,36 @@ struct ScanEpilogue {
     const uint32_t *cand_masks;  // mode 1
     uint8_t *improved;           // mode 1, nullable
 };
+
+// The epilogue of one tile, one warp per individual: store the cost, or
+// accept the candidate (copy its bitset, cost and improved flag) when it is
+// strictly cheaper than the current individual.
+template <int G>
+__device__ __forceinline__ void apply_epilogue(const unsigned long long *acc_s, const uint32_t *a0_s, const pm_prob &pr,
+                                               int64_t ind0, int warp, int nwarps, int lane, const ScanEpilogue &ep)
+{
+    const int32_t W = pr.W;
+    for (int i = warp; i < G * 32; i += nwarps) {
+        const int64_t t = ind0 + i;
+        if (t >= pr.pop)
+            break;
+        if (!((a0_s[i >> 5] >> (i & 31)) & 1u))
+            continue;
+        const int64_t sum = (int64_t)acc_s[i];
+        if (ep.costs != nullptr && lane == 0)
+            ep.costs[pr.out_base + t] = sum;
+        if (ep.mode == 1 && sum < ep.cur_cost[pr.ind_base + t]) {
+            const int64_t row = pr.word_base + t * W;
+            for (int q = lane; q < W; q += 32)
+                ep.cur_masks[row + q] = ep.cand_masks[row + q];
+            if (lane == 0) {
+                ep.cur_cost[pr.ind_base + t] = sum;
+                if (ep.improved)
+                    ep.improved[pr.ind_base + t] = 1;
+            }
+        }
+    }
+}
 
 // ---------------------------------------------------------------------------
 // The column scan kernel (with the split reduction and epilogue fused), over
@@ -281,94 +412,8 @@ __global__ void __launch_bounds__(1024) k_scan_columns(const pm_prob *__restrict
         for (int g = 0; g < G; ++g)
             acc[g] = 0ull;
 
-        if (any0 && c < c_end) {
-            uint32_t a[G];
-#pragma unroll
-            for (int g = 0; g < G; ++g)
-                a[g] = a0[g];
-            int32_t carry = 0;
-            int base = 0;
-            for (;;) {
-                uint32_t w[G];
-                if (base + lane < L) {
-                    load_cols<G>(colbits, j_cur, w);
-                } else {
-#pragma unroll
-                    for (int g = 0; g < G; ++g)
-                        w[g] = 0u;
-                }
-                uint32_t hit = 0;
-#pragma unroll
-                for (int g = 0; g < G; ++g) {
-                    w[g] &= a[g];
-                    hit |= w[g];
-                }
-                if (!__any_sync(PM_FULL_MASK, hit != 0u)) {
-                    carry += __reduce_add_sync(PM_FULL_MASK, d_cur);
-                } else {
-                    // running sum of Delta' up to this lane's rank = the sorted distance at that rank
-                    int32_t cs = d_cur;
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const int32_t y = __shfl_up_sync(PM_FULL_MASK, cs, o);
-                        if (lane >= o)
-                            cs += y;
-                    }
-                    cs += carry;
-                    carry = __shfl_sync(PM_FULL_MASK, cs, 31);
-#pragma unroll
-                    for (int g = 0; g < G; ++g) {
-                        uint32_t hl = __ballot_sync(PM_FULL_MASK, w[g] != 0u);
-                        if (hl == 0u)
-                            continue;
-                        if (__popc(hl) <= kSparseLanes) {
-                            uint32_t ag = a[g];
-                            do {
-                                const int r = __ffs(hl) - 1;
-                                hl &= hl - 1u;
-                                const uint32_t hb = __shfl_sync(PM_FULL_MASK, w[g], r) & ag;
-                                const int32_t v = __shfl_sync(PM_FULL_MASK, cs, r);
-                                if ((hb >> lane) & 1u)
-                                    acc[g] += (unsigned long long)(uint32_t)v;
-                                ag &= ~hb;
-                            } while (hl);
-                            a[g] = ag;
-                        } else {
-                            const uint32_t T = pm_transpose32(w[g], lane);
-                            const int f = __ffs(T) - 1;
-                            const int32_t v = __shfl_sync(PM_FULL_MASK, cs, f & 31);
-                            if (T)
-                                acc[g] += (unsigned long long)(uint32_t)v;
-                            a[g] &= ~__ballot_sync(PM_FULL_MASK, T != 0u);
-                        }
-                    }
-                }
-                uint32_t left = 0;
-#pragma unroll
-                for (int g = 0; g < G; ++g)
-                    left |= a[g];
-                base += 32;
-                if (left != 0u && base < L) {
-                    j_cur = j_nxt;
-                    d_cur = d_nxt;
-                    load(c, base + 32, j_nxt, d_nxt);
-                    continue;
-                }
-                // next client of this warp
-                c += nwarps;
-                if (c >= c_end)
-                    break;
-                j_cur = j_nc;
-                d_cur = d_nc;
-                load(c, 32, j_nxt, d_nxt);
-                load(c + nwarps, 0, j_nc, d_nc);
-                base = 0;
-                carry = 0;
-#pragma unroll
-                for (int g = 0; g < G; ++g)
-                    a[g] = a0[g];
-            }
-        }
+        if (any0 && c < c_end)
+            scan_clients<G>(colbits, a0, c, c_end, nwarps, L, lane, load, j_cur, d_cur, j_nxt, d_nxt, j_nc, d_nc, acc);
 #pragma unroll
         for (int g = 0; g < G; ++g)
             if (acc[g])
@@ -404,29 +449,8 @@ __global__ void __launch_bounds__(1024) k_scan_columns(const pm_prob *__restrict
                 __syncthreads();
             }
         }
-        if (finish) {
-            // epilogue: one warp per individual of the tile
-            for (int i = warp; i < G * 32; i += nwarps) {
-                const int64_t t = ind0 + i;
-                if (t >= pop)
-                    break;
-                if (!((a0_s[i >> 5] >> (i & 31)) & 1u))
-                    continue;
-                const int64_t sum = (int64_t)acc_s[i];
-                if (ep.costs != nullptr && lane == 0)
-                    ep.costs[pr.out_base + t] = sum;
-                if (ep.mode == 1 && sum < ep.cur_cost[pr.ind_base + t]) {
-                    const int64_t row = pr.word_base + t * W;
-                    for (int q = lane; q < W; q += 32)
-                        ep.cur_masks[row + q] = ep.cand_masks[row + q];
-                    if (lane == 0) {
-                        ep.cur_cost[pr.ind_base + t] = sum;
-                        if (ep.improved)
-                            ep.improved[pr.ind_base + t] = 1;
-                    }
-                }
-            }
-        }
+        if (finish)
+            apply_epilogue<G>(acc_s, a0_s, pr, ind0, warp, nwarps, lane, ep);
         __syncthreads();  // shared state (tile, acc_s, a0_s, pr_s) is reused by the next item
     }
 }
@@ -590,6 +614,7 @@ pm_status pm_fitness_init(const pm_instance *inst)
     return PM_OK;
 }
 
+
 // Resident CTAs per SM of the column kernel for (G, warps) at this instance's W.
 static int column_ctas_per_sm(const pm_instance *inst, int G, int warps)
 {
@@ -705,8 +730,8 @@ pm_status pm_launch_scan(const pm_scan_launch &L, const pm_accept_args &acc, int
         PM_CUDA(pm_launch(k_pop_to_columns, (unsigned)blocks, threads, 0, stream, L.masks, L.probs_dev, L.K, L.one,
                           L.jobs, G, L.colT));
     }
-    const unsigned grid = (unsigned)L.grid;
     const int threads = L.warps * 32;
+    const unsigned grid = (unsigned)L.grid;
     unsigned long long *accum = reinterpret_cast<unsigned long long *>(L.accum);
 #define PM_SCAN_ARGS L.probs_dev, L.K, L.one, L.items, L.colT, L.active, accum, L.tickets, L.err, ep
     switch (G) {

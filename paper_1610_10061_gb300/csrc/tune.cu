@@ -125,3 +125,34 @@ extern "C" pm_status pm_tune_eval(pm_instance *inst, int64_t pop, void *stream, 
     }
     return PM_OK;
 }
+
+extern "C" pm_status pm_set_eval_shape(pm_instance *inst, int64_t pop, const pm_eval_shape *shape)
+{
+    if (!inst || !shape || pop < 1 || pop > ((int64_t)1 << 31))
+        return PM_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> guard(inst->lock);
+    PM_CUDA(cudaSetDevice(inst->device));
+    pm_eval_plan pl;
+    if (shape->groups == 0) {
+        pl = pm_plan_eval_with(inst, pop, 0, 8, std::max(0, shape->splits));
+    } else {
+        if (shape->groups != 1 && shape->groups != 2 && shape->groups != 4)
+            return PM_ERR_INVALID_ARG;
+        if (shape->warps < 1 || shape->warps > 32)
+            return PM_ERR_INVALID_ARG;
+        pl = pm_plan_eval_with(inst, pop, shape->groups, shape->warps, std::max(0, shape->splits));
+        if (pl.groups != shape->groups)
+            return PM_ERR_UNSUPPORTED;
+    }
+    // scratch for the new shape (tickets and accumulators start at zero)
+    bool fresh = false;
+    PM_TRY(inst->partials.reserve(pm_plan_partial_bytes(pl, pop), &fresh));
+    if (fresh)
+        PM_CUDA(cudaMemset(inst->partials.ptr, 0, inst->partials.bytes));
+    PM_TRY(inst->tickets.reserve(pm_plan_ticket_bytes(pl), &fresh));
+    if (fresh)
+        PM_CUDA(cudaMemset(inst->tickets.ptr, 0, inst->tickets.bytes));
+    std::lock_guard<std::mutex> g(inst->plan_mu);
+    inst->tuned[pop] = pl;
+    return PM_OK;
+}

@@ -66,6 +66,7 @@ _SIGS = {
     "pm_eval_population_noalloc": ([_P, _P, _I64, _P, _P], _S),
     "pm_selftest_bounded_wait": ([ctypes.c_int, _P], _S),
     "pm_tune_eval": ([_P, _I64, _P, ctypes.POINTER(pm_eval_shape)], _S),
+    "pm_set_eval_shape": ([_P, _I64, ctypes.POINTER(pm_eval_shape)], _S),
     "pm_ga_create": ([_P, ctypes.c_uint64, _I64, ctypes.POINTER(pm_ga_params), _P, _PP], _S),
     "pm_ga_step": ([_P, _I64, _P, _P], _S),
     "pm_ga_result": ([_P, _P, _P, _P, _P, _P], _S),
@@ -186,6 +187,11 @@ def pm_tune_eval(inst, pop: int, stream=None):
     _check(_lib.pm_tune_eval(inst, pop, _stream(stream), ctypes.byref(out)), "pm_tune_eval")
     return dict(groups=out.groups, warps=out.warps, splits=out.splits, grid=out.grid, ms=out.ms,
                 candidates=out.candidates)
+
+
+def pm_set_eval_shape(inst, pop: int, groups: int, warps: int = 16, splits: int = 0):
+    shape = pm_eval_shape(groups, warps, splits, 0, 0.0, 0, 0)
+    _check(_lib.pm_set_eval_shape(inst, pop, ctypes.byref(shape)), "pm_set_eval_shape")
 
 
 def _params(deme=0, xover_rounds=-1, mut_tries=-1, saturation=0, stream_id=0, tune=False, model=None,
@@ -445,6 +451,10 @@ class Instance:
     def tune(self, pop: int, stream=None):
         """Autotune the evaluation tile shape for populations of `pop` (see pm_tune_eval)."""
         return pm_tune_eval(self.handle, int(pop), stream)
+
+    def set_shape(self, pop: int, groups: int, warps: int = 16, splits: int = 0):
+        """Pin the evaluation tile shape for populations of `pop` (see pm_set_eval_shape)."""
+        pm_set_eval_shape(self.handle, int(pop), groups, warps, splits)
 
     def close(self):
         if self.handle:

@@ -177,8 +177,10 @@ def test_full_size_euclid10000_sampled(pm, p):
 # The GA: bit-exact trajectories
 # --------------------------------------------------------------------------
 
-def _ga_compare(pm, d, p, pop, gens, check_every=1, **kw):
+def _ga_compare(pm, d, p, pop, gens, check_every=1, shape=None, **kw):
     inst = pm.Instance(d, p)
+    if shape is not None:
+        inst.set_shape(pop, **shape)
     opi, ode = oracle.tables(d, p)
     m = d.shape[1]
     okw = dict(kw)
@@ -313,3 +315,43 @@ def test_bounded_wait_times_out_and_context_survives(pm):
     inst = pm.Instance(d, 4)
     masks = random_masks(40, 50, 4, seed=2)
     np.testing.assert_array_equal(inst.eval(masks), oracle.eval_direct(d, masks))
+
+
+def _pinned_shapes(pm, inst, pop):
+    """Every evaluation shape (G, warps, splits) this instance accepts, pinned in turn; G = 0 is the row kernel."""
+    for G in (0, 1, 2, 4):
+        for warps in ((8,) if G == 0 else (8, 16, 32)):
+            for splits in (1, 3, 0):
+                try:
+                    inst.set_shape(pop, groups=G, warps=warps, splits=splits)
+                except pm.PMError as e:
+                    assert e.status == 3, e  # PM_ERR_UNSUPPORTED: does not fit
+                    continue
+                yield G, warps, splits
+
+
+@pytest.mark.parametrize("name,d,p", [s for s in _shapes() if s[0] in ("ties", "allzero", "L2", "big31", "graph",
+                                                                       "euclid", "p1")],
+                         ids=["ties", "allzero", "L2", "p1", "big31", "graph", "euclid"])
+def test_every_pinned_shape_bit_exact(pm, name, d, p):
+    """pm_set_eval_shape: each launch shape gives the oracle's costs (ragged populations, 1 or many splits)."""
+    m = d.shape[1]
+    inst = pm.Instance(d, p)
+    for pop in (33, 700):
+        masks = random_masks(pop, m, p, seed=5 * pop + m)
+        expect = oracle.eval_direct(d, masks)
+        seen = 0
+        for G, warps, splits in _pinned_shapes(pm, inst, pop):
+            np.testing.assert_array_equal(inst.eval(masks), expect, err_msg=f"G={G} warps={warps} splits={splits}")
+            seen += 1
+        assert seen >= 10, seen
+    with pytest.raises(pm.PMError):
+        inst.set_shape(64, groups=3, warps=16)
+    inst.close()
+
+
+def test_ga_on_pinned_shapes_matches_oracle(pm):
+    w = paper_shape_instance("graph900")
+    _ga_compare(pm, w["d"], w["p"], 1024, 2, check_every=1, shape=dict(groups=1, warps=8, splits=3))
+    _ga_compare(pm, euclid_instance(77, seed=11), 7, 128, 6, check_every=2, deme=16, seed=5,
+                shape=dict(groups=0, warps=8, splits=2))
