@@ -41,6 +41,9 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="graph900")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tables", default="delta", choices=["delta", "cumulative"],
+                    help="device tables: Delta' (the paper's increments, summed by the scan) or cumulative D' "
+                         "(their running sums, read at the first open rank)")
     ap.add_argument("--mode", default="ga", choices=["ga", "eval"],
                     help="ga: GA generations (default); eval: one fitness evaluation pass of a random population")
     return ap.parse_args()
@@ -251,7 +254,8 @@ def run_ours(args):
     d, p, pop, deme, lg, desc = workload(args.workload)
     n, m = d.shape
     stream = torch.cuda.current_stream()
-    inst = pm.Instance(d, p, device=local, stream=stream.cuda_stream)
+    cum = args.tables == "cumulative"
+    inst = pm.Instance(d, p, device=local, stream=stream.cuda_stream, cumulative=cum)
     shape = inst.tune(pop, stream=stream.cuda_stream)  # autotuned evaluation tile (kept by the instance)
     ga = pm.GA(inst, seed=0, pop=pop, deme=deme, stream_id=rank, stream=stream.cuda_stream)
     info = ga.info()
@@ -326,7 +330,7 @@ def run_ours(args):
         trace = torch.zeros(args.steps, dtype=torch.int64).pin_memory()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        h = pm.pm_instance_create(dh, n, m, p, local, stream.cuda_stream)
+        h = pm.pm_instance_create_ex(dh, n, m, p, local, stream.cuda_stream, pm.PM_TABLES_CUMULATIVE if cum else 0)
         bc, gr, ev = pm.pm_ga_run(h, 0, pop, args.steps, pm._params(deme=deme, stream_id=rank), best_mask, trace,
                                   stream.cuda_stream)
         pm.pm_instance_destroy(h)
@@ -346,7 +350,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": {"workload": args.workload, "description": desc, "n": int(n), "m": int(m), "p": int(p),
+            "config": {"tables": args.tables, "workload": args.workload, "description": desc, "n": int(n), "m": int(m), "p": int(p),
                        "pop": pop, "deme": deme, "xover_rounds": info["xover_rounds"],
                        "mut_tries": info["mut_tries"], "step": "one GA generation (one pm_ga_step graph launch)",
                        "l2": "flushed between timed steps (512 MiB write outside the events)",
@@ -380,12 +384,13 @@ def run_eval_mode(args):
     stream = torch.cuda.current_stream()
     # A1: the table build (radix sort + increments) from a device-resident distance matrix, timed alone
     dd = torch.from_numpy(d).cuda()
-    pm.Instance(dd, p, stream=stream.cuda_stream).close()  # warm-up
+    cum = args.tables == "cumulative"
+    pm.Instance(dd, p, stream=stream.cuda_stream, cumulative=cum).close()  # warm-up
     tb = []
     for _ in range(3):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        tmp = pm.Instance(dd, p, stream=stream.cuda_stream)
+        tmp = pm.Instance(dd, p, stream=stream.cuda_stream, cumulative=cum)
         e1.record(stream)
         torch.cuda.synchronize()
         tb.append(e0.elapsed_time(e1))
@@ -397,7 +402,7 @@ def run_eval_mode(args):
               "note": "pm_instance_create from device d: d >= 0 check, per-row LSD radix sort, Delta' epilogue; "
                       "bytes = d read + Pi'/Delta' written"}
     del dd
-    inst = pm.Instance(d, p, stream=stream.cuda_stream)
+    inst = pm.Instance(d, p, stream=stream.cuda_stream, cumulative=args.tables == "cumulative")
     shape = inst.tune(pop, stream=stream.cuda_stream)
     masks = random_masks(pop, m, p, seed=123)
     dmask = torch.from_numpy(masks.view(np.int32)).cuda()
@@ -429,7 +434,7 @@ def run_eval_mode(args):
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_ms,
             "ms_min": min(ms), "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
             "data": "synthetic",
-            "config": {"workload": args.workload, "n": int(n), "m": int(m), "p": int(p), "pop": pop,
+            "config": {"tables": args.tables, "workload": args.workload, "n": int(n), "m": int(m), "p": int(p), "pop": pop,
                        "step": "pm_eval_population of a uniform random population (device buffers)",
                        "eval_tile": {k: shape[k] for k in ("groups", "warps", "splits", "grid")},
                        "l2": "flushed between timed steps"},
@@ -460,7 +465,7 @@ def run_batched(args):
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
     t0 = time.perf_counter()
-    insts = [pm.Instance(d, p, stream=stream.cuda_stream) for d, p in data]
+    insts = [pm.Instance(d, p, stream=stream.cuda_stream, cumulative=args.tables == "cumulative") for d, p in data]
     tables_s = time.perf_counter() - t0
     batch = pm.Batch(insts)
     pop = 256
@@ -492,7 +497,7 @@ def run_batched(args):
     line = {"metric": METRIC, "value": (e1 - e0) / (ms / 1000), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": {"workload": f"batched{count}: {count} instances, n=m log-uniform [100,5000] "
+            "config": {"tables": args.tables, "workload": f"batched{count}: {count} instances, n=m log-uniform [100,5000] "
                                    f"(min {min(n_sizes)}, max {max(n_sizes)}), p U[5,n/10], half graph (4n edges, "
                                    "APSP) half Euclidean; pop 256 each in one deme; one launch per kernel per "
                                    "generation covers all instances",
@@ -529,7 +534,7 @@ def run_learned(args):
     w = paper_shape_instance(name)
     d, p, pop = w["d"], w["p"], w["pop"]
     n, m = d.shape
-    inst = pm.Instance(d, p, stream=stream.cuda_stream)
+    inst = pm.Instance(d, p, stream=stream.cuda_stream, cumulative=args.tables == "cumulative")
     inst.tune(pop, stream=stream.cuda_stream)
     budget = args.steps
 
@@ -597,7 +602,7 @@ def run_learned(args):
     line = {"metric": "time-to-target cost, learned vs plain GA", "value": lt, "unit": "s",
             "higher_is_better": False, "n_gpus": 1, "steps": budget, "warmup": 0, "vs_baseline": None,
             "dtype": "int64 (costs); bf16/fp32 (model)", "data": "synthetic",
-            "config": {"workload": f"{name}: clustered Euclidean n=m={n}, 50 components sigma 0.02, p={p}, "
+            "config": {"tables": args.tables, "workload": f"{name}: clustered Euclidean n=m={n}, 50 components sigma 0.02, p={p}, "
                                    f"pop {pop} in demes of 256; target = plain GA (seed 0) best after {budget} "
                                    "generations; each arm may run up to 4x that; seeds 0-4, medians",
                        "target": target, "train_tuples": int(X.shape[0]), "train_epochs": 6,

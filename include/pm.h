@@ -87,6 +87,22 @@ typedef struct pm_instance pm_instance;
 PM_API pm_status pm_instance_create(const int32_t *d, int64_t n, int64_t m, int64_t p, int device, void *stream,
                              pm_instance **out);
 
+/*
+ * pm_instance_create_ex -- pm_instance_create with flags.
+ * PM_TABLES_CUMULATIVE: the instance keeps D'_i = the running sums of
+ * Delta'_i (the sorted distances themselves) in place of Delta'_i.  The
+ * scan's result is the same integer (by Eq. 4 the Delta' terms up to the
+ * first open rank add up to the distance there); the evaluation reads that
+ * value instead of summing, so a 32-rank step needs no warp prefix sum and
+ * no carry.  No counterpart in the paper, which sums Delta' (Section 4.2).
+ * pm_instance_tables still returns Delta'.  Other flags: PM_ERR_INVALID_ARG.
+ */
+#define PM_TABLES_CUMULATIVE 1u
+PM_API pm_status pm_instance_create_ex(const int32_t *d, int64_t n, int64_t m, int64_t p, int device, void *stream,
+                                       uint32_t flags, pm_instance **out);
+/* The flags the instance was created with. */
+PM_API pm_status pm_instance_flags(const pm_instance *inst, uint32_t *flags);
+
 /* Release an instance and its device tables (NULL is accepted). */
 PM_API pm_status pm_instance_destroy(pm_instance *inst);
 
@@ -213,13 +229,21 @@ typedef struct pm_ga_params {
     int32_t mut_tries;    /* mutation tries per generation; < 0 = lg D (Section 3.2.2, step 5) */
     int64_t saturation;   /* S: stop when the best has not improved for S generations; 0 = off */
     uint32_t stream_id;   /* fourth word of every random-number counter (independent runs) */
-    uint32_t flags;       /* PM_GA_TUNE: run pm_tune_eval for this population size at creation */
+    uint32_t flags;       /* PM_GA_TUNE: run pm_tune_eval for this population size at creation;
+                             PM_GA_MIGRATE_TEAM: migration variant (ii) of Section 4.5 */
     struct pm_model *model;  /* learned swap proposal (see pm_model_create); NULL = the paper's GA only */
     int32_t candidates;      /* learned try: closed facilities (by gain) paired with every open one; <= 0: 4 */
     int32_t reserved;        /* must be 0 */
 } pm_ga_params;
 
 #define PM_GA_TUNE 1u
+/* Migration (Section 4.5).  Default, variant (i): from the second generation
+ * on, slot 0 of deme b receives deme b's best of the previous generation.
+ * PM_GA_MIGRATE_TEAM, variant (ii), where the bests of all demes travel
+ * together into one deme: deme 0 receives them, deme b's best into slot b
+ * (needs pop/deme <= deme, else PM_ERR_INVALID_ARG); every other individual
+ * is drawn afresh. */
+#define PM_GA_MIGRATE_TEAM 2u
 
 typedef struct pm_ga pm_ga;
 typedef struct pm_model pm_model;

@@ -78,7 +78,7 @@ def _load():
     lib.oracle_crossover_params.restype = None
     lib.oracle_swap_stats.argtypes = [P, P, I64, I64, I64, P, I64, I64, P, P, P, P]
     lib.oracle_ga_run.argtypes = [P, P, I64, I64, I64, U64, U32, I64, I64, ctypes.c_int32, ctypes.c_int32,
-                                  I64, I64, P, P, P, P, P, P, P, P]
+                                  I64, I64, P, P, P, P, P, P, P, P, ctypes.c_int32]
     _lib = lib
     return lib
 
@@ -149,6 +149,27 @@ def eval_scan(pi: np.ndarray, delta: np.ndarray, masks: np.ndarray, return_ksum:
     _check(_load().oracle_eval_scan(_ptr(pi), _ptr(delta), n, L, _ptr(masks), W, P, _ptr(out), _ptr(ks)),
            "eval_scan")
     return (out, int(ks[0])) if return_ksum else out
+
+
+def cumulative(delta: np.ndarray) -> np.ndarray:
+    """D' = the running sums of Delta' along each row (Eq. 4): D'_i[k] = sum_{s <= k} Delta'_i[s]."""
+    return np.cumsum(np.asarray(delta, dtype=np.int64), axis=1)
+
+
+def eval_cumulative(pi: np.ndarray, dcum: np.ndarray, masks: np.ndarray) -> np.ndarray:
+    """O3 over cumulative tables: per client, D' at the first rank whose facility is open (no summing)."""
+    pi = np.asarray(pi)
+    dcum = np.asarray(dcum, dtype=np.int64)
+    masks = np.ascontiguousarray(masks, dtype=np.uint32)
+    n, L = pi.shape
+    out = np.zeros(masks.shape[0], dtype=np.int64)
+    for t, row in enumerate(masks):
+        open_ = ((row[pi.astype(np.int64) >> 5] >> (pi.astype(np.uint32) & 31)) & 1).astype(bool)  # n x L
+        first = open_.argmax(axis=1)
+        if not open_[np.arange(n), first].all():
+            raise RuntimeError("a client has no open facility within the truncated row")
+        out[t] = int(dcum[np.arange(n), first].sum())
+    return out
 
 
 def hbp_polynomial(pi: np.ndarray, delta: np.ndarray) -> dict:
@@ -271,8 +292,10 @@ class GAState:
 
 def ga_run(pi, delta, m: int, p: int, seed: int, P: int, D: int | None = None, gens: int = 1,
            xover_rounds: int | None = None, mut_tries: int | None = None, saturation: int = 0,
-           state: GAState | None = None, record: bool = False, inst: int = 0):
+           state: GAState | None = None, record: bool = False, inst: int = 0, team: bool = False):
     """Run the reference GA for `gens` generations (Sections 3.1, 3.2.2, 4.5).
+
+    team=True selects migration variant (ii) of Section 4.5 (all deme bests into deme 0).
 
     Returns (state, trace, pops, costs); pops/costs are per-generation copies
     of the population after mutation when record=True.
@@ -292,7 +315,7 @@ def ga_run(pi, delta, m: int, p: int, seed: int, P: int, D: int | None = None, g
     ran = np.zeros(1, dtype=np.int64)
     rc = _load().oracle_ga_run(_ptr(pi), _ptr(delta), n, m, p, seed, inst, P, D, xover_rounds, mut_tries, gens,
                                saturation, _ptr(st.deme_best), _ptr(st.deme_cost), _ptr(st.best), _ptr(st.scalars),
-                               _ptr(pops), _ptr(costs), _ptr(trace), _ptr(ran))
+                               _ptr(pops), _ptr(costs), _ptr(trace), _ptr(ran), 1 if team else 0)
     _check(rc, "ga_run")
     k = int(ran[0])
     trace = trace[:k]

@@ -387,10 +387,12 @@ static int ilog2_exact(int64_t v)
 int oracle_ga_run(const uint16_t *pi, const int32_t *delta, int64_t n, int64_t m, int64_t p, uint64_t seed,
                   uint32_t inst, int64_t P, int64_t D, int32_t xover_rounds, int32_t mut_tries, int64_t gens,
                   int64_t S, uint32_t *deme_best, int64_t *deme_cost, uint32_t *best, int64_t *scalars,
-                  uint32_t *pop_out, int64_t *cost_out, int64_t *trace, int64_t *gens_run)
+                  uint32_t *pop_out, int64_t *cost_out, int64_t *trace, int64_t *gens_run, int32_t team)
 {
     int lgD = ilog2_exact(D);
     if (n < 1 || p < 1 || p >= m || D < 2 || lgD < 0 || P < D || P % D != 0 || xover_rounds < 0 || mut_tries < 0)
+        return OR_ERR_ARG;
+    if (team && P / D > D)
         return OR_ERR_ARG;
     ga_inst I = {pi, delta, n, m, p, m - p + 1, (m + 31) / 32};
     const int64_t W = I.W, NB = P / D;
@@ -410,10 +412,14 @@ int oracle_ga_run(const uint16_t *pi, const int32_t *delta, int64_t n, int64_t m
     int64_t ran = 0;
     for (int64_t gi = 0; gi < gens; ++gi) {
         const uint32_t g = (uint32_t)(g0 + gi);
-        /* new population; migration variant (i) into slot 0 of each deme */
+        /* new population and migration (Section 4.5): variant (i) copies deme b's best of the previous
+           generation into slot 0 of deme b; variant (ii) (team) copies every deme's best into deme 0,
+           deme b's into slot b */
         for (int64_t t = 0; t < P; ++t) {
-            if (g > 0 && t % D == 0)
+            if (g > 0 && !team && t % D == 0)
                 memcpy(X + t * W, deme_best + (t / D) * W, (size_t)W * sizeof(uint32_t));
+            else if (g > 0 && team && t < NB)
+                memcpy(X + t * W, deme_best + t * W, (size_t)W * sizeof(uint32_t));
             else
                 floyd_philox(m, p, seed, g, (uint32_t)t, inst, X + t * W, tmp);
         }

@@ -140,13 +140,13 @@ static pm_status create_impl(const int32_t *d, int64_t n, int64_t m, int64_t p, 
     return PM_OK;
 }
 
-extern "C" pm_status pm_instance_create(const int32_t *d, int64_t n, int64_t m, int64_t p, int device, void *stream,
-                                        pm_instance **out)
+extern "C" pm_status pm_instance_create_ex(const int32_t *d, int64_t n, int64_t m, int64_t p, int device,
+                                           void *stream, uint32_t flags, pm_instance **out)
 {
     if (!out)
         return PM_ERR_INVALID_ARG;
     *out = nullptr;
-    if (!d || n < 1 || m < 2 || p < 1 || p >= m || device < 0)
+    if (!d || n < 1 || m < 2 || p < 1 || p >= m || device < 0 || (flags & ~PM_TABLES_CUMULATIVE) != 0)
         return PM_ERR_INVALID_ARG;
     if (m > 65535)
         return PM_ERR_UNSUPPORTED;
@@ -155,12 +155,27 @@ extern "C" pm_status pm_instance_create(const int32_t *d, int64_t n, int64_t m, 
     pm_instance *inst = new (std::nothrow) pm_instance();
     if (!inst)
         return PM_ERR_OOM;
+    inst->cum = (flags & PM_TABLES_CUMULATIVE) != 0;
     pm_status st = create_impl(d, n, m, p, device, static_cast<cudaStream_t>(stream), inst);
     if (st != PM_OK) {
         destroy_instance(inst);
         return st;
     }
     *out = inst;
+    return PM_OK;
+}
+
+extern "C" pm_status pm_instance_create(const int32_t *d, int64_t n, int64_t m, int64_t p, int device, void *stream,
+                                        pm_instance **out)
+{
+    return pm_instance_create_ex(d, n, m, p, device, stream, 0u, out);
+}
+
+extern "C" pm_status pm_instance_flags(const pm_instance *inst, uint32_t *flags)
+{
+    if (!inst || !flags)
+        return PM_ERR_INVALID_ARG;
+    *flags = inst->cum ? PM_TABLES_CUMULATIVE : 0u;
     return PM_OK;
 }
 
@@ -199,9 +214,25 @@ extern "C" pm_status pm_instance_tables(const pm_instance *inst, uint16_t *pi_ou
     if (pi_out)
         PM_CUDA(cudaMemcpy2DAsync(pi_out, inst->L * sizeof(uint16_t), inst->pi, inst->stride * sizeof(uint16_t),
                                   inst->L * sizeof(uint16_t), inst->n, cudaMemcpyDefault, s));
-    if (delta_out)
+    if (delta_out && !inst->cum)
         PM_CUDA(cudaMemcpy2DAsync(delta_out, inst->L * sizeof(int32_t), inst->delta, inst->stride * sizeof(int32_t),
                                   inst->L * sizeof(int32_t), inst->n, cudaMemcpyDefault, s));
+    if (delta_out && inst->cum) {
+        // the instance holds D': its consecutive differences are Delta'
+        const size_t bytes = (size_t)inst->n * (size_t)inst->L * sizeof(int32_t);
+        if (pm_is_device_ptr(delta_out)) {
+            PM_TRY(pm_launch_increments(inst, delta_out, s));
+        } else {
+            int32_t *tmp = nullptr;
+            PM_CUDA(cudaMallocAsync(reinterpret_cast<void **>(&tmp), bytes, s));
+            pm_status st = pm_launch_increments(inst, tmp, s);
+            cudaError_t e = st == PM_OK ? cudaMemcpyAsync(delta_out, tmp, bytes, cudaMemcpyDeviceToHost, s)
+                                        : cudaSuccess;
+            cudaFreeAsync(tmp, s);
+            PM_TRY(st);
+            PM_CUDA(e);
+        }
+    }
     PM_CUDA(cudaStreamSynchronize(s));
     return PM_OK;
 }

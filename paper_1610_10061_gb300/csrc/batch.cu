@@ -69,6 +69,7 @@ pm_status pm_plan_multi(const std::vector<const pm_instance *> &insts, const std
         pr.W = (int32_t)in->W;
         pr.m = (int32_t)in->m;
         pr.p = (int32_t)in->p;
+        pr.cum = in->cum ? 1 : 0;
         pr.pop = pops[k];
         pr.tiles = std::max<int64_t>(1, pm_ceil_div(pops[k], 32 * G));
         const double want_items = total > 0 ? target_items * work[k] / total : 1.0;

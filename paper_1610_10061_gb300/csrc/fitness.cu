@@ -158,9 +158,13 @@ __global__ void k_pop_to_columns(const uint32_t *__restrict__ masks, const pm_pr
 // of client cc (Pi' and Delta', zeros past the row or past c_end); the
 // caller passes the first two steps of client c and the first step of client
 // c + step already loaded.
+//
+// With cumulative tables (cum) the row holds D' -- the running sums of Delta',
+// i.e. the sorted distances -- so a step needs neither the carry nor the warp
+// scan: the value at the first open rank is the term itself (Eq. 4 summed).
 template <int G, typename Ld>
 __device__ __forceinline__ void scan_clients(const uint32_t *__restrict__ colbits, const uint32_t (&a0)[G], int64_t c,
-                                             int64_t c_end, int step, int32_t L, int lane, Ld &load,
+                                             int64_t c_end, int step, int32_t L, int lane, bool cum, Ld &load,
                                              uint32_t j_cur, int32_t d_cur, uint32_t j_nxt, int32_t d_nxt,
                                              uint32_t j_nc, int32_t d_nc, unsigned long long (&acc)[G])
 {
@@ -186,18 +190,21 @@ __device__ __forceinline__ void scan_clients(const uint32_t *__restrict__ colbit
             hit |= w[g];
         }
         if (!__any_sync(PM_FULL_MASK, hit != 0u)) {
-            carry += __reduce_add_sync(PM_FULL_MASK, d_cur);
+            if (!cum)
+                carry += __reduce_add_sync(PM_FULL_MASK, d_cur);
         } else {
             // running sum of Delta' up to this lane's rank = the sorted distance at that rank
             int32_t cs = d_cur;
+            if (!cum) {
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int32_t y = __shfl_up_sync(PM_FULL_MASK, cs, o);
-                if (lane >= o)
-                    cs += y;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int32_t y = __shfl_up_sync(PM_FULL_MASK, cs, o);
+                    if (lane >= o)
+                        cs += y;
+                }
+                cs += carry;
+                carry = __shfl_sync(PM_FULL_MASK, cs, 31);
             }
-            cs += carry;
-            carry = __shfl_sync(PM_FULL_MASK, cs, 31);
 #pragma unroll
             for (int g = 0; g < G; ++g) {
                 uint32_t hl = __ballot_sync(PM_FULL_MASK, w[g] != 0u);
@@ -413,7 +420,8 @@ __global__ void __launch_bounds__(1024) k_scan_columns(const pm_prob *__restrict
             acc[g] = 0ull;
 
         if (any0 && c < c_end)
-            scan_clients<G>(colbits, a0, c, c_end, nwarps, L, lane, load, j_cur, d_cur, j_nxt, d_nxt, j_nc, d_nc, acc);
+            scan_clients<G>(colbits, a0, c, c_end, nwarps, L, lane, pr.cum != 0, load, j_cur, d_cur, j_nxt, d_nxt, j_nc,
+                            d_nc, acc);
 #pragma unroll
         for (int g = 0; g < G; ++g)
             if (acc[g])
@@ -464,7 +472,7 @@ __global__ void __launch_bounds__(256) k_scan_rows(const uint16_t *__restrict__ 
                                                    int64_t n, int32_t L, int64_t stride,
                                                    const uint32_t *__restrict__ masks, int32_t W, int64_t pop,
                                                    const uint32_t *__restrict__ active, int64_t clients_per_split,
-                                                   unsigned long long *__restrict__ partial)
+                                                   int cum, unsigned long long *__restrict__ partial)
 {
     pm_grid_dependency_wait();
     extern __shared__ __align__(16) uint32_t rowbits[];  // [warps][W]
@@ -499,17 +507,20 @@ __global__ void __launch_bounds__(256) k_scan_rows(const uint16_t *__restrict__ 
             const bool open = (r < L) && ((x[j >> 5] >> (j & 31)) & 1u);
             const uint32_t hit = __ballot_sync(PM_FULL_MASK, open);
             if (!hit) {
-                carry += __reduce_add_sync(PM_FULL_MASK, dl);
+                if (!cum)
+                    carry += __reduce_add_sync(PM_FULL_MASK, dl);
                 continue;
             }
-            int32_t cs = dl;
+            int32_t cs = dl;  // cumulative tables: already the running sum
+            if (!cum) {
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int32_t y = __shfl_up_sync(PM_FULL_MASK, cs, o);
-                if (lane >= o)
-                    cs += y;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int32_t y = __shfl_up_sync(PM_FULL_MASK, cs, o);
+                    if (lane >= o)
+                        cs += y;
+                }
+                cs += carry;
             }
-            cs += carry;
             acc += (unsigned long long)(uint32_t)__shfl_sync(PM_FULL_MASK, cs, __ffs(hit) - 1);
             break;
         }
@@ -702,6 +713,7 @@ pm_prob pm_single_prob(const pm_instance *inst, const pm_eval_plan &plan, int64_
     pr.W = (int32_t)inst->W;
     pr.m = (int32_t)inst->m;
     pr.p = (int32_t)inst->p;
+    pr.cum = inst->cum ? 1 : 0;
     pr.pop = pop;
     pr.tiles = plan.tiles;
     pr.splits = plan.splits;
@@ -784,7 +796,8 @@ pm_status pm_launch_eval(const pm_instance *inst, const pm_eval_plan &plan, cons
     const size_t smem = (size_t)plan.warps * inst->W * 4;
     dim3 grid((unsigned)plan.tiles, (unsigned)plan.splits);
     PM_CUDA(pm_launch(k_scan_rows, grid, plan.warps * 32, smem, stream, inst->pi, inst->delta, inst->n,
-                      (int32_t)inst->L, inst->stride, masks, (int32_t)inst->W, pop, active, cps, partials));
+                      (int32_t)inst->L, inst->stride, masks, (int32_t)inst->W, pop, active, cps, inst->cum ? 1 : 0,
+                      partials));
     const int64_t threads = 256;
     const int64_t blocks = pm_ceil_div(pop * 32, threads);
     PM_CUDA(pm_launch(k_reduce_accept, (unsigned)blocks, (unsigned)threads, 0, stream, partials, plan.splits, pop,

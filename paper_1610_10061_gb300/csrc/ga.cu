@@ -88,7 +88,8 @@ struct ga_prob {  // per instance layout of the GA arrays
     int64_t dword_base;  // deme_best rows
     int64_t best_base;   // best bitset
     int64_t col_base;    // facility-major tiles
-    uint32_t sid, pad;
+    uint32_t sid;
+    uint32_t team;  // migration variant (ii): all deme bests into deme 0
 };
 
 // ----------------------------- Philox4x32-10 --------------------------------
@@ -231,8 +232,11 @@ __global__ void __launch_bounds__(32) k_ga_init(const ga_prob *__restrict__ gps,
     uint32_t *row = rows_in_smem ? rows_s + (int64_t)lane * Ws : X + gp.word_base + t * W;
     if (t < gp.pop) {
         improved[gp.ind_base + t] = 0;
-        if (gen > 0 && (t % gp.D) == 0) {
-            const uint32_t *src = deme_best + gp.dword_base + (t / gp.D) * W;
+        // migration (Section 4.5): variant (i) puts deme b's best of the previous generation into slot 0 of
+        // deme b; variant (ii) puts all of them into deme 0, deme b's best into slot b
+        const bool migrant = gen > 0 && (gp.team ? t < gp.NB : (t % gp.D) == 0);
+        if (migrant) {
+            const uint32_t *src = deme_best + gp.dword_base + (gp.team ? t : t / gp.D) * W;
             for (int w = 0; w < W; ++w)
                 row[w] = src[w];
         } else {
@@ -751,6 +755,7 @@ struct pm_ga {
     int lgD = 0, R = 0, Q = 0;
     int64_t S = 0;
     uint32_t sid = 0;
+    bool team = false;  // migration variant (ii)
     bool single_row = false;  // one instance whose evaluation uses the row kernel
     pm_eval_plan single;      // K == 1: the single-instance plan
     pm_multi_plan plan;       // the scan plan over all instances
@@ -949,6 +954,7 @@ static pm_status ga_alloc(pm_ga *ga, cudaStream_t s)
         gp.dword_base = dwords;
         gp.best_base = bestw;
         gp.sid = ga->sid + (uint32_t)k;
+        gp.team = ga->team ? 1u : 0u;
         grp += pm_ceil_div(ga->P, 32);
         deme += ga->NB;
         dwords += ga->NB * in->W;
@@ -1010,7 +1016,7 @@ static pm_status ga_configure(pm_ga *ga, int64_t pop, uint64_t seed, const pm_ga
     prm.mut_tries = -1;
     if (params)
         prm = *params;
-    if ((prm.flags & ~PM_GA_TUNE) != 0 || prm.reserved != 0)
+    if ((prm.flags & ~(PM_GA_TUNE | PM_GA_MIGRATE_TEAM)) != 0 || prm.reserved != 0)
         return PM_ERR_INVALID_ARG;
     ga->model = prm.model;
     ga->T = prm.candidates > 0 ? prm.candidates : 4;
@@ -1035,6 +1041,9 @@ static pm_status ga_configure(pm_ga *ga, int64_t pop, uint64_t seed, const pm_ga
         return PM_ERR_INVALID_ARG;
     ga->S = prm.saturation;
     ga->sid = prm.stream_id;
+    ga->team = (prm.flags & PM_GA_MIGRATE_TEAM) != 0;
+    if (ga->team && ga->NB > D)
+        return PM_ERR_INVALID_ARG;  // deme 0 cannot hold every deme's best
     return PM_OK;
 }
 
@@ -1237,6 +1246,8 @@ struct ga_header {
     char magic[8];
     uint32_t version;
     uint32_t sid;
+    uint32_t flags;  // PM_GA_MIGRATE_TEAM
+    uint32_t pad;
     int64_t n, m, p, P, D, R, Q, S;
     uint64_t seed;
     ga_dev state;
@@ -1265,9 +1276,10 @@ extern "C" pm_status pm_ga_save(pm_ga *ga, void *buf, size_t *len, void *stream)
     const pm_instance *inst = ga->insts[0];
     PM_CUDA(cudaSetDevice(inst->device));
     ga_header h = {};
-    std::memcpy(h.magic, "PMGASAV2", 8);
-    h.version = 2;
+    std::memcpy(h.magic, "PMGASAV3", 8);
+    h.version = 3;
     h.sid = ga->sid;
+    h.flags = ga->team ? PM_GA_MIGRATE_TEAM : 0u;
     h.n = inst->n;
     h.m = inst->m;
     h.p = inst->p;
@@ -1303,7 +1315,7 @@ extern "C" pm_status pm_ga_load(pm_instance *inst, const void *buf, size_t len, 
     *out = nullptr;
     ga_header h;
     std::memcpy(&h, buf, sizeof(h));
-    if (std::memcmp(h.magic, "PMGASAV2", 8) != 0 || h.version != 2 || h.n != inst->n || h.m != inst->m ||
+    if (std::memcmp(h.magic, "PMGASAV3", 8) != 0 || h.version != 3 || h.n != inst->n || h.m != inst->m ||
         h.p != inst->p)
         return PM_ERR_INVALID_ARG;
     pm_ga_params prm = {};
@@ -1312,6 +1324,7 @@ extern "C" pm_status pm_ga_load(pm_instance *inst, const void *buf, size_t len, 
     prm.mut_tries = (int32_t)h.Q;
     prm.saturation = h.S;
     prm.stream_id = h.sid;
+    prm.flags = h.flags & PM_GA_MIGRATE_TEAM;
     pm_ga *ga = nullptr;
     PM_TRY(pm_ga_create(inst, h.seed, h.P, &prm, stream, &ga));
     if (len < ga_blob_size(ga)) {

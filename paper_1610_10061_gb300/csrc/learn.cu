@@ -627,7 +627,7 @@ __global__ void __launch_bounds__(1024) k_swap_stats(const uint16_t *__restrict_
                                                      const uint32_t *__restrict__ masks, int64_t pop,
                                                      unsigned long long *__restrict__ gain, int *__restrict__ cap,
                                                      unsigned long long *__restrict__ loss, int *__restrict__ assign,
-                                                     int in_smem)
+                                                     int in_smem, int cum)
 {
     extern __shared__ __align__(16) unsigned char sm[];
     const int64_t t = blockIdx.x;
@@ -666,21 +666,28 @@ __global__ void __launch_bounds__(1024) k_swap_stats(const uint16_t *__restrict_
             if (r < L) {
                 j = __ldg(prow + r);
                 dl = __ldg(drow + r);
+            } else if (cum) {
+                dl = __ldg(drow + L - 1);  // past the row the running sum stays at its last value
             }
             const bool open = (r < L) && ((bits[j >> 5] >> (j & 31)) & 1u);
             uint32_t bal = __ballot_sync(PM_FULL_MASK, open);
             if (bal == 0u && found == 0) {  // no open facility among these 32 ranks: only the carry moves
-                carry += __reduce_add_sync(PM_FULL_MASK, dl);
+                if (!cum)
+                    carry += __reduce_add_sync(PM_FULL_MASK, dl);
+                else
+                    carry = __shfl_sync(PM_FULL_MASK, dl, 31);
                 continue;
             }
-            int32_t cs = dl;
+            int32_t cs = dl;  // cumulative tables: already the running sum
+            if (!cum) {
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int32_t y = __shfl_up_sync(PM_FULL_MASK, cs, o);
-                if (lane >= o)
-                    cs += y;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int32_t y = __shfl_up_sync(PM_FULL_MASK, cs, o);
+                    if (lane >= o)
+                        cs += y;
+                }
+                cs += carry;
             }
-            cs += carry;
             if (found == 0 && bal) {
                 const int f = __ffs(bal) - 1;
                 d1 = __shfl_sync(PM_FULL_MASK, cs, f);
@@ -717,13 +724,15 @@ __global__ void __launch_bounds__(1024) k_swap_stats(const uint16_t *__restrict_
                 dl = __ldg(drow + r);
             }
             int32_t cs = dl;
+            if (!cum) {
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int32_t y = __shfl_up_sync(PM_FULL_MASK, cs, o);
-                if (lane >= o)
-                    cs += y;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int32_t y = __shfl_up_sync(PM_FULL_MASK, cs, o);
+                    if (lane >= o)
+                        cs += y;
+                }
+                cs += carry;
             }
-            cs += carry;
             if (r < r1) {
                 if (in_smem)
                     atomicAdd(Gs + j, (Acc)(uint32_t)(d1 - cs));
@@ -1326,7 +1335,7 @@ pm_status pm_launch_swap_stats(const pm_instance *inst, const uint32_t *masks, i
 #define PM_STATS_ARGS                                                                                              \
     inst->pi, inst->delta, inst->n, (int32_t)inst->L, inst->stride, (int32_t)inst->W, (int32_t)inst->m, masks, pop, \
         reinterpret_cast<unsigned long long *>(gain), cap, reinterpret_cast<unsigned long long *>(loss), assign,     \
-        in_smem ? 1 : 0
+        in_smem ? 1 : 0, inst->cum ? 1 : 0
     if (narrow && in_smem)
         k_swap_stats<unsigned int><<<(unsigned)pop, 1024, smem, s>>>(PM_STATS_ARGS);
     else

@@ -61,9 +61,10 @@ struct pm_eval_plan {
 // instance k are item_base .. item_base + tiles * splits - 1 (split-major).
 struct pm_prob {
     const uint16_t *pi;
-    const int32_t *delta;
+    const int32_t *delta;  // Delta', or D' (running sums) when cum
     int64_t n, stride;
     int32_t L, W, m, p;
+    int32_t cum, pad;
     int64_t pop;
     int64_t ind_base;   // accumulators, active bits, GA per-individual arrays
     int64_t out_base;   // caller's cost array
@@ -116,6 +117,7 @@ struct pm_instance {
     int device = 0;
     int64_t n = 0, m = 0, p = 0, L = 0, W = 0, stride = 0;
     int32_t max_d = 0;
+    bool cum = false;           // PM_TABLES_CUMULATIVE: delta holds D' (running sums of Delta') instead
     uint16_t *pi = nullptr;     // n x stride, Pi' (0-based facility ids)
     int32_t *delta = nullptr;   // n x stride, Delta'
     int sm_count = 0;
@@ -221,6 +223,8 @@ void pm_scan_launch_from(const pm_multi_plan &mp, const pm_prob *probs_dev, pm_s
 // Tables (tables.cu)
 // ---------------------------------------------------------------------------
 pm_status pm_build_tables(pm_instance *inst, const int32_t *d_dev, cudaStream_t stream);
+// Delta' of a cumulative instance (differences of its D' rows) into out (n x L, device).
+pm_status pm_launch_increments(const pm_instance *inst, int32_t *out, cudaStream_t stream);
 
 // ---------------------------------------------------------------------------
 // Small helpers

@@ -56,7 +56,7 @@ __global__ void k_minmax_init(int *out)
 }
 
 __global__ void __launch_bounds__(kSortThreads) k_tables(const int32_t *__restrict__ d, int64_t n, int32_t m,
-                                                         int32_t L, int64_t stride, int passes,
+                                                         int32_t L, int64_t stride, int passes, int cum,
                                                          uint16_t *__restrict__ pi, int32_t *__restrict__ delta,
                                                          unsigned char *__restrict__ gscratch)
 {
@@ -164,13 +164,14 @@ __global__ void __launch_bounds__(kSortThreads) k_tables(const int32_t *__restri
             vin = vout;
             vout = tv;
         }
-        // epilogue: Pi' and Delta' (rank 0: the distance itself)
+        // epilogue: Pi' and Delta' (rank 0: the distance itself), or D' (the sorted distances, which are the
+        // running sums of Delta') for cumulative tables
         uint16_t *prow = pi + row * stride;
         int32_t *qrow = delta + row * stride;
         for (int r = threadIdx.x; r < stride; r += blockDim.x) {
             if (r < L) {
                 prow[r] = vin[r];
-                qrow[r] = (int32_t)(kin[r] - (r > 0 ? kin[r - 1] : 0u));
+                qrow[r] = cum ? (int32_t)kin[r] : (int32_t)(kin[r] - (r > 0 ? kin[r - 1] : 0u));
             } else {
                 prow[r] = 0;
                 qrow[r] = 0;
@@ -180,7 +181,30 @@ __global__ void __launch_bounds__(kSortThreads) k_tables(const int32_t *__restri
     }
 }
 
+// Delta' = consecutive differences of D' (rank 0: the value itself), n x L dense rows.
+__global__ void k_increments(const int32_t *__restrict__ dcum, int64_t n, int32_t L, int64_t stride,
+                             int32_t *__restrict__ out)
+{
+    const int64_t total = n * (int64_t)L;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = k / L;
+        const int32_t r = (int32_t)(k - i * L);
+        const int32_t v = dcum[i * stride + r];
+        out[k] = r ? v - dcum[i * stride + r - 1] : v;
+    }
+}
+
 }  // namespace
+
+pm_status pm_launch_increments(const pm_instance *inst, int32_t *out, cudaStream_t stream)
+{
+    const int64_t total = inst->n * inst->L;
+    const int64_t blocks = std::min<int64_t>(pm_ceil_div(total, 256), (int64_t)inst->sm_count * 16);
+    k_increments<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, stream>>>(inst->delta, inst->n, (int32_t)inst->L,
+                                                                             inst->stride, out);
+    PM_CUDA(cudaGetLastError());
+    return PM_OK;
+}
 
 static int bits_needed(uint32_t v)
 {
@@ -226,7 +250,8 @@ pm_status pm_build_tables(pm_instance *inst, const int32_t *d_dev, cudaStream_t 
         PM_CUDA(cudaMallocAsync(reinterpret_cast<void **>(&gscratch), (size_t)grid * row_bytes, stream));
     }
     k_tables<<<(unsigned)grid, kSortThreads, dyn, stream>>>(d_dev, inst->n, (int32_t)inst->m, (int32_t)inst->L,
-                                                           inst->stride, passes, inst->pi, inst->delta, gscratch);
+                                                           inst->stride, passes, inst->cum ? 1 : 0, inst->pi,
+                                                           inst->delta, gscratch);
     cudaError_t le = cudaGetLastError();
     if (gscratch)
         cudaFreeAsync(gscratch, stream);

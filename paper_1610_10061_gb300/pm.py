@@ -49,6 +49,8 @@ class pm_eval_shape(ctypes.Structure):
 
 
 PM_GA_TUNE = 1
+PM_TABLES_CUMULATIVE = 1
+PM_GA_MIGRATE_TEAM = 2
 
 
 _P = ctypes.c_void_p
@@ -59,6 +61,8 @@ _S = ctypes.c_int
 _SIGS = {
     "pm_strerror": ([_S], ctypes.c_char_p),
     "pm_instance_create": ([_P, _I64, _I64, _I64, ctypes.c_int, _P, _PP], _S),
+    "pm_instance_create_ex": ([_P, _I64, _I64, _I64, ctypes.c_int, _P, ctypes.c_uint32, _PP], _S),
+    "pm_instance_flags": ([_P, ctypes.POINTER(ctypes.c_uint32)], _S),
     "pm_instance_destroy": ([_P], _S),
     "pm_instance_info": ([_P, _P, _P, _P, _P, _P, _P], _S),
     "pm_instance_tables": ([_P, _P, _P, _P], _S),
@@ -153,6 +157,19 @@ def pm_instance_create(d, n: int, m: int, p: int, device: int = 0, stream=None):
     return out
 
 
+def pm_instance_create_ex(d, n: int, m: int, p: int, device: int = 0, stream=None, flags: int = 0):
+    out = ctypes.c_void_p()
+    _check(_lib.pm_instance_create_ex(_addr(d), n, m, p, device, _stream(stream), flags, ctypes.byref(out)),
+           "pm_instance_create_ex")
+    return out
+
+
+def pm_instance_flags(inst) -> int:
+    out = ctypes.c_uint32()
+    _check(_lib.pm_instance_flags(inst, ctypes.byref(out)), "pm_instance_flags")
+    return int(out.value)
+
+
 def pm_instance_destroy(inst):
     _check(_lib.pm_instance_destroy(inst), "pm_instance_destroy")
 
@@ -195,9 +212,12 @@ def pm_set_eval_shape(inst, pop: int, groups: int, warps: int = 16, splits: int 
 
 
 def _params(deme=0, xover_rounds=-1, mut_tries=-1, saturation=0, stream_id=0, tune=False, model=None,
-            candidates=0):
+            candidates=0, migration="deme"):
+    if migration not in ("deme", "team"):
+        raise ValueError("migration is 'deme' (variant (i)) or 'team' (variant (ii))")
     mh = model.handle if isinstance(model, Model) else model
-    return pm_ga_params(deme, xover_rounds, mut_tries, saturation, stream_id, PM_GA_TUNE if tune else 0,
+    flags = (PM_GA_TUNE if tune else 0) | (PM_GA_MIGRATE_TEAM if migration == "team" else 0)
+    return pm_ga_params(deme, xover_rounds, mut_tries, saturation, stream_id, flags,
                         mh if mh is not None else None, candidates, 0)
 
 
@@ -422,11 +442,16 @@ def pm_ga_run(inst, seed: int, pop: int, gens: int, params: pm_ga_params | None 
 class Instance:
     """A p-median instance with its device-resident Pi'/Delta' tables."""
 
-    def __init__(self, d, p: int, device: int = 0, stream=None):
+    def __init__(self, d, p: int, device: int = 0, stream=None, cumulative: bool = False):
+        """cumulative=True keeps D' (running sums of Delta') on the device (PM_TABLES_CUMULATIVE)."""
         if isinstance(d, np.ndarray):
             d = np.ascontiguousarray(d, dtype=np.int32)
         n, m = int(d.shape[0]), int(d.shape[1])
-        self.handle = pm_instance_create(d, n, m, int(p), device, stream)
+        if cumulative:
+            self.handle = pm_instance_create_ex(d, n, m, int(p), device, stream, PM_TABLES_CUMULATIVE)
+        else:
+            self.handle = pm_instance_create(d, n, m, int(p), device, stream)
+        self.cumulative = bool(cumulative)
         info = pm_instance_info(self.handle)
         self.n, self.m, self.p, self.L, self.W, self.stride = (info[k] for k in ("n", "m", "p", "L", "W", "stride"))
 
@@ -473,13 +498,13 @@ class GA:
 
     def __init__(self, inst: Instance, seed: int, pop: int, deme: int = 0, xover_rounds: int = -1,
                  mut_tries: int = -1, saturation: int = 0, stream_id: int = 0, tune: bool = False, model=None,
-                 candidates: int = 0, stream=None, _handle=None):
+                 candidates: int = 0, migration: str = "deme", stream=None, _handle=None):
         self.inst = inst
         self.pop = int(pop)
         self.model = model
         self.handle = _handle if _handle is not None else pm_ga_create(
             inst.handle, seed, pop,
-            _params(deme, xover_rounds, mut_tries, saturation, stream_id, tune, model, candidates), stream)
+            _params(deme, xover_rounds, mut_tries, saturation, stream_id, tune, model, candidates, migration), stream)
 
     def step(self, gens: int, stream=None):
         trace = np.zeros(max(int(gens), 1), dtype=np.int64)
@@ -508,9 +533,7 @@ class GA:
     @classmethod
     def load(cls, inst: Instance, blob: bytes, stream=None):
         h = pm_ga_load(inst.handle, blob, stream)
-        import struct
-        P = struct.unpack_from("<q", blob, 8 + 4 + 4 + 8 * 3)[0]
-        return cls(inst, 0, P, _handle=h)
+        return cls(inst, 0, pm_ga_info(h)["pop"], _handle=h)
 
     def close(self):
         if self.handle:

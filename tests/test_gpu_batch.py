@@ -39,10 +39,11 @@ def _dev(masks_list):
     return torch.from_numpy(flat.view(np.int32)).cuda()
 
 
-@pytest.mark.parametrize("tune", [False, True])
-def test_batch_eval_bit_exact(pm, tune):
+@pytest.mark.parametrize("tune,mixed", [(False, False), (True, False), (False, True)])
+def test_batch_eval_bit_exact(pm, tune, mixed):
+    """mixed: every other instance keeps cumulative tables (D' instead of Delta') in the same launch."""
     inst_data = _uneven()
-    insts = [pm.Instance(d, p) for d, p in inst_data]
+    insts = [pm.Instance(d, p, cumulative=mixed and k % 2 == 1) for k, (d, p) in enumerate(inst_data)]
     batch = pm.Batch(insts)
     pops = [1000, 33, 64, 517, 129]
     masks = [random_masks(P, d.shape[1], p, seed=7 * k + P) for k, ((d, p), P) in enumerate(zip(inst_data, pops))]
@@ -73,10 +74,11 @@ def test_batch_eval_paper_shaped_instances(pm):
         np.testing.assert_array_equal(costs[256 * k:256 * (k + 1)], oracle.eval_scan(pi, de, mk))
 
 
-def test_batch_ga_matches_standalone_oracle_runs(pm):
+@pytest.mark.parametrize("mixed", [False, True])
+def test_batch_ga_matches_standalone_oracle_runs(pm, mixed):
     data = [(graph_instance(100, 200, seed=0), 5), (euclid_instance(150, seed=5), 12),
             (graph_instance(90, 200, seed=6), 9)]
-    insts = [pm.Instance(d, p) for d, p in data]
+    insts = [pm.Instance(d, p, cumulative=mixed and k != 1) for k, (d, p) in enumerate(data)]
     batch = pm.Batch(insts)
     P, D, G = 64, 32, 4
     ga = batch.ga(seed=21, pop=P, deme=D, stream_id=3)

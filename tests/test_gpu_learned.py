@@ -50,8 +50,9 @@ def _stats_gpu(pm, inst, masks):
     return g, c, lo, a
 
 
-@pytest.mark.parametrize("case", ["graph", "euclid", "ties", "gmm", "wide"])
-def test_swap_stats_bit_exact(pm, case):
+@pytest.mark.parametrize("cumulative", [False, True])
+@pytest.mark.parametrize("case", ["graph", "euclid", "ties", "gmm", "wide", "short"])
+def test_swap_stats_bit_exact(pm, case, cumulative):
     rng = np.random.default_rng(1)
     if case == "graph":
         d, p = graph_instance(100, 200, seed=0), 5
@@ -61,9 +62,11 @@ def test_swap_stats_bit_exact(pm, case):
         d, p = rng.integers(0, 4, size=(60, 90)).astype(np.int32), 7
     elif case == "gmm":
         d, p = gmm_instance(400, seed=2), 40
-    else:  # m large enough for the global-memory accumulators
+    elif case == "wide":  # m large enough for the global-memory accumulators
         d, p = rng.integers(0, 3000, size=(40, 10000)).astype(np.int32), 60
-    inst = pm.Instance(d, p)
+    else:  # L = 3: rows that often hold a single open facility (second distance = the row's last)
+        d, p = rng.integers(0, 50, size=(50, 40)).astype(np.int32), 38
+    inst = pm.Instance(d, p, cumulative=cumulative)
     masks = random_masks(37, d.shape[1], p, seed=3)
     got = [x.cpu().numpy() for x in _stats_gpu(pm, inst, masks)]
     pi, de = oracle.tables(d, p)

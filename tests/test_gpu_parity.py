@@ -177,22 +177,23 @@ def test_full_size_euclid10000_sampled(pm, p):
 # The GA: bit-exact trajectories
 # --------------------------------------------------------------------------
 
-def _ga_compare(pm, d, p, pop, gens, check_every=1, shape=None, **kw):
-    inst = pm.Instance(d, p)
+def _ga_compare(pm, d, p, pop, gens, check_every=1, shape=None, cumulative=False, **kw):
+    inst = pm.Instance(d, p, cumulative=cumulative)
     if shape is not None:
         inst.set_shape(pop, **shape)
     opi, ode = oracle.tables(d, p)
     m = d.shape[1]
     okw = dict(kw)
     sid = okw.pop("stream_id", 0)
+    migration = kw.get("migration", "deme")
     st, otrace, opops, ocosts = oracle.ga_run(opi, ode, m, p, seed=kw.get("seed", 0), P=pop, D=kw.get("deme") or None,
                                               gens=gens, xover_rounds=kw.get("xover_rounds"),
                                               mut_tries=kw.get("mut_tries"), saturation=kw.get("saturation", 0),
-                                              record=True, inst=sid)
+                                              record=True, inst=sid, team=migration == "team")
     ga = pm.GA(inst, seed=kw.get("seed", 0), pop=pop, deme=kw.get("deme") or 0,
                xover_rounds=-1 if kw.get("xover_rounds") is None else kw["xover_rounds"],
                mut_tries=-1 if kw.get("mut_tries") is None else kw["mut_tries"],
-               saturation=kw.get("saturation", 0), stream_id=sid)
+               saturation=kw.get("saturation", 0), stream_id=sid, migration=migration)
     done = 0
     traces = []
     while done < len(otrace):
@@ -234,6 +235,10 @@ def test_ga_graph900_first_generations(pm):
     dict(xover_rounds=0, mut_tries=3, seed=2),
     dict(xover_rounds=7, mut_tries=0, deme=8, seed=3),
     dict(stream_id=9, seed=4),
+    dict(migration="team", deme=16, seed=6),            # migration variant (ii) of Section 4.5
+    dict(migration="team", deme=16, seed=7, xover_rounds=20, mut_tries=20),
+    dict(xover_rounds=60, mut_tries=60, deme=16, seed=8),  # the paper's preset iteration counts (60, 20)
+    dict(xover_rounds=20, mut_tries=20, deme=32, seed=9),
 ])
 def test_ga_variants(pm, kw):
     d = euclid_instance(77, seed=11)
@@ -246,12 +251,13 @@ def test_ga_p1_and_saturation(pm):
     _ga_compare(pm, d, 3, 32, 300, check_every=300, deme=16, saturation=3)
 
 
-def test_ga_save_load_resume(pm):
+@pytest.mark.parametrize("migration", ["deme", "team"])
+def test_ga_save_load_resume(pm, migration):
     d = graph_instance(100, 200, seed=0)
     inst = pm.Instance(d, 5)
-    a = pm.GA(inst, seed=7, pop=64, deme=32)
+    a = pm.GA(inst, seed=7, pop=64, deme=8, migration=migration)
     ta = a.step(12)
-    b = pm.GA(inst, seed=7, pop=64, deme=32)
+    b = pm.GA(inst, seed=7, pop=64, deme=8, migration=migration)
     tb1 = b.step(5)
     blob = b.save()
     b.close()
@@ -355,3 +361,43 @@ def test_ga_on_pinned_shapes_matches_oracle(pm):
     _ga_compare(pm, w["d"], w["p"], 1024, 2, check_every=1, shape=dict(groups=1, warps=8, splits=3))
     _ga_compare(pm, euclid_instance(77, seed=11), 7, 128, 6, check_every=2, deme=16, seed=5,
                 shape=dict(groups=0, warps=8, splits=2))
+
+
+@pytest.mark.parametrize("name,d,p", _shapes(), ids=[s[0] for s in _shapes()])
+def test_cumulative_tables_bit_exact(pm, name, d, p):
+    """PM_TABLES_CUMULATIVE: the tables read back as Pi'/Delta', and every shape evaluates to the oracle's costs."""
+    m = d.shape[1]
+    inst = pm.Instance(d, p, cumulative=True)
+    assert pm.pm_instance_flags(inst.handle) == pm.PM_TABLES_CUMULATIVE
+    pi, de = inst.tables()
+    opi, ode = oracle.tables(d, p)
+    np.testing.assert_array_equal(pi, opi)
+    np.testing.assert_array_equal(de, ode)
+    dev = torch.zeros((d.shape[0], inst.L), dtype=torch.int32, device="cuda")
+    pm.pm_instance_tables(inst.handle, None, dev)
+    np.testing.assert_array_equal(dev.cpu().numpy(), ode)
+    for pop in (1, 33, 1000):
+        masks = random_masks(pop, m, p, seed=pop + 2 * m)
+        expect = oracle.eval_direct(d, masks)
+        np.testing.assert_array_equal(oracle.eval_cumulative(opi, oracle.cumulative(ode), masks), expect)
+        np.testing.assert_array_equal(inst.eval(masks), expect)
+        if pop == 1000:
+            for G, warps, splits in _pinned_shapes(pm, inst, pop):
+                np.testing.assert_array_equal(inst.eval(masks), expect, err_msg=f"G={G} warps={warps}")
+    inst.close()
+
+
+def test_cumulative_row_kernel_and_full_size_sample(pm):
+    rng = np.random.default_rng(8)
+    d = rng.integers(0, 1 << 20, size=(6, 60000)).astype(np.int32)  # m too large for facility-major tiles
+    inst = pm.Instance(d, 7, cumulative=True)
+    masks = random_masks(40, 60000, 7, seed=2)
+    np.testing.assert_array_equal(inst.eval(masks), oracle.eval_direct(d, masks))
+    inst.close()
+
+
+def test_ga_on_cumulative_tables_matches_oracle(pm):
+    w = paper_shape_instance("graph900")
+    _ga_compare(pm, w["d"], w["p"], 1024, 2, check_every=1, cumulative=True)
+    _ga_compare(pm, euclid_instance(77, seed=11), 7, 128, 6, check_every=2, deme=16, seed=5, cumulative=True,
+                migration="team")

@@ -361,3 +361,55 @@ def test_ga_saturation_stop():
     assert len(trace) < 500
     assert (trace[-5:] == trace[-1]).all()
     assert st.scalars[1] == 4
+
+
+def test_ga_migration_variants():
+    """Section 4.5's two migration variants, pinned by what each must do to the next population.
+
+    With no crossover or mutation the population at the end of a generation is the one it started with, so:
+    variant (i) puts deme b's best (lowest cost, then lowest index) of generation g-1 into slot 0 of deme b;
+    variant (ii) puts all deme bests into deme 0 (deme b's into slot b); every other individual is the same
+    fresh draw in both variants (same random-number counters), and generation 0 has no migrants at all.
+    """
+    w = paper_shape_instance("graph100")
+    d, p = w["d"], w["p"]
+    pi, de = oracle.tables(d, p)
+    P, D, G = 64, 8, 3
+    NB = P // D
+    runs = {}
+    for team in (False, True):
+        _, _, pops, costs = oracle.ga_run(pi, de, 100, p, seed=9, P=P, D=D, gens=G, xover_rounds=0, mut_tries=0,
+                                          record=True, team=team)
+        runs[team] = (pops, costs)
+    (pi_, ci), (pt, ct) = runs[False], runs[True]
+    np.testing.assert_array_equal(pi_[0], pt[0])
+    for g in range(1, G):
+        for team, (pops, costs) in runs.items():
+            for b in range(NB):
+                c = costs[g - 1, b * D:(b + 1) * D]
+                best = pops[g - 1, b * D + int(np.argmin(c))]  # argmin: lowest index among equal costs
+                slot = b if team else b * D
+                np.testing.assert_array_equal(pops[g, slot], best)
+        migrants = set(range(NB)) | set(range(0, P, D))
+        for t in range(P):
+            if t not in migrants:
+                np.testing.assert_array_equal(pi_[g, t], pt[g, t])
+    with pytest.raises(RuntimeError):  # deme 0 cannot hold 16 bests of demes of 4
+        oracle.ga_run(pi, de, 100, p, seed=0, P=64, D=4, gens=1, team=True)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_cumulative_tables_are_the_sorted_distances(seed):
+    """D' (running sums of Delta') is the row of sorted distances, and reading it at the first open rank gives
+    the direct cost of every p-subset: the cumulative evaluator's pins."""
+    rng = np.random.default_rng(100 + seed)
+    n, m = int(rng.integers(2, 12)), int(rng.integers(3, 9))
+    p = int(rng.integers(1, m))
+    d = rng.integers(0, [3, 40, 1000, 2**31 - 1][seed], size=(n, m)).astype(np.int32)
+    pi, de = oracle.tables(d, p)
+    dcum = oracle.cumulative(de)
+    np.testing.assert_array_equal(dcum, np.sort(d.astype(np.int64), axis=1)[:, :m - p + 1])
+    np.testing.assert_array_equal(dcum, np.take_along_axis(d.astype(np.int64), pi.astype(np.int64), axis=1))
+    sets = list(itertools.combinations(range(m), p))
+    masks = masks_from_sets(sets, m)
+    np.testing.assert_array_equal(oracle.eval_cumulative(pi, dcum, masks), oracle.eval_direct(d, masks))
