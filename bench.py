@@ -41,6 +41,8 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="graph900")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--init", default="floyd", choices=["floyd", "combinadic"],
+                    help="chromosome generation: Floyd sampling, or Section 4.1's random rank + lexicographic unranking")
     ap.add_argument("--tables", default="delta", choices=["delta", "cumulative"],
                     help="device tables: Delta' (the paper's increments, summed by the scan) or cumulative D' "
                          "(their running sums, read at the first open rank)")
@@ -257,7 +259,7 @@ def run_ours(args):
     cum = args.tables == "cumulative"
     inst = pm.Instance(d, p, device=local, stream=stream.cuda_stream, cumulative=cum)
     shape = inst.tune(pop, stream=stream.cuda_stream)  # autotuned evaluation tile (kept by the instance)
-    ga = pm.GA(inst, seed=0, pop=pop, deme=deme, stream_id=rank, stream=stream.cuda_stream)
+    ga = pm.GA(inst, seed=0, pop=pop, deme=deme, stream_id=rank, init=args.init, stream=stream.cuda_stream)
     info = ga.info()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
 
@@ -331,7 +333,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         h = pm.pm_instance_create_ex(dh, n, m, p, local, stream.cuda_stream, pm.PM_TABLES_CUMULATIVE if cum else 0)
-        bc, gr, ev = pm.pm_ga_run(h, 0, pop, args.steps, pm._params(deme=deme, stream_id=rank), best_mask, trace,
+        bc, gr, ev = pm.pm_ga_run(h, 0, pop, args.steps, pm._params(deme=deme, stream_id=rank, init=args.init),
+                                  best_mask, trace,
                                   stream.cuda_stream)
         pm.pm_instance_destroy(h)
         t1 = time.perf_counter()
@@ -350,7 +353,8 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": {"tables": args.tables, "workload": args.workload, "description": desc, "n": int(n), "m": int(m), "p": int(p),
+            "config": {"tables": args.tables, "init": args.init, "workload": args.workload, "description": desc,
+                       "n": int(n), "m": int(m), "p": int(p),
                        "pop": pop, "deme": deme, "xover_rounds": info["xover_rounds"],
                        "mut_tries": info["mut_tries"], "step": "one GA generation (one pm_ga_step graph launch)",
                        "l2": "flushed between timed steps (512 MiB write outside the events)",

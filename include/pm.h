@@ -230,7 +230,8 @@ typedef struct pm_ga_params {
     int64_t saturation;   /* S: stop when the best has not improved for S generations; 0 = off */
     uint32_t stream_id;   /* fourth word of every random-number counter (independent runs) */
     uint32_t flags;       /* PM_GA_TUNE: run pm_tune_eval for this population size at creation;
-                             PM_GA_MIGRATE_TEAM: migration variant (ii) of Section 4.5 */
+                             PM_GA_MIGRATE_TEAM: migration variant (ii) of Section 4.5;
+                             PM_GA_INIT_COMBINADIC: Section 4.1's chromosome generation */
     struct pm_model *model;  /* learned swap proposal (see pm_model_create); NULL = the paper's GA only */
     int32_t candidates;      /* learned try: closed facilities (by gain) paired with every open one; <= 0: 4 */
     int32_t reserved;        /* must be 0 */
@@ -244,6 +245,16 @@ typedef struct pm_ga_params {
  * (needs pop/deme <= deme, else PM_ERR_INVALID_ARG); every other individual
  * is drawn afresh. */
 #define PM_GA_MIGRATE_TEAM 2u
+/* Chromosome generation (Section 4.1).  Default: Floyd's sampling of a
+ * uniform p-subset (p Philox draws).  PM_GA_INIT_COMBINADIC: the paper's
+ * method -- a random rank below C(m, p), drawn exactly uniformly by
+ * rejection on multi-word Philox integers (C(900, 90) is about 2^418, past
+ * the 64-bit draw the section describes), then the combination of that rank
+ * in lexicographic order.  Needs a device table of the binomials the
+ * unranking meets ((p + 1) x (m - p + 1) entries of about log2(C(m, p))/32
+ * words, built at creation; PM_ERR_UNSUPPORTED above 4 GiB or C(m, p) above
+ * about 2^8100) and a single-instance GA. */
+#define PM_GA_INIT_COMBINADIC 4u
 
 typedef struct pm_ga pm_ga;
 typedef struct pm_model pm_model;

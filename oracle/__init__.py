@@ -78,9 +78,12 @@ def _load():
     lib.oracle_crossover_params.restype = None
     lib.oracle_swap_stats.argtypes = [P, P, I64, I64, I64, P, I64, I64, P, P, P, P]
     lib.oracle_ga_run.argtypes = [P, P, I64, I64, I64, U64, U32, I64, I64, ctypes.c_int32, ctypes.c_int32,
-                                  I64, I64, P, P, P, P, P, P, P, P, ctypes.c_int32]
+                                  I64, I64, P, P, P, P, P, P, P, P, ctypes.c_int32, _INIT_FN]
     _lib = lib
     return lib
+
+
+_INIT_FN = ctypes.CFUNCTYPE(None, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32))
 
 
 def _ptr(a):
@@ -292,10 +295,12 @@ class GAState:
 
 def ga_run(pi, delta, m: int, p: int, seed: int, P: int, D: int | None = None, gens: int = 1,
            xover_rounds: int | None = None, mut_tries: int | None = None, saturation: int = 0,
-           state: GAState | None = None, record: bool = False, inst: int = 0, team: bool = False):
+           state: GAState | None = None, record: bool = False, inst: int = 0, team: bool = False,
+           init: str = "floyd"):
     """Run the reference GA for `gens` generations (Sections 3.1, 3.2.2, 4.5).
 
     team=True selects migration variant (ii) of Section 4.5 (all deme bests into deme 0).
+    init="combinadic" draws fresh chromosomes as Section 4.1 does (oracle.combinadic), else Floyd sampling.
 
     Returns (state, trace, pops, costs); pops/costs are per-generation copies
     of the population after mutation when record=True.
@@ -313,9 +318,22 @@ def ga_run(pi, delta, m: int, p: int, seed: int, P: int, D: int | None = None, g
     pops = np.zeros((gens, P, W), dtype=np.uint32) if record else None
     costs = np.zeros((gens, P), dtype=np.int64) if record else None
     ran = np.zeros(1, dtype=np.int64)
+    if init == "combinadic":
+        from . import combinadic
+
+        def fresh(g, t, x):
+            words = combinadic.chromosome(seed, g, t, m, p, inst)
+            for w in range(W):
+                x[w] = int(words[w])
+
+        init_fn = _INIT_FN(fresh)
+    elif init == "floyd":
+        init_fn = _INIT_FN()
+    else:
+        raise ValueError("init is 'floyd' or 'combinadic'")
     rc = _load().oracle_ga_run(_ptr(pi), _ptr(delta), n, m, p, seed, inst, P, D, xover_rounds, mut_tries, gens,
                                saturation, _ptr(st.deme_best), _ptr(st.deme_cost), _ptr(st.best), _ptr(st.scalars),
-                               _ptr(pops), _ptr(costs), _ptr(trace), _ptr(ran), 1 if team else 0)
+                               _ptr(pops), _ptr(costs), _ptr(trace), _ptr(ran), 1 if team else 0, init_fn)
     _check(rc, "ga_run")
     k = int(ran[0])
     trace = trace[:k]

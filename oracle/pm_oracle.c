@@ -384,10 +384,15 @@ static int ilog2_exact(int64_t v)
     return ((1LL << r) == v) ? r : -1;
 }
 
+/* Chromosome generation supplied by the caller (the combinadic draw of Section 4.1 is written with exact
+   big integers in oracle/combinadic.py): writes the W words of individual `unit`'s fresh bitset. */
+typedef void (*oracle_init_fn)(uint32_t gen, uint32_t unit, uint32_t *x);
+
 int oracle_ga_run(const uint16_t *pi, const int32_t *delta, int64_t n, int64_t m, int64_t p, uint64_t seed,
                   uint32_t inst, int64_t P, int64_t D, int32_t xover_rounds, int32_t mut_tries, int64_t gens,
                   int64_t S, uint32_t *deme_best, int64_t *deme_cost, uint32_t *best, int64_t *scalars,
-                  uint32_t *pop_out, int64_t *cost_out, int64_t *trace, int64_t *gens_run, int32_t team)
+                  uint32_t *pop_out, int64_t *cost_out, int64_t *trace, int64_t *gens_run, int32_t team,
+                  oracle_init_fn init_fn)
 {
     int lgD = ilog2_exact(D);
     if (n < 1 || p < 1 || p >= m || D < 2 || lgD < 0 || P < D || P % D != 0 || xover_rounds < 0 || mut_tries < 0)
@@ -420,6 +425,8 @@ int oracle_ga_run(const uint16_t *pi, const int32_t *delta, int64_t n, int64_t m
                 memcpy(X + t * W, deme_best + (t / D) * W, (size_t)W * sizeof(uint32_t));
             else if (g > 0 && team && t < NB)
                 memcpy(X + t * W, deme_best + t * W, (size_t)W * sizeof(uint32_t));
+            else if (init_fn)
+                init_fn(g, (uint32_t)t, X + t * W);
             else
                 floyd_philox(m, p, seed, g, (uint32_t)t, inst, X + t * W, tmp);
         }

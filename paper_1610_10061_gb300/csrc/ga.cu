@@ -34,6 +34,7 @@
 // draw `slot` is word slot & 3.  U[0, N) = floor(u * N / 2^32).  Instance k
 // of a batch uses stream id (base + k).
 
+#include <cmath>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -56,6 +57,8 @@ const std::vector<const pm_instance *> &pm_batch_instances(const pm_batch *b);
 namespace {
 
 constexpr uint32_t OP_INIT = 0x001u;
+constexpr uint32_t OP_COMB = 0x002u;  // combinadic rank words (Section 4.1)
+constexpr int kCombTries = 64;        // rejection tries for a uniform rank below C(m, p)
 constexpr uint32_t OP_XOVER = 0x100u;
 constexpr uint32_t OP_MUT = 0x200u;
 
@@ -266,6 +269,253 @@ __global__ void __launch_bounds__(32) k_ga_init(const ga_prob *__restrict__ gps,
     } else {
         write_columns(X + gp.word_base + t0 * W, W, t0, gp, co, lane, 0, 1);
     }
+}
+
+// ------------------- combinadic chromosome generation -----------------------
+// Section 4.1 draws a chromosome as the i-th p-combination of {0..m-1} in
+// lexicographic order for a random i below C(m, p).  C(900, 90) is about
+// 2^418, so ranks are multi-word integers: K words, least significant
+// first.  A warp holds one such integer with Q = K/32 (rounded up to a power
+// of two) consecutive words per lane, lane l words [lQ, lQ + Q).
+//
+// Binomial table: the walk below only meets C(b + d, b) with b < p and
+// d <= m - p (b = choices left minus one, d = positions left minus choices
+// left), plus C(m, p) itself at b = p, d = m - p; entry (b, d) sits at word
+// ((b * (m - p + 1)) + d) * K.  Every entry is at most C(m, p), so K words
+// (the host's estimate of bits(C(m, p)) / 32, plus a spare word) hold it.
+
+// Pascal's rule along anti-diagonals s = b + d (each entry needs (b - 1, d)
+// and (b, d - 1) of the diagonal before): one CTA, a barrier per diagonal.
+// *overflow is set if a sum ever carries out of K words.
+__global__ void __launch_bounds__(1024) k_comb_table(uint32_t *__restrict__ T, int32_t m, int32_t p, int32_t K,
+                                                     int *__restrict__ overflow)
+{
+    const int64_t D1 = (int64_t)m - p + 1;
+    for (int32_t s = 0; s <= m; ++s) {
+        const int32_t b_lo = s - (m - p) > 0 ? s - (m - p) : 0;
+        const int32_t b_hi = s < p ? s : p;
+        for (int32_t b = b_lo + (int32_t)threadIdx.x; b <= b_hi; b += (int32_t)blockDim.x) {
+            const int32_t d = s - b;
+            uint32_t *out = T + ((int64_t)b * D1 + d) * K;
+            if (b == 0 || d == 0) {
+                out[0] = 1u;
+                for (int32_t w = 1; w < K; ++w)
+                    out[w] = 0u;
+            } else {
+                const uint32_t *x = T + ((int64_t)(b - 1) * D1 + d) * K;
+                const uint32_t *y = T + ((int64_t)b * D1 + d - 1) * K;
+                uint32_t carry = 0;
+                for (int32_t w = 0; w < K; ++w) {
+                    const unsigned long long v = (unsigned long long)x[w] + y[w] + carry;
+                    out[w] = (uint32_t)v;
+                    carry = (uint32_t)(v >> 32);
+                }
+                if (carry)
+                    atomicExch(overflow, 1);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <int Q>
+__device__ __forceinline__ void big_load(const uint32_t *__restrict__ e, int32_t K, int lane, uint32_t (&v)[Q])
+{
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int32_t w = lane * Q + q;
+        v[q] = w < K ? __ldg(e + w) : 0u;
+    }
+}
+
+// x < y for warp-held integers.
+template <int Q>
+__device__ __forceinline__ bool big_less(const uint32_t (&x)[Q], const uint32_t (&y)[Q])
+{
+    int cmp = 0;
+#pragma unroll
+    for (int q = Q - 1; q >= 0; --q)
+        if (cmp == 0 && x[q] != y[q])
+            cmp = x[q] < y[q] ? -1 : 1;
+    const uint32_t ne = __ballot_sync(PM_FULL_MASK, cmp != 0);
+    if (ne == 0u)
+        return false;
+    return __shfl_sync(PM_FULL_MASK, cmp, 31 - __clz(ne)) < 0;
+}
+
+// x -= y for warp-held integers with x >= y.  Each lane subtracts its words;
+// a lane passes a borrow up if it generated one, or if it received one and
+// its difference is zero.  Those two lane masks G and P give the borrow into
+// every lane at once: the carries of the 32-bit sum G + (G | P).
+template <int Q>
+__device__ __forceinline__ void big_sub(uint32_t (&x)[Q], const uint32_t (&y)[Q], int lane)
+{
+    uint32_t borrow = 0;
+    bool zero = true;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const uint32_t a = x[q], b = y[q];
+        const uint32_t d = a - b - borrow;
+        borrow = (a < b || (a == b && borrow)) ? 1u : 0u;
+        x[q] = d;
+        zero = zero && d == 0u;
+    }
+    const uint32_t G = __ballot_sync(PM_FULL_MASK, borrow != 0u);
+    const uint32_t P = __ballot_sync(PM_FULL_MASK, zero);
+    const uint32_t in = (G + (G | P)) ^ G ^ (G | P);
+    if ((in >> lane) & 1u) {
+        uint32_t b = 1u;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const uint32_t a = x[q];
+            x[q] = a - b;
+            b = (a < b) ? 1u : 0u;
+        }
+    }
+}
+
+// Fresh chromosomes by Section 4.1 (rank by bounded rejection on Philox
+// words, then lexicographic unranking) + migration, for single-instance GAs.
+// CTA = 32 warps = 32 individuals; warp j builds individual t0 + j's row in
+// X, then the CTA writes the columns.
+template <int Q>
+__global__ void __launch_bounds__(1024) k_ga_init_comb(ga_prob gp, uint32_t *__restrict__ X,
+                                                       uint8_t *__restrict__ improved, uint32_t *__restrict__ active,
+                                                       const uint32_t *__restrict__ deme_best,
+                                                       const uint32_t *__restrict__ T, int32_t K, uint64_t seed,
+                                                       const ga_dev *__restrict__ st, ColumnsOut co)
+{
+    pm_grid_dependency_wait();
+    __shared__ uint32_t on_s;
+    const int lane = threadIdx.x & 31;
+    const int j = threadIdx.x >> 5;
+    const int64_t t0 = (int64_t)blockIdx.x * 32;
+    const int64_t t = t0 + j;
+    const int32_t W = gp.W, m = gp.m, p = gp.p;
+    if (st[0].stop) {
+        if (threadIdx.x == 0)
+            active[t0 >> 5] = 0u;
+        return;
+    }
+    if (threadIdx.x == 0)
+        on_s = 0u;
+    __syncthreads();
+    const uint32_t gen = (uint32_t)st[0].gen;
+    if (t < gp.pop) {
+        if (lane == 0) {
+            improved[t] = 0;
+            atomicOr(&on_s, 1u << j);
+        }
+        uint32_t *row = X + gp.word_base + t * W;
+        const bool migrant = gen > 0 && (gp.team ? t < gp.NB : (t % gp.D) == 0);
+        if (migrant) {
+            const uint32_t *src = deme_best + gp.dword_base + (gp.team ? t : t / gp.D) * W;
+            for (int w = lane; w < W; w += 32)
+                row[w] = src[w];
+        } else {
+            const int64_t D1 = (int64_t)m - p + 1;
+            auto entry = [&](int32_t b, int32_t d) { return T + ((int64_t)b * D1 + d) * K; };
+            // C(m, p), its bit length and exact word count
+            uint32_t C[Q];
+            big_load<Q>(entry(p, m - p), K, lane, C);
+            int hiq = -1;
+#pragma unroll
+            for (int q = 0; q < Q; ++q)
+                if (C[q] != 0u)
+                    hiq = q;
+            const uint32_t nz = __ballot_sync(PM_FULL_MASK, hiq >= 0);
+            const int top = 31 - __clz(nz);  // C >= 2, so some word is nonzero
+            const int top_q = __shfl_sync(PM_FULL_MASK, hiq, top);
+            uint32_t top_word = 0u;
+#pragma unroll
+            for (int q = 0; q < Q; ++q)
+                if (q == top_q)
+                    top_word = C[q];
+            top_word = __shfl_sync(PM_FULL_MASK, top_word, top);
+            const int32_t wtop = top * Q + top_q;                  // most significant nonzero word
+            const int32_t bits = 32 * wtop + (32 - __clz(top_word));  // bit length of C(m, p)
+            const int32_t Kc = wtop + 1;
+            const uint32_t topmask = (bits - 32 * wtop) == 32 ? 0xffffffffu : ((1u << (bits - 32 * wtop)) - 1u);
+            // rank: try r uses draws r*Kc .. r*Kc + Kc - 1 (word w = draw r*Kc + w)
+            uint32_t x[Q];
+            bool got = false;
+            for (int r = 0; r < kCombTries && !got; ++r) {
+                uint32_t u[Q];
+#pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    const int32_t w = lane * Q + q;
+                    u[q] = 0u;
+                    if (w < Kc) {
+                        const uint32_t slot = (uint32_t)(r * Kc + w);
+                        u[q] = word_of(draw_block(seed, gen, (uint32_t)t, OP_COMB, slot >> 2, gp.sid), slot & 3u);
+                        if (w == wtop)
+                            u[q] &= topmask;
+                    }
+                }
+                if (big_less<Q>(u, C)) {
+#pragma unroll
+                    for (int q = 0; q < Q; ++q)
+                        x[q] = u[q];
+                    got = true;
+                }
+            }
+            if (!got) {
+#pragma unroll
+                for (int q = 0; q < Q; ++q)
+                    x[q] = 0u;
+            }
+            // unrank: elements e = 0, 1, ...; k still to choose among m - e; d = m - e - k
+            for (int w = lane; w < W; w += 32)
+                row[w] = 0u;
+            __syncwarp();
+            int32_t k = p, e = 0;
+            int32_t cur_w = 0;
+            uint32_t cur = 0u;
+            auto take = [&](int32_t pos) {
+                if ((pos >> 5) != cur_w) {
+                    if (lane == 0 && cur)
+                        row[cur_w] = cur;
+                    cur_w = pos >> 5;
+                    cur = 0u;
+                }
+                cur |= 1u << (pos & 31);
+            };
+            uint32_t c[Q], c_take[Q], c_skip[Q];
+            if (m - k > 0)
+                big_load<Q>(entry(k - 1, m - k), K, lane, c);
+            while (k > 0) {
+                const int32_t d = m - e - k;
+                if (d == 0) {  // as many positions left as choices: take them all
+                    for (int32_t q = 0; q < k; ++q)
+                        take(e + q);
+                    break;
+                }
+                // the next entry under either outcome, loaded before the decision
+                if (k >= 2)
+                    big_load<Q>(entry(k - 2, d), K, lane, c_take);
+                big_load<Q>(entry(k - 1, d - 1), K, lane, c_skip);
+                if (big_less<Q>(x, c)) {
+                    take(e);
+                    --k;
+#pragma unroll
+                    for (int q = 0; q < Q; ++q)
+                        c[q] = c_take[q];
+                } else {
+                    big_sub<Q>(x, c, lane);
+#pragma unroll
+                    for (int q = 0; q < Q; ++q)
+                        c[q] = c_skip[q];
+                }
+                ++e;
+            }
+            if (lane == 0 && cur)
+                row[cur_w] = cur;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        active[t0 >> 5] = on_s;
+    write_columns(X + gp.word_base + t0 * W, W, t0, gp, co, lane, j, 32);
 }
 
 // One crossover round (Section 4.3).  CTA = 32 warps = 32 individuals; warp
@@ -756,6 +1006,9 @@ struct pm_ga {
     int64_t S = 0;
     uint32_t sid = 0;
     bool team = false;  // migration variant (ii)
+    bool comb = false;  // Section 4.1 chromosome generation (combinadic)
+    int comb_K = 0, comb_Q = 0;
+    pm_dbuf comb_tab;
     bool single_row = false;  // one instance whose evaluation uses the row kernel
     pm_eval_plan single;      // K == 1: the single-instance plan
     pm_multi_plan plan;       // the scan plan over all instances
@@ -787,7 +1040,8 @@ static void ga_free(pm_ga *ga)
     pm_dbuf *bufs[] = {&ga->X,         &ga->Xc,   &ga->cost,  &ga->active, &ga->improved, &ga->deme_best,
                        &ga->deme_cost, &ga->best, &ga->trace, &ga->accum,  &ga->tickets,  &ga->columns,
                        &ga->st,        &ga->glob, &ga->err,   &ga->probs,  &ga->gprobs,
-                       &ga->s_gain,    &ga->s_cap, &ga->s_loss, &ga->s_assign, &ga->moves, &ga->xfeat, &ga->scores};
+                       &ga->s_gain,    &ga->s_cap, &ga->s_loss, &ga->s_assign, &ga->moves, &ga->xfeat, &ga->scores,
+                       &ga->comb_tab};
     for (pm_dbuf *b : bufs)
         b->release();
     delete ga;
@@ -843,8 +1097,31 @@ static pm_status enqueue_generation(pm_ga *ga, cudaStream_t s, cudaGraphConditio
     const size_t init_smem = (size_t)32 * (ga->Wmax | 1) * 4;
     const int rows_in_smem = init_smem <= 48 * 1024 ? 1 : 0;
 
-    PM_CUDA(pm_launch(k_ga_init, groups, 32, rows_in_smem ? init_smem : 0, s, gps, K, one, X, improved, active,
-                      static_cast<const uint32_t *>(ga->deme_best.ptr), ga->seed, st, co, rows_in_smem));
+    if (ga->comb) {
+        const uint32_t *T = static_cast<const uint32_t *>(ga->comb_tab.ptr);
+        const uint32_t *db = static_cast<const uint32_t *>(ga->deme_best.ptr);
+        switch (ga->comb_Q) {
+        case 1:
+            PM_CUDA(pm_launch(k_ga_init_comb<1>, groups, 1024, 0, s, one, X, improved, active, db, T, ga->comb_K,
+                              ga->seed, st, co));
+            break;
+        case 2:
+            PM_CUDA(pm_launch(k_ga_init_comb<2>, groups, 1024, 0, s, one, X, improved, active, db, T, ga->comb_K,
+                              ga->seed, st, co));
+            break;
+        case 4:
+            PM_CUDA(pm_launch(k_ga_init_comb<4>, groups, 1024, 0, s, one, X, improved, active, db, T, ga->comb_K,
+                              ga->seed, st, co));
+            break;
+        default:
+            PM_CUDA(pm_launch(k_ga_init_comb<8>, groups, 1024, 0, s, one, X, improved, active, db, T, ga->comb_K,
+                              ga->seed, st, co));
+            break;
+        }
+    } else {
+        PM_CUDA(pm_launch(k_ga_init, groups, 32, rows_in_smem ? init_smem : 0, s, gps, K, one, X, improved, active,
+                          static_cast<const uint32_t *>(ga->deme_best.ptr), ga->seed, st, co, rows_in_smem));
+    }
     pm_accept_args plain;
     plain.columns_ready = true;
     PM_TRY(ga_eval(ga, X, cost, plain, s));
@@ -1016,7 +1293,7 @@ static pm_status ga_configure(pm_ga *ga, int64_t pop, uint64_t seed, const pm_ga
     prm.mut_tries = -1;
     if (params)
         prm = *params;
-    if ((prm.flags & ~(PM_GA_TUNE | PM_GA_MIGRATE_TEAM)) != 0 || prm.reserved != 0)
+    if ((prm.flags & ~(PM_GA_TUNE | PM_GA_MIGRATE_TEAM | PM_GA_INIT_COMBINADIC)) != 0 || prm.reserved != 0)
         return PM_ERR_INVALID_ARG;
     ga->model = prm.model;
     ga->T = prm.candidates > 0 ? prm.candidates : 4;
@@ -1042,6 +1319,7 @@ static pm_status ga_configure(pm_ga *ga, int64_t pop, uint64_t seed, const pm_ga
     ga->S = prm.saturation;
     ga->sid = prm.stream_id;
     ga->team = (prm.flags & PM_GA_MIGRATE_TEAM) != 0;
+    ga->comb = (prm.flags & PM_GA_INIT_COMBINADIC) != 0;
     if (ga->team && ga->NB > D)
         return PM_ERR_INVALID_ARG;  // deme 0 cannot hold every deme's best
     return PM_OK;
@@ -1053,6 +1331,43 @@ static pm_status ga_create_common(pm_ga *ga, cudaStream_t s)
     if (st == PM_OK)
         st = build_graph(ga);
     return st;
+}
+
+// The binomial table of the combinadic generation (built once per GA on the
+// stream).  K = the words of C(m, p) from a log-gamma estimate plus a spare
+// word; the kernel reports an overflow if the estimate were ever short.
+static pm_status comb_prepare(pm_ga *ga, const pm_instance *inst, cudaStream_t s)
+{
+    const double log2c = (std::lgamma((double)inst->m + 1.0) - std::lgamma((double)inst->p + 1.0) -
+                          std::lgamma((double)(inst->m - inst->p) + 1.0)) / std::log(2.0);
+    const int K = (int)(log2c / 32.0) + 2;
+    int Q = 1;
+    while (Q * 32 < K)
+        Q *= 2;
+    if (Q > 8)
+        return PM_ERR_UNSUPPORTED;  // C(m, p) beyond 2^8192
+    const size_t bytes = (size_t)(inst->p + 1) * (size_t)(inst->m - inst->p + 1) * (size_t)K * 4;
+    if (bytes > ((size_t)4 << 30))
+        return PM_ERR_UNSUPPORTED;  // table above 4 GiB
+    ga->comb_K = K;
+    ga->comb_Q = Q;
+    PM_TRY(ga->comb_tab.reserve(bytes));
+    int *flag = nullptr;
+    PM_CUDA(cudaMallocAsync(reinterpret_cast<void **>(&flag), sizeof(int), s));
+    cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), s);
+    if (e == cudaSuccess) {
+        k_comb_table<<<1, 1024, 0, s>>>(static_cast<uint32_t *>(ga->comb_tab.ptr), (int32_t)inst->m, (int32_t)inst->p,
+                                        K, flag);
+        e = cudaGetLastError();
+    }
+    int overflow = 0;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&overflow, flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s);
+    cudaFreeAsync(flag, s);
+    PM_CUDA(e);
+    return overflow ? PM_ERR_UNSUPPORTED : PM_OK;
 }
 
 extern "C" pm_status pm_ga_create(pm_instance *inst, uint64_t seed, int64_t pop, const pm_ga_params *params,
@@ -1071,6 +1386,8 @@ extern "C" pm_status pm_ga_create(pm_instance *inst, uint64_t seed, int64_t pop,
         st = PM_ERR_CUDA;
     if (st == PM_OK && params && (params->flags & PM_GA_TUNE))
         st = pm_tune_eval(inst, pop, stream, nullptr);
+    if (st == PM_OK && ga->comb)
+        st = comb_prepare(ga, inst, static_cast<cudaStream_t>(stream));
     if (st == PM_OK && ga->model) {
         const size_t Pm = (size_t)pop * inst->m, C = (size_t)inst->p * ga->T;
         st = pm_learn_prepare(inst);
@@ -1110,8 +1427,8 @@ extern "C" pm_status pm_batch_ga_create(pm_batch *b, uint64_t seed, int64_t pop,
         ga->insts.push_back(const_cast<pm_instance *>(in));
     ga->K = (int)insts.size();
     pm_status st = ga_configure(ga, pop, seed, params);
-    if (st == PM_OK && ga->model)
-        st = PM_ERR_UNSUPPORTED;  // the learned try is for single-instance GAs
+    if (st == PM_OK && (ga->model || ga->comb))
+        st = PM_ERR_UNSUPPORTED;  // the learned try and the combinadic generation are for single-instance GAs
     // crossover runs for all instances or for none: p = 1 mixed with p >= 2 is not supported
     if (st == PM_OK) {
         const bool any1 = std::any_of(insts.begin(), insts.end(), [](const pm_instance *in) { return in->p < 2; });
@@ -1246,7 +1563,7 @@ struct ga_header {
     char magic[8];
     uint32_t version;
     uint32_t sid;
-    uint32_t flags;  // PM_GA_MIGRATE_TEAM
+    uint32_t flags;  // PM_GA_MIGRATE_TEAM, PM_GA_INIT_COMBINADIC
     uint32_t pad;
     int64_t n, m, p, P, D, R, Q, S;
     uint64_t seed;
@@ -1279,7 +1596,7 @@ extern "C" pm_status pm_ga_save(pm_ga *ga, void *buf, size_t *len, void *stream)
     std::memcpy(h.magic, "PMGASAV3", 8);
     h.version = 3;
     h.sid = ga->sid;
-    h.flags = ga->team ? PM_GA_MIGRATE_TEAM : 0u;
+    h.flags = (ga->team ? PM_GA_MIGRATE_TEAM : 0u) | (ga->comb ? PM_GA_INIT_COMBINADIC : 0u);
     h.n = inst->n;
     h.m = inst->m;
     h.p = inst->p;
@@ -1324,7 +1641,7 @@ extern "C" pm_status pm_ga_load(pm_instance *inst, const void *buf, size_t len, 
     prm.mut_tries = (int32_t)h.Q;
     prm.saturation = h.S;
     prm.stream_id = h.sid;
-    prm.flags = h.flags & PM_GA_MIGRATE_TEAM;
+    prm.flags = h.flags & (PM_GA_MIGRATE_TEAM | PM_GA_INIT_COMBINADIC);
     pm_ga *ga = nullptr;
     PM_TRY(pm_ga_create(inst, h.seed, h.P, &prm, stream, &ga));
     if (len < ga_blob_size(ga)) {

@@ -51,6 +51,7 @@ class pm_eval_shape(ctypes.Structure):
 PM_GA_TUNE = 1
 PM_TABLES_CUMULATIVE = 1
 PM_GA_MIGRATE_TEAM = 2
+PM_GA_INIT_COMBINADIC = 4
 
 
 _P = ctypes.c_void_p
@@ -212,11 +213,14 @@ def pm_set_eval_shape(inst, pop: int, groups: int, warps: int = 16, splits: int 
 
 
 def _params(deme=0, xover_rounds=-1, mut_tries=-1, saturation=0, stream_id=0, tune=False, model=None,
-            candidates=0, migration="deme"):
+            candidates=0, migration="deme", init="floyd"):
     if migration not in ("deme", "team"):
         raise ValueError("migration is 'deme' (variant (i)) or 'team' (variant (ii))")
+    if init not in ("floyd", "combinadic"):
+        raise ValueError("init is 'floyd' or 'combinadic'")
     mh = model.handle if isinstance(model, Model) else model
-    flags = (PM_GA_TUNE if tune else 0) | (PM_GA_MIGRATE_TEAM if migration == "team" else 0)
+    flags = ((PM_GA_TUNE if tune else 0) | (PM_GA_MIGRATE_TEAM if migration == "team" else 0)
+             | (PM_GA_INIT_COMBINADIC if init == "combinadic" else 0))
     return pm_ga_params(deme, xover_rounds, mut_tries, saturation, stream_id, flags,
                         mh if mh is not None else None, candidates, 0)
 
@@ -498,13 +502,14 @@ class GA:
 
     def __init__(self, inst: Instance, seed: int, pop: int, deme: int = 0, xover_rounds: int = -1,
                  mut_tries: int = -1, saturation: int = 0, stream_id: int = 0, tune: bool = False, model=None,
-                 candidates: int = 0, migration: str = "deme", stream=None, _handle=None):
+                 candidates: int = 0, migration: str = "deme", init: str = "floyd", stream=None, _handle=None):
         self.inst = inst
         self.pop = int(pop)
         self.model = model
         self.handle = _handle if _handle is not None else pm_ga_create(
             inst.handle, seed, pop,
-            _params(deme, xover_rounds, mut_tries, saturation, stream_id, tune, model, candidates, migration), stream)
+            _params(deme, xover_rounds, mut_tries, saturation, stream_id, tune, model, candidates, migration, init),
+            stream)
 
     def step(self, gens: int, stream=None):
         trace = np.zeros(max(int(gens), 1), dtype=np.int64)

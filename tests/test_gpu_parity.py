@@ -186,14 +186,15 @@ def _ga_compare(pm, d, p, pop, gens, check_every=1, shape=None, cumulative=False
     okw = dict(kw)
     sid = okw.pop("stream_id", 0)
     migration = kw.get("migration", "deme")
+    init = kw.get("init", "floyd")
     st, otrace, opops, ocosts = oracle.ga_run(opi, ode, m, p, seed=kw.get("seed", 0), P=pop, D=kw.get("deme") or None,
                                               gens=gens, xover_rounds=kw.get("xover_rounds"),
                                               mut_tries=kw.get("mut_tries"), saturation=kw.get("saturation", 0),
-                                              record=True, inst=sid, team=migration == "team")
+                                              record=True, inst=sid, team=migration == "team", init=init)
     ga = pm.GA(inst, seed=kw.get("seed", 0), pop=pop, deme=kw.get("deme") or 0,
                xover_rounds=-1 if kw.get("xover_rounds") is None else kw["xover_rounds"],
                mut_tries=-1 if kw.get("mut_tries") is None else kw["mut_tries"],
-               saturation=kw.get("saturation", 0), stream_id=sid, migration=migration)
+               saturation=kw.get("saturation", 0), stream_id=sid, migration=migration, init=init)
     done = 0
     traces = []
     while done < len(otrace):
@@ -401,3 +402,16 @@ def test_ga_on_cumulative_tables_matches_oracle(pm):
     _ga_compare(pm, w["d"], w["p"], 1024, 2, check_every=1, cumulative=True)
     _ga_compare(pm, euclid_instance(77, seed=11), 7, 128, 6, check_every=2, deme=16, seed=5, cumulative=True,
                 migration="team")
+
+
+@pytest.mark.parametrize("m,n,p,pop,gens,kw", [
+    (100, 100, 5, 64, 3, dict(deme=16, seed=3)),                       # C(100, 5): 2 words
+    (900, 120, 90, 64, 2, dict(deme=32, seed=4, xover_rounds=0, mut_tries=0)),  # C(900, 90): 14 words
+    (2000, 40, 600, 32, 2, dict(deme=16, seed=5, xover_rounds=1, mut_tries=1)),  # 56 words: two per lane
+    (64, 30, 1, 32, 2, dict(deme=16, seed=6)),                         # p = 1
+    (70, 30, 69, 32, 2, dict(deme=16, seed=7, migration="team")),      # p = m - 1
+])
+def test_ga_combinadic_generation_matches_oracle(pm, m, n, p, pop, gens, kw):
+    """Section 4.1's chromosome generation (multi-word random rank, lexicographic unranking) bit-exact."""
+    d = euclid_instance(m, seed=m)[:n]
+    _ga_compare(pm, d, p, pop, gens, check_every=1, init="combinadic", **kw)
