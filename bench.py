@@ -591,7 +591,9 @@ def run_learned(args):
     torch.cuda.nvtx.range_push("timed")
     for seed in range(5):
         for arm in ("plain", "learned"):
+            torch.cuda.nvtx.range_push(arm)
             tr, cum, evals = run(seed, arm == "learned", limit)
+            torch.cuda.nvtx.range_pop()
             hit = np.nonzero(tr <= target)[0]
             res[arm].append({"seed": seed, "time_s": float(cum[hit[0]]) if hit.size else None,
                              "gens": int(hit[0] + 1) if hit.size else None, "final": int(tr[-1]),

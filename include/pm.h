@@ -376,7 +376,7 @@ PM_API pm_status pm_model_set_params(pm_model *model, const float *params, void 
 PM_API pm_status pm_model_get_params(pm_model *model, float *params, void *stream);
 
 /* Predictions y (rows FP32, device) for inputs x (rows x 16 BF16 bit patterns,
- * device).  Asynchronous. */
+ * device, 16-byte aligned, else PM_ERR_INVALID_ARG).  Asynchronous. */
 PM_API pm_status pm_model_forward(pm_model *model, const uint16_t *x, int64_t rows, float *y, void *stream);
 
 /* Mean squared error of the predictions against targets t (rows FP32,

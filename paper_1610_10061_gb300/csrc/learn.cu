@@ -107,17 +107,22 @@ struct MlpTrainSmem {
 
 
 // ---------------------------------------------------------------------------
-// Inference forward on the 5th-generation tensor cores (tcgen05): 128 rows per
-// CTA; both layers are tcgen05.mma.cta_group::1.kind::f16 (BF16 x BF16 ->
-// FP32, M = N = 128) issued by one thread, operands in shared memory in the
-// K-major no-swizzle core-matrix layout (8 rows x 16 bytes per core matrix;
-// k-chunks 128 B apart, 8-row groups K*16 B apart), accumulators in tensor
-// memory (columns [0,128) layer 1, [128,256) layer 2), read back with
-// tcgen05.ld (thread = row) for the bias/ReLU/BF16 epilogues and the final
-// dot product with w3.  Completion is signalled by tcgen05.commit on an
-// mbarrier whose wait is bounded.
+// Inference forward on the 5th-generation tensor cores (tcgen05).  A
+// persistent grid (two CTAs per SM, each holding 256 TMEM columns) walks
+// 128-row tiles; each CTA stages W1 and W2 once.  Per tile both layers are
+// tcgen05.mma.cta_group::1.kind::f16 (BF16 x BF16 -> FP32, M = N = 128)
+// issued by one thread, operands in shared memory in the K-major no-swizzle
+// core-matrix layout (8 rows x 16 bytes per core matrix; k-chunks 128 B
+// apart, 8-row groups K*16 B apart), accumulators in tensor memory (columns
+// [0,128) layer 1, [128,256) layer 2).  Eight warps read them back with
+// tcgen05.ld (thread = row; warps w and w + 4 share TMEM lanes 32(w mod 4)
+// and split the 128 columns): bias, ReLU and a packed BF16 conversion
+// written as 16-byte rows of the next layer's A tile, then bias, ReLU, BF16
+// rounding and the dot product with w3.  Completion is signalled by
+// tcgen05.commit on an mbarrier whose wait is bounded.
 // ---------------------------------------------------------------------------
 constexpr int kTcRows = 128;
+constexpr int kTcThreads = 256;
 constexpr uint32_t kTmemCols = 256;
 constexpr uint32_t kTcSpinLimit = 1u << 22;
 // instruction descriptor: D F32 (bits 4-5 = 1), A BF16 (7-9 = 1), B BF16 (10-12 = 1), both K-major,
@@ -146,9 +151,9 @@ struct TcSmem {
     __nv_bfloat16 A2[kTcRows * kHid]; // H1 tile
     __nv_bfloat16 B2[kHid * kHid];    // W2 as (n = out, k = in)
     float b1[kHid], b2[kHid], w3[kHid];
+    float part[kTcRows];              // second-half partial dot products
     uint64_t bar;
     uint32_t tmem;
-    int ok;
 };
 
 __device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
@@ -197,18 +202,36 @@ __device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t phase)
     }
 }
 
-__global__ void __launch_bounds__(128) k_mlp_fwd_tc(const __nv_bfloat16 *__restrict__ X, int64_t rows,
-                                                    const __nv_bfloat16 *__restrict__ W1b,
-                                                    const __nv_bfloat16 *__restrict__ W2b,
-                                                    const __nv_bfloat16 *__restrict__ w3b,
-                                                    const float *__restrict__ P, float *__restrict__ y_out,
-                                                    int *__restrict__ err)
+// Two floats to a packed BF16 pair (round to nearest even), lo in the low half.
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
+{
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+
+__device__ __forceinline__ void tc_sync_for_mma()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // smem writes visible to the tensor core
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(kTcThreads) k_mlp_fwd_tc(const __nv_bfloat16 *__restrict__ X, int64_t rows,
+                                                           const __nv_bfloat16 *__restrict__ W1b,
+                                                           const __nv_bfloat16 *__restrict__ W2b,
+                                                           const __nv_bfloat16 *__restrict__ w3b,
+                                                           const float *__restrict__ P, float *__restrict__ y_out,
+                                                           int *__restrict__ err)
 {
     extern __shared__ __align__(1024) unsigned char tc_raw[];
     TcSmem &S = *reinterpret_cast<TcSmem *>(tc_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t row0 = (int64_t)blockIdx.x * kTcRows;
+    const int quad = warp & 3, half = warp >> 2;  // TMEM lanes 32*quad..; columns [64*half, 64*half + 64)
+    const int64_t tiles = (rows + kTcRows - 1) / kTcRows;
 
+    // weights and biases, once per CTA
     for (int i = tid; i < kIn * kHid; i += blockDim.x) {  // W1 [in][out]
         const int in = i / kHid, out = i % kHid;
         S.B1[core_idx(out, in, kIn)] = W1b[i];
@@ -217,15 +240,12 @@ __global__ void __launch_bounds__(128) k_mlp_fwd_tc(const __nv_bfloat16 *__restr
         const int in = i / kHid, out = i % kHid;
         S.B2[core_idx(out, in, kHid)] = W2b[i];
     }
-    for (int i = tid; i < kTcRows * kIn; i += blockDim.x) {
-        const int r = i / kIn, f = i % kIn;
-        S.A1[core_idx(r, f, kIn)] = (row0 + r < rows) ? X[(row0 + r) * kIn + f] : __float2bfloat16(0.f);
-    }
     for (int i = tid; i < kHid; i += blockDim.x) {
         S.b1[i] = P[kOffB1 + i];
         S.b2[i] = P[kOffB2 + i];
         S.w3[i] = __bfloat162float(w3b[i]);
     }
+    const float b3 = P[kOffB3];
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32_learn(&S.bar)), "r"(1u) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -237,37 +257,63 @@ __global__ void __launch_bounds__(128) k_mlp_fwd_tc(const __nv_bfloat16 *__restr
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // smem operands visible to the tensor core
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    tc_sync_for_mma();
     const uint32_t tmem = S.tmem;
-    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;  // this warp's TMEM lanes
-    const int r = warp * 32 + lane;                         // this thread's row
+    const uint32_t lane_off = (uint32_t)(quad * 32) << 16;  // this warp's TMEM lanes
+    const int r = quad * 32 + lane;                         // this thread's row of the tile
+    const int c0 = half * 64;                               // this thread's first column
 
-    // layer 1: D[0,128) = X W1
-    if (tid == 0) {
-        tc_mma(tmem, umma_desc(S.A1, 128, (kIn / 8) * 128), umma_desc(S.B1, 128, (kIn / 8) * 128), kIdesc, 0u);
-        tc_commit(&S.bar);
-    }
-    uint32_t pending = 0;  // phase of the last commit
-    bool ok = tc_wait(&S.bar, 0);
-    ok = __syncthreads_and(ok);
-    if (ok) {
+    uint32_t phase = 0;  // parity of the next commit's completion
+    bool ok = true;
+    // thread tid moves 16 bytes of the X tile: row tid/2, features 8*(tid&1) .. +7; the next tile's chunk is
+    // loaded into registers while the current tile is computed
+    const int xr = tid >> 1, xh = tid & 1;
+    auto load_x = [&](int64_t tile) {
+        const int64_t row = tile * kTcRows + xr;
+        return (tile < tiles && row < rows) ? __ldg(reinterpret_cast<const uint4 *>(X + row * kIn) + xh)
+                                            : make_uint4(0u, 0u, 0u, 0u);
+    };
+    uint4 x_next = load_x(blockIdx.x);
+    for (int64_t tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+        const int64_t row0 = tile * kTcRows;
+        // X tile: 128 rows x two 16-byte halves (features 0-7, 8-15) into the core-matrix layout
+        *reinterpret_cast<uint4 *>(reinterpret_cast<unsigned char *>(S.A1) + (xr >> 3) * 256 + xh * 128 +
+                                   (xr & 7) * 16) = x_next;
+        tc_sync_for_mma();
+        // layer 1: D[0,128) = X W1
+        if (tid == 0) {
+            tc_mma(tmem, umma_desc(S.A1, 128, (kIn / 8) * 128), umma_desc(S.B1, 128, (kIn / 8) * 128), kIdesc, 0u);
+            tc_commit(&S.bar);
+        }
+        x_next = load_x(tile + gridDim.x);
+        ok = tc_wait(&S.bar, phase);
+        ok = __syncthreads_and(ok);
+        if (!ok)
+            break;
+        phase ^= 1u;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        for (int c = 0; c < kHid / 32; ++c) {
+        // H1 = bf16(relu(acc + b1)): 8 consecutive columns of a row are one 16-byte chunk of A2
+        for (int cc = 0; cc < 64; cc += 32) {
             uint32_t v[32];
-            tc_ld32(tmem + lane_off + (uint32_t)(c * 32), v);
+            tc_ld32(tmem + lane_off + (uint32_t)(c0 + cc), v);
 #pragma unroll
-            for (int q = 0; q < 32; ++q) {
-                const int col = c * 32 + q;
-                S.A2[core_idx(r, col, kHid)] = __float2bfloat16(fmaxf(__uint_as_float(v[q]) + S.b1[col], 0.f));
+            for (int g = 0; g < 4; ++g) {
+                const int col = c0 + cc + 8 * g;
+                const float4 ba = *reinterpret_cast<const float4 *>(&S.b1[col]);
+                const float4 bb = *reinterpret_cast<const float4 *>(&S.b1[col + 4]);
+                uint4 o;
+                o.x = pack_bf16x2(fmaxf(__uint_as_float(v[8 * g + 0]) + ba.x, 0.f),
+                                  fmaxf(__uint_as_float(v[8 * g + 1]) + ba.y, 0.f));
+                o.y = pack_bf16x2(fmaxf(__uint_as_float(v[8 * g + 2]) + ba.z, 0.f),
+                                  fmaxf(__uint_as_float(v[8 * g + 3]) + ba.w, 0.f));
+                o.z = pack_bf16x2(fmaxf(__uint_as_float(v[8 * g + 4]) + bb.x, 0.f),
+                                  fmaxf(__uint_as_float(v[8 * g + 5]) + bb.y, 0.f));
+                o.w = pack_bf16x2(fmaxf(__uint_as_float(v[8 * g + 6]) + bb.z, 0.f),
+                                  fmaxf(__uint_as_float(v[8 * g + 7]) + bb.w, 0.f));
+                *reinterpret_cast<uint4 *>(S.A2 + core_idx(r, col, kHid)) = o;
             }
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        tc_sync_for_mma();
         // layer 2: D[128,256) = H1 W2, eight k-steps of 16
         if (tid == 0) {
 #pragma unroll
@@ -276,30 +322,39 @@ __global__ void __launch_bounds__(128) k_mlp_fwd_tc(const __nv_bfloat16 *__restr
                        umma_desc(S.B2 + s * 128, 128, (kHid / 8) * 128), kIdesc, s > 0 ? 1u : 0u);
             tc_commit(&S.bar);
         }
-        pending = 1;
-        ok = tc_wait(&S.bar, 1);
+        ok = tc_wait(&S.bar, phase);
         ok = __syncthreads_and(ok);
-        if (ok) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            float ysum = 0.f;
-            for (int c = 0; c < kHid / 32; ++c) {
-                uint32_t v[32];
-                tc_ld32(tmem + lane_off + 128u + (uint32_t)(c * 32), v);
+        if (!ok)
+            break;
+        phase ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // y = w3 . bf16(relu(acc + b2)) + b3, the two column halves added through shared memory
+        float ysum = 0.f;
+        for (int cc = 0; cc < 64; cc += 32) {
+            uint32_t v[32];
+            tc_ld32(tmem + lane_off + 128u + (uint32_t)(c0 + cc), v);
 #pragma unroll
-                for (int q = 0; q < 32; ++q) {
-                    const int col = c * 32 + q;
-                    const float h2 = __bfloat162float(__float2bfloat16(fmaxf(__uint_as_float(v[q]) + S.b2[col], 0.f)));
-                    ysum += h2 * S.w3[col];
-                }
+            for (int q = 0; q < 32; q += 2) {
+                const int col = c0 + cc + q;
+                const float2 bv = *reinterpret_cast<const float2 *>(&S.b2[col]);
+                const float2 wv = *reinterpret_cast<const float2 *>(&S.w3[col]);
+                const uint32_t hb = pack_bf16x2(fmaxf(__uint_as_float(v[q]) + bv.x, 0.f),
+                                                fmaxf(__uint_as_float(v[q + 1]) + bv.y, 0.f));
+                ysum = fmaf(__uint_as_float(hb << 16), wv.x, ysum);
+                ysum = fmaf(__uint_as_float(hb & 0xffff0000u), wv.y, ysum);
             }
-            if (row0 + r < rows)
-                y_out[row0 + r] = ysum + P[kOffB3];
         }
+        if (half == 1)
+            S.part[r] = ysum;
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();  // also: every warp is done with this tile's TMEM and A tiles
+        if (half == 0 && row0 + r < rows)
+            y_out[row0 + r] = ysum + S.part[r] + b3;
     }
     if (!ok) {
         if (tid == 0)
             atomicExch(err, (int)PM_ERR_TIMEOUT);
-        (void)tc_wait(&S.bar, pending);  // let an MMA in flight finish (bounded) before its memory is released
+        (void)tc_wait(&S.bar, phase);  // let an MMA in flight finish (bounded) before its memory is released
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -620,15 +675,16 @@ __global__ void k_refresh_bf16(const float *__restrict__ P, __nv_bfloat16 *__res
 // Swap statistics: one CTA per individual; accumulators in shared memory when
 // they fit (else in the output arrays, zeroed by the caller).
 // ---------------------------------------------------------------------------
-template <typename Acc>
-__global__ void __launch_bounds__(1024) k_swap_stats(const uint16_t *__restrict__ pi,
+template <typename Acc, bool kCum>
+__global__ void __launch_bounds__(1024, 2) k_swap_stats(const uint16_t *__restrict__ pi,
                                                      const int32_t *__restrict__ delta, int64_t n, int32_t L,
                                                      int64_t stride, int32_t W, int32_t m,
                                                      const uint32_t *__restrict__ masks, int64_t pop,
                                                      unsigned long long *__restrict__ gain, int *__restrict__ cap,
                                                      unsigned long long *__restrict__ loss, int *__restrict__ assign,
-                                                     int in_smem, int cum)
+                                                     int in_smem)
 {
+    constexpr bool cum = kCum;  // the tables hold D' (running sums of Delta')
     extern __shared__ __align__(16) unsigned char sm[];
     const int64_t t = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -1073,6 +1129,7 @@ pm_status pm_learn_prepare(const pm_instance *inst);
 
 struct pm_model {
     int device = 0;
+    int sm_count = 1;
     pm_dbuf P, M, V, G, W1b, W2b, w3b, loss, err;
     int64_t step = 0;
     std::mutex lock;
@@ -1117,6 +1174,10 @@ extern "C" pm_status pm_model_create(int device, uint64_t seed, pm_model **out)
     if (!md)
         return PM_ERR_OOM;
     md->device = device;
+    if (cudaDeviceGetAttribute(&md->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+        delete md;
+        return PM_ERR_CUDA;
+    }
     pm_status st = PM_OK;
     pm_dbuf *bufs[] = {&md->P, &md->M, &md->V, &md->G};
     for (pm_dbuf *b : bufs)
@@ -1225,8 +1286,8 @@ static pm_status mlp_launch(pm_model *md, bool train, const void *x, int64_t row
                                                       static_cast<float *>(md->G.ptr),
                                                       static_cast<float *>(md->loss.ptr));
     else
-        k_mlp_fwd_tc<<<(unsigned)pm_ceil_div(rows, kTcRows), 128, tc_smem(), s>>>(
-            X, rows, W1b, W2b, w3b, P, y, static_cast<int *>(md->err.ptr));
+        k_mlp_fwd_tc<<<(unsigned)std::min<int64_t>(pm_ceil_div(rows, kTcRows), 2 * (int64_t)md->sm_count),
+                       kTcThreads, tc_smem(), s>>>(X, rows, W1b, W2b, w3b, P, y, static_cast<int *>(md->err.ptr));
     PM_CUDA(cudaGetLastError());
     return PM_OK;
 }
@@ -1244,6 +1305,8 @@ extern "C" pm_status pm_model_forward(pm_model *md, const uint16_t *x, int64_t r
         return PM_ERR_INVALID_ARG;
     if (!pm_is_device_ptr(x) || !pm_is_device_ptr(y))
         return PM_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(x) & 15u) != 0)
+        return PM_ERR_INVALID_ARG;  // input rows are read as 16-byte vectors
     PM_CUDA(cudaSetDevice(md->device));
     return pm_model_forward_dev(md, x, rows, y, static_cast<cudaStream_t>(stream));
 }
@@ -1335,11 +1398,18 @@ pm_status pm_launch_swap_stats(const pm_instance *inst, const uint32_t *masks, i
 #define PM_STATS_ARGS                                                                                              \
     inst->pi, inst->delta, inst->n, (int32_t)inst->L, inst->stride, (int32_t)inst->W, (int32_t)inst->m, masks, pop, \
         reinterpret_cast<unsigned long long *>(gain), cap, reinterpret_cast<unsigned long long *>(loss), assign,     \
-        in_smem ? 1 : 0, inst->cum ? 1 : 0
-    if (narrow && in_smem)
-        k_swap_stats<unsigned int><<<(unsigned)pop, 1024, smem, s>>>(PM_STATS_ARGS);
-    else
-        k_swap_stats<unsigned long long><<<(unsigned)pop, 1024, smem, s>>>(PM_STATS_ARGS);
+        in_smem ? 1 : 0
+    if (narrow && in_smem) {
+        if (inst->cum)
+            k_swap_stats<unsigned int, true><<<(unsigned)pop, 1024, smem, s>>>(PM_STATS_ARGS);
+        else
+            k_swap_stats<unsigned int, false><<<(unsigned)pop, 1024, smem, s>>>(PM_STATS_ARGS);
+    } else {
+        if (inst->cum)
+            k_swap_stats<unsigned long long, true><<<(unsigned)pop, 1024, smem, s>>>(PM_STATS_ARGS);
+        else
+            k_swap_stats<unsigned long long, false><<<(unsigned)pop, 1024, smem, s>>>(PM_STATS_ARGS);
+    }
 #undef PM_STATS_ARGS
     PM_CUDA(cudaGetLastError());
     return PM_OK;
@@ -1410,8 +1480,12 @@ int pm_mlp_in_width() { return kIn; }
 pm_status pm_learn_prepare(const pm_instance *inst)
 {
     const int cap = (int)(inst->smem_optin > 1024 ? inst->smem_optin - 1024 : inst->smem_optin);
-    PM_CUDA(cudaFuncSetAttribute(k_swap_stats<unsigned int>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
-    PM_CUDA(cudaFuncSetAttribute(k_swap_stats<unsigned long long>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+    PM_CUDA(cudaFuncSetAttribute(k_swap_stats<unsigned int, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+    PM_CUDA(cudaFuncSetAttribute(k_swap_stats<unsigned int, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+    PM_CUDA(cudaFuncSetAttribute(k_swap_stats<unsigned long long, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 cap));
+    PM_CUDA(cudaFuncSetAttribute(k_swap_stats<unsigned long long, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 cap));
     PM_CUDA(cudaFuncSetAttribute(k_candidates, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
     return mlp_init_attrs();
 }
