@@ -271,6 +271,81 @@ __global__ void __launch_bounds__(32) k_ga_init(const ga_prob *__restrict__ gps,
     }
 }
 
+// The same fresh population as k_ga_init with one warp per individual: the
+// lanes compute the p Philox draws of Floyd's sampling in parallel (lane l
+// the counter blocks l, l + 32, ...), then lane 0 runs the p dependent
+// insertions on the warp's bitset in shared memory.  CTA = 32 warps = 32
+// individuals; needs 32 * W words of shared memory.
+__global__ void __launch_bounds__(1024) k_ga_init_warp(const ga_prob *__restrict__ gps, int K, ga_prob one,
+                                                       uint32_t *__restrict__ X, uint8_t *__restrict__ improved,
+                                                       uint32_t *__restrict__ active,
+                                                       const uint32_t *__restrict__ deme_best, uint64_t seed,
+                                                       const ga_dev *__restrict__ st, ColumnsOut co)
+{
+    pm_grid_dependency_wait();
+    extern __shared__ uint32_t wrows[];  // [32][W] bitsets, then [32][p] draws
+    __shared__ uint32_t on_s;
+    int k;
+    const ga_prob gp = prob_of_group(gps, K, one, blockIdx.x, k);
+    const int lane = threadIdx.x & 31;
+    const int j = threadIdx.x >> 5;
+    const int64_t t0 = (blockIdx.x - gp.grp_base) * 32;
+    const int64_t t = t0 + j;
+    const int32_t W = gp.W, m = gp.m, p = gp.p;
+    if (st[k].stop) {
+        if (threadIdx.x == 0)
+            active[(gp.ind_base + t0) >> 5] = 0u;
+        return;
+    }
+    if (threadIdx.x == 0)
+        on_s = 0u;
+    __syncthreads();
+    const uint32_t gen = (uint32_t)st[k].gen;
+    uint32_t *row = wrows + (int64_t)j * W;
+    uint32_t *draws = wrows + (int64_t)32 * W + (int64_t)j * p;
+    if (t < gp.pop) {
+        if (lane == 0) {
+            improved[gp.ind_base + t] = 0;
+            atomicOr(&on_s, 1u << j);
+        }
+        const bool migrant = gen > 0 && (gp.team ? t < gp.NB : (t % gp.D) == 0);
+        if (migrant) {
+            const uint32_t *src = deme_best + gp.dword_base + (gp.team ? t : t / gp.D) * W;
+            for (int w = lane; w < W; w += 32)
+                row[w] = src[w];
+        } else {
+            for (int w = lane; w < W; w += 32)
+                row[w] = 0u;
+            // draw q of Floyd's sampling is uniform below m - p + q + 1 (word q & 3 of counter block q >> 2)
+            for (int b = lane; 4 * b < p; b += 32) {
+                const uint4 v = draw_block(seed, gen, (uint32_t)t, OP_INIT, (uint32_t)b, gp.sid);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int q = 4 * b + i;
+                    if (q < p)
+                        draws[q] = uniform_below(word_of(v, (uint32_t)i), (uint32_t)(m - p + q + 1));
+                }
+            }
+            __syncwarp();
+            if (lane == 0) {
+                for (int q = 0; q < p; ++q) {
+                    const uint32_t c = draws[q];
+                    const uint32_t jj = (uint32_t)(m - p + q);
+                    const uint32_t pick = ((row[c >> 5] >> (c & 31)) & 1u) ? jj : c;
+                    row[pick >> 5] |= 1u << (pick & 31);
+                }
+            }
+        }
+        __syncwarp();
+        for (int w = lane; w < W; w += 32)
+            X[gp.word_base + t * W + w] = row[w];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        active[(gp.ind_base + t0) >> 5] = on_s;
+    write_columns(wrows, W, t0, gp, co, lane, j, 32);
+}
+
 // ------------------- combinadic chromosome generation -----------------------
 // Section 4.1 draws a chromosome as the i-th p-combination of {0..m-1} in
 // lexicographic order for a random i below C(m, p).  C(900, 90) is about
@@ -1096,6 +1171,10 @@ static pm_status enqueue_generation(pm_ga *ga, cudaStream_t s, cudaGraphConditio
     const unsigned groups = (unsigned)ga->groups_total;
     const size_t init_smem = (size_t)32 * (ga->Wmax | 1) * 4;
     const int rows_in_smem = init_smem <= 48 * 1024 ? 1 : 0;
+    int32_t pmax = 1;
+    for (const ga_prob &g : ga->gps)
+        pmax = std::max(pmax, g.p);
+    const size_t warp_init_smem = (size_t)32 * ((size_t)ga->Wmax + (size_t)pmax) * 4;
 
     if (ga->comb) {
         const uint32_t *T = static_cast<const uint32_t *>(ga->comb_tab.ptr);
@@ -1118,6 +1197,9 @@ static pm_status enqueue_generation(pm_ga *ga, cudaStream_t s, cudaGraphConditio
                               ga->seed, st, co));
             break;
         }
+    } else if (warp_init_smem <= 200 * 1024) {
+        PM_CUDA(pm_launch(k_ga_init_warp, groups, 1024, warp_init_smem, s, gps, K, one, X, improved, active,
+                          static_cast<const uint32_t *>(ga->deme_best.ptr), ga->seed, st, co));
     } else {
         PM_CUDA(pm_launch(k_ga_init, groups, 32, rows_in_smem ? init_smem : 0, s, gps, K, one, X, improved, active,
                           static_cast<const uint32_t *>(ga->deme_best.ptr), ga->seed, st, co, rows_in_smem));
@@ -1327,6 +1409,8 @@ static pm_status ga_configure(pm_ga *ga, int64_t pop, uint64_t seed, const pm_ga
 
 static pm_status ga_create_common(pm_ga *ga, cudaStream_t s)
 {
+    // the warp-per-individual initialisation may use up to 200 KB of shared memory (set outside any capture)
+    PM_CUDA(cudaFuncSetAttribute(k_ga_init_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     pm_status st = ga_alloc(ga, s);
     if (st == PM_OK)
         st = build_graph(ga);
