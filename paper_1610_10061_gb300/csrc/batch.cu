@@ -77,6 +77,7 @@ pm_status pm_plan_multi(const std::vector<const pm_instance *> &insts, const std
         splits = std::max<int64_t>(1, std::min<int64_t>(splits, std::max<int64_t>(1, in->n / warps)));
         pr.splits = splits;
         pr.cps = pm_ceil_div(in->n, splits);
+        pr.packed = pm_packed_reduction_ok(in, splits) ? 1 : 0;
         pr.ind_base = ind;
         pr.out_base = 0;  // set by the caller for packed outputs
         pr.word_base = words;

@@ -48,6 +48,7 @@ namespace {
 constexpr int kMaxG = 4;
 constexpr uint32_t kSpinLimit = 1u << 22;  // bounded mbarrier wait (a few seconds at most)
 constexpr int kSparseLanes = 3;            // resolve by walking hit lanes up to this many
+constexpr int kCountShift = 48;            // packed split reduction: count in bits 48..63, sum below
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -156,8 +157,7 @@ __global__ void k_pop_to_columns(const uint32_t *__restrict__ masks, const pm_pr
 // individuals; every resolved individual's distance is added to acc[g] at
 // the lane of the individual.  load(cc, base, j, dl) yields rank base + lane
 // of client cc (Pi' and Delta', zeros past the row or past c_end); the
-// caller passes the first two steps of client c and the first step of client
-// c + step already loaded.
+// caller passes the first two steps of clients c and c + step already loaded.
 //
 // With cumulative tables (cum) the row holds D' -- the running sums of Delta',
 // i.e. the sorted distances -- so a step needs neither the carry nor the warp
@@ -166,7 +166,8 @@ template <int G, typename Ld>
 __device__ __forceinline__ void scan_clients(const uint32_t *__restrict__ colbits, const uint32_t (&a0)[G], int64_t c,
                                              int64_t c_end, int step, int32_t L, int lane, bool cum, Ld &load,
                                              uint32_t j_cur, int32_t d_cur, uint32_t j_nxt, int32_t d_nxt,
-                                             uint32_t j_nc, int32_t d_nc, unsigned long long (&acc)[G])
+                                             uint32_t j_nc, int32_t d_nc, uint32_t j_nc1, int32_t d_nc1,
+                                             unsigned long long (&acc)[G])
 {
     uint32_t a[G];
 #pragma unroll
@@ -243,14 +244,16 @@ __device__ __forceinline__ void scan_clients(const uint32_t *__restrict__ colbit
             load(c, base + 32, j_nxt, d_nxt);
             continue;
         }
-        // next client of this warp
+        // next client of this warp: its first two steps were loaded a client ago; load the next one's
         c += step;
         if (c >= c_end)
             break;
         j_cur = j_nc;
         d_cur = d_nc;
-        load(c, 32, j_nxt, d_nxt);
+        j_nxt = j_nc1;
+        d_nxt = d_nc1;
         load(c + step, 0, j_nc, d_nc);
+        load(c + step, 32, j_nc1, d_nc1);
         base = 0;
         carry = 0;
 #pragma unroll
@@ -268,11 +271,12 @@ struct ScanEpilogue {
     uint8_t *improved;           // mode 1, nullable
 };
 
-// The epilogue of one tile, one warp per individual: store the cost, or
+// The epilogue of one tile's individuals marked in fin_s (bit i of word i/32),
+// one warp per individual: store the cost, or
 // accept the candidate (copy its bitset, cost and improved flag) when it is
 // strictly cheaper than the current individual.
 template <int G>
-__device__ __forceinline__ void apply_epilogue(const unsigned long long *acc_s, const uint32_t *a0_s, const pm_prob &pr,
+__device__ __forceinline__ void apply_epilogue(const unsigned long long *acc_s, const uint32_t *fin_s, const pm_prob &pr,
                                                int64_t ind0, int warp, int nwarps, int lane, const ScanEpilogue &ep)
 {
     const int32_t W = pr.W;
@@ -280,7 +284,7 @@ __device__ __forceinline__ void apply_epilogue(const unsigned long long *acc_s, 
         const int64_t t = ind0 + i;
         if (t >= pr.pop)
             break;
-        if (!((a0_s[i >> 5] >> (i & 31)) & 1u))
+        if (!((fin_s[i >> 5] >> (i & 31)) & 1u))
             continue;
         const int64_t sum = (int64_t)acc_s[i];
         if (ep.costs != nullptr && lane == 0)
@@ -316,7 +320,7 @@ __global__ void __launch_bounds__(1024) k_scan_columns(const pm_prob *__restrict
     pm_grid_dependency_wait();
     extern __shared__ __align__(128) uint32_t colbits[];  // [32W][G]
     __shared__ unsigned long long acc_s[G * 32];
-    __shared__ uint32_t a0_s[G];
+    __shared__ uint32_t a0_s[G], fin_s[G];
     __shared__ __align__(8) uint64_t bar;
     __shared__ int last_s;
     __shared__ pm_prob pr_s;
@@ -383,11 +387,12 @@ __global__ void __launch_bounds__(1024) k_scan_columns(const pm_prob *__restrict
             }
         };
         int64_t c = c_begin + warp;
-        uint32_t j_cur, j_nxt, j_nc;
-        int32_t d_cur, d_nxt, d_nc;
+        uint32_t j_cur, j_nxt, j_nc, j_nc1;
+        int32_t d_cur, d_nxt, d_nc, d_nc1;
         load(c, 0, j_cur, d_cur);
         load(c, 32, j_nxt, d_nxt);
         load(c + nwarps, 0, j_nc, d_nc);
+        load(c + nwarps, 32, j_nc1, d_nc1);
 
         if (reload) {
             // bounded wait for the tile (every thread waits)
@@ -421,7 +426,7 @@ __global__ void __launch_bounds__(1024) k_scan_columns(const pm_prob *__restrict
 
         if (any0 && c < c_end)
             scan_clients<G>(colbits, a0, c, c_end, nwarps, L, lane, pr.cum != 0, load, j_cur, d_cur, j_nxt, d_nxt, j_nc,
-                            d_nc, acc);
+                            d_nc, j_nc1, d_nc1, acc);
 #pragma unroll
         for (int g = 0; g < G; ++g)
             if (acc[g])
@@ -429,7 +434,30 @@ __global__ void __launch_bounds__(1024) k_scan_columns(const pm_prob *__restrict
         __syncthreads();
 
         bool finish = true;
-        if (pr.splits > 1) {
+        const uint32_t *fin = a0_s;  // individuals whose epilogue this CTA applies
+        if (pr.splits > 1 && pr.packed) {
+            // one atomic per individual carries the split's sum plus one count in the top 16 bits; the split
+            // that brings the count to `splits` holds the total, applies that individual's epilogue and leaves
+            // the word zero for the next launch -- no fences, no tile ticket
+            for (int i = threadIdx.x; i < G * 32; i += blockDim.x) {
+                const int64_t t = ind0 + i;
+                bool last = false;
+                if (t < pop && ((a0_s[i >> 5] >> (i & 31)) & 1u)) {
+                    const unsigned long long add = acc_s[i] + (1ull << kCountShift);
+                    const unsigned long long old = atomicAdd(accum + pr.ind_base + t, add);
+                    if ((old >> kCountShift) == (unsigned long long)(pr.splits - 1)) {
+                        acc_s[i] = (old + add) & ((1ull << kCountShift) - 1ull);
+                        accum[pr.ind_base + t] = 0ull;
+                        last = true;
+                    }
+                }
+                const uint32_t b = __ballot_sync(PM_FULL_MASK, last);
+                if ((i & 31) == 0)
+                    fin_s[i >> 5] = b;
+            }
+            __syncthreads();
+            fin = fin_s;
+        } else if (pr.splits > 1) {
             // add this split's sums into the instance's accumulators; the last split of the tile
             // (atomic ticket) reads the totals and leaves the accumulators zero again
             for (int i = threadIdx.x; i < G * 32; i += blockDim.x) {
@@ -458,7 +486,7 @@ __global__ void __launch_bounds__(1024) k_scan_columns(const pm_prob *__restrict
             }
         }
         if (finish)
-            apply_epilogue<G>(acc_s, a0_s, pr, ind0, warp, nwarps, lane, ep);
+            apply_epilogue<G>(acc_s, fin, pr, ind0, warp, nwarps, lane, ep);
         __syncthreads();  // shared state (tile, acc_s, a0_s, pr_s) is reused by the next item
     }
 }
@@ -714,6 +742,7 @@ pm_prob pm_single_prob(const pm_instance *inst, const pm_eval_plan &plan, int64_
     pr.m = (int32_t)inst->m;
     pr.p = (int32_t)inst->p;
     pr.cum = inst->cum ? 1 : 0;
+    pr.packed = pm_packed_reduction_ok(inst, plan.splits) ? 1 : 0;
     pr.pop = pop;
     pr.tiles = plan.tiles;
     pr.splits = plan.splits;

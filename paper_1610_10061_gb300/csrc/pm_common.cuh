@@ -64,7 +64,8 @@ struct pm_prob {
     const int32_t *delta;  // Delta', or D' (running sums) when cum
     int64_t n, stride;
     int32_t L, W, m, p;
-    int32_t cum, pad;
+    int32_t cum;
+    int32_t packed;  // split sums and a split count share one 64-bit word (see pm_packed_reduction_ok)
     int64_t pop;
     int64_t ind_base;   // accumulators, active bits, GA per-individual arrays
     int64_t out_base;   // caller's cost array
@@ -146,6 +147,14 @@ size_t pm_plan_ticket_bytes(const pm_eval_plan &plan);
 // Kernels one evaluation launches under the plan (column path: transpose +
 // scan with fused reduction; row path: scan + reduction).
 static inline int64_t pm_plan_kernels(const pm_eval_plan &plan) { return plan.groups ? 2 : 2; }
+// The packed split reduction holds a partial cost below 2^48 and a split
+// count below 2^16 in one 64-bit word: usable when every cost is below 2^47
+// (n * max d) and there are fewer than 2^16 splits.
+static inline bool pm_packed_reduction_ok(const pm_instance *inst, int64_t splits)
+{
+    const double bound = (double)inst->n * (double)std::max<int32_t>(inst->max_d, 1);
+    return splits < 65536 && bound < 140737488355328.0;  // 2^47
+}
 // Bytes of int64 partial sums (one per client split and individual).
 size_t pm_plan_partial_bytes(const pm_eval_plan &plan, int64_t pop);
 

@@ -415,3 +415,21 @@ def test_ga_combinadic_generation_matches_oracle(pm, m, n, p, pop, gens, kw):
     """Section 4.1's chromosome generation (multi-word random rank, lexicographic unranking) bit-exact."""
     d = euclid_instance(m, seed=m)[:n]
     _ga_compare(pm, d, p, pop, gens, check_every=1, init="combinadic", **kw)
+
+
+def test_split_reduction_both_protocols(pm):
+    """Costs below 2^47 use the packed split reduction (sum and split count in one atomic word); larger ones
+    (here n * max d > 2^47) fall back to per-tile tickets.  Both bit-exact, over several pinned split counts."""
+    rng = np.random.default_rng(21)
+    small = rng.integers(0, 1000, size=(300, 50)).astype(np.int32)
+    large = rng.integers(2**30, 2**31 - 1, size=(70000, 40)).astype(np.int32)  # 70000 * 2^31 > 2^47
+    for d, p in ((small, 6), (large, 5)):
+        inst = pm.Instance(d, p)
+        masks = random_masks(100, d.shape[1], p, seed=3)
+        expect = oracle.eval_direct(d, masks)
+        assert (d.shape[0] * int(d.max()) >= 2**47) == (d is large)  # the bound that selects the protocol
+        for G, splits in ((1, 3), (2, 7), (4, 2), (1, 1)):
+            inst.set_shape(100, groups=G, warps=8, splits=splits)
+            for _ in range(2):  # the second launch relies on the first leaving the scratch at zero
+                np.testing.assert_array_equal(inst.eval(masks), expect, err_msg=f"G={G} splits={splits}")
+        inst.close()
