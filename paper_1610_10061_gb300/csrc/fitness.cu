@@ -317,7 +317,8 @@ __global__ void __launch_bounds__(1024) k_scan_columns(const pm_prob *__restrict
                                                        int *__restrict__ tickets, int *__restrict__ err,
                                                        ScanEpilogue ep)
 {
-    pm_grid_dependency_wait();
+    // the previous kernel of the stream may still run until pm_grid_dependency_wait(): before it only the
+    // constant tables (Pi', Delta', the launch's problem table) are read
     extern __shared__ __align__(128) uint32_t colbits[];  // [32W][G]
     __shared__ unsigned long long acc_s[G * 32];
     __shared__ uint32_t a0_s[G], fin_s[G];
@@ -337,6 +338,7 @@ __global__ void __launch_bounds__(1024) k_scan_columns(const pm_prob *__restrict
 
     uint32_t phase = 0;
     int64_t loaded_tile = -1;  // global tile index of the tile in shared memory
+    bool waited = false;
     for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
         if (threadIdx.x == 0)
             pr_s = (K > 1) ? probs[find_prob(K, item, [&](int k) { return probs[k].item_base; })] : one;
@@ -352,6 +354,32 @@ __global__ void __launch_bounds__(1024) k_scan_columns(const pm_prob *__restrict
         const uint16_t *__restrict__ pi = pr.pi;
         const int32_t *__restrict__ delta = pr.delta;
         const bool reload = gtile != loaded_tile;
+
+        // first steps of this warp's first two clients (constant tables), loaded while the tile lands
+        const int64_t c_begin = split * pr.cps;
+        const int64_t c_end = (c_begin + pr.cps < pr.n) ? c_begin + pr.cps : pr.n;
+        auto load = [&](int64_t cc, int base, uint32_t &j, int32_t &dl) {
+            const int r = base + lane;
+            if (cc < c_end && r < L) {
+                j = __ldg(pi + cc * stride + r);
+                dl = __ldg(delta + cc * stride + r);
+            } else {
+                j = 0;
+                dl = 0;
+            }
+        };
+        int64_t c = c_begin + warp;
+        uint32_t j_cur, j_nxt, j_nc, j_nc1;
+        int32_t d_cur, d_nxt, d_nc, d_nc1;
+        load(c, 0, j_cur, d_cur);
+        load(c, 32, j_nxt, d_nxt);
+        load(c + nwarps, 0, j_nc, d_nc);
+        load(c + nwarps, 32, j_nc1, d_nc1);
+        if (!waited) {  // from here on: the columns, active bits and accumulators of the previous kernels
+            pm_grid_dependency_wait();
+            waited = true;
+        }
+
         if (reload && threadIdx.x == 0) {
             const uint32_t tile_bytes = (uint32_t)W * 32u * G * 4u;
             mbar_arrive_expect_tx(&bar, tile_bytes);
@@ -372,27 +400,6 @@ __global__ void __launch_bounds__(1024) k_scan_columns(const pm_prob *__restrict
         }
         for (int i = threadIdx.x; i < G * 32; i += blockDim.x)
             acc_s[i] = 0ull;
-
-        // first chunks of this warp's first two clients, loaded while the tile lands
-        const int64_t c_begin = split * pr.cps;
-        const int64_t c_end = (c_begin + pr.cps < pr.n) ? c_begin + pr.cps : pr.n;
-        auto load = [&](int64_t cc, int base, uint32_t &j, int32_t &dl) {
-            const int r = base + lane;
-            if (cc < c_end && r < L) {
-                j = __ldg(pi + cc * stride + r);
-                dl = __ldg(delta + cc * stride + r);
-            } else {
-                j = 0;
-                dl = 0;
-            }
-        };
-        int64_t c = c_begin + warp;
-        uint32_t j_cur, j_nxt, j_nc, j_nc1;
-        int32_t d_cur, d_nxt, d_nc, d_nc1;
-        load(c, 0, j_cur, d_cur);
-        load(c, 32, j_nxt, d_nxt);
-        load(c + nwarps, 0, j_nc, d_nc);
-        load(c + nwarps, 32, j_nc1, d_nc1);
 
         if (reload) {
             // bounded wait for the tile (every thread waits)
