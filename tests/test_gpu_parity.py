@@ -433,3 +433,26 @@ def test_split_reduction_both_protocols(pm):
             for _ in range(2):  # the second launch relies on the first leaving the scratch at zero
                 np.testing.assert_array_equal(inst.eval(masks), expect, err_msg=f"G={G} splits={splits}")
         inst.close()
+
+
+def test_client_sharded_evaluation_on_one_gpu(pm):
+    """Client blocks evaluated as separate instances add up to the full cost (the all-reduce of the
+    client-sharded evaluation, done here on the device with torch); with one rank the sharded evaluator is the
+    plain evaluation."""
+    from paper_1610_10061_gb300.shard import ShardedEvaluator, client_block
+
+    w = paper_shape_instance("graph900")
+    d, p = w["d"], w["p"]
+    masks = random_masks(256, 900, p, seed=13)
+    expect = oracle.eval_direct(d, masks)
+    dm = to_dev(masks)
+    total = torch.zeros(256, dtype=torch.int64, device="cuda")
+    for r in range(3):
+        lo, hi = client_block(900, r, 3)
+        inst = pm.Instance(d[lo:hi], p, cumulative=(r == 1))
+        total += inst.eval(dm)
+        inst.close()
+    np.testing.assert_array_equal(total.cpu().numpy(), expect)
+    ev = ShardedEvaluator(d, p)
+    np.testing.assert_array_equal(ev.eval(dm).cpu().numpy(), expect)
+    ev.close()
