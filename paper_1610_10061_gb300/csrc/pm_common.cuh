@@ -144,9 +144,6 @@ pm_eval_plan pm_plan_eval_with(const pm_instance *inst, int64_t pop, int G, int 
 // Bytes of per-tile tickets the plan needs (zero before the first launch;
 // every launch leaves them zero, whatever the plan).
 size_t pm_plan_ticket_bytes(const pm_eval_plan &plan);
-// Kernels one evaluation launches under the plan (column path: transpose +
-// scan with fused reduction; row path: scan + reduction).
-static inline int64_t pm_plan_kernels(const pm_eval_plan &plan) { return plan.groups ? 2 : 2; }
 // The packed split reduction holds a partial cost below 2^48 and a split
 // count below 2^16 in one 64-bit word: usable when every cost is below 2^47
 // (n * max d) and there are fewer than 2^16 splits.
