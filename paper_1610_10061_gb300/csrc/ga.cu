@@ -722,6 +722,54 @@ __device__ __forceinline__ uint32_t range_mask(int64_t lo, int64_t hi)  // bits 
     return upto & ~below;
 }
 
+// Try q's mutant F of the W-word row C (m bits) of individual t, built by a
+// warp (lanes over words): circular or block shift with the draws of
+// operation OP_MUT + q (reading R9).  F[a+i] = C[a + (i+kl) mod len].
+__device__ __forceinline__ void mutant_row(const uint32_t *__restrict__ C, uint32_t *__restrict__ F, int32_t W,
+                                           int32_t m, uint64_t seed, uint32_t gen, uint32_t t, uint32_t q,
+                                           uint32_t sid, int lane)
+{
+    const uint4 v0 = draw_block(seed, gen, (uint32_t)t, OP_MUT + q, 0, sid);
+    const uint32_t kind = uniform_below(v0.x, 2u);
+    const uint32_t right = uniform_below(v0.y, 2u);
+    int64_t a, len, kk;
+    if (kind == 0) {
+        a = 0;
+        len = m;
+        kk = 1 + uniform_below(v0.z, (uint32_t)(m - 1));
+    } else {
+        const uint4 v1 = draw_block(seed, gen, (uint32_t)t, OP_MUT + q, 1, sid);
+        const uint32_t x = uniform_below(v0.z, (uint32_t)m);
+        uint32_t y = uniform_below(v0.w, (uint32_t)(m - 1));
+        if (y >= x)
+            ++y;
+        const uint32_t lo = x < y ? x : y, hi = x < y ? y : x;
+        a = lo;
+        len = hi - lo + 1;
+        kk = 1 + uniform_below(v1.x, hi - lo);
+    }
+    const int64_t kl = right ? (len - kk) : kk;  // rotate left by kl, 1 <= kl < len
+    const int64_t pwrap = a + len - kl;          // positions >= pwrap wrap to the start of the block
+    for (int w = lane; w < W; w += 32) {
+        const int64_t pos0 = (int64_t)w * 32;
+        const int64_t in_lo = a > pos0 ? a : pos0;
+        const int64_t in_hi = (a + len) < (pos0 + 32) ? (a + len) : (pos0 + 32);
+        const uint32_t cw = __ldg(C + w);
+        if (in_lo >= in_hi) {
+            F[w] = cw;
+            continue;
+        }
+        uint32_t out = cw & ~range_mask(in_lo - pos0, in_hi - pos0);
+        const int64_t e1 = in_hi < pwrap ? in_hi : pwrap;
+        if (in_lo < e1)
+            out |= bits_from(C, W, pos0 + kl) & range_mask(in_lo - pos0, e1 - pos0);
+        const int64_t s2 = in_lo > pwrap ? in_lo : pwrap;
+        if (s2 < in_hi)
+            out |= bits_from(C, W, pos0 + kl - len) & range_mask(s2 - pos0, in_hi - pos0);
+        F[w] = out;
+    }
+}
+
 // One mutation try (Section 4.4).  CTA = 32 warps = 32 individuals; warp j
 // rotates individual t0 + j's bits [a, a+len) left by kl: F[a+i] =
 // C[a + (i+kl) mod len].  Each output word is at most three pieces, each a
@@ -752,48 +800,8 @@ __global__ void __launch_bounds__(1024) k_ga_mutate(const ga_prob *__restrict__ 
     if (t < gp.pop && improved[gp.ind_base + t] == 0) {
         if (lane == 0)
             atomicOr(&on_s, 1u << j);
-        const uint32_t gen = (uint32_t)st[k].gen;
-        const uint4 v0 = draw_block(seed, gen, (uint32_t)t, OP_MUT + q, 0, gp.sid);
-        const uint32_t kind = uniform_below(v0.x, 2u);
-        const uint32_t right = uniform_below(v0.y, 2u);
-        int64_t a, len, kk;
-        if (kind == 0) {
-            a = 0;
-            len = m;
-            kk = 1 + uniform_below(v0.z, (uint32_t)(m - 1));
-        } else {
-            const uint4 v1 = draw_block(seed, gen, (uint32_t)t, OP_MUT + q, 1, gp.sid);
-            const uint32_t x = uniform_below(v0.z, (uint32_t)m);
-            uint32_t y = uniform_below(v0.w, (uint32_t)(m - 1));
-            if (y >= x)
-                ++y;
-            const uint32_t lo = x < y ? x : y, hi = x < y ? y : x;
-            a = lo;
-            len = hi - lo + 1;
-            kk = 1 + uniform_below(v1.x, hi - lo);
-        }
-        const int64_t kl = right ? (len - kk) : kk;  // rotate left by kl, 1 <= kl < len
-        const int64_t pwrap = a + len - kl;          // positions >= pwrap wrap to the start of the block
-        const uint32_t *C = X + gp.word_base + t * W;
-        uint32_t *F = Xc + gp.word_base + t * W;
-        for (int w = lane; w < W; w += 32) {
-            const int64_t pos0 = (int64_t)w * 32;
-            const int64_t in_lo = a > pos0 ? a : pos0;
-            const int64_t in_hi = (a + len) < (pos0 + 32) ? (a + len) : (pos0 + 32);
-            const uint32_t cw = __ldg(C + w);
-            if (in_lo >= in_hi) {
-                F[w] = cw;
-                continue;
-            }
-            uint32_t out = cw & ~range_mask(in_lo - pos0, in_hi - pos0);
-            const int64_t e1 = in_hi < pwrap ? in_hi : pwrap;
-            if (in_lo < e1)
-                out |= bits_from(C, W, pos0 + kl) & range_mask(in_lo - pos0, e1 - pos0);
-            const int64_t s2 = in_lo > pwrap ? in_lo : pwrap;
-            if (s2 < in_hi)
-                out |= bits_from(C, W, pos0 + kl - len) & range_mask(s2 - pos0, in_hi - pos0);
-            F[w] = out;
-        }
+        mutant_row(X + gp.word_base + t * W, Xc + gp.word_base + t * W, W, m, seed, (uint32_t)st[k].gen, (uint32_t)t,
+                   q, gp.sid, lane);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -802,6 +810,98 @@ __global__ void __launch_bounds__(1024) k_ga_mutate(const ga_prob *__restrict__ 
             atomicAdd(reinterpret_cast<unsigned long long *>(&st[k].evals), (unsigned long long)__popc(on_s));
     }
     write_columns(Xc + gp.word_base + t0 * W, W, t0, gp, co, lane, j, 32);
+}
+
+// Speculative mutation cycle (single-instance GAs on the column path).  Every
+// try mutates the individual as it stood when the cycle began (an individual
+// stops at its first strict improvement), so all Q tries of all individuals
+// can be built and evaluated at once and the first improving try kept:
+// candidate u = q * pop + t is try q of individual t.  The result and the
+// evaluation count (tries an individual reaches) equal the cycle run try by
+// try; the tries after an individual's first improvement are evaluated but
+// not counted.  CTA = 32 warps = 32 candidates; `gq` lays out the Q x pop
+// candidates (pop = Q * pop, all bases 0) for the columns.
+__global__ void __launch_bounds__(1024) k_ga_mutate_all(ga_prob gp, ga_prob gq, int32_t Q,
+                                                        const uint32_t *__restrict__ X, uint32_t *__restrict__ XQ,
+                                                        uint32_t *__restrict__ activeQ,
+                                                        const uint8_t *__restrict__ improved, uint64_t seed,
+                                                        const ga_dev *__restrict__ st, ColumnsOut coQ)
+{
+    pm_grid_dependency_wait();
+    __shared__ uint32_t on_s;
+    const int lane = threadIdx.x & 31;
+    const int j = threadIdx.x >> 5;
+    const int64_t u0 = (int64_t)blockIdx.x * 32;
+    const int64_t u = u0 + j;
+    const int32_t W = gp.W;
+    if (st[0].stop) {
+        if (threadIdx.x == 0)
+            activeQ[u0 >> 5] = 0u;
+        return;
+    }
+    if (threadIdx.x == 0)
+        on_s = 0u;
+    __syncthreads();
+    if (u < gq.pop) {
+        const int64_t q = u / gp.pop, t = u - q * gp.pop;
+        if (improved[t] == 0) {
+            if (lane == 0)
+                atomicOr(&on_s, 1u << j);
+            mutant_row(X + t * W, XQ + u * W, W, gp.m, seed, (uint32_t)st[0].gen, (uint32_t)t, (uint32_t)q, gp.sid,
+                       lane);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        activeQ[u0 >> 5] = on_s;
+    write_columns(XQ + u0 * W, W, u0, gq, coQ, lane, j, 32);
+}
+
+// Keep each individual's first improving try (warp per individual, 8 per
+// CTA) and count the tries it reaches: q + 1 for an improvement at try q,
+// else Q; none for an individual already improved in this generation.
+__global__ void __launch_bounds__(256) k_ga_mutate_accept(ga_prob gp, int32_t Q, uint32_t *__restrict__ X,
+                                                          const uint32_t *__restrict__ XQ, int64_t *__restrict__ cost,
+                                                          const int64_t *__restrict__ costQ,
+                                                          uint8_t *__restrict__ improved, ga_dev *__restrict__ st)
+{
+    pm_grid_dependency_wait();
+    __shared__ unsigned long long tries_s;
+    const int lane = threadIdx.x & 31;
+    const int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int32_t W = gp.W;
+    if (st[0].stop)
+        return;
+    if (threadIdx.x == 0)
+        tries_s = 0ull;
+    __syncthreads();
+    if (t < gp.pop && improved[t] == 0) {
+        const int64_t c0 = cost[t];
+        int qs = Q;  // first improving try; every lane takes the same iterations and the same break
+        for (int base = 0; base < Q; base += 32) {
+            const int q = base + lane;
+            const bool hit = q < Q && costQ[(int64_t)q * gp.pop + t] < c0;
+            const uint32_t b = __ballot_sync(PM_FULL_MASK, hit);
+            if (b) {
+                qs = base + __ffs(b) - 1;
+                break;
+            }
+        }
+        if (qs < Q) {
+            const int64_t u = (int64_t)qs * gp.pop + t;
+            for (int w = lane; w < W; w += 32)
+                X[t * W + w] = XQ[u * W + w];
+            if (lane == 0) {
+                cost[t] = costQ[u];
+                improved[t] = 1;
+            }
+        }
+        if (lane == 0)
+            atomicAdd(&tries_s, (unsigned long long)(qs < Q ? qs + 1 : Q));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && tries_s)
+        atomicAdd(reinterpret_cast<unsigned long long *>(&st[0].evals), tries_s);
 }
 
 // Lowest (cost, index) in each deme -> deme_best / deme_cost.  One CTA per deme.
@@ -1085,6 +1185,12 @@ struct pm_ga {
     int comb_K = 0, comb_Q = 0;
     pm_dbuf comb_tab;
     bool single_row = false;  // one instance whose evaluation uses the row kernel
+    // speculative mutation cycle: all Q tries evaluated in one scan (single instance, column path)
+    bool spec = false;
+    pm_eval_plan spec_single;
+    pm_multi_plan spec_plan;
+    ga_prob gq{};
+    pm_dbuf XQ, costQ, activeQ, accumQ, ticketsQ, colQ;
     pm_eval_plan single;      // K == 1: the single-instance plan
     pm_multi_plan plan;       // the scan plan over all instances
     std::vector<ga_prob> gps;
@@ -1116,7 +1222,7 @@ static void ga_free(pm_ga *ga)
                        &ga->deme_cost, &ga->best, &ga->trace, &ga->accum,  &ga->tickets,  &ga->columns,
                        &ga->st,        &ga->glob, &ga->err,   &ga->probs,  &ga->gprobs,
                        &ga->s_gain,    &ga->s_cap, &ga->s_loss, &ga->s_assign, &ga->moves, &ga->xfeat, &ga->scores,
-                       &ga->comb_tab};
+                       &ga->comb_tab,  &ga->XQ,    &ga->costQ, &ga->activeQ, &ga->accumQ, &ga->ticketsQ, &ga->colQ};
     for (pm_dbuf *b : bufs)
         b->release();
     delete ga;
@@ -1127,6 +1233,14 @@ static void ga_free(pm_ga *ga)
 static bool graph_mode()
 {
     const char *v = std::getenv("PM_GA_GRAPH");
+    return !(v && v[0] == '0');
+}
+
+// PM_GA_SPEC=0 in the environment runs the mutation cycle try by try even where the speculative cycle applies
+// (identical results; for comparison).
+static bool spec_allowed()
+{
+    const char *v = std::getenv("PM_GA_SPEC");
     return !(v && v[0] == '0');
 }
 
@@ -1238,11 +1352,37 @@ static pm_status enqueue_generation(pm_ga *ga, cudaStream_t s, cudaGraphConditio
         acc.improved = improved;
         PM_TRY(ga_eval(ga, Xc, nullptr, acc, s));
     }
-    for (int q = 0; q < ga->Q; ++q) {
-        PM_CUDA(pm_launch(k_ga_mutate, groups, 1024, 0, s, gps, K, one, X, Xc, active, improved, (uint32_t)q,
-                          ga->seed, st, co));
-        acc.improved = improved;
-        PM_TRY(ga_eval(ga, Xc, nullptr, acc, s));
+    if (ga->spec) {
+        // all Q tries at once: mutants -> one scan storing their costs -> first improving try per individual
+        uint32_t *XQ = static_cast<uint32_t *>(ga->XQ.ptr);
+        uint32_t *activeQ = static_cast<uint32_t *>(ga->activeQ.ptr);
+        int64_t *costQ = static_cast<int64_t *>(ga->costQ.ptr);
+        ColumnsOut coQ;
+        coQ.colT = static_cast<uint32_t *>(ga->colQ.ptr);
+        coQ.G = ga->spec_plan.groups;
+        const int64_t QP = (int64_t)ga->Q * ga->P;
+        PM_CUDA(pm_launch(k_ga_mutate_all, (unsigned)pm_ceil_div(QP, 32), 1024, 0, s, one, ga->gq, (int32_t)ga->Q, X,
+                          XQ, activeQ, improved, ga->seed, st, coQ));
+        pm_scan_launch L;
+        pm_scan_launch_from(ga->spec_plan, nullptr, L);
+        L.masks = XQ;
+        L.colT = coQ.colT;
+        L.active = activeQ;
+        L.accum = static_cast<int64_t *>(ga->accumQ.ptr);
+        L.tickets = static_cast<int *>(ga->ticketsQ.ptr);
+        L.err = static_cast<int *>(ga->err.ptr);
+        pm_accept_args store;
+        store.columns_ready = true;
+        PM_TRY(pm_launch_scan(L, store, costQ, ga->spec_plan.smem, s));
+        PM_CUDA(pm_launch(k_ga_mutate_accept, (unsigned)pm_ceil_div(ga->P, 8), 256, 0, s, one, (int32_t)ga->Q, X, XQ,
+                          cost, costQ, improved, st));
+    } else {
+        for (int q = 0; q < ga->Q; ++q) {
+            PM_CUDA(pm_launch(k_ga_mutate, groups, 1024, 0, s, gps, K, one, X, Xc, active, improved, (uint32_t)q,
+                              ga->seed, st, co));
+            acc.improved = improved;
+            PM_TRY(ga_eval(ga, Xc, nullptr, acc, s));
+        }
     }
     const int dthreads = (int)pm_round_up(std::min<int64_t>(ga->D, 1024), 32);
     PM_CUDA(pm_launch(k_ga_deme_best, (unsigned)ga->demes_total, (unsigned)dthreads, 0, s, gps, K, one, X, cost,
@@ -1407,11 +1547,35 @@ static pm_status ga_configure(pm_ga *ga, int64_t pop, uint64_t seed, const pm_ga
     return PM_OK;
 }
 
+// Buffers of the speculative mutation cycle: Q x pop candidate bitsets, their
+// facility-major copy, active bits, costs and the scan's accumulators.
+static pm_status spec_alloc(pm_ga *ga, cudaStream_t s)
+{
+    const pm_instance *inst = ga->insts[0];
+    const int64_t QP = (int64_t)ga->Q * ga->P;
+    ga->gq = ga->gps[0];
+    ga->gq.pop = QP;
+    ga->gq.ind_base = ga->gq.word_base = ga->gq.grp_base = ga->gq.col_base = 0;
+    PM_TRY(ga->XQ.reserve((size_t)QP * inst->W * 4));
+    PM_TRY(ga->costQ.reserve((size_t)QP * 8));
+    PM_TRY(ga->activeQ.reserve((size_t)pm_round_up(pm_ceil_div(QP, 32) * 4, 256)));
+    PM_TRY(ga->accumQ.reserve((size_t)ga->spec_plan.ind_total * 8));
+    PM_TRY(ga->ticketsQ.reserve((size_t)pm_round_up(std::max<int64_t>(ga->spec_plan.tiles_total, 1) * 4, 256)));
+    PM_TRY(ga->colQ.reserve(std::max<size_t>((size_t)ga->spec_plan.cols_total * 4, 256)));
+    pm_dbuf *zero[] = {&ga->XQ, &ga->costQ, &ga->activeQ, &ga->accumQ, &ga->ticketsQ};
+    for (pm_dbuf *b : zero)
+        PM_CUDA(cudaMemsetAsync(b->ptr, 0, b->bytes, s));  // accumulators and tickets start at zero
+    PM_CUDA(cudaStreamSynchronize(s));
+    return PM_OK;
+}
+
 static pm_status ga_create_common(pm_ga *ga, cudaStream_t s)
 {
     // the warp-per-individual initialisation may use up to 200 KB of shared memory (set outside any capture)
     PM_CUDA(cudaFuncSetAttribute(k_ga_init_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     pm_status st = ga_alloc(ga, s);
+    if (st == PM_OK && ga->spec)
+        st = spec_alloc(ga, s);
     if (st == PM_OK)
         st = build_graph(ga);
     return st;
@@ -1487,7 +1651,19 @@ extern "C" pm_status pm_ga_create(pm_instance *inst, uint64_t seed, int64_t pop,
         ga->single = pm_plan_eval(inst, pop);
         ga->single_row = ga->single.groups == 0;
         ga->plan = pm_plan_from_single(inst, ga->single, pop);
-        st = ga_create_common(ga, static_cast<cudaStream_t>(stream));
+        if (!ga->single_row && ga->Q > 1 && spec_allowed()) {
+            const int64_t QP = (int64_t)ga->Q * pop;
+            if (params && (params->flags & PM_GA_TUNE))
+                st = pm_tune_eval(inst, QP, stream, nullptr);
+            if (st == PM_OK) {
+                ga->spec_single = pm_plan_eval(inst, QP);
+                ga->spec = ga->spec_single.groups > 0;
+                if (ga->spec)
+                    ga->spec_plan = pm_plan_from_single(inst, ga->spec_single, QP);
+            }
+        }
+        if (st == PM_OK)
+            st = ga_create_common(ga, static_cast<cudaStream_t>(stream));
     }
     if (st != PM_OK) {
         ga_free(ga);
@@ -1776,8 +1952,8 @@ extern "C" pm_status pm_ga_info(const pm_ga *ga, int64_t *pop, int64_t *deme, in
     if (mut_tries)
         *mut_tries = ga->Q;
     if (kernels_per_generation)
-        *kernels_per_generation = 1 + per_eval + rounds * (1 + per_eval) + ga->Q * (1 + per_eval) + 2 +
-                                  (ga->model ? 4 + per_eval : 0);
+        *kernels_per_generation = 1 + per_eval + rounds * (1 + per_eval) +
+                                  (ga->spec ? 3 : ga->Q * (1 + per_eval)) + 2 + (ga->model ? 4 + per_eval : 0);
     if (kernels_per_step_call)
         *kernels_per_step_call = graph_mode() ? 2 : 1;  // k_ga_begin (and the gate in graph mode)
     return PM_OK;

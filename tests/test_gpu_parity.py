@@ -456,3 +456,28 @@ def test_client_sharded_evaluation_on_one_gpu(pm):
     ev = ShardedEvaluator(d, p)
     np.testing.assert_array_equal(ev.eval(dm).cpu().numpy(), expect)
     ev.close()
+
+
+def test_speculative_mutation_cycle_matches_try_by_try(pm, monkeypatch):
+    """All Q mutation tries evaluated in one scan (the default for one instance on the column path) give the
+    same populations, costs and evaluation counts as the cycle run try by try (PM_GA_SPEC=0), and as the oracle."""
+    w = paper_shape_instance("graph900")
+    d, p = w["d"], w["p"]
+    inst = pm.Instance(d, p)
+    a = pm.GA(inst, seed=17, pop=512, deme=128)
+    ta = a.step(3)
+    info = a.info()
+    monkeypatch.setenv("PM_GA_SPEC", "0")
+    b = pm.GA(inst, seed=17, pop=512, deme=128)
+    tb = b.step(3)
+    np.testing.assert_array_equal(ta, tb)
+    for x, y in zip(a.population(), b.population()):
+        np.testing.assert_array_equal(x, y)
+    assert a.result()[:3] == b.result()[:3]
+    # the speculative cycle launches 3 kernels in place of 2 per try
+    assert info["kernels_per_generation"] == b.info()["kernels_per_generation"] - 2 * info["mut_tries"] + 3
+    monkeypatch.delenv("PM_GA_SPEC")
+    _ga_compare(pm, d, p, 512, 2, check_every=1, deme=128, seed=17, xover_rounds=2, mut_tries=20)
+    # more tries than a warp has lanes: the first improving try is searched 32 tries at a time
+    _ga_compare(pm, euclid_instance(77, seed=11), 7, 128, 4, check_every=1, deme=16, seed=8, xover_rounds=3,
+                mut_tries=33)
