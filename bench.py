@@ -562,11 +562,13 @@ def run_learned(args):
     X, T = torch.cat(xs), torch.cat(ts)
     torch.cuda.synchronize()
     log_s = time.perf_counter() - t0
-    t0 = time.perf_counter()
     model = pm.Model(seed=0)
-    losses = model.train(X, T, epochs=6, batch=4096, lr=2e-3, seed=0, stream=stream.cuda_stream)
+    mse_before, _ = model.grad(X, T)  # mean squared error over all logged tuples, untrained
+    t0 = time.perf_counter()
+    model.train(X, T, epochs=6, batch=4096, lr=2e-3, seed=0, stream=stream.cuda_stream)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
+    mse_after, _ = model.grad(X, T)
 
     def run(seed, use_model, gens):
         g = pm.GA(inst, seed=seed, pop=pop, deme=256, model=model if use_model else None,
@@ -612,7 +614,7 @@ def run_learned(args):
                                    f"pop {pop} in demes of 256; target = plain GA (seed 0) best after {budget} "
                                    "generations; each arm may run up to 4x that; seeds 0-4, medians",
                        "target": target, "train_tuples": int(X.shape[0]), "train_epochs": 6,
-                       "train_loss_first_last": [losses[0], losses[-1]], "log_s": log_s, "train_s": train_s},
+                       "train_mse_before_after": [mse_before, mse_after], "log_s": log_s, "train_s": train_s},
             "plain_time_s": pt, "learned_time_s": lt,
             "speedup": (pt / lt) if (pt and lt) else None,
             "plain_gens": med("plain", "gens"), "learned_gens": med("learned", "gens"),
