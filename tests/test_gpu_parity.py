@@ -481,3 +481,18 @@ def test_speculative_mutation_cycle_matches_try_by_try(pm, monkeypatch):
     # more tries than a warp has lanes: the first improving try is searched 32 tries at a time
     _ga_compare(pm, euclid_instance(77, seed=11), 7, 128, 4, check_every=1, deme=16, seed=8, xover_rounds=3,
                 mut_tries=33)
+
+
+@pytest.mark.parametrize("pop,deme", [(48, 16), (80, 16), (96, 32)])
+def test_ga_ragged_populations(pm, pop, deme):
+    """Populations that are not a multiple of 32: partial tiles in the scans, the speculative mutation
+    candidates (q * pop + t) straddling 32-candidate groups."""
+    _ga_compare(pm, graph_instance(120, 300, seed=pop), 6, pop, 4, check_every=1, deme=deme, seed=pop)
+
+
+def test_ga_very_large_m_row_path(pm):
+    """m = 60000: the facility-major tile does not fit in shared memory, so the GA evaluates with the row kernel
+    and initialises with one warp per 32 individuals (the bitsets do not fit either)."""
+    rng = np.random.default_rng(5)
+    d = rng.integers(0, 1 << 16, size=(6, 60000)).astype(np.int32)
+    _ga_compare(pm, d, 3, 64, 2, check_every=1, deme=32, seed=2, xover_rounds=2, mut_tries=2)
