@@ -14,6 +14,9 @@
 
 #include "pm_common.cuh"
 
+// Timed launches per autotuner candidate (after one warm-up); the median decides.
+static constexpr int kTuneReps = 5;
+
 static size_t tile_bytes(int64_t W, int G) { return (size_t)W * 32 * G * 4; }
 
 pm_status pm_plan_multi(const std::vector<const pm_instance *> &insts, const std::vector<int64_t> &pops, int G,
@@ -321,9 +324,9 @@ extern "C" pm_status pm_batch_tune(pm_batch *b, const int64_t *pops, void *strea
                 b->tuned_warps = warps;
                 b->tuned_ips = ips;
                 b->have_plan = false;
-                float t[3];
+                float t[kTuneReps];
                 st = batch_eval_impl(b, masks, pv, static_cast<int64_t *>(b->stage_costs.ptr), s);
-                for (int r = 0; r < 3 && st == PM_OK; ++r) {
+                for (int r = 0; r < kTuneReps && st == PM_OK; ++r) {
                     cudaEventRecord(e0, s);
                     st = batch_eval_impl(b, masks, pv, static_cast<int64_t *>(b->stage_costs.ptr), s);
                     cudaEventRecord(e1, s);
@@ -333,8 +336,8 @@ extern "C" pm_status pm_batch_tune(pm_batch *b, const int64_t *pops, void *strea
                 if (st != PM_OK)
                     break;
                 ++ncand;
-                std::sort(t, t + 3);
-                if (t[1] < best_ms) {
+                std::sort(t, t + kTuneReps);
+                if (t[kTuneReps / 2] < best_ms) {
                     best_ms = t[1];
                     bG = G;
                     bw = warps;

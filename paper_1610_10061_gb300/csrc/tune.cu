@@ -12,6 +12,9 @@
 
 #include "pm_common.cuh"
 
+// Timed launches per autotuner candidate (after one warm-up); the median decides.
+static constexpr int kTuneReps = 5;
+
 namespace {
 bool same_shape(const pm_eval_plan &a, const pm_eval_plan &b)
 {
@@ -86,8 +89,8 @@ extern "C" pm_status pm_tune_eval(pm_instance *inst, int64_t pop, void *stream, 
                                   static_cast<int *>(inst->err.ptr), acc, s);
         };
         st = run();  // warm-up
-        float t[3];
-        for (int r = 0; r < 3 && st == PM_OK; ++r) {
+        float t[kTuneReps];
+        for (int r = 0; r < kTuneReps && st == PM_OK; ++r) {
             cudaEventRecord(e0, s);
             st = run();
             cudaEventRecord(e1, s);
@@ -96,8 +99,8 @@ extern "C" pm_status pm_tune_eval(pm_instance *inst, int64_t pop, void *stream, 
         }
         if (st != PM_OK)
             break;
-        std::sort(t, t + 3);
-        if (t[1] < best_ms) {
+        std::sort(t, t + kTuneReps);
+        if (t[kTuneReps / 2] < best_ms) {
             best_ms = t[1];
             best = (int)k;
         }
