@@ -750,6 +750,14 @@ __global__ void __launch_bounds__(1024, 2) k_swap_stats(const uint16_t *__restri
                 r1 = base + f;
                 found = 1;
                 bal &= bal - 1u;
+                // the ranks of this step before r1 gain d1 - d(i, k) now; earlier steps are revisited below
+                if (lane < f) {
+                    if (in_smem)
+                        atomicAdd(Gs + j, (Acc)(uint32_t)(d1 - cs));
+                    else
+                        atomicAdd(gain + t * m + j, (unsigned long long)(uint32_t)(d1 - cs));
+                    atomicAdd(C + j, 1);
+                }
             }
             if (found == 1 && bal) {
                 d2 = __shfl_sync(PM_FULL_MASK, cs, __ffs(bal) - 1);
@@ -769,9 +777,10 @@ __global__ void __launch_bounds__(1024, 2) k_swap_stats(const uint16_t *__restri
                 atomicAdd(loss + t * m + f1, (unsigned long long)(uint32_t)(d2 - d1));
             atomicAdd(A + f1, 1);
         }
-        // pass 2: every facility ranked before r1 gains D1 - d(i, k)
+        // pass 2: the facilities of the steps before r1's step (no open one among them) gain d1 - d(i, k)
         carry = 0;
-        for (int base = 0; base < r1; base += 32) {
+        const int r1_step = r1 & ~31;
+        for (int base = 0; base < r1_step; base += 32) {
             const int r = base + lane;
             uint32_t j = 0;
             int32_t dl = 0;
