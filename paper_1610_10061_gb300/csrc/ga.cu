@@ -18,11 +18,13 @@
 //   mutation q       k_ga_mutate rotates the whole bitset or a block of it
 //                    (Section 4.4) for individuals not yet improved in this
 //                    generation; the first strictly cheaper mutant replaces
-//                    the individual (Section 3.2.2 step 5).
-//   k_ga_deme_best   lowest (cost, index) per deme (Section 3.2.2 step 7).
-//   k_ga_finish      per instance: global best (strict improvement),
-//                    saturation counter, trace, counters; the last instance
-//                    to finish sets the loop condition.
+//                    the individual (Section 3.2.2 step 5).  For one instance
+//                    on the column path all tries are built and evaluated at
+//                    once (k_ga_mutate_all, one scan, k_ga_mutate_accept).
+//   k_ga_generation_end  lowest (cost, index) per deme (Section 3.2.2 step
+//                    7); the last deme of an instance updates its global best
+//                    (strict improvement), saturation counter, trace and
+//                    counters; the last instance sets the loop condition.
 // The operators also write the facility-major copy of their output that the
 // scan reads, so no evaluation needs a separate transpose.  The loop is one
 // CUDA graph: a gate kernel and a conditional while-node whose body is one
@@ -71,14 +73,14 @@ struct ga_dev {            // per instance
     long long saturation;  // S (0 = off)
     long long *trace;      // this instance's trace for the current step
     int stop;              // saturation reached
-    int pad;
+    int deme_ticket;       // k_ga_generation_end: demes done this generation (zero at rest)
 };
 
 struct ga_glob {
     long long remaining;  // generations left in the current step
     long long step_gens;  // generations run in the current step
     int alive;            // instances not stopped
-    int done;             // k_ga_finish tickets
+    int done;             // k_ga_generation_end tickets (instances done this generation)
 };
 
 struct ga_prob {  // per instance layout of the GA arrays
@@ -605,7 +607,6 @@ __global__ void __launch_bounds__(1024) k_ga_crossover(const ga_prob *__restrict
                                                        uint32_t *__restrict__ active, uint32_t round, uint64_t seed,
                                                        ga_dev *__restrict__ st, ColumnsOut co)
 {
-    pm_grid_dependency_wait();
     __shared__ uint32_t valid_s;
     int k;
     const ga_prob gp = prob_of_group(gps, K, one, blockIdx.x, k);
@@ -614,7 +615,17 @@ __global__ void __launch_bounds__(1024) k_ga_crossover(const ga_prob *__restrict
     const int64_t t0 = (blockIdx.x - gp.grp_base) * 32;
     const int64_t t = t0 + j;
     const int32_t W = gp.W;
-    if (st[k].stop) {
+    // the generation counter and stop flag were written by an earlier generation's end, and the draws depend on
+    // nothing else: both are read before waiting for the previous kernel (the evaluation of the last round)
+    const bool stopped = st[k].stop != 0;
+    const int64_t stride = gp.D >> (1 + ((int)round % gp.lgD));
+    const int64_t partner = t ^ stride;
+    const uint32_t pair = (uint32_t)(t < partner ? t : partner);
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (!stopped && t < gp.pop)
+        v = draw_block(seed, (uint32_t)st[k].gen, pair, OP_XOVER + round, 0, gp.sid);
+    pm_grid_dependency_wait();
+    if (stopped) {
         if (threadIdx.x == 0)
             active[(gp.ind_base + t0) >> 5] = 0u;
         return;
@@ -624,11 +635,6 @@ __global__ void __launch_bounds__(1024) k_ga_crossover(const ga_prob *__restrict
     __syncthreads();
     const int p = gp.p;
     if (t < gp.pop) {
-        const uint32_t gen = (uint32_t)st[k].gen;
-        const int64_t stride = gp.D >> (1 + ((int)round % gp.lgD));
-        const int64_t partner = t ^ stride;
-        const uint32_t pair = (uint32_t)(t < partner ? t : partner);
-        const uint4 v = draw_block(seed, gen, pair, OP_XOVER + round, 0, gp.sid);
         const uint32_t r1 = uniform_below(v.x, (uint32_t)gp.m);
         const int i = 1 + (int)uniform_below(v.y, (uint32_t)(p / 2));
         const uint32_t *C = X + gp.word_base + t * W;
@@ -904,89 +910,92 @@ __global__ void __launch_bounds__(256) k_ga_mutate_accept(ga_prob gp, int32_t Q,
         atomicAdd(reinterpret_cast<unsigned long long *>(&st[0].evals), tries_s);
 }
 
-// Lowest (cost, index) in each deme -> deme_best / deme_cost.  One CTA per deme.
-__global__ void k_ga_deme_best(const ga_prob *__restrict__ gps, int K, ga_prob one, const uint32_t *__restrict__ X,
-                               const int64_t *__restrict__ cost, uint32_t *__restrict__ deme_best,
-                               int64_t *__restrict__ deme_cost, const ga_dev *__restrict__ st)
+// Generation end (Section 3.2.2 steps 7-8, Section 3.1 steps 13-14), one CTA
+// per deme: the deme's lowest (cost, index) -> deme_best / deme_cost.  The
+// last deme CTA of an instance (a ticket in its state, zero at rest) then
+// takes that instance's global best, saturation, trace and counters; the last
+// instance (a second ticket) advances the step and sets the loop condition.
+__global__ void k_ga_generation_end(const ga_prob *__restrict__ gps, int K, ga_prob one,
+                                    const uint32_t *__restrict__ X, const int64_t *__restrict__ cost,
+                                    uint32_t *__restrict__ deme_best, int64_t *__restrict__ deme_cost,
+                                    uint32_t *__restrict__ best, ga_dev *__restrict__ st, ga_glob *__restrict__ glob,
+                                    cudaGraphConditionalHandle h, int in_graph)
 {
     pm_grid_dependency_wait();
     __shared__ long long sc[32];
     __shared__ long long si[32];
     __shared__ long long win;
+    __shared__ int improve, last_deme, last_inst;
+    __shared__ int alive_s[32];
     int k = 0;
     ga_prob gp = one;
     if (K > 1) {
         k = find_k(K, blockIdx.x, [&](int i) { return gps[i].deme_base; });
         gp = gps[k];
     }
-    if (st[k].stop)
-        return;
-    const int64_t b = blockIdx.x - gp.deme_base;
-    const int32_t W = gp.W;
-    long long bc = 0x7fffffffffffffffLL, bi = 0x7fffffffffffffffLL;
-    for (int64_t i = threadIdx.x; i < gp.D; i += blockDim.x) {
-        const int64_t t = b * gp.D + i;
-        const long long c = cost[gp.ind_base + t];
-        if (c < bc || (c == bc && t < bi)) {
-            bc = c;
-            bi = t;
-        }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const long long oc = __shfl_xor_sync(PM_FULL_MASK, bc, o);
-        const long long oi = __shfl_xor_sync(PM_FULL_MASK, bi, o);
-        if (oc < bc || (oc == bc && oi < bi)) {
-            bc = oc;
-            bi = oi;
-        }
-    }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    if (lane == 0) {
-        sc[warp] = bc;
-        si[warp] = bi;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int w = 1; w < nw; ++w)
-            if (sc[w] < bc || (sc[w] == bc && si[w] < bi)) {
-                bc = sc[w];
-                bi = si[w];
-            }
-        win = bi;
-        deme_cost[gp.deme_base + b] = bc;
-    }
-    __syncthreads();
-    const int64_t tw = win;
-    for (int w = threadIdx.x; w < W; w += blockDim.x)
-        deme_best[gp.dword_base + b * W + w] = X[gp.word_base + tw * W + w];
-}
-
-// Per instance (one CTA each): global best, saturation, trace, counters.  The
-// last CTA (ticket) advances the step and sets the loop condition.
-__global__ void k_ga_finish(const ga_prob *__restrict__ gps, int K, ga_prob one,
-                            const uint32_t *__restrict__ deme_best, const int64_t *__restrict__ deme_cost,
-                            uint32_t *__restrict__ best, ga_dev *__restrict__ st, ga_glob *__restrict__ glob,
-                            cudaGraphConditionalHandle h, int in_graph)
-{
-    pm_grid_dependency_wait();
-    __shared__ long long sc[32];
-    __shared__ long long si[32];
-    __shared__ int improve;
-    __shared__ long long winner;
-    __shared__ int last;
-    __shared__ int alive_s[32];
-    const int k = blockIdx.x;
-    const ga_prob gp = K > 1 ? gps[k] : one;
     ga_dev &s = st[k];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    if (!s.stop) {
+    const int64_t b = blockIdx.x - gp.deme_base;
+    const int32_t W = gp.W;
+    const bool running = !s.stop;
+
+    // the deme's best
+    if (running) {
         long long bc = 0x7fffffffffffffffLL, bi = 0x7fffffffffffffffLL;
-        for (int64_t b = threadIdx.x; b < gp.NB; b += blockDim.x) {
-            const long long c = deme_cost[gp.deme_base + b];
-            if (c < bc || (c == bc && b < bi)) {
+        for (int64_t i = threadIdx.x; i < gp.D; i += blockDim.x) {
+            const int64_t t = b * gp.D + i;
+            const long long c = cost[gp.ind_base + t];
+            if (c < bc || (c == bc && t < bi)) {
                 bc = c;
-                bi = b;
+                bi = t;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const long long oc = __shfl_xor_sync(PM_FULL_MASK, bc, o);
+            const long long oi = __shfl_xor_sync(PM_FULL_MASK, bi, o);
+            if (oc < bc || (oc == bc && oi < bi)) {
+                bc = oc;
+                bi = oi;
+            }
+        }
+        if (lane == 0) {
+            sc[warp] = bc;
+            si[warp] = bi;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < nw; ++w)
+                if (sc[w] < bc || (sc[w] == bc && si[w] < bi)) {
+                    bc = sc[w];
+                    bi = si[w];
+                }
+            win = bi;
+            deme_cost[gp.deme_base + b] = bc;
+        }
+        __syncthreads();
+        const int64_t tw = win;
+        for (int w = threadIdx.x; w < W; w += blockDim.x)
+            deme_best[gp.dword_base + b * W + w] = X[gp.word_base + tw * W + w];
+    }
+
+    // the instance's last deme CTA goes on
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last_deme = (atomicAdd(&s.deme_ticket, 1) == (int)gp.NB - 1) ? 1 : 0;
+    }
+    __syncthreads();
+    if (!last_deme)
+        return;
+    __threadfence();
+    if (running) {
+        long long bc = 0x7fffffffffffffffLL, bi = 0x7fffffffffffffffLL;
+        for (int64_t d = threadIdx.x; d < gp.NB; d += blockDim.x) {
+            const long long c = __ldcg(reinterpret_cast<const long long *>(deme_cost) + gp.deme_base + d);
+            if (c < bc || (c == bc && d < bi)) {
+                bc = c;
+                bi = d;
             }
         }
 #pragma unroll
@@ -1011,7 +1020,7 @@ __global__ void k_ga_finish(const ga_prob *__restrict__ gps, int K, ga_prob one,
                 }
             const bool better = s.best_cost < 0 || bc < s.best_cost;
             improve = better ? 1 : 0;
-            winner = bi;
+            win = bi;
             if (better) {
                 s.best_cost = bc;
                 s.sat = 0;
@@ -1021,8 +1030,8 @@ __global__ void k_ga_finish(const ga_prob *__restrict__ gps, int K, ga_prob one,
         }
         __syncthreads();
         if (improve)
-            for (int w = threadIdx.x; w < gp.W; w += blockDim.x)
-                best[gp.best_base + w] = deme_best[gp.dword_base + winner * gp.W + w];
+            for (int w = threadIdx.x; w < W; w += blockDim.x)
+                best[gp.best_base + w] = __ldcg(deme_best + gp.dword_base + win * W + w);
         if (threadIdx.x == 0) {
             if (s.trace)
                 s.trace[glob->step_gens] = s.best_cost;
@@ -1034,11 +1043,12 @@ __global__ void k_ga_finish(const ga_prob *__restrict__ gps, int K, ga_prob one,
     }
     __syncthreads();
     if (threadIdx.x == 0) {
+        s.deme_ticket = 0;  // every deme of the instance has taken its ticket: reset for the next generation
         __threadfence();
-        last = (atomicAdd(&glob->done, 1) == K - 1) ? 1 : 0;
+        last_inst = (atomicAdd(&glob->done, 1) == K - 1) ? 1 : 0;
     }
     __syncthreads();
-    if (!last)
+    if (!last_inst)
         return;
     __threadfence();
     int alive = 0;
@@ -1385,12 +1395,9 @@ static pm_status enqueue_generation(pm_ga *ga, cudaStream_t s, cudaGraphConditio
         }
     }
     const int dthreads = (int)pm_round_up(std::min<int64_t>(ga->D, 1024), 32);
-    PM_CUDA(pm_launch(k_ga_deme_best, (unsigned)ga->demes_total, (unsigned)dthreads, 0, s, gps, K, one, X, cost,
-                      static_cast<uint32_t *>(ga->deme_best.ptr), static_cast<int64_t *>(ga->deme_cost.ptr), st));
-    PM_CUDA(pm_launch(k_ga_finish, (unsigned)K, 256, 0, s, gps, K, one,
-                      static_cast<const uint32_t *>(ga->deme_best.ptr),
-                      static_cast<const int64_t *>(ga->deme_cost.ptr), static_cast<uint32_t *>(ga->best.ptr), st,
-                      static_cast<ga_glob *>(ga->glob.ptr), h, in_graph));
+    PM_CUDA(pm_launch(k_ga_generation_end, (unsigned)ga->demes_total, (unsigned)dthreads, 0, s, gps, K, one, X,
+                      cost, static_cast<uint32_t *>(ga->deme_best.ptr), static_cast<int64_t *>(ga->deme_cost.ptr),
+                      static_cast<uint32_t *>(ga->best.ptr), st, static_cast<ga_glob *>(ga->glob.ptr), h, in_graph));
     return PM_OK;
 }
 
@@ -1953,7 +1960,7 @@ extern "C" pm_status pm_ga_info(const pm_ga *ga, int64_t *pop, int64_t *deme, in
         *mut_tries = ga->Q;
     if (kernels_per_generation)
         *kernels_per_generation = 1 + per_eval + rounds * (1 + per_eval) +
-                                  (ga->spec ? 3 : ga->Q * (1 + per_eval)) + 2 + (ga->model ? 4 + per_eval : 0);
+                                  (ga->spec ? 3 : ga->Q * (1 + per_eval)) + 1 + (ga->model ? 4 + per_eval : 0);
     if (kernels_per_step_call)
         *kernels_per_step_call = graph_mode() ? 2 : 1;  // k_ga_begin (and the gate in graph mode)
     return PM_OK;
