@@ -108,13 +108,13 @@ struct MlpTrainSmem {
 
 // ---------------------------------------------------------------------------
 // Inference forward on the 5th-generation tensor cores (tcgen05).  A
-// persistent grid (two CTAs per SM, each holding 256 TMEM columns) walks
+// persistent grid (three CTAs per SM, each holding 128 TMEM columns) walks
 // 128-row tiles; each CTA stages W1 and W2 once.  Per tile both layers are
 // tcgen05.mma.cta_group::1.kind::f16 (BF16 x BF16 -> FP32, M = N = 128)
 // issued by one thread, operands in shared memory in the K-major no-swizzle
 // core-matrix layout (8 rows x 16 bytes per core matrix; k-chunks 128 B
-// apart, 8-row groups K*16 B apart), accumulators in tensor memory (columns
-// [0,128) layer 1, [128,256) layer 2).  Eight warps read them back with
+// apart, 8-row groups K*16 B apart), accumulators in tensor memory (128
+// columns, layer 1's, then layer 2's once layer 1's are read).  Eight warps read them back with
 // tcgen05.ld (thread = row; warps w and w + 4 share TMEM lanes 32(w mod 4)
 // and split the 128 columns): bias, ReLU and a packed BF16 conversion
 // written as 16-byte rows of the next layer's A tile, then bias, ReLU, BF16
@@ -123,7 +123,7 @@ struct MlpTrainSmem {
 // ---------------------------------------------------------------------------
 constexpr int kTcRows = 128;
 constexpr int kTcThreads = 256;
-constexpr uint32_t kTmemCols = 256;
+constexpr uint32_t kTmemCols = 128;  // both layers' accumulators, one after the other
 constexpr uint32_t kTcSpinLimit = 1u << 22;
 // instruction descriptor: D F32 (bits 4-5 = 1), A BF16 (7-9 = 1), B BF16 (10-12 = 1), both K-major,
 // N >> 3 at bits 17-22, M >> 4 at bits 24-28
@@ -314,11 +314,11 @@ __global__ void __launch_bounds__(kTcThreads) k_mlp_fwd_tc(const __nv_bfloat16 *
             }
         }
         tc_sync_for_mma();
-        // layer 2: D[128,256) = H1 W2, eight k-steps of 16
+        // layer 2: D[0,128) = H1 W2 (layer 1's accumulators were read above), eight k-steps of 16
         if (tid == 0) {
 #pragma unroll
             for (int s = 0; s < kHid / 16; ++s)
-                tc_mma(tmem + 128u, umma_desc(S.A2 + s * 128, 128, (kHid / 8) * 128),
+                tc_mma(tmem, umma_desc(S.A2 + s * 128, 128, (kHid / 8) * 128),
                        umma_desc(S.B2 + s * 128, 128, (kHid / 8) * 128), kIdesc, s > 0 ? 1u : 0u);
             tc_commit(&S.bar);
         }
@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(kTcThreads) k_mlp_fwd_tc(const __nv_bfloat16 *
         float ysum = 0.f;
         for (int cc = 0; cc < 64; cc += 32) {
             uint32_t v[32];
-            tc_ld32(tmem + lane_off + 128u + (uint32_t)(c0 + cc), v);
+            tc_ld32(tmem + lane_off + (uint32_t)(c0 + cc), v);
 #pragma unroll
             for (int q = 0; q < 32; q += 2) {
                 const int col = c0 + cc + q;
@@ -1152,9 +1152,9 @@ static size_t mlp_smem(bool train)
     return s;
 }
 
-// dynamic shared memory of the tcgen05 forward: the tiles, padded so that at most two CTAs share an SM
-// (2 x 256 TMEM columns = the SM's 512)
-static size_t tc_smem() { return std::max<size_t>(sizeof(TcSmem) + 1024, 100 * 1024); }
+// dynamic shared memory of the tcgen05 forward (about 74 KB: three CTAs share an SM, and even four would hold
+// only 4 x 128 TMEM columns, the SM's 512)
+static size_t tc_smem() { return sizeof(TcSmem); }
 
 static pm_status mlp_init_attrs()
 {
@@ -1295,7 +1295,7 @@ static pm_status mlp_launch(pm_model *md, bool train, const void *x, int64_t row
                                                       static_cast<float *>(md->G.ptr),
                                                       static_cast<float *>(md->loss.ptr));
     else
-        k_mlp_fwd_tc<<<(unsigned)std::min<int64_t>(pm_ceil_div(rows, kTcRows), 2 * (int64_t)md->sm_count),
+        k_mlp_fwd_tc<<<(unsigned)std::min<int64_t>(pm_ceil_div(rows, kTcRows), 3 * (int64_t)md->sm_count),
                        kTcThreads, tc_smem(), s>>>(X, rows, W1b, W2b, w3b, P, y, static_cast<int *>(md->err.ptr));
     PM_CUDA(cudaGetLastError());
     return PM_OK;
