@@ -1581,8 +1581,14 @@ static pm_status ga_create_common(pm_ga *ga, cudaStream_t s)
     // the warp-per-individual initialisation may use up to 200 KB of shared memory (set outside any capture)
     PM_CUDA(cudaFuncSetAttribute(k_ga_init_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     pm_status st = ga_alloc(ga, s);
-    if (st == PM_OK && ga->spec)
-        st = spec_alloc(ga, s);
+    if (st == PM_OK && ga->spec && spec_alloc(ga, s) != PM_OK) {
+        // no room for the Q x pop candidates: run the mutation cycle try by try instead
+        pm_dbuf *bufs[] = {&ga->XQ, &ga->costQ, &ga->activeQ, &ga->accumQ, &ga->ticketsQ, &ga->colQ};
+        for (pm_dbuf *b : bufs)
+            b->release();
+        cudaGetLastError();
+        ga->spec = false;
+    }
     if (st == PM_OK)
         st = build_graph(ga);
     return st;
