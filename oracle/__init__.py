@@ -13,10 +13,16 @@ Evaluators (three independent routes to the same number):
   in z = 1 - x, like monomials merged and zero coefficients dropped.
 * ``eval_scan`` (O3) -- Section 4.2, the paper's Fitness function.
 
-Plus ``tables`` (Section 2.1, Eq. 4 and truncation), Philox4x32-10, Floyd
-sampling, the crossover (Section 4.3), shift mutation (Section 4.4) and the
-whole GA (Sections 3.1, 3.2.2, 4.5).  The C part lives in ``pm_oracle.c`` and
-is compiled with gcc into ``liboracle.so`` beside it on first use.
+Plus ``tables`` (Section 2.1, Eq. 4 and truncation), ``cumulative`` /
+``eval_cumulative`` (the running sums of Delta' read at the first open rank),
+Philox4x32-10, Floyd sampling, the crossover (Section 4.3), shift mutation
+(Section 4.4), the whole GA (Sections 3.1, 3.2.2, 4.5; Floyd or the
+combinadic generation of Section 4.1 from ``combinadic.py``; migration
+variants (i) and (ii)) and the swap statistics of the learned proposal
+(``mlp.py`` holds its features, perceptron and Adam).  The C part lives in
+``pm_oracle.c`` and is compiled with gcc into ``liboracle.so`` beside it on
+first use.  ``ga_run``: parity unpinned by the paper (its Figures 1-3 are
+missing); pinned by invariants, hand-worked operator cases and brute force.
 """
 
 from __future__ import annotations

@@ -25,19 +25,29 @@
  *                        (Salmon, Moraes, Dror, Shaw, SC'11); stands in for
  *                        the paper's cuRAND generator (Section 3.2.1).
  *   oracle_floyd_*       Random p-subset (Floyd's sampling, Bentley & Floyd,
- *                        CACM 1987); stands in for the combinadic generation
- *                        of Section 4.1 (a 64-bit rank cannot index C(m,p)).
+ *                        CACM 1987), the default chromosome generation (a
+ *                        64-bit rank cannot index C(m,p)); the paper's own
+ *                        combinadic generation of Section 4.1 is written with
+ *                        exact integers in combinadic.py and reaches the GA
+ *                        through oracle_ga_run's init_fn.
  *   oracle_crossover     Section 4.3.
  *   oracle_shift         Section 4.4 (circular and block shift).
  *   oracle_ga_run        Sections 3.1 and 3.2.2 (host steps 7-15, Evolve
- *                        steps 1-7) and Section 4.5 (migration variant (i)).
+ *                        steps 1-7) and Section 4.5 (migration variants (i)
+ *                        and (ii)).
+ *   oracle_swap_stats    Swap statistics of the learned proposal (no
+ *                        counterpart in the paper): per facility, the exact
+ *                        cost change of opening or closing it alone, from the
+ *                        same Pi'/Delta' scan as Section 4.2.
  *
  * Parity status: tables, O1 and O3 are pinned by the paper's Example 1 and by
- * brute force; Philox by its published known-answer vectors; the GA operators
- * by invariants and hand-worked cases from the prose of Sections 4.3-4.4 --
- * the paper's Figures 1-3 are missing, so the GA trajectory itself is pinned
- * only by those invariants (its exact random-draw discipline is this
- * library's own reading, not the paper's).
+ * brute force; Philox by its published known-answer vectors; Floyd sampling
+ * by exhaustive enumeration; the GA operators by invariants and hand-worked
+ * cases from the prose of Sections 4.3-4.4; swap statistics by the exact
+ * single-swap identities against O1.  oracle_ga_run: parity unpinned by the
+ * paper -- its Figures 1-3 are missing, so the GA trajectory is pinned only by
+ * those invariants and the migration-variant checks (its exact random-draw
+ * discipline is this library's own reading, not the paper's).
  */
 #include <stdint.h>
 #include <stdlib.h>
