@@ -266,7 +266,15 @@ typedef struct pm_model pm_model;
  * Random numbers: draw s of operation op for unit u in generation g is word
  * (s & 3) of Philox4x32-10(counter = (g, u, op*2^16 + s/4, stream_id),
  * key = (seed lo, seed hi)); U[0,N) = floor(u32 * N / 2^32).
- * Errors: PM_ERR_INVALID_ARG, PM_ERR_OOM, PM_ERR_CUDA.
+ * Mutation (Section 4.4): every try mutates the individual as it stood when
+ * the cycle began and an individual stops at its first strict improvement,
+ * so for a single-instance GA whose evaluation uses the column kernel all
+ * tries are built and evaluated in one pass (Q x pop candidates; falls back
+ * to try by try if they do not fit in memory, or with PM_GA_SPEC=0 in the
+ * environment).  Results and the evaluation count -- the tries each
+ * individual reaches -- are the same either way.
+ * Errors: PM_ERR_INVALID_ARG, PM_ERR_OOM, PM_ERR_CUDA; PM_ERR_UNSUPPORTED for
+ * PM_GA_INIT_COMBINADIC beyond its limits.
  */
 PM_API pm_status pm_ga_create(pm_instance *inst, uint64_t seed, int64_t pop, const pm_ga_params *params, void *stream,
                        pm_ga **out);
