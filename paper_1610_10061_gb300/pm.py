@@ -572,9 +572,10 @@ class Batch:
         return pm_batch_tune(self.handle, pops, stream)
 
     def ga(self, seed: int, pop: int, deme: int = 0, xover_rounds: int = -1, mut_tries: int = -1,
-           saturation: int = 0, stream_id: int = 0, tune: bool = False, stream=None):
+           saturation: int = 0, stream_id: int = 0, tune: bool = False, migration: str = "deme", stream=None):
         h = pm_batch_ga_create(self.handle, seed, pop,
-                               _params(deme, xover_rounds, mut_tries, saturation, stream_id, tune), stream)
+                               _params(deme, xover_rounds, mut_tries, saturation, stream_id, tune,
+                                       migration=migration), stream)
         return BatchGA(self, pop, h)
 
     def close(self):

@@ -127,3 +127,21 @@ def test_batch_rejects_mixed_p1(pm):
     with pytest.raises(pm.PMError) as e:
         batch.ga(seed=0, pop=32, deme=16)
     assert e.value.status == 3
+
+
+def test_batch_ga_team_migration_mixed_tables(pm):
+    """A batched GA with migration variant (ii) over instances with both table kinds: each instance equals the
+    stand-alone oracle run with its stream id."""
+    data = [(graph_instance(100, 200, seed=0), 5), (euclid_instance(150, seed=5), 12)]
+    insts = [pm.Instance(d, p, cumulative=(k == 0)) for k, (d, p) in enumerate(data)]
+    batch = pm.Batch(insts)
+    ga = batch.ga(seed=31, pop=64, deme=16, stream_id=7, migration="team")
+    trace = np.concatenate([ga.step(1) for _ in range(3)], axis=1)
+    for k, (d, p) in enumerate(data):
+        pi, de = oracle.tables(d, p)
+        st, otrace, opops, ocosts = oracle.ga_run(pi, de, d.shape[1], p, seed=31, P=64, D=16, gens=3, record=True,
+                                                  inst=7 + k, team=True)
+        np.testing.assert_array_equal(trace[k], otrace)
+        masks, costs = ga.population(k)
+        np.testing.assert_array_equal(masks, opops[-1])
+        np.testing.assert_array_equal(costs, ocosts[-1])

@@ -258,3 +258,16 @@ def test_learned_ga_is_exact_and_gains(pm):
     assert tl[-1] < tp[-1]
     first = int(np.argmax(tl <= tp[-1]))
     assert tl[first] <= tp[-1] and first < G - 1
+
+
+def test_learned_ga_on_cumulative_tables_is_exact(pm):
+    """The learned try reads swap statistics from cumulative tables (D') as well; every cost stays exact."""
+    d, p = gmm_instance(500, seed=7), 25
+    _, model, _ = _train_model(pm, d, p, seed=2, gens=3, epochs=4)
+    inst = pm.Instance(d, p, cumulative=True)
+    ga = pm.GA(inst, seed=9, pop=256, deme=64, model=model)
+    trace = ga.step(4)
+    masks, costs = ga.population()
+    np.testing.assert_array_equal(costs, oracle.eval_direct(d, masks))
+    assert all(len(s) == p for s in sets_from_masks(masks, 500))
+    assert (np.diff(trace) <= 0).all()

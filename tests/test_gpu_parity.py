@@ -496,3 +496,9 @@ def test_ga_very_large_m_row_path(pm):
     rng = np.random.default_rng(5)
     d = rng.integers(0, 1 << 16, size=(6, 60000)).astype(np.int32)
     _ga_compare(pm, d, 3, 64, 2, check_every=1, deme=32, seed=2, xover_rounds=2, mut_tries=2)
+
+
+def test_ga_feature_combinations(pm):
+    """Combinadic generation on cumulative tables with migration variant (ii), against the oracle."""
+    _ga_compare(pm, euclid_instance(150, seed=21)[:90], 12, 128, 3, check_every=1, deme=32, seed=4,
+                init="combinadic", migration="team", cumulative=True)
