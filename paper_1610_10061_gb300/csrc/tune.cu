@@ -4,6 +4,9 @@
 // facilities) an evaluation is a few microseconds of dependent shuffles per
 // client and wants many small CTAs; for long scans it is issue-bound and
 // wants large tiles that share each staged row chunk among 128 individuals.
+// The candidates cover both mask layouts: facility-major bit columns (the
+// column kernel, G x 32 individuals per shared-memory load) and
+// individual-major bitsets (the row kernel, one individual per warp).
 // Rather than model that, the tuner times the candidate shapes on the
 // instance itself and keeps the fastest per population size.
 
@@ -50,6 +53,9 @@ extern "C" pm_status pm_tune_eval(pm_instance *inst, int64_t pop, void *stream, 
             }
         }
     }
+    // the other mask layout: individual-major bitsets, one warp per individual (the row kernel)
+    if ((size_t)8 * inst->W * 4 + 1024 <= inst->smem_optin)
+        cands.push_back(pm_plan_eval_with(inst, pop, 0, 8, 0));
     if (cands.empty())
         cands.push_back(pm_plan_eval_with(inst, pop, 0, 8, 0));
 
