@@ -35,8 +35,6 @@ pm_status pm_plan_multi(const std::vector<const pm_instance *> &insts, const std
     if (out.smem > budget)
         return PM_ERR_UNSUPPORTED;
     int slots_per_sm = 0;
-    const void *fn = nullptr;
-    (void)fn;
     // resident CTAs per SM for this shape and shared memory
     {
         const int by_smem = (int)std::max<size_t>(1, i0->smem_optin / std::max<size_t>(out.smem + 2048, 1));

@@ -872,7 +872,6 @@ __global__ void __launch_bounds__(256) k_candidates(const uint32_t *__restrict__
     for (int i = threadIdx.x; i < p; i += blockDim.x)
         open_s[i] = 0;  // a bitset with fewer than p open facilities still yields valid ids
     __syncthreads();
-    __shared__ unsigned long long top_g[8];
     __shared__ int32_t top_k[8];
     __shared__ int32_t nopen;
     const int64_t t = blockIdx.x;
@@ -952,7 +951,6 @@ __global__ void __launch_bounds__(256) k_candidates(const uint32_t *__restrict__
                 }
             if (k0 == 0x7fffffff)  // fewer than T closed facilities: repeat the previous one
                 k0 = b > 0 ? top_k[b - 1] : 0;
-            top_g[b] = g0;
             top_k[b] = k0;
         }
         __syncthreads();
