@@ -259,6 +259,7 @@ def run_ours(args):
     cum = args.tables == "cumulative"
     inst = pm.Instance(d, p, device=local, stream=stream.cuda_stream, cumulative=cum)
     shape = inst.tune(pop, stream=stream.cuda_stream)  # autotuned evaluation tile (kept by the instance)
+    spec_shape = inst.tune(pop * lg, stream=stream.cuda_stream)  # the lg(deme) mutation tries evaluated together
     ga = pm.GA(inst, seed=0, pop=pop, deme=deme, stream_id=rank, init=args.init, stream=stream.cuda_stream)
     info = ga.info()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
@@ -359,6 +360,7 @@ def run_ours(args):
                        "mut_tries": info["mut_tries"], "step": "one GA generation (one pm_ga_step graph launch)",
                        "l2": "flushed between timed steps (512 MiB write outside the events)",
                        "eval_tile": {k: shape[k] for k in ("groups", "warps", "splits", "grid")},
+                       "mutation_eval_tile": {k: spec_shape[k] for k in ("groups", "warps", "splits", "grid")},
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "evals": int(tot_evals), "best_cost": int(best),
             "gpu_launches": int((info["kernels_per_generation"] + info["kernels_per_step_call"]) * args.steps),
