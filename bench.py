@@ -196,7 +196,88 @@ def cpu_baseline(d, p, pop, deme, budget_s=12.0):
     dt = time.perf_counter() - t0
     return {"value": st.evals / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{gens} generations of the same GA (pop {pop}, demes of {deme}) on the same instance, "
-                      f"{st.evals} evaluations in {dt:.1f} s, single-threaded C oracle (gcc -O2)"}
+                      f"{st.evals} evaluations in {dt:.1f} s, single-threaded C oracle (gcc -O2)",
+            "host": host_description()}
+
+
+def host_description():
+    """The host the oracle ran on: architecture, usable cores and the CPU model where /proc/cpuinfo names one."""
+    import platform
+
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    model = None
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware") and ":" in line:
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"machine": platform.machine(), "cores": cores, "cpu": model}
+
+
+def cpu_eval_baseline(d, p, masks, budget_s=6.0):
+    """The oracle's evaluators, as they stand, timed on bounded samples of the same evaluation pass.
+
+    O3 (the paper's scan over Pi'/Delta', oracle tables) on one thread, then on one thread per usable host core
+    over a static partition of a sample of the individuals (ctypes releases the interpreter lock inside the C
+    call, so the threads run in parallel), and O1 (the direct min over every facility) on one thread.
+    """
+    import threading
+
+    import numpy as np
+
+    import oracle
+
+    host = host_description()
+    cores = host["cores"]
+    pi, de = oracle.tables(d, p)
+    pop = masks.shape[0]
+
+    def one_thread(fn, budget):  # chunks of the pass, wrapping around, for about `budget` seconds
+        done, at, chunk = 0, 0, 8
+        t0 = time.perf_counter()
+        while True:
+            x = masks[at:at + chunk]
+            fn(x)
+            done += x.shape[0]
+            at = (at + x.shape[0]) % pop
+            if time.perf_counter() - t0 > budget:
+                break
+            chunk = min(chunk * 2, 256)
+        return done, time.perf_counter() - t0
+
+    n1, t1 = one_thread(lambda x: oracle.eval_scan(pi, de, x), budget_s / 3)
+    r1 = n1 / t1
+    # all cores: a sample of about budget/3 seconds of work per thread, whole individuals per thread
+    per = max(1, min(-(-pop // cores), int(r1 * budget_s / 3)))
+    sample = masks[: min(pop, per * cores)]
+    parts = np.array_split(sample, cores)
+    nthreads = sum(1 for part in parts if len(part))
+    reps = 0
+    t0 = time.perf_counter()
+    while True:  # repeat a short pass until the sample takes about budget/3 seconds
+        threads = [threading.Thread(target=oracle.eval_scan, args=(pi, de, part)) for part in parts if len(part)]
+        for th in threads:
+            th.start()
+        for th in threads:
+            th.join()
+        reps += 1
+        if time.perf_counter() - t0 > budget_s / 3:
+            break
+    tall = time.perf_counter() - t0
+    nd, td = one_thread(lambda x: oracle.eval_direct(d, x), budget_s / 3)
+    return {"value": reps * sample.shape[0] / tall, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+            "sample": f"O3 scan (plain C, gcc -O2) of {sample.shape[0]} of the pass's {pop} individuals "
+                      f"x {reps}, {nthreads} threads over a static partition, {tall:.2f} s",
+            "single_core": {"value": r1, "unit": UNIT, "cores": 1,
+                            "sample": f"O3 scan of {n1} individuals of the pass on one thread, {t1:.2f} s"},
+            "direct_single_core": {"value": nd / td, "unit": UNIT, "cores": 1,
+                                   "sample": f"O1 direct min over all {d.shape[1]} facilities, {nd} individuals "
+                                             f"on one thread, {td:.2f} s"},
+            "host": host}
 
 
 def run_reference(args):
@@ -448,6 +529,8 @@ def run_eval_mode(args):
                          "frac": achieved / peak, "traffic": profiled_traffic(args.workload),
                          "alg_bytes_per_launch": alg_bytes, "peak_source": f"{peak_kind} burst copy bandwidth"},
             "gpu_launches": 2 * args.steps, "tables": tables, "clocks": clk}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_eval_baseline(d, p, masks)
     print(json.dumps(line), flush=True)
 
 
