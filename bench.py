@@ -407,24 +407,24 @@ def run_ours(args):
                         "evaluation scans; the tables are L2-resident at this size"}
 
     # ---- end to end through the C ABI with host buffers ----
-    e2e = None
-    if rank == 0 or True:
-        dh = torch.from_numpy(d).pin_memory()
-        best_mask = torch.zeros(W, dtype=torch.int32).pin_memory()
-        trace = torch.zeros(args.steps, dtype=torch.int64).pin_memory()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        h = pm.pm_instance_create_ex(dh, n, m, p, local, stream.cuda_stream, pm.PM_TABLES_CUMULATIVE if cum else 0)
-        bc, gr, ev = pm.pm_ga_run(h, 0, pop, args.steps, pm._params(deme=deme, stream_id=rank, init=args.init),
-                                  best_mask, trace,
-                                  stream.cuda_stream)
-        pm.pm_instance_destroy(h)
-        t1 = time.perf_counter()
-        e2e = {"value": ev / (t1 - t0), "unit": UNIT,
-               "h2d_bytes_per_step": n * m * 4 / args.steps,
-               "d2h_bytes_per_step": (W * 4 + 8 * 3) / args.steps + 8,
-               "note": f"pm_instance_create from pinned host d + pm_ga_run({args.steps} generations) with host "
-                       "best mask and trace; copies amortised over the steps of one job"}
+    # every rank runs its own replica end to end
+    dh = torch.from_numpy(d).pin_memory()
+    best_mask = torch.zeros(W, dtype=torch.int32).pin_memory()
+    trace = torch.zeros(args.steps, dtype=torch.int64).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h = pm.pm_instance_create_ex(dh, n, m, p, local, stream.cuda_stream, pm.PM_TABLES_CUMULATIVE if cum else 0)
+    bc, gr, ev = pm.pm_ga_run(h, 0, pop, args.steps, pm._params(deme=deme, stream_id=rank, init=args.init),
+                              best_mask, trace,
+                              stream.cuda_stream)
+    pm.pm_instance_destroy(h)
+    t1 = time.perf_counter()
+    ev_all, e2e_ms = combine_ranks(ev, 1000.0 * (t1 - t0), device="cuda")  # whole job: sum of evals, slowest rank
+    e2e = {"value": ev_all / (e2e_ms / 1000.0), "unit": UNIT,
+           "h2d_bytes_per_step": n * m * 4 / args.steps,
+           "d2h_bytes_per_step": (W * 4 + 8 * 3) / args.steps + 8,
+           "note": f"pm_instance_create from pinned host d + pm_ga_run({args.steps} generations) with host "
+                   "best mask and trace; copies amortised over the steps of one job"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
