@@ -205,16 +205,18 @@ def host_description():
     import platform
 
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
-    model = None
+    model, fields = None, {}
     try:
         with open("/proc/cpuinfo") as fh:
             for line in fh:
-                key = line.split(":")[0].strip().lower()
-                if key in ("model name", "cpu model", "hardware") and ":" in line:
-                    model = line.split(":", 1)[1].strip()
-                    break
+                if ":" in line:
+                    key, val = (x.strip() for x in line.split(":", 1))
+                    fields.setdefault(key.lower(), val)
     except OSError:
         pass
+    model = fields.get("model name") or fields.get("cpu model")
+    if model is None and "cpu part" in fields:  # Arm: implementer and part numbers (0x41/0xd4f: Neoverse V2)
+        model = f"implementer {fields.get('cpu implementer')} part {fields['cpu part']}"
     return {"machine": platform.machine(), "cores": cores, "cpu": model}
 
 

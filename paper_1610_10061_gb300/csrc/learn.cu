@@ -675,14 +675,13 @@ __global__ void k_refresh_bf16(const float *__restrict__ P, __nv_bfloat16 *__res
 // Swap statistics: one CTA per individual; accumulators in shared memory when
 // they fit (else in the output arrays, zeroed by the caller).
 // ---------------------------------------------------------------------------
-template <typename Acc, bool kCum>
+template <typename Acc, bool kCum, bool kSmem>
 __global__ void __launch_bounds__(1024, 2) k_swap_stats(const uint16_t *__restrict__ pi,
                                                      const int32_t *__restrict__ delta, int64_t n, int32_t L,
                                                      int64_t stride, int32_t W, int32_t m,
                                                      const uint32_t *__restrict__ masks, int64_t pop,
                                                      unsigned long long *__restrict__ gain, int *__restrict__ cap,
-                                                     unsigned long long *__restrict__ loss, int *__restrict__ assign,
-                                                     int in_smem)
+                                                     unsigned long long *__restrict__ loss, int *__restrict__ assign)
 {
     constexpr bool cum = kCum;  // the tables hold D' (running sums of Delta')
     extern __shared__ __align__(16) unsigned char sm[];
@@ -690,13 +689,41 @@ __global__ void __launch_bounds__(1024, 2) k_swap_stats(const uint16_t *__restri
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     uint32_t *bits = reinterpret_cast<uint32_t *>(sm);
     const size_t off = ((size_t)W * 4 + 15) & ~size_t(15);
-    // accumulators: in shared memory (Acc: 32 or 64 bits, chosen by the host so sums cannot overflow) or
-    // directly in the outputs (64 bits, zeroed by the caller)
+    // accumulators: in shared memory (kSmem; Acc of 32 or 64 bits, chosen by the host so sums cannot overflow)
+    // or directly in the outputs (64 bits, zeroed by the caller)
     Acc *Gs = reinterpret_cast<Acc *>(sm + off);
     Acc *Ls = Gs + m;
     int *Cs = reinterpret_cast<int *>(Ls + m);
     int *As = Cs + m;
-    if (in_smem) {
+    const int64_t tm = t * m;
+    auto add_stat = [&](bool first, uint32_t k, int32_t v) {  // add_loss if first, else add_gain
+        if constexpr (kSmem) {
+            atomicAdd((first ? Ls : Gs) + k, (Acc)(uint32_t)v);
+            atomicAdd((first ? As : Cs) + k, 1);
+        } else {
+            atomicAdd((first ? loss : gain) + tm + k, (unsigned long long)(uint32_t)v);
+            atomicAdd((first ? assign : cap) + tm + k, 1);
+        }
+    };
+    auto add_gain = [&](uint32_t k, int32_t v) {  // facility k (closed, ranked before the first open) gains v
+        if constexpr (kSmem) {
+            atomicAdd(Gs + k, (Acc)(uint32_t)v);
+            atomicAdd(Cs + k, 1);
+        } else {
+            atomicAdd(gain + tm + k, (unsigned long long)(uint32_t)v);
+            atomicAdd(cap + tm + k, 1);
+        }
+    };
+    auto add_loss = [&](uint32_t j, int32_t v) {  // the first open facility j would lose v
+        if constexpr (kSmem) {
+            atomicAdd(Ls + j, (Acc)(uint32_t)v);
+            atomicAdd(As + j, 1);
+        } else {
+            atomicAdd(loss + tm + j, (unsigned long long)(uint32_t)v);
+            atomicAdd(assign + tm + j, 1);
+        }
+    };
+    if constexpr (kSmem) {
         for (int j = threadIdx.x; j < m; j += blockDim.x) {
             Gs[j] = 0;
             Ls[j] = 0;
@@ -704,17 +731,91 @@ __global__ void __launch_bounds__(1024, 2) k_swap_stats(const uint16_t *__restri
             As[j] = 0;
         }
     }
-    int *C = in_smem ? Cs : cap + t * m;
-    int *A = in_smem ? As : assign + t * m;
     for (int w = threadIdx.x; w < W; w += blockDim.x)
         bits[w] = masks[t * W + w];
+    // the first 32 ranks of this warp's first client (constant tables: no dependence on the zeroing above)
+    const int nc = (int)n;        // clients (the tables of one GPU hold far fewer than 2^31 rows)
+    const int st = (int)stride;   // row stride of Pi'/Delta' (at most 65536)
+    uint32_t j_nx = 0;
+    int32_t d_nx = 0;
+    if (warp < nc && lane < L) {
+        j_nx = __ldg(pi + (size_t)warp * st + lane);
+        d_nx = __ldg(delta + (size_t)warp * st + lane);
+    }
     __syncthreads();
-    for (int64_t i = warp; i < n; i += nwarps) {
-        const uint16_t *prow = pi + i * stride;
-        const int32_t *drow = delta + i * stride;
-        // pass 1: first and second open ranks and their distances
+    for (int i = warp; i < nc; i += nwarps) {
+        // first 32 ranks (loaded a client ahead).  When the first open rank r1 is among them -- the usual
+        // case unless p/m is tiny -- every gain comes from this step: the ranks before r1 gain d1 - d(i, k) and
+        // the facility at r1 loses d2 - d1, with d2 at the second open rank (later steps are read only for it).
+        {
+            const uint32_t j0 = j_nx;
+            const int32_t d0 = d_nx;
+            const int inext = i + nwarps;  // the next client's first step, loaded while this one runs
+            j_nx = 0;
+            d_nx = 0;
+            if (inext < nc && lane < L) {
+                j_nx = __ldg(pi + (size_t)inext * st + lane);
+                d_nx = __ldg(delta + (size_t)inext * st + lane);
+            }
+            const bool open0 = (lane < L) && ((bits[j0 >> 5] >> (j0 & 31)) & 1u);
+            const uint32_t bal0 = __ballot_sync(PM_FULL_MASK, open0);
+            if (bal0 != 0u) {
+                int32_t cs = d0;  // running sum to this lane's rank (cumulative tables: the value itself)
+                if (!cum) {
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int32_t y = __shfl_up_sync(PM_FULL_MASK, cs, o);
+                        if (lane >= o)
+                            cs += y;
+                    }
+                }
+                const int f1 = __ffs(bal0) - 1;
+                const int32_t d1 = __shfl_sync(PM_FULL_MASK, cs, f1);
+                const uint32_t rest = bal0 & (bal0 - 1u);
+                int32_t d2;
+                if (rest != 0u) {
+                    d2 = __shfl_sync(PM_FULL_MASK, cs, __ffs(rest) - 1);
+                } else {  // the second open rank lies beyond this step, or the row holds no second one
+                    const uint16_t *prow = pi + (size_t)i * st;
+                    const int32_t *drow = delta + (size_t)i * st;
+                    int32_t carry = __shfl_sync(PM_FULL_MASK, cs, 31);  // Delta': running sum at rank 31
+                    bool got = false;
+                    d2 = 0;
+                    for (int base = 32; base < L; base += 32) {
+                        const int r = base + lane;
+                        uint32_t j = 0;
+                        int32_t dl = 0;
+                        if (r < L) {
+                            j = __ldg(prow + r);
+                            dl = __ldg(drow + r);
+                        }
+                        const uint32_t bal = __ballot_sync(PM_FULL_MASK, (r < L) && ((bits[j >> 5] >> (j & 31)) & 1u));
+                        if (bal != 0u) {
+                            const int f = __ffs(bal) - 1;
+                            d2 = cum ? __shfl_sync(PM_FULL_MASK, dl, f)
+                                     : carry + __reduce_add_sync(PM_FULL_MASK, lane <= f ? dl : 0);
+                            got = true;
+                            break;
+                        }
+                        if (!cum)
+                            carry += __reduce_add_sync(PM_FULL_MASK, dl);
+                    }
+                    if (!got)  // the last distance of the truncated row
+                        d2 = cum ? __ldg(drow + L - 1) : carry;
+                }
+                if (lane <= f1) {  // one pair of atomics per lane: lane f1 holds the first open facility itself
+                    const bool first = lane == f1;
+                    add_stat(first, j0, first ? d2 - d1 : d1 - cs);
+                }
+                continue;
+            }
+        }
+        // general path -- pass 1: first and second open ranks and their distances
+        const uint16_t *prow = pi + (size_t)i * st;
+        const int32_t *drow = delta + (size_t)i * st;
         int32_t carry = 0, d1 = 0, d2 = 0;
         int r1 = -1, found = 0;
+        uint32_t f1 = 0;
         for (int base = 0; base < L && found < 2; base += 32) {
             const int r = base + lane;
             uint32_t j = 0;
@@ -747,17 +848,13 @@ __global__ void __launch_bounds__(1024, 2) k_swap_stats(const uint16_t *__restri
             if (found == 0 && bal) {
                 const int f = __ffs(bal) - 1;
                 d1 = __shfl_sync(PM_FULL_MASK, cs, f);
+                f1 = __shfl_sync(PM_FULL_MASK, j, f);
                 r1 = base + f;
                 found = 1;
                 bal &= bal - 1u;
                 // the ranks of this step before r1 gain d1 - d(i, k) now; earlier steps are revisited below
-                if (lane < f) {
-                    if (in_smem)
-                        atomicAdd(Gs + j, (Acc)(uint32_t)(d1 - cs));
-                    else
-                        atomicAdd(gain + t * m + j, (unsigned long long)(uint32_t)(d1 - cs));
-                    atomicAdd(C + j, 1);
-                }
+                if (lane < f)
+                    add_gain(j, d1 - cs);
             }
             if (found == 1 && bal) {
                 d2 = __shfl_sync(PM_FULL_MASK, cs, __ffs(bal) - 1);
@@ -769,14 +866,8 @@ __global__ void __launch_bounds__(1024, 2) k_swap_stats(const uint16_t *__restri
             continue;  // fewer than p open facilities: no statistics for this client
         if (found == 1)
             d2 = carry;  // no second open facility within the table
-        if (lane == 0) {
-            const uint32_t f1 = __ldg(prow + r1);
-            if (in_smem)
-                atomicAdd(Ls + f1, (Acc)(uint32_t)(d2 - d1));
-            else
-                atomicAdd(loss + t * m + f1, (unsigned long long)(uint32_t)(d2 - d1));
-            atomicAdd(A + f1, 1);
-        }
+        if (lane == 0)
+            add_loss(f1, d2 - d1);
         // pass 2: the facilities of the steps before r1's step (no open one among them) gain d1 - d(i, k)
         carry = 0;
         const int r1_step = r1 & ~31;
@@ -798,23 +889,18 @@ __global__ void __launch_bounds__(1024, 2) k_swap_stats(const uint16_t *__restri
                 }
                 cs += carry;
             }
-            if (r < r1) {
-                if (in_smem)
-                    atomicAdd(Gs + j, (Acc)(uint32_t)(d1 - cs));
-                else
-                    atomicAdd(gain + t * m + j, (unsigned long long)(uint32_t)(d1 - cs));
-                atomicAdd(C + j, 1);
-            }
+            if (r < r1)
+                add_gain(j, d1 - cs);
             carry = __shfl_sync(PM_FULL_MASK, cs, 31);
         }
     }
-    if (in_smem) {
+    if constexpr (kSmem) {
         __syncthreads();
         for (int j = threadIdx.x; j < m; j += blockDim.x) {
-            gain[t * m + j] = (unsigned long long)Gs[j];
-            loss[t * m + j] = (unsigned long long)Ls[j];
-            cap[t * m + j] = Cs[j];
-            assign[t * m + j] = As[j];
+            gain[tm + j] = (unsigned long long)Gs[j];
+            loss[tm + j] = (unsigned long long)Ls[j];
+            cap[tm + j] = Cs[j];
+            assign[tm + j] = As[j];
         }
     }
 }
@@ -1404,19 +1490,21 @@ pm_status pm_launch_swap_stats(const pm_instance *inst, const uint32_t *masks, i
     }
 #define PM_STATS_ARGS                                                                                              \
     inst->pi, inst->delta, inst->n, (int32_t)inst->L, inst->stride, (int32_t)inst->W, (int32_t)inst->m, masks, pop, \
-        reinterpret_cast<unsigned long long *>(gain), cap, reinterpret_cast<unsigned long long *>(loss), assign,     \
-        in_smem ? 1 : 0
-    if (narrow && in_smem) {
-        if (inst->cum)
-            k_swap_stats<unsigned int, true><<<(unsigned)pop, 1024, smem, s>>>(PM_STATS_ARGS);
-        else
-            k_swap_stats<unsigned int, false><<<(unsigned)pop, 1024, smem, s>>>(PM_STATS_ARGS);
-    } else {
-        if (inst->cum)
-            k_swap_stats<unsigned long long, true><<<(unsigned)pop, 1024, smem, s>>>(PM_STATS_ARGS);
-        else
-            k_swap_stats<unsigned long long, false><<<(unsigned)pop, 1024, smem, s>>>(PM_STATS_ARGS);
-    }
+        reinterpret_cast<unsigned long long *>(gain), cap, reinterpret_cast<unsigned long long *>(loss), assign
+#define PM_STATS_LAUNCH(ACC, SMEM)                                                                                 \
+    do {                                                                                                           \
+        if (inst->cum)                                                                                             \
+            k_swap_stats<ACC, true, SMEM><<<(unsigned)pop, 1024, smem, s>>>(PM_STATS_ARGS);                        \
+        else                                                                                                       \
+            k_swap_stats<ACC, false, SMEM><<<(unsigned)pop, 1024, smem, s>>>(PM_STATS_ARGS);                       \
+    } while (0)
+    if (narrow && in_smem)
+        PM_STATS_LAUNCH(unsigned int, true);
+    else if (in_smem)
+        PM_STATS_LAUNCH(unsigned long long, true);
+    else
+        PM_STATS_LAUNCH(unsigned long long, false);
+#undef PM_STATS_LAUNCH
 #undef PM_STATS_ARGS
     PM_CUDA(cudaGetLastError());
     return PM_OK;
@@ -1487,12 +1575,15 @@ int pm_mlp_in_width() { return kIn; }
 pm_status pm_learn_prepare(const pm_instance *inst)
 {
     const int cap = (int)(inst->smem_optin > 1024 ? inst->smem_optin - 1024 : inst->smem_optin);
-    PM_CUDA(cudaFuncSetAttribute(k_swap_stats<unsigned int, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
-    PM_CUDA(cudaFuncSetAttribute(k_swap_stats<unsigned int, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
-    PM_CUDA(cudaFuncSetAttribute(k_swap_stats<unsigned long long, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    // the shared-memory accumulator variants (the global one holds only the bitset: at most 8 KB)
+    PM_CUDA(cudaFuncSetAttribute(k_swap_stats<unsigned int, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  cap));
-    PM_CUDA(cudaFuncSetAttribute(k_swap_stats<unsigned long long, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    PM_CUDA(cudaFuncSetAttribute(k_swap_stats<unsigned int, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  cap));
+    PM_CUDA(cudaFuncSetAttribute(k_swap_stats<unsigned long long, false, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+    PM_CUDA(cudaFuncSetAttribute(k_swap_stats<unsigned long long, true, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
     PM_CUDA(cudaFuncSetAttribute(k_candidates, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
     return mlp_init_attrs();
 }

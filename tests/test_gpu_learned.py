@@ -51,8 +51,11 @@ def _stats_gpu(pm, inst, masks):
 
 
 @pytest.mark.parametrize("cumulative", [False, True])
-@pytest.mark.parametrize("case", ["graph", "euclid", "ties", "gmm", "wide", "short"])
+@pytest.mark.parametrize("case", ["graph", "euclid", "ties", "gmm", "wide", "wide64", "global", "short"])
 def test_swap_stats_bit_exact(pm, case, cumulative):
+    """Every accumulator variant: 32-bit shared (n max d < 2^32), 64-bit shared, and the output arrays in global
+    memory once 24 m bytes of 64-bit accumulators exceed a CTA's shared memory; p/m from 0.6 % (the first two open
+    ranks rarely among the first 32) to 95 %."""
     rng = np.random.default_rng(1)
     if case == "graph":
         d, p = graph_instance(100, 200, seed=0), 5
@@ -62,8 +65,12 @@ def test_swap_stats_bit_exact(pm, case, cumulative):
         d, p = rng.integers(0, 4, size=(60, 90)).astype(np.int32), 7
     elif case == "gmm":
         d, p = gmm_instance(400, seed=2), 40
-    elif case == "wide":  # m large enough for the global-memory accumulators
+    elif case == "wide":  # m = 10000 with 32-bit shared accumulators (160 KB)
         d, p = rng.integers(0, 3000, size=(40, 10000)).astype(np.int32), 60
+    elif case == "wide64":  # n max d >= 2^32: 64-bit shared accumulators (120 KB)
+        d, p = rng.integers(0, 1 << 27, size=(40, 5000)).astype(np.int32), 50
+    elif case == "global":  # 64-bit accumulators for m = 10000 (240 KB) do not fit: global memory
+        d, p = rng.integers(0, 1 << 27, size=(40, 10000)).astype(np.int32), 500
     else:  # L = 3: rows that often hold a single open facility (second distance = the row's last)
         d, p = rng.integers(0, 50, size=(50, 40)).astype(np.int32), 38
     inst = pm.Instance(d, p, cumulative=cumulative)
