@@ -36,7 +36,10 @@ UNIT = "evals/s"
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 2000 GA generations, about half a second of GPU time so that the "
+                         "clock samples fall inside the timed region; 200 evaluation passes; 50 batched "
+                         "generations; 20 target generations for the learned comparison)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="graph900")
@@ -112,16 +115,22 @@ def profiled_traffic(name):
 
 
 class Clocks:
-    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region.
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
-         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-         "clocks_event_reasons.sw_power_cap")
+    start() returns once the sampler has written its first line, so the timed region that follows is covered;
+    stop() keeps the samples whose timestamps fall between the two calls (all samples, flagged, if none do).
+    """
+
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 100
 
     def __init__(self, index):
         self.index = index
         self.proc = None
         self.path = None
+        self.t_start = self.t_end = None
 
     def start(self):
         try:
@@ -129,39 +138,59 @@ class Clocks:
             os.close(fd)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
-                                         stderr=subprocess.DEVNULL)
+                                          "--format=csv,noheader,nounits", "-lms", str(self.PERIOD_MS)],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        deadline = time.time() + 5.0
+        while time.time() < deadline and os.path.getsize(self.path) == 0 and self.proc.poll() is None:
+            time.sleep(0.01)
+        self.t_start = time.time()
+
+    @staticmethod
+    def _stamp(text):
+        import datetime
+
+        for fmt in ("%Y/%m/%d %H:%M:%S.%f", "%Y/%m/%d %H:%M:%S"):
+            try:
+                return datetime.datetime.strptime(text, fmt).timestamp()
+            except ValueError:
+                continue
+        return None
 
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
-        time.sleep(0.25)
+        self.t_end = time.time()
+        time.sleep(2 * self.PERIOD_MS / 1000)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
         self.fh.close()
-        sm, mx, reasons = [], [], set()
+        rows = []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         with open(self.path) as fh:
             for line in fh:
                 parts = [x.strip() for x in line.split(",")]
-                if len(parts) < 9:
+                if len(parts) < 10:
                     continue
                 try:
-                    sm.append(float(parts[1]))
-                    mx.append(float(parts[2]))
+                    rows.append((self._stamp(parts[0]), float(parts[2]), float(parts[3]),
+                                 [nm for nm, v in zip(names, parts[6:10]) if v.lower() == "active"]))
                 except ValueError:
                     continue
-                for nm, v in zip(names, parts[5:9]):
-                    if v.lower() == "active":
-                        reasons.add(nm)
         os.unlink(self.path)
+        inside = [r for r in rows if r[0] is not None and self.t_start - 0.05 <= r[0] <= self.t_end + 0.05]
+        use = inside if inside else rows
+        sm = [r[1] for r in use]
+        mx = [r[2] for r in use]
+        reasons = sorted({nm for r in use for nm in r[3]})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": reasons, "samples": len(use), "in_timed_region": bool(inside),
+                "timed_region_s": round(self.t_end - self.t_start, 3)}
 
 
 def combine_ranks(evals, ms, device="cpu"):
@@ -297,21 +326,28 @@ def run_reference(args):
     for _ in range(args.warmup):
         st, _, _, _ = oracle.ga_run(pi, de, m, p, seed=0, P=pop, D=deme, gens=1, state=st)
     e0 = st.evals if st else 0
+    budget_s = 60.0  # the oracle takes about 0.2 s per generation: the timed sample stops after a minute
+    timed = 0
     t0 = time.perf_counter()
     for _ in range(args.steps):
         st, _, _, _ = oracle.ga_run(pi, de, m, p, seed=0, P=pop, D=deme, gens=1, state=st)
+        timed += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
     dt = time.perf_counter() - t0
     evals = st.evals - e0
     value = evals / dt
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / max(args.steps, 1),
+        "steps": timed, "steps_requested": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * dt / max(timed, 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": {"workload": args.workload, "description": desc, "n": int(d.shape[0]), "m": m, "p": p,
                    "pop": pop, "deme": deme, "step": "one GA generation", "parallelism": "none (host CPU)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1,
-                         "sample": f"{args.steps} generations timed after {args.warmup} warm-up generations, "
-                                   "single-threaded C oracle (gcc -O2)"},
+                         "sample": f"{timed} of {args.steps} requested generations (at most {budget_s:.0f} s) "
+                                   f"timed after {args.warmup} warm-up generations, single-threaded C oracle "
+                                   "(gcc -O2)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -585,6 +621,38 @@ def run_batched(args):
     e1 = sum(pm.pm_ga_instance_result(ga.handle, k, None, stream.cuda_stream)[2] for k in range(count))
     n_sizes = [d.shape[0] for d, _ in data]
     tables_bytes = sum(d.shape[0] * (((d.shape[1] - p + 1) + 31) // 32 * 32) * 6 for d, p in data)
+
+    # ---- roofline of the dominant kernel: one batched evaluation pass of random populations, timed alone ----
+    from paper_1610_10061_gb300.inputs import random_masks
+
+    pops = [pop] * count
+    masks = np.concatenate([random_masks(pop, d.shape[1], p, seed=123 + k).reshape(-1)
+                            for k, (d, p) in enumerate(data)])
+    dmask = torch.from_numpy(masks.view(np.int32)).cuda()
+    dcost = torch.empty(pop * count, dtype=torch.int64, device="cuda")
+    for _ in range(3):
+        batch.eval(dmask, pops, dcost, stream=stream.cuda_stream)
+    reps = 10
+    es = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+    ee = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+    for k in range(reps):
+        flush.zero_()
+        es[k].record(stream)
+        batch.eval(dmask, pops, dcost, stream=stream.cuda_stream)
+        ee[k].record(stream)
+    torch.cuda.synchronize()
+    eval_ms = statistics.mean(a.elapsed_time(b) for a, b in zip(es, ee))
+    # per evaluation of instance (n, m, p): the scanned Pi'/Delta' prefix n (m+1)/(p+1) x 6 B, the bitset, the cost
+    alg_bytes = sum(pop * (d.shape[0] * (d.shape[1] + 1) / (p + 1) * 6 + 4 * ((d.shape[1] + 31) // 32) + 8)
+                    for d, p in data)
+    peak, peak_kind = measured_peaks()
+    achieved = alg_bytes / (eval_ms / 1000.0) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "batched fitness evaluation (transpose + column scan over all instances)",
+                "peak_source": f"{peak_kind} burst copy bandwidth", "launch_ms": eval_ms,
+                "alg_bytes_per_launch": alg_bytes,
+                "note": "algorithmic bytes = sum over instances of pop * (n*(m+1)/(p+1)*6 + 4W + 8); each row chunk "
+                        "a CTA fetches serves 128 individuals, so this exceeds the DRAM bytes moved"}
     line = {"metric": METRIC, "value": (e1 - e0) / (ms / 1000), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
@@ -597,7 +665,7 @@ def run_batched(args):
                        "l2": "flushed between timed steps"},
             "evals": int(e1 - e0),
             "gpu_launches": int((info["kernels_per_generation"] + info["kernels_per_step_call"]) * args.steps),
-            "clocks": clk}
+            "roofline": roofline, "clocks": clk}
     print(json.dumps(line), flush=True)
 
 
@@ -712,6 +780,15 @@ def run_learned(args):
 
 def main():
     args = parse_args()
+    if args.steps is None:
+        if args.impl != "reference" and args.workload.startswith("learned_"):
+            args.steps = 20
+        elif args.impl != "reference" and args.workload.startswith("batched"):
+            args.steps = 50
+        elif args.impl != "reference" and args.mode == "eval":
+            args.steps = 200
+        else:
+            args.steps = 2000
     if args.impl == "reference":
         run_reference(args)
     elif args.workload.startswith("learned_"):
