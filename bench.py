@@ -87,6 +87,15 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+def measured_bf16_peak():
+    """Dense BF16 tensor peak (TFLOP/s): the measured cuBLAS burst figure for a kernel timed alone."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["bf16_tflops"]), "measured"
+    except Exception:
+        return 1900.0, "fallback"
+
+
 def fitness_source_hash():
     h = hashlib.sha256()
     for f in ("fitness.cu", "pm_common.cuh"):
@@ -754,6 +763,9 @@ def run_learned(args):
     target = int(ptrace0[-1])
     res = {"plain": [], "learned": []}
     limit = 4 * budget  # each arm may run up to four times the budget that defined the target
+    clocks = Clocks(0)
+    torch.cuda.synchronize()
+    clocks.start()
     torch.cuda.nvtx.range_push("timed")
     for seed in range(5):
         for arm in ("plain", "learned"):
@@ -765,6 +777,35 @@ def run_learned(args):
                              "gens": int(hit[0] + 1) if hit.size else None, "final": int(tr[-1]),
                              "ms_per_gen": float(cum[-1] / limit * 1000.0), "evals": int(evals)})
     torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+
+    # ---- roofline of the tensor-core kernel: the perceptron forward over the logged feature rows, timed alone ----
+    rows = int(X.shape[0])
+    y = torch.empty(rows, dtype=torch.float32, device="cuda")
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(3):
+        pm.pm_model_forward(model.handle, X, rows, y, stream.cuda_stream)
+    reps = 20
+    es = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+    ee = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+    for k in range(reps):
+        flush.zero_()
+        es[k].record(stream)
+        pm.pm_model_forward(model.handle, X, rows, y, stream.cuda_stream)
+        ee[k].record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = statistics.mean(a.elapsed_time(b) for a, b in zip(es, ee))
+    flop = rows * 2.0 * (16 * 128 + 128 * 128 + 128)  # the three layers' multiply-adds per row
+    tpeak, tkind = measured_bf16_peak()
+    tflops = flop / (fwd_ms / 1000.0) / 1e12
+    roofline = {"bound": "tensor", "achieved": tflops, "peak": tpeak, "unit": "TFLOP/s", "frac": tflops / tpeak,
+                "traffic": None, "kernel": "k_mlp_fwd_tc (tcgen05 perceptron forward, BF16 operands, FP32 TMEM "
+                                          "accumulators)",
+                "peak_source": f"{tkind} cuBLAS bf16 burst", "launch_ms": fwd_ms, "flop_per_launch": flop,
+                "rows": rows, "note": "FLOP = rows x 2 x (16x128 + 128x128 + 128); the logged training tuples' "
+                                      "feature rows as input; in a learned generation the kernel scores pop x p x 4 "
+                                      "candidate rows"}
 
     def med(arm, key):
         vals = [r[key] for r in res[arm] if r[key] is not None]
@@ -783,7 +824,7 @@ def run_learned(args):
             "speedup": (pt / lt) if (pt and lt) else None,
             "plain_gens": med("plain", "gens"), "learned_gens": med("learned", "gens"),
             "plain_ms_per_gen": med("plain", "ms_per_gen"), "learned_ms_per_gen": med("learned", "ms_per_gen"),
-            "runs": res}
+            "roofline": roofline, "clocks": clk, "runs": res}
     print(json.dumps(line), flush=True)
 
 
