@@ -780,19 +780,21 @@ def run_learned(args):
     torch.cuda.synchronize()
     clk = clocks.stop()
 
-    # ---- roofline of the tensor-core kernel: the perceptron forward over the logged feature rows, timed alone ----
-    rows = int(X.shape[0])
+    # ---- roofline of the tensor-core kernel: the perceptron forward, timed alone, over as many rows as a learned
+    # generation scores (pop x p x 4 candidate moves), taken from the logged feature rows ----
+    rows = pop * p * 4
+    Xf = X.repeat((rows + X.shape[0] - 1) // X.shape[0], 1)[:rows].contiguous()
     y = torch.empty(rows, dtype=torch.float32, device="cuda")
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     for _ in range(3):
-        pm.pm_model_forward(model.handle, X, rows, y, stream.cuda_stream)
+        pm.pm_model_forward(model.handle, Xf, rows, y, stream.cuda_stream)
     reps = 20
     es = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
     ee = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
     for k in range(reps):
         flush.zero_()
         es[k].record(stream)
-        pm.pm_model_forward(model.handle, X, rows, y, stream.cuda_stream)
+        pm.pm_model_forward(model.handle, Xf, rows, y, stream.cuda_stream)
         ee[k].record(stream)
     torch.cuda.synchronize()
     fwd_ms = statistics.mean(a.elapsed_time(b) for a, b in zip(es, ee))
@@ -803,9 +805,8 @@ def run_learned(args):
                 "traffic": None, "kernel": "k_mlp_fwd_tc (tcgen05 perceptron forward, BF16 operands, FP32 TMEM "
                                           "accumulators)",
                 "peak_source": f"{tkind} cuBLAS bf16 burst", "launch_ms": fwd_ms, "flop_per_launch": flop,
-                "rows": rows, "note": "FLOP = rows x 2 x (16x128 + 128x128 + 128); the logged training tuples' "
-                                      "feature rows as input; in a learned generation the kernel scores pop x p x 4 "
-                                      "candidate rows"}
+                "rows": rows, "note": "FLOP = rows x 2 x (16x128 + 128x128 + 128); rows = pop x p x 4, the candidate "
+                                      "moves a learned generation scores, filled with the logged feature rows"}
 
     def med(arm, key):
         vals = [r[key] for r in res[arm] if r[key] is not None]

@@ -116,9 +116,9 @@ struct MlpTrainSmem {
 // apart, 8-row groups K*16 B apart), accumulators in tensor memory (128
 // columns, layer 1's, then layer 2's once layer 1's are read).  Eight warps read them back with
 // tcgen05.ld (thread = row; warps w and w + 4 share TMEM lanes 32(w mod 4)
-// and split the 128 columns): bias, ReLU and a packed BF16 conversion
-// written as 16-byte rows of the next layer's A tile, then bias, ReLU, BF16
-// rounding and the dot product with w3.  Completion is signalled by
+// and split the 128 columns): bias, then ReLU and BF16 rounding in one
+// conversion per pair, written as 16-byte rows of the next layer's A tile;
+// then the same for layer 2 and the dot product with w3.  Completion is signalled by
 // tcgen05.commit on an mbarrier whose wait is bounded.
 // ---------------------------------------------------------------------------
 constexpr int kTcRows = 128;
@@ -202,11 +202,11 @@ __device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t phase)
     }
 }
 
-// Two floats to a packed BF16 pair (round to nearest even), lo in the low half.
-__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
+// Two floats to a packed BF16 pair of their ReLUs (round to nearest even), lo in the low half.
+__device__ __forceinline__ uint32_t pack_relu_bf16x2(float lo, float hi)
 {
     uint32_t r;
-    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
     return r;
 }
 
@@ -302,14 +302,10 @@ __global__ void __launch_bounds__(kTcThreads) k_mlp_fwd_tc(const __nv_bfloat16 *
                 const float4 ba = *reinterpret_cast<const float4 *>(&S.b1[col]);
                 const float4 bb = *reinterpret_cast<const float4 *>(&S.b1[col + 4]);
                 uint4 o;
-                o.x = pack_bf16x2(fmaxf(__uint_as_float(v[8 * g + 0]) + ba.x, 0.f),
-                                  fmaxf(__uint_as_float(v[8 * g + 1]) + ba.y, 0.f));
-                o.y = pack_bf16x2(fmaxf(__uint_as_float(v[8 * g + 2]) + ba.z, 0.f),
-                                  fmaxf(__uint_as_float(v[8 * g + 3]) + ba.w, 0.f));
-                o.z = pack_bf16x2(fmaxf(__uint_as_float(v[8 * g + 4]) + bb.x, 0.f),
-                                  fmaxf(__uint_as_float(v[8 * g + 5]) + bb.y, 0.f));
-                o.w = pack_bf16x2(fmaxf(__uint_as_float(v[8 * g + 6]) + bb.z, 0.f),
-                                  fmaxf(__uint_as_float(v[8 * g + 7]) + bb.w, 0.f));
+                o.x = pack_relu_bf16x2(__uint_as_float(v[8 * g + 0]) + ba.x, __uint_as_float(v[8 * g + 1]) + ba.y);
+                o.y = pack_relu_bf16x2(__uint_as_float(v[8 * g + 2]) + ba.z, __uint_as_float(v[8 * g + 3]) + ba.w);
+                o.z = pack_relu_bf16x2(__uint_as_float(v[8 * g + 4]) + bb.x, __uint_as_float(v[8 * g + 5]) + bb.y);
+                o.w = pack_relu_bf16x2(__uint_as_float(v[8 * g + 6]) + bb.z, __uint_as_float(v[8 * g + 7]) + bb.w);
                 *reinterpret_cast<uint4 *>(S.A2 + core_idx(r, col, kHid)) = o;
             }
         }
@@ -338,8 +334,7 @@ __global__ void __launch_bounds__(kTcThreads) k_mlp_fwd_tc(const __nv_bfloat16 *
                 const int col = c0 + cc + q;
                 const float2 bv = *reinterpret_cast<const float2 *>(&S.b2[col]);
                 const float2 wv = *reinterpret_cast<const float2 *>(&S.w3[col]);
-                const uint32_t hb = pack_bf16x2(fmaxf(__uint_as_float(v[q]) + bv.x, 0.f),
-                                                fmaxf(__uint_as_float(v[q + 1]) + bv.y, 0.f));
+                const uint32_t hb = pack_relu_bf16x2(__uint_as_float(v[q]) + bv.x, __uint_as_float(v[q + 1]) + bv.y);
                 ysum = fmaf(__uint_as_float(hb << 16), wv.x, ysum);
                 ysum = fmaf(__uint_as_float(hb & 0xffff0000u), wv.y, ysum);
             }
