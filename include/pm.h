@@ -219,6 +219,21 @@ PM_API pm_status pm_set_eval_shape(pm_instance *inst, int64_t pop, const pm_eval
  */
 PM_API pm_status pm_selftest_bounded_wait(int device, void *stream);
 
+/*
+ * pm_debug_fail_alloc -- failure injection for tests (no counterpart in the
+ * paper).  After `after` more successful device allocations by this library,
+ * the next one fails on the host, without calling CUDA, and the call that
+ * made it returns PM_ERR_OOM having launched nothing on that memory and
+ * freed what it had obtained (one exception: a GA that cannot get the
+ * buffers of the speculative mutation cycle runs the cycle try by try, with
+ * the same results, instead of failing); the injection then disarms itself.
+ * A negative `after` disarms it (the default).  pending (host, nullable)
+ * receives the allocations that were still to succeed before the failure
+ * armed until now, or -1 if none was armed or it has happened.
+ * Process-wide; not meant for concurrent use.  Always PM_OK.
+ */
+PM_API pm_status pm_debug_fail_alloc(int64_t after, int64_t *pending);
+
 /* ------------------------------------------------------------------------
  * The genetic algorithm (Sections 3.1, 3.2.2, 4.3-4.5) on the device.
  * ------------------------------------------------------------------------ */

@@ -1,10 +1,12 @@
 // C ABI: instances, population evaluation, status strings (include/pm.h).
 
+#include <atomic>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <new>
 
+#include "pm_alloc.h"
 #include "pm_common.cuh"
 
 void pm_note_cuda_error(cudaError_t e, const char *what, const char *file, int line)
@@ -12,6 +14,46 @@ void pm_note_cuda_error(cudaError_t e, const char *what, const char *file, int l
     static const bool verbose = std::getenv("PM_VERBOSE") != nullptr;
     if (verbose)
         std::fprintf(stderr, "libpmgpu: %s failed at %s:%d: %s\n", what, file, line, cudaGetErrorString(e));
+}
+
+// Injected allocation failure (pm_debug_fail_alloc): the number of allocations still to succeed before one
+// fails, or -1 when none is armed.
+static std::atomic<long long> g_fail_after{-1};
+
+static bool injected_failure()
+{
+    long long k = g_fail_after.load();
+    while (k >= 0) {
+        if (g_fail_after.compare_exchange_weak(k, k - 1))
+            return k == 0;  // this allocation is the one that fails; the counter is now -1 (disarmed)
+    }
+    return false;
+}
+
+cudaError_t pm_device_malloc(void **ptr, size_t bytes)
+{
+    if (injected_failure()) {
+        *ptr = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(ptr, bytes);
+}
+
+cudaError_t pm_device_malloc_async(void **ptr, size_t bytes, cudaStream_t s)
+{
+    if (injected_failure()) {
+        *ptr = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMallocAsync(ptr, bytes, s);
+}
+
+extern "C" pm_status pm_debug_fail_alloc(int64_t after, int64_t *pending)
+{
+    const long long prev = g_fail_after.exchange(after < 0 ? -1 : (long long)after);
+    if (pending)
+        *pending = (int64_t)prev;
+    return PM_OK;
 }
 
 pm_status pm_dbuf::reserve(size_t want, bool *fresh)
@@ -22,7 +64,7 @@ pm_status pm_dbuf::reserve(size_t want, bool *fresh)
         return PM_OK;
     release();
     size_t sz = want < 256 ? 256 : want;
-    cudaError_t e = cudaMalloc(&ptr, sz);
+    cudaError_t e = pm_device_malloc(&ptr, sz);
     if (e != cudaSuccess) {
         ptr = nullptr;
         bytes = 0;
@@ -115,8 +157,8 @@ static pm_status create_impl(const int32_t *d, int64_t n, int64_t m, int64_t p, 
     PM_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
     inst->smem_optin = (size_t)v;
     const size_t tab = (size_t)n * (size_t)inst->stride;
-    PM_CUDA(cudaMalloc(reinterpret_cast<void **>(&inst->pi), tab * sizeof(uint16_t)));
-    PM_CUDA(cudaMalloc(reinterpret_cast<void **>(&inst->delta), tab * sizeof(int32_t)));
+    PM_CUDA(pm_device_malloc(reinterpret_cast<void **>(&inst->pi), tab * sizeof(uint16_t)));
+    PM_CUDA(pm_device_malloc(reinterpret_cast<void **>(&inst->delta), tab * sizeof(int32_t)));
     PM_TRY(inst->err.reserve(256));
     PM_CUDA(cudaMemsetAsync(inst->err.ptr, 0, 256, stream));
     PM_TRY(pm_fitness_init(inst));
@@ -124,7 +166,7 @@ static pm_status create_impl(const int32_t *d, int64_t n, int64_t m, int64_t p, 
     int32_t *tmp = nullptr;
     if (!pm_is_device_ptr(d)) {
         const size_t bytes = (size_t)n * (size_t)m * sizeof(int32_t);
-        PM_CUDA(cudaMallocAsync(reinterpret_cast<void **>(&tmp), bytes, stream));
+        PM_CUDA(pm_device_malloc_async(reinterpret_cast<void **>(&tmp), bytes, stream));
         cudaError_t e = cudaMemcpyAsync(tmp, d, bytes, cudaMemcpyHostToDevice, stream);
         if (e != cudaSuccess) {
             cudaFreeAsync(tmp, stream);
@@ -224,7 +266,7 @@ extern "C" pm_status pm_instance_tables(const pm_instance *inst, uint16_t *pi_ou
             PM_TRY(pm_launch_increments(inst, delta_out, s));
         } else {
             int32_t *tmp = nullptr;
-            PM_CUDA(cudaMallocAsync(reinterpret_cast<void **>(&tmp), bytes, s));
+            PM_CUDA(pm_device_malloc_async(reinterpret_cast<void **>(&tmp), bytes, s));
             pm_status st = pm_launch_increments(inst, tmp, s);
             cudaError_t e = st == PM_OK ? cudaMemcpyAsync(delta_out, tmp, bytes, cudaMemcpyDeviceToHost, s)
                                         : cudaSuccess;

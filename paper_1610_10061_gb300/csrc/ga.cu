@@ -42,6 +42,7 @@
 #include <new>
 #include <vector>
 
+#include "pm_alloc.h"
 #include "pm_common.cuh"
 
 // batch.cu
@@ -1614,7 +1615,7 @@ static pm_status comb_prepare(pm_ga *ga, const pm_instance *inst, cudaStream_t s
     ga->comb_Q = Q;
     PM_TRY(ga->comb_tab.reserve(bytes));
     int *flag = nullptr;
-    PM_CUDA(cudaMallocAsync(reinterpret_cast<void **>(&flag), sizeof(int), s));
+    PM_CUDA(pm_device_malloc_async(reinterpret_cast<void **>(&flag), sizeof(int), s));
     cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), s);
     if (e == cudaSuccess) {
         k_comb_table<<<1, 1024, 0, s>>>(static_cast<uint32_t *>(ga->comb_tab.ptr), (int32_t)inst->m, (int32_t)inst->p,

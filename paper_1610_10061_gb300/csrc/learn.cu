@@ -36,6 +36,7 @@
 #include <new>
 #include <vector>
 
+#include "pm_alloc.h"
 #include "pm_common.cuh"
 
 namespace {
@@ -1598,7 +1599,7 @@ extern "C" pm_status pm_log_moves(pm_instance *inst, const uint32_t *masks, cons
     const size_t Pm = (size_t)pop * inst->m, rows = (size_t)pop * per;
     char *buf = nullptr;
     const size_t bytes = Pm * 24 + rows * inst->W * 4 + rows * 8 + 1024;
-    PM_CUDA(cudaMallocAsync(reinterpret_cast<void **>(&buf), bytes, s));
+    PM_CUDA(pm_device_malloc_async(reinterpret_cast<void **>(&buf), bytes, s));
     int64_t *gain = reinterpret_cast<int64_t *>(buf);
     int64_t *loss = gain + Pm;
     int32_t *cap = reinterpret_cast<int32_t *>(loss + Pm);

@@ -23,6 +23,7 @@
 // epilogue writes Pi' and the differences Delta' into rows padded to a stride
 // of round_up(L, 32) elements (padding = 0).
 
+#include "pm_alloc.h"
 #include "pm_common.cuh"
 
 namespace {
@@ -247,7 +248,7 @@ pm_status pm_build_tables(pm_instance *inst, const int32_t *d_dev, cudaStream_t 
         grid = std::min<int64_t>(inst->n, (int64_t)inst->sm_count * per_sm);
     } else {
         grid = std::min<int64_t>(inst->n, (int64_t)inst->sm_count);
-        PM_CUDA(cudaMallocAsync(reinterpret_cast<void **>(&gscratch), (size_t)grid * row_bytes, stream));
+        PM_CUDA(pm_device_malloc_async(reinterpret_cast<void **>(&gscratch), (size_t)grid * row_bytes, stream));
     }
     k_tables<<<(unsigned)grid, kSortThreads, dyn, stream>>>(d_dev, inst->n, (int32_t)inst->m, (int32_t)inst->L,
                                                            inst->stride, passes, inst->cum ? 1 : 0, inst->pi,

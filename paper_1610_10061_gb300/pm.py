@@ -70,6 +70,7 @@ _SIGS = {
     "pm_eval_population": ([_P, _P, _I64, _P, ctypes.c_int, _P], _S),
     "pm_eval_population_noalloc": ([_P, _P, _I64, _P, _P], _S),
     "pm_selftest_bounded_wait": ([ctypes.c_int, _P], _S),
+    "pm_debug_fail_alloc": ([_I64, _P], _S),
     "pm_tune_eval": ([_P, _I64, _P, ctypes.POINTER(pm_eval_shape)], _S),
     "pm_set_eval_shape": ([_P, _I64, ctypes.POINTER(pm_eval_shape)], _S),
     "pm_ga_create": ([_P, ctypes.c_uint64, _I64, ctypes.POINTER(pm_ga_params), _P, _PP], _S),
@@ -198,6 +199,15 @@ def pm_eval_population_noalloc(inst, masks, pop: int, costs, stream=None):
 def pm_selftest_bounded_wait(device: int = 0, stream=None) -> int:
     """Status recorded by a kernel whose wait can never complete (PM_ERR_TIMEOUT = 7 when the bound works)."""
     return int(_lib.pm_selftest_bounded_wait(device, _stream(stream)))
+
+
+def pm_debug_fail_alloc(after: int) -> int:
+    """Make the library's device allocation after `after` more successful ones fail with PM_ERR_OOM (negative:
+    off).  Returns the allocations that were still to succeed before the previously armed failure (-1: none armed,
+    or it has happened)."""
+    pending = ctypes.c_int64(-1)
+    _check(_lib.pm_debug_fail_alloc(int(after), ctypes.byref(pending)), "pm_debug_fail_alloc")
+    return int(pending.value)
 
 
 def pm_tune_eval(inst, pop: int, stream=None):
