@@ -432,11 +432,13 @@ def run_ours(args):
     reps = 30
     es = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
     ee = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+    torch.cuda.nvtx.range_push("roofline")
     for k in range(reps):
         flush.zero_()
         es[k].record(stream)
         pm.pm_eval_population(inst.handle, dmask, pop, dcost, 0, stream.cuda_stream)
         ee[k].record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     eval_ms = statistics.mean(a.elapsed_time(b) for a, b in zip(es, ee))
     W = (m + 31) // 32
@@ -653,11 +655,13 @@ def run_batched(args):
     reps = 10
     es = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
     ee = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+    torch.cuda.nvtx.range_push("roofline")
     for k in range(reps):
         flush.zero_()
         es[k].record(stream)
         batch.eval(dmask, pops, dcost, stream=stream.cuda_stream)
         ee[k].record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     eval_ms = statistics.mean(a.elapsed_time(b) for a, b in zip(es, ee))
     # per evaluation of instance (n, m, p): the scanned Pi'/Delta' prefix n (m+1)/(p+1) x 6 B, the bitset, the cost
@@ -791,11 +795,13 @@ def run_learned(args):
     reps = 20
     es = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
     ee = [torch.cuda.Event(enable_timing=True) for _ in range(reps)]
+    torch.cuda.nvtx.range_push("roofline")
     for k in range(reps):
         flush.zero_()
         es[k].record(stream)
         pm.pm_model_forward(model.handle, Xf, rows, y, stream.cuda_stream)
         ee[k].record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     fwd_ms = statistics.mean(a.elapsed_time(b) for a, b in zip(es, ee))
     flop = rows * 2.0 * (16 * 128 + 128 * 128 + 128)  # the three layers' multiply-adds per row
