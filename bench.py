@@ -670,7 +670,8 @@ def run_batched(args):
     peak, peak_kind = measured_peaks()
     achieved = alg_bytes / (eval_ms / 1000.0) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "batched fitness evaluation (transpose + column scan over all instances)",
+                "traffic": profiled_traffic(args.workload),
+                "kernel": "batched fitness evaluation (transpose + column scan over all instances)",
                 "peak_source": f"{peak_kind} burst copy bandwidth", "launch_ms": eval_ms,
                 "alg_bytes_per_launch": alg_bytes,
                 "note": "algorithmic bytes = sum over instances of pop * (n*(m+1)/(p+1)*6 + 4W + 8); each row chunk "
