@@ -577,7 +577,7 @@ def run_eval_mode(args):
     achieved = alg_bytes / (mean_ms / 1000) / 1e9
     line = {"metric": "fitness evals/s (one evaluation pass)", "value": pop / (mean_ms / 1000), "unit": UNIT,
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_ms,
-            "ms_min": min(ms), "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "ms_min": min(ms), "ms_max": max(ms), "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
             "data": "synthetic",
             "config": {"tables": args.tables, "workload": args.workload, "n": int(n), "m": int(m), "p": int(p), "pop": pop,
                        "step": "pm_eval_population of a uniform random population (device buffers)",
