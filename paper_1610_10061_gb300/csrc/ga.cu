@@ -356,17 +356,31 @@ __global__ void __launch_bounds__(1024) k_ga_init_warp(const ga_prob *__restrict
 // first.  A warp holds one such integer with Q = K/32 (rounded up to a power
 // of two) consecutive words per lane, lane l words [lQ, lQ + Q).
 //
-// Binomial table: the walk below only meets C(b + d, b) with b < p and
-// d <= m - p (b = choices left minus one, d = positions left minus choices
-// left), plus C(m, p) itself at b = p, d = m - p; entry (b, d) sits at word
-// ((b * (m - p + 1)) + d) * K.  Every entry is at most C(m, p), so K words
-// (the host's estimate of bits(C(m, p)) / 32, plus a spare word) hold it.
+// Binomial table: the unranking below only meets C(b + d, b) with b <= p
+// and d <= m - p (b = choices left, d = positions left minus choices left);
+// entry (b, d) sits at word ((b * (m - p + 1)) + d) * K.  Every entry is at
+// most C(m, p), so K words (the host's estimate of bits(C(m, p)) / 32, plus a
+// spare word) hold it.  After the entries, one 64-bit head per entry, same
+// index: (bit length << 32) | the entry's 32 most significant bits (the entry
+// itself below 2^32).  Heads order like the values they head, and equal heads
+// below 2^32 mean equal values.
+
+// word offset of the heads: after the entries' words, rounded up to 8 bytes
+static inline size_t comb_head_offset(size_t entries, int32_t K) { return (entries * (size_t)K + 1) & ~(size_t)1; }
+
+__device__ __forceinline__ uint64_t big_head(uint32_t top_word, uint32_t below, int32_t wtop)
+{
+    const int32_t r = 32 - __clz(top_word);  // bits used in the top word (top_word != 0)
+    const int32_t bits = 32 * wtop + r;
+    const uint32_t t32 = (wtop == 0 || r == 32) ? top_word : ((top_word << (32 - r)) | (below >> r));
+    return ((uint64_t)(uint32_t)bits << 32) | t32;
+}
 
 // Pascal's rule along anti-diagonals s = b + d (each entry needs (b - 1, d)
 // and (b, d - 1) of the diagonal before): one CTA, a barrier per diagonal.
 // *overflow is set if a sum ever carries out of K words.
-__global__ void __launch_bounds__(1024) k_comb_table(uint32_t *__restrict__ T, int32_t m, int32_t p, int32_t K,
-                                                     int *__restrict__ overflow)
+__global__ void __launch_bounds__(1024) k_comb_table(uint32_t *__restrict__ T, uint64_t *__restrict__ H, int32_t m,
+                                                     int32_t p, int32_t K, int *__restrict__ overflow)
 {
     const int64_t D1 = (int64_t)m - p + 1;
     for (int32_t s = 0; s <= m; ++s) {
@@ -391,6 +405,10 @@ __global__ void __launch_bounds__(1024) k_comb_table(uint32_t *__restrict__ T, i
                 if (carry)
                     atomicExch(overflow, 1);
             }
+            int32_t wt = K - 1;  // every entry is at least 1
+            while (wt > 0 && out[wt] == 0u)
+                --wt;
+            H[(int64_t)b * D1 + d] = big_head(out[wt], wt > 0 ? out[wt - 1] : 0u, wt);
         }
         __syncthreads();
     }
@@ -419,6 +437,35 @@ __device__ __forceinline__ bool big_less(const uint32_t (&x)[Q], const uint32_t 
     if (ne == 0u)
         return false;
     return __shfl_sync(PM_FULL_MASK, cmp, 31 - __clz(ne)) < 0;
+}
+
+// Word w (the same for every lane) of a warp-held integer.
+template <int Q>
+__device__ __forceinline__ uint32_t big_word(const uint32_t (&x)[Q], int32_t w)
+{
+    uint32_t v = 0u;
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+        if (q == (w % Q))
+            v = x[q];
+    return __shfl_sync(PM_FULL_MASK, v, w / Q);
+}
+
+// Head (as in the binomial table) of a nonzero warp-held integer, and its most significant nonzero word.
+template <int Q>
+__device__ __forceinline__ uint64_t big_head_warp(const uint32_t (&x)[Q], int32_t &wtop)
+{
+    int hiq = -1;
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+        if (x[q] != 0u)
+            hiq = q;
+    const uint32_t nz = __ballot_sync(PM_FULL_MASK, hiq >= 0);
+    const int top = 31 - __clz(nz);
+    wtop = top * Q + __shfl_sync(PM_FULL_MASK, hiq, top);
+    const uint32_t top_word = big_word<Q>(x, wtop);
+    const uint32_t below = wtop > 0 ? big_word<Q>(x, wtop - 1) : 0u;
+    return big_head(top_word, below, wtop);
 }
 
 // x -= y for warp-held integers with x >= y.  Each lane subtracts its words;
@@ -460,7 +507,8 @@ template <int Q>
 __global__ void __launch_bounds__(1024) k_ga_init_comb(ga_prob gp, uint32_t *__restrict__ X,
                                                        uint8_t *__restrict__ improved, uint32_t *__restrict__ active,
                                                        const uint32_t *__restrict__ deme_best,
-                                                       const uint32_t *__restrict__ T, int32_t K, uint64_t seed,
+                                                       const uint32_t *__restrict__ T,
+                                                       const uint64_t *__restrict__ H, int32_t K, uint64_t seed,
                                                        const ga_dev *__restrict__ st, ColumnsOut co)
 {
     pm_grid_dependency_wait();
@@ -542,11 +590,15 @@ __global__ void __launch_bounds__(1024) k_ga_init_comb(ga_prob gp, uint32_t *__r
                 for (int q = 0; q < Q; ++q)
                     x[q] = 0u;
             }
-            // unrank: elements e = 0, 1, ...; k still to choose among m - e; d = m - e - k
+            // unrank.  State: next position e, k still to choose, d = m - e - k, and y = C(m - e, k) - x
+            // (1 <= y; x = the rank among the combinations of the remaining positions).  Skipping s
+            // positions passes over C(m - e, k) - C(m - e - s, k) combinations (hockey stick), so the next
+            // element is e + s* with s* the smallest s where C(k + d - s - 1, k) < y; then y loses that
+            // binomial, k drops by one and d by s*.  A warp tests 32 values of s at once on the heads.
             for (int w = lane; w < W; w += 32)
                 row[w] = 0u;
             __syncwarp();
-            int32_t k = p, e = 0;
+            int32_t k = p, e = 0, d = m - p;
             int32_t cur_w = 0;
             uint32_t cur = 0u;
             auto take = [&](int32_t pos) {
@@ -558,33 +610,59 @@ __global__ void __launch_bounds__(1024) k_ga_init_comb(ga_prob gp, uint32_t *__r
                 }
                 cur |= 1u << (pos & 31);
             };
-            uint32_t c[Q], c_take[Q], c_skip[Q];
-            if (m - k > 0)
-                big_load<Q>(entry(k - 1, m - k), K, lane, c);
+            uint32_t y[Q];
+#pragma unroll
+            for (int q = 0; q < Q; ++q)
+                y[q] = C[q];
+            big_sub<Q>(y, x, lane);
+            int32_t ywtop;
+            uint64_t hy = big_head_warp<Q>(y, ywtop);
+            // heads of the first 32 candidates, C(k + d - 1 - lane, k)
+            uint64_t hc = (d - 1 - lane >= 0) ? __ldg(H + (int64_t)k * D1 + (d - 1 - lane)) : 0ull;
             while (k > 0) {
-                const int32_t d = m - e - k;
                 if (d == 0) {  // as many positions left as choices: take them all
                     for (int32_t q = 0; q < k; ++q)
                         take(e + q);
                     break;
                 }
-                // the next entry under either outcome, loaded before the decision
-                if (k >= 2)
-                    big_load<Q>(entry(k - 2, d), K, lane, c_take);
-                big_load<Q>(entry(k - 1, d - 1), K, lane, c_skip);
-                if (big_less<Q>(x, c)) {
-                    take(e);
-                    --k;
-#pragma unroll
-                    for (int q = 0; q < Q; ++q)
-                        c[q] = c_take[q];
-                } else {
-                    big_sub<Q>(x, c, lane);
-#pragma unroll
-                    for (int q = 0; q < Q; ++q)
-                        c[q] = c_skip[q];
+                int32_t s_star = -1;
+                for (int32_t s0 = 0; s_star < 0; s0 += 32) {
+                    const int32_t dd = d - 1 - (s0 + lane);  // candidate s = s0 + lane tests C(k + dd, k)
+                    if (s0 > 0)
+                        hc = dd >= 0 ? __ldg(H + (int64_t)k * D1 + dd) : 0ull;
+                    // dd < 0: the binomial is 0 < y.  Different heads decide; equal heads below 2^32 mean equal
+                    // values; otherwise compare the words from y's top word down (rare)
+                    bool less = dd < 0 || hc < hy;
+                    bool open = dd >= 0 && hc == hy && (hy >> 32) > 32u;
+                    const uint32_t *ew = T + ((int64_t)k * D1 + (dd >= 0 ? dd : 0)) * K;
+                    for (int32_t w = ywtop; w >= 0 && __any_sync(PM_FULL_MASK, open); --w) {
+                        const uint32_t yw = big_word<Q>(y, w);
+                        if (open) {
+                            const uint32_t v = __ldg(ew + w);
+                            if (v != yw) {
+                                less = v < yw;
+                                open = false;
+                            }
+                        }
+                    }
+                    const uint32_t hit = __ballot_sync(PM_FULL_MASK, less);
+                    if (hit)
+                        s_star = s0 + __ffs(hit) - 1;
                 }
-                ++e;
+                take(e + s_star);
+                const int32_t dsub = d - s_star - 1;  // y loses C(k + dsub, k) (nothing when dsub < 0)
+                const int32_t k1 = k - 1, d1 = d - s_star;
+                // the next step's first candidates, loaded while y is updated
+                hc = (k1 > 0 && d1 - 1 - lane >= 0) ? __ldg(H + (int64_t)k1 * D1 + (d1 - 1 - lane)) : 0ull;
+                if (dsub >= 0) {
+                    uint32_t c[Q];
+                    big_load<Q>(entry(k, dsub), K, lane, c);
+                    big_sub<Q>(y, c, lane);
+                    hy = big_head_warp<Q>(y, ywtop);
+                }
+                k = k1;
+                d = d1;
+                e += s_star + 1;
             }
             if (lane == 0 && cur)
                 row[cur_w] = cur;
@@ -1194,6 +1272,7 @@ struct pm_ga {
     bool team = false;  // migration variant (ii)
     bool comb = false;  // Section 4.1 chromosome generation (combinadic)
     int comb_K = 0, comb_Q = 0;
+    size_t comb_entries = 0;
     pm_dbuf comb_tab;
     bool single_row = false;  // one instance whose evaluation uses the row kernel
     // speculative mutation cycle: all Q tries evaluated in one scan (single instance, column path)
@@ -1303,22 +1382,23 @@ static pm_status enqueue_generation(pm_ga *ga, cudaStream_t s, cudaGraphConditio
 
     if (ga->comb) {
         const uint32_t *T = static_cast<const uint32_t *>(ga->comb_tab.ptr);
+        const uint64_t *Hh = reinterpret_cast<const uint64_t *>(T + comb_head_offset(ga->comb_entries, ga->comb_K));
         const uint32_t *db = static_cast<const uint32_t *>(ga->deme_best.ptr);
         switch (ga->comb_Q) {
         case 1:
-            PM_CUDA(pm_launch(k_ga_init_comb<1>, groups, 1024, 0, s, one, X, improved, active, db, T, ga->comb_K,
+            PM_CUDA(pm_launch(k_ga_init_comb<1>, groups, 1024, 0, s, one, X, improved, active, db, T, Hh, ga->comb_K,
                               ga->seed, st, co));
             break;
         case 2:
-            PM_CUDA(pm_launch(k_ga_init_comb<2>, groups, 1024, 0, s, one, X, improved, active, db, T, ga->comb_K,
+            PM_CUDA(pm_launch(k_ga_init_comb<2>, groups, 1024, 0, s, one, X, improved, active, db, T, Hh, ga->comb_K,
                               ga->seed, st, co));
             break;
         case 4:
-            PM_CUDA(pm_launch(k_ga_init_comb<4>, groups, 1024, 0, s, one, X, improved, active, db, T, ga->comb_K,
+            PM_CUDA(pm_launch(k_ga_init_comb<4>, groups, 1024, 0, s, one, X, improved, active, db, T, Hh, ga->comb_K,
                               ga->seed, st, co));
             break;
         default:
-            PM_CUDA(pm_launch(k_ga_init_comb<8>, groups, 1024, 0, s, one, X, improved, active, db, T, ga->comb_K,
+            PM_CUDA(pm_launch(k_ga_init_comb<8>, groups, 1024, 0, s, one, X, improved, active, db, T, Hh, ga->comb_K,
                               ga->seed, st, co));
             break;
         }
@@ -1608,18 +1688,21 @@ static pm_status comb_prepare(pm_ga *ga, const pm_instance *inst, cudaStream_t s
         Q *= 2;
     if (Q > 8)
         return PM_ERR_UNSUPPORTED;  // C(m, p) beyond 2^8192
-    const size_t bytes = (size_t)(inst->p + 1) * (size_t)(inst->m - inst->p + 1) * (size_t)K * 4;
+    const size_t entries = (size_t)(inst->p + 1) * (size_t)(inst->m - inst->p + 1);
+    const size_t bytes = comb_head_offset(entries, K) * 4 + entries * 8;  // the entries, then their heads
     if (bytes > ((size_t)4 << 30))
         return PM_ERR_UNSUPPORTED;  // table above 4 GiB
     ga->comb_K = K;
     ga->comb_Q = Q;
+    ga->comb_entries = entries;
     PM_TRY(ga->comb_tab.reserve(bytes));
     int *flag = nullptr;
     PM_CUDA(pm_device_malloc_async(reinterpret_cast<void **>(&flag), sizeof(int), s));
     cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), s);
     if (e == cudaSuccess) {
-        k_comb_table<<<1, 1024, 0, s>>>(static_cast<uint32_t *>(ga->comb_tab.ptr), (int32_t)inst->m, (int32_t)inst->p,
-                                        K, flag);
+        uint32_t *T = static_cast<uint32_t *>(ga->comb_tab.ptr);
+        k_comb_table<<<1, 1024, 0, s>>>(T, reinterpret_cast<uint64_t *>(T + comb_head_offset(entries, K)),
+                                        (int32_t)inst->m, (int32_t)inst->p, K, flag);
         e = cudaGetLastError();
     }
     int overflow = 0;
