@@ -4,11 +4,14 @@
 //
 // One generation (the paper's Evolve call plus the host's population
 // renewal and migration):
-//   k_ga_init        fresh random population by Floyd sampling of a p-subset
-//                    (the paper draws a random combinadic rank, Section 4.1;
-//                    a 64-bit rank cannot index C(m,p) for the sizes used
-//                    here); for generation g > 0 slot 0 of every deme gets that
-//                    deme's best of generation g-1 (Section 4.5, variant (i)).
+//   k_ga_init_warp   fresh random population by Floyd sampling of a p-subset
+//                    (k_ga_init where its shared memory does not fit), or with
+//                    k_ga_init_comb the paper's generation (Section 4.1): a
+//                    uniform multi-word rank below C(m, p) and the combination
+//                    of that rank in lexicographic order; for generation g > 0
+//                    slot 0 of every deme gets that deme's best of generation
+//                    g-1 (Section 4.5, variant (i); variant (ii) puts every
+//                    deme's best into deme 0).
 //   evaluate         the column scan (fitness.cu, Section 4.2).
 //   crossover r      k_ga_crossover builds every child (butterfly partner
 //                    t XOR (D >> (1 + r mod lg D)), Section 3.2.2 step 3), the
