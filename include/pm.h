@@ -173,6 +173,34 @@ PM_API pm_status pm_eval_population_noalloc(pm_instance *inst, const uint32_t *m
                                             void *stream);
 
 /*
+ * The two launches of a column-kernel evaluation as separate calls (no
+ * counterpart in the paper; Section 4.2's Fitness over a population kept in
+ * facility-major form, the form the GA's operators write).
+ *
+ * pm_columns_layout -- the facility-major form the evaluation of `pop`
+ * individuals on inst uses: *groups = G (tiles of 32 G individuals) and
+ * *words = the uint32 words of the whole copy (both nullable).  Word
+ * (tile * 32W + j) * G + g, for j < 32W with W = ceil(m / 32), has bit b set
+ * iff individual tile * 32G + 32g + b (< pop) has facility j open; every
+ * other bit is 0.  Errors: PM_ERR_INVALID_ARG; PM_ERR_UNSUPPORTED when this
+ * size is evaluated by the row kernel (very large m, or a pinned or tuned
+ * row shape), which has no such form.
+ *
+ * pm_population_columns -- writes that form of the bitsets `masks` (device,
+ * as pm_eval_population) into `cols` (device, *words words from
+ * pm_columns_layout for the same pop; caller-owned).  Asynchronous.
+ *
+ * pm_eval_columns -- costs (device, pop int64) of the population held in
+ * `cols` in that form; the same costs as pm_eval_population of the bitsets.
+ * Asynchronous.  Both: PM_ERR_INVALID_ARG for host pointers or bad sizes,
+ * PM_ERR_UNSUPPORTED as pm_columns_layout, PM_ERR_OOM, PM_ERR_CUDA.
+ */
+PM_API pm_status pm_columns_layout(pm_instance *inst, int64_t pop, int32_t *groups, int64_t *words);
+PM_API pm_status pm_population_columns(pm_instance *inst, const uint32_t *masks, int64_t pop, uint32_t *cols,
+                                       void *stream);
+PM_API pm_status pm_eval_columns(pm_instance *inst, const uint32_t *cols, int64_t pop, int64_t *costs, void *stream);
+
+/*
  * pm_tune_eval -- autotune the tile shape of pm_eval_population for `pop`
  * individuals on this instance (no counterpart in the paper, whose Fitness
  * runs one thread per chromosome).  Candidates: facility-major tiles of

@@ -279,6 +279,54 @@ extern "C" pm_status pm_instance_tables(const pm_instance *inst, uint16_t *pi_ou
     return PM_OK;
 }
 
+extern "C" pm_status pm_columns_layout(pm_instance *inst, int64_t pop, int32_t *groups, int64_t *words)
+{
+    if (!inst || pop < 1)
+        return PM_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> guard(inst->lock);
+    const pm_eval_plan plan = pm_plan_eval(inst, pop);
+    if (groups)
+        *groups = plan.groups;
+    if (words)
+        *words = plan.groups ? (int64_t)(pm_plan_column_bytes(inst, plan) / 4) : 0;
+    return plan.groups ? PM_OK : PM_ERR_UNSUPPORTED;
+}
+
+extern "C" pm_status pm_population_columns(pm_instance *inst, const uint32_t *masks, int64_t pop, uint32_t *cols,
+                                           void *stream)
+{
+    if (!inst || pop < 1 || !masks || !cols || !pm_is_device_ptr(masks) || !pm_is_device_ptr(cols))
+        return PM_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> guard(inst->lock);
+    PM_CUDA(cudaSetDevice(inst->device));
+    return pm_launch_columns(inst, pm_plan_eval(inst, pop), masks, pop, cols, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" pm_status pm_eval_columns(pm_instance *inst, const uint32_t *cols, int64_t pop, int64_t *costs,
+                                     void *stream)
+{
+    if (!inst || pop < 1 || !cols || !costs || !pm_is_device_ptr(cols) || !pm_is_device_ptr(costs))
+        return PM_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> guard(inst->lock);
+    PM_CUDA(cudaSetDevice(inst->device));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const pm_eval_plan plan = pm_plan_eval(inst, pop);
+    if (!plan.groups)
+        return PM_ERR_UNSUPPORTED;
+    bool fresh = false;
+    PM_TRY(inst->partials.reserve(pm_plan_partial_bytes(plan, pop), &fresh));
+    if (fresh)  // accumulators start at zero; launches leave them zero
+        PM_CUDA(cudaMemsetAsync(inst->partials.ptr, 0, inst->partials.bytes, s));
+    PM_TRY(inst->tickets.reserve(pm_plan_ticket_bytes(plan), &fresh));
+    if (fresh)
+        PM_CUDA(cudaMemsetAsync(inst->tickets.ptr, 0, inst->tickets.bytes, s));
+    pm_accept_args acc;
+    acc.columns_ready = true;  // the scan reads `cols` as they are; no transpose
+    return pm_launch_eval(inst, plan, nullptr, pop, nullptr, costs, static_cast<int64_t *>(inst->partials.ptr),
+                          static_cast<int *>(inst->tickets.ptr), const_cast<uint32_t *>(cols),
+                          static_cast<int *>(inst->err.ptr), acc, s);
+}
+
 extern "C" pm_status pm_eval_population(pm_instance *inst, const uint32_t *masks, int64_t pop, int64_t *costs,
                                         int checked, void *stream)
 {

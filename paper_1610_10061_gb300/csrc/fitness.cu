@@ -759,6 +759,26 @@ pm_prob pm_single_prob(const pm_instance *inst, const pm_eval_plan &plan, int64_
 
 // Enqueue the transpose (unless the caller wrote the columns) and the column
 // scan of a launch; smem = the tile bytes of the launch's widest instance.
+static pm_status launch_transpose(const uint32_t *masks, const pm_prob *probs, int K, const pm_prob &one, int64_t jobs,
+                                  int G, uint32_t *colT, cudaStream_t stream)
+{
+    const int threads = 256;
+    const int64_t blocks = std::min<int64_t>(pm_ceil_div(jobs, threads / 32), (int64_t)2048);
+    PM_CUDA(pm_launch(k_pop_to_columns, (unsigned)blocks, threads, 0, stream, masks, probs, K, one, jobs, G, colT));
+    return PM_OK;
+}
+
+pm_status pm_launch_columns(const pm_instance *inst, const pm_eval_plan &plan, const uint32_t *masks, int64_t pop,
+                            uint32_t *colT, cudaStream_t stream)
+{
+    if (pop <= 0)
+        return PM_OK;
+    if (plan.groups == 0)
+        return PM_ERR_UNSUPPORTED;
+    return launch_transpose(masks, nullptr, 1, pm_single_prob(inst, plan, pop), plan.tiles * plan.groups * inst->W,
+                            plan.groups, colT, stream);
+}
+
 pm_status pm_launch_scan(const pm_scan_launch &L, const pm_accept_args &acc, int64_t *costs, size_t smem,
                          cudaStream_t stream)
 {
@@ -772,12 +792,8 @@ pm_status pm_launch_scan(const pm_scan_launch &L, const pm_accept_args &acc, int
     ep.cand_masks = acc.cand_masks;
     ep.improved = acc.improved;
     const int G = L.groups;
-    if (!acc.columns_ready) {
-        const int threads = 256;
-        const int64_t blocks = std::min<int64_t>(pm_ceil_div(L.jobs, threads / 32), (int64_t)2048);
-        PM_CUDA(pm_launch(k_pop_to_columns, (unsigned)blocks, threads, 0, stream, L.masks, L.probs_dev, L.K, L.one,
-                          L.jobs, G, L.colT));
-    }
+    if (!acc.columns_ready)
+        PM_TRY(launch_transpose(L.masks, L.probs_dev, L.K, L.one, L.jobs, G, L.colT, stream));
     const int threads = L.warps * 32;
     const unsigned grid = (unsigned)L.grid;
     unsigned long long *accum = reinterpret_cast<unsigned long long *>(L.accum);

@@ -194,6 +194,10 @@ pm_prob pm_single_prob(const pm_instance *inst, const pm_eval_plan &plan, int64_
 pm_status pm_launch_eval(const pm_instance *inst, const pm_eval_plan &plan, const uint32_t *masks, int64_t pop,
                          const uint32_t *active, int64_t *costs, int64_t *partials, int *tickets, uint32_t *colT,
                          int *err, const pm_accept_args &acc, cudaStream_t stream);
+// The facility-major copy of (masks, pop) for the column kernel of `plan` (PM_ERR_UNSUPPORTED for the row
+// kernel): the first of the two launches of pm_launch_eval.
+pm_status pm_launch_columns(const pm_instance *inst, const pm_eval_plan &plan, const uint32_t *masks, int64_t pop,
+                            uint32_t *colT, cudaStream_t stream);
 // Bytes of the facility-major copy of the population the plan needs.
 size_t pm_plan_column_bytes(const pm_instance *inst, const pm_eval_plan &plan);
 // One-time per-process kernel attributes (dynamic shared memory opt-in).

@@ -71,6 +71,9 @@ _SIGS = {
     "pm_eval_population_noalloc": ([_P, _P, _I64, _P, _P], _S),
     "pm_selftest_bounded_wait": ([ctypes.c_int, _P], _S),
     "pm_debug_fail_alloc": ([_I64, _P], _S),
+    "pm_columns_layout": ([_P, _I64, _P, _P], _S),
+    "pm_population_columns": ([_P, _P, _I64, _P, _P], _S),
+    "pm_eval_columns": ([_P, _P, _I64, _P, _P], _S),
     "pm_tune_eval": ([_P, _I64, _P, ctypes.POINTER(pm_eval_shape)], _S),
     "pm_set_eval_shape": ([_P, _I64, ctypes.POINTER(pm_eval_shape)], _S),
     "pm_ga_create": ([_P, ctypes.c_uint64, _I64, ctypes.POINTER(pm_ga_params), _P, _PP], _S),
@@ -208,6 +211,22 @@ def pm_debug_fail_alloc(after: int) -> int:
     pending = ctypes.c_int64(-1)
     _check(_lib.pm_debug_fail_alloc(int(after), ctypes.byref(pending)), "pm_debug_fail_alloc")
     return int(pending.value)
+
+
+def pm_columns_layout(inst, pop: int):
+    """(G, words) of the facility-major form the evaluation of `pop` individuals uses."""
+    g = ctypes.c_int32()
+    w = ctypes.c_int64()
+    _check(_lib.pm_columns_layout(inst, pop, ctypes.byref(g), ctypes.byref(w)), "pm_columns_layout")
+    return int(g.value), int(w.value)
+
+
+def pm_population_columns(inst, masks, pop: int, cols, stream=None):
+    _check(_lib.pm_population_columns(inst, _addr(masks), pop, _addr(cols), _stream(stream)), "pm_population_columns")
+
+
+def pm_eval_columns(inst, cols, pop: int, costs, stream=None):
+    _check(_lib.pm_eval_columns(inst, _addr(cols), pop, _addr(costs), _stream(stream)), "pm_eval_columns")
 
 
 def pm_tune_eval(inst, pop: int, stream=None):

@@ -502,3 +502,58 @@ def test_ga_feature_combinations(pm):
     """Combinadic generation on cumulative tables with migration variant (ii), against the oracle."""
     _ga_compare(pm, euclid_instance(150, seed=21)[:90], 12, 128, 3, check_every=1, deme=32, seed=4,
                 init="combinadic", migration="team", cumulative=True)
+
+
+def _columns_layout(masks, m, G):
+    """The documented facility-major form, built here from the bitsets: word (tile * 32W + j) * G + g has bit b
+    set iff individual tile * 32G + 32g + b has facility j open."""
+    pop, W = masks.shape
+    tiles = -(-pop // (32 * G))
+    bits = ((masks[:, :, None].astype(np.uint64) >> np.arange(32, dtype=np.uint64)) & 1).reshape(pop, 32 * W)
+    padded = np.zeros((tiles * 32 * G, 32 * W), dtype=np.uint64)
+    padded[:pop] = bits
+    per = padded.reshape(tiles, G, 32, 32 * W)  # [tile, g, b, j]
+    words = (per << np.arange(32, dtype=np.uint64)[None, None, :, None]).sum(axis=2)  # [tile, g, j]
+    return words.transpose(0, 2, 1).astype(np.uint32).reshape(-1)
+
+
+@pytest.mark.parametrize("shape", [(4, 32, 0), (2, 8, 0), (1, 16, 3)])
+@pytest.mark.parametrize("pop", [1, 97, 1024])
+def test_columns_api_matches_oracle_and_layout(pm, shape, pop):
+    """pm_population_columns writes the documented form; pm_eval_columns on it gives the oracle's costs."""
+    d, p = graph_instance(300, 1200, seed=5), 17
+    inst = pm.Instance(d, p)
+    G, warps, splits = shape
+    inst.set_shape(pop, groups=G, warps=warps, splits=splits)
+    g, words = pm.pm_columns_layout(inst.handle, pop)
+    assert g == G
+    masks = random_masks(pop, 300, p, seed=pop)
+    want_cols = _columns_layout(masks, 300, G)
+    assert words == want_cols.size
+    cols = torch.full((words,), -1, dtype=torch.int32, device="cuda")  # every word must be written
+    pm.pm_population_columns(inst.handle, to_dev(masks), pop, cols)
+    np.testing.assert_array_equal(cols.cpu().numpy().view(np.uint32), want_cols)
+    costs = torch.empty(pop, dtype=torch.int64, device="cuda")
+    pm.pm_eval_columns(inst.handle, cols, pop, costs)
+    np.testing.assert_array_equal(costs.cpu().numpy(), oracle.eval_direct(d, masks))
+    # columns built on the host from the documented form evaluate the same
+    cols2 = torch.from_numpy(want_cols.view(np.int32)).cuda()
+    pm.pm_eval_columns(inst.handle, cols2, pop, costs)
+    np.testing.assert_array_equal(costs.cpu().numpy(), oracle.eval_direct(d, masks))
+    inst.close()
+
+
+def test_columns_api_refuses_the_row_kernel_and_host_pointers(pm):
+    d, p = graph_instance(100, 200, seed=0), 5
+    inst = pm.Instance(d, p)
+    inst.set_shape(64, groups=0, warps=8)
+    with pytest.raises(pm.PMError) as e:
+        pm.pm_columns_layout(inst.handle, 64)
+    assert e.value.status == 3  # PM_ERR_UNSUPPORTED
+    inst.set_shape(64, groups=2, warps=8)
+    g, words = pm.pm_columns_layout(inst.handle, 64)
+    host = np.zeros(words, dtype=np.uint32)
+    with pytest.raises(pm.PMError) as e:
+        pm.pm_eval_columns(inst.handle, host, 64, torch.empty(64, dtype=torch.int64, device="cuda"))
+    assert e.value.status == 1  # PM_ERR_INVALID_ARG
+    inst.close()
