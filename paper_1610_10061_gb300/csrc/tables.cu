@@ -19,7 +19,11 @@
 //             that digit plus the number of equal-digit lanes below it, then
 //             the group leader advances the offset.
 // Keys (uint32) and ids (uint16) live in shared memory when the row fits
-// (12 bytes per element), else in a per-CTA global scratch slice.  The
+// (12 bytes per element), else in a per-CTA global scratch slice.  When every
+// distance is below 2^16 (kPacked) a key and its id share one word,
+// (distance << 16) | id, and the digits come from the upper half: 8 bytes per
+// element, so two 10000-wide rows sort at once on an SM, and a scatter moves
+// one word.  The
 // epilogue writes Pi' and the differences Delta' into rows padded to a stride
 // of round_up(L, 32) elements (padding = 0).
 
@@ -56,6 +60,7 @@ __global__ void k_minmax_init(int *out)
     out[1] = (int)0x80000000;
 }
 
+template <bool kPacked>
 __global__ void __launch_bounds__(kSortThreads) k_tables(const int32_t *__restrict__ d, int64_t n, int32_t m,
                                                          int32_t L, int64_t stride, int passes, int cum,
                                                          uint16_t *__restrict__ pi, int32_t *__restrict__ delta,
@@ -68,10 +73,12 @@ __global__ void __launch_bounds__(kSortThreads) k_tables(const int32_t *__restri
 
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    unsigned char *buf = gscratch ? gscratch + (size_t)blockIdx.x * (size_t)m * 12 : sm_raw;
+    constexpr size_t kElemBytes = kPacked ? 8 : 12;
+    constexpr uint32_t kKeyShift = kPacked ? 16 : 0;  // where the distance's digits start in a key word
+    unsigned char *buf = gscratch ? gscratch + (size_t)blockIdx.x * (size_t)m * kElemBytes : sm_raw;
     uint32_t *keysA = reinterpret_cast<uint32_t *>(buf);
     uint32_t *keysB = keysA + m;
-    uint16_t *valsA = reinterpret_cast<uint16_t *>(keysB + m);
+    uint16_t *valsA = reinterpret_cast<uint16_t *>(keysB + m);  // unused when kPacked
     uint16_t *valsB = valsA + m;
     const int seg = (((m + kSortWarps - 1) / kSortWarps) + 31) & ~31;
     const int s_begin = warp * seg;
@@ -81,14 +88,18 @@ __global__ void __launch_bounds__(kSortThreads) k_tables(const int32_t *__restri
     for (int64_t row = blockIdx.x; row < n; row += gridDim.x) {
         const int32_t *drow = d + row * (int64_t)m;
         for (int i = threadIdx.x; i < m; i += blockDim.x) {
-            keysA[i] = (uint32_t)__ldg(drow + i);
-            valsA[i] = (uint16_t)i;
+            if constexpr (kPacked) {
+                keysA[i] = ((uint32_t)__ldg(drow + i) << 16) | (uint32_t)i;
+            } else {
+                keysA[i] = (uint32_t)__ldg(drow + i);
+                valsA[i] = (uint16_t)i;
+            }
         }
         __syncthreads();
         uint32_t *kin = keysA, *kout = keysB;
         uint16_t *vin = valsA, *vout = valsB;
         for (int pass = 0; pass < passes; ++pass) {
-            const int shift = 8 * pass;
+            const int shift = kKeyShift + 8 * pass;
             for (int i = threadIdx.x; i < kSortWarps * 256; i += blockDim.x)
                 (&whist[0][0])[i] = 0;
             __syncthreads();
@@ -143,14 +154,16 @@ __global__ void __launch_bounds__(kSortThreads) k_tables(const int32_t *__restri
                 uint16_t val = 0;
                 if (valid) {
                     key = kin[i];
-                    val = vin[i];
+                    if constexpr (!kPacked)
+                        val = vin[i];
                 }
                 const uint32_t dig = valid ? ((key >> shift) & 255u) : 256u;
                 const unsigned peers = __match_any_sync(PM_FULL_MASK, dig);
                 if (valid) {
                     const uint32_t pos = whist[warp][dig] + __popc(peers & lt_mask);
                     kout[pos] = key;
-                    vout[pos] = val;
+                    if constexpr (!kPacked)
+                        vout[pos] = val;
                 }
                 __syncwarp();
                 if (valid && lane == __ffs(peers) - 1)
@@ -171,8 +184,10 @@ __global__ void __launch_bounds__(kSortThreads) k_tables(const int32_t *__restri
         int32_t *qrow = delta + row * stride;
         for (int r = threadIdx.x; r < stride; r += blockDim.x) {
             if (r < L) {
-                prow[r] = vin[r];
-                qrow[r] = cum ? (int32_t)kin[r] : (int32_t)(kin[r] - (r > 0 ? kin[r - 1] : 0u));
+                const uint32_t dist = kin[r] >> kKeyShift;
+                const uint32_t prev = r > 0 ? kin[r - 1] >> kKeyShift : 0u;
+                prow[r] = kPacked ? (uint16_t)(kin[r] & 0xffffu) : vin[r];
+                qrow[r] = cum ? (int32_t)dist : (int32_t)(dist - prev);
             } else {
                 prow[r] = 0;
                 qrow[r] = 0;
@@ -234,8 +249,9 @@ pm_status pm_build_tables(pm_instance *inst, const int32_t *d_dev, cudaStream_t 
         return PM_ERR_NEGATIVE_DIST;
     inst->max_d = host_mm[1];
     const int passes = (bits_needed((uint32_t)host_mm[1]) + 7) / 8;
+    const bool packed = host_mm[1] < 65536;  // distance and facility id in one 32-bit word
 
-    const size_t row_bytes = (size_t)inst->m * 12;
+    const size_t row_bytes = (size_t)inst->m * (packed ? 8 : 12);
     const size_t static_bytes = sizeof(uint32_t) * (kSortWarps * 256 + 256 + 8) + 1024;
     const bool in_smem = row_bytes + static_bytes <= inst->smem_optin;
     unsigned char *gscratch = nullptr;
@@ -243,16 +259,24 @@ pm_status pm_build_tables(pm_instance *inst, const int32_t *d_dev, cudaStream_t 
     size_t dyn = 0;
     if (in_smem) {
         dyn = row_bytes;
-        PM_CUDA(cudaFuncSetAttribute(k_tables, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+        PM_CUDA(cudaFuncSetAttribute(packed ? k_tables<true> : k_tables<false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
         const int64_t per_sm = std::max<int64_t>(1, std::min<int64_t>(4, (int64_t)(inst->smem_optin / (dyn + static_bytes))));
         grid = std::min<int64_t>(inst->n, (int64_t)inst->sm_count * per_sm);
     } else {
         grid = std::min<int64_t>(inst->n, (int64_t)inst->sm_count);
         PM_CUDA(pm_device_malloc_async(reinterpret_cast<void **>(&gscratch), (size_t)grid * row_bytes, stream));
     }
-    k_tables<<<(unsigned)grid, kSortThreads, dyn, stream>>>(d_dev, inst->n, (int32_t)inst->m, (int32_t)inst->L,
-                                                           inst->stride, passes, inst->cum ? 1 : 0, inst->pi,
-                                                           inst->delta, gscratch);
+    if (packed)
+        k_tables<true><<<(unsigned)grid, kSortThreads, dyn, stream>>>(d_dev, inst->n, (int32_t)inst->m,
+                                                                     (int32_t)inst->L, inst->stride, passes,
+                                                                     inst->cum ? 1 : 0, inst->pi, inst->delta,
+                                                                     gscratch);
+    else
+        k_tables<false><<<(unsigned)grid, kSortThreads, dyn, stream>>>(d_dev, inst->n, (int32_t)inst->m,
+                                                                      (int32_t)inst->L, inst->stride, passes,
+                                                                      inst->cum ? 1 : 0, inst->pi, inst->delta,
+                                                                      gscratch);
     cudaError_t le = cudaGetLastError();
     if (gscratch)
         cudaFreeAsync(gscratch, stream);
