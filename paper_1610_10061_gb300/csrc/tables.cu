@@ -11,21 +11,22 @@
 // order, so a stable sort on the distance alone yields the (distance, id)
 // order; only ceil(bits(max d) / 8) passes are needed.  Each pass:
 //   count   - every warp owns a contiguous segment of the row and walks it 32
-//             keys at a time; __match_any_sync groups equal digits, the lowest
-//             lane of each group adds the group size to the warp's histogram;
+//             keys at a time, one shared-memory atomic per key into the warp's
+//             histogram (faster than grouping equal digits first, even when
+//             every key of a row is equal);
 //   offsets - per digit, the running count over warps, plus the exclusive
 //             scan over digits;
-//   scatter - the same walk; a key's destination is its warp's offset for
-//             that digit plus the number of equal-digit lanes below it, then
-//             the group leader advances the offset.
+//   scatter - the same walk; nine ballots give each lane the lanes holding
+//             the same digit, a key's destination is its warp's offset for that
+//             digit plus the number of those lanes below it, then the lowest of
+//             them advances the offset.
 // Keys (uint32) and ids (uint16) live in shared memory when the row fits
 // (12 bytes per element), else in a per-CTA global scratch slice.  When every
 // distance is below 2^16 (kPacked) a key and its id share one word,
 // (distance << 16) | id, and the digits come from the upper half: 8 bytes per
 // element, so two 10000-wide rows sort at once on an SM, and a scatter moves
-// one word.  The
-// epilogue writes Pi' and the differences Delta' into rows padded to a stride
-// of round_up(L, 32) elements (padding = 0).
+// one word.  The epilogue writes Pi' and the differences Delta' into rows
+// padded to a stride of round_up(L, 32) elements (padding = 0).
 
 #include "pm_alloc.h"
 #include "pm_common.cuh"
@@ -58,6 +59,19 @@ __global__ void k_minmax_init(int *out)
 {
     out[0] = 0x7fffffff;
     out[1] = (int)0x80000000;
+}
+
+// The lanes whose 9-bit value equals this lane's (digits 0..255, 256 = no key): one ballot per bit.  Faster
+// here than __match_any_sync, whose latency sits on every step of the scatter walk.
+__device__ __forceinline__ unsigned equal_digit_lanes(uint32_t dig)
+{
+    unsigned peers = PM_FULL_MASK;
+#pragma unroll
+    for (int b = 0; b < 9; ++b) {
+        const unsigned bb = __ballot_sync(PM_FULL_MASK, (dig >> b) & 1u);
+        peers &= ((dig >> b) & 1u) ? bb : ~bb;
+    }
+    return peers;
 }
 
 template <bool kPacked>
@@ -107,11 +121,8 @@ __global__ void __launch_bounds__(kSortThreads) k_tables(const int32_t *__restri
             for (int base = s_begin; base < s_end; base += 32) {
                 const int i = base + lane;
                 const bool valid = i < s_end;
-                const uint32_t dig = valid ? ((kin[i] >> shift) & 255u) : 256u;
-                const unsigned peers = __match_any_sync(PM_FULL_MASK, dig);
-                if (valid && lane == __ffs(peers) - 1)
-                    whist[warp][dig] += __popc(peers);
-                __syncwarp();
+                if (valid)
+                    atomicAdd(&whist[warp][(kin[i] >> shift) & 255u], 1u);
             }
             __syncthreads();
             // offsets: per digit over warps, then exclusive scan over digits
@@ -158,7 +169,7 @@ __global__ void __launch_bounds__(kSortThreads) k_tables(const int32_t *__restri
                         val = vin[i];
                 }
                 const uint32_t dig = valid ? ((key >> shift) & 255u) : 256u;
-                const unsigned peers = __match_any_sync(PM_FULL_MASK, dig);
+                const unsigned peers = equal_digit_lanes(dig);
                 if (valid) {
                     const uint32_t pos = whist[warp][dig] + __popc(peers & lt_mask);
                     kout[pos] = key;
