@@ -740,6 +740,7 @@ __global__ void __launch_bounds__(1024, 2) k_swap_stats(const uint16_t *__restri
     }
     __syncthreads();
     for (int i = warp; i < nc; i += nwarps) {
+        int32_t d_carry0 = 0;  // Delta': the sum of the first 32 increments (D': the value at rank 31)
         // first 32 ranks (loaded a client ahead).  When the first open rank r1 is among them -- the usual
         // case unless p/m is tiny -- every gain comes from this step: the ranks before r1 gain d1 - d(i, k) and
         // the facility at r1 loses d2 - d1, with d2 at the second open rank (later steps are read only for it).
@@ -805,14 +806,19 @@ __global__ void __launch_bounds__(1024, 2) k_swap_stats(const uint16_t *__restri
                 }
                 continue;
             }
+            // no open facility among the first 32 ranks: the general path goes on from rank 32 with their sum
+            if (!cum)
+                d_carry0 = __reduce_add_sync(PM_FULL_MASK, d0);
+            else
+                d_carry0 = __shfl_sync(PM_FULL_MASK, d0, 31);
         }
         // general path -- pass 1: first and second open ranks and their distances
         const uint16_t *prow = pi + (size_t)i * st;
         const int32_t *drow = delta + (size_t)i * st;
-        int32_t carry = 0, d1 = 0, d2 = 0;
+        int32_t carry = d_carry0, d1 = 0, d2 = 0;
         int r1 = -1, found = 0;
         uint32_t f1 = 0;
-        for (int base = 0; base < L && found < 2; base += 32) {
+        for (int base = 32; base < L && found < 2; base += 32) {
             const int r = base + lane;
             uint32_t j = 0;
             int32_t dl = 0;
@@ -824,7 +830,7 @@ __global__ void __launch_bounds__(1024, 2) k_swap_stats(const uint16_t *__restri
             }
             const bool open = (r < L) && ((bits[j >> 5] >> (j & 31)) & 1u);
             uint32_t bal = __ballot_sync(PM_FULL_MASK, open);
-            if (bal == 0u && found == 0) {  // no open facility among these 32 ranks: only the carry moves
+            if (bal == 0u) {  // no open facility among these 32 ranks: only the carry moves
                 if (!cum)
                     carry += __reduce_add_sync(PM_FULL_MASK, dl);
                 else
