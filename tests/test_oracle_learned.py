@@ -8,7 +8,6 @@ differences; Adam to a two-step example worked by hand from Kingma & Ba's
 Algorithm 1.
 """
 
-import itertools
 
 import numpy as np
 import pytest
