@@ -112,6 +112,34 @@ def time_scan_alone(pm, torch, inst, dmask, pop, dcost, flush, stream, reps):
     return statistics.mean(a.elapsed_time(b) for a, b in zip(es, ee))
 
 
+def brute_force_optimum(pm, torch, inst, m, p, stream, chunk=1 << 22):
+    """The optimum of a small instance: every p-subset evaluated by the library (pm_eval_population), in chunks.
+    Rank N of the combinatorial number system is turned into its subset by taking, for k = p .. 1, the largest c
+    with C(c, k) <= N and subtracting C(c, k).  Returns (cost, bitset words, subsets evaluated)."""
+    import math
+
+    total = math.comb(m, p)
+    W = (m + 31) // 32
+    binom = torch.tensor([[math.comb(c, k) for c in range(m)] for k in range(p + 1)], dtype=torch.int64,
+                         device="cuda")
+    best_cost, best_mask = None, None
+    costs = torch.empty(chunk, dtype=torch.int64, device="cuda")
+    for start in range(0, total, chunk):
+        N = torch.arange(start, min(total, start + chunk), dtype=torch.int64, device="cuda")
+        cnt = N.numel()
+        words = torch.zeros((cnt, W), dtype=torch.int64, device="cuda")
+        for k in range(p, 0, -1):
+            c = torch.searchsorted(binom[k], N, right=True) - 1
+            N = N - binom[k][c]
+            words.scatter_add_(1, (c // 32).unsqueeze(1), torch.bitwise_left_shift(torch.ones_like(c), c % 32).unsqueeze(1))
+        masks = (words - ((words >> 31) << 32)).to(torch.int32).contiguous()  # the same 32 bits, as int32
+        pm.pm_eval_population(inst.handle, masks, cnt, costs, 0, stream.cuda_stream)
+        v, i = torch.min(costs[:cnt], dim=0)
+        if best_cost is None or int(v) < best_cost:
+            best_cost, best_mask = int(v), masks[int(i)].cpu()
+    return best_cost, best_mask, total
+
+
 def measured_bf16_peak():
     """Dense BF16 tensor peak (TFLOP/s): the measured cuBLAS burst figure for a kernel timed alone."""
     try:
@@ -730,11 +758,13 @@ def run_batched(args):
 def run_learned(args):
     """Time-to-target of the GA with the learned swap proposal against the plain GA (same GB300).
 
-    Workload gmm5000_p{50,500}: clustered Euclidean n = m = 5000 (50 Gaussian components, sigma 0.02), pop 1024
-    in demes of 256.  The model is trained on tuples (individual, move, exact cost change) logged from plain-GA
-    populations of a separate run (seed 1000).  Target = the best cost the plain GA (seed 0) reaches in
-    `--steps` generations; each arm's time-to-target is the summed CUDA-event time of its generations up to the
-    first one whose best cost is at or below the target (seeds 0..4, medians; training time reported apart).
+    Workloads: gmm5000_p{50,500}, clustered Euclidean n = m = 5000 (50 Gaussian components, sigma 0.02), pop 1024
+    in demes of 256, target = the best cost the plain GA (seed 0) reaches in `--steps` generations; and graph100
+    (the paper's pmed1 shape: n = m = 100, 200 edges, p = 5, pop 64), target = the optimum itself, found by
+    evaluating every p-subset on the GPU.  The model is trained on tuples (individual, move, exact cost change)
+    logged from plain-GA populations of a separate run (seed 1000).  Each arm's time-to-target is the summed
+    CUDA-event time of its generations up to the first one whose best cost is at or below the target (seeds 0..4,
+    medians; training time reported apart).
     """
     import numpy as np
     import torch
@@ -754,12 +784,19 @@ def run_learned(args):
     inst = pm.Instance(d, p, stream=stream.cuda_stream, cumulative=args.tables == "cumulative")
     inst.tune(pop, stream=stream.cuda_stream)
     budget = args.steps
+    deme = min(pop, 256)
+    optimum = None
+    if name == "graph100":  # the target is the brute-force optimum (cfg of the paper's pmed1 shape)
+        t0 = time.perf_counter()
+        optimum, _, subsets = brute_force_optimum(pm, torch, inst, m, p, stream)
+        torch.cuda.synchronize()
+        brute_s = time.perf_counter() - t0
 
     # ---- log ~1M training tuples from plain-GA populations (a separate run) and train ----
     t0 = time.perf_counter()
     per = 64
     log_gens = max(1, (1 << 20) // (pop * per))
-    ga = pm.GA(inst, seed=1000, pop=pop, deme=256, stream=stream.cuda_stream)
+    ga = pm.GA(inst, seed=1000, pop=pop, deme=deme, stream=stream.cuda_stream)
     xs, ts = [], []
     costs_dev = torch.empty(pop, dtype=torch.int64, device="cuda")
     masks_dev = torch.empty((pop, inst.W), dtype=torch.int32, device="cuda")
@@ -784,7 +821,7 @@ def run_learned(args):
     mse_after, _ = model.grad(X, T)
 
     def run(seed, use_model, gens):
-        g = pm.GA(inst, seed=seed, pop=pop, deme=256, model=model if use_model else None,
+        g = pm.GA(inst, seed=seed, pop=pop, deme=deme, model=model if use_model else None,
                   stream=stream.cuda_stream)
         ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(gens)]
         ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(gens)]
@@ -799,10 +836,14 @@ def run_learned(args):
         g.close()
         return tr.cpu().numpy(), np.cumsum(ms) / 1000.0, evals
 
-    ptrace0, _, _ = run(0, False, budget)
-    target = int(ptrace0[-1])
+    if optimum is not None:
+        target = optimum
+        limit = max(4 * budget, 200)  # the paper's pmed1-shaped runs: up to 200 generations
+    else:
+        ptrace0, _, _ = run(0, False, budget)
+        target = int(ptrace0[-1])
+        limit = 4 * budget  # each arm may run up to four times the budget that defined the target
     res = {"plain": [], "learned": []}
-    limit = 4 * budget  # each arm may run up to four times the budget that defined the target
     clocks = Clocks(0)
     torch.cuda.synchronize()
     clocks.start()
@@ -851,21 +892,34 @@ def run_learned(args):
                                       "moves a learned generation scores, filled with the logged feature rows"}
 
     def med(arm, key):
-        vals = [r[key] for r in res[arm] if r[key] is not None]
-        return float(np.median(vals)) if len(vals) == len(res[arm]) else None
+        """Median over the seeds; a run that never reached the target counts as slower than every run that did
+        (a censored median), so the median exists while at least half of the runs reached it."""
+        vals = sorted(float("inf") if r[key] is None else r[key] for r in res[arm])
+        k = len(vals)
+        v = vals[k // 2] if k % 2 else 0.5 * (vals[k // 2 - 1] + vals[k // 2])
+        return None if v == float("inf") else float(v)
 
     lt, pt = med("learned", "time_s"), med("plain", "time_s")
+    if optimum is not None:
+        desc = (f"{name}: connected random graph n=m={n} ({w.get('edges', 2 * n)} edges, weights U[1,100], APSP), "
+                f"p={p}, pop {pop} in one deme of {deme}; each arm may run up to {limit} generations; "
+                "seeds 0-4, medians")
+        target_kind = (f"the optimum: all {subsets} {p}-subsets evaluated by pm_eval_population on the GPU in "
+                       f"{brute_s:.2f} s")
+    else:
+        desc = (f"{name}: clustered Euclidean n=m={n}, 50 components sigma 0.02, p={p}, pop {pop} in demes of "
+                f"{deme}; each arm may run up to {limit} generations; seeds 0-4, medians")
+        target_kind = f"the best cost of the plain GA (seed 0) after {budget} generations"
     line = {"metric": "time-to-target cost, learned vs plain GA", "value": lt, "unit": "s",
             "higher_is_better": False, "n_gpus": 1, "steps": budget, "warmup": 0, "vs_baseline": None,
             "dtype": "int64 (costs); bf16/fp32 (model)", "data": "synthetic",
-            "config": {"tables": args.tables, "workload": f"{name}: clustered Euclidean n=m={n}, 50 components sigma 0.02, p={p}, "
-                                   f"pop {pop} in demes of 256; target = plain GA (seed 0) best after {budget} "
-                                   "generations; each arm may run up to 4x that; seeds 0-4, medians",
-                       "target": target, "train_tuples": int(X.shape[0]), "train_epochs": 6,
+            "config": {"tables": args.tables, "workload": desc, "target": target, "target_kind": target_kind,
+                       "train_tuples": int(X.shape[0]), "train_epochs": 6,
                        "train_mse_before_after": [mse_before, mse_after], "log_s": log_s, "train_s": train_s},
             "plain_time_s": pt, "learned_time_s": lt,
             "speedup": (pt / lt) if (pt and lt) else None,
             "plain_gens": med("plain", "gens"), "learned_gens": med("learned", "gens"),
+            "reached": {arm: sum(r["time_s"] is not None for r in res[arm]) for arm in res},
             "plain_ms_per_gen": med("plain", "ms_per_gen"), "learned_ms_per_gen": med("learned", "ms_per_gen"),
             "roofline": roofline, "clocks": clk, "runs": res}
     print(json.dumps(line), flush=True)
