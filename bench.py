@@ -176,6 +176,40 @@ def profiled_traffic(name):
         return None
 
 
+def parse_clock_samples(lines, t_start, t_end):
+    """Median SM clock, max clock and throttle reasons of nvidia-smi CSV lines (timestamp, index, clocks.sm,
+    clocks.max.sm, power, active reasons, hw_slowdown, hw_thermal_slowdown, sw_thermal_slowdown, sw_power_cap),
+    over the samples taken in [t_start, t_end] (every sample, flagged, if none falls there)."""
+    rows = []
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in lines:
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 10:
+            continue
+        try:
+            rows.append((Clocks._stamp(parts[0]), float(parts[2]), float(parts[3]),
+                         [nm for nm, v in zip(names, parts[6:10]) if v.lower() == "active"]))
+        except ValueError:
+            continue
+    inside = [r for r in rows if r[0] is not None and t_start - 0.05 <= r[0] <= t_end + 0.05]
+    use = inside if inside else rows
+    sm = [r[1] for r in use]
+    mx = [r[2] for r in use]
+    return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+            "reasons": sorted({nm for r in use for nm in r[3]}), "samples": len(use), "in_timed_region": bool(inside)}
+
+
+def censored_median(values):
+    """Median of per-seed results where None (the target never reached) counts as slower than any result: None
+    when at least half of the runs never reached it."""
+    vals = sorted(float("inf") if v is None else v for v in values)
+    k = len(vals)
+    if k == 0:
+        return None
+    v = vals[k // 2] if k % 2 else 0.5 * (vals[k // 2 - 1] + vals[k // 2])
+    return None if v == float("inf") else float(v)
+
+
 class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region.
 
@@ -232,27 +266,12 @@ class Clocks:
         except Exception:
             self.proc.kill()
         self.fh.close()
-        rows = []
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         with open(self.path) as fh:
-            for line in fh:
-                parts = [x.strip() for x in line.split(",")]
-                if len(parts) < 10:
-                    continue
-                try:
-                    rows.append((self._stamp(parts[0]), float(parts[2]), float(parts[3]),
-                                 [nm for nm, v in zip(names, parts[6:10]) if v.lower() == "active"]))
-                except ValueError:
-                    continue
+            lines = fh.readlines()
         os.unlink(self.path)
-        inside = [r for r in rows if r[0] is not None and self.t_start - 0.05 <= r[0] <= self.t_end + 0.05]
-        use = inside if inside else rows
-        sm = [r[1] for r in use]
-        mx = [r[2] for r in use]
-        reasons = sorted({nm for r in use for nm in r[3]})
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(use), "in_timed_region": bool(inside),
-                "timed_region_s": round(self.t_end - self.t_start, 3)}
+        out = parse_clock_samples(lines, self.t_start, self.t_end)
+        out["timed_region_s"] = round(self.t_end - self.t_start, 3)
+        return out
 
 
 def combine_ranks(evals, ms, device="cpu"):
@@ -892,12 +911,7 @@ def run_learned(args):
                                       "moves a learned generation scores, filled with the logged feature rows"}
 
     def med(arm, key):
-        """Median over the seeds; a run that never reached the target counts as slower than every run that did
-        (a censored median), so the median exists while at least half of the runs reached it."""
-        vals = sorted(float("inf") if r[key] is None else r[key] for r in res[arm])
-        k = len(vals)
-        v = vals[k // 2] if k % 2 else 0.5 * (vals[k // 2 - 1] + vals[k // 2])
-        return None if v == float("inf") else float(v)
+        return censored_median([r[key] for r in res[arm]])
 
     lt, pt = med("learned", "time_s"), med("plain", "time_s")
     if optimum is not None:
