@@ -157,8 +157,9 @@ def fitness_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(name):
-    """DRAM bytes per launch of the scan kernel from the committed ncu summary, if it matches this source."""
+def profiled_value(name, key):
+    """A figure of the scan kernel from its committed ncu summary (profiles/fitness_scan_<name>.md), if that
+    summary was taken on this source (its source_hash); else None."""
     path = os.path.join(ROOT, "profiles", f"fitness_scan_{name}.md")
     if not os.path.exists(path):
         return None
@@ -171,9 +172,34 @@ def profiled_traffic(name):
     if vals.get("source_hash") != fitness_source_hash():
         return None
     try:
-        return float(vals["dram_bytes_per_launch"])
+        return float(vals[key])
     except (KeyError, ValueError):
         return None
+
+
+def profiled_traffic(name):
+    """DRAM bytes per launch of the scan kernel from the committed ncu summary, if it matches this source."""
+    return profiled_value(name, "dram_bytes_per_launch")
+
+
+# Instruction-issue peak of the GB300: 152 SMs x 4 SM sub-partitions x one warp-instruction per cycle at the
+# maximum SM clock of 2070 MHz.
+ISSUE_PEAK = 152 * 4 * 2.07e9
+
+
+def issue_roofline(name, launch_ms):
+    """The scan kernel against the SM instruction-issue peak: warp-instructions per launch (ncu, committed
+    summary) over the live CUDA-event launch time.  None without a summary for this source."""
+    inst = profiled_value(name, "warp_instructions_per_launch")
+    if inst is None or not launch_ms:
+        return None
+    achieved = inst / (launch_ms / 1000.0)
+    return {"bound": "issue", "achieved": achieved, "peak": ISSUE_PEAK, "unit": "warp-instructions/s",
+            "frac": achieved / ISSUE_PEAK, "instructions_per_launch": inst,
+            "peak_source": "152 SMs x 4 sub-partitions x 1 warp-instruction/cycle x 2070 MHz",
+            "note": "the bound the scan meets in practice (integer, shuffle and shared-memory work on L2-resident "
+                    "rows); instruction count from the committed ncu summary of this source and workload, time "
+                    "measured live"}
 
 
 def parse_clock_samples(lines, t_start, t_end):
@@ -603,7 +629,8 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "evals": int(tot_evals), "best_cost": int(best),
             "gpu_launches": int((info["kernels_per_generation"] + info["kernels_per_step_call"]) * args.steps),
-            "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
+            "roofline": roofline, "roofline_issue": issue_roofline(args.workload, eval_ms),
+            "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -697,6 +724,7 @@ def run_eval_mode(args):
                          "kernel": "k_scan_columns" if scan_ms is not None else "row kernel + reduction",
                          "launch_ms": kernel_ms, "pass_ms": mean_ms,
                          "alg_bytes_per_launch": alg_bytes, "peak_source": f"{peak_kind} burst copy bandwidth"},
+            "roofline_issue": issue_roofline(args.workload, kernel_ms),
             "gpu_launches": 2 * args.steps, "tables": tables, "clocks": clk}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_eval_baseline(d, p, masks)
@@ -799,7 +827,7 @@ def run_batched(args):
                        "l2": "flushed between timed steps"},
             "evals": int(e1 - e0),
             "gpu_launches": int((info["kernels_per_generation"] + info["kernels_per_step_call"]) * args.steps),
-            "roofline": roofline, "clocks": clk}
+            "roofline": roofline, "roofline_issue": issue_roofline(args.workload, eval_ms), "clocks": clk}
     print(json.dumps(line), flush=True)
 
 

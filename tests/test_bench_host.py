@@ -47,3 +47,16 @@ def test_censored_median():
 def test_host_description_names_the_cores():
     h = bench.host_description()
     assert h["cores"] >= 1 and h["machine"]
+
+
+def test_issue_roofline_from_the_committed_profiles():
+    """The instruction-issue peak is the unit count times the clock; the profiles' instruction counts give a fraction
+    below 1 at the measured launch times (skipped when the profiles predate the kernel source)."""
+    import pytest
+
+    assert bench.ISSUE_PEAK == 152 * 4 * 2.07e9
+    r = bench.issue_roofline("euclid10000_p100", 1.142)
+    if r is None:
+        pytest.skip("profiles were taken on another kernel source")
+    assert 0.3 < r["frac"] < 1.0 and r["bound"] == "issue"
+    assert bench.issue_roofline("no_such_workload", 1.0) is None
