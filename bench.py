@@ -494,17 +494,17 @@ def run_ours(args):
     import torch
 
     rank, world, local = dist_env()
+    torch.cuda.set_device(local)  # before the process group, so that NCCL binds each rank to its own GPU
     if world > 1:
         import torch.distributed as dist
 
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local)
     from paper_1610_10061_gb300 import build
 
     if rank == 0:
         build.build()
     if world > 1:
-        torch.distributed.barrier()
+        torch.distributed.barrier(device_ids=[local])
     from paper_1610_10061_gb300 import pm
     from paper_1610_10061_gb300.inputs import random_masks
 
@@ -528,7 +528,7 @@ def run_ours(args):
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     if world > 1:
-        torch.distributed.barrier()
+        torch.distributed.barrier(device_ids=[local])
     torch.cuda.synchronize()
     clocks.start()
     torch.cuda.nvtx.range_push("timed")
@@ -540,7 +540,7 @@ def run_ours(args):
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     if world > 1:
-        torch.distributed.barrier()
+        torch.distributed.barrier(device_ids=[local])
     clk = clocks.stop()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = float(sum(step_ms))
