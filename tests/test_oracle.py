@@ -413,3 +413,28 @@ def test_cumulative_tables_are_the_sorted_distances(seed):
     sets = list(itertools.combinations(range(m), p))
     masks = masks_from_sets(sets, m)
     np.testing.assert_array_equal(oracle.eval_cumulative(pi, dcum, masks), oracle.eval_direct(d, masks))
+
+
+@pytest.mark.parametrize("name", ["graph100", "graph900"])
+def test_mean_scan_length_at_the_bench_workloads(name):
+    """The algorithmic bytes the benchmark reports use E[k] = (m+1)/(p+1) ranks per (individual, client) for uniform
+    random p-subsets (pinned at small sizes by test_mean_scan_length_closed_form).  At the benchmark's own instances
+    the oracle's exact count of visited ranks agrees within sampling error, and that count equals a brute-force
+    first-open rank."""
+    w = paper_shape_instance(name)
+    d, p = w["d"], w["p"]
+    n, m = d.shape
+    pi, de = oracle.tables(d, p)
+    pop = 512
+    masks = random_masks(pop, m, p, seed=21)
+    _, ksum = oracle.eval_scan(pi, de, masks, return_ksum=True)
+    ek = (m + 1) / (p + 1)
+    mean = ksum / (pop * n)
+    # the variance of k for one pair is below E[k]^2; pairs of one individual are correlated, so bound the error by
+    # the individuals alone (pop independent samples of a per-individual mean)
+    assert abs(mean - ek) < 4 * ek / np.sqrt(pop), (mean, ek)
+    # exact count on a few individuals by brute force
+    open_ = ((masks[:8, :, None] >> np.arange(32, dtype=np.uint32)) & 1).reshape(8, -1)[:, :m].astype(bool)
+    _, k8 = oracle.eval_scan(pi, de, masks[:8], return_ksum=True)
+    brute = sum(int(np.argmax(open_[t][pi[i].astype(np.int64)])) + 1 for t in range(8) for i in range(n))
+    assert k8 == brute
