@@ -101,12 +101,25 @@ __global__ void __launch_bounds__(kSortThreads) k_tables(const int32_t *__restri
 
     for (int64_t row = blockIdx.x; row < n; row += gridDim.x) {
         const int32_t *drow = d + row * (int64_t)m;
-        for (int i = threadIdx.x; i < m; i += blockDim.x) {
-            if constexpr (kPacked) {
-                keysA[i] = ((uint32_t)__ldg(drow + i) << 16) | (uint32_t)i;
-            } else {
-                keysA[i] = (uint32_t)__ldg(drow + i);
-                valsA[i] = (uint16_t)i;
+        // the row into shared memory, eight independent loads in flight per thread before any is used
+        for (int i0 = threadIdx.x; i0 < m; i0 += 8 * blockDim.x) {
+            uint32_t v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int i = i0 + u * (int)blockDim.x;
+                v[u] = i < m ? (uint32_t)__ldg(drow + i) : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int i = i0 + u * (int)blockDim.x;
+                if (i < m) {
+                    if constexpr (kPacked) {
+                        keysA[i] = (v[u] << 16) | (uint32_t)i;
+                    } else {
+                        keysA[i] = v[u];
+                        valsA[i] = (uint16_t)i;
+                    }
+                }
             }
         }
         __syncthreads();
