@@ -150,10 +150,16 @@ def measured_bf16_peak():
 
 
 def fitness_source_hash():
+    """Hash of the scan kernel's code (fitness.cu and pm_common.cuh without their comments and blank lines): the
+    key that ties a committed ncu summary to the code it was taken on."""
+    import re
+
     h = hashlib.sha256()
     for f in ("fitness.cu", "pm_common.cuh"):
-        with open(os.path.join(ROOT, "paper_1610_10061_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1610_10061_gb300", "csrc", f)) as fh:
+            text = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        h.update("\n".join(line.rstrip() for line in text.splitlines() if line.strip()).encode())
     return h.hexdigest()[:16]
 
 

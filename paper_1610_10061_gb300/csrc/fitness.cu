@@ -11,8 +11,11 @@
 //    tile of 32*G individuals, word (j, g) holds bit b = "individual
 //    tile*32G + 32g + b has facility j open".  One shared-memory load of the
 //    G words of facility j (128 bits for G = 4) tests 32G individuals.
-//  * A CTA owns one tile; its m x G words are brought into shared memory with
-//    TMA bulk copies (cp.async.bulk + mbarrier).  Grid.y splits the clients.
+//  * Work items are (client split, tile) pairs, split-major, walked by a
+//    persistent grid so that CTAs running at the same time stream the same
+//    rows through L2.  A CTA brings its tile's 32W x G words into shared
+//    memory with TMA bulk copies (cp.async.bulk + mbarrier, bounded wait)
+//    and keeps them while consecutive items share the tile.
 //  * A warp takes one client at a time and walks its row 32 ranks per step:
 //    lane r holds Pi'[r] and Delta'[r] (coalesced loads, the next step and
 //    the next client's first step prefetched into registers).  If no still
@@ -26,13 +29,16 @@
 //    individual's first open rank with one find-first-set.  Resolved
 //    individuals leave the active set; the walk ends when none is left.
 //  * Per-lane int64 sums are combined in shared memory.  With one client
-//    split the CTA applies the epilogue itself; otherwise every CTA adds its
-//    sums into per-individual int64 accumulators (integers, so the order of
-//    the atomic additions does not matter) and the last CTA of the tile (an
-//    atomic ticket) reads the totals, zeroes the accumulators for the next
-//    launch and applies the epilogue: a plain store of the cost, or the GA's
+//    split the CTA applies the epilogue itself.  Otherwise each split adds
+//    its sum and a count of one into a single 64-bit word per individual
+//    (sum in bits 0..47, count above); the split whose atomic completes the
+//    count holds the total, zeroes the word for the next launch and applies
+//    that individual's epilogue -- a plain store of the cost, or the GA's
 //    acceptance (replace the current individual iff the candidate is
-//    strictly cheaper).
+//    strictly cheaper).  Integer sums do not depend on the order of the
+//    additions.  Where n * max d could reach 2^47 the splits add plain int64
+//    sums and the last CTA of the tile (an atomic ticket) applies the
+//    epilogues.
 //
 // For very large m (the facility-major tile does not fit in shared memory)
 // a "row" kernel keeps each individual's own bitset in shared memory and
