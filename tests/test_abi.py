@@ -67,3 +67,40 @@ def test_invalid_arguments_rejected_before_any_device_work(lib):
     with pytest.raises(pm.PMError) as e:
         pm.pm_instance_create(big, 1, 70000, 3)
     assert e.value.status == 3
+
+
+def _header_defines():
+    out = {}
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", h)).read()
+            for name, val in re.findall(r"^#define\s+(PM_[A-Z_]+)\s+(\d+)u?\s*$", text, flags=re.M):
+                out[name] = int(val)
+    return out
+
+
+def test_binding_flags_match_the_header():
+    from paper_1610_10061_gb300 import pm
+
+    defs = _header_defines()
+    for name in ("PM_GA_TUNE", "PM_GA_MIGRATE_TEAM", "PM_GA_INIT_COMBINADIC", "PM_TABLES_CUMULATIVE"):
+        assert getattr(pm, name) == defs[name], name
+
+
+def test_ga_params_marshalling():
+    """The binding's GA parameters land in the C struct as the header describes (no GPU needed)."""
+    from paper_1610_10061_gb300 import pm
+
+    q = pm._params(deme=64, xover_rounds=20, mut_tries=60, saturation=7, stream_id=3, tune=True,
+                   migration="team", init="combinadic", candidates=5)
+    assert (q.deme, q.xover_rounds, q.mut_tries, q.saturation, q.stream_id, q.candidates) == (64, 20, 60, 7, 3, 5)
+    assert q.flags == pm.PM_GA_TUNE | pm.PM_GA_MIGRATE_TEAM | pm.PM_GA_INIT_COMBINADIC
+    assert not q.model
+    d = pm._params()
+    assert (d.deme, d.xover_rounds, d.mut_tries, d.flags) == (0, -1, -1, 0)  # library defaults: lg D tries
+    with pytest.raises(ValueError):
+        pm._params(migration="ring")
+    with pytest.raises(ValueError):
+        pm._params(init="lhs")
+    # status codes name themselves
+    assert "PM_ERR_OOM" in pm.pm_strerror(6) and "PM_ERR_TIMEOUT" in pm.pm_strerror(7)
