@@ -138,7 +138,12 @@ PM_API pm_status pm_instance_tables(const pm_instance *inst, uint16_t *pi_out, i
  *           bitset with fewer than p open facilities may yield a meaningless
  *           cost for that individual (never a fault).
  * Asynchronous when masks and costs are device memory and checked == 0.
- * Errors: PM_ERR_INVALID_ARG, PM_ERR_MASK, PM_ERR_OOM, PM_ERR_CUDA.
+ * Errors: PM_ERR_INVALID_ARG, PM_ERR_MASK, PM_ERR_OOM, PM_ERR_CUDA, and
+ * PM_ERR_TIMEOUT when a bounded device-side wait of the scan gave up (the
+ * costs are then unreliable).  A synchronous call (host costs, or checked)
+ * reports it directly; an asynchronous one leaves it for pm_eval_status.
+ * After reporting it the instance's scratch is reset, so later evaluations
+ * are correct again.
  */
 PM_API pm_status pm_eval_population(pm_instance *inst, const uint32_t *masks, int64_t pop, int64_t *costs, int checked,
                              void *stream);
@@ -167,10 +172,26 @@ PM_API pm_status pm_eval_population(pm_instance *inst, const uint32_t *masks, in
  * calls share the one array and each call overwrites it, so calls whose work
  * overlaps on the GPU (different streams, or different instances at the same
  * time) race and must be serialised by the caller.  Asynchronous on
- * `stream`.  Errors: PM_ERR_INVALID_ARG, PM_ERR_CUDA.
+ * `stream`.  Errors: PM_ERR_INVALID_ARG, PM_ERR_CUDA.  A device-side failure
+ * (PM_ERR_TIMEOUT: a bounded wait of the scan gave up, the costs of that
+ * call are unreliable) cannot be returned by this asynchronous call: the
+ * array keeps it in an error word until pm_eval_status, which reads it
+ * (synchronising) and clears it.
  */
 PM_API pm_status pm_eval_population_noalloc(pm_instance *inst, const uint32_t *masks, int64_t pop, int64_t *costs,
                                             void *stream);
+
+/*
+ * pm_eval_status -- synchronise `stream` and report a device-side failure of
+ * the asynchronous evaluations on inst since the last report: PM_ERR_TIMEOUT
+ * when a bounded wait of the scan gave up in pm_eval_population,
+ * pm_eval_columns or pm_eval_population_noalloc (whose fixed array belongs to
+ * inst's device, so a failure there is reported for any instance on that
+ * device), else PM_OK.  Reading clears the record and resets the scratch the
+ * failed launch left behind.  No counterpart in the paper.  Errors:
+ * PM_ERR_INVALID_ARG, PM_ERR_CUDA.
+ */
+PM_API pm_status pm_eval_status(pm_instance *inst, void *stream);
 
 /*
  * The two launches of a column-kernel evaluation as separate calls (no
@@ -261,6 +282,20 @@ PM_API pm_status pm_selftest_bounded_wait(int device, void *stream);
  * Process-wide; not meant for concurrent use.  Always PM_OK.
  */
 PM_API pm_status pm_debug_fail_alloc(int64_t after, int64_t *pending);
+
+/*
+ * pm_debug_scan_timeout -- failure injection for tests (no counterpart in the
+ * paper).  In the next `launches` launches of the column scan (by any call)
+ * the odd-numbered CTAs issue no tile copy, so their bounded wait for the
+ * tile runs out after a few thousand polls with nothing in flight; each of
+ * them records PM_ERR_TIMEOUT in the launch's error word and returns, while
+ * the even-numbered CTAs finish their work items and leave their split sums
+ * behind, as a real timeout would.  No fault, trap or hang: this is the
+ * exit every wait in the library takes.  launches <= 0 disarms it (the
+ * default).  pending (host, nullable) receives the launches still armed until
+ * now.  Process-wide; not meant for concurrent use.  Always PM_OK.
+ */
+PM_API pm_status pm_debug_scan_timeout(int64_t launches, int64_t *pending);
 
 /* ------------------------------------------------------------------------
  * The genetic algorithm (Sections 3.1, 3.2.2, 4.3-4.5) on the device.

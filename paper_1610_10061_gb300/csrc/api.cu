@@ -384,8 +384,21 @@ extern "C" pm_status pm_eval_population(pm_instance *inst, const uint32_t *masks
         int err = 0;
         PM_CUDA(cudaMemcpyAsync(&err, inst->err.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
         PM_CUDA(cudaStreamSynchronize(s));
-        if (err)
+        if (err) {
+            PM_TRY(pm_reset_eval_scratch(inst, s));
             return (pm_status)err;
+        }
     }
+    return PM_OK;
+}
+
+pm_status pm_reset_eval_scratch(pm_instance *inst, cudaStream_t s)
+{
+    // a CTA that gave up left its split's sums (and maybe a tile ticket) behind
+    pm_dbuf *bufs[] = {&inst->err, &inst->partials, &inst->tickets};
+    for (pm_dbuf *b : bufs)
+        if (b->ptr)
+            PM_CUDA(cudaMemsetAsync(b->ptr, 0, b->bytes, s));
+    PM_CUDA(cudaStreamSynchronize(s));
     return PM_OK;
 }

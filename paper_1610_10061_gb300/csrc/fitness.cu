@@ -45,6 +45,7 @@
 // resolves one individual per warp step with a ballot; a separate kernel
 // adds its splits.
 
+#include <atomic>
 #include <cstdio>
 
 #include "pm_common.cuh"
@@ -53,6 +54,7 @@ namespace {
 
 constexpr int kMaxG = 4;
 constexpr uint32_t kSpinLimit = 1u << 22;  // bounded mbarrier wait (a few seconds at most)
+constexpr uint32_t kStallSpinLimit = 1u << 14;  // the poll limit of a launch armed by pm_debug_scan_timeout
 constexpr int kSparseLanes = 3;            // resolve by walking hit lanes up to this many
 constexpr int kCountShift = 48;            // packed split reduction: count in bits 48..63, sum below
 
@@ -321,7 +323,7 @@ __global__ void __launch_bounds__(1024) k_scan_columns(const pm_prob *__restrict
                                                        const uint32_t *__restrict__ active,
                                                        unsigned long long *__restrict__ accum,
                                                        int *__restrict__ tickets, int *__restrict__ err,
-                                                       ScanEpilogue ep)
+                                                       ScanEpilogue ep, uint32_t stall)
 {
     // the previous kernel of the stream may still run until pm_grid_dependency_wait(): before it only the
     // constant tables (Pi', Delta', the launch's problem table) are read
@@ -335,6 +337,9 @@ __global__ void __launch_bounds__(1024) k_scan_columns(const pm_prob *__restrict
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
+    // a launch armed by pm_debug_scan_timeout stalls its odd-numbered CTAs; the even ones finish their items, so
+    // the stalled launch leaves partial sums (and tile tickets) behind, as a real timeout would
+    const bool stalled = stall != 0u && (blockIdx.x & 1u) != 0u;
 
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
@@ -386,7 +391,9 @@ __global__ void __launch_bounds__(1024) k_scan_columns(const pm_prob *__restrict
             waited = true;
         }
 
-        if (reload && threadIdx.x == 0) {
+        // stalled (failure-detection tests only): no copy is issued and nothing arrives on the barrier, so the
+        // bounded wait below runs out with nothing in flight
+        if (reload && threadIdx.x == 0 && !stalled) {
             const uint32_t tile_bytes = (uint32_t)W * 32u * G * 4u;
             mbar_arrive_expect_tx(&bar, tile_bytes);
             const char *src = reinterpret_cast<const char *>(colT + pr.col_base + tile * (int64_t)W * 32 * G);
@@ -409,13 +416,14 @@ __global__ void __launch_bounds__(1024) k_scan_columns(const pm_prob *__restrict
 
         if (reload) {
             // bounded wait for the tile (every thread waits)
+            const uint32_t limit = stalled ? kStallSpinLimit : kSpinLimit;
             uint32_t spins = 0;
             while (!mbar_try_wait(&bar, phase)) {
-                if (++spins > kSpinLimit) {
+                if (++spins > limit) {
                     if (threadIdx.x == 0)
                         atomicExch(err, (int)PM_ERR_TIMEOUT);
                     uint32_t extra = 0;  // the copy may still land: wait once more, bounded, then leave
-                    while (!mbar_try_wait(&bar, phase) && ++extra < kSpinLimit) {
+                    while (!mbar_try_wait(&bar, phase) && ++extra < limit) {
                     }
                     return;
                 }
@@ -763,6 +771,27 @@ pm_prob pm_single_prob(const pm_instance *inst, const pm_eval_plan &plan, int64_
     return pr;  // every base 0
 }
 
+// Scan launches still to be armed by pm_debug_scan_timeout.
+static std::atomic<long long> g_scan_stall{0};
+
+static bool take_stall()
+{
+    long long k = g_scan_stall.load();
+    while (k > 0) {
+        if (g_scan_stall.compare_exchange_weak(k, k - 1))
+            return true;
+    }
+    return false;
+}
+
+extern "C" pm_status pm_debug_scan_timeout(int64_t launches, int64_t *pending)
+{
+    const long long prev = g_scan_stall.exchange(launches > 0 ? (long long)launches : 0);
+    if (pending)
+        *pending = (int64_t)prev;
+    return PM_OK;
+}
+
 // Enqueue the transpose (unless the caller wrote the columns) and the column
 // scan of a launch; smem = the tile bytes of the launch's widest instance.
 static pm_status launch_transpose(const uint32_t *masks, const pm_prob *probs, int K, const pm_prob &one, int64_t jobs,
@@ -803,7 +832,8 @@ pm_status pm_launch_scan(const pm_scan_launch &L, const pm_accept_args &acc, int
     const int threads = L.warps * 32;
     const unsigned grid = (unsigned)L.grid;
     unsigned long long *accum = reinterpret_cast<unsigned long long *>(L.accum);
-#define PM_SCAN_ARGS L.probs_dev, L.K, L.one, L.items, L.colT, L.active, accum, L.tickets, L.err, ep
+    const uint32_t stall = take_stall() ? 1u : 0u;
+#define PM_SCAN_ARGS L.probs_dev, L.K, L.one, L.items, L.colT, L.active, accum, L.tickets, L.err, ep, stall
     switch (G) {
     case 1:
         PM_CUDA(pm_launch(k_scan_columns<1>, grid, threads, smem, stream, PM_SCAN_ARGS));
@@ -932,12 +962,41 @@ extern "C" pm_status pm_eval_population_noalloc(pm_instance *inst, const uint32_
     int *tickets = reinterpret_cast<int *>(base + 256);
     uint32_t *colT = reinterpret_cast<uint32_t *>(base + 256 + tick);
     int64_t *partials = reinterpret_cast<int64_t *>(base + 256 + tick + cols);
-    // the array keeps the previous call's contents: the error word, the tile
-    // tickets and the accumulators must start at zero
-    PM_CUDA(cudaMemsetAsync(base, 0, 256 + tick, s));
+    // the array keeps the previous call's contents: the tile tickets and the
+    // accumulators must start at zero.  The error word is not cleared here: it
+    // keeps the first failure until pm_eval_status reads and clears it (it is
+    // zero when the library is loaded).
+    PM_CUDA(cudaMemsetAsync(base + 256, 0, tick, s));
     PM_CUDA(cudaMemsetAsync(partials, 0, part, s));
     pm_accept_args acc;
     return pm_launch_eval(inst, plan, masks, pop, nullptr, costs, partials, tickets, colT, err, acc, s);
+}
+
+extern "C" pm_status pm_eval_status(pm_instance *inst, void *stream)
+{
+    if (!inst)
+        return PM_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> guard(inst->lock);
+    PM_CUDA(cudaSetDevice(inst->device));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned char *na = nullptr;
+    {
+        std::lock_guard<std::mutex> g(g_noalloc_mu);
+        if (inst->device < kNoAllocMaxDevices)
+            na = static_cast<unsigned char *>(g_noalloc_addr[inst->device]);
+    }
+    int words[2] = {0, 0};
+    PM_CUDA(cudaMemcpyAsync(&words[0], inst->err.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (na)
+        PM_CUDA(cudaMemcpyAsync(&words[1], na, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PM_CUDA(cudaStreamSynchronize(s));
+    if (words[0])
+        PM_TRY(pm_reset_eval_scratch(inst, s));
+    if (words[1]) {
+        PM_CUDA(cudaMemsetAsync(na, 0, 256, s));
+        PM_CUDA(cudaStreamSynchronize(s));
+    }
+    return (pm_status)(words[0] ? words[0] : words[1]);
 }
 
 extern "C" pm_status pm_selftest_bounded_wait(int device, void *stream)

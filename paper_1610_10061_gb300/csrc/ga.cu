@@ -812,7 +812,9 @@ __device__ __forceinline__ uint32_t range_mask(int64_t lo, int64_t hi)  // bits 
 
 // Try q's mutant F of the W-word row C (m bits) of individual t, built by a
 // warp (lanes over words): circular or block shift with the draws of
-// operation OP_MUT + q (reading R9).  F[a+i] = C[a + (i+kl) mod len].
+// operation OP_MUT + q -- kind and direction from draws 0 and 1, the
+// circular amount or the block's two ends from draws 2 and 3, the block's
+// amount from draw 4.  F[a+i] = C[a + (i+kl) mod len].
 __device__ __forceinline__ void mutant_row(const uint32_t *__restrict__ C, uint32_t *__restrict__ F, int32_t W,
                                            int32_t m, uint64_t seed, uint32_t gen, uint32_t t, uint32_t q,
                                            uint32_t sid, int lane)
@@ -1814,12 +1816,21 @@ extern "C" pm_status pm_batch_ga_create(pm_batch *b, uint64_t seed, int64_t pop,
     return PM_OK;
 }
 
+// Report (and clear) a device-side failure recorded since the last check.  A scan CTA that gave up left its
+// split's sums and tile tickets behind: they are zeroed so that later generations evaluate correctly.
 static pm_status check_err(pm_ga *ga, cudaStream_t s)
 {
     int e = 0;
     PM_CUDA(cudaMemcpyAsync(&e, ga->err.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
     PM_CUDA(cudaStreamSynchronize(s));
-    return e ? (pm_status)e : PM_OK;
+    if (!e)
+        return PM_OK;
+    pm_dbuf *bufs[] = {&ga->err, &ga->accum, &ga->tickets, &ga->accumQ, &ga->ticketsQ};
+    for (pm_dbuf *b : bufs)
+        if (b->ptr)
+            PM_CUDA(cudaMemsetAsync(b->ptr, 0, b->bytes, s));
+    PM_CUDA(cudaStreamSynchronize(s));
+    return (pm_status)e;
 }
 
 extern "C" pm_status pm_ga_step(pm_ga *ga, int64_t gens, int64_t *trace, void *stream)

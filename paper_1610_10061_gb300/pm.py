@@ -71,6 +71,8 @@ _SIGS = {
     "pm_eval_population_noalloc": ([_P, _P, _I64, _P, _P], _S),
     "pm_selftest_bounded_wait": ([ctypes.c_int, _P], _S),
     "pm_debug_fail_alloc": ([_I64, _P], _S),
+    "pm_debug_scan_timeout": ([_I64, _P], _S),
+    "pm_eval_status": ([_P, _P], _S),
     "pm_columns_layout": ([_P, _I64, _P, _P], _S),
     "pm_population_columns": ([_P, _P, _I64, _P, _P], _S),
     "pm_eval_columns": ([_P, _P, _I64, _P, _P], _S),
@@ -211,6 +213,20 @@ def pm_debug_fail_alloc(after: int) -> int:
     pending = ctypes.c_int64(-1)
     _check(_lib.pm_debug_fail_alloc(int(after), ctypes.byref(pending)), "pm_debug_fail_alloc")
     return int(pending.value)
+
+
+def pm_debug_scan_timeout(launches: int) -> int:
+    """Arm the next `launches` column-scan launches to skip their tile copy, so that their bounded wait runs out
+    (PM_ERR_TIMEOUT, no fault).  Returns the launches that were still armed."""
+    pending = ctypes.c_int64(0)
+    _check(_lib.pm_debug_scan_timeout(int(launches), ctypes.byref(pending)), "pm_debug_scan_timeout")
+    return int(pending.value)
+
+
+def pm_eval_status(inst, stream=None) -> int:
+    """Status of the asynchronous evaluations on inst since the last report (0 or PM_ERR_TIMEOUT = 7); clears
+    the record."""
+    return int(_lib.pm_eval_status(inst, _stream(stream)))
 
 
 def pm_columns_layout(inst, pop: int):

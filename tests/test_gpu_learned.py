@@ -151,6 +151,25 @@ def test_mlp_forward_and_gradients(pm, rows):
         _scale_close(G[name], gref[name])
 
 
+def test_mlp_forward_every_cta_walks_several_tiles(pm):
+    """The tensor-core forward is persistent: min(tiles, 3 x SMs) CTAs walk 128-row tiles, prefetching the next
+    tile's inputs, flipping the MMA barrier's phase and reusing TMEM from tile to tile.  Five tiles per CTA plus a
+    ragged last tile (77 rows), every row against the oracle."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    rows = 5 * 3 * sms * 128 + 77
+    model = pm.Model(seed=3)
+    params = mlp.init_params(seed=5)
+    for k in ("b1", "b2", "b3"):
+        params[k] = np.random.default_rng(6).normal(0, 0.1, size=params[k].shape)
+    model.set_params(mlp.flatten(params).astype(np.float32))
+    p32 = mlp.unflatten(model.params().astype(np.float64))
+    X, _ = _random_batch(rows, 7)
+    xd = torch.from_numpy(X.astype(np.float32)).to(torch.bfloat16).cuda()
+    y = model.forward(xd).cpu().numpy()
+    yref, _ = mlp.forward(p32, X, bf16=True)
+    _scale_close(y, yref)
+
+
 def test_adam_step_matches_oracle(pm):
     model = pm.Model(seed=2)
     X, t = _random_batch(512, 9)
