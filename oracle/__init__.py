@@ -67,6 +67,7 @@ def _load():
     lib.oracle_tables.argtypes = [P, I64, I64, I64, P, P]
     lib.oracle_eval_direct.argtypes = [P, I64, I64, P, I64, I64, P]
     lib.oracle_eval_scan.argtypes = [P, P, I64, I64, P, I64, I64, P, P]
+    lib.oracle_brute_force.argtypes = [P, I64, I64, I64, I64, I64, P, P]
     lib.oracle_philox4x32_10.argtypes = [P, P, P]
     lib.oracle_philox4x32_10.restype = None
     lib.oracle_draw.argtypes = [U64, U32, U32, U32, U32, U32]
@@ -217,6 +218,29 @@ def brute_force(d: np.ndarray, p: int):
         if best is None or c[k] < best[0]:
             best = (int(c[k]), part[k])
     return best
+
+
+def brute_force_c(d: np.ndarray, p: int, threads: int | None = None):
+    """Minimum of the objective over all C(m, p) open sets by the C enumeration (oracle_brute_force): one task per
+    smallest facility a (the subsets whose smallest element is a), run on host threads; the smallest (cost,
+    subset) wins, so ties go to the lexicographically first subset.  Returns (cost, sorted facility tuple)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    lib = _load()
+    d = np.ascontiguousarray(d, dtype=np.int32)
+    n, m = d.shape
+    if threads is None:
+        threads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+
+    def one(a):
+        cost = np.zeros(1, dtype=np.int64)
+        best = np.zeros(p, dtype=np.int32)
+        _check(lib.oracle_brute_force(_ptr(d), n, m, p, a, a + 1, _ptr(cost), _ptr(best)), "brute_force")
+        return int(cost[0]), tuple(int(j) for j in best)
+
+    with ThreadPoolExecutor(max(1, threads)) as ex:
+        results = list(ex.map(one, range(m - p + 1)))
+    return min(results)
 
 
 # --------------------------------------------------------------------------

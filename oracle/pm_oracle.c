@@ -21,6 +21,8 @@
  *                        clients of the nearest open facility).  O1.
  *   oracle_eval_scan     Section 4.2, the Fitness function (scan Delta' in
  *                        Pi' order up to the first open facility).  O3.
+ *   oracle_brute_force   Section 1, Eqs. 1-3 minimised over every p-subset
+ *                        (lexicographic enumeration, O1's cost per subset).
  *   oracle_philox4x32_10 Philox4x32-10 from its published definition
  *                        (Salmon, Moraes, Dror, Shaw, SC'11); stands in for
  *                        the paper's cuRAND generator (Section 3.2.1).
@@ -140,6 +142,56 @@ int oracle_eval_direct(const int32_t *d, int64_t n, int64_t m, const uint32_t *m
         }
         costs[t] = total;
     }
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Brute force.  Section 1, Eqs. 1-3 minimised by enumeration: every         */
+/* p-subset whose smallest facility lies in [lo, hi), visited in             */
+/* lexicographic order, costed by O1's definition (each client's nearest     */
+/* facility of the subset, summed).  Ties keep the lexicographically first   */
+/* subset.  best_set receives the p facility ids of the best subset in       */
+/* ascending order.  Splitting [0, m - p + 1) into ranges lets callers run   */
+/* ranges on several host threads and keep the smallest (cost, subset).      */
+/* ------------------------------------------------------------------------ */
+
+int oracle_brute_force(const int32_t *d, int64_t n, int64_t m, int64_t p, int64_t lo, int64_t hi, int64_t *best_cost,
+                       int32_t *best_set)
+{
+    if (n < 1 || p < 1 || p > m || lo < 0 || hi > m - p + 1 || lo >= hi)
+        return OR_ERR_ARG;
+    int64_t *s = (int64_t *)malloc((size_t)p * sizeof(int64_t));
+    if (!s)
+        return OR_ERR_OOM;
+    for (int64_t k = 0; k < p; ++k)
+        s[k] = lo + k;  /* the first subset whose smallest facility is lo */
+    *best_cost = -1;
+    while (s[0] < hi) {
+        int64_t total = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            int32_t nearest = d[i * m + s[0]];
+            for (int64_t k = 1; k < p; ++k)
+                if (d[i * m + s[k]] < nearest)
+                    nearest = d[i * m + s[k]];
+            total += nearest;
+        }
+        if (*best_cost < 0 || total < *best_cost) {
+            *best_cost = total;
+            for (int64_t k = 0; k < p; ++k)
+                best_set[k] = (int32_t)s[k];
+        }
+        /* the next subset in lexicographic order: raise the last element that can still rise, then make the
+           elements after it consecutive */
+        int64_t k = p - 1;
+        while (k >= 0 && s[k] == m - p + k)
+            --k;
+        if (k < 0)
+            break;
+        s[k] += 1;
+        for (int64_t q = k + 1; q < p; ++q)
+            s[q] = s[q - 1] + 1;
+    }
+    free(s);
     return OR_OK;
 }
 

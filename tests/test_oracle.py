@@ -178,6 +178,37 @@ def test_brute_force_sub20_and_oracle_ga_finds_it():
     assert trace[-1] == best
 
 
+def test_brute_force_enumeration_in_c_matches_the_python_one(example1):
+    """oracle_brute_force (lexicographic enumeration in C, split by smallest facility over host threads) against
+    the itertools enumeration costed by O1: the printed Example 1 (optimum {1, 4} = 35, 1-based), the derived
+    20-node sub-instance and small random instances with many ties."""
+    C = _arr(example1["C"], np.int32)
+    assert oracle.brute_force_c(C, 2) == (35, (0, 3))
+    w = paper_shape_instance("graph100_sub20")
+    assert oracle.brute_force_c(w["d"], w["p"]) == oracle.brute_force(w["d"], w["p"])
+    rng = np.random.default_rng(5)
+    for m, p, hi in [(12, 3, 4), (15, 1, 50), (14, 13, 9), (11, 5, 3)]:
+        d = rng.integers(0, hi, size=(9, m)).astype(np.int32)
+        assert oracle.brute_force_c(d, p, threads=3) == oracle.brute_force(d, p)
+
+
+def test_graph100_optimum_golden():
+    """The stored optimum of the 100-node graph instance (tests/golden/graph100_optimum.txt, written by the
+    oracle's brute force over all C(100, 5) open sets): its cost is O1 of its open set, and no single swap (close
+    one open facility, open one closed facility) is cheaper.  The full enumeration is re-run below."""
+    from conftest import load_golden
+
+    g = load_golden("graph100_optimum.txt")
+    cost, best = g["cost"][0][0], tuple(g["open"][0])
+    w = paper_shape_instance("graph100")
+    d, p = w["d"], w["p"]
+    assert len(best) == p == 5 and list(best) == sorted(set(best))
+    assert oracle.eval_direct(d, masks_from_sets([best], 100))[0] == cost
+    swaps = [tuple(sorted((set(best) - {j}) | {k})) for j in best for k in range(100) if k not in best]
+    assert (oracle.eval_direct(d, masks_from_sets(swaps, 100)) >= cost).all()
+    assert oracle.brute_force_c(d, p) == (cost, best)
+
+
 # --------------------------------------------------------------------------
 # Philox4x32-10 and the draw mapping
 # --------------------------------------------------------------------------
