@@ -478,6 +478,27 @@ PM_API pm_status pm_model_train_step(pm_model *model, const uint16_t *x, const f
                                      float *loss, void *stream);
 
 /*
+ * pm_model_train -- `epochs` passes of Adam (as pm_model_train_step) over the
+ * rows (x: rows x 16 BF16 bit patterns, t: rows FP32 targets; device memory)
+ * in mini-batches of `batch` rows (the last one of an epoch may be shorter),
+ * the order drawn afresh each epoch on the device: position i of epoch e
+ * holds row pi_e(i), pi_e a keyed permutation of [0, rows) -- a four-round
+ * Feistel network on the smallest even number of bits b with 2^b >= rows
+ * (halves of b/2 bits; round r maps (L, R) to (R, L ^ (f(R ^ K_r) mod
+ * 2^(b/2))), f = MurmurHash3's 32-bit finaliser; the result is (L << b/2) | R),
+ * applied again while the result is >= rows; the round keys K_0..K_3 are the
+ * words of Philox4x32-10(counter (e, 0, 0x300 * 2^16, 0), key (seed lo, seed
+ * hi)).  The training kernel reads its rows through the permutation (no copy
+ * of the data).  losses (nullable; host or device): one FP32 per step, the
+ * batch's mean squared error before its update, epochs * ceil(rows / batch)
+ * entries; a host array synchronises `stream`, else the call is
+ * asynchronous.  No counterpart in the paper.  Errors: PM_ERR_INVALID_ARG
+ * (rows >= 2^31, host x or t, batch < 1, lr <= 0), PM_ERR_OOM, PM_ERR_CUDA.
+ */
+PM_API pm_status pm_model_train(pm_model *model, const uint16_t *x, const float *t, int64_t rows, int32_t epochs,
+                                int64_t batch, float lr, uint64_t seed, float *losses, void *stream);
+
+/*
  * pm_swap_stats -- per individual and facility (pop x m arrays, device):
  * gain[k] = the cost saved by opening closed facility k alone, cap[k] = the
  * clients it would take, loss[j] = the cost added by closing open facility j

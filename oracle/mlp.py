@@ -133,6 +133,76 @@ def adam_step(params, grads, state, lr):
     return params
 
 
+# --------------------------------------------------------------------------
+# Training: the epoch shuffle and the loop (the library's pm_model_train)
+# --------------------------------------------------------------------------
+
+OP_SHUFFLE = 0x300
+
+
+def fmix32(h: int) -> int:
+    """MurmurHash3's 32-bit finaliser (Appleby): xor-shift 16, multiply 0x85ebca6b, xor-shift 13, multiply
+    0xc2b2ae35, xor-shift 16, all mod 2^32."""
+    h &= 0xFFFFFFFF
+    h ^= h >> 16
+    h = (h * 0x85EBCA6B) & 0xFFFFFFFF
+    h ^= h >> 13
+    h = (h * 0xC2B2AE35) & 0xFFFFFFFF
+    h ^= h >> 16
+    return h
+
+
+def shuffle_keys(seed: int, epoch: int):
+    """The four Feistel round keys of an epoch: the words of Philox4x32-10 at counter (epoch, 0, 0x300 * 2^16, 0)
+    with key (seed lo, seed hi)."""
+    from oracle import philox4x32_10
+
+    return [int(v) for v in philox4x32_10([epoch, 0, OP_SHUFFLE << 16, 0],
+                                          [seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF])]
+
+
+def shuffle_order(rows: int, seed: int, epoch: int):
+    """Row held by each position of the epoch: a four-round Feistel network on the smallest even number of bits
+    b >= 2 with 2^b >= rows (round r: (L, R) -> (R, L ^ (fmix32(R ^ K_r) mod 2^(b/2)))), re-applied while the
+    result is >= rows (cycle walking)."""
+    keys = shuffle_keys(seed, epoch)
+    bits = 2
+    while (1 << bits) < rows:
+        bits += 2
+    half = bits // 2
+    mask = (1 << half) - 1
+
+    def once(x):
+        L, R = x >> half, x & mask
+        for r in range(4):
+            L, R = R, L ^ (fmix32(R ^ keys[r]) & mask)
+        return (L << half) | R
+
+    out = []
+    for i in range(rows):
+        x = once(i)
+        while x >= rows:
+            x = once(x)
+        out.append(x)
+    return np.array(out, dtype=np.int64)
+
+
+def train(params, X, t, epochs: int, batch: int, lr: float, seed: int, state=None):
+    """Adam over `epochs` passes of (X, t) in mini-batches of `batch` rows taken in the order of shuffle_order;
+    returns (params, state, the mean squared error of every batch before its update)."""
+    state = adam_init(params) if state is None else state
+    rows = X.shape[0]
+    losses = []
+    for e in range(epochs):
+        order = shuffle_order(rows, seed, e)
+        for b0 in range(0, rows, batch):
+            idx = order[b0:b0 + batch]
+            loss, g = loss_and_grads(params, X[idx], np.asarray(t)[idx], bf16=True)
+            losses.append(loss)
+            adam_step(params, g, state, lr)
+    return params, state, losses
+
+
 def flatten(params):
     """Parameters in the library's flat order: W1 (16x128), b1, W2 (128x128), b2, w3, b3."""
     return np.concatenate([params["W1"].ravel(), params["b1"], params["W2"].ravel(), params["b2"], params["w3"],

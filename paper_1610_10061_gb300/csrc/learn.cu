@@ -93,6 +93,7 @@ struct MlpSmem {
     __nv_bfloat16 H1[kRows * kLdH];    // [r][unit]
     float b1[kHid], b2[kHid], w3[kHid];
     float y[kRows];
+    long long src[kRows];              // source row of each of the CTA's rows (its position through the shuffle)
 };
 
 struct MlpTrainSmem {
@@ -358,6 +359,49 @@ __global__ void __launch_bounds__(kTcThreads) k_mlp_fwd_tc(const __nv_bfloat16 *
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
 
+// Epoch shuffle of the training rows: position i of an epoch holds row
+// pi(i), pi a keyed permutation of [0, total): a four-round Feistel network on
+// the `2 half` low bits (the smallest even bit count covering total), whose
+// round function is MurmurHash3's 32-bit finaliser of (right half ^ round
+// key), applied again while the result is >= total (cycle walking: the cycle
+// through i returns below total, at the latest at i itself).  half == 0: the
+// identity (position i holds row i).
+struct RowMap {
+    uint32_t key[4];
+    int32_t half;
+    int64_t total;
+    int64_t pos0;  // position of the launch's first row
+};
+
+__device__ __forceinline__ uint32_t fmix32(uint32_t h)
+{
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+
+__device__ __forceinline__ int64_t shuffled_row(const RowMap &mp, int64_t i)
+{
+    if (mp.half == 0)
+        return i;
+    const uint32_t mask = (1u << mp.half) - 1u;
+    uint32_t x = (uint32_t)i;
+    do {
+        uint32_t L = x >> mp.half, R = x & mask;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const uint32_t nl = R;
+            R = L ^ (fmix32(R ^ mp.key[r]) & mask);
+            L = nl;
+        }
+        x = (L << mp.half) | R;
+    } while ((int64_t)x >= mp.total);
+    return (int64_t)x;
+}
+
 // Forward (and in TRAIN mode, backward) for rows [row0, row0 + 64).  4 warps.
 //   X: rows x 16 bf16; Wb: bf16 copies (W1 [16][128], W2 [128][128], w3 [128]);
 //   P: fp32 masters (biases read from here); y: rows fp32 predictions.
@@ -368,7 +412,7 @@ __global__ void __launch_bounds__(128) k_mlp(const __nv_bfloat16 *__restrict__ X
                                              const __nv_bfloat16 *__restrict__ W2b,
                                              const __nv_bfloat16 *__restrict__ w3b, const float *__restrict__ P,
                                              float *__restrict__ y_out, const float *__restrict__ t, float inv_batch,
-                                             float *__restrict__ grads, float *__restrict__ loss)
+                                             float *__restrict__ grads, float *__restrict__ loss, RowMap map)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     MlpSmem &S = *reinterpret_cast<MlpSmem *>(smem_raw);
@@ -393,9 +437,12 @@ __global__ void __launch_bounds__(128) k_mlp(const __nv_bfloat16 *__restrict__ X
         S.b2[i] = P[kOffB2 + i];
         S.w3[i] = __bfloat162float(w3b[i]);
     }
+    for (int r = tid; r < kRows; r += blockDim.x)
+        S.src[r] = (row0 + r < rows) ? (long long)shuffled_row(map, map.pos0 + row0 + r) : -1ll;
+    __syncthreads();
     for (int i = tid; i < kRows * kIn; i += blockDim.x) {
         const int r = i / kIn, f = i % kIn;
-        const __nv_bfloat16 v = (row0 + r < rows) ? X[(row0 + r) * kIn + f] : __float2bfloat16(0.0f);
+        const __nv_bfloat16 v = (row0 + r < rows) ? X[S.src[r] * kIn + f] : __float2bfloat16(0.0f);
         S.X[r * kLdX + f] = v;
         if (TRAIN)
             T.XT[f * kLdR + r] = v;
@@ -487,7 +534,7 @@ __global__ void __launch_bounds__(128) k_mlp(const __nv_bfloat16 *__restrict__ X
         const int r = tid;
         float dy = 0.f, sq = 0.f;
         if (row0 + r < rows) {
-            const float e = S.y[r] - t[row0 + r];
+            const float e = S.y[r] - t[S.src[r]];
             dy = 2.f * e * inv_batch;
             sq = e * e;
         }
@@ -631,15 +678,23 @@ __global__ void __launch_bounds__(128) k_mlp(const __nv_bfloat16 *__restrict__ X
 }
 
 // Adam (Kingma & Ba 2015, Algorithm 1) on the FP32 masters; refreshes the BF16 copies.
+// The gradient buffer is left zero for the next step.  loss_word (nullable): the step's sum of squares, which
+// thread 0 moves (times inv_rows) into *loss_out and clears.
 __global__ void k_adam(float *__restrict__ P, float *__restrict__ M, float *__restrict__ V,
-                       const float *__restrict__ G, int n, float lr, float bc1, float bc2,
+                       float *__restrict__ G, int n, float lr, float bc1, float bc2,
                        __nv_bfloat16 *__restrict__ W1b, __nv_bfloat16 *__restrict__ W2b,
-                       __nv_bfloat16 *__restrict__ w3b)
+                       __nv_bfloat16 *__restrict__ w3b, float *__restrict__ loss_word, float *__restrict__ loss_out,
+                       float inv_rows)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0 && loss_word != nullptr) {
+        *loss_out = *loss_word * inv_rows;
+        *loss_word = 0.f;
+    }
     if (i >= n)
         return;
     const float g = G[i];
+    G[i] = 0.f;
     const float m = 0.9f * M[i] + 0.1f * g;
     const float v = 0.999f * V[i] + 0.001f * g * g;
     M[i] = m;
@@ -1368,7 +1423,7 @@ extern "C" pm_status pm_model_get_params(pm_model *md, float *params, void *stre
 }
 
 static pm_status mlp_launch(pm_model *md, bool train, const void *x, int64_t rows, float *y, const float *t,
-                            float inv_batch, cudaStream_t s)
+                            float inv_batch, cudaStream_t s, RowMap map = RowMap{})
 {
     const unsigned grid = (unsigned)pm_ceil_div(rows, kRows);
     const __nv_bfloat16 *X = static_cast<const __nv_bfloat16 *>(x);
@@ -1379,7 +1434,7 @@ static pm_status mlp_launch(pm_model *md, bool train, const void *x, int64_t row
     if (train)
         k_mlp<true><<<grid, 128, mlp_smem(true), s>>>(X, rows, W1b, W2b, w3b, P, y, t, inv_batch,
                                                       static_cast<float *>(md->G.ptr),
-                                                      static_cast<float *>(md->loss.ptr));
+                                                      static_cast<float *>(md->loss.ptr), map);
     else
         k_mlp_fwd_tc<<<(unsigned)std::min<int64_t>(pm_ceil_div(rows, kTcRows), 3 * (int64_t)md->sm_count),
                        kTcThreads, tc_smem(), s>>>(X, rows, W1b, W2b, w3b, P, y, static_cast<int *>(md->err.ptr));
@@ -1461,11 +1516,92 @@ extern "C" pm_status pm_model_train_step(pm_model *md, const uint16_t *x, const 
     const float bc1 = 1.f - std::pow(0.9f, (float)md->step), bc2 = 1.f - std::pow(0.999f, (float)md->step);
     k_adam<<<(kParams + 255) / 256, 256, 0, s>>>(
         static_cast<float *>(md->P.ptr), static_cast<float *>(md->M.ptr), static_cast<float *>(md->V.ptr),
-        static_cast<const float *>(md->G.ptr), kParams, lr, bc1, bc2, static_cast<__nv_bfloat16 *>(md->W1b.ptr),
-        static_cast<__nv_bfloat16 *>(md->W2b.ptr), static_cast<__nv_bfloat16 *>(md->w3b.ptr));
+        static_cast<float *>(md->G.ptr), kParams, lr, bc1, bc2, static_cast<__nv_bfloat16 *>(md->W1b.ptr),
+        static_cast<__nv_bfloat16 *>(md->W2b.ptr), static_cast<__nv_bfloat16 *>(md->w3b.ptr), nullptr, nullptr,
+        0.f);
     PM_CUDA(cudaGetLastError());
     if (loss)
         PM_CUDA(cudaStreamSynchronize(s));
+    return PM_OK;
+}
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) on the host: the round keys of the epoch shuffle.
+static void philox10_host(uint32_t c[4], uint32_t k0, uint32_t k1)
+{
+    for (int round = 0; round < 10; ++round) {
+        if (round) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c[0], p1 = (uint64_t)0xCD9E8D57u * c[2];
+        const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+    }
+}
+
+constexpr uint32_t kOpShuffle = 0x300u;  // operation id of the epoch shuffle's draws
+
+extern "C" pm_status pm_model_train(pm_model *md, const uint16_t *x, const float *t, int64_t rows, int32_t epochs,
+                                    int64_t batch, float lr, uint64_t seed, float *losses, void *stream)
+{
+    if (!md || !x || !t || rows < 1 || rows >= ((int64_t)1 << 31) || epochs < 0 || batch < 1 || !(lr > 0.f))
+        return PM_ERR_INVALID_ARG;
+    if (!pm_is_device_ptr(x) || !pm_is_device_ptr(t))
+        return PM_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> g(md->lock);
+    PM_CUDA(cudaSetDevice(md->device));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t per_epoch = pm_ceil_div(rows, batch);
+    const int64_t steps = per_epoch * (int64_t)epochs;
+    if (steps == 0)
+        return PM_OK;
+    const bool losses_dev = losses && pm_is_device_ptr(losses);
+    // the step losses (device), then the predictions of the training kernel (scratch)
+    const size_t loss_bytes = (size_t)pm_round_up(steps * 4, 256);
+    const int64_t bmax = std::min(batch, rows);
+    PM_TRY(md->loss.reserve(256 + loss_bytes + (size_t)bmax * 4));
+    char *lb = static_cast<char *>(md->loss.ptr);
+    float *loss_word = reinterpret_cast<float *>(lb);
+    float *step_loss = losses_dev ? losses : reinterpret_cast<float *>(lb + 256);
+    float *y = reinterpret_cast<float *>(lb + 256 + loss_bytes);
+    PM_CUDA(cudaMemsetAsync(md->G.ptr, 0, kParams * sizeof(float), s));
+    PM_CUDA(cudaMemsetAsync(loss_word, 0, sizeof(float), s));
+    int bits = 2;
+    while (bits < 62 && ((int64_t)1 << bits) < rows)
+        bits += 2;
+    int64_t k = 0;
+    for (int32_t e = 0; e < epochs; ++e) {
+        RowMap map{};
+        uint32_t c[4] = {(uint32_t)e, 0u, kOpShuffle << 16, 0u};
+        philox10_host(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+        for (int r = 0; r < 4; ++r)
+            map.key[r] = c[r];
+        map.half = bits / 2;
+        map.total = rows;
+        for (int64_t b0 = 0; b0 < rows; b0 += batch, ++k) {
+            const int64_t nrow = std::min(batch, rows - b0);
+            map.pos0 = b0;
+            PM_TRY(mlp_launch(md, true, x, nrow, y, t, 1.0f / (float)nrow, s, map));
+            md->step += 1;
+            const float bc1 = 1.f - std::pow(0.9f, (float)md->step);
+            const float bc2 = 1.f - std::pow(0.999f, (float)md->step);
+            k_adam<<<(kParams + 255) / 256, 256, 0, s>>>(
+                static_cast<float *>(md->P.ptr), static_cast<float *>(md->M.ptr), static_cast<float *>(md->V.ptr),
+                static_cast<float *>(md->G.ptr), kParams, lr, bc1, bc2, static_cast<__nv_bfloat16 *>(md->W1b.ptr),
+                static_cast<__nv_bfloat16 *>(md->W2b.ptr), static_cast<__nv_bfloat16 *>(md->w3b.ptr), loss_word,
+                step_loss + k, 1.0f / (float)nrow);
+            PM_CUDA(cudaGetLastError());
+        }
+    }
+    if (losses && !losses_dev) {
+        PM_CUDA(cudaMemcpyAsync(losses, step_loss, (size_t)steps * 4, cudaMemcpyDeviceToHost, s));
+        PM_CUDA(cudaStreamSynchronize(s));
+    }
     return PM_OK;
 }
 

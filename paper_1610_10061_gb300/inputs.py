@@ -192,6 +192,16 @@ def paper_shape_instance(name: str) -> dict:
     raise KeyError(name)
 
 
+def training_instances(name: str, count: int = 4) -> list:
+    """Instances of the same shape as workload `name` but other instance seeds (10, 11, ...): the learned swap
+    proposal is trained on their logged moves and timed on the workload's own instance, which it never sees."""
+    if name == "graph100":
+        return [graph_instance(100, 200, seed=10 + k) for k in range(count)]
+    if name.startswith("gmm5000"):
+        return [gmm_instance(5000, seed=10 + k) for k in range(count)]
+    raise KeyError(name)
+
+
 def _batched_one(spec):
     k, n, p, sub = spec
     if k % 2 == 0:

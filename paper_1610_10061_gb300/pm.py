@@ -101,6 +101,7 @@ _SIGS = {
     "pm_model_forward": ([_P, _P, _I64, _P, _P], _S),
     "pm_model_grad": ([_P, _P, _P, _I64, _P, _P, _P], _S),
     "pm_model_train_step": ([_P, _P, _P, _I64, ctypes.c_float, _P, _P], _S),
+    "pm_model_train": ([_P, _P, _P, _I64, ctypes.c_int32, _I64, ctypes.c_float, ctypes.c_uint64, _P, _P], _S),
     "pm_swap_stats": ([_P, _P, _I64, _P, _P, _P, _P, _P], _S),
     "pm_move_features": ([_P, _P, _P, _P, _P, _P, _P, _I64, _I64, _P, _P], _S),
     "pm_log_moves": ([_P, _P, _P, _I64, _I64, ctypes.c_uint64, _P, _P, _P, _P], _S),
@@ -312,6 +313,11 @@ def pm_model_train_step(md, x, t, rows: int, lr: float, want_loss: bool = False,
     return loss.value if want_loss else None
 
 
+def pm_model_train(model, x, t, rows: int, epochs: int, batch: int, lr: float, seed: int, losses=None, stream=None):
+    _check(_lib.pm_model_train(model, _addr(x), _addr(t), int(rows), int(epochs), int(batch), ctypes.c_float(lr),
+                               ctypes.c_uint64(seed), _addr(losses), _stream(stream)), "pm_model_train")
+
+
 def pm_swap_stats(inst, masks, pop: int, gain, cap, loss, assign, stream=None):
     _check(_lib.pm_swap_stats(inst, _addr(masks), pop, _addr(gain), _addr(cap), _addr(loss), _addr(assign),
                               _stream(stream)), "pm_swap_stats")
@@ -354,21 +360,13 @@ class Model:
         return loss, g
 
     def train(self, x, t, epochs: int = 3, batch: int = 4096, lr: float = 1e-3, seed: int = 0, stream=None):
-        """Adam on (x, t) (device tensors) in shuffled mini-batches; returns each epoch's last batch loss."""
-        import torch
-        rows = x.shape[0]
-        gen = torch.Generator(device="cpu").manual_seed(seed)
-        losses = []
-        for _ in range(epochs):
-            perm = torch.randperm(rows, generator=gen).to(x.device)
-            xs, ts = x[perm].contiguous(), t[perm].contiguous()
-            last = None
-            for b0 in range(0, rows, batch):
-                nrow = min(batch, rows - b0)
-                final = b0 + batch >= rows  # read the loss (a synchronisation) once per epoch
-                last = pm_model_train_step(self.handle, xs[b0:b0 + nrow], ts[b0:b0 + nrow], nrow, lr, final, stream)
-            losses.append(last)
-        return losses
+        """Adam on (x, t) (device tensors) in mini-batches shuffled on the device (pm_model_train); returns the
+        loss of every step (numpy, float32)."""
+        rows = int(x.shape[0])
+        steps = int(epochs) * (-(-rows // int(batch)))
+        losses = np.zeros(max(steps, 1), dtype=np.float32)
+        pm_model_train(self.handle, x, t, rows, int(epochs), int(batch), float(lr), int(seed), losses, stream)
+        return losses[:steps]
 
     def close(self):
         if self.handle:

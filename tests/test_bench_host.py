@@ -55,8 +55,15 @@ def test_issue_roofline_from_the_committed_profiles():
     import pytest
 
     assert bench.ISSUE_PEAK == 152 * 4 * 2.07e9
+    none = bench.issue_roofline("no_such_workload", 1.0)
+    assert none["bound"] == "alu" and none["achieved"] is None and none["frac"] is None
     r = bench.issue_roofline("euclid10000_p100", 1.142)
-    if r is None:
+    if r["achieved"] is None:
         pytest.skip("profiles were taken on another kernel source")
-    assert 0.3 < r["frac"] < 1.0 and r["bound"] == "issue"
-    assert bench.issue_roofline("no_such_workload", 1.0) is None
+    assert 0.3 < r["frac"] < 1.0 and r["bound"] == "alu"
+    assert r["achieved"] == pytest.approx(r["instructions_per_launch"] / 1.142e-3)
+
+
+def test_golden_optimum_reader():
+    cost, best = bench.golden_optimum("graph100")
+    assert cost == 5747 and best == (5, 17, 40, 42, 57)

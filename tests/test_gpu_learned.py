@@ -170,6 +170,55 @@ def test_mlp_forward_every_cta_walks_several_tiles(pm):
     _scale_close(y, yref)
 
 
+def _heavy_batch(rows, seed):
+    """Inputs as _random_batch, targets whose scale varies widely from row to row, so that every batch's loss
+    depends on which rows the shuffle put into it."""
+    X, _ = _random_batch(rows, seed)
+    rng = np.random.default_rng(seed + 1)
+    t = rng.normal(0, 1, size=rows) * np.exp(rng.normal(0, 1, size=rows))
+    return X, t
+
+
+def test_model_train_follows_the_oracle_loop(pm):
+    """pm_model_train (the whole loop behind the C ABI: the keyed epoch shuffle, mini-batches, Adam) against the
+    oracle's loop with the same permutation: every step's loss, and the parameters after the last step."""
+    rows, batch, epochs, lr, seed = 1500, 256, 2, 2e-3, 77
+    model = pm.Model(seed=4)
+    params = mlp.init_params(seed=4)
+    for k in ("b1", "b2", "b3"):
+        params[k] = np.random.default_rng(5).normal(0, 0.1, size=params[k].shape)
+    model.set_params(mlp.flatten(params).astype(np.float32))
+    p32 = mlp.unflatten(model.params().astype(np.float64))
+    X, t = _heavy_batch(rows, 13)
+    xd = torch.from_numpy(X.astype(np.float32)).to(torch.bfloat16).cuda()
+    td = torch.from_numpy(t.astype(np.float32)).cuda()
+    losses = model.train(xd, td, epochs=epochs, batch=batch, lr=lr, seed=seed)
+    pref, _, oloss = mlp.train({k: v.copy() for k, v in p32.items()}, X, t, epochs, batch, lr, seed)
+    assert len(losses) == len(oloss) == epochs * 6
+    _scale_close(np.asarray(losses, dtype=np.float64), np.asarray(oloss))
+    got = mlp.unflatten(model.params().astype(np.float64))
+    steps = len(oloss)
+    for name in ("W1", "b1", "W2", "b2", "w3", "b3"):  # Adam moves each weight by at most lr per step
+        np.testing.assert_allclose(got[name], pref[name], rtol=0, atol=0.25 * lr * steps)
+    # another seed gives another order, hence other batch losses from the same start
+    model.set_params(mlp.flatten(p32).astype(np.float32))
+    other = model.train(xd, td, epochs=1, batch=batch, lr=lr, seed=seed + 1)
+    assert np.abs(np.asarray(other[1:]) - np.asarray(losses[1:6])).max() > 0.05 * np.abs(losses[1:6]).max()
+
+
+def test_model_train_is_repeatable_for_a_seed(pm):
+    X, t = _heavy_batch(5000, 17)
+    xd = torch.from_numpy(X.astype(np.float32)).to(torch.bfloat16).cuda()
+    td = torch.from_numpy(t.astype(np.float32)).cuda()
+    runs = []
+    for _ in range(2):
+        model = pm.Model(seed=6)
+        runs.append(model.train(xd, td, epochs=3, batch=1000, lr=1e-3, seed=5))
+    # the same batches in the same order: equal up to the order of the FP32 gradient additions
+    np.testing.assert_allclose(runs[0], runs[1], rtol=1e-3)
+    assert runs[0][-1] < runs[0][0]
+
+
 def test_adam_step_matches_oracle(pm):
     model = pm.Model(seed=2)
     X, t = _random_batch(512, 9)

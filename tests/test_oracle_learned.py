@@ -114,3 +114,55 @@ def test_move_features_and_target():
     # first-order estimate loss - gain bounds the exact change from above (closing j can only lose less
     # once k is open, opening k can only gain more once j is closed... or equal)
     assert after - cost[0] <= loss[0, j] - 0 and after - cost[0] >= -gain[0, k]
+
+
+def test_fmix32_published_values():
+    """MurmurHash3_x86_32 of the empty input with seed s is fmix32(s) (no blocks, no tail, length 0): its published
+    test values for seeds 0, 1 and 0xffffffff."""
+    assert mlp.fmix32(0) == 0
+    assert mlp.fmix32(1) == 0x514E28B7
+    assert mlp.fmix32(0xFFFFFFFF) == 0x81F16F39
+
+
+@pytest.mark.parametrize("rows", [1, 2, 3, 4, 5, 17, 64, 100, 1000, 4097])
+def test_shuffle_order_is_a_permutation(rows):
+    for epoch in range(3):
+        order = mlp.shuffle_order(rows, seed=12345, epoch=epoch)
+        assert sorted(order.tolist()) == list(range(rows))
+
+
+def test_shuffle_order_changes_with_epoch_and_seed_and_mixes():
+    a = mlp.shuffle_order(1000, 7, 0)
+    assert not np.array_equal(a, mlp.shuffle_order(1000, 7, 1))
+    assert not np.array_equal(a, mlp.shuffle_order(1000, 8, 0))
+    # no longer sorted in long runs: few positions keep their row, successive rows scatter
+    assert (a == np.arange(1000)).sum() < 20
+    assert np.abs(np.diff(a)).mean() > 100
+
+
+def test_shuffle_keys_are_the_philox_words():
+    import oracle
+
+    k = mlp.shuffle_keys(0x123456789, 4)
+    assert k == [int(v) for v in oracle.philox4x32_10([4, 0, 0x300 << 16, 0], [0x23456789, 0x1])]
+
+
+def test_train_loop_reduces_the_loss_and_follows_adam_step_by_step():
+    rng = np.random.default_rng(3)
+    X = np.zeros((300, 16))
+    X[:, :8] = rng.normal(0, 1, size=(300, 8))
+    X = mlp.bf16_round(X)
+    t = X[:, 0] - 0.5 * X[:, 1] + 0.1
+    p0 = mlp.init_params(seed=1)
+    p1, _, losses = mlp.train({k: v.copy() for k, v in p0.items()}, X, t, epochs=4, batch=64, lr=3e-3, seed=9)
+    assert len(losses) == 4 * 5
+    assert np.mean(losses[-5:]) < 0.5 * np.mean(losses[:5])
+    # the first two steps by hand: the first two batches of epoch 0 in the shuffled order, one Adam update between
+    order = mlp.shuffle_order(300, 9, 0)
+    q = {k: v.copy() for k, v in p0.items()}
+    st = mlp.adam_init(q)
+    loss, g = mlp.loss_and_grads(q, X[order[:64]], t[order[:64]], bf16=True)
+    assert loss == losses[0]
+    mlp.adam_step(q, g, st, 3e-3)
+    loss2, _ = mlp.loss_and_grads(q, X[order[64:128]], t[order[64:128]], bf16=True)
+    assert loss2 == losses[1]
