@@ -52,6 +52,9 @@ def parse_args():
     ap.add_argument("--tables", default="delta", choices=["delta", "cumulative"],
                     help="device tables: Delta' (the paper's increments, summed by the scan) or cumulative D' "
                          "(their running sums, read at the first open rank)")
+    ap.add_argument("--evaluator", default="scan", choices=["scan", "hbp"],
+                    help="eval mode: the scan of Section 4.2 (default), or the reduced Hammer-Beresnev polynomial "
+                         "of Section 2.1 (pm_hbp_eval) timed beside it on the same population")
     ap.add_argument("--mode", default="ga", choices=["ga", "eval"],
                     help="ga: GA generations (default); eval: one fitness evaluation pass of a random population")
     return ap.parse_args()
@@ -778,6 +781,61 @@ def eval_pass_record(pm, torch, name, tables="delta", steps=None, warmup=3, budg
     return rec, masks, d, p
 
 
+def run_hbp_mode(args):
+    """The reduced Hammer-Beresnev polynomial (Section 2.1) as an evaluator: its build time, size, and one
+    evaluation pass of `pop` random p-subsets against the scan's pass on the same population (CUDA events, L2
+    flushed between steps; the costs of both are compared)."""
+    import numpy as np
+    import torch
+
+    from paper_1610_10061_gb300 import build
+    from paper_1610_10061_gb300.inputs import random_masks
+
+    build.build()
+    from paper_1610_10061_gb300 import pm
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    w = cached_instance(args.workload)
+    d, p, pop = w["d"], w["p"], w["pop"]
+    n, m = d.shape
+    inst = pm.Instance(d, p, stream=stream.cuda_stream, cumulative=args.tables == "cumulative")
+    inst.tune(pop, stream=stream.cuda_stream)
+    pm.Polynomial(inst).close()  # first launches outside the timing
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    poly = pm.Polynomial(inst)
+    build_s = time.perf_counter() - t0
+    dmask = torch.from_numpy(random_masks(pop, m, p, seed=123).view(np.int32)).cuda()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    out = {}
+    for name, fn in (("hbp", lambda c: poly.eval(dmask, c)),
+                     ("scan", lambda c: pm.pm_eval_population(inst.handle, dmask, pop, c, 0, stream.cuda_stream))):
+        c = torch.empty(pop, dtype=torch.int64, device="cuda")
+        for _ in range(args.warmup):
+            fn(c)
+        steps = args.steps or 10
+        es = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ee = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        for k in range(steps):
+            flush.zero_()
+            es[k].record(stream)
+            fn(c)
+            ee[k].record(stream)
+        torch.cuda.synchronize()
+        out[name] = (statistics.mean(a.elapsed_time(b) for a, b in zip(es, ee)), c.cpu().numpy())
+    assert np.array_equal(out["hbp"][1], out["scan"][1])
+    line = {"metric": "fitness evals/s (one evaluation pass), reduced polynomial vs scan", "unit": UNIT,
+            "value": pop / (out["hbp"][0] / 1000), "higher_is_better": True, "n_gpus": 1, "data": "synthetic",
+            "dtype": "int64", "config": {"workload": args.workload, "n": int(n), "m": int(m), "p": int(p), "pop": pop,
+                                         "l2": "flushed between timed steps"},
+            "hbp": {"terms": poly.terms, "terms_before_merge": int(n * (m - p + 1)), "build_s": build_s,
+                    "ms_per_pass": out["hbp"][0], "evals_per_s": pop / (out["hbp"][0] / 1000)},
+            "scan": {"ms_per_pass": out["scan"][0], "evals_per_s": pop / (out["scan"][0] / 1000)},
+            "scan_over_hbp": out["hbp"][0] / out["scan"][0], "costs_equal": True}
+    print(json.dumps(line), flush=True)
+
+
 def run_eval_mode(args):
     """One evaluation pass of `pop` uniformly random p-subsets per step (the fitness-throughput workload)."""
     import torch
@@ -1146,6 +1204,8 @@ def main():
         run_learned(args)
     elif args.workload.startswith("batched"):
         run_batched(args)
+    elif args.mode == "eval" and args.evaluator == "hbp":
+        run_hbp_mode(args)
     elif args.mode == "eval":
         run_eval_mode(args)
     else:

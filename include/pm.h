@@ -298,6 +298,43 @@ PM_API pm_status pm_debug_fail_alloc(int64_t after, int64_t *pending);
 PM_API pm_status pm_debug_scan_timeout(int64_t launches, int64_t *pending);
 
 /* ------------------------------------------------------------------------
+ * The Hammer-Beresnev polynomial (Section 2.1, Eq. 6, Example 1): a second
+ * evaluator of the same costs, for small instances and for checking.
+ * ------------------------------------------------------------------------ */
+
+typedef struct pm_hbp pm_hbp;
+
+/*
+ * pm_hbp_create -- the reduced polynomial of inst on the device: client i
+ * contributes Delta'_i[k] times the monomial over the facility set
+ * {Pi'_i[0], ..., Pi'_i[k-1]} (k = 0 .. L-1; k = 0 is the constant term),
+ * in the variables z_j = 1 - x_j; like monomials (equal sets from different
+ * clients) are merged by adding coefficients and zero coefficients dropped,
+ * as Example 1 reduces its 15 terms to 7.  The merge is exact: terms are
+ * grouped by set size and a hash of the set, and a term joins a group only
+ * after its set has been compared facility by facility with the group's.
+ * Synchronises `stream`.  Errors: PM_ERR_INVALID_ARG, PM_ERR_UNSUPPORTED
+ * (n * L above 2^26 terms or more than 8 GiB of monomials), PM_ERR_OOM,
+ * PM_ERR_CUDA.
+ */
+PM_API pm_status pm_hbp_create(pm_instance *inst, void *stream, pm_hbp **out);
+PM_API pm_status pm_hbp_destroy(pm_hbp *h);
+/* Number of monomials after the merge and W = ceil(m/32) (either nullable). */
+PM_API pm_status pm_hbp_info(const pm_hbp *h, int64_t *terms, int64_t *W);
+/* The monomials, in no particular order: sets (terms x W uint32 bitsets,
+ * facility j in the set iff bit (j & 31) of word j >> 5) and coeffs (terms
+ * int64); host or device memory, either nullable.  Synchronises `stream`. */
+PM_API pm_status pm_hbp_terms(const pm_hbp *h, uint32_t *sets, int64_t *coeffs, void *stream);
+/*
+ * pm_hbp_eval -- the polynomial's value for each of `pop` bitsets (masks,
+ * device, the layout of pm_eval_population): the sum of the coefficients of
+ * the monomials with no open facility.  It equals pm_eval_population's cost
+ * (Eq. 4).  costs: device, pop int64.  Asynchronous.  Work: terms x W words
+ * per individual.  Errors: PM_ERR_INVALID_ARG, PM_ERR_CUDA.
+ */
+PM_API pm_status pm_hbp_eval(pm_hbp *h, const uint32_t *masks, int64_t pop, int64_t *costs, void *stream);
+
+/* ------------------------------------------------------------------------
  * The genetic algorithm (Sections 3.1, 3.2.2, 4.3-4.5) on the device.
  * ------------------------------------------------------------------------ */
 

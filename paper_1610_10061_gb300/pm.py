@@ -101,6 +101,11 @@ _SIGS = {
     "pm_model_forward": ([_P, _P, _I64, _P, _P], _S),
     "pm_model_grad": ([_P, _P, _P, _I64, _P, _P, _P], _S),
     "pm_model_train_step": ([_P, _P, _P, _I64, ctypes.c_float, _P, _P], _S),
+    "pm_hbp_create": ([_P, _P, _P], _S),
+    "pm_hbp_destroy": ([_P], _S),
+    "pm_hbp_info": ([_P, _P, _P], _S),
+    "pm_hbp_terms": ([_P, _P, _P, _P], _S),
+    "pm_hbp_eval": ([_P, _P, _I64, _P, _P], _S),
     "pm_model_train": ([_P, _P, _P, _I64, ctypes.c_int32, _I64, ctypes.c_float, ctypes.c_uint64, _P, _P], _S),
     "pm_swap_stats": ([_P, _P, _I64, _P, _P, _P, _P, _P], _S),
     "pm_move_features": ([_P, _P, _P, _P, _P, _P, _P, _I64, _I64, _P, _P], _S),
@@ -311,6 +316,71 @@ def pm_model_train_step(md, x, t, rows: int, lr: float, want_loss: bool = False,
     _check(_lib.pm_model_train_step(md, _addr(x), _addr(t), rows, lr, ctypes.byref(loss) if want_loss else None,
                                     _stream(stream)), "pm_model_train_step")
     return loss.value if want_loss else None
+
+
+def pm_hbp_create(inst, stream=None):
+    h = ctypes.c_void_p()
+    _check(_lib.pm_hbp_create(inst, _stream(stream), ctypes.byref(h)), "pm_hbp_create")
+    return h
+
+
+def pm_hbp_destroy(h):
+    _check(_lib.pm_hbp_destroy(h), "pm_hbp_destroy")
+
+
+def pm_hbp_info(h):
+    terms, W = ctypes.c_int64(), ctypes.c_int64()
+    _check(_lib.pm_hbp_info(h, ctypes.byref(terms), ctypes.byref(W)), "pm_hbp_info")
+    return int(terms.value), int(W.value)
+
+
+def pm_hbp_terms(h, sets, coeffs, stream=None):
+    _check(_lib.pm_hbp_terms(h, _addr(sets), _addr(coeffs), _stream(stream)), "pm_hbp_terms")
+
+
+def pm_hbp_eval(h, masks, pop: int, costs, stream=None):
+    _check(_lib.pm_hbp_eval(h, _addr(masks), int(pop), _addr(costs), _stream(stream)), "pm_hbp_eval")
+
+
+class Polynomial:
+    """The reduced Hammer-Beresnev polynomial of an Instance, built and evaluated on the device."""
+
+    def __init__(self, inst, stream=None):
+        self.inst = inst
+        self.handle = pm_hbp_create(inst.handle, stream)
+        self.terms, self.W = pm_hbp_info(self.handle)
+
+    def monomials(self):
+        """{frozenset of facility ids: coefficient} (host)."""
+        sets = np.zeros((max(self.terms, 1), self.W), dtype=np.uint32)
+        coeffs = np.zeros(max(self.terms, 1), dtype=np.int64)
+        pm_hbp_terms(self.handle, sets, coeffs)
+        out = {}
+        for q in range(self.terms):
+            bits = np.nonzero(np.unpackbits(sets[q].view(np.uint8), bitorder="little"))[0]
+            out[frozenset(int(j) for j in bits)] = int(coeffs[q])
+        return out
+
+    def eval(self, masks, costs=None, stream=None):
+        """Values at a device population (torch CUDA tensor of pop x W int32 words)."""
+        import torch
+
+        pop = int(masks.shape[0])
+        if costs is None:
+            costs = torch.empty(pop, dtype=torch.int64, device=masks.device)
+        pm_hbp_eval(self.handle, masks, pop, costs, stream)
+        return costs
+
+    def close(self):
+        if self.handle:
+            pm_hbp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def pm_model_train(model, x, t, rows: int, epochs: int, batch: int, lr: float, seed: int, losses=None, stream=None):
