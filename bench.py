@@ -162,12 +162,12 @@ def measured_bf16_peak():
 
 
 def fitness_source_hash():
-    """Hash of the scan kernel's code (fitness.cu and pm_common.cuh without their comments and blank lines): the
-    key that ties a committed ncu summary to the code it was taken on."""
+    """Hash of the scan kernel's code (fitness.cu, scan_walk.cuh and pm_common.cuh without their comments and blank
+    lines): the key that ties a committed ncu summary to the code it was taken on."""
     import re
 
     h = hashlib.sha256()
-    for f in ("fitness.cu", "pm_common.cuh"):
+    for f in ("fitness.cu", "scan_walk.cuh", "pm_common.cuh"):
         with open(os.path.join(ROOT, "paper_1610_10061_gb300", "csrc", f)) as fh:
             text = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
         text = re.sub(r"//[^\n]*", "", text)

@@ -290,7 +290,10 @@ PM_API pm_status pm_debug_fail_alloc(int64_t after, int64_t *pending);
  * tile runs out after a few thousand polls with nothing in flight; each of
  * them records PM_ERR_TIMEOUT in the launch's error word and returns, while
  * the even-numbered CTAs finish their work items and leave their split sums
- * behind, as a real timeout would.  No fault, trap or hang: this is the
+ * behind, as a real timeout would.  A GA whose generations run in the
+ * persistent kernel consumes an armed launch there instead: its CTA 0 leaves
+ * at once, so the first grid barrier runs out (after 20 ms) in every other
+ * CTA, which records PM_ERR_TIMEOUT and leaves.  No fault, trap or hang: this is the
  * exit every wait in the library takes.  launches <= 0 disarms it (the
  * default).  pending (host, nullable) receives the launches still armed until
  * now.  Process-wide; not meant for concurrent use.  Always PM_OK.

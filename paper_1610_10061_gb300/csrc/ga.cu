@@ -47,6 +47,7 @@
 
 #include "pm_alloc.h"
 #include "pm_common.cuh"
+#include "scan_walk.cuh"
 
 // batch.cu
 pm_status pm_batch_ga_plan(pm_batch *b, int64_t pop, pm_multi_plan &out);
@@ -146,6 +147,27 @@ __device__ __forceinline__ uint32_t lowest_bits(uint32_t x, int k)
     return r;
 }
 
+// Loads of data another CTA may have written earlier in the same kernel (the
+// persistent generation kernel) go through L2 (kCG); the per-phase kernels
+// read data of earlier launches and keep their usual loads.
+template <bool kCG>
+__device__ __forceinline__ uint32_t ld_row(const uint32_t *p)
+{
+    if constexpr (kCG)
+        return __ldcg(p);
+    else
+        return *p;
+}
+
+template <bool kCG>
+__device__ __forceinline__ uint32_t ld_ro(const uint32_t *p)
+{
+    if constexpr (kCG)
+        return __ldcg(p);
+    else
+        return __ldg(p);
+}
+
 // Largest k with base(k) <= x.
 template <typename F>
 __device__ __forceinline__ int find_k(int K, int64_t x, F base)
@@ -199,7 +221,7 @@ __device__ __forceinline__ void write_columns(const uint32_t *rows, int64_t rs, 
 
 // ------------------------------- kernels -----------------------------------
 
-__global__ void k_ga_begin(ga_glob *glob, ga_dev *st, int K, long long gens, long long *trace)
+__global__ void k_ga_begin(ga_glob *glob, ga_dev *st, int K, long long gens, long long *trace, unsigned *bar)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < K)
@@ -207,6 +229,8 @@ __global__ void k_ga_begin(ga_glob *glob, ga_dev *st, int K, long long gens, lon
     if (k == 0) {
         glob->remaining = gens;
         glob->step_gens = 0;
+        if (bar)
+            bar[0] = 0u;  // the persistent kernel's barrier starts with no arrivals, whatever a failed launch left
     }
 }
 
@@ -277,6 +301,48 @@ __global__ void __launch_bounds__(32) k_ga_init(const ga_prob *__restrict__ gps,
     }
 }
 
+// Individual t of generation gen into the W-word row `row` (shared memory), by
+// one warp: a migrant (Section 4.5) copies its deme's best of the previous
+// generation; any other individual is a fresh p-subset by Floyd's sampling,
+// the lanes computing the p Philox draws in parallel (lane l the counter
+// blocks l, l + 32, ...; draw q is uniform below m - p + q + 1) into `draws`
+// (p words, shared) and lane 0 running the p dependent insertions.
+template <bool kCG>
+__device__ __forceinline__ void fresh_individual(const ga_prob &gp, int64_t t, uint32_t gen, uint64_t seed,
+                                                 const uint32_t *__restrict__ deme_best, uint32_t *row,
+                                                 uint32_t *draws, int lane)
+{
+    const int32_t W = gp.W, m = gp.m, p = gp.p;
+    const bool migrant = gen > 0 && (gp.team ? t < gp.NB : (t % gp.D) == 0);
+    if (migrant) {
+        const uint32_t *src = deme_best + gp.dword_base + (gp.team ? t : t / gp.D) * W;
+        for (int w = lane; w < W; w += 32)
+            row[w] = ld_row<kCG>(src + w);
+    } else {
+        for (int w = lane; w < W; w += 32)
+            row[w] = 0u;
+        for (int b = lane; 4 * b < p; b += 32) {
+            const uint4 v = draw_block(seed, gen, (uint32_t)t, OP_INIT, (uint32_t)b, gp.sid);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int q = 4 * b + i;
+                if (q < p)
+                    draws[q] = uniform_below(word_of(v, (uint32_t)i), (uint32_t)(m - p + q + 1));
+            }
+        }
+        __syncwarp();
+        if (lane == 0) {
+            for (int q = 0; q < p; ++q) {
+                const uint32_t c = draws[q];
+                const uint32_t jj = (uint32_t)(m - p + q);
+                const uint32_t pick = ((row[c >> 5] >> (c & 31)) & 1u) ? jj : c;
+                row[pick >> 5] |= 1u << (pick & 31);
+            }
+        }
+    }
+    __syncwarp();
+}
+
 // The same fresh population as k_ga_init with one warp per individual: the
 // lanes compute the p Philox draws of Floyd's sampling in parallel (lane l
 // the counter blocks l, l + 32, ...), then lane 0 runs the p dependent
@@ -314,35 +380,7 @@ __global__ void __launch_bounds__(1024) k_ga_init_warp(const ga_prob *__restrict
             improved[gp.ind_base + t] = 0;
             atomicOr(&on_s, 1u << j);
         }
-        const bool migrant = gen > 0 && (gp.team ? t < gp.NB : (t % gp.D) == 0);
-        if (migrant) {
-            const uint32_t *src = deme_best + gp.dword_base + (gp.team ? t : t / gp.D) * W;
-            for (int w = lane; w < W; w += 32)
-                row[w] = src[w];
-        } else {
-            for (int w = lane; w < W; w += 32)
-                row[w] = 0u;
-            // draw q of Floyd's sampling is uniform below m - p + q + 1 (word q & 3 of counter block q >> 2)
-            for (int b = lane; 4 * b < p; b += 32) {
-                const uint4 v = draw_block(seed, gen, (uint32_t)t, OP_INIT, (uint32_t)b, gp.sid);
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int q = 4 * b + i;
-                    if (q < p)
-                        draws[q] = uniform_below(word_of(v, (uint32_t)i), (uint32_t)(m - p + q + 1));
-                }
-            }
-            __syncwarp();
-            if (lane == 0) {
-                for (int q = 0; q < p; ++q) {
-                    const uint32_t c = draws[q];
-                    const uint32_t jj = (uint32_t)(m - p + q);
-                    const uint32_t pick = ((row[c >> 5] >> (c & 31)) & 1u) ? jj : c;
-                    row[pick >> 5] |= 1u << (pick & 31);
-                }
-            }
-        }
-        __syncwarp();
+        fresh_individual<false>(gp, t, gen, seed, deme_best, row, draws, lane);
         for (int w = lane; w < W; w += 32)
             X[gp.word_base + t * W + w] = row[w];
     }
@@ -677,13 +715,77 @@ __global__ void __launch_bounds__(1024) k_ga_init_comb(ga_prob gp, uint32_t *__r
     write_columns(X + gp.word_base + t0 * W, W, t0, gp, co, lane, j, 32);
 }
 
+// The child F of C and its couple Kp (W-word rows) for the pair's draws (r1, i), built by one warp (Section
+// 4.3, reading R6): the positions r1, r1+1, ... (circularly) are visited as W+1 segments -- word w0 = r1/32 from
+// bit r1%32 up, the following words, and word w0 below bit r1%32; a warp scan of the per-segment counts of 0->1
+// and 1->0 candidates (C != couple) tells each segment how many of its candidates to take, the lowest bits
+// (earliest positions) of a segment first.  Returns whether i candidates of each kind were found (the crossover
+// succeeded); the same on every lane.
+template <bool kCG>
+__device__ __forceinline__ bool crossover_child(const uint32_t *C, const uint32_t *Kp, uint32_t *F, int32_t W,
+                                                uint32_t r1, int i, int lane)
+{
+    const int w0 = (int)(r1 >> 5);
+    const uint32_t b0 = r1 & 31u;
+    int c01 = 0, c10 = 0;    // candidates in the segments of earlier rounds
+    uint32_t w0change = 0u;  // changes to word w0 (first and last segment)
+    for (int base = 0; base <= W; base += 32) {
+        const int sidx = base + lane;
+        uint32_t z = 0u, o = 0u, cw = 0u;
+        int w = -1;
+        if (sidx <= W) {
+            uint32_t seg;
+            if (sidx == 0) {
+                w = w0;
+                seg = 0xffffffffu << b0;
+            } else if (sidx < W) {
+                w = w0 + sidx;
+                if (w >= W)
+                    w -= W;
+                seg = 0xffffffffu;
+            } else {
+                w = w0;
+                seg = b0 ? ((1u << b0) - 1u) : 0u;
+            }
+            cw = ld_row<kCG>(C + w);
+            const uint32_t kw = ld_row<kCG>(Kp + w);
+            z = ~cw & kw & seg;
+            o = cw & ~kw & seg;
+        }
+        // exclusive warp scan of the two counts packed in one word
+        const uint32_t nz = __popc(z), no = __popc(o);
+        const uint32_t packed = nz | (no << 16);
+        uint32_t incl = packed;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t y = __shfl_up_sync(PM_FULL_MASK, incl, off);
+            if (lane >= off)
+                incl += y;
+        }
+        const uint32_t excl = incl - packed;
+        const int before01 = c01 + (int)(excl & 0xffffu);
+        const int before10 = c10 + (int)(excl >> 16);
+        const int take01 = min(max(i - before01, 0), (int)nz);
+        const int take10 = min(max(i - before10, 0), (int)no);
+        const uint32_t change = lowest_bits(z, take01) | lowest_bits(o, take10);
+        if (w >= 0) {
+            if (sidx == 0 || sidx == W)
+                w0change |= change;
+            else
+                F[w] = cw ^ change;
+        }
+        const uint32_t tot = __shfl_sync(PM_FULL_MASK, incl, 31);
+        c01 += (int)(tot & 0xffffu);
+        c10 += (int)(tot >> 16);
+    }
+    w0change = __reduce_or_sync(PM_FULL_MASK, w0change);
+    if (lane == 0)
+        F[w0] = ld_row<kCG>(C + w0) ^ w0change;
+    return c01 >= i && c10 >= i;
+}
+
 // One crossover round (Section 4.3).  CTA = 32 warps = 32 individuals; warp
-// j builds the child of individual t0 + j.  The positions r1, r1+1, ...
-// (circularly) are visited as W+1 segments: word w0 = r1/32 from bit r1%32
-// up, the following words, and word w0 below bit r1%32.  A warp scan of the
-// per-segment counts of 0->1 and 1->0 candidates (C != couple) tells each
-// segment how many of its candidates to take; within a segment the lowest
-// bits (earliest positions) come first.
+// j builds the child of individual t0 + j (crossover_child).
 __global__ void __launch_bounds__(1024) k_ga_crossover(const ga_prob *__restrict__ gps, int K, ga_prob one,
                                                        const uint32_t *__restrict__ X, uint32_t *__restrict__ Xc,
                                                        uint32_t *__restrict__ active, uint32_t round, uint64_t seed,
@@ -719,66 +821,9 @@ __global__ void __launch_bounds__(1024) k_ga_crossover(const ga_prob *__restrict
     if (t < gp.pop) {
         const uint32_t r1 = uniform_below(v.x, (uint32_t)gp.m);
         const int i = 1 + (int)uniform_below(v.y, (uint32_t)(p / 2));
-        const uint32_t *C = X + gp.word_base + t * W;
-        const uint32_t *Kp = X + gp.word_base + partner * W;
-        uint32_t *F = Xc + gp.word_base + t * W;
-        const int w0 = (int)(r1 >> 5);
-        const uint32_t b0 = r1 & 31u;
-        int c01 = 0, c10 = 0;    // candidates in the segments of earlier rounds
-        uint32_t w0change = 0u;  // changes to word w0 (first and last segment)
-        for (int base = 0; base <= W; base += 32) {
-            const int sidx = base + lane;
-            uint32_t z = 0u, o = 0u, cw = 0u;
-            int w = -1;
-            if (sidx <= W) {
-                uint32_t seg;
-                if (sidx == 0) {
-                    w = w0;
-                    seg = 0xffffffffu << b0;
-                } else if (sidx < W) {
-                    w = w0 + sidx;
-                    if (w >= W)
-                        w -= W;
-                    seg = 0xffffffffu;
-                } else {
-                    w = w0;
-                    seg = b0 ? ((1u << b0) - 1u) : 0u;
-                }
-                cw = C[w];
-                const uint32_t kw = Kp[w];
-                z = ~cw & kw & seg;
-                o = cw & ~kw & seg;
-            }
-            // exclusive warp scan of the two counts packed in one word
-            const uint32_t nz = __popc(z), no = __popc(o);
-            const uint32_t packed = nz | (no << 16);
-            uint32_t incl = packed;
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const uint32_t y = __shfl_up_sync(PM_FULL_MASK, incl, off);
-                if (lane >= off)
-                    incl += y;
-            }
-            const uint32_t excl = incl - packed;
-            const int before01 = c01 + (int)(excl & 0xffffu);
-            const int before10 = c10 + (int)(excl >> 16);
-            const int take01 = min(max(i - before01, 0), (int)nz);
-            const int take10 = min(max(i - before10, 0), (int)no);
-            const uint32_t change = lowest_bits(z, take01) | lowest_bits(o, take10);
-            if (w >= 0) {
-                if (sidx == 0 || sidx == W)
-                    w0change |= change;
-                else
-                    F[w] = cw ^ change;
-            }
-            const uint32_t tot = __shfl_sync(PM_FULL_MASK, incl, 31);
-            c01 += (int)(tot & 0xffffu);
-            c10 += (int)(tot >> 16);
-        }
-        w0change = __reduce_or_sync(PM_FULL_MASK, w0change);
-        if (lane == 0)
-            F[w0] = C[w0] ^ w0change;
-        if (lane == 0 && p / 2 > 0 && c01 >= i && c10 >= i)
+        const bool ok = crossover_child<false>(X + gp.word_base + t * W, X + gp.word_base + partner * W,
+                                               Xc + gp.word_base + t * W, W, r1, i, lane);
+        if (lane == 0 && p / 2 > 0 && ok)
             atomicOr(&valid_s, 1u << j);
     }
     __syncthreads();
@@ -792,14 +837,15 @@ __global__ void __launch_bounds__(1024) k_ga_crossover(const ga_prob *__restrict
 
 // 32 bits of the bitset C starting at bit position s (s may be as low as
 // -31; bits read from below position 0 are zero).
+template <bool kCG>
 __device__ __forceinline__ uint32_t bits_from(const uint32_t *C, int32_t W, int64_t s)
 {
     if (s < 0)
-        return __ldg(C) << (uint32_t)(-s);
+        return ld_ro<kCG>(C) << (uint32_t)(-s);
     const int64_t q = s >> 5;
     const uint32_t r = (uint32_t)(s & 31);
-    const uint32_t lo = __ldg(C + q);
-    const uint32_t hi = (q + 1 < W) ? __ldg(C + q + 1) : 0u;
+    const uint32_t lo = ld_ro<kCG>(C + q);
+    const uint32_t hi = (q + 1 < W) ? ld_ro<kCG>(C + q + 1) : 0u;
     return __funnelshift_r(lo, hi, r);
 }
 
@@ -815,6 +861,7 @@ __device__ __forceinline__ uint32_t range_mask(int64_t lo, int64_t hi)  // bits 
 // operation OP_MUT + q -- kind and direction from draws 0 and 1, the
 // circular amount or the block's two ends from draws 2 and 3, the block's
 // amount from draw 4.  F[a+i] = C[a + (i+kl) mod len].
+template <bool kCG = false>
 __device__ __forceinline__ void mutant_row(const uint32_t *__restrict__ C, uint32_t *__restrict__ F, int32_t W,
                                            int32_t m, uint64_t seed, uint32_t gen, uint32_t t, uint32_t q,
                                            uint32_t sid, int lane)
@@ -844,7 +891,7 @@ __device__ __forceinline__ void mutant_row(const uint32_t *__restrict__ C, uint3
         const int64_t pos0 = (int64_t)w * 32;
         const int64_t in_lo = a > pos0 ? a : pos0;
         const int64_t in_hi = (a + len) < (pos0 + 32) ? (a + len) : (pos0 + 32);
-        const uint32_t cw = __ldg(C + w);
+        const uint32_t cw = ld_ro<kCG>(C + w);
         if (in_lo >= in_hi) {
             F[w] = cw;
             continue;
@@ -852,10 +899,10 @@ __device__ __forceinline__ void mutant_row(const uint32_t *__restrict__ C, uint3
         uint32_t out = cw & ~range_mask(in_lo - pos0, in_hi - pos0);
         const int64_t e1 = in_hi < pwrap ? in_hi : pwrap;
         if (in_lo < e1)
-            out |= bits_from(C, W, pos0 + kl) & range_mask(in_lo - pos0, e1 - pos0);
+            out |= bits_from<kCG>(C, W, pos0 + kl) & range_mask(in_lo - pos0, e1 - pos0);
         const int64_t s2 = in_lo > pwrap ? in_lo : pwrap;
         if (s2 < in_hi)
-            out |= bits_from(C, W, pos0 + kl - len) & range_mask(s2 - pos0, in_hi - pos0);
+            out |= bits_from<kCG>(C, W, pos0 + kl - len) & range_mask(s2 - pos0, in_hi - pos0);
         F[w] = out;
     }
 }
@@ -1229,6 +1276,507 @@ __global__ void __launch_bounds__(1024) k_ga_learned_pick(const ga_prob *__restr
     write_columns(Xc + gp.word_base + t0 * W, W, t0, gp, co, lane, j, 32);
 }
 
+// ---------------------------------------------------------------------------
+// The persistent generation kernel.  For one instance evaluated by the column
+// scan, with the speculative mutation cycle, Floyd generation and no learned
+// try (the default GA), one cooperative launch runs all the generations of a
+// pm_ga_step call: the phases of the per-phase kernels above -- population,
+// evaluation, lg D x (crossover, evaluation with acceptance), all mutation
+// tries, their evaluation, first improving try, deme bests, global best --
+// separated by grid-wide barriers instead of kernel boundaries.  A phase
+// works on the same per-warp operators (fresh_individual, crossover_child,
+// mutant_row) and the same client walk (scan_clients), so the population of
+// every generation is the one the per-phase kernels produce.  Data another
+// CTA wrote earlier in the launch is read through L2 (ld.cg); tiles are
+// copied into shared memory with coherent vector loads.
+// ---------------------------------------------------------------------------
+
+constexpr int kFusedThreads = 1024;
+constexpr uint64_t kBarrierTimeoutNs = 4000000000ull;  // a grid barrier gives up after 4 s
+constexpr uint64_t kStallTimeoutNs = 20000000ull;      // 20 ms in a launch armed by pm_debug_scan_timeout
+constexpr uint32_t kBarrierSpinCap = 1u << 26;         // and after this many polls whatever the timer says
+
+struct FusedArgs {
+    ga_prob gp;                      // the instance (bases 0)
+    ga_prob gq;                      // layout of the Q x pop mutation candidates (pop = Q * pop)
+    const uint16_t *pi;
+    const int32_t *delta;
+    int64_t n, stride;
+    int32_t L, cum;
+    int64_t tiles, splits, cps;      // the population's scans: tiles of 32 G individuals x client splits
+    int64_t tilesQ, splitsQ, cpsQ;   // the candidates' scan
+    int32_t R, Q;
+    uint64_t seed;
+    uint32_t *X, *Xc, *XQ;           // population, crossover children, mutation candidates (rows)
+    uint32_t *colT, *colQ;           // facility-major copies of children / candidates
+    uint32_t *active, *activeQ;      // bit per individual / candidate: evaluated in this scan
+    int64_t *cost, *costQ;
+    unsigned long long *accum, *accumQ;  // packed split reduction words, zero at rest
+    uint8_t *improved;
+    uint32_t *deme_best;
+    int64_t *deme_cost;
+    uint32_t *best;
+    ga_dev *st;
+    ga_glob *glob;
+    unsigned *bar;                   // [0] arrivals at the current barrier, [1] barriers completed
+    int *err;
+    uint32_t stall;                  // failure-detection tests: CTA 0 leaves before the first barrier
+};
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier of the cooperative launch: thread 0 of every CTA arrives on bar[0]; the last arrival resets
+// it and advances bar[1]; the others poll bar[1] for at most kBarrierTimeoutNs (and kBarrierSpinCap polls), then
+// record PM_ERR_TIMEOUT and the CTA leaves (false).  Writes before the barrier are visible to L2 loads after it.
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err, int *ok_s, uint64_t limit_ns = kBarrierTimeoutNs)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned target = ld_acquire_u32(bar + 1) + 1u;
+        __threadfence();
+        if (atomicAdd(bar, 1u) + 1u == gridDim.x) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            st_release_u32(bar + 1, target);
+        } else {
+            const uint64_t t0 = global_ns();
+            uint32_t spins = 0;
+            while (ld_acquire_u32(bar + 1) != target) {
+                if (++spins > kBarrierSpinCap || global_ns() - t0 > limit_ns) {
+                    atomicExch(err, (int)PM_ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        *ok_s = ok;
+    }
+    __syncthreads();
+    return *ok_s != 0;
+}
+
+enum FusedScanMode { kScanStore = 0, kScanAccept = 1, kScanCandidates = 2 };
+
+// One scan phase: the (client split, tile) items of the population (kScanStore: costs; kScanAccept: a child
+// replaces its parent when strictly cheaper) or of the mutation candidates (kScanCandidates: their costs), with
+// the packed split reduction of the column kernel; then the grid barrier.
+template <int G>
+__device__ __forceinline__ bool fused_scan(const FusedArgs &a, int mode, uint32_t *colbits, unsigned long long *acc_s,
+                           uint32_t *a0_s, uint32_t *fin_s, int *ok_s)
+{
+    const bool cand = mode == kScanCandidates;
+    const int64_t tiles = cand ? a.tilesQ : a.tiles, splits = cand ? a.splitsQ : a.splits;
+    const int64_t cps = cand ? a.cpsQ : a.cps, pop = cand ? a.gq.pop : a.gp.pop;
+    const uint32_t *colT = cand ? a.colQ : a.colT;
+    const uint32_t *active = cand ? a.activeQ : a.active;
+    unsigned long long *accum = cand ? a.accumQ : a.accum;
+    const int32_t W = a.gp.W, L = a.L;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int64_t tile_words = (int64_t)W * 32 * G;
+    int64_t loaded = -1;
+    for (int64_t item = blockIdx.x; item < tiles * splits; item += gridDim.x) {
+        const int64_t tile = item % tiles, split = item / tiles;
+        const int64_t ind0 = tile * 32 * G;
+        const int64_t c_begin = split * cps;
+        const int64_t c_end = (c_begin + cps < a.n) ? c_begin + cps : a.n;
+        auto load = [&](int64_t cc, int base, uint32_t &j, int32_t &dl) {
+            const int r = base + lane;
+            if (cc < c_end && r < L) {
+                j = __ldg(a.pi + cc * a.stride + r);
+                dl = __ldg(a.delta + cc * a.stride + r);
+            } else {
+                j = 0;
+                dl = 0;
+            }
+        };
+        int64_t c = c_begin + warp;
+        uint32_t j_cur, j_nxt, j_nc, j_nc1;
+        int32_t d_cur, d_nxt, d_nc, d_nc1;
+        load(c, 0, j_cur, d_cur);
+        load(c, 32, j_nxt, d_nxt);
+        load(c + nwarps, 0, j_nc, d_nc);
+        load(c + nwarps, 32, j_nc1, d_nc1);
+        if (tile != loaded) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(colT + tile * tile_words);
+            uint4 *dst = reinterpret_cast<uint4 *>(colbits);
+            for (int64_t q = threadIdx.x; q < tile_words / 4; q += blockDim.x)
+                dst[q] = __ldcg(src + q);
+            loaded = tile;
+        }
+        if (warp < G) {
+            const int64_t t = ind0 + 32 * warp + lane;
+            const bool on = t < pop && ((__ldcg(active + (t >> 5)) >> (t & 31)) & 1u);
+            const uint32_t b = __ballot_sync(PM_FULL_MASK, on);
+            if (lane == 0)
+                a0_s[warp] = b;
+        }
+        for (int q = threadIdx.x; q < G * 32; q += blockDim.x)
+            acc_s[q] = 0ull;
+        __syncthreads();
+        uint32_t a0[G];
+        uint32_t any0 = 0;
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            a0[g] = a0_s[g];
+            any0 |= a0[g];
+        }
+        unsigned long long acc[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+            acc[g] = 0ull;
+        if (any0 && c < c_end)
+            scan_clients<G>(colbits, a0, c, c_end, nwarps, L, lane, a.cum != 0, load, j_cur, d_cur, j_nxt, d_nxt,
+                            j_nc, d_nc, j_nc1, d_nc1, acc);
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+            if (acc[g])
+                atomicAdd(&acc_s[g * 32 + lane], acc[g]);
+        __syncthreads();
+        const uint32_t *fin = a0_s;
+        if (splits > 1) {
+            // one atomic per individual carries the split's sum and a count of one (bits 48..63); the split that
+            // completes the count holds the total and leaves the word zero
+            for (int q = threadIdx.x; q < G * 32; q += blockDim.x) {
+                const int64_t t = ind0 + q;
+                bool last = false;
+                if (t < pop && ((a0_s[q >> 5] >> (q & 31)) & 1u)) {
+                    const unsigned long long add = acc_s[q] + (1ull << 48);
+                    const unsigned long long old = atomicAdd(accum + t, add);
+                    if ((old >> 48) == (unsigned long long)(splits - 1)) {
+                        acc_s[q] = (old + add) & ((1ull << 48) - 1ull);
+                        accum[t] = 0ull;
+                        last = true;
+                    }
+                }
+                const uint32_t b = __ballot_sync(PM_FULL_MASK, last);
+                if ((q & 31) == 0)
+                    fin_s[q >> 5] = b;
+            }
+            __syncthreads();
+            fin = fin_s;
+        }
+        for (int q = warp; q < G * 32; q += nwarps) {
+            const int64_t t = ind0 + q;
+            if (t >= pop)
+                break;
+            if (!((fin[q >> 5] >> (q & 31)) & 1u))
+                continue;
+            const int64_t sum = (int64_t)acc_s[q];
+            if (mode == kScanStore) {
+                if (lane == 0)
+                    a.cost[t] = sum;
+            } else if (mode == kScanCandidates) {
+                if (lane == 0)
+                    a.costQ[t] = sum;
+            } else if (sum < (int64_t)__ldcg(reinterpret_cast<const long long *>(a.cost + t))) {
+                for (int w = lane; w < W; w += 32)
+                    a.X[t * W + w] = __ldcg(a.Xc + t * W + w);
+                if (lane == 0)
+                    a.cost[t] = sum;
+            }
+        }
+        __syncthreads();
+    }
+    return grid_barrier(a.bar, a.err, ok_s);
+}
+
+template <int G>
+__global__ void __launch_bounds__(kFusedThreads, 1) k_ga_fused(const __grid_constant__ FusedArgs a)
+{
+    extern __shared__ __align__(16) uint32_t fsm[];
+    __shared__ unsigned long long acc_s[G * 32];
+    __shared__ uint32_t a0_s[G], fin_s[G];
+    __shared__ uint32_t on_s;
+    __shared__ unsigned long long tries_s;
+    __shared__ int ok_s;
+    __shared__ long long sc[32], si[32];
+    __shared__ long long win_s;
+    __shared__ int improve_s;
+    const ga_prob &gp = a.gp;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int32_t W = gp.W, p = gp.p;
+    const int64_t P = gp.pop, QP = a.gq.pop;
+    const int64_t groups = (P + 31) / 32, groupsQ = (QP + 31) / 32;
+    ga_dev *st = a.st;
+    ColumnsOut co{a.colT, G}, coQ{a.colQ, G};
+    if (a.stall) {
+        // failure-detection tests: CTA 0 never arrives, so the first barrier runs out (after kStallTimeoutNs)
+        // in every other CTA, which records PM_ERR_TIMEOUT and leaves; nothing is in flight
+        if (blockIdx.x == 0)
+            return;
+        grid_barrier(a.bar, a.err, &ok_s, kStallTimeoutNs);
+        return;
+    }
+    for (;;) {
+        // every CTA reads what the last barrier published (or k_ga_begin, before the launch)
+        const long long remaining = __ldcg(&a.glob->remaining);
+        const int stop = __ldcg(&st->stop);
+        if (remaining <= 0 || stop)
+            return;
+        const uint32_t gen = (uint32_t)__ldcg(&st->gen);
+
+        // ---- A2: fresh population with migration: rows, facility-major copy, active bits ----
+        for (int64_t vb = blockIdx.x; vb < groups; vb += gridDim.x) {
+            const int64_t t0 = vb * 32, t = t0 + warp;
+            uint32_t *row = fsm + (int64_t)warp * W;
+            uint32_t *draws = fsm + (int64_t)32 * W + (int64_t)warp * p;
+            if (t < P) {
+                if (lane == 0)
+                    a.improved[t] = 0;
+                fresh_individual<true>(gp, t, gen, a.seed, a.deme_best, row, draws, lane);
+                for (int w = lane; w < W; w += 32)
+                    a.X[t * W + w] = row[w];
+            }
+            __syncthreads();
+            if (threadIdx.x == 0)
+                a.active[vb] = (P - t0 >= 32) ? 0xffffffffu : ((1u << (P - t0)) - 1u);
+            write_columns(fsm, W, t0, gp, co, lane, warp, nwarps);
+            __syncthreads();
+        }
+        if (!grid_barrier(a.bar, a.err, &ok_s))
+            return;
+        // ---- A3: evaluation ----
+        if (!fused_scan<G>(a, kScanStore, fsm, acc_s, a0_s, fin_s, &ok_s))
+            return;
+        // ---- A4: crossover rounds (children from the population as the round starts; acceptance) ----
+        if (p / 2 > 0) {
+            for (int32_t r = 0; r < a.R; ++r) {
+                const int64_t stride = gp.D >> (1 + (r % gp.lgD));
+                for (int64_t vb = blockIdx.x; vb < groups; vb += gridDim.x) {
+                    const int64_t t0 = vb * 32, t = t0 + warp;
+                    uint32_t *row = fsm + (int64_t)warp * W;
+                    if (threadIdx.x == 0)
+                        on_s = 0u;
+                    __syncthreads();
+                    if (t < P) {
+                        const int64_t partner = t ^ stride;
+                        const uint32_t pair = (uint32_t)(t < partner ? t : partner);
+                        const uint4 v = draw_block(a.seed, gen, pair, OP_XOVER + (uint32_t)r, 0, gp.sid);
+                        const uint32_t r1 = uniform_below(v.x, (uint32_t)gp.m);
+                        const int i = 1 + (int)uniform_below(v.y, (uint32_t)(p / 2));
+                        const bool ok = crossover_child<true>(a.X + t * W, a.X + partner * W, row, W, r1, i, lane);
+                        __syncwarp();
+                        for (int w = lane; w < W; w += 32)
+                            a.Xc[t * W + w] = row[w];
+                        if (lane == 0 && ok)
+                            atomicOr(&on_s, 1u << warp);
+                    } else {
+                        for (int w = lane; w < W; w += 32)
+                            row[w] = 0u;
+                    }
+                    __syncthreads();
+                    if (threadIdx.x == 0) {
+                        a.active[vb] = on_s;
+                        if (on_s)
+                            atomicAdd(reinterpret_cast<unsigned long long *>(&st->evals),
+                                      (unsigned long long)__popc(on_s));
+                    }
+                    write_columns(fsm, W, t0, gp, co, lane, warp, nwarps);
+                    __syncthreads();
+                }
+                if (!grid_barrier(a.bar, a.err, &ok_s))
+                    return;
+                if (!fused_scan<G>(a, kScanAccept, fsm, acc_s, a0_s, fin_s, &ok_s))
+                    return;
+            }
+        }
+        // ---- A5: every mutation try of every individual, one scan, first improving try ----
+        for (int64_t vb = blockIdx.x; vb < groupsQ; vb += gridDim.x) {
+            const int64_t u0 = vb * 32, u = u0 + warp;
+            uint32_t *row = fsm + (int64_t)warp * W;
+            if (threadIdx.x == 0)
+                on_s = 0u;
+            __syncthreads();
+            bool built = false;
+            if (u < QP) {
+                const int64_t q = u / P, t = u - q * P;
+                if (__ldcg(a.improved + t) == 0) {
+                    mutant_row<true>(a.X + t * W, row, W, gp.m, a.seed, gen, (uint32_t)t, (uint32_t)q, gp.sid, lane);
+                    __syncwarp();
+                    for (int w = lane; w < W; w += 32)
+                        a.XQ[u * W + w] = row[w];
+                    if (lane == 0)
+                        atomicOr(&on_s, 1u << warp);
+                    built = true;
+                }
+            }
+            if (!built)
+                for (int w = lane; w < W; w += 32)
+                    row[w] = 0u;
+            __syncthreads();
+            if (threadIdx.x == 0)
+                a.activeQ[vb] = on_s;
+            write_columns(fsm, W, u0, a.gq, coQ, lane, warp, nwarps);
+            __syncthreads();
+        }
+        if (!grid_barrier(a.bar, a.err, &ok_s))
+            return;
+        if (!fused_scan<G>(a, kScanCandidates, fsm, acc_s, a0_s, fin_s, &ok_s))
+            return;
+        for (int64_t vb = blockIdx.x; vb < groups; vb += gridDim.x) {
+            const int64_t t = vb * 32 + warp;
+            if (threadIdx.x == 0)
+                tries_s = 0ull;
+            __syncthreads();
+            if (t < P && __ldcg(a.improved + t) == 0) {
+                const int64_t c0 = __ldcg(reinterpret_cast<const long long *>(a.cost + t));
+                int qs = a.Q;
+                for (int base = 0; base < a.Q; base += 32) {
+                    const int q = base + lane;
+                    const bool hit =
+                        q < a.Q && __ldcg(reinterpret_cast<const long long *>(a.costQ + (int64_t)q * P + t)) < c0;
+                    const uint32_t b = __ballot_sync(PM_FULL_MASK, hit);
+                    if (b) {
+                        qs = base + __ffs(b) - 1;
+                        break;
+                    }
+                }
+                if (qs < a.Q) {
+                    const int64_t u = (int64_t)qs * P + t;
+                    for (int w = lane; w < W; w += 32)
+                        a.X[t * W + w] = __ldcg(a.XQ + u * W + w);
+                    if (lane == 0) {
+                        a.cost[t] = __ldcg(reinterpret_cast<const long long *>(a.costQ + u));
+                        a.improved[t] = 1;
+                    }
+                }
+                if (lane == 0)
+                    atomicAdd(&tries_s, (unsigned long long)(qs < a.Q ? qs + 1 : a.Q));
+            }
+            __syncthreads();
+            if (threadIdx.x == 0 && tries_s)
+                atomicAdd(reinterpret_cast<unsigned long long *>(&st->evals), tries_s);
+        }
+        if (!grid_barrier(a.bar, a.err, &ok_s))
+            return;
+        // ---- A6: deme bests (lowest cost, then lowest index) ----
+        for (int64_t b = blockIdx.x; b < gp.NB; b += gridDim.x) {
+            long long bc = 0x7fffffffffffffffLL, bi = 0x7fffffffffffffffLL;
+            for (int64_t i = threadIdx.x; i < gp.D; i += blockDim.x) {
+                const int64_t t = b * gp.D + i;
+                const long long c = __ldcg(reinterpret_cast<const long long *>(a.cost + t));
+                if (c < bc || (c == bc && t < bi)) {
+                    bc = c;
+                    bi = t;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const long long oc = __shfl_xor_sync(PM_FULL_MASK, bc, o);
+                const long long oi = __shfl_xor_sync(PM_FULL_MASK, bi, o);
+                if (oc < bc || (oc == bc && oi < bi)) {
+                    bc = oc;
+                    bi = oi;
+                }
+            }
+            if (lane == 0) {
+                sc[warp] = bc;
+                si[warp] = bi;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                for (int w = 1; w < nwarps; ++w)
+                    if (sc[w] < bc || (sc[w] == bc && si[w] < bi)) {
+                        bc = sc[w];
+                        bi = si[w];
+                    }
+                win_s = bi;
+                a.deme_cost[b] = bc;
+            }
+            __syncthreads();
+            for (int w = threadIdx.x; w < W; w += blockDim.x)
+                a.deme_best[b * W + w] = __ldcg(a.X + win_s * W + w);
+            __syncthreads();
+        }
+        if (!grid_barrier(a.bar, a.err, &ok_s))
+            return;
+        // ---- global best, saturation, trace, counters (one CTA) ----
+        if (blockIdx.x == 0) {
+            long long bc = 0x7fffffffffffffffLL, bi = 0x7fffffffffffffffLL;
+            for (int64_t d = threadIdx.x; d < gp.NB; d += blockDim.x) {
+                const long long c = __ldcg(reinterpret_cast<const long long *>(a.deme_cost) + d);
+                if (c < bc || (c == bc && d < bi)) {
+                    bc = c;
+                    bi = d;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const long long oc = __shfl_xor_sync(PM_FULL_MASK, bc, o);
+                const long long oi = __shfl_xor_sync(PM_FULL_MASK, bi, o);
+                if (oc < bc || (oc == bc && oi < bi)) {
+                    bc = oc;
+                    bi = oi;
+                }
+            }
+            if (lane == 0) {
+                sc[warp] = bc;
+                si[warp] = bi;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                for (int w = 1; w < nwarps; ++w)
+                    if (sc[w] < bc || (sc[w] == bc && si[w] < bi)) {
+                        bc = sc[w];
+                        bi = si[w];
+                    }
+                const long long prev = __ldcg(&st->best_cost);
+                const bool better = prev < 0 || bc < prev;
+                improve_s = better ? 1 : 0;
+                win_s = bi;
+                long long sat = __ldcg(&st->sat);
+                if (better) {
+                    st->best_cost = bc;
+                    sat = 0;
+                } else {
+                    sat += 1;
+                }
+                st->sat = sat;
+                const long long step = __ldcg(&a.glob->step_gens);
+                if (st->trace)
+                    st->trace[step] = better ? bc : prev;
+                // the generation's initial evaluation (the crossover and mutation phases added theirs atomically)
+                atomicAdd(reinterpret_cast<unsigned long long *>(&st->evals), (unsigned long long)P);
+                st->gen = (long long)gen + 1;
+                st->total_gens = __ldcg(&st->total_gens) + 1;
+                const long long S = st->saturation;
+                const int stopped = (S > 0 && sat >= S) ? 1 : 0;
+                st->stop = stopped;
+                a.glob->alive = stopped ? 0 : 1;
+                a.glob->step_gens = step + 1;
+                a.glob->remaining = __ldcg(&a.glob->remaining) - 1;
+            }
+            __syncthreads();
+            if (improve_s)
+                for (int w = threadIdx.x; w < W; w += blockDim.x)
+                    a.best[w] = __ldcg(a.deme_best + win_s * W + w);
+        }
+        if (!grid_barrier(a.bar, a.err, &ok_s))
+            return;
+    }
+}
+
+
 // Uniform random p-subsets (Floyd sampling, generation 0, no migration), one
 // thread per individual, bitsets written in place.
 __global__ void k_random_population(uint32_t *__restrict__ X, int64_t P, int32_t W, int32_t m, int32_t p,
@@ -1292,6 +1840,13 @@ struct pm_ga {
     int64_t groups_total = 0, demes_total = 0, dwords_total = 0, best_total = 0, Wmax = 0;
     pm_dbuf X, Xc, cost, active, improved, deme_best, deme_cost, best, trace, accum, tickets, columns, st, glob, err,
         probs, gprobs;
+    // the persistent generation kernel (one cooperative launch per pm_ga_step) when the GA qualifies
+    bool fused = false;
+    int fused_G = 4;
+    unsigned fused_grid = 0;
+    size_t fused_smem = 0;
+    int64_t f_tiles = 0, f_splits = 1, f_cps = 0, f_tilesQ = 0, f_splitsQ = 1, f_cpsQ = 0;
+    pm_dbuf bar;
     // learned swap proposal (single-instance GAs)
     pm_model *model = nullptr;
     int T = 4;
@@ -1317,7 +1872,8 @@ static void ga_free(pm_ga *ga)
                        &ga->deme_cost, &ga->best, &ga->trace, &ga->accum,  &ga->tickets,  &ga->columns,
                        &ga->st,        &ga->glob, &ga->err,   &ga->probs,  &ga->gprobs,
                        &ga->s_gain,    &ga->s_cap, &ga->s_loss, &ga->s_assign, &ga->moves, &ga->xfeat, &ga->scores,
-                       &ga->comb_tab,  &ga->XQ,    &ga->costQ, &ga->activeQ, &ga->accumQ, &ga->ticketsQ, &ga->colQ};
+                       &ga->comb_tab,  &ga->XQ,    &ga->costQ, &ga->activeQ, &ga->accumQ, &ga->ticketsQ, &ga->colQ,
+                       &ga->bar};
     for (pm_dbuf *b : bufs)
         b->release();
     delete ga;
@@ -1662,6 +2218,148 @@ static pm_status spec_alloc(pm_ga *ga, cudaStream_t s)
     return PM_OK;
 }
 
+// PM_GA_FUSED=0 in the environment keeps the per-phase kernels (and the graph) for every GA, for comparison.
+static bool fused_allowed()
+{
+    const char *v = std::getenv("PM_GA_FUSED");
+    return !(v && v[0] == '0');
+}
+
+// Client splits of a persistent scan over `tiles` tiles on `grid` CTAs: the S (1 <= S <= smax) that minimises
+// the items a CTA walks per split, ceil(tiles * S / grid) / S, the smallest S on ties (fewer, larger items).
+static int64_t fused_splits(int64_t tiles, int64_t grid, int64_t smax)
+{
+    int64_t best = 1;
+    double best_cost = 1e300;
+    for (int64_t S = 1; S <= std::max<int64_t>(smax, 1); ++S) {
+        const double c = (double)pm_ceil_div(tiles * S, grid) / (double)S;
+        if (c < best_cost - 1e-12) {
+            best_cost = c;
+            best = S;
+        }
+    }
+    return best;
+}
+
+template <int G>
+static const void *fused_fn()
+{
+    return reinterpret_cast<const void *>(k_ga_fused<G>);
+}
+
+// Decide whether this GA runs its generations in the persistent kernel, and size it: one instance on the
+// column path with the speculative mutation cycle, Floyd generation, no learned try, the packed split
+// reduction, and a device that supports cooperative launches with one 1024-thread CTA per SM resident.
+static pm_status fused_prepare(pm_ga *ga, cudaStream_t s)
+{
+    ga->fused = false;
+    if (!fused_allowed() || ga->K != 1 || ga->single_row || !ga->spec || ga->model || ga->comb)
+        return PM_OK;
+    const pm_instance *inst = ga->insts[0];
+    const int G = ga->plan.groups;
+    if (G != 1 && G != 2 && G != 4)
+        return PM_OK;
+    int coop = 0;
+    PM_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, inst->device));
+    if (!coop)
+        return PM_OK;
+    const int64_t W = inst->W, P = ga->P, QP = (int64_t)ga->Q * P;
+    const size_t smem = (size_t)std::max<int64_t>(32 * W * G, 32 * (W + inst->p)) * 4;
+    if (smem > 200 * 1024)
+        return PM_OK;
+    const void *fn = G == 4 ? fused_fn<4>() : (G == 2 ? fused_fn<2>() : fused_fn<1>());
+    PM_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    PM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kFusedThreads, smem));
+    if (per_sm < 1)
+        return PM_OK;
+    const int64_t grid = (int64_t)per_sm * inst->sm_count;
+    const int64_t smax = std::max<int64_t>(1, inst->n / (kFusedThreads / 32));  // every warp gets a client
+    ga->f_tiles = pm_ceil_div(P, 32 * G);
+    ga->f_splits = fused_splits(ga->f_tiles, grid, smax);
+    ga->f_cps = pm_ceil_div(inst->n, ga->f_splits);
+    ga->f_tilesQ = pm_ceil_div(QP, 32 * G);
+    ga->f_splitsQ = fused_splits(ga->f_tilesQ, grid, smax);
+    ga->f_cpsQ = pm_ceil_div(inst->n, ga->f_splitsQ);
+    if (!pm_packed_reduction_ok(inst, std::max(ga->f_splits, ga->f_splitsQ)))
+        return PM_OK;
+    // the candidates' facility-major copy in this G, the population's in the plan's G (the same G)
+    PM_TRY(ga->colQ.reserve((size_t)ga->f_tilesQ * W * 32 * G * 4));
+    PM_TRY(ga->bar.reserve(256));
+    PM_CUDA(cudaMemsetAsync(ga->bar.ptr, 0, 256, s));
+    PM_CUDA(cudaStreamSynchronize(s));
+    ga->fused_G = G;
+    ga->fused_grid = (unsigned)grid;
+    ga->fused_smem = smem;
+    ga->fused = true;
+    return PM_OK;
+}
+
+static pm_status fused_launch(pm_ga *ga, cudaStream_t s)
+{
+    const pm_instance *inst = ga->insts[0];
+    FusedArgs a{};
+    a.gp = ga->gps[0];
+    a.gq = ga->gq;
+    a.pi = inst->pi;
+    a.delta = inst->delta;
+    a.n = inst->n;
+    a.stride = inst->stride;
+    a.L = (int32_t)inst->L;
+    a.cum = inst->cum ? 1 : 0;
+    a.tiles = ga->f_tiles;
+    a.splits = ga->f_splits;
+    a.cps = ga->f_cps;
+    a.tilesQ = ga->f_tilesQ;
+    a.splitsQ = ga->f_splitsQ;
+    a.cpsQ = ga->f_cpsQ;
+    a.R = ga->gps[0].p / 2 > 0 ? ga->R : 0;
+    a.Q = ga->Q;
+    a.seed = ga->seed;
+    a.X = static_cast<uint32_t *>(ga->X.ptr);
+    a.Xc = static_cast<uint32_t *>(ga->Xc.ptr);
+    a.XQ = static_cast<uint32_t *>(ga->XQ.ptr);
+    a.colT = static_cast<uint32_t *>(ga->columns.ptr);
+    a.colQ = static_cast<uint32_t *>(ga->colQ.ptr);
+    a.active = static_cast<uint32_t *>(ga->active.ptr);
+    a.activeQ = static_cast<uint32_t *>(ga->activeQ.ptr);
+    a.cost = static_cast<int64_t *>(ga->cost.ptr);
+    a.costQ = static_cast<int64_t *>(ga->costQ.ptr);
+    a.accum = static_cast<unsigned long long *>(ga->accum.ptr);
+    a.accumQ = static_cast<unsigned long long *>(ga->accumQ.ptr);
+    a.improved = static_cast<uint8_t *>(ga->improved.ptr);
+    a.deme_best = static_cast<uint32_t *>(ga->deme_best.ptr);
+    a.deme_cost = static_cast<int64_t *>(ga->deme_cost.ptr);
+    a.best = static_cast<uint32_t *>(ga->best.ptr);
+    a.st = static_cast<ga_dev *>(ga->st.ptr);
+    a.glob = static_cast<ga_glob *>(ga->glob.ptr);
+    a.bar = static_cast<unsigned *>(ga->bar.ptr);
+    a.err = static_cast<int *>(ga->err.ptr);
+    a.stall = pm_take_scan_stall() ? 1u : 0u;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ga->fused_grid);
+    cfg.blockDim = dim3(kFusedThreads);
+    cfg.dynamicSmemBytes = ga->fused_smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    switch (ga->fused_G) {
+    case 1:
+        PM_CUDA(cudaLaunchKernelEx(&cfg, k_ga_fused<1>, a));
+        break;
+    case 2:
+        PM_CUDA(cudaLaunchKernelEx(&cfg, k_ga_fused<2>, a));
+        break;
+    default:
+        PM_CUDA(cudaLaunchKernelEx(&cfg, k_ga_fused<4>, a));
+        break;
+    }
+    return PM_OK;
+}
+
 static pm_status ga_create_common(pm_ga *ga, cudaStream_t s)
 {
     // the warp-per-individual initialisation may use up to 200 KB of shared memory (set outside any capture)
@@ -1675,6 +2373,8 @@ static pm_status ga_create_common(pm_ga *ga, cudaStream_t s)
         cudaGetLastError();
         ga->spec = false;
     }
+    if (st == PM_OK)
+        st = fused_prepare(ga, s);
     if (st == PM_OK)
         st = build_graph(ga);
     return st;
@@ -1825,7 +2525,7 @@ static pm_status check_err(pm_ga *ga, cudaStream_t s)
     PM_CUDA(cudaStreamSynchronize(s));
     if (!e)
         return PM_OK;
-    pm_dbuf *bufs[] = {&ga->err, &ga->accum, &ga->tickets, &ga->accumQ, &ga->ticketsQ};
+    pm_dbuf *bufs[] = {&ga->err, &ga->accum, &ga->tickets, &ga->accumQ, &ga->ticketsQ, &ga->bar};
     for (pm_dbuf *b : bufs)
         if (b->ptr)
             PM_CUDA(cudaMemsetAsync(b->ptr, 0, b->bytes, s));
@@ -1852,9 +2552,12 @@ extern "C" pm_status pm_ga_step(pm_ga *ga, int64_t gens, int64_t *trace, void *s
     }
     k_ga_begin<<<(unsigned)pm_ceil_div(ga->K, 256), 256, 0, s>>>(static_cast<ga_glob *>(ga->glob.ptr),
                                                                 static_cast<ga_dev *>(ga->st.ptr), ga->K,
-                                                                (long long)gens, tr);
+                                                                (long long)gens, tr,
+                                                                static_cast<unsigned *>(ga->bar.ptr));
     PM_CUDA(cudaGetLastError());
-    if (graph_mode()) {
+    if (ga->fused) {
+        PM_TRY(fused_launch(ga, s));
+    } else if (graph_mode()) {
         PM_CUDA(cudaGraphLaunch(ga->exec, s));
     } else {
         // the same kernels, enqueued generation by generation (profilers cannot see
@@ -2062,6 +2765,13 @@ extern "C" pm_status pm_ga_info(const pm_ga *ga, int64_t *pop, int64_t *deme, in
         *xover_rounds = ga->R;
     if (mut_tries)
         *mut_tries = ga->Q;
+    if (ga->fused) {  // k_ga_begin and one persistent launch per call, whatever the number of generations
+        if (kernels_per_generation)
+            *kernels_per_generation = 0;
+        if (kernels_per_step_call)
+            *kernels_per_step_call = 2;
+        return PM_OK;
+    }
     if (kernels_per_generation)
         *kernels_per_generation = 1 + per_eval + rounds * (1 + per_eval) +
                                   (ga->spec ? 3 : ga->Q * (1 + per_eval)) + 1 + (ga->model ? 4 + per_eval : 0);

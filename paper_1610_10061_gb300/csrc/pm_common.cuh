@@ -202,6 +202,8 @@ pm_status pm_launch_columns(const pm_instance *inst, const pm_eval_plan &plan, c
 size_t pm_plan_column_bytes(const pm_instance *inst, const pm_eval_plan &plan);
 // One-time per-process kernel attributes (dynamic shared memory opt-in).
 pm_status pm_fitness_init(const pm_instance *inst);
+// Consume one launch armed by pm_debug_scan_timeout (true if one was armed).
+bool pm_take_scan_stall();
 // After a device-side failure of an evaluation on inst (its error word set): clear the error word and bring
 // the accumulators and tickets back to zero, so later evaluations start from a clean state.  Synchronises s.
 pm_status pm_reset_eval_scratch(pm_instance *inst, cudaStream_t s);

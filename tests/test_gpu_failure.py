@@ -88,9 +88,10 @@ def test_asynchronous_call_leaves_the_timeout_for_pm_eval_status(pm, name, d, p,
 
 
 def test_ga_reports_the_timeout_and_later_generations_evaluate_exactly(pm, monkeypatch):
-    """Stream mode (the graph keeps the launches it captured at creation): the generation whose first scan gave
-    up reports PM_ERR_TIMEOUT at the next synchronising call; the GA's scratch is reset, so the costs of later
-    generations equal the direct evaluation of their bitsets."""
+    """Per-phase kernels in stream mode (the graph keeps the launches it captured at creation): the generation
+    whose first scan gave up reports PM_ERR_TIMEOUT at the next synchronising call; the GA's scratch is reset, so
+    the costs of later generations equal the direct evaluation of their bitsets."""
+    monkeypatch.setenv("PM_GA_FUSED", "0")
     monkeypatch.setenv("PM_GA_GRAPH", "0")
     d = graph_instance(200, 600, seed=3)
     inst = pm.Instance(d, 8)
@@ -103,3 +104,30 @@ def test_ga_reports_the_timeout_and_later_generations_evaluate_exactly(pm, monke
     ga.step(3)
     masks, costs = ga.population()
     np.testing.assert_array_equal(costs, oracle.eval_direct(d, masks))
+
+
+def test_persistent_generation_kernel_barrier_timeout(pm):
+    """The persistent generation kernel's grid barrier: armed on the host, CTA 0 of the next launch leaves at once,
+    so every other CTA's bounded wait at the first barrier runs out (20 ms), records PM_ERR_TIMEOUT and leaves.
+    The next steps start from the same generation and run as usual: the population's costs equal the direct
+    evaluation and the GA continues like an untouched one."""
+    d = graph_instance(200, 600, seed=3)
+    inst = pm.Instance(d, 8)
+    ga = pm.GA(inst, seed=1, pop=256, deme=64)
+    assert ga.info()["kernels_per_generation"] == 0  # the persistent kernel runs this GA
+    ref = pm.GA(inst, seed=1, pop=256, deme=64)
+    ga.step(2)
+    ref.step(2)
+    pm.pm_debug_scan_timeout(1)
+    with pytest.raises(pm.PMError) as e:
+        ga.step(1)
+    assert e.value.status == PM_ERR_TIMEOUT
+    assert pm.pm_debug_scan_timeout(0) == 0
+    ga.step(3)
+    ref.step(3)
+    masks, costs = ga.population()
+    np.testing.assert_array_equal(costs, oracle.eval_direct(d, masks))
+    rm, rc = ref.population()
+    np.testing.assert_array_equal(masks, rm)
+    np.testing.assert_array_equal(costs, rc)
+    assert ga.result()[:3] == ref.result()[:3]

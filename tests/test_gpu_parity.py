@@ -312,7 +312,9 @@ def test_ga_save_load_resume(pm, migration):
 
 
 def test_ga_stream_launch_mode_matches_graph_mode(pm, monkeypatch):
-    """PM_GA_GRAPH=0 (direct stream launches, for profilers) gives the graph mode's results bit for bit."""
+    """PM_GA_GRAPH=0 (direct stream launches, for profilers) gives the graph mode's results bit for bit (both with
+    the per-phase kernels: PM_GA_FUSED=0)."""
+    monkeypatch.setenv("PM_GA_FUSED", "0")
     d = graph_instance(100, 200, seed=0)
     inst = pm.Instance(d, 5)
     a = pm.GA(inst, seed=3, pop=128, deme=32)
@@ -326,6 +328,53 @@ def test_ga_stream_launch_mode_matches_graph_mode(pm, monkeypatch):
     assert a.result()[:3] == b.result()[:3]
     # saturation stop in stream mode, against the oracle
     _ga_compare(pm, graph_instance(30, 60, seed=1), 3, 32, 300, check_every=300, deme=16, saturation=4)
+
+
+def _ga_run_pair(pm, monkeypatch, d, p, pop, gens, steps, **kw):
+    """The same GA twice, with the persistent generation kernel (default) and with the per-phase kernels
+    (PM_GA_FUSED=0): traces, populations, costs and results."""
+    inst = pm.Instance(d, p, cumulative=kw.pop("cumulative", False))
+    out = []
+    for fused in (True, False):
+        if fused:
+            monkeypatch.delenv("PM_GA_FUSED", raising=False)
+        else:
+            monkeypatch.setenv("PM_GA_FUSED", "0")
+        ga = pm.GA(inst, pop=pop, **kw)
+        info = ga.info()
+        assert (info["kernels_per_generation"] == 0) == fused, info
+        traces = [ga.step(k) for k in steps]
+        out.append((np.concatenate(traces), *ga.population(), ga.result()))
+        ga.close()
+    monkeypatch.delenv("PM_GA_FUSED", raising=False)
+    (ta, ma, ca, ra), (tb, mb, cb, rb) = out
+    np.testing.assert_array_equal(ta, tb)
+    np.testing.assert_array_equal(ma, mb)
+    np.testing.assert_array_equal(ca, cb)
+    assert ra[:3] == rb[:3]
+    np.testing.assert_array_equal(ra[3], rb[3])
+    return ta
+
+
+@pytest.mark.parametrize("case", ["graph900", "euclid_ragged", "team_cum", "deme2", "p1_sat"])
+def test_persistent_generation_kernel_equals_the_per_phase_kernels(pm, monkeypatch, case):
+    """One cooperative launch per pm_ga_step (grid barriers between the phases) against the per-phase kernels:
+    bit-identical GA at the benchmark's shape, a ragged population, migration variant (ii) on cumulative tables,
+    demes of 2, and p = 1 with a saturation stop inside a step."""
+    if case == "graph900":
+        w = paper_shape_instance("graph900")
+        _ga_run_pair(pm, monkeypatch, w["d"], w["p"], 1024, 6, [1, 2, 3], seed=3, deme=256)
+    elif case == "euclid_ragged":
+        _ga_run_pair(pm, monkeypatch, euclid_instance(333, seed=4), 17, 96, 5, [2, 3], seed=1, deme=32)
+    elif case == "team_cum":
+        _ga_run_pair(pm, monkeypatch, graph_instance(150, 400, seed=2), 9, 256, 4, [4], seed=2, deme=16,
+                     migration="team", cumulative=True)
+    elif case == "deme2":
+        _ga_run_pair(pm, monkeypatch, euclid_instance(70, seed=6), 5, 64, 5, [5], seed=7, deme=2)
+    else:
+        tr = _ga_run_pair(pm, monkeypatch, graph_instance(45, 100, seed=4), 1, 64, 300, [300], seed=5, deme=16,
+                          saturation=3)
+        assert len(tr) < 300
 
 
 @pytest.mark.parametrize("name,d,p", [s for s in _shapes() if s[0] in ("ties", "p1", "graph", "euclid")],
