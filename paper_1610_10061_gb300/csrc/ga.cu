@@ -2453,7 +2453,7 @@ extern "C" pm_status pm_ga_create(pm_instance *inst, uint64_t seed, int64_t pop,
         ga->single = pm_plan_eval(inst, pop);
         ga->single_row = ga->single.groups == 0;
         ga->plan = pm_plan_from_single(inst, ga->single, pop);
-        if (!ga->single_row && ga->Q > 1 && spec_allowed()) {
+        if (!ga->single_row && ga->Q >= 1 && spec_allowed()) {
             const int64_t QP = (int64_t)ga->Q * pop;
             if (params && (params->flags & PM_GA_TUNE))
                 st = pm_tune_eval(inst, QP, stream, nullptr);
