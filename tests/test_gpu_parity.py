@@ -552,6 +552,7 @@ def test_speculative_mutation_cycle_matches_try_by_try(pm, monkeypatch):
     w = paper_shape_instance("graph900")
     d, p = w["d"], w["p"]
     inst = pm.Instance(d, p)
+    monkeypatch.setenv("PM_GA_FUSED", "0")  # the per-phase kernels, whose launches are counted below
     a = pm.GA(inst, seed=17, pop=512, deme=128)
     ta = a.step(3)
     info = a.info()
