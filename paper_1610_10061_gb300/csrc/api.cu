@@ -80,7 +80,7 @@ pm_status pm_dbuf::reserve(size_t want, bool *fresh)
 void pm_dbuf::release()
 {
     if (ptr)
-        cudaFree(ptr);
+        pm_clear_error(cudaFree(ptr));
     ptr = nullptr;
     bytes = 0;
 }
@@ -125,11 +125,11 @@ static void destroy_instance(pm_instance *inst)
 {
     if (!inst)
         return;
-    cudaSetDevice(inst->device);
+    pm_clear_error(cudaSetDevice(inst->device));
     if (inst->pi)
-        cudaFree(inst->pi);
+        pm_clear_error(cudaFree(inst->pi));
     if (inst->delta)
-        cudaFree(inst->delta);
+        pm_clear_error(cudaFree(inst->delta));
     inst->stage_masks.release();
     inst->stage_costs.release();
     inst->partials.release();
@@ -295,6 +295,7 @@ extern "C" pm_status pm_columns_layout(pm_instance *inst, int64_t pop, int32_t *
 extern "C" pm_status pm_population_columns(pm_instance *inst, const uint32_t *masks, int64_t pop, uint32_t *cols,
                                            void *stream)
 {
+    pm_clear_stale_error();
     if (!inst || pop < 1 || !masks || !cols || !pm_is_device_ptr(masks) || !pm_is_device_ptr(cols))
         return PM_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> guard(inst->lock);
@@ -305,6 +306,7 @@ extern "C" pm_status pm_population_columns(pm_instance *inst, const uint32_t *ma
 extern "C" pm_status pm_eval_columns(pm_instance *inst, const uint32_t *cols, int64_t pop, int64_t *costs,
                                      void *stream)
 {
+    pm_clear_stale_error();
     if (!inst || pop < 1 || !cols || !costs || !pm_is_device_ptr(cols) || !pm_is_device_ptr(costs))
         return PM_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> guard(inst->lock);
@@ -330,6 +332,7 @@ extern "C" pm_status pm_eval_columns(pm_instance *inst, const uint32_t *cols, in
 extern "C" pm_status pm_eval_population(pm_instance *inst, const uint32_t *masks, int64_t pop, int64_t *costs,
                                         int checked, void *stream)
 {
+    pm_clear_stale_error();
     if (!inst || pop < 0)
         return PM_ERR_INVALID_ARG;
     if (pop == 0)

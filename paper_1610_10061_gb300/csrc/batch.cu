@@ -213,7 +213,7 @@ extern "C" pm_status pm_batch_destroy(pm_batch *b)
 {
     if (!b)
         return PM_OK;
-    cudaSetDevice(b->device);
+    pm_clear_error(cudaSetDevice(b->device));
     pm_dbuf *bufs[] = {&b->probs, &b->accum, &b->tickets, &b->columns, &b->err, &b->stage_masks, &b->stage_costs};
     for (pm_dbuf *x : bufs)
         x->release();

@@ -1294,7 +1294,7 @@ __global__ void __launch_bounds__(1024) k_ga_learned_pick(const ga_prob *__restr
 constexpr int kFusedThreads = 1024;
 constexpr uint64_t kBarrierTimeoutNs = 4000000000ull;  // a grid barrier gives up after 4 s
 constexpr uint64_t kStallTimeoutNs = 20000000ull;      // 20 ms in a launch armed by pm_debug_scan_timeout
-constexpr uint32_t kBarrierSpinCap = 1u << 26;         // and after this many polls whatever the timer says
+constexpr uint32_t kBarrierSpinCap = 1u << 23;         // and after this many polls whatever the timer says
 
 struct FusedArgs {
     ga_prob gp;                      // the instance (bases 0)
@@ -1342,33 +1342,36 @@ __device__ __forceinline__ uint64_t global_ns()
     return t;
 }
 
-// Grid-wide barrier of the cooperative launch: thread 0 of every CTA arrives on bar[0]; the last arrival resets
-// it and advances bar[1]; the others poll bar[1] for at most kBarrierTimeoutNs (and kBarrierSpinCap polls), then
-// record PM_ERR_TIMEOUT and the CTA leaves (false).  Writes before the barrier are visible to L2 loads after it.
-__device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err, int *ok_s, uint64_t limit_ns = kBarrierTimeoutNs)
+// Grid-wide barrier of the cooperative launch.  bar[1] counts the barriers completed; every CTA read it once at
+// the start of the launch (no barrier completes before every CTA has arrived, so they all read the same value)
+// and counts its own barriers in *passed.  Thread 0 of each CTA arrives on bar[0] with a release-ordered atomic;
+// the last arrival resets bar[0] and publishes the new count with a release store; the others poll it with
+// acquire loads for at most limit_ns (and kBarrierSpinCap polls), then record PM_ERR_TIMEOUT and the CTA leaves
+// (false).  Writes before the barrier are visible to loads after it that bypass L1 (ld.cg) or acquire.
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err, int *ok_s, unsigned *passed,
+                                             uint64_t limit_ns = kBarrierTimeoutNs)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        const unsigned target = ld_acquire_u32(bar + 1) + 1u;
-        __threadfence();
-        if (atomicAdd(bar, 1u) + 1u == gridDim.x) {
-            atomicExch(bar, 0u);
-            __threadfence();
+        const unsigned target = *passed + 1u;
+        unsigned old;
+        asm volatile("atom.add.release.gpu.global.u32 %0, [%1], 1;" : "=r"(old) : "l"(bar) : "memory");
+        if (old + 1u == gridDim.x) {
+            bar[0] = 0u;  // ordered before the release below; nobody arrives again before seeing it
             st_release_u32(bar + 1, target);
         } else {
             const uint64_t t0 = global_ns();
             uint32_t spins = 0;
             while (ld_acquire_u32(bar + 1) != target) {
-                if (++spins > kBarrierSpinCap || global_ns() - t0 > limit_ns) {
+                if (++spins > kBarrierSpinCap || ((spins & 63u) == 0u && global_ns() - t0 > limit_ns)) {
                     atomicExch(err, (int)PM_ERR_TIMEOUT);
                     ok = 0;
                     break;
                 }
-                __nanosleep(64);
             }
         }
-        __threadfence();
+        *passed = target;
         *ok_s = ok;
     }
     __syncthreads();
@@ -1382,7 +1385,7 @@ enum FusedScanMode { kScanStore = 0, kScanAccept = 1, kScanCandidates = 2 };
 // the packed split reduction of the column kernel; then the grid barrier.
 template <int G>
 __device__ __forceinline__ bool fused_scan(const FusedArgs &a, int mode, uint32_t *colbits, unsigned long long *acc_s,
-                           uint32_t *a0_s, uint32_t *fin_s, int *ok_s)
+                                           uint32_t *a0_s, uint32_t *fin_s, int *ok_s, unsigned *passed_s)
 {
     const bool cand = mode == kScanCandidates;
     const int64_t tiles = cand ? a.tilesQ : a.tiles, splits = cand ? a.splitsQ : a.splits;
@@ -1497,7 +1500,7 @@ __device__ __forceinline__ bool fused_scan(const FusedArgs &a, int mode, uint32_
         }
         __syncthreads();
     }
-    return grid_barrier(a.bar, a.err, ok_s);
+    return grid_barrier(a.bar, a.err, ok_s, passed_s);
 }
 
 template <int G>
@@ -1512,6 +1515,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_ga_fused(const __grid_cons
     __shared__ long long sc[32], si[32];
     __shared__ long long win_s;
     __shared__ int improve_s;
+    __shared__ unsigned passed_s;  // barriers this CTA has passed (thread 0's count; the launch starts at bar[1])
+    if (threadIdx.x == 0)
+        passed_s = ld_acquire_u32(a.bar + 1);
     const ga_prob &gp = a.gp;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int32_t W = gp.W, p = gp.p;
@@ -1524,7 +1530,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_ga_fused(const __grid_cons
         // in every other CTA, which records PM_ERR_TIMEOUT and leaves; nothing is in flight
         if (blockIdx.x == 0)
             return;
-        grid_barrier(a.bar, a.err, &ok_s, kStallTimeoutNs);
+        grid_barrier(a.bar, a.err, &ok_s, &passed_s, kStallTimeoutNs);
         return;
     }
     for (;;) {
@@ -1553,10 +1559,10 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_ga_fused(const __grid_cons
             write_columns(fsm, W, t0, gp, co, lane, warp, nwarps);
             __syncthreads();
         }
-        if (!grid_barrier(a.bar, a.err, &ok_s))
+        if (!grid_barrier(a.bar, a.err, &ok_s, &passed_s))
             return;
         // ---- A3: evaluation ----
-        if (!fused_scan<G>(a, kScanStore, fsm, acc_s, a0_s, fin_s, &ok_s))
+        if (!fused_scan<G>(a, kScanStore, fsm, acc_s, a0_s, fin_s, &ok_s, &passed_s))
             return;
         // ---- A4: crossover rounds (children from the population as the round starts; acceptance) ----
         if (p / 2 > 0) {
@@ -1594,9 +1600,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_ga_fused(const __grid_cons
                     write_columns(fsm, W, t0, gp, co, lane, warp, nwarps);
                     __syncthreads();
                 }
-                if (!grid_barrier(a.bar, a.err, &ok_s))
+                if (!grid_barrier(a.bar, a.err, &ok_s, &passed_s))
                     return;
-                if (!fused_scan<G>(a, kScanAccept, fsm, acc_s, a0_s, fin_s, &ok_s))
+                if (!fused_scan<G>(a, kScanAccept, fsm, acc_s, a0_s, fin_s, &ok_s, &passed_s))
                     return;
             }
         }
@@ -1629,9 +1635,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_ga_fused(const __grid_cons
             write_columns(fsm, W, u0, a.gq, coQ, lane, warp, nwarps);
             __syncthreads();
         }
-        if (!grid_barrier(a.bar, a.err, &ok_s))
+        if (!grid_barrier(a.bar, a.err, &ok_s, &passed_s))
             return;
-        if (!fused_scan<G>(a, kScanCandidates, fsm, acc_s, a0_s, fin_s, &ok_s))
+        if (!fused_scan<G>(a, kScanCandidates, fsm, acc_s, a0_s, fin_s, &ok_s, &passed_s))
             return;
         for (int64_t vb = blockIdx.x; vb < groups; vb += gridDim.x) {
             const int64_t t = vb * 32 + warp;
@@ -1667,7 +1673,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_ga_fused(const __grid_cons
             if (threadIdx.x == 0 && tries_s)
                 atomicAdd(reinterpret_cast<unsigned long long *>(&st->evals), tries_s);
         }
-        if (!grid_barrier(a.bar, a.err, &ok_s))
+        if (!grid_barrier(a.bar, a.err, &ok_s, &passed_s))
             return;
         // ---- A6: deme bests (lowest cost, then lowest index) ----
         for (int64_t b = blockIdx.x; b < gp.NB; b += gridDim.x) {
@@ -1708,7 +1714,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_ga_fused(const __grid_cons
                 a.deme_best[b * W + w] = __ldcg(a.X + win_s * W + w);
             __syncthreads();
         }
-        if (!grid_barrier(a.bar, a.err, &ok_s))
+        if (!grid_barrier(a.bar, a.err, &ok_s, &passed_s))
             return;
         // ---- global best, saturation, trace, counters (one CTA) ----
         if (blockIdx.x == 0) {
@@ -1771,7 +1777,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_ga_fused(const __grid_cons
                 for (int w = threadIdx.x; w < W; w += blockDim.x)
                     a.best[w] = __ldcg(a.deme_best + win_s * W + w);
         }
-        if (!grid_barrier(a.bar, a.err, &ok_s))
+        if (!grid_barrier(a.bar, a.err, &ok_s, &passed_s))
             return;
     }
 }
@@ -1816,6 +1822,7 @@ pm_status pm_launch_random_population(const pm_instance *inst, uint64_t seed, in
 
 struct pm_ga {
     std::vector<pm_instance *> insts;
+    int device = 0;  // the instances' device (kept here: a GA may outlive the handles it was created on)
     int K = 1;
     uint64_t seed = 0;
     int64_t P = 0, D = 0, NB = 0;
@@ -1860,14 +1867,13 @@ static void ga_free(pm_ga *ga)
 {
     if (!ga)
         return;
-    if (!ga->insts.empty())
-        cudaSetDevice(ga->insts[0]->device);
+    pm_clear_error(cudaSetDevice(ga->device));
     if (ga->exec)
-        cudaGraphExecDestroy(ga->exec);
+        pm_clear_error(cudaGraphExecDestroy(ga->exec));
     if (ga->graph)
-        cudaGraphDestroy(ga->graph);
+        pm_clear_error(cudaGraphDestroy(ga->graph));
     if (ga->cap)
-        cudaStreamDestroy(ga->cap);
+        pm_clear_error(cudaStreamDestroy(ga->cap));
     pm_dbuf *bufs[] = {&ga->X,         &ga->Xc,   &ga->cost,  &ga->active, &ga->improved, &ga->deme_best,
                        &ga->deme_cost, &ga->best, &ga->trace, &ga->accum,  &ga->tickets,  &ga->columns,
                        &ga->st,        &ga->glob, &ga->err,   &ga->probs,  &ga->gprobs,
@@ -2430,6 +2436,7 @@ extern "C" pm_status pm_ga_create(pm_instance *inst, uint64_t seed, int64_t pop,
     if (!ga)
         return PM_ERR_OOM;
     ga->insts.push_back(inst);
+    ga->device = inst->device;
     ga->K = 1;
     pm_status st = ga_configure(ga, pop, seed, params);
     if (st == PM_OK && cudaSetDevice(inst->device) != cudaSuccess)
@@ -2487,6 +2494,7 @@ extern "C" pm_status pm_batch_ga_create(pm_batch *b, uint64_t seed, int64_t pop,
         return PM_ERR_OOM;
     for (const pm_instance *in : insts)
         ga->insts.push_back(const_cast<pm_instance *>(in));
+    ga->device = insts.empty() ? 0 : insts[0]->device;
     ga->K = (int)insts.size();
     pm_status st = ga_configure(ga, pop, seed, params);
     if (st == PM_OK && (ga->model || ga->comb))
@@ -2540,7 +2548,8 @@ extern "C" pm_status pm_ga_step(pm_ga *ga, int64_t gens, int64_t *trace, void *s
     if (gens == 0)
         return PM_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    PM_CUDA(cudaSetDevice(ga->insts[0]->device));
+    pm_clear_stale_error();
+    PM_CUDA(cudaSetDevice(ga->device));
     const bool trace_dev = trace && pm_is_device_ptr(trace);
     long long *tr = nullptr;
     const size_t tbytes = (size_t)gens * ga->K * 8;

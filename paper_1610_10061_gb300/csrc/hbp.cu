@@ -257,7 +257,7 @@ extern "C" pm_status pm_hbp_destroy(pm_hbp *h)
 {
     if (!h)
         return PM_OK;
-    cudaSetDevice(h->device);
+    pm_clear_error(cudaSetDevice(h->device));
     h->sets.release();
     h->coeffs.release();
     delete h;
@@ -335,6 +335,7 @@ extern "C" pm_status pm_hbp_create(pm_instance *inst, void *stream, pm_hbp **out
     if (inst->n * inst->L > kMaxTerms)
         return PM_ERR_UNSUPPORTED;
     std::lock_guard<std::mutex> guard(inst->lock);
+    pm_clear_stale_error();
     PM_CUDA(cudaSetDevice(inst->device));
     pm_hbp *h = new (std::nothrow) pm_hbp();
     if (!h)
@@ -386,6 +387,7 @@ extern "C" pm_status pm_hbp_eval(pm_hbp *h, const uint32_t *masks, int64_t pop, 
         return PM_OK;
     if (!masks || !costs || !pm_is_device_ptr(masks) || !pm_is_device_ptr(costs))
         return PM_ERR_INVALID_ARG;
+    pm_clear_stale_error();
     PM_CUDA(cudaSetDevice(h->device));
     const size_t smem = (size_t)h->W * 4;
     k_hbp_eval<<<(unsigned)pop, 256, smem, static_cast<cudaStream_t>(stream)>>>(

@@ -1385,7 +1385,7 @@ extern "C" pm_status pm_model_destroy(pm_model *md)
 {
     if (!md)
         return PM_OK;
-    cudaSetDevice(md->device);
+    pm_clear_error(cudaSetDevice(md->device));
     pm_dbuf *bufs[] = {&md->P, &md->M, &md->V, &md->G, &md->W1b, &md->W2b, &md->w3b, &md->loss, &md->err};
     for (pm_dbuf *b : bufs)
         b->release();

@@ -36,6 +36,16 @@
 
 void pm_note_cuda_error(cudaError_t e, const char *what, const char *file, int line);
 
+// A failed CUDA runtime call leaves its (non-sticky) error for the next cudaGetLastError of the thread, where
+// it would be taken for a failed launch.  Calls whose result is not needed (releases, device selection in
+// destroy paths) clear it; entry points that launch clear what other code left before their first launch.
+inline void pm_clear_error(cudaError_t e)
+{
+    if (e != cudaSuccess)
+        (void)cudaGetLastError();
+}
+inline void pm_clear_stale_error() { (void)cudaGetLastError(); }
+
 // A device buffer owned by the library that grows on demand.
 struct pm_dbuf {
     void *ptr = nullptr;
