@@ -261,16 +261,23 @@ static inline int64_t pm_round_up(int64_t a, int64_t b) { return pm_ceil_div(a, 
 
 // 32 x 32 bit-matrix transpose across a warp: on entry lane l holds row l
 // (bit c = element (l, c)); on exit lane c holds column c (bit l = element
-// (l, c)).  Five butterfly exchanges.
+// (l, c)).  Five butterfly exchanges; in exchange j (16, 8, 4, 2, 1) with the
+// partner lane l ^ j, the lane with bit j set keeps the upper j bits of each
+// 2j-bit block and takes the partner's upper j bits into the lower ones, the
+// other lane the reverse.  Rotating the partner's word by j (right for the
+// first lane, left for the second) puts exactly those bits in place, so an
+// exchange is a shuffle, a rotation by a per-lane amount and one masked merge.
 __device__ __forceinline__ uint32_t pm_transpose32(uint32_t x, int lane)
 {
     const uint32_t masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
 #pragma unroll
     for (int s = 0; s < 5; ++s) {
         const int j = 16 >> s;
-        const uint32_t m = masks[s];
+        const bool up = (lane & j) != 0;
+        const uint32_t keep = up ? ~masks[s] : masks[s];
         const uint32_t y = __shfl_xor_sync(PM_FULL_MASK, x, j);
-        x = (lane & j) ? ((x & ~m) | ((y & ~m) >> j)) : ((x & m) | ((y & m) << j));
+        const uint32_t r = __funnelshift_l(y, y, up ? 32 - j : j);  // y rotated right (up) or left by j
+        x = (x & keep) | (r & ~keep);
     }
     return x;
 }
