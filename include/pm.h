@@ -390,7 +390,11 @@ typedef struct pm_model pm_model;
  * tries are built and evaluated in one pass (Q x pop candidates; falls back
  * to try by try if they do not fit in memory, or with PM_GA_SPEC=0 in the
  * environment).  Results and the evaluation count -- the tries each
- * individual reaches -- are the same either way.
+ * individual reaches -- are the same either way.  With PM_GA_FUSED=1 in the
+ * environment, such a GA with Floyd generation and no model runs all the
+ * generations of a pm_ga_step call in one cooperative persistent launch,
+ * its phases separated by grid-wide barriers (bounded: PM_ERR_TIMEOUT after
+ * 4 s); the populations are the same.
  * Errors: PM_ERR_INVALID_ARG, PM_ERR_OOM, PM_ERR_CUDA; PM_ERR_UNSUPPORTED for
  * PM_GA_INIT_COMBINADIC beyond its limits.
  */

@@ -2224,11 +2224,13 @@ static pm_status spec_alloc(pm_ga *ga, cudaStream_t s)
     return PM_OK;
 }
 
-// PM_GA_FUSED=0 in the environment keeps the per-phase kernels (and the graph) for every GA, for comparison.
+// PM_GA_FUSED=1 in the environment runs qualifying GAs in the persistent kernel; by default every GA uses the
+// per-phase kernels and the graph, which measured faster on all but the largest scans (a grid barrier over
+// the whole GPU costs about as much as the kernel boundary it replaces).
 static bool fused_allowed()
 {
     const char *v = std::getenv("PM_GA_FUSED");
-    return !(v && v[0] == '0');
+    return v && v[0] == '1';
 }
 
 // Client splits of a persistent scan over `tiles` tiles on `grid` CTAs: the S (1 <= S <= smax) that minimises

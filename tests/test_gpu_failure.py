@@ -91,7 +91,6 @@ def test_ga_reports_the_timeout_and_later_generations_evaluate_exactly(pm, monke
     """Per-phase kernels in stream mode (the graph keeps the launches it captured at creation): the generation
     whose first scan gave up reports PM_ERR_TIMEOUT at the next synchronising call; the GA's scratch is reset, so
     the costs of later generations equal the direct evaluation of their bitsets."""
-    monkeypatch.setenv("PM_GA_FUSED", "0")
     monkeypatch.setenv("PM_GA_GRAPH", "0")
     d = graph_instance(200, 600, seed=3)
     inst = pm.Instance(d, 8)
@@ -106,11 +105,12 @@ def test_ga_reports_the_timeout_and_later_generations_evaluate_exactly(pm, monke
     np.testing.assert_array_equal(costs, oracle.eval_direct(d, masks))
 
 
-def test_persistent_generation_kernel_barrier_timeout(pm):
+def test_persistent_generation_kernel_barrier_timeout(pm, monkeypatch):
     """The persistent generation kernel's grid barrier: armed on the host, CTA 0 of the next launch leaves at once,
     so every other CTA's bounded wait at the first barrier runs out (20 ms), records PM_ERR_TIMEOUT and leaves.
     The next steps start from the same generation and run as usual: the population's costs equal the direct
     evaluation and the GA continues like an untouched one."""
+    monkeypatch.setenv("PM_GA_FUSED", "1")
     d = graph_instance(200, 600, seed=3)
     inst = pm.Instance(d, 8)
     ga = pm.GA(inst, seed=1, pop=256, deme=64)

@@ -312,9 +312,7 @@ def test_ga_save_load_resume(pm, migration):
 
 
 def test_ga_stream_launch_mode_matches_graph_mode(pm, monkeypatch):
-    """PM_GA_GRAPH=0 (direct stream launches, for profilers) gives the graph mode's results bit for bit (both with
-    the per-phase kernels: PM_GA_FUSED=0)."""
-    monkeypatch.setenv("PM_GA_FUSED", "0")
+    """PM_GA_GRAPH=0 (direct stream launches, for profilers) gives the graph mode's results bit for bit."""
     d = graph_instance(100, 200, seed=0)
     inst = pm.Instance(d, 5)
     a = pm.GA(inst, seed=3, pop=128, deme=32)
@@ -331,15 +329,15 @@ def test_ga_stream_launch_mode_matches_graph_mode(pm, monkeypatch):
 
 
 def _ga_run_pair(pm, monkeypatch, d, p, pop, gens, steps, **kw):
-    """The same GA twice, with the persistent generation kernel (default) and with the per-phase kernels
-    (PM_GA_FUSED=0): traces, populations, costs and results."""
+    """The same GA twice, with the persistent generation kernel (PM_GA_FUSED=1) and with the per-phase kernels
+    (the default): traces, populations, costs and results."""
     inst = pm.Instance(d, p, cumulative=kw.pop("cumulative", False))
     out = []
     for fused in (True, False):
         if fused:
-            monkeypatch.delenv("PM_GA_FUSED", raising=False)
+            monkeypatch.setenv("PM_GA_FUSED", "1")
         else:
-            monkeypatch.setenv("PM_GA_FUSED", "0")
+            monkeypatch.delenv("PM_GA_FUSED", raising=False)
         ga = pm.GA(inst, pop=pop, **kw)
         info = ga.info()
         assert (info["kernels_per_generation"] == 0) == fused, info
@@ -552,7 +550,6 @@ def test_speculative_mutation_cycle_matches_try_by_try(pm, monkeypatch):
     w = paper_shape_instance("graph900")
     d, p = w["d"], w["p"]
     inst = pm.Instance(d, p)
-    monkeypatch.setenv("PM_GA_FUSED", "0")  # the per-phase kernels, whose launches are counted below
     a = pm.GA(inst, seed=17, pop=512, deme=128)
     ta = a.step(3)
     info = a.info()
