@@ -394,4 +394,23 @@ pm_status pm_batch_ga_plan(pm_batch *b, int64_t pop, pm_multi_plan &out)
     return PM_OK;
 }
 
+// The speculative mutation cycle's candidates of a batched GA: popQ = Q x pop per instance, planned with the
+// tile shape the GA's own scans use (tuned for pop, or the default); costs indexed like the GA's.
+pm_status pm_batch_ga_plan_candidates(pm_batch *b, int64_t pop, int64_t popQ, pm_multi_plan &out)
+{
+    std::vector<int64_t> pv(b->insts.size(), pop), pq(b->insts.size(), popQ);
+    int G, warps, ips;
+    if (b->tuned_pops == pv) {
+        G = b->tuned_G;
+        warps = b->tuned_warps;
+        ips = b->tuned_ips;
+    } else {
+        default_shape(b, G, warps, ips);
+    }
+    PM_TRY(pm_plan_multi(b->insts, pq, G, warps, ips, out));
+    for (auto &pr : out.probs)
+        pr.out_base = pr.ind_base;
+    return PM_OK;
+}
+
 const std::vector<const pm_instance *> &pm_batch_instances(const pm_batch *b) { return b->insts; }

@@ -51,6 +51,7 @@
 
 // batch.cu
 pm_status pm_batch_ga_plan(pm_batch *b, int64_t pop, pm_multi_plan &out);
+pm_status pm_batch_ga_plan_candidates(pm_batch *b, int64_t pop, int64_t popQ, pm_multi_plan &out);
 // learn.cu
 pm_status pm_learn_prepare(const pm_instance *inst);
 pm_status pm_launch_swap_stats(const pm_instance *inst, const uint32_t *masks, int64_t pop, int64_t *gain,
@@ -949,31 +950,41 @@ __global__ void __launch_bounds__(1024) k_ga_mutate(const ga_prob *__restrict__ 
     write_columns(Xc + gp.word_base + t0 * W, W, t0, gp, co, lane, j, 32);
 }
 
-// Speculative mutation cycle (single-instance GAs on the column path).  Every
-// try mutates the individual as it stood when the cycle began (an individual
-// stops at its first strict improvement), so all Q tries of all individuals
-// can be built and evaluated at once and the first improving try kept:
-// candidate u = q * pop + t is try q of individual t.  The result and the
-// evaluation count (tries an individual reaches) equal the cycle run try by
-// try; the tries after an individual's first improvement are evaluated but
-// not counted.  CTA = 32 warps = 32 candidates; `gq` lays out the Q x pop
-// candidates (pop = Q * pop, all bases 0) for the columns.
-__global__ void __launch_bounds__(1024) k_ga_mutate_all(ga_prob gp, ga_prob gq, int32_t Q,
-                                                        const uint32_t *__restrict__ X, uint32_t *__restrict__ XQ,
-                                                        uint32_t *__restrict__ activeQ,
+// Speculative mutation cycle (GAs on the column path).  Every try mutates the
+// individual as it stood when the cycle began (an individual stops at its
+// first strict improvement), so all Q tries of all individuals can be built
+// and evaluated at once and the first improving try kept: candidate u =
+// q * pop + t of an instance is try q of its individual t.  The result and
+// the evaluation count (tries an individual reaches) equal the cycle run try
+// by try; the tries after an individual's first improvement are evaluated
+// but not counted.  CTA = 32 warps = 32 candidates of one instance; gqs[k]
+// (or oneq for one instance) lays out instance k's Q x pop candidates: their
+// rows, facility-major tiles, active bits and costs (ind_base), and their
+// first 32-candidate group (grp_base).
+__global__ void __launch_bounds__(1024) k_ga_mutate_all(const ga_prob *__restrict__ gps,
+                                                        const ga_prob *__restrict__ gqs, int K, ga_prob one,
+                                                        ga_prob oneq, int32_t Q, const uint32_t *__restrict__ X,
+                                                        uint32_t *__restrict__ XQ, uint32_t *__restrict__ activeQ,
                                                         const uint8_t *__restrict__ improved, uint64_t seed,
                                                         const ga_dev *__restrict__ st, ColumnsOut coQ)
 {
     pm_grid_dependency_wait();
     __shared__ uint32_t on_s;
+    int k = 0;
+    ga_prob gp = one, gq = oneq;
+    if (K > 1) {
+        k = find_k(K, blockIdx.x, [&](int i) { return gqs[i].grp_base; });
+        gp = gps[k];
+        gq = gqs[k];
+    }
     const int lane = threadIdx.x & 31;
     const int j = threadIdx.x >> 5;
-    const int64_t u0 = (int64_t)blockIdx.x * 32;
+    const int64_t u0 = ((int64_t)blockIdx.x - gq.grp_base) * 32;
     const int64_t u = u0 + j;
     const int32_t W = gp.W;
-    if (st[0].stop) {
+    if (st[k].stop) {
         if (threadIdx.x == 0)
-            activeQ[u0 >> 5] = 0u;
+            activeQ[(gq.ind_base + u0) >> 5] = 0u;
         return;
     }
     if (threadIdx.x == 0)
@@ -981,43 +992,52 @@ __global__ void __launch_bounds__(1024) k_ga_mutate_all(ga_prob gp, ga_prob gq, 
     __syncthreads();
     if (u < gq.pop) {
         const int64_t q = u / gp.pop, t = u - q * gp.pop;
-        if (improved[t] == 0) {
+        if (improved[gp.ind_base + t] == 0) {
             if (lane == 0)
                 atomicOr(&on_s, 1u << j);
-            mutant_row(X + t * W, XQ + u * W, W, gp.m, seed, (uint32_t)st[0].gen, (uint32_t)t, (uint32_t)q, gp.sid,
-                       lane);
+            mutant_row(X + gp.word_base + t * W, XQ + gq.word_base + u * W, W, gp.m, seed, (uint32_t)st[k].gen,
+                       (uint32_t)t, (uint32_t)q, gp.sid, lane);
         }
     }
     __syncthreads();
     if (threadIdx.x == 0)
-        activeQ[u0 >> 5] = on_s;
-    write_columns(XQ + u0 * W, W, u0, gq, coQ, lane, j, 32);
+        activeQ[(gq.ind_base + u0) >> 5] = on_s;
+    write_columns(XQ + gq.word_base + u0 * W, W, u0, gq, coQ, lane, j, 32);
 }
 
 // Keep each individual's first improving try (warp per individual, 8 per
-// CTA) and count the tries it reaches: q + 1 for an improvement at try q,
-// else Q; none for an individual already improved in this generation.
-__global__ void __launch_bounds__(256) k_ga_mutate_accept(ga_prob gp, int32_t Q, uint32_t *__restrict__ X,
+// CTA, individuals numbered as in the GA's scans: instance k's start at
+// gps[k].ind_base) and count the tries it reaches: q + 1 for an improvement
+// at try q, else Q; none for an individual already improved in this
+// generation.
+__global__ void __launch_bounds__(256) k_ga_mutate_accept(const ga_prob *__restrict__ gps,
+                                                          const ga_prob *__restrict__ gqs, int K, ga_prob one,
+                                                          ga_prob oneq, int32_t Q, uint32_t *__restrict__ X,
                                                           const uint32_t *__restrict__ XQ, int64_t *__restrict__ cost,
                                                           const int64_t *__restrict__ costQ,
                                                           uint8_t *__restrict__ improved, ga_dev *__restrict__ st)
 {
     pm_grid_dependency_wait();
     __shared__ unsigned long long tries_s;
+    __shared__ int k0_s;
     const int lane = threadIdx.x & 31;
-    const int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int32_t W = gp.W;
-    if (st[0].stop)
-        return;
-    if (threadIdx.x == 0)
+    const int64_t gi = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    auto inst_of = [&](int64_t x) { return K > 1 ? find_k(K, x, [&](int i) { return gps[i].ind_base; }) : 0; };
+    if (threadIdx.x == 0) {
         tries_s = 0ull;
+        k0_s = inst_of((int64_t)blockIdx.x * (blockDim.x >> 5));
+    }
     __syncthreads();
-    if (t < gp.pop && improved[t] == 0) {
-        const int64_t c0 = cost[t];
+    const int k = inst_of(gi);
+    const ga_prob gp = K > 1 ? gps[k] : one, gq = K > 1 ? gqs[k] : oneq;
+    const int64_t t = gi - gp.ind_base;
+    const int32_t W = gp.W;
+    if (t < gp.pop && !st[k].stop && improved[gp.ind_base + t] == 0) {
+        const int64_t c0 = cost[gp.ind_base + t];
         int qs = Q;  // first improving try; every lane takes the same iterations and the same break
         for (int base = 0; base < Q; base += 32) {
             const int q = base + lane;
-            const bool hit = q < Q && costQ[(int64_t)q * gp.pop + t] < c0;
+            const bool hit = q < Q && costQ[gq.ind_base + (int64_t)q * gp.pop + t] < c0;
             const uint32_t b = __ballot_sync(PM_FULL_MASK, hit);
             if (b) {
                 qs = base + __ffs(b) - 1;
@@ -1027,18 +1047,23 @@ __global__ void __launch_bounds__(256) k_ga_mutate_accept(ga_prob gp, int32_t Q,
         if (qs < Q) {
             const int64_t u = (int64_t)qs * gp.pop + t;
             for (int w = lane; w < W; w += 32)
-                X[t * W + w] = XQ[u * W + w];
+                X[gp.word_base + t * W + w] = XQ[gq.word_base + u * W + w];
             if (lane == 0) {
-                cost[t] = costQ[u];
-                improved[t] = 1;
+                cost[gp.ind_base + t] = costQ[gq.ind_base + u];
+                improved[gp.ind_base + t] = 1;
             }
         }
-        if (lane == 0)
-            atomicAdd(&tries_s, (unsigned long long)(qs < Q ? qs + 1 : Q));
+        if (lane == 0) {
+            const unsigned long long tr = (unsigned long long)(qs < Q ? qs + 1 : Q);
+            if (k == k0_s)
+                atomicAdd(&tries_s, tr);
+            else
+                atomicAdd(reinterpret_cast<unsigned long long *>(&st[k].evals), tr);
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0 && tries_s)
-        atomicAdd(reinterpret_cast<unsigned long long *>(&st[0].evals), tries_s);
+        atomicAdd(reinterpret_cast<unsigned long long *>(&st[k0_s].evals), tries_s);
 }
 
 // Generation end (Section 3.2.2 steps 7-8, Section 3.1 steps 13-14), one CTA
@@ -1839,8 +1864,10 @@ struct pm_ga {
     bool spec = false;
     pm_eval_plan spec_single;
     pm_multi_plan spec_plan;
-    ga_prob gq{};
-    pm_dbuf XQ, costQ, activeQ, accumQ, ticketsQ, colQ;
+    ga_prob gq{};                // instance 0's candidates
+    std::vector<ga_prob> gqs;    // every instance's candidates
+    int64_t groupsQ_total = 0;   // 32-candidate groups over all instances
+    pm_dbuf XQ, costQ, activeQ, accumQ, ticketsQ, colQ, gqprobs, probsQ;
     pm_eval_plan single;      // K == 1: the single-instance plan
     pm_multi_plan plan;       // the scan plan over all instances
     std::vector<ga_prob> gps;
@@ -1879,7 +1906,7 @@ static void ga_free(pm_ga *ga)
                        &ga->st,        &ga->glob, &ga->err,   &ga->probs,  &ga->gprobs,
                        &ga->s_gain,    &ga->s_cap, &ga->s_loss, &ga->s_assign, &ga->moves, &ga->xfeat, &ga->scores,
                        &ga->comb_tab,  &ga->XQ,    &ga->costQ, &ga->activeQ, &ga->accumQ, &ga->ticketsQ, &ga->colQ,
-                       &ga->bar};
+                       &ga->bar,       &ga->gqprobs, &ga->probsQ};
     for (pm_dbuf *b : bufs)
         b->release();
     delete ga;
@@ -2018,11 +2045,11 @@ static pm_status enqueue_generation(pm_ga *ga, cudaStream_t s, cudaGraphConditio
         ColumnsOut coQ;
         coQ.colT = static_cast<uint32_t *>(ga->colQ.ptr);
         coQ.G = ga->spec_plan.groups;
-        const int64_t QP = (int64_t)ga->Q * ga->P;
-        PM_CUDA(pm_launch(k_ga_mutate_all, (unsigned)pm_ceil_div(QP, 32), 1024, 0, s, one, ga->gq, (int32_t)ga->Q, X,
-                          XQ, activeQ, improved, ga->seed, st, coQ));
+        const ga_prob *gqs = static_cast<const ga_prob *>(ga->gqprobs.ptr);
+        PM_CUDA(pm_launch(k_ga_mutate_all, (unsigned)ga->groupsQ_total, 1024, 0, s, gps, gqs, K, one, ga->gq,
+                          (int32_t)ga->Q, X, XQ, activeQ, improved, ga->seed, st, coQ));
         pm_scan_launch L;
-        pm_scan_launch_from(ga->spec_plan, nullptr, L);
+        pm_scan_launch_from(ga->spec_plan, static_cast<const pm_prob *>(ga->probsQ.ptr), L);
         L.masks = XQ;
         L.colT = coQ.colT;
         L.active = activeQ;
@@ -2032,8 +2059,8 @@ static pm_status enqueue_generation(pm_ga *ga, cudaStream_t s, cudaGraphConditio
         pm_accept_args store;
         store.columns_ready = true;
         PM_TRY(pm_launch_scan(L, store, costQ, ga->spec_plan.smem, s));
-        PM_CUDA(pm_launch(k_ga_mutate_accept, (unsigned)pm_ceil_div(ga->P, 8), 256, 0, s, one, (int32_t)ga->Q, X, XQ,
-                          cost, costQ, improved, st));
+        PM_CUDA(pm_launch(k_ga_mutate_accept, (unsigned)pm_ceil_div(ga->plan.ind_total, 8), 256, 0, s, gps, gqs, K,
+                          one, ga->gq, (int32_t)ga->Q, X, XQ, cost, costQ, improved, st));
     } else {
         for (int q = 0; q < ga->Q; ++q) {
             PM_CUDA(pm_launch(k_ga_mutate, groups, 1024, 0, s, gps, K, one, X, Xc, active, improved, (uint32_t)q,
@@ -2202,24 +2229,42 @@ static pm_status ga_configure(pm_ga *ga, int64_t pop, uint64_t seed, const pm_ga
     return PM_OK;
 }
 
-// Buffers of the speculative mutation cycle: Q x pop candidate bitsets, their
-// facility-major copy, active bits, costs and the scan's accumulators.
+// Buffers of the speculative mutation cycle: Q x pop candidate bitsets per instance, their facility-major
+// copy, active bits, costs and the scan's accumulators, laid out by spec_plan; the candidates' per-instance
+// layout (ga_prob) and scan table (pm_prob) on the device for batched GAs.
 static pm_status spec_alloc(pm_ga *ga, cudaStream_t s)
 {
-    const pm_instance *inst = ga->insts[0];
+    const int K = ga->K;
     const int64_t QP = (int64_t)ga->Q * ga->P;
-    ga->gq = ga->gps[0];
-    ga->gq.pop = QP;
-    ga->gq.ind_base = ga->gq.word_base = ga->gq.grp_base = ga->gq.col_base = 0;
-    PM_TRY(ga->XQ.reserve((size_t)QP * inst->W * 4));
-    PM_TRY(ga->costQ.reserve((size_t)QP * 8));
-    PM_TRY(ga->activeQ.reserve((size_t)pm_round_up(pm_ceil_div(QP, 32) * 4, 256)));
-    PM_TRY(ga->accumQ.reserve((size_t)ga->spec_plan.ind_total * 8));
-    PM_TRY(ga->ticketsQ.reserve((size_t)pm_round_up(std::max<int64_t>(ga->spec_plan.tiles_total, 1) * 4, 256)));
-    PM_TRY(ga->colQ.reserve(std::max<size_t>((size_t)ga->spec_plan.cols_total * 4, 256)));
+    ga->gqs.resize(K);
+    int64_t grp = 0;
+    for (int k = 0; k < K; ++k) {
+        const pm_prob &pr = ga->spec_plan.probs[k];
+        ga_prob &gq = ga->gqs[k];
+        gq = ga->gps[k];
+        gq.pop = QP;
+        gq.ind_base = pr.ind_base;
+        gq.word_base = pr.word_base;
+        gq.col_base = pr.col_base;
+        gq.grp_base = grp;
+        grp += pm_ceil_div(QP, 32);
+    }
+    ga->gq = ga->gqs[0];
+    ga->groupsQ_total = grp;
+    const pm_multi_plan &sp = ga->spec_plan;
+    PM_TRY(ga->XQ.reserve((size_t)sp.words_total * 4));
+    PM_TRY(ga->costQ.reserve((size_t)sp.ind_total * 8));
+    PM_TRY(ga->activeQ.reserve((size_t)pm_round_up(pm_ceil_div(sp.ind_total, 32) * 4, 256)));
+    PM_TRY(ga->accumQ.reserve((size_t)sp.ind_total * 8));
+    PM_TRY(ga->ticketsQ.reserve((size_t)pm_round_up(std::max<int64_t>(sp.tiles_total, 1) * 4, 256)));
+    PM_TRY(ga->colQ.reserve(std::max<size_t>((size_t)sp.cols_total * 4, 256)));
+    PM_TRY(ga->gqprobs.reserve(sizeof(ga_prob) * K));
+    PM_TRY(ga->probsQ.reserve(sizeof(pm_prob) * K));
     pm_dbuf *zero[] = {&ga->XQ, &ga->costQ, &ga->activeQ, &ga->accumQ, &ga->ticketsQ};
     for (pm_dbuf *b : zero)
         PM_CUDA(cudaMemsetAsync(b->ptr, 0, b->bytes, s));  // accumulators and tickets start at zero
+    PM_CUDA(cudaMemcpyAsync(ga->gqprobs.ptr, ga->gqs.data(), sizeof(ga_prob) * K, cudaMemcpyHostToDevice, s));
+    PM_CUDA(cudaMemcpyAsync(ga->probsQ.ptr, sp.probs.data(), sizeof(pm_prob) * K, cudaMemcpyHostToDevice, s));
     PM_CUDA(cudaStreamSynchronize(s));
     return PM_OK;
 }
@@ -2375,7 +2420,8 @@ static pm_status ga_create_common(pm_ga *ga, cudaStream_t s)
     pm_status st = ga_alloc(ga, s);
     if (st == PM_OK && ga->spec && spec_alloc(ga, s) != PM_OK) {
         // no room for the Q x pop candidates: run the mutation cycle try by try instead
-        pm_dbuf *bufs[] = {&ga->XQ, &ga->costQ, &ga->activeQ, &ga->accumQ, &ga->ticketsQ, &ga->colQ};
+        pm_dbuf *bufs[] = {&ga->XQ, &ga->costQ, &ga->activeQ, &ga->accumQ, &ga->ticketsQ, &ga->colQ,
+                           &ga->gqprobs, &ga->probsQ};
         for (pm_dbuf *b : bufs)
             b->release();
         cudaGetLastError();
@@ -2516,6 +2562,10 @@ extern "C" pm_status pm_batch_ga_create(pm_batch *b, uint64_t seed, int64_t pop,
     }
     if (st == PM_OK)
         st = pm_batch_ga_plan(b, pop, ga->plan);
+    if (st == PM_OK && ga->Q >= 1 && spec_allowed()) {
+        st = pm_batch_ga_plan_candidates(b, pop, (int64_t)ga->Q * pop, ga->spec_plan);
+        ga->spec = st == PM_OK;
+    }
     if (st == PM_OK)
         st = ga_create_common(ga, static_cast<cudaStream_t>(stream));
     if (st != PM_OK) {
