@@ -631,6 +631,10 @@ PM_API pm_status pm_batch_tune(pm_batch *b, const int64_t *pops, void *stream, p
  * pm_ga_instance_result, pm_ga_instance_population, pm_ga_info and
  * pm_ga_destroy on the result.  All instances must have p >= 2, or all
  * p = 1 (PM_ERR_UNSUPPORTED otherwise).  PM_GA_TUNE runs pm_batch_tune.
+ * The mutation tries run one by one; with PM_GA_SPEC=1 in the environment
+ * they are built and evaluated together for all instances (every
+ * instance's Q x pop candidates in one launch and one scan) with the same
+ * results.
  */
 PM_API pm_status pm_batch_ga_create(pm_batch *b, uint64_t seed, int64_t pop, const pm_ga_params *params, void *stream,
                                     pm_ga **out);

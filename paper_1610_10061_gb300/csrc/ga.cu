@@ -1928,6 +1928,13 @@ static bool spec_allowed()
     return !(v && v[0] == '0');
 }
 
+// PM_GA_SPEC=1: the speculative cycle for batched GAs too.
+static bool spec_forced()
+{
+    const char *v = std::getenv("PM_GA_SPEC");
+    return v && v[0] == '1';
+}
+
 static pm_status ga_eval(pm_ga *ga, const uint32_t *masks, int64_t *costs, const pm_accept_args &acc,
                          cudaStream_t s)
 {
@@ -2562,7 +2569,10 @@ extern "C" pm_status pm_batch_ga_create(pm_batch *b, uint64_t seed, int64_t pop,
     }
     if (st == PM_OK)
         st = pm_batch_ga_plan(b, pop, ga->plan);
-    if (st == PM_OK && ga->Q >= 1 && spec_allowed()) {
+    // batched GAs evaluate their mutation tries one by one unless PM_GA_SPEC=1: their scans are long, and the
+    // tries after an individual's first improvement, which the speculative cycle evaluates too, cost more than
+    // the launches it saves (256 uneven instances: 20.4 ms per generation against 19.8 ms try by try)
+    if (st == PM_OK && ga->Q >= 1 && spec_forced()) {
         st = pm_batch_ga_plan_candidates(b, pop, (int64_t)ga->Q * pop, ga->spec_plan);
         ga->spec = st == PM_OK;
     }

@@ -74,8 +74,11 @@ def test_batch_eval_paper_shaped_instances(pm):
         np.testing.assert_array_equal(costs[256 * k:256 * (k + 1)], oracle.eval_scan(pi, de, mk))
 
 
-@pytest.mark.parametrize("mixed", [False, True])
-def test_batch_ga_matches_standalone_oracle_runs(pm, mixed):
+@pytest.mark.parametrize("mixed,spec", [(False, False), (True, False), (False, True), (True, True)])
+def test_batch_ga_matches_standalone_oracle_runs(pm, monkeypatch, mixed, spec):
+    """spec: PM_GA_SPEC=1, every instance's mutation tries built and evaluated together (one launch, one scan)."""
+    if spec:
+        monkeypatch.setenv("PM_GA_SPEC", "1")
     data = [(graph_instance(100, 200, seed=0), 5), (euclid_instance(150, seed=5), 12),
             (graph_instance(90, 200, seed=6), 9)]
     insts = [pm.Instance(d, p, cumulative=mixed and k != 1) for k, (d, p) in enumerate(data)]
@@ -97,6 +100,8 @@ def test_batch_ga_matches_standalone_oracle_runs(pm, mixed):
         np.testing.assert_array_equal(best, st.best)
     info = ga.info()
     assert info["pop"] == P and info["deme"] == D
+    lgD = 5
+    assert info["kernels_per_generation"] == 2 + lgD * 2 + (3 if spec else lgD * 2) + 1
 
 
 def test_batch_ga_instances_stop_independently(pm):
