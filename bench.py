@@ -55,6 +55,9 @@ def parse_args():
     ap.add_argument("--evaluator", default="scan", choices=["scan", "hbp"],
                     help="eval mode: the scan of Section 4.2 (default), or the reduced Hammer-Beresnev polynomial "
                          "of Section 2.1 (pm_hbp_eval) timed beside it on the same population")
+    ap.add_argument("--layouts", action="store_true",
+                    help="eval mode: also time the mask layouts pinned in turn -- the tuned facility-major bit "
+                         "columns, the row kernel with bitsets and the row kernel with byte masks")
     ap.add_argument("--mode", default="ga", choices=["ga", "eval"],
                     help="ga: GA generations (default); eval: one fitness evaluation pass of a random population")
     return ap.parse_args()
@@ -858,9 +861,54 @@ def run_eval_mode(args):
                        "eval_tile": rec["eval_tile"], "l2": "flushed between timed steps"},
             "roofline": rec["roofline"], "roofline_issue": rec["roofline_issue"],
             "gpu_launches": 2 * rec["steps"], "tables": rec.get("tables_build"), "clocks": rec["clocks"]}
+    if args.layouts:
+        line["layouts"] = layout_times(pm, torch, d, p, masks, args.tables)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_eval_baseline(d, p, masks)
     print(json.dumps(line), flush=True)
+
+
+def layout_times(pm, torch, d, p, masks, tables):
+    """Median CUDA-event time (ms, L2 flushed, 20 passes) of one evaluation pass per mask layout: the tuned
+    facility-major bit columns, the row kernel with bitsets (groups 0), the row kernel with byte masks (-1)."""
+    import numpy as np
+
+    pop, m = masks.shape[0], d.shape[1]
+    stream = torch.cuda.current_stream()
+    dmask = torch.from_numpy(masks.view(np.int32)).cuda()
+    dcost = torch.empty(pop, dtype=torch.int64, device="cuda")
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    out = {}
+    ref = None
+    for name, shape in (("columns_tuned", None), ("rows_bitsets", 0), ("rows_bytes", -1)):
+        inst = pm.Instance(d, p, stream=stream.cuda_stream, cumulative=tables == "cumulative")
+        try:
+            if shape is None:
+                tuned = inst.tune(pop, stream=stream.cuda_stream)
+            else:
+                inst.set_shape(pop, groups=shape, warps=8, splits=0)
+        except pm.PMError as e:
+            out[name] = f"unsupported: {e}"
+            inst.close()
+            continue
+        for _ in range(3):
+            pm.pm_eval_population(inst.handle, dmask, pop, dcost, 0, stream.cuda_stream)
+        es = [torch.cuda.Event(enable_timing=True) for _ in range(20)]
+        ee = [torch.cuda.Event(enable_timing=True) for _ in range(20)]
+        for k in range(20):
+            flush.zero_()
+            es[k].record(stream)
+            pm.pm_eval_population(inst.handle, dmask, pop, dcost, 0, stream.cuda_stream)
+            ee[k].record(stream)
+        torch.cuda.synchronize()
+        got = dcost.cpu().numpy()
+        assert ref is None or np.array_equal(got, ref)
+        ref = got
+        out[name] = statistics.median(a.elapsed_time(b) for a, b in zip(es, ee))
+        if shape is None:
+            out["columns_tuned_shape"] = {k: tuned[k] for k in ("groups", "warps", "splits", "grid")}
+        inst.close()
+    return out
 
 
 def run_batched(args):

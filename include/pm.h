@@ -227,16 +227,18 @@ PM_API pm_status pm_eval_columns(pm_instance *inst, const uint32_t *cols, int64_
  * runs one thread per chromosome).  Candidates: facility-major tiles of
  * 32, 64 or 128 individuals per CTA (groups = 1, 2, 4; those whose tile fits
  * in shared memory), 8, 16 or 32 warps per CTA, and client splits around the
- * one-wave default (x1/2, x1, x2); the row kernel when no tile fits.  Each
+ * one-wave default (x1/2, x1, x2); the row kernel with bitsets and with byte
+ * masks (one byte per facility, where 8 warps' masks fit in shared memory).  Each
  * candidate evaluates a uniformly random population (Floyd sampling, fixed
- * seed) once untimed and three times timed with CUDA events on `stream`; the
+ * seed) once untimed and five times timed with CUDA events on `stream`; the
  * fastest median is kept for this (instance, pop) and used by every later
  * evaluation of that size (pm_eval_population, pm_eval_population_noalloc
  * and GAs created afterwards).  chosen (nullable, host) receives it.
  * Synchronises `stream`.  Errors: PM_ERR_INVALID_ARG, PM_ERR_OOM, PM_ERR_CUDA.
  */
 typedef struct pm_eval_shape {
-    int32_t groups;   /* 32-individual groups per CTA tile (1, 2, 4); 0 = row kernel */
+    int32_t groups;   /* 32-individual groups per CTA tile (1, 2, 4); 0 = row kernel (bitsets in shared memory);
+                         -1 = row kernel with byte masks (each bitset expanded to a byte per facility) */
     int32_t warps;    /* warps per CTA */
     int32_t splits;   /* client splits: work items per tile */
     int32_t grid;     /* CTAs launched (persistent over tiles x splits) */
@@ -252,7 +254,8 @@ PM_API pm_status pm_tune_eval(pm_instance *inst, int64_t pop, void *stream, pm_e
  * candidates and reserved are ignored) for evaluations of `pop` individuals on inst
  * and for GAs created afterwards, in place of the heuristic or a tuned
  * shape (no counterpart in the paper: it pins a launch shape for
- * reproducible timing and tests).  groups 0 selects the row kernel; splits 0
+ * reproducible timing and tests).  groups 0 selects the row kernel, -1 the
+ * row kernel with byte masks (PM_ERR_UNSUPPORTED where they do not fit); splits 0
  * the default split count.  The costs do not depend on the shape.  Errors:
  * PM_ERR_INVALID_ARG (bad values), PM_ERR_UNSUPPORTED (the shape does not
  * fit this instance's shared-memory budget).

@@ -385,9 +385,14 @@ __global__ void __launch_bounds__(1024) k_scan_columns(const pm_prob *__restrict
 
 // ---------------------------------------------------------------------------
 // Row kernel (fallback for m too large for facility-major tiles): one warp
-// per individual, the individual's bitset in shared memory, one ballot per
-// 32 ranks.  Grid: (ceil(pop / warps), splits).
+// per individual, the individual's mask in shared memory, one ballot per
+// 32 ranks.  Grid: (ceil(pop / warps), splits).  The mask is the bitset
+// (W words per warp) or, with kBytes, the bitset expanded to one byte per
+// facility (32 W bytes per warp; a facility's test is one byte load instead
+// of a word load, a shift and a mask) -- the byte-mask layout the autotuner
+// weighs against the bit layouts.
 // ---------------------------------------------------------------------------
+template <bool kBytes>
 __global__ void __launch_bounds__(256) k_scan_rows(const uint16_t *__restrict__ pi, const int32_t *__restrict__ delta,
                                                    int64_t n, int32_t L, int64_t stride,
                                                    const uint32_t *__restrict__ masks, int32_t W, int64_t pop,
@@ -395,7 +400,7 @@ __global__ void __launch_bounds__(256) k_scan_rows(const uint16_t *__restrict__ 
                                                    int cum, unsigned long long *__restrict__ partial)
 {
     pm_grid_dependency_wait();
-    extern __shared__ __align__(16) uint32_t rowbits[];  // [warps][W]
+    extern __shared__ __align__(16) uint32_t rowbits[];  // [warps][W] words, or [warps][8W] words of bytes
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
@@ -405,10 +410,21 @@ __global__ void __launch_bounds__(256) k_scan_rows(const uint16_t *__restrict__ 
         return;
     if (active != nullptr && !((__ldg(active + (t >> 5)) >> (t & 31)) & 1u))
         return;
-    uint32_t *x = rowbits + (int64_t)warp * W;
-    for (int w = lane; w < W; w += 32)
-        x[w] = __ldg(masks + t * W + w);
+    uint32_t *x = rowbits + (int64_t)warp * W * (kBytes ? 8 : 1);
+    for (int w = lane; w < W; w += 32) {
+        const uint32_t v = __ldg(masks + t * W + w);
+        if constexpr (kBytes) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {  // facilities 32w + 4q .. 32w + 4q + 3 -> bytes 0..3 of word 8w + q
+                const uint32_t b = v >> (4 * q);
+                x[8 * w + q] = (b & 1u) | ((b & 2u) << 7) | ((b & 4u) << 14) | ((b & 8u) << 21);
+            }
+        } else {
+            x[w] = v;
+        }
+    }
     __syncwarp();
+    const uint8_t *xb = reinterpret_cast<const uint8_t *>(x);
     const int64_t c_begin = (int64_t)split * clients_per_split;
     const int64_t c_end = (c_begin + clients_per_split < n) ? c_begin + clients_per_split : n;
     unsigned long long acc = 0ull;
@@ -424,7 +440,11 @@ __global__ void __launch_bounds__(256) k_scan_rows(const uint16_t *__restrict__ 
                 j = __ldg(prow + r);
                 dl = __ldg(drow + r);
             }
-            const bool open = (r < L) && ((x[j >> 5] >> (j & 31)) & 1u);
+            bool open;
+            if constexpr (kBytes)
+                open = (r < L) && xb[j] != 0;
+            else
+                open = (r < L) && ((x[j >> 5] >> (j & 31)) & 1u);
             const uint32_t hit = __ballot_sync(PM_FULL_MASK, open);
             if (!hit) {
                 if (!cum)
@@ -541,7 +561,8 @@ pm_status pm_fitness_init(const pm_instance *inst)
     PM_CUDA(cudaFuncSetAttribute(k_scan_columns<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
     PM_CUDA(cudaFuncSetAttribute(k_scan_columns<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
     PM_CUDA(cudaFuncSetAttribute(k_scan_columns<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
-    PM_CUDA(cudaFuncSetAttribute(k_scan_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+    PM_CUDA(cudaFuncSetAttribute(k_scan_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+    PM_CUDA(cudaFuncSetAttribute(k_scan_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
     return PM_OK;
 }
 
@@ -570,6 +591,7 @@ pm_eval_plan pm_plan_eval_with(const pm_instance *inst, int64_t pop, int G, int 
         plan.groups = 0;  // row kernel
         plan.warps = 8;
         plan.tiles = pm_ceil_div(pop, plan.warps);
+        plan.bytes = (G < 0 && (size_t)plan.warps * inst->W * 32 + 1024 <= inst->smem_optin) ? 1 : 0;
         ctas_per_sm = 8;
     } else {
         plan.groups = G;
@@ -757,11 +779,16 @@ pm_status pm_launch_eval(const pm_instance *inst, const pm_eval_plan &plan, cons
     ep.cand_masks = acc.cand_masks;
     ep.improved = acc.improved;
     const int64_t cps = pm_ceil_div(inst->n, plan.splits);
-    const size_t smem = (size_t)plan.warps * inst->W * 4;
+    const size_t smem = (size_t)plan.warps * inst->W * 4 * (plan.bytes ? 8 : 1);
     dim3 grid((unsigned)plan.tiles, (unsigned)plan.splits);
-    PM_CUDA(pm_launch(k_scan_rows, grid, plan.warps * 32, smem, stream, inst->pi, inst->delta, inst->n,
-                      (int32_t)inst->L, inst->stride, masks, (int32_t)inst->W, pop, active, cps, inst->cum ? 1 : 0,
-                      partials));
+    if (plan.bytes)
+        PM_CUDA(pm_launch(k_scan_rows<true>, grid, plan.warps * 32, smem, stream, inst->pi, inst->delta, inst->n,
+                          (int32_t)inst->L, inst->stride, masks, (int32_t)inst->W, pop, active, cps,
+                          inst->cum ? 1 : 0, partials));
+    else
+        PM_CUDA(pm_launch(k_scan_rows<false>, grid, plan.warps * 32, smem, stream, inst->pi, inst->delta, inst->n,
+                          (int32_t)inst->L, inst->stride, masks, (int32_t)inst->W, pop, active, cps,
+                          inst->cum ? 1 : 0, partials));
     const int64_t threads = 256;
     const int64_t blocks = pm_ceil_div(pop * 32, threads);
     PM_CUDA(pm_launch(k_reduce_accept, (unsigned)blocks, (unsigned)threads, 0, stream, partials, plan.splits, pop,

@@ -62,6 +62,7 @@ struct pm_eval_plan {
     int splits = 1;       // CTAs per individual tile along the client axis
     int64_t tiles = 0;    // ceil(pop / (32 G))
     int64_t grid = 0;     // CTAs launched (column kernel: persistent over tiles x splits items)
+    int bytes = 0;        // row kernel only: each warp's bitset expanded to one byte per facility (byte masks)
 };
 
 // One instance inside an evaluation launch (host and device).  Individuals

@@ -21,8 +21,11 @@ static constexpr int kTuneReps = 5;
 namespace {
 bool same_shape(const pm_eval_plan &a, const pm_eval_plan &b)
 {
-    return a.groups == b.groups && a.warps == b.warps && a.splits == b.splits;
+    return a.groups == b.groups && a.warps == b.warps && a.splits == b.splits && a.bytes == b.bytes;
 }
+
+// The shape as the ABI reports it: groups -1 is the row kernel with byte masks.
+int32_t abi_groups(const pm_eval_plan &p) { return p.groups == 0 && p.bytes ? -1 : p.groups; }
 }  // namespace
 
 extern "C" pm_status pm_tune_eval(pm_instance *inst, int64_t pop, void *stream, pm_eval_shape *chosen)
@@ -53,9 +56,12 @@ extern "C" pm_status pm_tune_eval(pm_instance *inst, int64_t pop, void *stream, 
             }
         }
     }
-    // the other mask layout: individual-major bitsets, one warp per individual (the row kernel)
+    // the other mask layouts: individual-major bitsets, one warp per individual (the row kernel), and the same
+    // with each bitset expanded to one byte per facility (byte masks)
     if ((size_t)8 * inst->W * 4 + 1024 <= inst->smem_optin)
         cands.push_back(pm_plan_eval_with(inst, pop, 0, 8, 0));
+    if ((size_t)8 * inst->W * 32 + 1024 <= inst->smem_optin)
+        cands.push_back(pm_plan_eval_with(inst, pop, -1, 8, 0));
     if (cands.empty())
         cands.push_back(pm_plan_eval_with(inst, pop, 0, 8, 0));
 
@@ -107,7 +113,7 @@ extern "C" pm_status pm_tune_eval(pm_instance *inst, int64_t pop, void *stream, 
             break;
         std::sort(t, t + kTuneReps);
         if (t[kTuneReps / 2] < best_ms) {
-            best_ms = t[1];
+            best_ms = t[kTuneReps / 2];
             best = (int)k;
         }
     }
@@ -124,7 +130,7 @@ extern "C" pm_status pm_tune_eval(pm_instance *inst, int64_t pop, void *stream, 
         inst->tuned[pop] = cands[best];
     }
     if (chosen) {
-        chosen->groups = cands[best].groups;
+        chosen->groups = abi_groups(cands[best]);
         chosen->warps = cands[best].warps;
         chosen->splits = cands[best].splits;
         chosen->grid = (int32_t)cands[best].grid;
@@ -142,8 +148,10 @@ extern "C" pm_status pm_set_eval_shape(pm_instance *inst, int64_t pop, const pm_
     std::lock_guard<std::mutex> guard(inst->lock);
     PM_CUDA(cudaSetDevice(inst->device));
     pm_eval_plan pl;
-    if (shape->groups == 0) {
-        pl = pm_plan_eval_with(inst, pop, 0, 8, std::max(0, shape->splits));
+    if (shape->groups == 0 || shape->groups == -1) {
+        pl = pm_plan_eval_with(inst, pop, shape->groups, 8, std::max(0, shape->splits));
+        if (shape->groups == -1 && !pl.bytes)
+            return PM_ERR_UNSUPPORTED;  // the byte masks of 8 warps do not fit in shared memory
     } else {
         if (shape->groups != 1 && shape->groups != 2 && shape->groups != 4)
             return PM_ERR_INVALID_ARG;

@@ -411,9 +411,10 @@ def test_bounded_wait_times_out_and_context_survives(pm):
 
 
 def _pinned_shapes(pm, inst, pop):
-    """Every evaluation shape (G, warps, splits) this instance accepts, pinned in turn; G = 0 is the row kernel."""
-    for G in (0, 1, 2, 4):
-        for warps in ((8,) if G == 0 else (8, 16, 32)):
+    """Every evaluation shape (G, warps, splits) this instance accepts, pinned in turn; G = 0 is the row kernel
+    with bitsets, G = -1 the row kernel with byte masks."""
+    for G in (-1, 0, 1, 2, 4):
+        for warps in ((8,) if G <= 0 else (8, 16, 32)):
             for splits in (1, 3, 0):
                 try:
                     inst.set_shape(pop, groups=G, warps=warps, splits=splits)
@@ -448,6 +449,8 @@ def test_ga_on_pinned_shapes_matches_oracle(pm):
     _ga_compare(pm, w["d"], w["p"], 1024, 2, check_every=1, shape=dict(groups=1, warps=8, splits=3))
     _ga_compare(pm, euclid_instance(77, seed=11), 7, 128, 6, check_every=2, deme=16, seed=5,
                 shape=dict(groups=0, warps=8, splits=2))
+    _ga_compare(pm, euclid_instance(77, seed=11), 7, 128, 6, check_every=2, deme=16, seed=6,
+                shape=dict(groups=-1, warps=8, splits=2))  # byte masks
 
 
 @pytest.mark.parametrize("name,d,p", _shapes(), ids=[s[0] for s in _shapes()])
