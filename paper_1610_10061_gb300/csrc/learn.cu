@@ -741,39 +741,28 @@ __global__ void __launch_bounds__(1024, 2) k_swap_stats(const uint16_t *__restri
     uint32_t *bits = reinterpret_cast<uint32_t *>(sm);
     const size_t off = ((size_t)W * 4 + 15) & ~size_t(15);
     // accumulators: in shared memory (kSmem; Acc of 32 or 64 bits, chosen by the host so sums cannot overflow)
-    // or directly in the outputs (64 bits, zeroed by the caller).  With 32-bit sums a gain and its count share one
-    // 64-bit word (count in the upper half), so a gain is one shared atomic: GCs[k] replaces Gs[k] and Cs[k].
-    constexpr bool kPackedGain = kSmem && sizeof(Acc) == 4;
+    // or directly in the outputs (64 bits, zeroed by the caller)
     Acc *Gs = reinterpret_cast<Acc *>(sm + off);
     Acc *Ls = Gs + m;
     int *Cs = reinterpret_cast<int *>(Ls + m);
     int *As = Cs + m;
-    unsigned long long *GCs = reinterpret_cast<unsigned long long *>(sm + off);  // [m], then Ls [m], As [m]
-    if constexpr (kPackedGain) {
-        Ls = reinterpret_cast<Acc *>(GCs + m);
-        As = reinterpret_cast<int *>(Ls + m);
-    }
     const int64_t tm = t * m;
+    auto add_stat = [&](bool first, uint32_t k, int32_t v) {  // add_loss if first, else add_gain
+        if constexpr (kSmem) {
+            atomicAdd((first ? Ls : Gs) + k, (Acc)(uint32_t)v);
+            atomicAdd((first ? As : Cs) + k, 1);
+        } else {
+            atomicAdd((first ? loss : gain) + tm + k, (unsigned long long)(uint32_t)v);
+            atomicAdd((first ? assign : cap) + tm + k, 1);
+        }
+    };
     auto add_gain = [&](uint32_t k, int32_t v) {  // facility k (closed, ranked before the first open) gains v
-        if constexpr (kPackedGain) {
-            atomicAdd(GCs + k, (1ull << 32) | (unsigned long long)(uint32_t)v);
-        } else if constexpr (kSmem) {
+        if constexpr (kSmem) {
             atomicAdd(Gs + k, (Acc)(uint32_t)v);
             atomicAdd(Cs + k, 1);
         } else {
             atomicAdd(gain + tm + k, (unsigned long long)(uint32_t)v);
             atomicAdd(cap + tm + k, 1);
-        }
-    };
-    auto add_stat = [&](bool first, uint32_t k, int32_t v) {  // add_loss if first, else add_gain
-        if (!first) {
-            add_gain(k, v);
-        } else if constexpr (kSmem) {
-            atomicAdd(Ls + k, (Acc)(uint32_t)v);
-            atomicAdd(As + k, 1);
-        } else {
-            atomicAdd(loss + tm + k, (unsigned long long)(uint32_t)v);
-            atomicAdd(assign + tm + k, 1);
         }
     };
     auto add_loss = [&](uint32_t j, int32_t v) {  // the first open facility j would lose v
@@ -785,13 +774,7 @@ __global__ void __launch_bounds__(1024, 2) k_swap_stats(const uint16_t *__restri
             atomicAdd(assign + tm + j, 1);
         }
     };
-    if constexpr (kPackedGain) {
-        for (int j = threadIdx.x; j < m; j += blockDim.x) {
-            GCs[j] = 0ull;
-            Ls[j] = 0;
-            As[j] = 0;
-        }
-    } else if constexpr (kSmem) {
+    if constexpr (kSmem) {
         for (int j = threadIdx.x; j < m; j += blockDim.x) {
             Gs[j] = 0;
             Ls[j] = 0;
@@ -968,16 +951,7 @@ __global__ void __launch_bounds__(1024, 2) k_swap_stats(const uint16_t *__restri
             carry = __shfl_sync(PM_FULL_MASK, cs, 31);
         }
     }
-    if constexpr (kPackedGain) {
-        __syncthreads();
-        for (int j = threadIdx.x; j < m; j += blockDim.x) {
-            const unsigned long long gc = GCs[j];
-            gain[tm + j] = gc & 0xffffffffull;
-            cap[tm + j] = (int)(gc >> 32);
-            loss[tm + j] = (unsigned long long)Ls[j];
-            assign[tm + j] = As[j];
-        }
-    } else if constexpr (kSmem) {
+    if constexpr (kSmem) {
         __syncthreads();
         for (int j = threadIdx.x; j < m; j += blockDim.x) {
             gain[tm + j] = (unsigned long long)Gs[j];
