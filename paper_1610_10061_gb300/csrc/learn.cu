@@ -32,6 +32,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -677,6 +678,347 @@ __global__ void __launch_bounds__(128) k_mlp(const __nv_bfloat16 *__restrict__ X
     }
 }
 
+// ---------------------------------------------------------------------------
+// Training (forward and backward) on the tcgen05 tensor cores.  A CTA takes
+// up to kTrTiles 128-row tiles of the batch (rows read through the epoch's
+// permutation); per tile, with one thread issuing every MMA (BF16 operands
+// in shared memory in the K-major no-swizzle core-matrix layout, FP32
+// accumulators in tensor memory):
+//   layer 1   C0 = X W1                       (M 128, N 128, K 16)
+//   layer 2   C0 = H1 W2                      (K 128)
+//   dH1       C0 = dH2 W2^T                   (A = dH2 rows, B = W2 rows)
+//   dW2      C2 += H1^T dH2                   (A = H1^T, B = dH2^T; K = the tile's rows)
+//   dW1^T    C3 += dH1^T X                    (N 16)
+// where H1, H2 are the BF16 hidden activations after ReLU, dy = 2 (y - t) / B,
+// dH2 = BF16(dy w3 [H2 > 0]) and dH1 = BF16((dH2 W2^T) [H1 > 0]) -- the
+// arithmetic of the mma.sync kernel above and of the oracle with BF16
+// rounding.  The weight gradients accumulate in tensor memory over the CTA's
+// tiles and reach the global gradient with one atomic per parameter per CTA;
+// the bias and w3 gradients are column sums in shared memory.  Eight warps
+// read the accumulators (warps w and w + 4 share TMEM lanes 32 (w mod 4) and
+// take half the columns each); every wait on an MMA is bounded.
+// ---------------------------------------------------------------------------
+constexpr int kTrTiles = 4;                // 128-row tiles per CTA per step
+constexpr int kTrThreads = 256;
+constexpr uint32_t kTrTmemCols = 512;      // C0 [0,128), C2 [128,256), C3 [256,272)
+constexpr int kLdT = 130;                  // row stride (elements) of the plain H2^T copy: odd in words
+constexpr uint32_t kIdescN16 = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+
+struct TrSmem {
+    __nv_bfloat16 AX[kTcRows * kIn];    // X tile as (m = row, k = feature)
+    __nv_bfloat16 BXT[kIn * kTcRows];   // X^T as (n = feature, k = row)
+    __nv_bfloat16 BW1[kHid * kIn];      // W1 as (n = out, k = in)
+    __nv_bfloat16 BW2T[kHid * kHid];    // W2 as (n = out, k = in): layer 2
+    __nv_bfloat16 BW2[kHid * kHid];     // W2 as (n = in, k = out): dH1 = dH2 W2^T
+    __nv_bfloat16 R[kTcRows * kHid];    // H1 as (m = row, k = unit), then dH2
+    __nv_bfloat16 T1[kHid * kTcRows];   // H1^T as (m = unit, k = row), then dH1^T
+    __nv_bfloat16 T2[kHid * kTcRows];   // dH2^T as (n = unit, k = row)
+    __nv_bfloat16 H2T[kHid * kLdT];     // H2 as [unit][row] (plain), for the w3 gradient
+    float b1[kHid], b2[kHid], w3[kHid];
+    float part[kTcRows], tgt[kTcRows], dy[kTcRows];
+    float gb1[kHid], gb2[kHid], gw3[kHid];  // this CTA's bias and w3 gradients
+    uint32_t mask1[kTcRows * 4];        // H1 > 0: row r, bit (unit & 31) of word 4 r + unit / 32
+    float gb3, sq;
+    uint64_t bar;
+    uint32_t tmem;
+};
+
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&v)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ float bf16_lo(uint32_t p) { return __uint_as_float(p << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t p) { return __uint_as_float(p & 0xffff0000u); }
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
+{
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+
+__global__ void __launch_bounds__(kTrThreads, 1) k_mlp_train_tc(const __nv_bfloat16 *__restrict__ X, int64_t rows,
+                                                                const __nv_bfloat16 *__restrict__ W1b,
+                                                                const __nv_bfloat16 *__restrict__ W2b,
+                                                                const __nv_bfloat16 *__restrict__ w3b,
+                                                                const float *__restrict__ P,
+                                                                const float *__restrict__ t, float inv_batch,
+                                                                float *__restrict__ grads, float *__restrict__ loss,
+                                                                RowMap map, int *__restrict__ err)
+{
+    extern __shared__ __align__(1024) unsigned char tr_raw[];
+    TrSmem &S = *reinterpret_cast<TrSmem *>(tr_raw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int quad = warp & 3, half = warp >> 2;
+    const int64_t tiles = (rows + kTcRows - 1) / kTcRows;
+
+    for (int i = tid; i < kIn * kHid; i += blockDim.x) {  // W1 [in][out]
+        const int in = i / kHid, out = i % kHid;
+        S.BW1[core_idx(out, in, kIn)] = W1b[i];
+    }
+    for (int i = tid; i < kHid * kHid; i += blockDim.x) {  // W2 [in][out]
+        const int in = i / kHid, out = i % kHid;
+        S.BW2T[core_idx(out, in, kHid)] = W2b[i];
+        S.BW2[core_idx(in, out, kHid)] = W2b[i];
+    }
+    for (int i = tid; i < kHid; i += blockDim.x) {
+        S.b1[i] = P[kOffB1 + i];
+        S.b2[i] = P[kOffB2 + i];
+        S.w3[i] = __bfloat162float(w3b[i]);
+        S.gb1[i] = 0.f;
+        S.gb2[i] = 0.f;
+        S.gw3[i] = 0.f;
+    }
+    const float b3 = P[kOffB3];
+    if (tid == 0) {
+        S.gb3 = 0.f;
+        S.sq = 0.f;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32_learn(&S.bar)), "r"(1u) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32_learn(&S.tmem)),
+                     "r"(kTrTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_sync_for_mma();
+    const uint32_t tmem = S.tmem, C0 = tmem, C2 = tmem + 128u, C3 = tmem + 256u;
+    const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
+    const int r = quad * 32 + lane;  // this thread's row of the tile (its TMEM lane)
+    const int c0 = half * 64;        // its first column
+    constexpr uint32_t kSbo = (kHid / 8) * 128;
+
+    uint32_t phase = 0;
+    bool ok = true, any = false;
+    auto wait_mma = [&]() {
+        bool w = tc_wait(&S.bar, phase);
+        w = __syncthreads_and(w);
+        phase ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        return w;
+    };
+    const int64_t last = blockIdx.x * (int64_t)kTrTiles + kTrTiles;
+    for (int64_t tile = blockIdx.x * (int64_t)kTrTiles; tile < tiles && tile < last && ok; ++tile) {
+        const int64_t pos0 = tile * kTcRows;
+        // ---- the tile's rows: X (both layouts) and targets ----
+        {
+            const int xr = tid >> 1, xh = tid & 1;
+            const bool valid = pos0 + xr < rows;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            int64_t src = 0;
+            if (valid) {
+                src = shuffled_row(map, map.pos0 + pos0 + xr);
+                v = __ldg(reinterpret_cast<const uint4 *>(X + src * kIn) + xh);
+            }
+            *reinterpret_cast<uint4 *>(reinterpret_cast<unsigned char *>(S.AX) + (xr >> 3) * 256 + xh * 128 +
+                                       (xr & 7) * 16) = v;
+            const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int f = 8 * xh + 2 * q;
+                reinterpret_cast<uint16_t *>(S.BXT)[core_idx(f, xr, kTcRows)] = (uint16_t)(wv[q] & 0xffffu);
+                reinterpret_cast<uint16_t *>(S.BXT)[core_idx(f + 1, xr, kTcRows)] = (uint16_t)(wv[q] >> 16);
+            }
+            if (xh == 0)
+                S.tgt[xr] = valid ? t[src] : 0.f;
+        }
+        const int nvalid = (int)((rows - pos0) < kTcRows ? (rows - pos0) : kTcRows);
+        tc_sync_for_mma();
+        if (tid == 0) {  // layer 1
+            tc_mma(C0, umma_desc(S.AX, 128, (kIn / 8) * 128), umma_desc(S.BW1, 128, (kIn / 8) * 128), kIdesc, 0u);
+            tc_commit(&S.bar);
+        }
+        if (!(ok = wait_mma()))
+            break;
+        // ---- H1 = bf16(relu(C0 + b1)) into R (rows) and T1 (transposed); its sign bits ----
+        for (int cc = 0; cc < 64; cc += 32) {
+            uint32_t v[32];
+            tc_ld32(C0 + lane_off + (uint32_t)(c0 + cc), v);
+            uint32_t bits = 0u;
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+                const int col = c0 + cc + 8 * g;
+                uint32_t pk[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    pk[q] = pack_relu_bf16x2(__uint_as_float(v[8 * g + 2 * q]) + S.b1[col + 2 * q],
+                                             __uint_as_float(v[8 * g + 2 * q + 1]) + S.b1[col + 2 * q + 1]);
+                    const float lo = bf16_lo(pk[q]), hi = bf16_hi(pk[q]);
+                    bits |= (lo > 0.f ? 1u : 0u) << (8 * g + 2 * q);
+                    bits |= (hi > 0.f ? 1u : 0u) << (8 * g + 2 * q + 1);
+                    reinterpret_cast<uint16_t *>(S.T1)[core_idx(col + 2 * q, r, kTcRows)] = (uint16_t)(pk[q] & 0xffffu);
+                    reinterpret_cast<uint16_t *>(S.T1)[core_idx(col + 2 * q + 1, r, kTcRows)] = (uint16_t)(pk[q] >> 16);
+                }
+                *reinterpret_cast<uint4 *>(S.R + core_idx(r, col, kHid)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            }
+            S.mask1[4 * r + (c0 + cc) / 32] = bits;
+        }
+        tc_sync_for_mma();
+        if (tid == 0) {  // layer 2
+#pragma unroll
+            for (int s = 0; s < kHid / 16; ++s)
+                tc_mma(C0, umma_desc(S.R + s * 128, 128, kSbo), umma_desc(S.BW2T + s * 128, 128, kSbo), kIdesc,
+                       s > 0 ? 1u : 0u);
+            tc_commit(&S.bar);
+        }
+        if (!(ok = wait_mma()))
+            break;
+        // ---- H2 = bf16(relu(C0 + b2)) (kept packed), y, dy, then dH2 into R and T2 ----
+        uint32_t h2[32];  // this thread's 64 columns of H2, packed pairs
+        float ysum = 0.f;
+        for (int cc = 0; cc < 64; cc += 32) {
+            uint32_t v[32];
+            tc_ld32(C0 + lane_off + (uint32_t)(c0 + cc), v);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const int col = c0 + cc + 2 * q;
+                const uint32_t hb = pack_relu_bf16x2(__uint_as_float(v[2 * q]) + S.b2[col],
+                                                     __uint_as_float(v[2 * q + 1]) + S.b2[col + 1]);
+                h2[cc / 2 + q] = hb;
+                ysum = fmaf(bf16_lo(hb), S.w3[col], ysum);
+                ysum = fmaf(bf16_hi(hb), S.w3[col + 1], ysum);
+                S.H2T[col * kLdT + r] = __ushort_as_bfloat16((unsigned short)(hb & 0xffffu));
+                S.H2T[(col + 1) * kLdT + r] = __ushort_as_bfloat16((unsigned short)(hb >> 16));
+            }
+        }
+        if (half == 1)
+            S.part[r] = ysum;
+        __syncthreads();
+        if (half == 0) {
+            const bool valid = r < nvalid;
+            const float e = valid ? (ysum + S.part[r] + b3 - S.tgt[r]) : 0.f;
+            const float dyv = valid ? 2.f * e * inv_batch : 0.f;
+            S.dy[r] = dyv;
+            float sq = e * e, d = dyv;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                sq += __shfl_xor_sync(PM_FULL_MASK, sq, o);
+                d += __shfl_xor_sync(PM_FULL_MASK, d, o);
+            }
+            if (lane == 0) {
+                atomicAdd(&S.sq, sq);
+                atomicAdd(&S.gb3, d);
+            }
+        }
+        __syncthreads();
+        {
+            const float dyr = S.dy[r];
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+                const int col = c0 + 2 * q;
+                const float g0 = bf16_lo(h2[q]) > 0.f ? dyr * S.w3[col] : 0.f;
+                const float g1 = bf16_hi(h2[q]) > 0.f ? dyr * S.w3[col + 1] : 0.f;
+                h2[q] = pack_bf16x2(g0, g1);  // dH2, packed
+                reinterpret_cast<uint16_t *>(S.T2)[core_idx(col, r, kTcRows)] = (uint16_t)(h2[q] & 0xffffu);
+                reinterpret_cast<uint16_t *>(S.T2)[core_idx(col + 1, r, kTcRows)] = (uint16_t)(h2[q] >> 16);
+            }
+#pragma unroll
+            for (int g = 0; g < 8; ++g)
+                *reinterpret_cast<uint4 *>(S.R + core_idx(r, c0 + 8 * g, kHid)) =
+                    make_uint4(h2[4 * g], h2[4 * g + 1], h2[4 * g + 2], h2[4 * g + 3]);
+        }
+        tc_sync_for_mma();
+        if (tid == 0) {  // dH1 pre-activation, and dW2 += H1^T dH2
+#pragma unroll
+            for (int s = 0; s < kHid / 16; ++s)
+                tc_mma(C0, umma_desc(S.R + s * 128, 128, kSbo), umma_desc(S.BW2 + s * 128, 128, kSbo), kIdesc,
+                       s > 0 ? 1u : 0u);
+#pragma unroll
+            for (int s = 0; s < kTcRows / 16; ++s)
+                tc_mma(C2, umma_desc(S.T1 + s * 128, 128, kSbo), umma_desc(S.T2 + s * 128, 128, kSbo), kIdesc,
+                       (any || s > 0) ? 1u : 0u);
+            tc_commit(&S.bar);
+        }
+        // column sums of this tile while the tensor cores run: the w3 and layer-2 bias gradients
+        if (tid < kHid) {
+            float gw = 0.f, gb = 0.f;
+            for (int rr = 0; rr < nvalid; ++rr) {
+                gw = fmaf(__bfloat162float(S.H2T[tid * kLdT + rr]), S.dy[rr], gw);
+                gb += __bfloat162float(S.T2[core_idx(tid, rr, kTcRows)]);
+            }
+            S.gw3[tid] += gw;
+            S.gb2[tid] += gb;
+        }
+        if (!(ok = wait_mma()))
+            break;
+        // ---- dH1 = bf16(C0 [H1 > 0]) into T1 (transposed) ----
+        for (int cc = 0; cc < 64; cc += 32) {
+            uint32_t v[32];
+            tc_ld32(C0 + lane_off + (uint32_t)(c0 + cc), v);
+            const uint32_t bits = S.mask1[4 * r + (c0 + cc) / 32];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const int col = c0 + cc + 2 * q;
+                const float g0 = ((bits >> (2 * q)) & 1u) ? __uint_as_float(v[2 * q]) : 0.f;
+                const float g1 = ((bits >> (2 * q + 1)) & 1u) ? __uint_as_float(v[2 * q + 1]) : 0.f;
+                const uint32_t pk = pack_bf16x2(g0, g1);
+                reinterpret_cast<uint16_t *>(S.T1)[core_idx(col, r, kTcRows)] = (uint16_t)(pk & 0xffffu);
+                reinterpret_cast<uint16_t *>(S.T1)[core_idx(col + 1, r, kTcRows)] = (uint16_t)(pk >> 16);
+            }
+        }
+        tc_sync_for_mma();
+        if (tid == 0) {  // dW1^T += dH1^T X
+#pragma unroll
+            for (int s = 0; s < kTcRows / 16; ++s)
+                tc_mma(C3, umma_desc(S.T1 + s * 128, 128, kSbo), umma_desc(S.BXT + s * 128, 128, kSbo), kIdescN16,
+                       (any || s > 0) ? 1u : 0u);
+            tc_commit(&S.bar);
+        }
+        if (tid < kHid) {  // the layer-1 bias gradient: row sums of dH1^T
+            float gb = 0.f;
+            for (int rr = 0; rr < nvalid; ++rr)
+                gb += __bfloat162float(S.T1[core_idx(tid, rr, kTcRows)]);
+            S.gb1[tid] += gb;
+        }
+        if (!(ok = wait_mma()))
+            break;
+        any = true;
+    }
+    if (ok && any) {
+        // this CTA's weight gradients from tensor memory: dW2 (lane = in, column = out), dW1^T (lane = out,
+        // column = in feature)
+        for (int cc = 0; cc < 64; cc += 32) {
+            uint32_t v[32];
+            tc_ld32(C2 + lane_off + (uint32_t)(c0 + cc), v);
+#pragma unroll
+            for (int q = 0; q < 32; ++q)
+                atomicAdd(grads + kOffW2 + r * kHid + c0 + cc + q, __uint_as_float(v[q]));
+        }
+        if (half == 0) {
+            uint32_t v[16];
+            tc_ld16(C3 + lane_off, v);
+#pragma unroll
+            for (int f = 0; f < 16; ++f)
+                atomicAdd(grads + kOffW1 + f * kHid + r, __uint_as_float(v[f]));
+        }
+        if (tid < kHid) {
+            atomicAdd(grads + kOffB1 + tid, S.gb1[tid]);
+            atomicAdd(grads + kOffB2 + tid, S.gb2[tid]);
+            atomicAdd(grads + kOffW3 + tid, S.gw3[tid]);
+        }
+        if (tid == 0) {
+            atomicAdd(grads + kOffB3, S.gb3);
+            atomicAdd(loss, S.sq);
+        }
+    }
+    if (!ok) {
+        if (tid == 0)
+            atomicExch(err, (int)PM_ERR_TIMEOUT);
+        (void)tc_wait(&S.bar, phase);  // let an MMA in flight finish (bounded) before its memory is released
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTrTmemCols) : "memory");
+}
+
 // Adam (Kingma & Ba 2015, Algorithm 1) on the FP32 masters; refreshes the BF16 copies.
 // The gradient buffer is left zero for the next step.  loss_word (nullable): the step's sum of squares, which
 // thread 0 moves (times inv_rows) into *loss_out and clears.
@@ -1297,9 +1639,20 @@ static size_t mlp_smem(bool train)
 // only 4 x 128 TMEM columns, the SM's 512)
 static size_t tc_smem() { return sizeof(TcSmem); }
 
+// PM_TRAIN_TC=0 in the environment trains with the mma.sync kernel instead of the tcgen05 one (for comparison).
+static bool train_tc()
+{
+    static const bool on = [] {
+        const char *e = std::getenv("PM_TRAIN_TC");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
+
 static pm_status mlp_init_attrs()
 {
     PM_CUDA(cudaFuncSetAttribute(k_mlp_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem()));
+    PM_CUDA(cudaFuncSetAttribute(k_mlp_train_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TrSmem)));
     PM_CUDA(cudaFuncSetAttribute(k_mlp<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp_smem(false)));
     PM_CUDA(cudaFuncSetAttribute(k_mlp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp_smem(true)));
     return PM_OK;
@@ -1431,7 +1784,11 @@ static pm_status mlp_launch(pm_model *md, bool train, const void *x, int64_t row
     const __nv_bfloat16 *W2b = static_cast<const __nv_bfloat16 *>(md->W2b.ptr);
     const __nv_bfloat16 *w3b = static_cast<const __nv_bfloat16 *>(md->w3b.ptr);
     const float *P = static_cast<const float *>(md->P.ptr);
-    if (train)
+    if (train && train_tc())
+        k_mlp_train_tc<<<(unsigned)pm_ceil_div(pm_ceil_div(rows, kTcRows), kTrTiles), kTrThreads, sizeof(TrSmem),
+                         s>>>(X, rows, W1b, W2b, w3b, P, t, inv_batch, static_cast<float *>(md->G.ptr),
+                              static_cast<float *>(md->loss.ptr), map, static_cast<int *>(md->err.ptr));
+    else if (train)
         k_mlp<true><<<grid, 128, mlp_smem(true), s>>>(X, rows, W1b, W2b, w3b, P, y, t, inv_batch,
                                                       static_cast<float *>(md->G.ptr),
                                                       static_cast<float *>(md->loss.ptr), map);
@@ -1487,7 +1844,7 @@ static pm_status model_grad(pm_model *md, const uint16_t *x, const float *t, int
 extern "C" pm_status pm_model_grad(pm_model *md, const uint16_t *x, const float *t, int64_t rows, float *grads,
                                    float *loss, void *stream)
 {
-    if (!md || !x || !t || rows < 1)
+    if (!md || !x || !t || rows < 1 || (reinterpret_cast<uintptr_t>(x) & 15u) != 0)
         return PM_ERR_INVALID_ARG;
     if (!pm_is_device_ptr(x) || !pm_is_device_ptr(t))
         return PM_ERR_INVALID_ARG;
@@ -1504,7 +1861,7 @@ extern "C" pm_status pm_model_grad(pm_model *md, const uint16_t *x, const float 
 extern "C" pm_status pm_model_train_step(pm_model *md, const uint16_t *x, const float *t, int64_t rows, float lr,
                                          float *loss, void *stream)
 {
-    if (!md || !x || !t || rows < 1 || !(lr > 0.f))
+    if (!md || !x || !t || rows < 1 || !(lr > 0.f) || (reinterpret_cast<uintptr_t>(x) & 15u) != 0)
         return PM_ERR_INVALID_ARG;
     if (!pm_is_device_ptr(x) || !pm_is_device_ptr(t))
         return PM_ERR_INVALID_ARG;
@@ -1549,7 +1906,8 @@ constexpr uint32_t kOpShuffle = 0x300u;  // operation id of the epoch shuffle's 
 extern "C" pm_status pm_model_train(pm_model *md, const uint16_t *x, const float *t, int64_t rows, int32_t epochs,
                                     int64_t batch, float lr, uint64_t seed, float *losses, void *stream)
 {
-    if (!md || !x || !t || rows < 1 || rows >= ((int64_t)1 << 31) || epochs < 0 || batch < 1 || !(lr > 0.f))
+    if (!md || !x || !t || rows < 1 || rows >= ((int64_t)1 << 31) || epochs < 0 || batch < 1 || !(lr > 0.f) ||
+        (reinterpret_cast<uintptr_t>(x) & 15u) != 0)
         return PM_ERR_INVALID_ARG;
     if (!pm_is_device_ptr(x) || !pm_is_device_ptr(t))
         return PM_ERR_INVALID_ARG;
