@@ -680,7 +680,7 @@ __global__ void __launch_bounds__(128) k_mlp(const __nv_bfloat16 *__restrict__ X
 
 // ---------------------------------------------------------------------------
 // Training (forward and backward) on the tcgen05 tensor cores.  A CTA takes
-// up to kTrTiles 128-row tiles of the batch (rows read through the epoch's
+// `tpc` consecutive 128-row tiles of the batch (rows read through the epoch's
 // permutation); per tile, with one thread issuing every MMA (BF16 operands
 // in shared memory in the K-major no-swizzle core-matrix layout, FP32
 // accumulators in tensor memory):
@@ -698,7 +698,6 @@ __global__ void __launch_bounds__(128) k_mlp(const __nv_bfloat16 *__restrict__ X
 // read the accumulators (warps w and w + 4 share TMEM lanes 32 (w mod 4) and
 // take half the columns each); every wait on an MMA is bounded.
 // ---------------------------------------------------------------------------
-constexpr int kTrTiles = 4;                // 128-row tiles per CTA per step
 constexpr int kTrThreads = 256;
 constexpr uint32_t kTrTmemCols = 512;      // C0 [0,128), C2 [128,256), C3 [256,272)
 constexpr int kLdT = 130;                  // row stride (elements) of the plain H2^T copy: odd in words
@@ -749,7 +748,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_mlp_train_tc(const __nv_bfloa
                                                                 const float *__restrict__ P,
                                                                 const float *__restrict__ t, float inv_batch,
                                                                 float *__restrict__ grads, float *__restrict__ loss,
-                                                                RowMap map, int *__restrict__ err)
+                                                                RowMap map, int tpc, int *__restrict__ err)
 {
     extern __shared__ __align__(1024) unsigned char tr_raw[];
     TrSmem &S = *reinterpret_cast<TrSmem *>(tr_raw);
@@ -804,8 +803,8 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_mlp_train_tc(const __nv_bfloa
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         return w;
     };
-    const int64_t last = blockIdx.x * (int64_t)kTrTiles + kTrTiles;
-    for (int64_t tile = blockIdx.x * (int64_t)kTrTiles; tile < tiles && tile < last && ok; ++tile) {
+    const int64_t last = blockIdx.x * (int64_t)tpc + tpc;
+    for (int64_t tile = blockIdx.x * (int64_t)tpc; tile < tiles && tile < last && ok; ++tile) {
         const int64_t pos0 = tile * kTcRows;
         // ---- the tile's rows: X (both layouts) and targets ----
         {
@@ -1784,10 +1783,15 @@ static pm_status mlp_launch(pm_model *md, bool train, const void *x, int64_t row
     const __nv_bfloat16 *W2b = static_cast<const __nv_bfloat16 *>(md->W2b.ptr);
     const __nv_bfloat16 *w3b = static_cast<const __nv_bfloat16 *>(md->w3b.ptr);
     const float *P = static_cast<const float *>(md->P.ptr);
-    if (train && train_tc())
-        k_mlp_train_tc<<<(unsigned)pm_ceil_div(pm_ceil_div(rows, kTcRows), kTrTiles), kTrThreads, sizeof(TrSmem),
-                         s>>>(X, rows, W1b, W2b, w3b, P, t, inv_batch, static_cast<float *>(md->G.ptr),
-                              static_cast<float *>(md->loss.ptr), map, static_cast<int *>(md->err.ptr));
+    if (train && train_tc()) {
+        // one tile per CTA while the batch fits the GPU (a training step's latency), more per CTA beyond it (fewer
+        // gradient atomics: the weight gradients accumulate in tensor memory)
+        const int64_t tiles = pm_ceil_div(rows, kTcRows);
+        const int tpc = (int)std::max<int64_t>(1, pm_ceil_div(tiles, (int64_t)md->sm_count));
+        k_mlp_train_tc<<<(unsigned)pm_ceil_div(tiles, tpc), kTrThreads, sizeof(TrSmem), s>>>(
+            X, rows, W1b, W2b, w3b, P, t, inv_batch, static_cast<float *>(md->G.ptr),
+            static_cast<float *>(md->loss.ptr), map, tpc, static_cast<int *>(md->err.ptr));
+    }
     else if (train)
         k_mlp<true><<<grid, 128, mlp_smem(true), s>>>(X, rows, W1b, W2b, w3b, P, y, t, inv_batch,
                                                       static_cast<float *>(md->G.ptr),
