@@ -21,12 +21,14 @@
 // Perceptron: x(16) -> 128 (ReLU) -> 128 (ReLU) -> 1, y = prediction of the
 // cost change / Z.  Parameters, flat FP32 masters: W1 [16][128], b1 [128],
 // W2 [128][128], b2 [128], w3 [128], b3 [1] (row = input unit); BF16
-// copies of W1, W2, w3 feed mma.sync.m16n8k16.  Hidden activations are
+// copies of W1, W2, w3 feed the tensor cores.  Hidden activations are
 // rounded to BF16 after the ReLU; gradients of the hidden layers are rounded
-// to BF16 before they enter a tensor-core product.  One CTA handles 64 rows:
-// forward, and in training the whole backward pass, with the weight
-// gradients of its rows added atomically into an FP32 gradient buffer; then
-// one Adam kernel updates the masters and refreshes the BF16 copies.
+// to BF16 before they enter a tensor-core product.  Inference runs on
+// tcgen05 (k_mlp_fwd_tc), and so does training (k_mlp_train_tc: forward and
+// the whole backward pass per 128-row tile, weight gradients accumulated in
+// tensor memory and added into an FP32 gradient buffer); the mma.sync
+// kernel k_mlp (64 rows per CTA) remains for comparison.  One Adam kernel
+// updates the masters and refreshes the BF16 copies.
 
 #include <cuda_bf16.h>
 
