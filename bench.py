@@ -164,17 +164,30 @@ def measured_bf16_peak():
         return 1900.0, "fallback"
 
 
-def fitness_source_hash():
-    """Hash of the scan kernel's code (fitness.cu, scan_walk.cuh and pm_common.cuh without their comments and blank
-    lines): the key that ties a committed ncu summary to the code it was taken on."""
+def scan_source_text(read):
+    """The code of the scan kernel k_scan_columns: its region of fitness.cu (from the epilogue arguments to the row
+    kernel), the client walk (scan_walk.cuh) and the bit transpose of pm_common.cuh.  read(name) returns a source
+    file's text."""
+    fit = read("fitness.cu")
+    parts = [fit[fit.index("struct ScanEpilogue {"):fit.index("// Row kernel (fallback")], read("scan_walk.cuh")]
+    common = read("pm_common.cuh")
+    i = common.index("__device__ __forceinline__ uint32_t pm_transpose32")
+    parts.append(common[i:common.index("\n}\n", i) + 3])
+    return "\n".join(parts)
+
+
+def fitness_source_hash(read=None):
+    """Hash of the scan kernel's code (scan_source_text without comments and blank lines): the key that ties a
+    committed ncu summary to the code it was taken on."""
     import re
 
-    h = hashlib.sha256()
-    for f in ("fitness.cu", "scan_walk.cuh", "pm_common.cuh"):
-        with open(os.path.join(ROOT, "paper_1610_10061_gb300", "csrc", f)) as fh:
-            text = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
-        text = re.sub(r"//[^\n]*", "", text)
-        h.update("\n".join(line.rstrip() for line in text.splitlines() if line.strip()).encode())
+    if read is None:
+        def read(name):
+            with open(os.path.join(ROOT, "paper_1610_10061_gb300", "csrc", name)) as fh:
+                return fh.read()
+    text = re.sub(r"/\*.*?\*/", "", scan_source_text(read), flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    h = hashlib.sha256("\n".join(line.rstrip() for line in text.splitlines() if line.strip()).encode())
     return h.hexdigest()[:16]
 
 
