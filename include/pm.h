@@ -230,8 +230,9 @@ PM_API pm_status pm_eval_columns(pm_instance *inst, const uint32_t *cols, int64_
  * one-wave default (x1/2, x1, x2); the row kernel with bitsets and with byte
  * masks (one byte per facility, where 8 warps' masks fit in shared memory).  Each
  * candidate evaluates a uniformly random population (Floyd sampling, fixed
- * seed) once untimed and five times timed with CUDA events on `stream`; the
- * fastest median is kept for this (instance, pop) and used by every later
+ * seed) once untimed, then five times eight back-to-back evaluations timed
+ * with CUDA events on `stream` (the GA chains its evaluations the same way);
+ * the fastest median is kept for this (instance, pop) and used by every later
  * evaluation of that size (pm_eval_population, pm_eval_population_noalloc
  * and GAs created afterwards).  chosen (nullable, host) receives it.
  * Synchronises `stream`.  Errors: PM_ERR_INVALID_ARG, PM_ERR_OOM, PM_ERR_CUDA.

@@ -15,8 +15,11 @@
 
 #include "pm_common.cuh"
 
-// Timed launches per autotuner candidate (after one warm-up); the median decides.
+// Timed repetitions per autotuner candidate (after one warm-up); the median decides.  Each repetition is a
+// sequence of kTuneChain back-to-back launches, as the GA chains its evaluations (programmatic dependent launch
+// overlaps a launch's start with the previous one's end), and counts as its mean.
 static constexpr int kTuneReps = 5;
+static constexpr int kTuneChain = 8;
 
 namespace {
 bool same_shape(const pm_eval_plan &a, const pm_eval_plan &b)
@@ -104,10 +107,12 @@ extern "C" pm_status pm_tune_eval(pm_instance *inst, int64_t pop, void *stream, 
         float t[kTuneReps];
         for (int r = 0; r < kTuneReps && st == PM_OK; ++r) {
             cudaEventRecord(e0, s);
-            st = run();
+            for (int c = 0; c < kTuneChain && st == PM_OK; ++c)
+                st = run();
             cudaEventRecord(e1, s);
             if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t[r], e0, e1) != cudaSuccess)
                 st = PM_ERR_CUDA;
+            t[r] /= (float)kTuneChain;
         }
         if (st != PM_OK)
             break;
