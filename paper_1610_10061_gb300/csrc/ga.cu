@@ -790,8 +790,9 @@ __device__ __forceinline__ bool crossover_child(const uint32_t *C, const uint32_
 __global__ void __launch_bounds__(1024) k_ga_crossover(const ga_prob *__restrict__ gps, int K, ga_prob one,
                                                        const uint32_t *__restrict__ X, uint32_t *__restrict__ Xc,
                                                        uint32_t *__restrict__ active, uint32_t round, uint64_t seed,
-                                                       ga_dev *__restrict__ st, ColumnsOut co)
+                                                       ga_dev *__restrict__ st, ColumnsOut co, int rows_in_smem)
 {
+    extern __shared__ uint32_t crows[];  // [32][W] the children, when rows_in_smem (transposed from here)
     __shared__ uint32_t valid_s;
     int k;
     const ga_prob gp = prob_of_group(gps, K, one, blockIdx.x, k);
@@ -822,8 +823,14 @@ __global__ void __launch_bounds__(1024) k_ga_crossover(const ga_prob *__restrict
     if (t < gp.pop) {
         const uint32_t r1 = uniform_below(v.x, (uint32_t)gp.m);
         const int i = 1 + (int)uniform_below(v.y, (uint32_t)(p / 2));
-        const bool ok = crossover_child<false>(X + gp.word_base + t * W, X + gp.word_base + partner * W,
-                                               Xc + gp.word_base + t * W, W, r1, i, lane);
+        uint32_t *F = rows_in_smem ? crows + (int64_t)j * W : Xc + gp.word_base + t * W;
+        const bool ok = crossover_child<false>(X + gp.word_base + t * W, X + gp.word_base + partner * W, F, W, r1,
+                                               i, lane);
+        if (rows_in_smem) {
+            __syncwarp();
+            for (int w = lane; w < W; w += 32)
+                Xc[gp.word_base + t * W + w] = F[w];
+        }
         if (lane == 0 && p / 2 > 0 && ok)
             atomicOr(&valid_s, 1u << j);
     }
@@ -833,7 +840,10 @@ __global__ void __launch_bounds__(1024) k_ga_crossover(const ga_prob *__restrict
         if (valid_s)
             atomicAdd(reinterpret_cast<unsigned long long *>(&st[k].evals), (unsigned long long)__popc(valid_s));
     }
-    write_columns(Xc + gp.word_base + t0 * W, W, t0, gp, co, lane, j, 32);
+    if (rows_in_smem)  // rows of individuals past the population were never written: write_columns reads them as 0
+        write_columns(crows, W, t0, gp, co, lane, j, 32);
+    else
+        write_columns(Xc + gp.word_base + t0 * W, W, t0, gp, co, lane, j, 32);
 }
 
 // 32 bits of the bitset C starting at bit position s (s may be as low as
@@ -966,9 +976,11 @@ __global__ void __launch_bounds__(1024) k_ga_mutate_all(const ga_prob *__restric
                                                         ga_prob oneq, int32_t Q, const uint32_t *__restrict__ X,
                                                         uint32_t *__restrict__ XQ, uint32_t *__restrict__ activeQ,
                                                         const uint8_t *__restrict__ improved, uint64_t seed,
-                                                        const ga_dev *__restrict__ st, ColumnsOut coQ)
+                                                        const ga_dev *__restrict__ st, ColumnsOut coQ,
+                                                        int rows_in_smem)
 {
     pm_grid_dependency_wait();
+    extern __shared__ uint32_t mrows[];  // [32][W] the mutants, when rows_in_smem (transposed from here)
     __shared__ uint32_t on_s;
     int k = 0;
     ga_prob gp = one, gq = oneq;
@@ -995,14 +1007,26 @@ __global__ void __launch_bounds__(1024) k_ga_mutate_all(const ga_prob *__restric
         if (improved[gp.ind_base + t] == 0) {
             if (lane == 0)
                 atomicOr(&on_s, 1u << j);
-            mutant_row(X + gp.word_base + t * W, XQ + gq.word_base + u * W, W, gp.m, seed, (uint32_t)st[k].gen,
-                       (uint32_t)t, (uint32_t)q, gp.sid, lane);
+            uint32_t *F = rows_in_smem ? mrows + (int64_t)j * W : XQ + gq.word_base + u * W;
+            mutant_row(X + gp.word_base + t * W, F, W, gp.m, seed, (uint32_t)st[k].gen, (uint32_t)t, (uint32_t)q,
+                       gp.sid, lane);
+            if (rows_in_smem) {
+                __syncwarp();
+                for (int w = lane; w < W; w += 32)
+                    XQ[gq.word_base + u * W + w] = F[w];
+            }
+        } else if (rows_in_smem) {
+            for (int w = lane; w < W; w += 32)
+                mrows[(int64_t)j * W + w] = 0u;  // not evaluated (inactive); its column bits are masked anyway
         }
     }
     __syncthreads();
     if (threadIdx.x == 0)
         activeQ[(gq.ind_base + u0) >> 5] = on_s;
-    write_columns(XQ + gq.word_base + u0 * W, W, u0, gq, coQ, lane, j, 32);
+    if (rows_in_smem)
+        write_columns(mrows, W, u0, gq, coQ, lane, j, 32);
+    else
+        write_columns(XQ + gq.word_base + u0 * W, W, u0, gq, coQ, lane, j, 32);
 }
 
 // Keep each individual's first improving try (warp per individual, 8 per
@@ -1980,6 +2004,9 @@ static pm_status enqueue_generation(pm_ga *ga, cudaStream_t s, cudaGraphConditio
     for (const ga_prob &g : ga->gps)
         pmax = std::max(pmax, g.p);
     const size_t warp_init_smem = (size_t)32 * ((size_t)ga->Wmax + (size_t)pmax) * 4;
+    // crossover children and mutants are built in shared memory (and transposed from there) when 32 rows fit
+    // in the default 48 KB; only the column path has columns to write
+    const size_t rows_smem = (!ga->single_row && (size_t)32 * ga->Wmax * 4 <= 48 * 1024) ? (size_t)32 * ga->Wmax * 4 : 0;
 
     if (ga->comb) {
         const uint32_t *T = static_cast<const uint32_t *>(ga->comb_tab.ptr);
@@ -2022,8 +2049,8 @@ static pm_status enqueue_generation(pm_ga *ga, cudaStream_t s, cudaGraphConditio
     acc.columns_ready = true;
     if (ga->gps[0].p / 2 > 0) {  // p = 1: no crossover (a batch has p >= 2 everywhere or p = 1 everywhere)
         for (int r = 0; r < ga->R; ++r) {
-            PM_CUDA(pm_launch(k_ga_crossover, groups, 1024, 0, s, gps, K, one, X, Xc, active, (uint32_t)r, ga->seed,
-                              st, co));
+            PM_CUDA(pm_launch(k_ga_crossover, groups, 1024, rows_smem, s, gps, K, one, X, Xc, active, (uint32_t)r,
+                              ga->seed, st, co, rows_smem ? 1 : 0));
             acc.improved = nullptr;
             PM_TRY(ga_eval(ga, Xc, nullptr, acc, s));
         }
@@ -2053,8 +2080,8 @@ static pm_status enqueue_generation(pm_ga *ga, cudaStream_t s, cudaGraphConditio
         coQ.colT = static_cast<uint32_t *>(ga->colQ.ptr);
         coQ.G = ga->spec_plan.groups;
         const ga_prob *gqs = static_cast<const ga_prob *>(ga->gqprobs.ptr);
-        PM_CUDA(pm_launch(k_ga_mutate_all, (unsigned)ga->groupsQ_total, 1024, 0, s, gps, gqs, K, one, ga->gq,
-                          (int32_t)ga->Q, X, XQ, activeQ, improved, ga->seed, st, coQ));
+        PM_CUDA(pm_launch(k_ga_mutate_all, (unsigned)ga->groupsQ_total, 1024, rows_smem, s, gps, gqs, K, one,
+                          ga->gq, (int32_t)ga->Q, X, XQ, activeQ, improved, ga->seed, st, coQ, rows_smem ? 1 : 0));
         pm_scan_launch L;
         pm_scan_launch_from(ga->spec_plan, static_cast<const pm_prob *>(ga->probsQ.ptr), L);
         L.masks = XQ;
