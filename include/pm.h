@@ -407,8 +407,9 @@ PM_API pm_status pm_ga_create(pm_instance *inst, uint64_t seed, int64_t pop, con
 
 /*
  * pm_ga_step -- run up to `gens` more generations on the device (one CUDA
- * graph launch; the loop is a conditional while-node, so the host is not
- * involved between generations).  A generation is: a fresh random
+ * graph launch: for gens = 1 a plain graph of the generation's kernels, else
+ * a conditional while-node around them, so the host is not involved between
+ * generations).  A generation is: a fresh random
  * population (Floyd sampling) whose slot 0 of every deme receives that
  * deme's best of the previous generation (migration, Section 4.5 variant
  * (i)); evaluation; crossover rounds with butterfly partners t XOR
@@ -469,7 +470,9 @@ PM_API pm_status pm_ga_destroy(pm_ga *ga);
  * pm_ga_info -- the resolved parameters of a GA (any output may be NULL):
  * pop, deme size D, crossover rounds, mutation tries, and the number of
  * library kernels one generation launches (the graph body), plus the number
- * launched once per pm_ga_step call (outside the body).  No device work.
+ * launched once per pm_ga_step call of one generation (outside the body; a
+ * graph-mode call of several generations also launches the loop's gate
+ * kernel).  No device work.
  */
 PM_API pm_status pm_ga_info(const pm_ga *ga, int64_t *pop, int64_t *deme, int32_t *xover_rounds, int32_t *mut_tries,
                             int64_t *kernels_per_generation, int64_t *kernels_per_step_call);

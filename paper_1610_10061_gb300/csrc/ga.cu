@@ -307,7 +307,15 @@ __global__ void __launch_bounds__(32) k_ga_init(const ga_prob *__restrict__ gps,
 // generation; any other individual is a fresh p-subset by Floyd's sampling,
 // the lanes computing the p Philox draws in parallel (lane l the counter
 // blocks l, l + 32, ...; draw q is uniform below m - p + q + 1) into `draws`
-// (p words, shared) and lane 0 running the p dependent insertions.
+// (p words, shared).  Floyd's insertions are sequential -- draw q takes c_q
+// unless c_q is already in the set, else m - p + q -- and are resolved 32 at
+// a time, lane l taking draw q0 + l: against the set of the earlier batches
+// by one bit test, against the earlier lanes of its batch by iterating
+// "take m - p + q iff c_q is in the set or is an earlier lane's current
+// pick" to its fixed point (after iteration i lanes 0..i hold the sequential
+// picks, so at most 32 iterations, usually one).  The picks are distinct
+// (m - p + q exceeds every earlier pick), so the batch is inserted with one
+// atomic OR per lane.
 template <bool kCG>
 __device__ __forceinline__ void fresh_individual(const ga_prob &gp, int64_t t, uint32_t gen, uint64_t seed,
                                                  const uint32_t *__restrict__ deme_best, uint32_t *row,
@@ -332,13 +340,29 @@ __device__ __forceinline__ void fresh_individual(const ga_prob &gp, int64_t t, u
             }
         }
         __syncwarp();
-        if (lane == 0) {
-            for (int q = 0; q < p; ++q) {
-                const uint32_t c = draws[q];
-                const uint32_t jj = (uint32_t)(m - p + q);
-                const uint32_t pick = ((row[c >> 5] >> (c & 31)) & 1u) ? jj : c;
-                row[pick >> 5] |= 1u << (pick & 31);
+        for (int q0 = 0; q0 < p; q0 += 32) {
+            const int q = q0 + lane;
+            const bool live = q < p;
+            const int nb = (p - q0) < 32 ? (p - q0) : 32;
+            const uint32_t c = live ? draws[q] : 0u;
+            const uint32_t jj = (uint32_t)(m - p + q);
+            const bool inset = live && ((row[c >> 5] >> (c & 31)) & 1u) != 0u;
+            uint32_t pick = inset ? jj : c;
+            for (int it = 0; it < nb; ++it) {
+                bool taken = false;  // c is the current pick of an earlier lane of the batch
+                for (int l = 0; l < nb; ++l) {
+                    const uint32_t pl = __shfl_sync(PM_FULL_MASK, pick, l);
+                    taken |= (l < lane) && (pl == c);
+                }
+                const uint32_t np = (inset || taken) ? jj : c;
+                const bool changed = __any_sync(PM_FULL_MASK, live && np != pick);
+                pick = np;
+                if (!changed)
+                    break;
             }
+            if (live)
+                atomicOr(&row[pick >> 5], 1u << (pick & 31));
+            __syncwarp();
         }
     }
     __syncwarp();
@@ -971,7 +995,7 @@ __global__ void __launch_bounds__(1024) k_ga_mutate(const ga_prob *__restrict__ 
 // (or oneq for one instance) lays out instance k's Q x pop candidates: their
 // rows, facility-major tiles, active bits and costs (ind_base), and their
 // first 32-candidate group (grp_base).
-__global__ void __launch_bounds__(1024) k_ga_mutate_all(const ga_prob *__restrict__ gps,
+__global__ void __launch_bounds__(1024, 2) k_ga_mutate_all(const ga_prob *__restrict__ gps,
                                                         const ga_prob *__restrict__ gqs, int K, ga_prob one,
                                                         ga_prob oneq, int32_t Q, const uint32_t *__restrict__ X,
                                                         uint32_t *__restrict__ XQ, uint32_t *__restrict__ activeQ,
@@ -1244,6 +1268,146 @@ __global__ void k_ga_generation_end(const ga_prob *__restrict__ gps, int K, ga_p
             a += alive_s[w];
         glob->alive = a;
         glob->done = 0;
+        glob->step_gens += 1;
+        glob->remaining -= 1;
+        if (in_graph)
+            cudaGraphSetConditional(h, (glob->remaining > 0 && a > 0) ? 1u : 0u);
+    }
+}
+
+// The generation end of a single-instance GA (same results as
+// k_ga_generation_end) in one CTA of 1024 threads, without tickets: each warp
+// reduces (cost, index) over its 32 individuals by a butterfly whose first
+// lg(min(D, 32)) steps stay inside a deme; demes wider than a warp combine
+// their warps' minima in shared memory.  The global best is the lowest
+// (cost, index) over all individuals -- the same individual as the lowest
+// (cost, deme) over the deme bests.  Rows are copied by all threads.
+__global__ void __launch_bounds__(1024) k_ga_generation_end_one(ga_prob gp, const uint32_t *__restrict__ X,
+                                                                const int64_t *__restrict__ cost,
+                                                                uint32_t *__restrict__ deme_best,
+                                                                int64_t *__restrict__ deme_cost,
+                                                                uint32_t *__restrict__ best, ga_dev *__restrict__ st,
+                                                                ga_glob *__restrict__ glob,
+                                                                cudaGraphConditionalHandle h, int in_graph)
+{
+    pm_grid_dependency_wait();
+    __shared__ long long wc[32], wi[32];  // per-warp minima of the current 1024-individual tile
+    __shared__ long long gc[32], gi[32];  // per-warp minima over all tiles
+    __shared__ int win_s[1024];           // winner of each deme of the tile (D <= 32: one per D lanes)
+    __shared__ long long gwin;
+    __shared__ int improve;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    ga_dev &s = st[0];
+    const bool running = !s.stop;
+    const int32_t W = gp.W;
+    const int64_t D = gp.D;
+    const int seg = D < 32 ? (int)D : 32;
+    constexpr long long kNone = 0x7fffffffffffffffLL;
+    if (running) {
+        long long mc = kNone, mi = kNone;  // this warp's minimum over all tiles (lane 0)
+        for (int64_t t0 = 0; t0 < gp.pop; t0 += 1024) {
+            const int64_t t = t0 + threadIdx.x;
+            long long c = kNone, i = kNone;
+            if (t < gp.pop) {
+                c = cost[gp.ind_base + t];
+                i = t;
+            }
+            long long sc = c, si = i;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const long long oc = __shfl_xor_sync(PM_FULL_MASK, c, o);
+                const long long oi = __shfl_xor_sync(PM_FULL_MASK, i, o);
+                if (oc < c || (oc == c && oi < i)) {
+                    c = oc;
+                    i = oi;
+                }
+                if (o == seg / 2) {  // the deme's (or the warp's, for D >= 32) minimum
+                    sc = c;
+                    si = i;
+                }
+            }
+            if (seg == 1) {
+                sc = c;
+                si = i;
+            }
+            if (lane == 0) {
+                wc[warp] = c;
+                wi[warp] = i;
+                if (c < mc || (c == mc && i < mi)) {
+                    mc = c;
+                    mi = i;
+                }
+            }
+            const int nd = (int)((gp.pop - t0) < 1024 ? (gp.pop - t0) : 1024) / (int)D;  // demes of the tile
+            if (D <= 32) {
+                if ((lane % seg) == 0 && t < gp.pop) {
+                    const int64_t d = t / D;
+                    deme_cost[gp.deme_base + d] = sc;
+                    win_s[threadIdx.x / seg] = (int)(si - t0);
+                }
+            }
+            __syncthreads();
+            if (D > 32 && threadIdx.x < nd) {
+                const int per = (int)(D >> 5);
+                long long bc = kNone, bi = kNone;
+                for (int w = threadIdx.x * per; w < (threadIdx.x + 1) * per; ++w)
+                    if (wc[w] < bc || (wc[w] == bc && wi[w] < bi)) {
+                        bc = wc[w];
+                        bi = wi[w];
+                    }
+                deme_cost[gp.deme_base + t0 / D + threadIdx.x] = bc;
+                win_s[threadIdx.x] = (int)(bi - t0);
+            }
+            __syncthreads();
+            for (int64_t x = threadIdx.x; x < (int64_t)nd * W; x += blockDim.x) {
+                const int64_t d = x / W, w = x - d * W;
+                deme_best[gp.dword_base + (t0 / D + d) * W + w] = X[gp.word_base + (t0 + win_s[d]) * W + w];
+            }
+            __syncthreads();
+        }
+        if (lane == 0) {
+            gc[warp] = mc;
+            gi[warp] = mi;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            long long c = gc[lane], i = gi[lane];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const long long oc = __shfl_xor_sync(PM_FULL_MASK, c, o);
+                const long long oi = __shfl_xor_sync(PM_FULL_MASK, i, o);
+                if (oc < c || (oc == c && oi < i)) {
+                    c = oc;
+                    i = oi;
+                }
+            }
+            if (lane == 0) {
+                const bool better = s.best_cost < 0 || c < s.best_cost;
+                improve = better ? 1 : 0;
+                gwin = i;
+                if (better) {
+                    s.best_cost = c;
+                    s.sat = 0;
+                } else {
+                    s.sat += 1;
+                }
+                if (s.trace)
+                    s.trace[glob->step_gens] = s.best_cost;
+                s.evals += gp.pop;
+                s.gen += 1;
+                s.total_gens += 1;
+                s.stop = (s.saturation > 0 && s.sat >= s.saturation) ? 1 : 0;
+            }
+        }
+        __syncthreads();
+        if (improve)
+            for (int w = threadIdx.x; w < W; w += blockDim.x)
+                best[gp.best_base + w] = X[gp.word_base + gwin * W + w];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int a = s.stop ? 0 : 1;
+        glob->alive = a;
         glob->step_gens += 1;
         glob->remaining -= 1;
         if (in_graph)
@@ -1911,7 +2075,8 @@ struct pm_ga {
     pm_dbuf s_gain, s_cap, s_loss, s_assign, moves, xfeat, scores;
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
+    cudaGraphExec_t exec = nullptr;   // gate + conditional while-node over the generation
+    cudaGraphExec_t exec1 = nullptr;  // one generation, no loop (calls of one generation)
 };
 
 static void ga_free(pm_ga *ga)
@@ -1921,6 +2086,8 @@ static void ga_free(pm_ga *ga)
     pm_clear_error(cudaSetDevice(ga->device));
     if (ga->exec)
         pm_clear_error(cudaGraphExecDestroy(ga->exec));
+    if (ga->exec1)
+        pm_clear_error(cudaGraphExecDestroy(ga->exec1));
     if (ga->graph)
         pm_clear_error(cudaGraphDestroy(ga->graph));
     if (ga->cap)
@@ -2103,6 +2270,13 @@ static pm_status enqueue_generation(pm_ga *ga, cudaStream_t s, cudaGraphConditio
             PM_TRY(ga_eval(ga, Xc, nullptr, acc, s));
         }
     }
+    if (K == 1) {
+        PM_CUDA(pm_launch(k_ga_generation_end_one, 1u, 1024u, 0, s, one, X, cost,
+                          static_cast<uint32_t *>(ga->deme_best.ptr), static_cast<int64_t *>(ga->deme_cost.ptr),
+                          static_cast<uint32_t *>(ga->best.ptr), st, static_cast<ga_glob *>(ga->glob.ptr), h,
+                          in_graph));
+        return PM_OK;
+    }
     const int dthreads = (int)pm_round_up(std::min<int64_t>(ga->D, 1024), 32);
     PM_CUDA(pm_launch(k_ga_generation_end, (unsigned)ga->demes_total, (unsigned)dthreads, 0, s, gps, K, one, X,
                       cost, static_cast<uint32_t *>(ga->deme_best.ptr), static_cast<int64_t *>(ga->deme_cost.ptr),
@@ -2140,6 +2314,17 @@ static pm_status build_graph(pm_ga *ga)
     PM_TRY(st_gen);
     PM_CUDA(e);
     PM_CUDA(cudaGraphInstantiate(&ga->exec, ga->graph, 0));
+    // the same generation as a plain graph for calls of one generation: entering and leaving a conditional
+    // body costs about 6 us each way, a tenth of a graph900 generation
+    PM_CUDA(cudaStreamBeginCapture(ga->cap, cudaStreamCaptureModeThreadLocal));
+    st_gen = enqueue_generation(ga, ga->cap, h, 0);
+    cudaGraph_t one = nullptr;
+    e = cudaStreamEndCapture(ga->cap, &one);
+    PM_TRY(st_gen);
+    PM_CUDA(e);
+    e = cudaGraphInstantiate(&ga->exec1, one, 0);
+    pm_clear_error(cudaGraphDestroy(one));
+    PM_CUDA(e);
     return PM_OK;
 }
 
@@ -2656,7 +2841,7 @@ extern "C" pm_status pm_ga_step(pm_ga *ga, int64_t gens, int64_t *trace, void *s
     if (ga->fused) {
         PM_TRY(fused_launch(ga, s));
     } else if (graph_mode()) {
-        PM_CUDA(cudaGraphLaunch(ga->exec, s));
+        PM_CUDA(cudaGraphLaunch(gens == 1 ? ga->exec1 : ga->exec, s));
     } else {
         // the same kernels, enqueued generation by generation (profilers cannot see
         // kernels inside conditional graphs); saturation needs the host to look
@@ -2874,7 +3059,7 @@ extern "C" pm_status pm_ga_info(const pm_ga *ga, int64_t *pop, int64_t *deme, in
         *kernels_per_generation = 1 + per_eval + rounds * (1 + per_eval) +
                                   (ga->spec ? 3 : ga->Q * (1 + per_eval)) + 1 + (ga->model ? 4 + per_eval : 0);
     if (kernels_per_step_call)
-        *kernels_per_step_call = graph_mode() ? 2 : 1;  // k_ga_begin (and the gate in graph mode)
+        *kernels_per_step_call = 1;  // k_ga_begin (a graph-mode call of several generations adds the loop's gate)
     return PM_OK;
 }
 

@@ -328,6 +328,33 @@ def test_ga_stream_launch_mode_matches_graph_mode(pm, monkeypatch):
     _ga_compare(pm, graph_instance(30, 60, seed=1), 3, 32, 300, check_every=300, deme=16, saturation=4)
 
 
+def test_one_generation_calls_equal_one_long_call(pm, monkeypatch):
+    """Calls of one generation run a plain graph of the generation (no conditional loop); stepping one generation
+    at a time gives the same traces, populations and results as one call of many generations, including across
+    a saturation stop (the later one-generation calls change nothing)."""
+    monkeypatch.delenv("PM_GA_GRAPH", raising=False)
+    w = paper_shape_instance("graph900")
+    inst = pm.Instance(w["d"], w["p"])
+    a = pm.GA(inst, seed=5, pop=512, deme=128)
+    ta = a.step(6)
+    b = pm.GA(inst, seed=5, pop=512, deme=128)
+    tb = np.concatenate([b.step(1) for _ in range(6)])
+    np.testing.assert_array_equal(ta, tb)
+    for x, y in zip(a.population(), b.population()):
+        np.testing.assert_array_equal(x, y)
+    assert a.result()[:3] == b.result()[:3]
+    d = graph_instance(30, 60, seed=1)
+    small = pm.Instance(d, 3)
+    a = pm.GA(small, seed=2, pop=32, deme=16, saturation=3)
+    a.step(60)
+    b = pm.GA(small, seed=2, pop=32, deme=16, saturation=3)
+    for _ in range(60):
+        b.step(1)
+    ra, rb = a.result(), b.result()
+    assert ra[:3] == rb[:3] and ra[1] < 60  # stopped by saturation, at the same generation
+    np.testing.assert_array_equal(ra[3], rb[3])
+
+
 def _ga_run_pair(pm, monkeypatch, d, p, pop, gens, steps, **kw):
     """The same GA twice, with the persistent generation kernel (PM_GA_FUSED=1) and with the per-phase kernels
     (the default): traces, populations, costs and results."""
