@@ -60,7 +60,21 @@ def parse_args():
                          "columns, the row kernel with bitsets and the row kernel with byte masks")
     ap.add_argument("--mode", default="ga", choices=["ga", "eval"],
                     help="ga: GA generations (default); eval: one fitness evaluation pass of a random population")
+    ap.add_argument("--eval-tile", default=None, metavar="G,WARPS,SPLITS",
+                    help="ga mode: pin the population's evaluation tile instead of autotuning it (for profiling "
+                         "runs, whose timings would steer the autotuner elsewhere)")
+    ap.add_argument("--mutation-tile", default=None, metavar="G,WARPS,SPLITS",
+                    help="ga mode: pin the tile of the mutation candidates' evaluation")
     return ap.parse_args()
+
+
+def tile_shape(pm, inst, pop, spec, stream):
+    """The autotuned evaluation tile for `pop`, or the one pinned by a --*-tile argument ("G,WARPS,SPLITS")."""
+    if not spec:
+        return inst.tune(pop, stream=stream)
+    g, w, sp = (int(x) for x in spec.split(","))
+    pm.pm_set_eval_shape(inst.handle, pop, g, w, sp)
+    return {"groups": g, "warps": w, "splits": sp, "grid": None, "pinned": True}
 
 
 def dist_env():
@@ -555,8 +569,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     cum = args.tables == "cumulative"
     inst = pm.Instance(d, p, device=local, stream=stream.cuda_stream, cumulative=cum)
-    shape = inst.tune(pop, stream=stream.cuda_stream)  # autotuned evaluation tile (kept by the instance)
-    spec_shape = inst.tune(pop * lg, stream=stream.cuda_stream)  # the lg(deme) mutation tries evaluated together
+    shape = tile_shape(pm, inst, pop, args.eval_tile, stream.cuda_stream)  # kept by the instance
+    spec_shape = tile_shape(pm, inst, pop * lg, args.mutation_tile, stream.cuda_stream)  # the lg(deme) tries together
     ga = pm.GA(inst, seed=0, pop=pop, deme=deme, stream_id=rank, init=args.init, stream=stream.cuda_stream)
     info = ga.info()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
