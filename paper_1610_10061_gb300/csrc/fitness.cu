@@ -555,14 +555,24 @@ const void *scan_fn()
 
 static size_t column_smem_bytes(int64_t W, int G) { return (size_t)W * 32 * G * 4; }
 
+// Let `fn` take all the opt-in shared memory its static shared memory leaves.
+template <typename F>
+static pm_status allow_dynamic_smem(const pm_instance *inst, F *fn)
+{
+    cudaFuncAttributes fa;
+    PM_CUDA(cudaFuncGetAttributes(&fa, fn));
+    const size_t cap = inst->smem_optin > fa.sharedSizeBytes ? inst->smem_optin - fa.sharedSizeBytes : 0;
+    PM_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap));
+    return PM_OK;
+}
+
 pm_status pm_fitness_init(const pm_instance *inst)
 {
-    const int cap = (int)(inst->smem_optin > 2048 ? inst->smem_optin - 2048 : inst->smem_optin);
-    PM_CUDA(cudaFuncSetAttribute(k_scan_columns<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
-    PM_CUDA(cudaFuncSetAttribute(k_scan_columns<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
-    PM_CUDA(cudaFuncSetAttribute(k_scan_columns<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
-    PM_CUDA(cudaFuncSetAttribute(k_scan_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
-    PM_CUDA(cudaFuncSetAttribute(k_scan_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+    PM_TRY(allow_dynamic_smem(inst, k_scan_columns<1>));
+    PM_TRY(allow_dynamic_smem(inst, k_scan_columns<2>));
+    PM_TRY(allow_dynamic_smem(inst, k_scan_columns<4>));
+    PM_TRY(allow_dynamic_smem(inst, k_scan_rows<false>));
+    PM_TRY(allow_dynamic_smem(inst, k_scan_rows<true>));
     return PM_OK;
 }
 
