@@ -27,17 +27,12 @@
 //   k_ga_generation_end  lowest (cost, index) per deme (Section 3.2.2 step
 //                    7); the last deme of an instance updates its global best
 //                    (strict improvement), saturation counter, trace and
-//                    counters; the last instance sets the loop condition
-//                    (k_ga_generation_end_one: the same for one instance in
-//                    one CTA).
+//                    counters; the last instance sets the loop condition.
 // The operators also write the facility-major copy of their output that the
-// scan reads, so no evaluation needs a separate transpose; the initialisation,
-// crossover and mutant kernels take 8 individuals per CTA and write their
-// byte of each column word, so their work spreads over every SM.  A call of
-// several generations is one CUDA graph: a gate kernel and a conditional
-// while-node whose body is one generation; a call of one generation launches
-// a plain graph of the body.  An instance that reached its saturation limit
-// stops: its kernels do nothing while the others go on.
+// scan reads, so no evaluation needs a separate transpose.  The loop is one
+// CUDA graph: a gate kernel and a conditional while-node whose body is one
+// generation.  An instance that reached its saturation limit stops: its
+// kernels do nothing while the others go on.
 //
 // Random numbers: Philox4x32-10 (Salmon et al., SC'11), stateless, keyed by
 // (seed) with counter (generation, unit, op * 2^16 + slot / 4, stream id);
@@ -225,35 +220,6 @@ __device__ __forceinline__ void write_columns(const uint32_t *rows, int64_t rs, 
     }
 }
 
-// The same for 8 rows: individuals t0 .. t0+7 (t0 a multiple of 8) are byte
-// t0%32/8 of their group's column words, so each facility's byte is stored on
-// its own (CTAs of 8 individuals write disjoint bytes of the same words).
-__device__ __forceinline__ void write_columns8(const uint32_t *rows, int64_t rs, int64_t t0, const ga_prob &gp,
-                                               ColumnsOut co, int lane, int w_begin, int w_step)
-{
-    if (co.colT == nullptr)
-        return;
-    const int32_t W = gp.W;
-    const int64_t tile = t0 / (32 * co.G);
-    const int32_t g = (int32_t)((t0 / 32) % co.G);
-    const int sub = (int)((t0 & 31) >> 3);
-    uint8_t *base = reinterpret_cast<uint8_t *>(co.colT + gp.col_base);
-    for (int w = w_begin; w < W; w += w_step) {
-        uint32_t b = 0u;
-#pragma unroll
-        for (int r = 0; r < 8; ++r)
-            if (t0 + r < gp.pop)
-                b |= ((rows[(int64_t)r * rs + w] >> lane) & 1u) << r;
-        base[((tile * (int64_t)W * 32 + (int64_t)w * 32 + lane) * co.G + g) * 4 + sub] = (uint8_t)b;
-    }
-}
-
-// Byte t0%32/8 of the active word of individuals t0 .. t0+7 (instance-relative t0, a multiple of 8).
-__device__ __forceinline__ void set_active8(uint32_t *active, const ga_prob &gp, int64_t t0, uint32_t bits)
-{
-    reinterpret_cast<uint8_t *>(active)[((gp.ind_base + t0) >> 5) * 4 + ((t0 & 31) >> 3)] = (uint8_t)bits;
-}
-
 // ------------------------------- kernels -----------------------------------
 
 __global__ void k_ga_begin(ga_glob *glob, ga_dev *st, int K, long long gens, long long *trace, unsigned *bar)
@@ -402,31 +368,30 @@ __device__ __forceinline__ void fresh_individual(const ga_prob &gp, int64_t t, u
     __syncwarp();
 }
 
-// The same fresh population as k_ga_init with one warp per individual
-// (fresh_individual: the lanes draw in parallel and resolve Floyd's
-// insertions 32 at a time).  CTA = 8 warps = 8 individuals (a quarter of a
-// 32-individual group, so the population spreads over the whole GPU); needs
-// 8 * (W + p) words of shared memory.
-__global__ void __launch_bounds__(256) k_ga_init_warp(const ga_prob *__restrict__ gps, int K, ga_prob one,
-                                                      uint32_t *__restrict__ X, uint8_t *__restrict__ improved,
-                                                      uint32_t *__restrict__ active,
-                                                      const uint32_t *__restrict__ deme_best, uint64_t seed,
-                                                      const ga_dev *__restrict__ st, ColumnsOut co)
+// The same fresh population as k_ga_init with one warp per individual: the
+// lanes compute the p Philox draws of Floyd's sampling in parallel (lane l
+// the counter blocks l, l + 32, ...), then lane 0 runs the p dependent
+// insertions on the warp's bitset in shared memory.  CTA = 32 warps = 32
+// individuals; needs 32 * W words of shared memory.
+__global__ void __launch_bounds__(1024) k_ga_init_warp(const ga_prob *__restrict__ gps, int K, ga_prob one,
+                                                       uint32_t *__restrict__ X, uint8_t *__restrict__ improved,
+                                                       uint32_t *__restrict__ active,
+                                                       const uint32_t *__restrict__ deme_best, uint64_t seed,
+                                                       const ga_dev *__restrict__ st, ColumnsOut co)
 {
     pm_grid_dependency_wait();
-    extern __shared__ uint32_t wrows[];  // [8][W] bitsets, then [8][p] draws
+    extern __shared__ uint32_t wrows[];  // [32][W] bitsets, then [32][p] draws
     __shared__ uint32_t on_s;
     int k;
-    const int64_t gid = blockIdx.x >> 2;
-    const ga_prob gp = prob_of_group(gps, K, one, gid, k);
+    const ga_prob gp = prob_of_group(gps, K, one, blockIdx.x, k);
     const int lane = threadIdx.x & 31;
     const int j = threadIdx.x >> 5;
-    const int64_t t0 = (gid - gp.grp_base) * 32 + 8 * (blockIdx.x & 3);
+    const int64_t t0 = (blockIdx.x - gp.grp_base) * 32;
     const int64_t t = t0 + j;
-    const int32_t W = gp.W, p = gp.p;
+    const int32_t W = gp.W, m = gp.m, p = gp.p;
     if (st[k].stop) {
         if (threadIdx.x == 0)
-            set_active8(active, gp, t0, 0u);
+            active[(gp.ind_base + t0) >> 5] = 0u;
         return;
     }
     if (threadIdx.x == 0)
@@ -434,7 +399,7 @@ __global__ void __launch_bounds__(256) k_ga_init_warp(const ga_prob *__restrict_
     __syncthreads();
     const uint32_t gen = (uint32_t)st[k].gen;
     uint32_t *row = wrows + (int64_t)j * W;
-    uint32_t *draws = wrows + (int64_t)8 * W + (int64_t)j * p;
+    uint32_t *draws = wrows + (int64_t)32 * W + (int64_t)j * p;
     if (t < gp.pop) {
         if (lane == 0) {
             improved[gp.ind_base + t] = 0;
@@ -446,8 +411,8 @@ __global__ void __launch_bounds__(256) k_ga_init_warp(const ga_prob *__restrict_
     }
     __syncthreads();
     if (threadIdx.x == 0)
-        set_active8(active, gp, t0, on_s);
-    write_columns8(wrows, W, t0, gp, co, lane, j, 8);
+        active[(gp.ind_base + t0) >> 5] = on_s;
+    write_columns(wrows, W, t0, gp, co, lane, j, 32);
 }
 
 // ------------------- combinadic chromosome generation -----------------------
@@ -844,22 +809,20 @@ __device__ __forceinline__ bool crossover_child(const uint32_t *C, const uint32_
     return c01 >= i && c10 >= i;
 }
 
-// One crossover round (Section 4.3).  CTA = 8 warps = 8 individuals (a
-// quarter of a 32-individual group, so the round's children spread over the
-// whole GPU); warp j builds the child of individual t0 + j (crossover_child).
-__global__ void __launch_bounds__(256) k_ga_crossover(const ga_prob *__restrict__ gps, int K, ga_prob one,
-                                                      const uint32_t *__restrict__ X, uint32_t *__restrict__ Xc,
-                                                      uint32_t *__restrict__ active, uint32_t round, uint64_t seed,
-                                                      ga_dev *__restrict__ st, ColumnsOut co, int rows_in_smem)
+// One crossover round (Section 4.3).  CTA = 32 warps = 32 individuals; warp
+// j builds the child of individual t0 + j (crossover_child).
+__global__ void __launch_bounds__(1024) k_ga_crossover(const ga_prob *__restrict__ gps, int K, ga_prob one,
+                                                       const uint32_t *__restrict__ X, uint32_t *__restrict__ Xc,
+                                                       uint32_t *__restrict__ active, uint32_t round, uint64_t seed,
+                                                       ga_dev *__restrict__ st, ColumnsOut co, int rows_in_smem)
 {
-    extern __shared__ uint32_t crows[];  // [8][W] the children, when rows_in_smem (transposed from here)
+    extern __shared__ uint32_t crows[];  // [32][W] the children, when rows_in_smem (transposed from here)
     __shared__ uint32_t valid_s;
     int k;
-    const int64_t gid = blockIdx.x >> 2;
-    const ga_prob gp = prob_of_group(gps, K, one, gid, k);
+    const ga_prob gp = prob_of_group(gps, K, one, blockIdx.x, k);
     const int lane = threadIdx.x & 31;
     const int j = threadIdx.x >> 5;
-    const int64_t t0 = (gid - gp.grp_base) * 32 + 8 * (blockIdx.x & 3);
+    const int64_t t0 = (blockIdx.x - gp.grp_base) * 32;
     const int64_t t = t0 + j;
     const int32_t W = gp.W;
     // the generation counter and stop flag were written by an earlier generation's end, and the draws depend on
@@ -874,7 +837,7 @@ __global__ void __launch_bounds__(256) k_ga_crossover(const ga_prob *__restrict_
     pm_grid_dependency_wait();
     if (stopped) {
         if (threadIdx.x == 0)
-            set_active8(active, gp, t0, 0u);
+            active[(gp.ind_base + t0) >> 5] = 0u;
         return;
     }
     if (threadIdx.x == 0)
@@ -897,14 +860,14 @@ __global__ void __launch_bounds__(256) k_ga_crossover(const ga_prob *__restrict_
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        set_active8(active, gp, t0, valid_s);
+        active[(gp.ind_base + t0) >> 5] = valid_s;
         if (valid_s)
             atomicAdd(reinterpret_cast<unsigned long long *>(&st[k].evals), (unsigned long long)__popc(valid_s));
     }
-    if (rows_in_smem)  // rows of individuals past the population were never written: write_columns8 skips them
-        write_columns8(crows, W, t0, gp, co, lane, j, 8);
+    if (rows_in_smem)  // rows of individuals past the population were never written: write_columns reads them as 0
+        write_columns(crows, W, t0, gp, co, lane, j, 32);
     else
-        write_columns8(Xc + gp.word_base + t0 * W, W, t0, gp, co, lane, j, 8);
+        write_columns(Xc + gp.word_base + t0 * W, W, t0, gp, co, lane, j, 32);
 }
 
 // 32 bits of the bitset C starting at bit position s (s may be as low as
@@ -1031,35 +994,33 @@ __global__ void __launch_bounds__(1024) k_ga_mutate(const ga_prob *__restrict__ 
 // but not counted.  CTA = 32 warps = 32 candidates of one instance; gqs[k]
 // (or oneq for one instance) lays out instance k's Q x pop candidates: their
 // rows, facility-major tiles, active bits and costs (ind_base), and their
-// first 32-candidate group (grp_base).  CTA = 8 warps = 8 candidates (a
-// quarter of a 32-candidate group).
-__global__ void __launch_bounds__(256) k_ga_mutate_all(const ga_prob *__restrict__ gps,
-                                                       const ga_prob *__restrict__ gqs, int K, ga_prob one,
-                                                       ga_prob oneq, int32_t Q, const uint32_t *__restrict__ X,
-                                                       uint32_t *__restrict__ XQ, uint32_t *__restrict__ activeQ,
-                                                       const uint8_t *__restrict__ improved, uint64_t seed,
-                                                       const ga_dev *__restrict__ st, ColumnsOut coQ,
-                                                       int rows_in_smem)
+// first 32-candidate group (grp_base).
+__global__ void __launch_bounds__(1024, 2) k_ga_mutate_all(const ga_prob *__restrict__ gps,
+                                                        const ga_prob *__restrict__ gqs, int K, ga_prob one,
+                                                        ga_prob oneq, int32_t Q, const uint32_t *__restrict__ X,
+                                                        uint32_t *__restrict__ XQ, uint32_t *__restrict__ activeQ,
+                                                        const uint8_t *__restrict__ improved, uint64_t seed,
+                                                        const ga_dev *__restrict__ st, ColumnsOut coQ,
+                                                        int rows_in_smem)
 {
     pm_grid_dependency_wait();
-    extern __shared__ uint32_t mrows[];  // [8][W] the mutants, when rows_in_smem (transposed from here)
+    extern __shared__ uint32_t mrows[];  // [32][W] the mutants, when rows_in_smem (transposed from here)
     __shared__ uint32_t on_s;
     int k = 0;
     ga_prob gp = one, gq = oneq;
-    const int64_t gid = blockIdx.x >> 2;
     if (K > 1) {
-        k = find_k(K, gid, [&](int i) { return gqs[i].grp_base; });
+        k = find_k(K, blockIdx.x, [&](int i) { return gqs[i].grp_base; });
         gp = gps[k];
         gq = gqs[k];
     }
     const int lane = threadIdx.x & 31;
     const int j = threadIdx.x >> 5;
-    const int64_t u0 = (gid - gq.grp_base) * 32 + 8 * (blockIdx.x & 3);
+    const int64_t u0 = ((int64_t)blockIdx.x - gq.grp_base) * 32;
     const int64_t u = u0 + j;
     const int32_t W = gp.W;
     if (st[k].stop) {
         if (threadIdx.x == 0)
-            set_active8(activeQ, gq, u0, 0u);
+            activeQ[(gq.ind_base + u0) >> 5] = 0u;
         return;
     }
     if (threadIdx.x == 0)
@@ -1085,11 +1046,11 @@ __global__ void __launch_bounds__(256) k_ga_mutate_all(const ga_prob *__restrict
     }
     __syncthreads();
     if (threadIdx.x == 0)
-        set_active8(activeQ, gq, u0, on_s);
+        activeQ[(gq.ind_base + u0) >> 5] = on_s;
     if (rows_in_smem)
-        write_columns8(mrows, W, u0, gq, coQ, lane, j, 8);
+        write_columns(mrows, W, u0, gq, coQ, lane, j, 32);
     else
-        write_columns8(XQ + gq.word_base + u0 * W, W, u0, gq, coQ, lane, j, 8);
+        write_columns(XQ + gq.word_base + u0 * W, W, u0, gq, coQ, lane, j, 32);
 }
 
 // Keep each individual's first improving try (warp per individual, 8 per
@@ -2209,10 +2170,10 @@ static pm_status enqueue_generation(pm_ga *ga, cudaStream_t s, cudaGraphConditio
     int32_t pmax = 1;
     for (const ga_prob &g : ga->gps)
         pmax = std::max(pmax, g.p);
-    const size_t warp_init_smem = (size_t)8 * ((size_t)ga->Wmax + (size_t)pmax) * 4;
-    // crossover children and mutants are built in shared memory (and transposed from there) when a CTA's 8 rows
-    // fit in the default 48 KB; only the column path has columns to write
-    const size_t rows_smem8 = (!ga->single_row && (size_t)8 * ga->Wmax * 4 <= 48 * 1024) ? (size_t)8 * ga->Wmax * 4 : 0;
+    const size_t warp_init_smem = (size_t)32 * ((size_t)ga->Wmax + (size_t)pmax) * 4;
+    // crossover children and mutants are built in shared memory (and transposed from there) when 32 rows fit
+    // in the default 48 KB; only the column path has columns to write
+    const size_t rows_smem = (!ga->single_row && (size_t)32 * ga->Wmax * 4 <= 48 * 1024) ? (size_t)32 * ga->Wmax * 4 : 0;
 
     if (ga->comb) {
         const uint32_t *T = static_cast<const uint32_t *>(ga->comb_tab.ptr);
@@ -2237,7 +2198,7 @@ static pm_status enqueue_generation(pm_ga *ga, cudaStream_t s, cudaGraphConditio
             break;
         }
     } else if (warp_init_smem <= 200 * 1024) {
-        PM_CUDA(pm_launch(k_ga_init_warp, groups * 4, 256, warp_init_smem, s, gps, K, one, X, improved, active,
+        PM_CUDA(pm_launch(k_ga_init_warp, groups, 1024, warp_init_smem, s, gps, K, one, X, improved, active,
                           static_cast<const uint32_t *>(ga->deme_best.ptr), ga->seed, st, co));
     } else {
         PM_CUDA(pm_launch(k_ga_init, groups, 32, rows_in_smem ? init_smem : 0, s, gps, K, one, X, improved, active,
@@ -2255,8 +2216,8 @@ static pm_status enqueue_generation(pm_ga *ga, cudaStream_t s, cudaGraphConditio
     acc.columns_ready = true;
     if (ga->gps[0].p / 2 > 0) {  // p = 1: no crossover (a batch has p >= 2 everywhere or p = 1 everywhere)
         for (int r = 0; r < ga->R; ++r) {
-            PM_CUDA(pm_launch(k_ga_crossover, groups * 4, 256, rows_smem8, s, gps, K, one, X, Xc, active,
-                              (uint32_t)r, ga->seed, st, co, rows_smem8 ? 1 : 0));
+            PM_CUDA(pm_launch(k_ga_crossover, groups, 1024, rows_smem, s, gps, K, one, X, Xc, active, (uint32_t)r,
+                              ga->seed, st, co, rows_smem ? 1 : 0));
             acc.improved = nullptr;
             PM_TRY(ga_eval(ga, Xc, nullptr, acc, s));
         }
@@ -2286,8 +2247,8 @@ static pm_status enqueue_generation(pm_ga *ga, cudaStream_t s, cudaGraphConditio
         coQ.colT = static_cast<uint32_t *>(ga->colQ.ptr);
         coQ.G = ga->spec_plan.groups;
         const ga_prob *gqs = static_cast<const ga_prob *>(ga->gqprobs.ptr);
-        PM_CUDA(pm_launch(k_ga_mutate_all, (unsigned)ga->groupsQ_total * 4, 256, rows_smem8, s, gps, gqs, K, one,
-                          ga->gq, (int32_t)ga->Q, X, XQ, activeQ, improved, ga->seed, st, coQ, rows_smem8 ? 1 : 0));
+        PM_CUDA(pm_launch(k_ga_mutate_all, (unsigned)ga->groupsQ_total, 1024, rows_smem, s, gps, gqs, K, one,
+                          ga->gq, (int32_t)ga->Q, X, XQ, activeQ, improved, ga->seed, st, coQ, rows_smem ? 1 : 0));
         pm_scan_launch L;
         pm_scan_launch_from(ga->spec_plan, static_cast<const pm_prob *>(ga->probsQ.ptr), L);
         L.masks = XQ;
