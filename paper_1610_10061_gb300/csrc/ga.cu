@@ -27,12 +27,15 @@
 //   k_ga_generation_end  lowest (cost, index) per deme (Section 3.2.2 step
 //                    7); the last deme of an instance updates its global best
 //                    (strict improvement), saturation counter, trace and
-//                    counters; the last instance sets the loop condition.
+//                    counters; the last instance sets the loop condition
+//                    (k_ga_generation_end_one: the same for one instance in
+//                    one CTA).
 // The operators also write the facility-major copy of their output that the
-// scan reads, so no evaluation needs a separate transpose.  The loop is one
-// CUDA graph: a gate kernel and a conditional while-node whose body is one
-// generation.  An instance that reached its saturation limit stops: its
-// kernels do nothing while the others go on.
+// scan reads, so no evaluation needs a separate transpose.  A call of several
+// generations is one CUDA graph: a gate kernel and a conditional while-node
+// whose body is one generation; a call of one generation launches a plain
+// graph of the body.  An instance that reached its saturation limit stops:
+// its kernels do nothing while the others go on.
 //
 // Random numbers: Philox4x32-10 (Salmon et al., SC'11), stateless, keyed by
 // (seed) with counter (generation, unit, op * 2^16 + slot / 4, stream id);
@@ -368,11 +371,11 @@ __device__ __forceinline__ void fresh_individual(const ga_prob &gp, int64_t t, u
     __syncwarp();
 }
 
-// The same fresh population as k_ga_init with one warp per individual: the
-// lanes compute the p Philox draws of Floyd's sampling in parallel (lane l
-// the counter blocks l, l + 32, ...), then lane 0 runs the p dependent
-// insertions on the warp's bitset in shared memory.  CTA = 32 warps = 32
-// individuals; needs 32 * W words of shared memory.
+// The same fresh population as k_ga_init with one warp per individual
+// (fresh_individual: the lanes compute the p Philox draws of Floyd's sampling
+// in parallel and resolve its insertions 32 at a time on the warp's bitset in
+// shared memory).  CTA = 32 warps = 32 individuals; needs 32 * (W + p) words
+// of shared memory.
 __global__ void __launch_bounds__(1024) k_ga_init_warp(const ga_prob *__restrict__ gps, int K, ga_prob one,
                                                        uint32_t *__restrict__ X, uint8_t *__restrict__ improved,
                                                        uint32_t *__restrict__ active,
