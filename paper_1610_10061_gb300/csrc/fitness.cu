@@ -630,8 +630,11 @@ pm_eval_plan pm_plan_eval(const pm_instance *inst, int64_t pop)
     }
     const size_t budget = inst->smem_optin > 4096 ? inst->smem_optin - 4096 : 0;
     int G = kMaxG;
-    // fewer groups for small populations (keep >= 8 tiles) or when the tile does not fit
-    while (G > 1 && (pop <= (int64_t)32 * (G / 2) * 8 || column_smem_bytes(inst->W, G) > budget))
+    // fewer groups for small populations or when the tile does not fit: keep >= 8 tiles, or >= 16 where a
+    // client's walk is short (expected first open rank (m+1)/(p+1) below 32: one or two steps, so the
+    // launch's fixed costs weigh more than the per-step savings of wide tiles)
+    const int64_t min_tiles = (inst->m + 1) < 32 * (inst->p + 1) ? 16 : 8;
+    while (G > 1 && (pop <= (int64_t)32 * (G / 2) * min_tiles || column_smem_bytes(inst->W, G) > budget))
         G /= 2;
     // 32 warps when only one CTA fits per SM, else 16
     const int warps = 2 * column_smem_bytes(inst->W, G) + 8192 > inst->smem_optin ? 32 : 16;
