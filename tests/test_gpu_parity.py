@@ -311,6 +311,20 @@ def test_ga_save_load_resume(pm, migration):
     assert a.result()[:3] == c.result()[:3]
 
 
+@pytest.mark.parametrize("pop,deme", [(2048, 16), (2048, 512), (3072, 1024)])
+def test_generation_end_over_several_tiles(pm, pop, deme):
+    """The one-CTA generation end walks the population 1024 individuals at a time: demes narrower than a warp
+    (reduced inside the warp butterfly), demes of several warps and of a whole tile, over two and three tiles."""
+    _ga_compare(pm, graph_instance(150, 400, seed=3), 8, pop, 3, check_every=1, deme=deme, seed=9)
+
+
+@pytest.mark.parametrize("m,p", [(40, 39), (64, 33), (96, 70), (70, 64)])
+def test_floyd_batches_with_many_collisions(pm, m, p):
+    """Floyd's insertions resolved 32 at a time where draws collide often (p close to m: a draw hits the set of
+    the earlier batches or an earlier lane's pick), against the oracle's sequential insertions."""
+    _ga_compare(pm, euclid_instance(m, seed=m + p), p, 64, 3, check_every=1, deme=32, seed=m)
+
+
 def test_ga_stream_launch_mode_matches_graph_mode(pm, monkeypatch):
     """PM_GA_GRAPH=0 (direct stream launches, for profilers) gives the graph mode's results bit for bit."""
     d = graph_instance(100, 200, seed=0)
