@@ -223,6 +223,13 @@ __device__ __forceinline__ void write_columns(const uint32_t *rows, int64_t rs, 
     }
 }
 
+// The first 64 ranks of every row of one instance's tables (n = 0: none).
+struct TablePrefix {
+    const uint16_t *pi;
+    const int32_t *delta;
+    int64_t n, stride;
+};
+
 // ------------------------------- kernels -----------------------------------
 
 __global__ void k_ga_begin(ga_glob *glob, ga_dev *st, int K, long long gens, long long *trace, unsigned *bar)
@@ -380,8 +387,17 @@ __global__ void __launch_bounds__(1024) k_ga_init_warp(const ga_prob *__restrict
                                                        uint32_t *__restrict__ X, uint8_t *__restrict__ improved,
                                                        uint32_t *__restrict__ active,
                                                        const uint32_t *__restrict__ deme_best, uint64_t seed,
-                                                       const ga_dev *__restrict__ st, ColumnsOut co)
+                                                       const ga_dev *__restrict__ st, ColumnsOut co,
+                                                       TablePrefix tp)
 {
+    // the tables are constant: their rows' first ranks go to L2 while the previous kernel finishes, for the
+    // generation's first scan (the only one that may find them evicted)
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < tp.n; i += (int64_t)gridDim.x * blockDim.x) {
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(tp.pi + i * tp.stride));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(tp.delta + i * tp.stride));
+        if (tp.stride > 32)  // the row's second 128-byte line of Delta' (rows are padded to a multiple of 32)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(tp.delta + i * tp.stride + 32));
+    }
     pm_grid_dependency_wait();
     extern __shared__ uint32_t wrows[];  // [32][W] bitsets, then [32][p] draws
     __shared__ uint32_t on_s;
@@ -894,15 +910,18 @@ __device__ __forceinline__ uint32_t range_mask(int64_t lo, int64_t hi)  // bits 
     return upto & ~below;
 }
 
-// Try q's mutant F of the W-word row C (m bits) of individual t, built by a
-// warp (lanes over words): circular or block shift with the draws of
-// operation OP_MUT + q -- kind and direction from draws 0 and 1, the
-// circular amount or the block's two ends from draws 2 and 3, the block's
-// amount from draw 4.  F[a+i] = C[a + (i+kl) mod len].
-template <bool kCG = false>
-__device__ __forceinline__ void mutant_row(const uint32_t *__restrict__ C, uint32_t *__restrict__ F, int32_t W,
-                                           int32_t m, uint64_t seed, uint32_t gen, uint32_t t, uint32_t q,
-                                           uint32_t sid, int lane)
+// Try q's shift of individual t: circular or block shift with the draws of
+// operation OP_MUT + q -- kind and direction from draws 0 and 1, the circular
+// amount or the block's two ends from draws 2 and 3, the block's amount from
+// draw 4.  The mutant rotates bits [a, a+len) left by kl: F[a+i] =
+// C[a + (i+kl) mod len].  Depends on nothing a kernel of the generation
+// writes, so callers may take it before waiting for the previous kernel.
+struct MutantShift {
+    int64_t a, len, kl;
+};
+
+__device__ __forceinline__ MutantShift mutant_shift(int32_t m, uint64_t seed, uint32_t gen, uint32_t t, uint32_t q,
+                                                    uint32_t sid)
 {
     const uint4 v0 = draw_block(seed, gen, (uint32_t)t, OP_MUT + q, 0, sid);
     const uint32_t kind = uniform_below(v0.x, 2u);
@@ -923,8 +942,20 @@ __device__ __forceinline__ void mutant_row(const uint32_t *__restrict__ C, uint3
         len = hi - lo + 1;
         kk = 1 + uniform_below(v1.x, hi - lo);
     }
-    const int64_t kl = right ? (len - kk) : kk;  // rotate left by kl, 1 <= kl < len
-    const int64_t pwrap = a + len - kl;          // positions >= pwrap wrap to the start of the block
+    MutantShift ms;
+    ms.a = a;
+    ms.len = len;
+    ms.kl = right ? (len - kk) : kk;  // rotate left by kl, 1 <= kl < len
+    return ms;
+}
+
+// The mutant F of the W-word row C for a shift, built by a warp (lanes over words).
+template <bool kCG = false>
+__device__ __forceinline__ void mutant_row_shift(const uint32_t *__restrict__ C, uint32_t *__restrict__ F, int32_t W,
+                                                 const MutantShift &ms, int lane)
+{
+    const int64_t a = ms.a, len = ms.len, kl = ms.kl;
+    const int64_t pwrap = a + len - kl;  // positions >= pwrap wrap to the start of the block
     for (int w = lane; w < W; w += 32) {
         const int64_t pos0 = (int64_t)w * 32;
         const int64_t in_lo = a > pos0 ? a : pos0;
@@ -943,6 +974,15 @@ __device__ __forceinline__ void mutant_row(const uint32_t *__restrict__ C, uint3
             out |= bits_from<kCG>(C, W, pos0 + kl - len) & range_mask(s2 - pos0, in_hi - pos0);
         F[w] = out;
     }
+}
+
+// Try q's mutant F of the W-word row C (m bits) of individual t, built by a warp.
+template <bool kCG = false>
+__device__ __forceinline__ void mutant_row(const uint32_t *__restrict__ C, uint32_t *__restrict__ F, int32_t W,
+                                           int32_t m, uint64_t seed, uint32_t gen, uint32_t t, uint32_t q,
+                                           uint32_t sid, int lane)
+{
+    mutant_row_shift<kCG>(C, F, W, mutant_shift(m, seed, gen, t, q, sid), lane);
 }
 
 // One mutation try (Section 4.4).  CTA = 32 warps = 32 individuals; warp j
@@ -1006,7 +1046,6 @@ __global__ void __launch_bounds__(1024, 2) k_ga_mutate_all(const ga_prob *__rest
                                                         const ga_dev *__restrict__ st, ColumnsOut coQ,
                                                         int rows_in_smem)
 {
-    pm_grid_dependency_wait();
     extern __shared__ uint32_t mrows[];  // [32][W] the mutants, when rows_in_smem (transposed from here)
     __shared__ uint32_t on_s;
     int k = 0;
@@ -1021,7 +1060,15 @@ __global__ void __launch_bounds__(1024, 2) k_ga_mutate_all(const ga_prob *__rest
     const int64_t u0 = ((int64_t)blockIdx.x - gq.grp_base) * 32;
     const int64_t u = u0 + j;
     const int32_t W = gp.W;
-    if (st[k].stop) {
+    // the shift's draws depend on the generation counter and the stop flag, written by an earlier generation's
+    // end: taken before waiting for the previous kernel (the evaluation of the last crossover round)
+    const bool stopped = st[k].stop != 0;
+    const int64_t q_u = u / gp.pop, t_u = u - q_u * gp.pop;
+    MutantShift ms{0, 1, 0};
+    if (!stopped && u < gq.pop)
+        ms = mutant_shift(gp.m, seed, (uint32_t)st[k].gen, (uint32_t)t_u, (uint32_t)q_u, gp.sid);
+    pm_grid_dependency_wait();
+    if (stopped) {
         if (threadIdx.x == 0)
             activeQ[(gq.ind_base + u0) >> 5] = 0u;
         return;
@@ -1030,13 +1077,12 @@ __global__ void __launch_bounds__(1024, 2) k_ga_mutate_all(const ga_prob *__rest
         on_s = 0u;
     __syncthreads();
     if (u < gq.pop) {
-        const int64_t q = u / gp.pop, t = u - q * gp.pop;
+        const int64_t t = t_u;
         if (improved[gp.ind_base + t] == 0) {
             if (lane == 0)
                 atomicOr(&on_s, 1u << j);
             uint32_t *F = rows_in_smem ? mrows + (int64_t)j * W : XQ + gq.word_base + u * W;
-            mutant_row(X + gp.word_base + t * W, F, W, gp.m, seed, (uint32_t)st[k].gen, (uint32_t)t, (uint32_t)q,
-                       gp.sid, lane);
+            mutant_row_shift(X + gp.word_base + t * W, F, W, ms, lane);
             if (rows_in_smem) {
                 __syncwarp();
                 for (int w = lane; w < W; w += 32)
@@ -2201,8 +2247,15 @@ static pm_status enqueue_generation(pm_ga *ga, cudaStream_t s, cudaGraphConditio
             break;
         }
     } else if (warp_init_smem <= 200 * 1024) {
+        TablePrefix tp{nullptr, nullptr, 0, 0};
+        if (K == 1) {
+            tp.pi = ga->insts[0]->pi;
+            tp.delta = ga->insts[0]->delta;
+            tp.n = ga->insts[0]->n;
+            tp.stride = ga->insts[0]->stride;
+        }
         PM_CUDA(pm_launch(k_ga_init_warp, groups, 1024, warp_init_smem, s, gps, K, one, X, improved, active,
-                          static_cast<const uint32_t *>(ga->deme_best.ptr), ga->seed, st, co));
+                          static_cast<const uint32_t *>(ga->deme_best.ptr), ga->seed, st, co, tp));
     } else {
         PM_CUDA(pm_launch(k_ga_init, groups, 32, rows_in_smem ? init_smem : 0, s, gps, K, one, X, improved, active,
                           static_cast<const uint32_t *>(ga->deme_best.ptr), ga->seed, st, co, rows_in_smem));
