@@ -1,5 +1,6 @@
 // C ABI: instances, population evaluation, status strings (include/pm.h).
 
+#include <algorithm>
 #include <atomic>
 #include <cstdio>
 #include <cstdlib>
@@ -79,10 +80,32 @@ pm_status pm_dbuf::reserve(size_t want, bool *fresh)
 
 void pm_dbuf::release()
 {
-    if (ptr)
+    if (ptr && !borrowed)
         pm_clear_error(cudaFree(ptr));
     ptr = nullptr;
     bytes = 0;
+    borrowed = false;
+}
+
+pm_status pm_carve(pm_dbuf &arena, const pm_part *parts, int count)
+{
+    size_t total = 0;
+    for (int k = 0; k < count; ++k) {
+        parts[k].buf->release();
+        total += (std::max<size_t>(parts[k].bytes, 256) + 255) & ~size_t(255);
+    }
+    arena.release();
+    PM_TRY(arena.reserve(total));
+    char *base = static_cast<char *>(arena.ptr);
+    size_t off = 0;
+    for (int k = 0; k < count; ++k) {
+        const size_t sz = std::max<size_t>(parts[k].bytes, 256);
+        parts[k].buf->ptr = base + off;
+        parts[k].buf->bytes = sz;
+        parts[k].buf->borrowed = true;
+        off += (sz + 255) & ~size_t(255);
+    }
+    return PM_OK;
 }
 
 bool pm_is_device_ptr(const void *p)
@@ -126,10 +149,6 @@ static void destroy_instance(pm_instance *inst)
     if (!inst)
         return;
     pm_clear_error(cudaSetDevice(inst->device));
-    if (inst->pi)
-        pm_clear_error(cudaFree(inst->pi));
-    if (inst->delta)
-        pm_clear_error(cudaFree(inst->delta));
     inst->stage_masks.release();
     inst->stage_costs.release();
     inst->partials.release();
@@ -137,6 +156,7 @@ static void destroy_instance(pm_instance *inst)
     inst->columns.release();
     inst->flag.release();
     inst->err.release();
+    inst->tab_arena.release();  // the tables, err and flag
     delete inst;
 }
 
@@ -157,9 +177,12 @@ static pm_status create_impl(const int32_t *d, int64_t n, int64_t m, int64_t p, 
     PM_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
     inst->smem_optin = (size_t)v;
     const size_t tab = (size_t)n * (size_t)inst->stride;
-    PM_CUDA(pm_device_malloc(reinterpret_cast<void **>(&inst->pi), tab * sizeof(uint16_t)));
-    PM_CUDA(pm_device_malloc(reinterpret_cast<void **>(&inst->delta), tab * sizeof(int32_t)));
-    PM_TRY(inst->err.reserve(256));
+    pm_dbuf dbuf, pbuf;
+    const pm_part parts[] = {{&inst->err, 256}, {&inst->flag, 256}, {&dbuf, tab * sizeof(int32_t)},
+                             {&pbuf, tab * sizeof(uint16_t)}};
+    PM_TRY(pm_carve(inst->tab_arena, parts, 4));
+    inst->delta = static_cast<int32_t *>(dbuf.ptr);
+    inst->pi = static_cast<uint16_t *>(pbuf.ptr);
     PM_CUDA(cudaMemsetAsync(inst->err.ptr, 0, 256, stream));
     PM_TRY(pm_fitness_init(inst));
     const int32_t *d_dev = d;

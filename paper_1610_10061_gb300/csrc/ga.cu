@@ -2111,6 +2111,7 @@ struct pm_ga {
     int64_t groups_total = 0, demes_total = 0, dwords_total = 0, best_total = 0, Wmax = 0;
     pm_dbuf X, Xc, cost, active, improved, deme_best, deme_cost, best, trace, accum, tickets, columns, st, glob, err,
         probs, gprobs;
+    pm_dbuf arena, arenaQ;  // the memory of the buffers above (arena) and of the candidates' buffers (arenaQ)
     // the persistent generation kernel (one cooperative launch per pm_ga_step) when the GA qualifies
     bool fused = false;
     int fused_G = 4;
@@ -2126,6 +2127,7 @@ struct pm_ga {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;   // gate + conditional while-node over the generation
     cudaGraphExec_t exec1 = nullptr;  // one generation, no loop (calls of one generation)
+    int graphs = 3;                   // which of the two to build: bit 0 exec, bit 1 exec1 (pm_ga_run: one)
 };
 
 static void ga_free(pm_ga *ga)
@@ -2146,7 +2148,7 @@ static void ga_free(pm_ga *ga)
                        &ga->st,        &ga->glob, &ga->err,   &ga->probs,  &ga->gprobs,
                        &ga->s_gain,    &ga->s_cap, &ga->s_loss, &ga->s_assign, &ga->moves, &ga->xfeat, &ga->scores,
                        &ga->comb_tab,  &ga->XQ,    &ga->costQ, &ga->activeQ, &ga->accumQ, &ga->ticketsQ, &ga->colQ,
-                       &ga->bar,       &ga->gqprobs, &ga->probsQ};
+                       &ga->bar,       &ga->gqprobs, &ga->probsQ, &ga->arena, &ga->arenaQ};
     for (pm_dbuf *b : bufs)
         b->release();
     delete ga;
@@ -2340,8 +2342,26 @@ static pm_status enqueue_generation(pm_ga *ga, cudaStream_t s, cudaGraphConditio
     return PM_OK;
 }
 
+// The generation as a plain graph for calls of one generation: entering and leaving a conditional body costs
+// about 6 us each way, a tenth of a graph900 generation.
+static pm_status build_graph_one(pm_ga *ga)
+{
+    PM_CUDA(cudaStreamBeginCapture(ga->cap, cudaStreamCaptureModeThreadLocal));
+    pm_status st_gen = enqueue_generation(ga, ga->cap, 0, 0);
+    cudaGraph_t one = nullptr;
+    cudaError_t e = cudaStreamEndCapture(ga->cap, &one);
+    PM_TRY(st_gen);
+    PM_CUDA(e);
+    e = cudaGraphInstantiate(&ga->exec1, one, 0);
+    pm_clear_error(cudaGraphDestroy(one));
+    PM_CUDA(e);
+    return PM_OK;
+}
+
 static pm_status build_graph(pm_ga *ga)
 {
+    if (!(ga->graphs & 1))
+        return build_graph_one(ga);
     PM_CUDA(cudaGraphCreate(&ga->graph, 0));
     cudaGraphConditionalHandle h;
     PM_CUDA(cudaGraphConditionalHandleCreate(&h, ga->graph, 0, cudaGraphCondAssignDefault));
@@ -2370,18 +2390,7 @@ static pm_status build_graph(pm_ga *ga)
     PM_TRY(st_gen);
     PM_CUDA(e);
     PM_CUDA(cudaGraphInstantiate(&ga->exec, ga->graph, 0));
-    // the same generation as a plain graph for calls of one generation: entering and leaving a conditional
-    // body costs about 6 us each way, a tenth of a graph900 generation
-    PM_CUDA(cudaStreamBeginCapture(ga->cap, cudaStreamCaptureModeThreadLocal));
-    st_gen = enqueue_generation(ga, ga->cap, h, 0);
-    cudaGraph_t one = nullptr;
-    e = cudaStreamEndCapture(ga->cap, &one);
-    PM_TRY(st_gen);
-    PM_CUDA(e);
-    e = cudaGraphInstantiate(&ga->exec1, one, 0);
-    pm_clear_error(cudaGraphDestroy(one));
-    PM_CUDA(e);
-    return PM_OK;
+    return (ga->graphs & 2) ? build_graph_one(ga) : PM_OK;
 }
 
 // Layout of the GA arrays over the instances, the scan plan and the buffers.
@@ -2423,29 +2432,36 @@ static pm_status ga_alloc(pm_ga *ga, cudaStream_t s)
     ga->best_total = bestw;
     ga->Wmax = Wmax;
     const size_t words = (size_t)ga->plan.words_total, inds = (size_t)ga->plan.ind_total;
-    PM_TRY(ga->X.reserve(words * 4));
-    PM_TRY(ga->Xc.reserve(words * 4));
-    PM_TRY(ga->cost.reserve(inds * 8));
-    PM_TRY(ga->active.reserve(inds / 8 + 4));
-    PM_TRY(ga->improved.reserve(inds));
-    PM_TRY(ga->deme_best.reserve((size_t)dwords * 4));
-    PM_TRY(ga->deme_cost.reserve((size_t)deme * 8));
-    PM_TRY(ga->best.reserve((size_t)bestw * 4));
-    PM_TRY(ga->trace.reserve(8 * 1024));
     const size_t acc_bytes = ga->single_row ? pm_plan_partial_bytes(ga->single, ga->P) : inds * 8;
     const size_t tick_bytes = (size_t)pm_round_up(std::max<int64_t>(ga->plan.tiles_total, 1) * 4, 256);
-    PM_TRY(ga->accum.reserve(acc_bytes));
-    PM_TRY(ga->tickets.reserve(tick_bytes));
-    PM_TRY(ga->columns.reserve(std::max<size_t>((size_t)ga->plan.cols_total * 4, 256)));
-    PM_TRY(ga->st.reserve(sizeof(ga_dev) * K));
-    PM_TRY(ga->glob.reserve(sizeof(ga_glob)));
-    PM_TRY(ga->err.reserve(256));
-    PM_TRY(ga->probs.reserve(sizeof(pm_prob) * K));
-    PM_TRY(ga->gprobs.reserve(sizeof(ga_prob) * K));
-    pm_dbuf *zero[] = {&ga->X,         &ga->Xc,        &ga->cost, &ga->active,  &ga->improved, &ga->deme_best,
-                       &ga->deme_cost, &ga->best,      &ga->accum, &ga->tickets, &ga->err};
-    for (pm_dbuf *b : zero)
-        PM_CUDA(cudaMemsetAsync(b->ptr, 0, b->bytes, s));  // accumulators and tickets start at zero
+    // every buffer of the GA's state in one allocation, zeroed at once (accumulators and tickets must start at
+    // zero; the rest is written before it is read); the tables the host fills (st, glob, probs, gprobs) come
+    // last, in one copy
+    const pm_part parts[] = {{&ga->X, words * 4},
+                             {&ga->Xc, words * 4},
+                             {&ga->cost, inds * 8},
+                             {&ga->active, inds / 8 + 4},
+                             {&ga->improved, inds},
+                             {&ga->deme_best, (size_t)dwords * 4},
+                             {&ga->deme_cost, (size_t)deme * 8},
+                             {&ga->best, (size_t)bestw * 4},
+                             {&ga->trace, 8 * 1024},
+                             {&ga->accum, acc_bytes},
+                             {&ga->tickets, tick_bytes},
+                             {&ga->columns, (size_t)ga->plan.cols_total * 4},
+                             {&ga->err, 256},
+                             {&ga->st, sizeof(ga_dev) * K},
+                             {&ga->glob, sizeof(ga_glob)},
+                             {&ga->probs, sizeof(pm_prob) * K},
+                             {&ga->gprobs, sizeof(ga_prob) * K}};
+    PM_TRY(pm_carve(ga->arena, parts, (int)(sizeof(parts) / sizeof(parts[0]))));
+    char *base = static_cast<char *>(ga->arena.ptr);
+    const size_t host_off = static_cast<char *>(ga->st.ptr) - base;
+    PM_CUDA(cudaMemsetAsync(base, 0, host_off, s));
+    std::vector<char> host(ga->arena.bytes - host_off, 0);
+    auto put = [&](const pm_dbuf &b, const void *src, size_t n) {
+        std::memcpy(host.data() + (static_cast<char *>(b.ptr) - base - host_off), src, n);
+    };
     std::vector<ga_dev> h(K);
     for (int k = 0; k < K; ++k) {
         h[k] = ga_dev{};
@@ -2454,10 +2470,11 @@ static pm_status ga_alloc(pm_ga *ga, cudaStream_t s)
     }
     ga_glob g = {};
     g.alive = K;
-    PM_CUDA(cudaMemcpyAsync(ga->st.ptr, h.data(), sizeof(ga_dev) * K, cudaMemcpyHostToDevice, s));
-    PM_CUDA(cudaMemcpyAsync(ga->glob.ptr, &g, sizeof(g), cudaMemcpyHostToDevice, s));
-    PM_CUDA(cudaMemcpyAsync(ga->probs.ptr, ga->plan.probs.data(), sizeof(pm_prob) * K, cudaMemcpyHostToDevice, s));
-    PM_CUDA(cudaMemcpyAsync(ga->gprobs.ptr, ga->gps.data(), sizeof(ga_prob) * K, cudaMemcpyHostToDevice, s));
+    put(ga->st, h.data(), sizeof(ga_dev) * K);
+    put(ga->glob, &g, sizeof(g));
+    put(ga->probs, ga->plan.probs.data(), sizeof(pm_prob) * K);
+    put(ga->gprobs, ga->gps.data(), sizeof(ga_prob) * K);
+    PM_CUDA(cudaMemcpyAsync(ga->st.ptr, host.data(), host.size(), cudaMemcpyHostToDevice, s));
     PM_CUDA(cudaStreamSynchronize(s));
     PM_CUDA(cudaStreamCreateWithFlags(&ga->cap, cudaStreamNonBlocking));
     return PM_OK;
@@ -2527,19 +2544,25 @@ static pm_status spec_alloc(pm_ga *ga, cudaStream_t s)
     ga->gq = ga->gqs[0];
     ga->groupsQ_total = grp;
     const pm_multi_plan &sp = ga->spec_plan;
-    PM_TRY(ga->XQ.reserve((size_t)sp.words_total * 4));
-    PM_TRY(ga->costQ.reserve((size_t)sp.ind_total * 8));
-    PM_TRY(ga->activeQ.reserve((size_t)pm_round_up(pm_ceil_div(sp.ind_total, 32) * 4, 256)));
-    PM_TRY(ga->accumQ.reserve((size_t)sp.ind_total * 8));
-    PM_TRY(ga->ticketsQ.reserve((size_t)pm_round_up(std::max<int64_t>(sp.tiles_total, 1) * 4, 256)));
-    PM_TRY(ga->colQ.reserve(std::max<size_t>((size_t)sp.cols_total * 4, 256)));
-    PM_TRY(ga->gqprobs.reserve(sizeof(ga_prob) * K));
-    PM_TRY(ga->probsQ.reserve(sizeof(pm_prob) * K));
-    pm_dbuf *zero[] = {&ga->XQ, &ga->costQ, &ga->activeQ, &ga->accumQ, &ga->ticketsQ};
-    for (pm_dbuf *b : zero)
-        PM_CUDA(cudaMemsetAsync(b->ptr, 0, b->bytes, s));  // accumulators and tickets start at zero
-    PM_CUDA(cudaMemcpyAsync(ga->gqprobs.ptr, ga->gqs.data(), sizeof(ga_prob) * K, cudaMemcpyHostToDevice, s));
-    PM_CUDA(cudaMemcpyAsync(ga->probsQ.ptr, sp.probs.data(), sizeof(pm_prob) * K, cudaMemcpyHostToDevice, s));
+    // one allocation: the candidates' buffers (zeroed: accumulators and tickets start at zero), then the two
+    // tables the host fills, in one copy
+    const pm_part parts[] = {{&ga->XQ, (size_t)sp.words_total * 4},
+                             {&ga->costQ, (size_t)sp.ind_total * 8},
+                             {&ga->activeQ, (size_t)pm_round_up(pm_ceil_div(sp.ind_total, 32) * 4, 256)},
+                             {&ga->accumQ, (size_t)sp.ind_total * 8},
+                             {&ga->ticketsQ, (size_t)pm_round_up(std::max<int64_t>(sp.tiles_total, 1) * 4, 256)},
+                             {&ga->colQ, (size_t)sp.cols_total * 4},
+                             {&ga->gqprobs, sizeof(ga_prob) * K},
+                             {&ga->probsQ, sizeof(pm_prob) * K}};
+    PM_TRY(pm_carve(ga->arenaQ, parts, (int)(sizeof(parts) / sizeof(parts[0]))));
+    char *base = static_cast<char *>(ga->arenaQ.ptr);
+    const size_t host_off = static_cast<char *>(ga->gqprobs.ptr) - base;
+    PM_CUDA(cudaMemsetAsync(base, 0, host_off, s));
+    std::vector<char> host(ga->arenaQ.bytes - host_off, 0);
+    std::memcpy(host.data(), ga->gqs.data(), sizeof(ga_prob) * K);
+    std::memcpy(host.data() + (static_cast<char *>(ga->probsQ.ptr) - base - host_off), sp.probs.data(),
+                sizeof(pm_prob) * K);
+    PM_CUDA(cudaMemcpyAsync(ga->gqprobs.ptr, host.data(), host.size(), cudaMemcpyHostToDevice, s));
     PM_CUDA(cudaStreamSynchronize(s));
     return PM_OK;
 }
@@ -2696,7 +2719,7 @@ static pm_status ga_create_common(pm_ga *ga, cudaStream_t s)
     if (st == PM_OK && ga->spec && spec_alloc(ga, s) != PM_OK) {
         // no room for the Q x pop candidates: run the mutation cycle try by try instead
         pm_dbuf *bufs[] = {&ga->XQ, &ga->costQ, &ga->activeQ, &ga->accumQ, &ga->ticketsQ, &ga->colQ,
-                           &ga->gqprobs, &ga->probsQ};
+                           &ga->gqprobs, &ga->probsQ, &ga->arenaQ};
         for (pm_dbuf *b : bufs)
             b->release();
         cudaGetLastError();
@@ -2749,8 +2772,8 @@ static pm_status comb_prepare(pm_ga *ga, const pm_instance *inst, cudaStream_t s
     return overflow ? PM_ERR_UNSUPPORTED : PM_OK;
 }
 
-extern "C" pm_status pm_ga_create(pm_instance *inst, uint64_t seed, int64_t pop, const pm_ga_params *params,
-                                  void *stream, pm_ga **out)
+static pm_status ga_create_single(pm_instance *inst, uint64_t seed, int64_t pop, const pm_ga_params *params,
+                                  void *stream, int graphs, pm_ga **out)
 {
     if (!out || !inst)
         return PM_ERR_INVALID_ARG;
@@ -2758,6 +2781,7 @@ extern "C" pm_status pm_ga_create(pm_instance *inst, uint64_t seed, int64_t pop,
     pm_ga *ga = new (std::nothrow) pm_ga();
     if (!ga)
         return PM_ERR_OOM;
+    ga->graphs = graphs;
     ga->insts.push_back(inst);
     ga->device = inst->device;
     ga->K = 1;
@@ -2803,6 +2827,12 @@ extern "C" pm_status pm_ga_create(pm_instance *inst, uint64_t seed, int64_t pop,
     }
     *out = ga;
     return PM_OK;
+}
+
+extern "C" pm_status pm_ga_create(pm_instance *inst, uint64_t seed, int64_t pop, const pm_ga_params *params,
+                                  void *stream, pm_ga **out)
+{
+    return ga_create_single(inst, seed, pop, params, stream, 3, out);
 }
 
 extern "C" pm_status pm_batch_ga_create(pm_batch *b, uint64_t seed, int64_t pop, const pm_ga_params *params,
@@ -2897,7 +2927,7 @@ extern "C" pm_status pm_ga_step(pm_ga *ga, int64_t gens, int64_t *trace, void *s
     if (ga->fused) {
         PM_TRY(fused_launch(ga, s));
     } else if (graph_mode()) {
-        PM_CUDA(cudaGraphLaunch(gens == 1 ? ga->exec1 : ga->exec, s));
+        PM_CUDA(cudaGraphLaunch((gens == 1 && ga->exec1) || !ga->exec ? ga->exec1 : ga->exec, s));
     } else {
         // the same kernels, enqueued generation by generation (profilers cannot see
         // kernels inside conditional graphs); saturation needs the host to look
@@ -3132,7 +3162,8 @@ extern "C" pm_status pm_ga_run(pm_instance *inst, uint64_t seed, int64_t pop, in
     if (!inst || gens < 0)
         return PM_ERR_INVALID_ARG;
     pm_ga *ga = nullptr;
-    PM_TRY(pm_ga_create(inst, seed, pop, params, stream, &ga));
+    // one job of `gens` generations: only the graph that runs them is built
+    PM_TRY(ga_create_single(inst, seed, pop, params, stream, gens == 1 ? 2 : 1, &ga));
     pm_status st = pm_ga_step(ga, gens, trace, stream);
     if (st == PM_OK)
         st = pm_ga_result(ga, best_cost, best_mask, gens_run, evals, stream);

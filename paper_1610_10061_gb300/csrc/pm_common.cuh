@@ -46,14 +46,26 @@ inline void pm_clear_error(cudaError_t e)
 }
 inline void pm_clear_stale_error() { (void)cudaGetLastError(); }
 
-// A device buffer owned by the library that grows on demand.
+// A device buffer owned by the library that grows on demand, or a slice of
+// another buffer (pm_carve), which release() only forgets.
 struct pm_dbuf {
     void *ptr = nullptr;
     size_t bytes = 0;
-    // Grow to at least `want` bytes; *fresh (optional) tells whether new memory was allocated.
+    bool borrowed = false;
+    // Grow to at least `want` bytes; *fresh (optional) tells whether new memory was allocated.  A slice that is
+    // too small is forgotten and replaced by memory of its own.
     pm_status reserve(size_t want, bool *fresh = nullptr);
     void release();
 };
+
+// One device allocation (`arena`, replacing what it held) laid out as consecutive 256-byte aligned slices of
+// at least max(size, 256) bytes, handed to the parts as borrowed buffers: one cudaMalloc and, at release, one
+// cudaFree for a group of buffers that live and die together.  The parts' previous memory is released first.
+struct pm_part {
+    pm_dbuf *buf;
+    size_t bytes;
+};
+pm_status pm_carve(pm_dbuf &arena, const pm_part *parts, int count);
 
 // Scratch for one fitness launch configuration (partial sums per client split).
 struct pm_eval_plan {
@@ -136,6 +148,7 @@ struct pm_instance {
     size_t smem_optin = 0;
     // staging and scratch for pm_eval_population
     pm_dbuf stage_masks, stage_costs, partials, tickets, columns, flag, err;
+    pm_dbuf tab_arena;  // one allocation holding delta, pi, err and flag
     std::mutex lock;
     // evaluation plans chosen by the autotuner, by population size
     mutable std::mutex plan_mu;
