@@ -2111,7 +2111,7 @@ struct pm_ga {
     int64_t groups_total = 0, demes_total = 0, dwords_total = 0, best_total = 0, Wmax = 0;
     pm_dbuf X, Xc, cost, active, improved, deme_best, deme_cost, best, trace, accum, tickets, columns, st, glob, err,
         probs, gprobs;
-    pm_dbuf arena, arenaQ;  // the memory of the buffers above (arena) and of the candidates' buffers (arenaQ)
+    pm_dbuf arena;  // the memory of the buffers above and of the candidates' buffers
     // the persistent generation kernel (one cooperative launch per pm_ga_step) when the GA qualifies
     bool fused = false;
     int fused_G = 4;
@@ -2148,7 +2148,7 @@ static void ga_free(pm_ga *ga)
                        &ga->st,        &ga->glob, &ga->err,   &ga->probs,  &ga->gprobs,
                        &ga->s_gain,    &ga->s_cap, &ga->s_loss, &ga->s_assign, &ga->moves, &ga->xfeat, &ga->scores,
                        &ga->comb_tab,  &ga->XQ,    &ga->costQ, &ga->activeQ, &ga->accumQ, &ga->ticketsQ, &ga->colQ,
-                       &ga->bar,       &ga->gqprobs, &ga->probsQ, &ga->arena, &ga->arenaQ};
+                       &ga->bar,       &ga->gqprobs, &ga->probsQ, &ga->arena};
     for (pm_dbuf *b : bufs)
         b->release();
     delete ga;
@@ -2394,7 +2394,7 @@ static pm_status build_graph(pm_ga *ga)
 }
 
 // Layout of the GA arrays over the instances, the scan plan and the buffers.
-static pm_status ga_alloc(pm_ga *ga, cudaStream_t s)
+static void ga_layout(pm_ga *ga)
 {
     const int K = ga->K;
     ga->gps.resize(K);
@@ -2431,32 +2431,76 @@ static pm_status ga_alloc(pm_ga *ga, cudaStream_t s)
     ga->dwords_total = dwords;
     ga->best_total = bestw;
     ga->Wmax = Wmax;
+}
+
+// Layout of the speculative mutation cycle's candidates: Q x pop candidate bitsets per instance, their
+// facility-major copy, active bits, costs and the scan's accumulators, laid out by spec_plan; the candidates'
+// per-instance layout (ga_prob) and scan table (pm_prob) on the device for batched GAs.
+static void spec_layout(pm_ga *ga)
+{
+    const int K = ga->K;
+    const int64_t QP = (int64_t)ga->Q * ga->P;
+    ga->gqs.resize(K);
+    int64_t grp = 0;
+    for (int k = 0; k < K; ++k) {
+        const pm_prob &pr = ga->spec_plan.probs[k];
+        ga_prob &gq = ga->gqs[k];
+        gq = ga->gps[k];
+        gq.pop = QP;
+        gq.ind_base = pr.ind_base;
+        gq.word_base = pr.word_base;
+        gq.col_base = pr.col_base;
+        gq.grp_base = grp;
+        grp += pm_ceil_div(QP, 32);
+    }
+    ga->gq = ga->gqs[0];
+    ga->groupsQ_total = grp;
+}
+
+// The GA's device buffers, and those of the speculative cycle when `with_spec`, in one allocation: first the
+// buffers zeroed at once (accumulators and tickets must start at zero; the rest is written before it is read),
+// then the tables the host fills (st, glob, probs, gprobs and the candidates' gqprobs, probsQ), in one copy.
+static pm_status ga_alloc(pm_ga *ga, cudaStream_t s, bool with_spec)
+{
+    const int K = ga->K;
     const size_t words = (size_t)ga->plan.words_total, inds = (size_t)ga->plan.ind_total;
     const size_t acc_bytes = ga->single_row ? pm_plan_partial_bytes(ga->single, ga->P) : inds * 8;
     const size_t tick_bytes = (size_t)pm_round_up(std::max<int64_t>(ga->plan.tiles_total, 1) * 4, 256);
-    // every buffer of the GA's state in one allocation, zeroed at once (accumulators and tickets must start at
-    // zero; the rest is written before it is read); the tables the host fills (st, glob, probs, gprobs) come
-    // last, in one copy
-    const pm_part parts[] = {{&ga->X, words * 4},
-                             {&ga->Xc, words * 4},
-                             {&ga->cost, inds * 8},
-                             {&ga->active, inds / 8 + 4},
-                             {&ga->improved, inds},
-                             {&ga->deme_best, (size_t)dwords * 4},
-                             {&ga->deme_cost, (size_t)deme * 8},
-                             {&ga->best, (size_t)bestw * 4},
-                             {&ga->trace, 8 * 1024},
-                             {&ga->accum, acc_bytes},
-                             {&ga->tickets, tick_bytes},
-                             {&ga->columns, (size_t)ga->plan.cols_total * 4},
-                             {&ga->err, 256},
-                             {&ga->st, sizeof(ga_dev) * K},
-                             {&ga->glob, sizeof(ga_glob)},
-                             {&ga->probs, sizeof(pm_prob) * K},
-                             {&ga->gprobs, sizeof(ga_prob) * K}};
-    PM_TRY(pm_carve(ga->arena, parts, (int)(sizeof(parts) / sizeof(parts[0]))));
+    const pm_multi_plan &sp = ga->spec_plan;
+    std::vector<pm_part> parts = {{&ga->X, words * 4},
+                                  {&ga->Xc, words * 4},
+                                  {&ga->cost, inds * 8},
+                                  {&ga->active, inds / 8 + 4},
+                                  {&ga->improved, inds},
+                                  {&ga->deme_best, (size_t)ga->dwords_total * 4},
+                                  {&ga->deme_cost, (size_t)ga->demes_total * 8},
+                                  {&ga->best, (size_t)ga->best_total * 4},
+                                  {&ga->trace, 8 * 1024},
+                                  {&ga->accum, acc_bytes},
+                                  {&ga->tickets, tick_bytes},
+                                  {&ga->columns, (size_t)ga->plan.cols_total * 4},
+                                  {&ga->err, 256}};
+    if (with_spec) {
+        const pm_part q[] = {{&ga->XQ, (size_t)sp.words_total * 4},
+                             {&ga->costQ, (size_t)sp.ind_total * 8},
+                             {&ga->activeQ, (size_t)pm_round_up(pm_ceil_div(sp.ind_total, 32) * 4, 256)},
+                             {&ga->accumQ, (size_t)sp.ind_total * 8},
+                             {&ga->ticketsQ, (size_t)pm_round_up(std::max<int64_t>(sp.tiles_total, 1) * 4, 256)},
+                             {&ga->colQ, (size_t)sp.cols_total * 4}};
+        parts.insert(parts.end(), q, q + 6);
+    }
+    const size_t n_zero = parts.size();
+    parts.push_back({&ga->st, sizeof(ga_dev) * K});
+    parts.push_back({&ga->glob, sizeof(ga_glob)});
+    parts.push_back({&ga->probs, sizeof(pm_prob) * K});
+    parts.push_back({&ga->gprobs, sizeof(ga_prob) * K});
+    if (with_spec) {
+        parts.push_back({&ga->gqprobs, sizeof(ga_prob) * K});
+        parts.push_back({&ga->probsQ, sizeof(pm_prob) * K});
+    }
+    PM_TRY(pm_carve(ga->arena, parts.data(), (int)parts.size()));
     char *base = static_cast<char *>(ga->arena.ptr);
-    const size_t host_off = static_cast<char *>(ga->st.ptr) - base;
+    const size_t host_off = static_cast<char *>(parts[n_zero].buf->ptr) - base;
     PM_CUDA(cudaMemsetAsync(base, 0, host_off, s));
     std::vector<char> host(ga->arena.bytes - host_off, 0);
     auto put = [&](const pm_dbuf &b, const void *src, size_t n) {
@@ -2474,9 +2518,12 @@ static pm_status ga_alloc(pm_ga *ga, cudaStream_t s)
     put(ga->glob, &g, sizeof(g));
     put(ga->probs, ga->plan.probs.data(), sizeof(pm_prob) * K);
     put(ga->gprobs, ga->gps.data(), sizeof(ga_prob) * K);
-    PM_CUDA(cudaMemcpyAsync(ga->st.ptr, host.data(), host.size(), cudaMemcpyHostToDevice, s));
+    if (with_spec) {
+        put(ga->gqprobs, ga->gqs.data(), sizeof(ga_prob) * K);
+        put(ga->probsQ, sp.probs.data(), sizeof(pm_prob) * K);
+    }
+    PM_CUDA(cudaMemcpyAsync(base + host_off, host.data(), host.size(), cudaMemcpyHostToDevice, s));
     PM_CUDA(cudaStreamSynchronize(s));
-    PM_CUDA(cudaStreamCreateWithFlags(&ga->cap, cudaStreamNonBlocking));
     return PM_OK;
 }
 
@@ -2518,52 +2565,6 @@ static pm_status ga_configure(pm_ga *ga, int64_t pop, uint64_t seed, const pm_ga
     ga->comb = (prm.flags & PM_GA_INIT_COMBINADIC) != 0;
     if (ga->team && ga->NB > D)
         return PM_ERR_INVALID_ARG;  // deme 0 cannot hold every deme's best
-    return PM_OK;
-}
-
-// Buffers of the speculative mutation cycle: Q x pop candidate bitsets per instance, their facility-major
-// copy, active bits, costs and the scan's accumulators, laid out by spec_plan; the candidates' per-instance
-// layout (ga_prob) and scan table (pm_prob) on the device for batched GAs.
-static pm_status spec_alloc(pm_ga *ga, cudaStream_t s)
-{
-    const int K = ga->K;
-    const int64_t QP = (int64_t)ga->Q * ga->P;
-    ga->gqs.resize(K);
-    int64_t grp = 0;
-    for (int k = 0; k < K; ++k) {
-        const pm_prob &pr = ga->spec_plan.probs[k];
-        ga_prob &gq = ga->gqs[k];
-        gq = ga->gps[k];
-        gq.pop = QP;
-        gq.ind_base = pr.ind_base;
-        gq.word_base = pr.word_base;
-        gq.col_base = pr.col_base;
-        gq.grp_base = grp;
-        grp += pm_ceil_div(QP, 32);
-    }
-    ga->gq = ga->gqs[0];
-    ga->groupsQ_total = grp;
-    const pm_multi_plan &sp = ga->spec_plan;
-    // one allocation: the candidates' buffers (zeroed: accumulators and tickets start at zero), then the two
-    // tables the host fills, in one copy
-    const pm_part parts[] = {{&ga->XQ, (size_t)sp.words_total * 4},
-                             {&ga->costQ, (size_t)sp.ind_total * 8},
-                             {&ga->activeQ, (size_t)pm_round_up(pm_ceil_div(sp.ind_total, 32) * 4, 256)},
-                             {&ga->accumQ, (size_t)sp.ind_total * 8},
-                             {&ga->ticketsQ, (size_t)pm_round_up(std::max<int64_t>(sp.tiles_total, 1) * 4, 256)},
-                             {&ga->colQ, (size_t)sp.cols_total * 4},
-                             {&ga->gqprobs, sizeof(ga_prob) * K},
-                             {&ga->probsQ, sizeof(pm_prob) * K}};
-    PM_TRY(pm_carve(ga->arenaQ, parts, (int)(sizeof(parts) / sizeof(parts[0]))));
-    char *base = static_cast<char *>(ga->arenaQ.ptr);
-    const size_t host_off = static_cast<char *>(ga->gqprobs.ptr) - base;
-    PM_CUDA(cudaMemsetAsync(base, 0, host_off, s));
-    std::vector<char> host(ga->arenaQ.bytes - host_off, 0);
-    std::memcpy(host.data(), ga->gqs.data(), sizeof(ga_prob) * K);
-    std::memcpy(host.data() + (static_cast<char *>(ga->probsQ.ptr) - base - host_off), sp.probs.data(),
-                sizeof(pm_prob) * K);
-    PM_CUDA(cudaMemcpyAsync(ga->gqprobs.ptr, host.data(), host.size(), cudaMemcpyHostToDevice, s));
-    PM_CUDA(cudaStreamSynchronize(s));
     return PM_OK;
 }
 
@@ -2711,20 +2712,33 @@ static pm_status fused_launch(pm_ga *ga, cudaStream_t s)
     return PM_OK;
 }
 
+// The stream the generation graphs are captured on.
+static pm_status ga_make_stream(pm_ga *ga)
+{
+    PM_CUDA(cudaStreamCreateWithFlags(&ga->cap, cudaStreamNonBlocking));
+    return PM_OK;
+}
+
 static pm_status ga_create_common(pm_ga *ga, cudaStream_t s)
 {
     // the warp-per-individual initialisation may use up to 200 KB of shared memory (set outside any capture)
     PM_CUDA(cudaFuncSetAttribute(k_ga_init_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    pm_status st = ga_alloc(ga, s);
-    if (st == PM_OK && ga->spec && spec_alloc(ga, s) != PM_OK) {
+    ga_layout(ga);
+    if (ga->spec)
+        spec_layout(ga);
+    pm_status st = ga_alloc(ga, s, ga->spec);
+    if (st != PM_OK && ga->spec) {
         // no room for the Q x pop candidates: run the mutation cycle try by try instead
         pm_dbuf *bufs[] = {&ga->XQ, &ga->costQ, &ga->activeQ, &ga->accumQ, &ga->ticketsQ, &ga->colQ,
-                           &ga->gqprobs, &ga->probsQ, &ga->arenaQ};
+                           &ga->gqprobs, &ga->probsQ};
         for (pm_dbuf *b : bufs)
             b->release();
         cudaGetLastError();
         ga->spec = false;
+        st = ga_alloc(ga, s, false);
     }
+    if (st == PM_OK)
+        st = ga_make_stream(ga);
     if (st == PM_OK)
         st = fused_prepare(ga, s);
     if (st == PM_OK)
