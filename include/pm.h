@@ -354,7 +354,8 @@ typedef struct pm_ga_params {
     uint32_t flags;       /* PM_GA_TUNE: run pm_tune_eval for this population size at creation;
                              PM_GA_MIGRATE_TEAM: migration variant (ii) of Section 4.5;
                              PM_GA_INIT_COMBINADIC: Section 4.1's chromosome generation */
-    struct pm_model *model;  /* learned swap proposal (see pm_model_create); NULL = the paper's GA only */
+    struct pm_model *model;  /* learned swap proposal (see pm_model_create; the GA's creation builds the
+                                instance's D' copy of pm_swap_stats); NULL = the paper's GA only */
     int32_t candidates;      /* learned try: closed facilities (by gain) paired with every open one; <= 0: 4 */
     int32_t reserved;        /* must be 0 */
 } pm_ga_params;
@@ -555,8 +556,12 @@ PM_API pm_status pm_model_train(pm_model *model, const uint16_t *x, const float 
  * clients it would take, loss[j] = the cost added by closing open facility j
  * alone (second-nearest minus nearest over j's clients, second-nearest taken
  * within the truncated table), assign[j] = the clients j serves.  From the
- * same scan over Pi'/Delta' as the fitness (Section 4.2), continued to the
- * second open rank.  Asynchronous.
+ * same walk over Pi' as the fitness (Section 4.2), continued to the second
+ * open rank, reading the sorted distances D' (the running sums of Delta').
+ * For an instance with Delta' tables the first call builds that D' copy
+ * (n x row_stride int32, kept until pm_instance_destroy) on `stream` and
+ * waits for it; PM_ERR_OOM if it cannot be allocated.  Asynchronous after
+ * that.
  */
 PM_API pm_status pm_swap_stats(pm_instance *inst, const uint32_t *masks, int64_t pop, int64_t *gain, int32_t *cap,
                                int64_t *loss, int32_t *assign, void *stream);
@@ -582,7 +587,8 @@ PM_API pm_status pm_move_features(pm_instance *inst, const int64_t *gain, const 
  * moves (pop x per x 2 int32), their feature rows x (pop x per x 16 BF16)
  * and targets t (pop x per FP32) = (exact cost after the swap - cost) / Z,
  * the swapped bitsets evaluated by the fitness kernels.  All device memory.
- * Allocates stream-ordered scratch.  Asynchronous.
+ * Allocates stream-ordered scratch; the first call on an instance with
+ * Delta' tables also builds its D' copy (see pm_swap_stats).  Asynchronous.
  */
 PM_API pm_status pm_log_moves(pm_instance *inst, const uint32_t *masks, const int64_t *costs, int64_t pop, int64_t per,
                               uint64_t seed, uint16_t *x, float *t, int32_t *moves, void *stream);

@@ -157,6 +157,7 @@ static void destroy_instance(pm_instance *inst)
     inst->flag.release();
     inst->err.release();
     inst->tab_arena.release();  // the tables, err and flag
+    inst->dsorted.release();
     delete inst;
 }
 

@@ -56,7 +56,7 @@
 pm_status pm_batch_ga_plan(pm_batch *b, int64_t pop, pm_multi_plan &out);
 pm_status pm_batch_ga_plan_candidates(pm_batch *b, int64_t pop, int64_t popQ, pm_multi_plan &out);
 // learn.cu
-pm_status pm_learn_prepare(const pm_instance *inst);
+pm_status pm_learn_prepare(const pm_instance *inst, cudaStream_t s);
 pm_status pm_launch_swap_stats(const pm_instance *inst, const uint32_t *masks, int64_t pop, int64_t *gain,
                                int32_t *cap, int64_t *loss, int32_t *assign, cudaStream_t s);
 pm_status pm_launch_candidates(const pm_instance *inst, const uint32_t *masks, int64_t pop, const int64_t *gain,
@@ -2808,7 +2808,7 @@ static pm_status ga_create_single(pm_instance *inst, uint64_t seed, int64_t pop,
         st = comb_prepare(ga, inst, static_cast<cudaStream_t>(stream));
     if (st == PM_OK && ga->model) {
         const size_t Pm = (size_t)pop * inst->m, C = (size_t)inst->p * ga->T;
-        st = pm_learn_prepare(inst);
+        st = pm_learn_prepare(inst, static_cast<cudaStream_t>(stream));
         if (st == PM_OK) st = ga->s_gain.reserve(Pm * 8);
         if (st == PM_OK) st = ga->s_loss.reserve(Pm * 8);
         if (st == PM_OK) st = ga->s_cap.reserve(Pm * 4);

@@ -1066,18 +1066,51 @@ __global__ void k_refresh_bf16(const float *__restrict__ P, __nv_bfloat16 *__res
 }
 
 // ---------------------------------------------------------------------------
-// Swap statistics: one CTA per individual; accumulators in shared memory when
-// they fit (else in the output arrays, zeroed by the caller).
+// D' from Delta': per row the running sums of the increments up to each rank
+// (the row's sorted distances, Eq. 4 summed), zero in the padding past L.  One
+// warp per row, 32 ranks per step with a carry.
 // ---------------------------------------------------------------------------
-template <typename Acc, bool kCum, bool kSmem>
+__global__ void k_running_sums(const int32_t *__restrict__ delta, int64_t n, int32_t L, int64_t stride,
+                               int32_t *__restrict__ out)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
+        const int32_t *row = delta + i * stride;
+        int32_t *orow = out + i * stride;
+        int32_t carry = 0;
+        for (int64_t base = 0; base < stride; base += 32) {
+            const int64_t r = base + lane;
+            int32_t v = r < L ? __ldg(row + r) : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t y = __shfl_up_sync(PM_FULL_MASK, v, o);
+                if (lane >= o)
+                    v += y;
+            }
+            v += carry;
+            if (r < stride)
+                orow[r] = r < L ? v : 0;
+            carry = __shfl_sync(PM_FULL_MASK, v, 31);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Swap statistics: one CTA per individual over the rows of Pi' and of the
+// sorted distances D' (the instance's table when it is cumulative, else the
+// running sums of Delta' built once per instance), so that a rank's distance
+// is one load and needs no scan; accumulators in shared memory when they fit
+// (else in the output arrays, zeroed by the caller).
+// ---------------------------------------------------------------------------
+template <typename Acc, bool kSmem>
 __global__ void __launch_bounds__(1024, 2) k_swap_stats(const uint16_t *__restrict__ pi,
-                                                     const int32_t *__restrict__ delta, int64_t n, int32_t L,
+                                                     const int32_t *__restrict__ dist, int64_t n, int32_t L,
                                                      int64_t stride, int32_t W, int32_t m,
                                                      const uint32_t *__restrict__ masks, int64_t pop,
                                                      unsigned long long *__restrict__ gain, int *__restrict__ cap,
                                                      unsigned long long *__restrict__ loss, int *__restrict__ assign)
 {
-    constexpr bool cum = kCum;  // the tables hold D' (running sums of Delta')
     extern __shared__ __align__(16) unsigned char sm[];
     const int64_t t = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -1099,24 +1132,8 @@ __global__ void __launch_bounds__(1024, 2) k_swap_stats(const uint16_t *__restri
             atomicAdd((first ? assign : cap) + tm + k, 1);
         }
     };
-    auto add_gain = [&](uint32_t k, int32_t v) {  // facility k (closed, ranked before the first open) gains v
-        if constexpr (kSmem) {
-            atomicAdd(Gs + k, (Acc)(uint32_t)v);
-            atomicAdd(Cs + k, 1);
-        } else {
-            atomicAdd(gain + tm + k, (unsigned long long)(uint32_t)v);
-            atomicAdd(cap + tm + k, 1);
-        }
-    };
-    auto add_loss = [&](uint32_t j, int32_t v) {  // the first open facility j would lose v
-        if constexpr (kSmem) {
-            atomicAdd(Ls + j, (Acc)(uint32_t)v);
-            atomicAdd(As + j, 1);
-        } else {
-            atomicAdd(loss + tm + j, (unsigned long long)(uint32_t)v);
-            atomicAdd(assign + tm + j, 1);
-        }
-    };
+    auto add_gain = [&](uint32_t k, int32_t v) { add_stat(false, k, v); };  // closed k, ranked before the first open
+    auto add_loss = [&](uint32_t j, int32_t v) { add_stat(true, j, v); };   // the first open facility j
     if constexpr (kSmem) {
         for (int j = threadIdx.x; j < m; j += blockDim.x) {
             Gs[j] = 0;
@@ -1129,19 +1146,20 @@ __global__ void __launch_bounds__(1024, 2) k_swap_stats(const uint16_t *__restri
         bits[w] = masks[t * W + w];
     // the first 32 ranks of this warp's first client (constant tables: no dependence on the zeroing above)
     const int nc = (int)n;        // clients (the tables of one GPU hold far fewer than 2^31 rows)
-    const int st = (int)stride;   // row stride of Pi'/Delta' (at most 65536)
+    const int st = (int)stride;   // row stride of Pi'/D' (at most 65536)
     uint32_t j_nx = 0;
     int32_t d_nx = 0;
     if (warp < nc && lane < L) {
         j_nx = __ldg(pi + (size_t)warp * st + lane);
-        d_nx = __ldg(delta + (size_t)warp * st + lane);
+        d_nx = __ldg(dist + (size_t)warp * st + lane);
     }
     __syncthreads();
     for (int i = warp; i < nc; i += nwarps) {
-        int32_t d_carry0 = 0;  // Delta': the sum of the first 32 increments (D': the value at rank 31)
-        // first 32 ranks (loaded a client ahead).  When the first open rank r1 is among them -- the usual
-        // case unless p/m is tiny -- every gain comes from this step: the ranks before r1 gain d1 - d(i, k) and
-        // the facility at r1 loses d2 - d1, with d2 at the second open rank (later steps are read only for it).
+        const uint16_t *prow = pi + (size_t)i * st;
+        const int32_t *drow = dist + (size_t)i * st;
+        // first 32 ranks (loaded a client ahead).  When the first open rank r1 is among them -- the usual case
+        // unless p/m is tiny -- every gain comes from this step: the ranks before r1 gain d1 - d(i, k) and the
+        // facility at r1 loses d2 - d1, with d2 at the second open rank (later steps are read only for it).
         {
             const uint32_t j0 = j_nx;
             const int32_t d0 = d_nx;
@@ -1150,30 +1168,18 @@ __global__ void __launch_bounds__(1024, 2) k_swap_stats(const uint16_t *__restri
             d_nx = 0;
             if (inext < nc && lane < L) {
                 j_nx = __ldg(pi + (size_t)inext * st + lane);
-                d_nx = __ldg(delta + (size_t)inext * st + lane);
+                d_nx = __ldg(dist + (size_t)inext * st + lane);
             }
             const bool open0 = (lane < L) && ((bits[j0 >> 5] >> (j0 & 31)) & 1u);
             const uint32_t bal0 = __ballot_sync(PM_FULL_MASK, open0);
             if (bal0 != 0u) {
-                int32_t cs = d0;  // running sum to this lane's rank (cumulative tables: the value itself)
-                if (!cum) {
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const int32_t y = __shfl_up_sync(PM_FULL_MASK, cs, o);
-                        if (lane >= o)
-                            cs += y;
-                    }
-                }
                 const int f1 = __ffs(bal0) - 1;
-                const int32_t d1 = __shfl_sync(PM_FULL_MASK, cs, f1);
+                const int32_t d1 = __shfl_sync(PM_FULL_MASK, d0, f1);
                 const uint32_t rest = bal0 & (bal0 - 1u);
                 int32_t d2;
                 if (rest != 0u) {
-                    d2 = __shfl_sync(PM_FULL_MASK, cs, __ffs(rest) - 1);
+                    d2 = __shfl_sync(PM_FULL_MASK, d0, __ffs(rest) - 1);
                 } else {  // the second open rank lies beyond this step, or the row holds no second one
-                    const uint16_t *prow = pi + (size_t)i * st;
-                    const int32_t *drow = delta + (size_t)i * st;
-                    int32_t carry = __shfl_sync(PM_FULL_MASK, cs, 31);  // Delta': running sum at rank 31
                     bool got = false;
                     d2 = 0;
                     for (int base = 32; base < L; base += 32) {
@@ -1186,34 +1192,23 @@ __global__ void __launch_bounds__(1024, 2) k_swap_stats(const uint16_t *__restri
                         }
                         const uint32_t bal = __ballot_sync(PM_FULL_MASK, (r < L) && ((bits[j >> 5] >> (j & 31)) & 1u));
                         if (bal != 0u) {
-                            const int f = __ffs(bal) - 1;
-                            d2 = cum ? __shfl_sync(PM_FULL_MASK, dl, f)
-                                     : carry + __reduce_add_sync(PM_FULL_MASK, lane <= f ? dl : 0);
+                            d2 = __shfl_sync(PM_FULL_MASK, dl, __ffs(bal) - 1);
                             got = true;
                             break;
                         }
-                        if (!cum)
-                            carry += __reduce_add_sync(PM_FULL_MASK, dl);
                     }
                     if (!got)  // the last distance of the truncated row
-                        d2 = cum ? __ldg(drow + L - 1) : carry;
+                        d2 = __ldg(drow + L - 1);
                 }
                 if (lane <= f1) {  // one pair of atomics per lane: lane f1 holds the first open facility itself
                     const bool first = lane == f1;
-                    add_stat(first, j0, first ? d2 - d1 : d1 - cs);
+                    add_stat(first, j0, first ? d2 - d1 : d1 - d0);
                 }
                 continue;
             }
-            // no open facility among the first 32 ranks: the general path goes on from rank 32 with their sum
-            if (!cum)
-                d_carry0 = __reduce_add_sync(PM_FULL_MASK, d0);
-            else
-                d_carry0 = __shfl_sync(PM_FULL_MASK, d0, 31);
         }
-        // general path -- pass 1: first and second open ranks and their distances
-        const uint16_t *prow = pi + (size_t)i * st;
-        const int32_t *drow = delta + (size_t)i * st;
-        int32_t carry = d_carry0, d1 = 0, d2 = 0;
+        // general path (no open facility among the first 32 ranks) -- pass 1: first and second open ranks
+        int32_t d1 = 0, d2 = 0;
         int r1 = -1, found = 0;
         uint32_t f1 = 0;
         for (int base = 32; base < L && found < 2; base += 32) {
@@ -1223,75 +1218,37 @@ __global__ void __launch_bounds__(1024, 2) k_swap_stats(const uint16_t *__restri
             if (r < L) {
                 j = __ldg(prow + r);
                 dl = __ldg(drow + r);
-            } else if (cum) {
-                dl = __ldg(drow + L - 1);  // past the row the running sum stays at its last value
             }
-            const bool open = (r < L) && ((bits[j >> 5] >> (j & 31)) & 1u);
-            uint32_t bal = __ballot_sync(PM_FULL_MASK, open);
-            if (bal == 0u) {  // no open facility among these 32 ranks: only the carry moves
-                if (!cum)
-                    carry += __reduce_add_sync(PM_FULL_MASK, dl);
-                else
-                    carry = __shfl_sync(PM_FULL_MASK, dl, 31);
+            uint32_t bal = __ballot_sync(PM_FULL_MASK, (r < L) && ((bits[j >> 5] >> (j & 31)) & 1u));
+            if (bal == 0u)
                 continue;
-            }
-            int32_t cs = dl;  // cumulative tables: already the running sum
-            if (!cum) {
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int32_t y = __shfl_up_sync(PM_FULL_MASK, cs, o);
-                    if (lane >= o)
-                        cs += y;
-                }
-                cs += carry;
-            }
-            if (found == 0 && bal) {
+            if (found == 0) {
                 const int f = __ffs(bal) - 1;
-                d1 = __shfl_sync(PM_FULL_MASK, cs, f);
+                d1 = __shfl_sync(PM_FULL_MASK, dl, f);
                 f1 = __shfl_sync(PM_FULL_MASK, j, f);
                 r1 = base + f;
                 found = 1;
                 bal &= bal - 1u;
                 // the ranks of this step before r1 gain d1 - d(i, k) now; earlier steps are revisited below
                 if (lane < f)
-                    add_gain(j, d1 - cs);
+                    add_gain(j, d1 - dl);
             }
             if (found == 1 && bal) {
-                d2 = __shfl_sync(PM_FULL_MASK, cs, __ffs(bal) - 1);
+                d2 = __shfl_sync(PM_FULL_MASK, dl, __ffs(bal) - 1);
                 found = 2;
             }
-            carry = __shfl_sync(PM_FULL_MASK, cs, 31);
         }
         if (found == 0)
             continue;  // fewer than p open facilities: no statistics for this client
         if (found == 1)
-            d2 = carry;  // no second open facility within the table
+            d2 = __ldg(drow + L - 1);  // no second open facility within the table: its last distance
         if (lane == 0)
             add_loss(f1, d2 - d1);
         // pass 2: the facilities of the steps before r1's step (no open one among them) gain d1 - d(i, k)
-        carry = 0;
         const int r1_step = r1 & ~31;
         for (int base = 0; base < r1_step; base += 32) {
             const int r = base + lane;
-            uint32_t j = 0;
-            int32_t dl = 0;
-            if (r < r1) {
-                j = __ldg(prow + r);
-                dl = __ldg(drow + r);
-            }
-            int32_t cs = dl;
-            if (!cum) {
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int32_t y = __shfl_up_sync(PM_FULL_MASK, cs, o);
-                    if (lane >= o)
-                        cs += y;
-                }
-                cs += carry;
-            }
-            if (r < r1)
-                add_gain(j, d1 - cs);
-            carry = __shfl_sync(PM_FULL_MASK, cs, 31);
+            add_gain(__ldg(prow + r), d1 - __ldg(drow + r));
         }
     }
     if constexpr (kSmem) {
@@ -1618,7 +1575,7 @@ __global__ void k_targets(const int64_t *__restrict__ before, const int64_t *__r
 // Host side: the model object
 // ---------------------------------------------------------------------------
 
-pm_status pm_learn_prepare(const pm_instance *inst);
+pm_status pm_learn_prepare(const pm_instance *inst, cudaStream_t s);
 
 struct pm_model {
     int device = 0;
@@ -1990,23 +1947,20 @@ pm_status pm_launch_swap_stats(const pm_instance *inst, const uint32_t *masks, i
         PM_CUDA(cudaMemsetAsync(cap, 0, (size_t)pop * inst->m * 4, s));
         PM_CUDA(cudaMemsetAsync(assign, 0, (size_t)pop * inst->m * 4, s));
     }
+    // the sorted distances: the instance's own table when cumulative, else the running sums that
+    // pm_learn_prepare builds (every caller prepares the instance first)
+    const int32_t *dist = inst->cum ? inst->delta : static_cast<const int32_t *>(inst->dsorted.ptr);
+    if (!dist)
+        return PM_ERR_INVALID_ARG;
 #define PM_STATS_ARGS                                                                                              \
-    inst->pi, inst->delta, inst->n, (int32_t)inst->L, inst->stride, (int32_t)inst->W, (int32_t)inst->m, masks, pop, \
+    inst->pi, dist, inst->n, (int32_t)inst->L, inst->stride, (int32_t)inst->W, (int32_t)inst->m, masks, pop,       \
         reinterpret_cast<unsigned long long *>(gain), cap, reinterpret_cast<unsigned long long *>(loss), assign
-#define PM_STATS_LAUNCH(ACC, SMEM)                                                                                 \
-    do {                                                                                                           \
-        if (inst->cum)                                                                                             \
-            k_swap_stats<ACC, true, SMEM><<<(unsigned)pop, 1024, smem, s>>>(PM_STATS_ARGS);                        \
-        else                                                                                                       \
-            k_swap_stats<ACC, false, SMEM><<<(unsigned)pop, 1024, smem, s>>>(PM_STATS_ARGS);                       \
-    } while (0)
     if (narrow && in_smem)
-        PM_STATS_LAUNCH(unsigned int, true);
+        k_swap_stats<unsigned int, true><<<(unsigned)pop, 1024, smem, s>>>(PM_STATS_ARGS);
     else if (in_smem)
-        PM_STATS_LAUNCH(unsigned long long, true);
+        k_swap_stats<unsigned long long, true><<<(unsigned)pop, 1024, smem, s>>>(PM_STATS_ARGS);
     else
-        PM_STATS_LAUNCH(unsigned long long, false);
-#undef PM_STATS_LAUNCH
+        k_swap_stats<unsigned long long, false><<<(unsigned)pop, 1024, smem, s>>>(PM_STATS_ARGS);
 #undef PM_STATS_ARGS
     PM_CUDA(cudaGetLastError());
     return PM_OK;
@@ -2022,7 +1976,7 @@ extern "C" pm_status pm_swap_stats(pm_instance *inst, const uint32_t *masks, int
         if (!pm_is_device_ptr(p))
             return PM_ERR_INVALID_ARG;
     PM_CUDA(cudaSetDevice(inst->device));
-    PM_TRY(pm_learn_prepare(inst));
+    PM_TRY(pm_learn_prepare(inst, static_cast<cudaStream_t>(stream)));
     return pm_launch_swap_stats(inst, masks, pop, gain, cap, loss, assign, static_cast<cudaStream_t>(stream));
 }
 
@@ -2074,18 +2028,31 @@ pm_status pm_launch_candidates(const pm_instance *inst, const uint32_t *masks, i
 int pm_mlp_in_width() { return kIn; }
 
 // Kernel attributes of the learned path for this instance (call outside stream capture).
-pm_status pm_learn_prepare(const pm_instance *inst)
+pm_status pm_learn_prepare(const pm_instance *inst, cudaStream_t s)
 {
+    if (!inst->cum) {
+        // the running sums D' of a Delta' instance, once (on s, waited for: later launches may use any stream)
+        std::lock_guard<std::mutex> g(inst->dsorted_mu);
+        if (!inst->dsorted.ptr) {
+            const size_t bytes = (size_t)inst->n * (size_t)inst->stride * sizeof(int32_t);
+            PM_TRY(inst->dsorted.reserve(bytes));
+            const int64_t blocks = std::min<int64_t>(pm_ceil_div(inst->n, 8), (int64_t)inst->sm_count * 8);
+            k_running_sums<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, s>>>(
+                inst->delta, inst->n, (int32_t)inst->L, inst->stride, static_cast<int32_t *>(inst->dsorted.ptr));
+            cudaError_t e = cudaGetLastError();
+            if (e == cudaSuccess)
+                e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) {
+                inst->dsorted.release();
+                PM_CUDA(e);
+            }
+        }
+    }
     const int cap = (int)(inst->smem_optin > 1024 ? inst->smem_optin - 1024 : inst->smem_optin);
     // the shared-memory accumulator variants (the global one holds only the bitset: at most 8 KB)
-    PM_CUDA(cudaFuncSetAttribute(k_swap_stats<unsigned int, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    PM_CUDA(cudaFuncSetAttribute(k_swap_stats<unsigned int, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+    PM_CUDA(cudaFuncSetAttribute(k_swap_stats<unsigned long long, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  cap));
-    PM_CUDA(cudaFuncSetAttribute(k_swap_stats<unsigned int, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 cap));
-    PM_CUDA(cudaFuncSetAttribute(k_swap_stats<unsigned long long, false, true>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
-    PM_CUDA(cudaFuncSetAttribute(k_swap_stats<unsigned long long, true, true>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
     PM_CUDA(cudaFuncSetAttribute(k_candidates, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
     return mlp_init_attrs();
 }
@@ -2100,8 +2067,8 @@ extern "C" pm_status pm_log_moves(pm_instance *inst, const uint32_t *masks, cons
         if (!pm_is_device_ptr(ptr))
             return PM_ERR_INVALID_ARG;
     PM_CUDA(cudaSetDevice(inst->device));
-    PM_TRY(pm_learn_prepare(inst));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    PM_TRY(pm_learn_prepare(inst, s));
     const size_t Pm = (size_t)pop * inst->m, rows = (size_t)pop * per;
     char *buf = nullptr;
     const size_t bytes = Pm * 24 + rows * inst->W * 4 + rows * 8 + 1024;

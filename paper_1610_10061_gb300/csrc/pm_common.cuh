@@ -149,6 +149,10 @@ struct pm_instance {
     // staging and scratch for pm_eval_population
     pm_dbuf stage_masks, stage_costs, partials, tickets, columns, flag, err;
     pm_dbuf tab_arena;  // one allocation holding delta, pi, err and flag
+    // Delta' instances: the running sums D' (the sorted distances), built once on the first request for swap
+    // statistics, which then read distances directly instead of re-summing increments
+    mutable pm_dbuf dsorted;
+    mutable std::mutex dsorted_mu;
     std::mutex lock;
     // evaluation plans chosen by the autotuner, by population size
     mutable std::mutex plan_mu;
