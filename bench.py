@@ -701,8 +701,9 @@ def run_ours(args):
 def extra_records(pm, torch, args):
     """The other rows of the metric, measured in the default run after the headline's timed region: one
     evaluation pass of 4096 random p-subsets on the Euclidean n = m = 10000 instance for p = 10, 100, 1000 (the
-    fitness-throughput workload, tables far larger than L2), and the learned-vs-plain time-to-target on the
-    clustered n = m = 5000 instance (p = 500 and 50) and on the 100-node graph instance (target: its optimum)."""
+    fitness-throughput workload, tables far larger than L2), the learned-vs-plain time-to-target on the
+    clustered n = m = 5000 instance (p = 500 and 50) and on the 100-node graph instance (target: its optimum), and
+    20 generations of the 256 uneven instances evolved as one batch (the `--workload batched256` line)."""
     out = {"eval_euclid10000": [], "learned": {}}
     t0 = time.perf_counter()
     for p in (10, 100, 1000):
@@ -710,6 +711,7 @@ def extra_records(pm, torch, args):
         out["eval_euclid10000"].append(rec)
     for name in ("gmm5000_p500", "gmm5000_p50", "graph100"):
         out["learned"][name] = learned_record(pm, torch, name, args.tables, limit=400 if name == "graph100" else 600)
+    out["batched256"] = batched_record(pm, torch, 256, args.tables, steps=20, warmup=3)
     out["extra_s"] = time.perf_counter() - t0
     return out
 
@@ -940,14 +942,6 @@ def layout_times(pm, torch, d, p, masks, tables):
 
 def run_batched(args):
     """256 uneven instances evolved together: one launch per kernel of a generation covers them all."""
-    import numpy as np
-
-    from paper_1610_10061_gb300.inputs import batched_instances
-
-    count = int(args.workload[len("batched"):] or 256)
-    t0 = time.perf_counter()
-    data = batched_instances(count, seed=3, workers=max(1, (os.cpu_count() or 2) - 1))
-    gen_s = time.perf_counter() - t0
     import torch
 
     from paper_1610_10061_gb300 import build
@@ -956,9 +950,24 @@ def run_batched(args):
     from paper_1610_10061_gb300 import pm
 
     torch.cuda.set_device(0)
+    count = int(args.workload[len("batched"):] or 256)
+    line = batched_record(pm, torch, count, args.tables, args.steps, args.warmup)
+    print(json.dumps(line), flush=True)
+
+
+def batched_record(pm, torch, count, tables="delta", steps=50, warmup=5):
+    """`count` uneven instances (cfg4's recipe) evolved together, one generation per timed step (L2 flushed
+    between steps), with the roofline of one batched evaluation pass; the bench line of `--workload batchedN`."""
+    import numpy as np
+
+    from paper_1610_10061_gb300.inputs import batched_instances
+
+    t0 = time.perf_counter()
+    data = batched_instances(count, seed=3, workers=max(1, (os.cpu_count() or 2) - 1))
+    gen_s = time.perf_counter() - t0
     stream = torch.cuda.current_stream()
     t0 = time.perf_counter()
-    insts = [pm.Instance(d, p, stream=stream.cuda_stream, cumulative=args.tables == "cumulative") for d, p in data]
+    insts = [pm.Instance(d, p, stream=stream.cuda_stream, cumulative=tables == "cumulative") for d, p in data]
     tables_s = time.perf_counter() - t0
     batch = pm.Batch(insts)
     pop = 256
@@ -966,16 +975,16 @@ def run_batched(args):
     ga = batch.ga(seed=0, pop=pop, deme=256, stream=stream.cuda_stream)
     info = ga.info()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         pm.pm_ga_step(ga.handle, 1, None, stream.cuda_stream)
     torch.cuda.synchronize()
     e0 = sum(pm.pm_ga_instance_result(ga.handle, k, None, stream.cuda_stream)[2] for k in range(count))
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     clocks = Clocks(0)
     clocks.start()
     torch.cuda.nvtx.range_push("timed")
-    for k in range(args.steps):
+    for k in range(steps):
         flush.zero_()
         starts[k].record(stream)
         pm.pm_ga_step(ga.handle, 1, None, stream.cuda_stream)
@@ -1016,16 +1025,16 @@ def run_batched(args):
     peak, peak_kind = measured_peaks()
     achieved = alg_bytes / (eval_ms / 1000.0) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": profiled_traffic(args.workload),
+                "traffic": profiled_traffic(f"batched{count}"),
                 "kernel": "batched fitness evaluation (transpose + column scan over all instances)",
                 "peak_source": f"{peak_kind} burst copy bandwidth", "launch_ms": eval_ms,
                 "alg_bytes_per_launch": alg_bytes,
                 "note": "algorithmic bytes = sum over instances of pop * (n*(m+1)/(p+1)*6 + 4W + 8); each row chunk "
                         "a CTA fetches serves 128 individuals, so this exceeds the DRAM bytes moved"}
-    line = {"metric": METRIC, "value": (e1 - e0) / (ms / 1000), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+    line = {"metric": METRIC, "value": (e1 - e0) / (ms / 1000), "unit": UNIT, "n_gpus": 1, "steps": steps,
+            "warmup": warmup, "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": {"tables": args.tables, "workload": f"batched{count}: {count} instances, n=m log-uniform [100,5000] "
+            "config": {"tables": tables, "workload": f"batched{count}: {count} instances, n=m log-uniform [100,5000] "
                                    f"(min {min(n_sizes)}, max {max(n_sizes)}), p U[5,n/10], half graph (4n edges, "
                                    "APSP) half Euclidean; pop 256 each in one deme; one launch per kernel per "
                                    "generation covers all instances",
@@ -1033,9 +1042,13 @@ def run_batched(args):
                        "tables_build_s": tables_s, "step": "one generation of every instance's GA",
                        "l2": "flushed between timed steps"},
             "evals": int(e1 - e0),
-            "gpu_launches": int((info["kernels_per_generation"] + info["kernels_per_step_call"]) * args.steps),
-            "roofline": roofline, "roofline_issue": issue_roofline(args.workload, eval_ms), "clocks": clk}
-    print(json.dumps(line), flush=True)
+            "gpu_launches": int((info["kernels_per_generation"] + info["kernels_per_step_call"]) * steps),
+            "roofline": roofline, "roofline_issue": issue_roofline(f"batched{count}", eval_ms), "clocks": clk}
+    ga.close()
+    batch.close()
+    for inst in insts:
+        inst.close()
+    return line
 
 
 def learned_record(pm, torch, name, tables="delta", seeds=range(5), target_gens=300, limit=600):
