@@ -652,22 +652,28 @@ def run_ours(args):
     dh = torch.from_numpy(d).pin_memory()
     best_mask = torch.zeros(W, dtype=torch.int32).pin_memory()
     trace = torch.zeros(args.steps, dtype=torch.int64).pin_memory()
+
+    def e2e_job():
+        h = pm.pm_instance_create_ex(dh, n, m, p, local, stream.cuda_stream, pm.PM_TABLES_CUMULATIVE if cum else 0)
+        out = pm.pm_ga_run(h, 0, pop, args.steps, pm._params(deme=deme, stream_id=rank, init=args.init),
+                           best_mask, trace, stream.cuda_stream)
+        pm.pm_instance_destroy(h)
+        return out
+
+    e2e_job()  # untimed: the process's first job of this kind loads the kernels only its graph uses
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    h = pm.pm_instance_create_ex(dh, n, m, p, local, stream.cuda_stream, pm.PM_TABLES_CUMULATIVE if cum else 0)
-    bc, gr, ev = pm.pm_ga_run(h, 0, pop, args.steps, pm._params(deme=deme, stream_id=rank, init=args.init),
-                              best_mask, trace,
-                              stream.cuda_stream)
-    pm.pm_instance_destroy(h)
+    bc, gr, ev = e2e_job()
     t1 = time.perf_counter()
     ev_all, e2e_ms = combine_ranks(ev, 1000.0 * (t1 - t0), device="cuda")  # whole job: sum of evals, slowest rank
     e2e = {"value": ev_all / (e2e_ms / 1000.0), "unit": UNIT,
            "h2d_bytes_per_step": n * m * 4 / args.steps,
            "d2h_bytes_per_step": (W * 4 + 8 * 3) / args.steps + 8,
            "note": f"pm_instance_create from pinned host d + pm_ga_run({args.steps} generations) with host "
-                   "best mask and trace; copies amortised over the steps of one job, whose generations run as "
-                   "one graph launch (device-side loop, no L2 flush between generations), whereas the "
-                   "device-timed value launches each generation alone after an L2 flush"}
+                   "best mask and trace + pm_instance_destroy, one job timed after one identical untimed job; "
+                   "copies amortised over the steps of the job, whose generations run as one graph launch "
+                   "(device-side loop, no L2 flush between generations), whereas the device-timed value "
+                   "launches each generation alone after an L2 flush"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
