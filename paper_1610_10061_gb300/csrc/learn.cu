@@ -12,7 +12,9 @@
 //   assign[f1] += 1
 // gain[k] is exactly what opening k alone saves and loss[j] what closing j
 // alone costs; the perceptron predicts the exact cost change of the swap
-// (close j, open k) from these first-order quantities.
+// (close j, open k) from these first-order quantities.  The statistics walk
+// the rows of Pi' against the sorted distances D' (an instance with Delta'
+// tables builds a D' copy once), so d(i, k) at a rank is a single load.
 //
 // Features of a move (8, zero-padded to 16 for one tensor-core k-step), Z =
 // max(cost / p, 1):  loss_j/Z, gain_k/Z, assign_j/(n/p), cap_k/(n/p),
