@@ -30,6 +30,12 @@
  *    library's own device buffers (the call then synchronises `stream`).
  *  - All device work runs in the library's own CUDA kernels; there is no CPU
  *    fallback.  A failed CUDA call is reported as PM_ERR_CUDA.
+ *  - Device memory of the library's objects comes from a memory pool of the
+ *    library's own per device.  Releasing an object waits, as cudaFree
+ *    does, for the device's launches, then keeps up to 256 MiB of the freed
+ *    memory mapped for later allocations (the rest goes back to the driver
+ *    at the next synchronisation).  PM_POOL=0 in the environment allocates
+ *    with cudaMalloc and cudaFree instead.
  */
 #ifndef PM_H
 #define PM_H

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "pm_alloc.h"
@@ -31,13 +32,110 @@ static bool injected_failure()
     return false;
 }
 
+// The library's device memory comes from one memory pool per device, which keeps up to kPoolKeepBytes of
+// released memory mapped for the next allocations: cudaMalloc and cudaFree cost tens of microseconds each on
+// GB300, a pool allocation or release a few.  Memory above that amount goes back to the driver at the next
+// synchronisation.  A device without memory pools falls back to cudaMalloc / cudaFree.
+constexpr size_t kPoolKeepBytes = (size_t)256 << 20;
+constexpr int kMaxDevices = 64;
+
+namespace {
+struct DevicePool {
+    bool tried = false;
+    cudaMemPool_t pool = nullptr;  // null: this device allocates with cudaMalloc
+    cudaStream_t stream = nullptr;  // allocations and releases of pm_dbuf memory are ordered on it
+};
+std::mutex g_pool_mu;
+DevicePool g_pools[kMaxDevices];
+}  // namespace
+
+// The current device's pool (created on first use; never destroyed: it lives as long as the process).
+static DevicePool *device_pool()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> g(g_pool_mu);
+    DevicePool &dp = g_pools[dev];
+    if (!dp.tried) {
+        dp.tried = true;
+        int supported = 0;
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        cudaStream_t st = nullptr;
+        uint64_t keep = kPoolKeepBytes;
+        const char *env = std::getenv("PM_POOL");  // PM_POOL=0: cudaMalloc / cudaFree (for comparison)
+        bool ok = !(env && env[0] == '0') &&
+                  cudaDeviceGetAttribute(&supported, cudaDevAttrMemoryPoolsSupported, dev) == cudaSuccess &&
+                  supported && cudaMemPoolCreate(&pool, &props) == cudaSuccess;
+        ok = ok && cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep) == cudaSuccess;
+        ok = ok && cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess;
+        if (ok) {
+            dp.pool = pool;
+            dp.stream = st;
+        } else {
+            if (st)
+                (void)cudaStreamDestroy(st);
+            if (pool)
+                (void)cudaMemPoolDestroy(pool);
+            (void)cudaGetLastError();
+        }
+    }
+    return &dp;
+}
+
 cudaError_t pm_device_malloc(void **ptr, size_t bytes)
 {
     if (injected_failure()) {
         *ptr = nullptr;
         return cudaErrorMemoryAllocation;
     }
-    return cudaMalloc(ptr, bytes);
+    DevicePool *dp = device_pool();
+    if (!dp || !dp->pool)
+        return cudaMalloc(ptr, bytes);
+    // ordered on the pool's stream, then waited for: the memory is ready for any stream, as cudaMalloc's is
+    cudaError_t e = cudaMallocFromPoolAsync(ptr, bytes, dp->pool, dp->stream);
+    if (e != cudaSuccess)
+        return e;
+    e = cudaStreamSynchronize(dp->stream);
+    if (e != cudaSuccess) {
+        (void)cudaFreeAsync(*ptr, dp->stream);
+        *ptr = nullptr;
+    }
+    return e;
+}
+
+void pm_device_free(void *ptr)
+{
+    if (!ptr)
+        return;
+    int cur = 0, dev = 0;
+    cudaPointerAttributes a;
+    if (cudaGetDevice(&cur) != cudaSuccess || cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return;
+    }
+    dev = a.device;
+    if (dev != cur && cudaSetDevice(dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return;
+    }
+    DevicePool *dp = device_pool();
+    if (!dp || !dp->pool) {
+        pm_clear_error(cudaFree(ptr));
+    } else {
+        // as cudaFree does, wait for every launch that may still use the memory, then return it to the pool
+        pm_clear_error(cudaDeviceSynchronize());
+        pm_clear_error(cudaFreeAsync(ptr, dp->stream));
+    }
+    if (dev != cur)
+        pm_clear_error(cudaSetDevice(cur));
 }
 
 cudaError_t pm_device_malloc_async(void **ptr, size_t bytes, cudaStream_t s)
@@ -46,7 +144,10 @@ cudaError_t pm_device_malloc_async(void **ptr, size_t bytes, cudaStream_t s)
         *ptr = nullptr;
         return cudaErrorMemoryAllocation;
     }
-    return cudaMallocAsync(ptr, bytes, s);
+    DevicePool *dp = device_pool();
+    if (!dp || !dp->pool)
+        return cudaMallocAsync(ptr, bytes, s);
+    return cudaMallocFromPoolAsync(ptr, bytes, dp->pool, s);
 }
 
 extern "C" pm_status pm_debug_fail_alloc(int64_t after, int64_t *pending)
@@ -81,7 +182,7 @@ pm_status pm_dbuf::reserve(size_t want, bool *fresh)
 void pm_dbuf::release()
 {
     if (ptr && !borrowed)
-        pm_clear_error(cudaFree(ptr));
+        pm_device_free(ptr);
     ptr = nullptr;
     bytes = 0;
     borrowed = false;

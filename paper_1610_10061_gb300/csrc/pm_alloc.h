@@ -9,9 +9,15 @@
 
 #include <cstddef>
 
-// cudaMalloc, or cudaErrorMemoryAllocation without calling CUDA when the
-// armed failure is due.
+// Device memory from the library's pool of the current device, ready for any
+// stream when the call returns (as cudaMalloc's); or cudaErrorMemoryAllocation
+// without calling CUDA when the armed failure is due.
 cudaError_t pm_device_malloc(void **ptr, size_t bytes);
 
-// cudaMallocAsync on stream s, with the same injected failure.
+// Releases memory of pm_device_malloc after every launch on its device has
+// finished (as cudaFree waits); the pool keeps it for later allocations.
+void pm_device_free(void *ptr);
+
+// Stream-ordered memory from the same pool on stream s (released with
+// cudaFreeAsync on s), with the same injected failure.
 cudaError_t pm_device_malloc_async(void **ptr, size_t bytes, cudaStream_t s);
