@@ -34,8 +34,10 @@
 // scan reads, so no evaluation needs a separate transpose.  A call of several
 // generations is one CUDA graph: a gate kernel and a conditional while-node
 // whose body is one generation; a call of one generation launches a plain
-// graph of the body.  An instance that reached its saturation limit stops:
-// its kernels do nothing while the others go on.
+// graph of the body (pm_ga_run, a single call, captures only the one it
+// launches).  An instance that reached its saturation limit stops: its
+// kernels do nothing while the others go on.  A GA's device buffers (and the
+// speculative cycle's candidates) are slices of one allocation.
 //
 // Random numbers: Philox4x32-10 (Salmon et al., SC'11), stateless, keyed by
 // (seed) with counter (generation, unit, op * 2^16 + slot / 4, stream id);
