@@ -1305,6 +1305,15 @@ __global__ void k_move_features(const unsigned long long *__restrict__ gain, con
 // facilities with the largest gain (ties: lower id), each paired with every
 // open facility: C = p * T rows (j = the a-th open facility, k = the b-th
 // best, row a * T + b).
+constexpr int kMaxCand = 8;  // closed candidates per individual in the learned try (pm_ga_params.candidates <= 8)
+
+// (g, k) ahead of (h, j) in the candidates' order: gain descending, facility id ascending; an empty slot is
+// (0, INT32_MAX), behind every facility.
+__device__ __forceinline__ bool cand_before(unsigned long long g, int32_t k, unsigned long long h, int32_t j)
+{
+    return g > h || (g == h && k < j);
+}
+
 __global__ void __launch_bounds__(256) k_candidates(const uint32_t *__restrict__ masks, int32_t W, int32_t m,
                                                     int32_t p, int64_t n, const unsigned long long *__restrict__ gain,
                                                     const int *__restrict__ cap,
@@ -1312,12 +1321,15 @@ __global__ void __launch_bounds__(256) k_candidates(const uint32_t *__restrict__
                                                     const int *__restrict__ assign, const int64_t *__restrict__ costs,
                                                     int T, int32_t *__restrict__ moves, __nv_bfloat16 *__restrict__ X)
 {
+    constexpr int32_t kNone = 0x7fffffff;
     extern __shared__ __align__(16) unsigned char sm[];
     int32_t *open_s = reinterpret_cast<int32_t *>(sm);  // p entries
     for (int i = threadIdx.x; i < p; i += blockDim.x)
         open_s[i] = 0;  // a bitset with fewer than p open facilities still yields valid ids
     __syncthreads();
-    __shared__ int32_t top_k[8];
+    __shared__ int32_t top_k[kMaxCand];
+    __shared__ unsigned long long top_g[kMaxCand];
+    __shared__ float top_f1[kMaxCand], top_f3[kMaxCand], top_f6[kMaxCand];
     __shared__ int32_t nopen;
     const int64_t t = blockIdx.x;
     const uint32_t *x = masks + t * W;
@@ -1350,33 +1362,43 @@ __global__ void __launch_bounds__(256) k_candidates(const uint32_t *__restrict__
         if (lane == 0)
             nopen = cnt < p ? cnt : p;
     }
-    // top-T closed facilities by gain: T rounds of a block-wide (gain desc, id asc) arg-max
+    // top-T closed facilities by gain, in one pass over the gains: each thread keeps its own best T (in the
+    // candidates' order) of the facilities it reads, then T rounds of a block-wide arg-max over the threads'
+    // heads, the winner's owner dropping it -- the same T facilities, in the same order, as T arg-max passes
+    unsigned long long lg[kMaxCand];
+    int32_t lk[kMaxCand];
+#pragma unroll
+    for (int i = 0; i < kMaxCand; ++i) {
+        lg[i] = 0ull;
+        lk[i] = kNone;
+    }
+    for (int k = tid; k < m; k += blockDim.x) {
+        if ((x[k >> 5] >> (k & 31)) & 1u)
+            continue;
+        unsigned long long cg = gain[t * m + k];
+        int32_t ck = k;
+#pragma unroll
+        for (int i = 0; i < kMaxCand; ++i) {  // insertion: the displaced entry moves down
+            if (i < T && cand_before(cg, ck, lg[i], lk[i])) {
+                const unsigned long long tg = lg[i];
+                const int32_t tk = lk[i];
+                lg[i] = cg;
+                lk[i] = ck;
+                cg = tg;
+                ck = tk;
+            }
+        }
+    }
     __shared__ unsigned long long red_g[8];
     __shared__ int32_t red_k[8];
     for (int b = 0; b < T; ++b) {
-        unsigned long long bg = 0ull;
-        int32_t bk = 0x7fffffff;
-        bool have = false;
-        for (int k = tid; k < m; k += blockDim.x) {
-            if ((x[k >> 5] >> (k & 31)) & 1u)
-                continue;
-            bool taken = false;
-            for (int q = 0; q < b; ++q)
-                taken = taken || (top_k[q] == k);
-            if (taken)
-                continue;
-            const unsigned long long gk = gain[t * m + k];
-            if (!have || gk > bg || (gk == bg && k < bk)) {
-                bg = gk;
-                bk = k;
-                have = true;
-            }
-        }
+        unsigned long long bg = lg[0];
+        int32_t bk = lk[0];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             const unsigned long long og = __shfl_xor_sync(PM_FULL_MASK, bg, o);
             const int32_t ok = __shfl_xor_sync(PM_FULL_MASK, bk, o);
-            if (ok != 0x7fffffff && (bk == 0x7fffffff || og > bg || (og == bg && ok < bk))) {
+            if (cand_before(og, ok, bg, bk)) {
                 bg = og;
                 bk = ok;
             }
@@ -1390,28 +1412,62 @@ __global__ void __launch_bounds__(256) k_candidates(const uint32_t *__restrict__
             unsigned long long g0 = red_g[0];
             int32_t k0 = red_k[0];
             for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
-                if (red_k[w] != 0x7fffffff && (k0 == 0x7fffffff || red_g[w] > g0 || (red_g[w] == g0 && red_k[w] < k0))) {
+                if (cand_before(red_g[w], red_k[w], g0, k0)) {
                     g0 = red_g[w];
                     k0 = red_k[w];
                 }
-            if (k0 == 0x7fffffff)  // fewer than T closed facilities: repeat the previous one
+            if (k0 == kNone)  // fewer than T closed facilities: repeat the previous one
                 k0 = b > 0 ? top_k[b - 1] : 0;
             top_k[b] = k0;
         }
         __syncthreads();
+        if (lk[0] != kNone && lk[0] == top_k[b]) {  // the owner drops the winner
+#pragma unroll
+            for (int i = 0; i + 1 < kMaxCand; ++i) {
+                lg[i] = lg[i + 1];
+                lk[i] = lk[i + 1];
+            }
+            lg[kMaxCand - 1] = 0ull;
+            lk[kMaxCand - 1] = kNone;
+        }
     }
     const float Z = fmaxf((float)costs[t] / (float)p, 1.f);
     const float per = (float)n / (float)p, ratio = (float)p / (float)m;
-    const int64_t C = (int64_t)p * T;
-    for (int64_t row = tid; row < C; row += blockDim.x) {
-        const int a = (int)(row / T), b = (int)(row % T);
-        const int32_t j = open_s[a < nopen ? a : 0], k = top_k[b];
-        const int64_t idx = t * C + row;
-        moves[idx * 2] = j;
-        moves[idx * 2 + 1] = k;
-        const unsigned long long lj = loss[t * m + j], gk = gain[t * m + k];
-        move_feature_row(X + idx * kIn, (float)lj, (float)gk, (float)assign[t * m + j], (float)cap[t * m + k], Z, per,
-                         ratio, (float)((long long)lj - (long long)gk));
+    // the features that depend on the candidate k alone, once per k
+    if (tid < T) {
+        const int32_t k = top_k[tid];
+        const unsigned long long gk = gain[t * m + k];
+        top_g[tid] = gk;
+        top_f1[tid] = (float)gk / Z;
+        top_f3[tid] = (float)cap[t * m + k] / per;
+        top_f6[tid] = log1pf(top_f1[tid]);
+    }
+    __syncthreads();
+    // rows a*T .. a*T + T-1: open facility a (the first open one stands in past nopen) with each candidate; the
+    // features of j once per a; a row is 16 BF16 (8 features, 8 zeros) written as two 16-byte stores
+    const uint32_t bf_ratio = (uint32_t)__bfloat16_as_ushort(__float2bfloat16(ratio));
+    for (int a = tid; a < p; a += blockDim.x) {
+        const int32_t j = open_s[a < nopen ? a : 0];
+        const unsigned long long lj = loss[t * m + j];
+        const float f0 = (float)lj / Z;
+        const float f2 = (float)assign[t * m + j] / per;
+        const float f5 = log1pf(f0);
+        const uint32_t bf0 = (uint32_t)__bfloat16_as_ushort(__float2bfloat16(f0));
+        const uint32_t bf2 = (uint32_t)__bfloat16_as_ushort(__float2bfloat16(f2));
+        const uint32_t bf5 = (uint32_t)__bfloat16_as_ushort(__float2bfloat16(f5));
+        for (int b = 0; b < T; ++b) {
+            const int64_t idx = t * (int64_t)p * T + (int64_t)a * T + b;
+            const float f4 = (float)((long long)lj - (long long)top_g[b]) / Z;
+            uint4 v;
+            v.x = bf0 | ((uint32_t)__bfloat16_as_ushort(__float2bfloat16(top_f1[b])) << 16);
+            v.y = bf2 | ((uint32_t)__bfloat16_as_ushort(__float2bfloat16(top_f3[b])) << 16);
+            v.z = (uint32_t)__bfloat16_as_ushort(__float2bfloat16(f4)) | (bf5 << 16);
+            v.w = (uint32_t)__bfloat16_as_ushort(__float2bfloat16(top_f6[b])) | (bf_ratio << 16);
+            uint4 *out = reinterpret_cast<uint4 *>(X + idx * kIn);
+            out[0] = v;
+            out[1] = make_uint4(0u, 0u, 0u, 0u);
+            reinterpret_cast<int2 *>(moves)[idx] = make_int2(j, top_k[b]);
+        }
     }
 }
 
