@@ -1213,13 +1213,21 @@ __global__ void __launch_bounds__(1024, 2) k_swap_stats(const uint16_t *__restri
         int32_t d1 = 0, d2 = 0;
         int r1 = -1, found = 0;
         uint32_t f1 = 0;
+        uint32_t j_nx1 = 0;  // the next step's ranks, loaded one step ahead
+        int32_t d_nx1 = 0;
+        if (32 + lane < L) {
+            j_nx1 = __ldg(prow + 32 + lane);
+            d_nx1 = __ldg(drow + 32 + lane);
+        }
         for (int base = 32; base < L && found < 2; base += 32) {
             const int r = base + lane;
-            uint32_t j = 0;
-            int32_t dl = 0;
-            if (r < L) {
-                j = __ldg(prow + r);
-                dl = __ldg(drow + r);
+            const uint32_t j = j_nx1;
+            const int32_t dl = d_nx1;
+            j_nx1 = 0;
+            d_nx1 = 0;
+            if (r + 32 < L) {
+                j_nx1 = __ldg(prow + r + 32);
+                d_nx1 = __ldg(drow + r + 32);
             }
             uint32_t bal = __ballot_sync(PM_FULL_MASK, (r < L) && ((bits[j >> 5] >> (j & 31)) & 1u));
             if (bal == 0u)
