@@ -2129,7 +2129,10 @@ struct pm_ga {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;   // gate + conditional while-node over the generation
     cudaGraphExec_t exec1 = nullptr;  // one generation, no loop (calls of one generation)
+    cudaGraph_t graph1 = nullptr;     // the graph exec1 was instantiated from
     int graphs = 3;                   // which of the two to build: bit 0 exec, bit 1 exec1 (pm_ga_run: one)
+    // the root node of each graph: k_ga_begin, whose arguments (generation budget, trace) each call sets
+    cudaGraphNode_t begin_node = nullptr, begin_node1 = nullptr;
 };
 
 static void ga_free(pm_ga *ga)
@@ -2143,6 +2146,8 @@ static void ga_free(pm_ga *ga)
         pm_clear_error(cudaGraphExecDestroy(ga->exec1));
     if (ga->graph)
         pm_clear_error(cudaGraphDestroy(ga->graph));
+    if (ga->graph1)
+        pm_clear_error(cudaGraphDestroy(ga->graph1));
     if (ga->cap)
         pm_clear_error(cudaStreamDestroy(ga->cap));
     pm_dbuf *bufs[] = {&ga->X,         &ga->Xc,   &ga->cost,  &ga->active, &ga->improved, &ga->deme_best,
@@ -2344,19 +2349,56 @@ static pm_status enqueue_generation(pm_ga *ga, cudaStream_t s, cudaGraphConditio
     return PM_OK;
 }
 
+// k_ga_begin's kernel-node parameters for a call of `gens` generations writing its trace to `tr` (nullptr:
+// none); `args` holds the values the returned parameters point to.
+struct BeginArgs {
+    ga_glob *glob;
+    ga_dev *st;
+    int K;
+    long long gens;
+    long long *tr;
+    unsigned *bar;
+    void *ptrs[6];
+};
+
+static cudaKernelNodeParams begin_params(pm_ga *ga, long long gens, long long *tr, BeginArgs &a)
+{
+    a.glob = static_cast<ga_glob *>(ga->glob.ptr);
+    a.st = static_cast<ga_dev *>(ga->st.ptr);
+    a.K = ga->K;
+    a.gens = gens;
+    a.tr = tr;
+    a.bar = static_cast<unsigned *>(ga->bar.ptr);
+    a.ptrs[0] = &a.glob;
+    a.ptrs[1] = &a.st;
+    a.ptrs[2] = &a.K;
+    a.ptrs[3] = &a.gens;
+    a.ptrs[4] = &a.tr;
+    a.ptrs[5] = &a.bar;
+    cudaKernelNodeParams kp = {};
+    kp.func = reinterpret_cast<void *>(k_ga_begin);
+    kp.gridDim = dim3((unsigned)pm_ceil_div(ga->K, 256));
+    kp.blockDim = dim3(256);
+    kp.kernelParams = a.ptrs;
+    return kp;
+}
+
 // The generation as a plain graph for calls of one generation: entering and leaving a conditional body costs
-// about 6 us each way, a tenth of a graph900 generation.
+// about 6 us each way, a tenth of a graph900 generation.  Its root is k_ga_begin, so a call is one graph launch.
 static pm_status build_graph_one(pm_ga *ga)
 {
-    PM_CUDA(cudaStreamBeginCapture(ga->cap, cudaStreamCaptureModeThreadLocal));
+    PM_CUDA(cudaGraphCreate(&ga->graph1, 0));
+    BeginArgs ba;
+    const cudaKernelNodeParams kp = begin_params(ga, 1, nullptr, ba);
+    PM_CUDA(cudaGraphAddKernelNode(&ga->begin_node1, ga->graph1, nullptr, 0, &kp));
+    PM_CUDA(cudaStreamBeginCaptureToGraph(ga->cap, ga->graph1, &ga->begin_node1, nullptr, 1,
+                                          cudaStreamCaptureModeThreadLocal));
     pm_status st_gen = enqueue_generation(ga, ga->cap, 0, 0);
-    cudaGraph_t one = nullptr;
-    cudaError_t e = cudaStreamEndCapture(ga->cap, &one);
+    cudaGraph_t captured = nullptr;
+    cudaError_t e = cudaStreamEndCapture(ga->cap, &captured);
     PM_TRY(st_gen);
     PM_CUDA(e);
-    e = cudaGraphInstantiate(&ga->exec1, one, 0);
-    pm_clear_error(cudaGraphDestroy(one));
-    PM_CUDA(e);
+    PM_CUDA(cudaGraphInstantiate(&ga->exec1, ga->graph1, 0));
     return PM_OK;
 }
 
@@ -2375,8 +2417,11 @@ static pm_status build_graph(pm_ga *ga)
     kp.gridDim = dim3(1);
     kp.blockDim = dim3(1);
     kp.kernelParams = gate_args;
+    BeginArgs ba;
+    const cudaKernelNodeParams bp = begin_params(ga, 1, nullptr, ba);
+    PM_CUDA(cudaGraphAddKernelNode(&ga->begin_node, ga->graph, nullptr, 0, &bp));
     cudaGraphNode_t gate;
-    PM_CUDA(cudaGraphAddKernelNode(&gate, ga->graph, nullptr, 0, &kp));
+    PM_CUDA(cudaGraphAddKernelNode(&gate, ga->graph, &ga->begin_node, 1, &kp));
     cudaGraphNodeParams cp = {};
     cp.type = cudaGraphNodeTypeConditional;
     cp.conditional.handle = h;
@@ -2935,15 +2980,25 @@ extern "C" pm_status pm_ga_step(pm_ga *ga, int64_t gens, int64_t *trace, void *s
         PM_TRY(ga->trace.reserve(tbytes));
         tr = static_cast<long long *>(ga->trace.ptr);
     }
-    k_ga_begin<<<(unsigned)pm_ceil_div(ga->K, 256), 256, 0, s>>>(static_cast<ga_glob *>(ga->glob.ptr),
-                                                                static_cast<ga_dev *>(ga->st.ptr), ga->K,
-                                                                (long long)gens, tr,
-                                                                static_cast<unsigned *>(ga->bar.ptr));
-    PM_CUDA(cudaGetLastError());
+    const bool graph = !ga->fused && graph_mode();
+    if (!graph) {
+        k_ga_begin<<<(unsigned)pm_ceil_div(ga->K, 256), 256, 0, s>>>(static_cast<ga_glob *>(ga->glob.ptr),
+                                                                    static_cast<ga_dev *>(ga->st.ptr), ga->K,
+                                                                    (long long)gens, tr,
+                                                                    static_cast<unsigned *>(ga->bar.ptr));
+        PM_CUDA(cudaGetLastError());
+    }
     if (ga->fused) {
         PM_TRY(fused_launch(ga, s));
-    } else if (graph_mode()) {
-        PM_CUDA(cudaGraphLaunch((gens == 1 && ga->exec1) || !ga->exec ? ga->exec1 : ga->exec, s));
+    } else if (graph) {
+        // the graph's root runs k_ga_begin with this call's budget and trace (the update applies to this and
+        // later launches of the graph, not to launches already enqueued)
+        const bool one = (gens == 1 && ga->exec1) || !ga->exec;
+        BeginArgs ba;
+        const cudaKernelNodeParams kp = begin_params(ga, (long long)gens, tr, ba);
+        PM_CUDA(cudaGraphExecKernelNodeSetParams(one ? ga->exec1 : ga->exec, one ? ga->begin_node1 : ga->begin_node,
+                                                 &kp));
+        PM_CUDA(cudaGraphLaunch(one ? ga->exec1 : ga->exec, s));
     } else {
         // the same kernels, enqueued generation by generation (profilers cannot see
         // kernels inside conditional graphs); saturation needs the host to look
