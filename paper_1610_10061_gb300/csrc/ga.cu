@@ -61,6 +61,10 @@ pm_status pm_batch_ga_plan_candidates(pm_batch *b, int64_t pop, int64_t popQ, pm
 pm_status pm_learn_prepare(const pm_instance *inst, cudaStream_t s);
 pm_status pm_launch_swap_stats(const pm_instance *inst, const uint32_t *masks, int64_t pop, int64_t *gain,
                                int32_t *cap, int64_t *loss, int32_t *assign, cudaStream_t s);
+// the two above in one kernel when the statistics fit in shared memory (the arrays are then left unwritten)
+pm_status pm_launch_learned_candidates(const pm_instance *inst, const uint32_t *masks, int64_t pop, int64_t *gain,
+                                       int32_t *cap, int64_t *loss, int32_t *assign, const int64_t *costs, int T,
+                                       int32_t *moves, uint16_t *x, cudaStream_t s);
 pm_status pm_launch_candidates(const pm_instance *inst, const uint32_t *masks, int64_t pop, const int64_t *gain,
                                const int32_t *cap, const int64_t *loss, const int32_t *assign, const int64_t *costs,
                                int T, int32_t *moves, uint16_t *x, cudaStream_t s);
@@ -2294,8 +2298,7 @@ static pm_status enqueue_generation(pm_ga *ga, cudaStream_t s, cudaGraphConditio
         int32_t *capc = static_cast<int32_t *>(ga->s_cap.ptr), *asg = static_cast<int32_t *>(ga->s_assign.ptr);
         int32_t *moves = static_cast<int32_t *>(ga->moves.ptr);
         const int64_t C = inst->p * ga->T;
-        PM_TRY(pm_launch_swap_stats(inst, X, ga->P, gain, capc, loss, asg, s));
-        PM_TRY(pm_launch_candidates(inst, X, ga->P, gain, capc, loss, asg, cost, ga->T, moves,
+        PM_TRY(pm_launch_learned_candidates(inst, X, ga->P, gain, capc, loss, asg, cost, ga->T, moves,
                                     static_cast<uint16_t *>(ga->xfeat.ptr), s));
         PM_TRY(pm_model_forward_dev(ga->model, ga->xfeat.ptr, ga->P * C, static_cast<float *>(ga->scores.ptr), s));
         PM_CUDA(pm_launch(k_ga_learned_pick, groups, 1024, 0, s, gps, K, one, X, Xc, active, improved,

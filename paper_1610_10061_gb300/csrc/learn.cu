@@ -1098,6 +1098,155 @@ __global__ void k_running_sums(const int32_t *__restrict__ delta, int64_t n, int
     }
 }
 
+constexpr int kMaxCand = 8;  // closed candidates per individual in the learned try (pm_ga_params.candidates <= 8)
+
+// (g, k) ahead of (h, j) in the candidates' order: gain descending, facility id ascending; an empty slot is
+// (0, INT32_MAX), behind every facility.
+__device__ __forceinline__ bool cand_before(unsigned long long g, int32_t k, unsigned long long h, int32_t j)
+{
+    return g > h || (g == h && k < j);
+}
+
+// The learned try's candidate moves straight from one individual's statistics
+// in shared memory (the fused form of k_candidates, which reads them back from
+// global memory): the open facilities in ascending order, the T closed
+// facilities of largest gain (ties: lower id) by T block-wide arg-max passes,
+// and the p * T feature rows (row a * T + b: the a-th open facility with the
+// b-th candidate; the first open one stands in past the open count), each
+// computed as k_candidates computes it.
+struct CandOut {
+    const int64_t *costs;  // the individuals' exact costs
+    int32_t *moves;        // pop x p x T (j, k) pairs
+    __nv_bfloat16 *X;      // pop x p x T feature rows of 16 BF16
+    int32_t p;
+    int32_t T;
+    int64_t n;
+};
+
+template <typename Acc>
+__device__ __forceinline__ void candidates_from_stats(const uint32_t *bits, const Acc *Gs, const Acc *Ls,
+                                                      const int *Cs, const int *As, int32_t *open_s, int32_t W,
+                                                      int32_t m, int64_t t, const CandOut &co)
+{
+    constexpr int32_t kNone = 0x7fffffff;
+    __shared__ int32_t top_k[kMaxCand];
+    __shared__ unsigned long long top_g[kMaxCand];
+    __shared__ float top_f1[kMaxCand], top_f3[kMaxCand], top_f6[kMaxCand];
+    __shared__ unsigned long long red_g[32];
+    __shared__ int32_t red_k[32];
+    __shared__ int32_t nopen;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int32_t p = co.p, T = co.T;
+    for (int i = tid; i < p; i += blockDim.x)
+        open_s[i] = 0;  // a bitset with fewer than p open facilities still yields valid ids
+    __syncthreads();
+    if (warp == 0) {
+        int cnt = 0;
+        for (int base = 0; base < W; base += 32) {
+            const int w = base + lane;
+            const uint32_t word = w < W ? bits[w] : 0u;
+            const int pc = __popc(word);
+            int incl = pc;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(PM_FULL_MASK, incl, o);
+                if (lane >= o)
+                    incl += y;
+            }
+            int pos = cnt + incl - pc;
+            uint32_t rest = word;
+            while (rest) {
+                const int b = __ffs(rest) - 1;
+                rest &= rest - 1u;
+                if (pos < p)
+                    open_s[pos] = w * 32 + b;
+                ++pos;
+            }
+            cnt += __shfl_sync(PM_FULL_MASK, incl, 31);
+        }
+        if (lane == 0)
+            nopen = cnt < p ? cnt : p;
+    }
+    for (int b = 0; b < T; ++b) {
+        unsigned long long bg = 0ull;
+        int32_t bk = kNone;
+        for (int k = tid; k < m; k += blockDim.x) {
+            if ((bits[k >> 5] >> (k & 31)) & 1u)
+                continue;
+            bool taken = false;
+            for (int q = 0; q < b; ++q)
+                taken = taken || (top_k[q] == k);
+            const unsigned long long gk = (unsigned long long)Gs[k];
+            if (!taken && cand_before(gk, k, bg, bk)) {
+                bg = gk;
+                bk = k;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long og = __shfl_xor_sync(PM_FULL_MASK, bg, o);
+            const int32_t ok = __shfl_xor_sync(PM_FULL_MASK, bk, o);
+            if (cand_before(og, ok, bg, bk)) {
+                bg = og;
+                bk = ok;
+            }
+        }
+        if (lane == 0) {
+            red_g[warp] = bg;
+            red_k[warp] = bk;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            unsigned long long g0 = red_g[0];
+            int32_t k0 = red_k[0];
+            for (int w = 1; w < nwarps; ++w)
+                if (cand_before(red_g[w], red_k[w], g0, k0)) {
+                    g0 = red_g[w];
+                    k0 = red_k[w];
+                }
+            if (k0 == kNone)  // fewer than T closed facilities: repeat the previous one
+                k0 = b > 0 ? top_k[b - 1] : 0;
+            top_k[b] = k0;
+        }
+        __syncthreads();
+    }
+    const float Z = fmaxf((float)co.costs[t] / (float)p, 1.f);
+    const float per = (float)co.n / (float)p, ratio = (float)p / (float)m;
+    if (tid < T) {
+        const int32_t k = top_k[tid];
+        const unsigned long long gk = (unsigned long long)Gs[k];
+        top_g[tid] = gk;
+        top_f1[tid] = (float)gk / Z;
+        top_f3[tid] = (float)Cs[k] / per;
+        top_f6[tid] = log1pf(top_f1[tid]);
+    }
+    __syncthreads();
+    const uint32_t bf_ratio = (uint32_t)__bfloat16_as_ushort(__float2bfloat16(ratio));
+    for (int a = tid; a < p; a += blockDim.x) {
+        const int32_t j = open_s[a < nopen ? a : 0];
+        const unsigned long long lj = (unsigned long long)Ls[j];
+        const float f0 = (float)lj / Z;
+        const float f2 = (float)As[j] / per;
+        const float f5 = log1pf(f0);
+        const uint32_t bf0 = (uint32_t)__bfloat16_as_ushort(__float2bfloat16(f0));
+        const uint32_t bf2 = (uint32_t)__bfloat16_as_ushort(__float2bfloat16(f2));
+        const uint32_t bf5 = (uint32_t)__bfloat16_as_ushort(__float2bfloat16(f5));
+        for (int b = 0; b < T; ++b) {
+            const int64_t idx = t * (int64_t)p * T + (int64_t)a * T + b;
+            const float f4 = (float)((long long)lj - (long long)top_g[b]) / Z;
+            uint4 v;
+            v.x = bf0 | ((uint32_t)__bfloat16_as_ushort(__float2bfloat16(top_f1[b])) << 16);
+            v.y = bf2 | ((uint32_t)__bfloat16_as_ushort(__float2bfloat16(top_f3[b])) << 16);
+            v.z = (uint32_t)__bfloat16_as_ushort(__float2bfloat16(f4)) | (bf5 << 16);
+            v.w = (uint32_t)__bfloat16_as_ushort(__float2bfloat16(top_f6[b])) | (bf_ratio << 16);
+            uint4 *out = reinterpret_cast<uint4 *>(co.X + idx * kIn);
+            out[0] = v;
+            out[1] = make_uint4(0u, 0u, 0u, 0u);
+            reinterpret_cast<int2 *>(co.moves)[idx] = make_int2(j, top_k[b]);
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Swap statistics: one CTA per individual over the rows of Pi' and of the
 // sorted distances D' (the instance's table when it is cumulative, else the
@@ -1105,13 +1254,14 @@ __global__ void k_running_sums(const int32_t *__restrict__ delta, int64_t n, int
 // is one load and needs no scan; accumulators in shared memory when they fit
 // (else in the output arrays, zeroed by the caller).
 // ---------------------------------------------------------------------------
-template <typename Acc, bool kSmem>
+template <typename Acc, bool kSmem, bool kCand>
 __global__ void __launch_bounds__(1024, 2) k_swap_stats(const uint16_t *__restrict__ pi,
                                                      const int32_t *__restrict__ dist, int64_t n, int32_t L,
                                                      int64_t stride, int32_t W, int32_t m,
                                                      const uint32_t *__restrict__ masks, int64_t pop,
                                                      unsigned long long *__restrict__ gain, int *__restrict__ cap,
-                                                     unsigned long long *__restrict__ loss, int *__restrict__ assign)
+                                                     unsigned long long *__restrict__ loss, int *__restrict__ assign,
+                                                     CandOut co)
 {
     extern __shared__ __align__(16) unsigned char sm[];
     const int64_t t = blockIdx.x;
@@ -1263,11 +1413,17 @@ __global__ void __launch_bounds__(1024, 2) k_swap_stats(const uint16_t *__restri
     }
     if constexpr (kSmem) {
         __syncthreads();
-        for (int j = threadIdx.x; j < m; j += blockDim.x) {
-            gain[tm + j] = (unsigned long long)Gs[j];
-            loss[tm + j] = (unsigned long long)Ls[j];
-            cap[tm + j] = Cs[j];
-            assign[tm + j] = As[j];
+        if constexpr (kCand) {  // the learned try's candidates from the statistics in place (kept off global memory)
+            const size_t open_off = ((size_t)(reinterpret_cast<unsigned char *>(As + m) - sm) + 15) & ~size_t(15);
+            candidates_from_stats<Acc>(bits, Gs, Ls, Cs, As, reinterpret_cast<int32_t *>(sm + open_off), W, m, t,
+                                       co);
+        } else {
+            for (int j = threadIdx.x; j < m; j += blockDim.x) {
+                gain[tm + j] = (unsigned long long)Gs[j];
+                loss[tm + j] = (unsigned long long)Ls[j];
+                cap[tm + j] = Cs[j];
+                assign[tm + j] = As[j];
+            }
         }
     }
 }
@@ -1313,15 +1469,6 @@ __global__ void k_move_features(const unsigned long long *__restrict__ gain, con
 // facilities with the largest gain (ties: lower id), each paired with every
 // open facility: C = p * T rows (j = the a-th open facility, k = the b-th
 // best, row a * T + b).
-constexpr int kMaxCand = 8;  // closed candidates per individual in the learned try (pm_ga_params.candidates <= 8)
-
-// (g, k) ahead of (h, j) in the candidates' order: gain descending, facility id ascending; an empty slot is
-// (0, INT32_MAX), behind every facility.
-__device__ __forceinline__ bool cand_before(unsigned long long g, int32_t k, unsigned long long h, int32_t j)
-{
-    return g > h || (g == h && k < j);
-}
-
 __global__ void __launch_bounds__(256) k_candidates(const uint32_t *__restrict__ masks, int32_t W, int32_t m,
                                                     int32_t p, int64_t n, const unsigned long long *__restrict__ gain,
                                                     const int *__restrict__ cap,
@@ -2018,15 +2165,16 @@ pm_status pm_launch_swap_stats(const pm_instance *inst, const uint32_t *masks, i
     const int32_t *dist = inst->cum ? inst->delta : static_cast<const int32_t *>(inst->dsorted.ptr);
     if (!dist)
         return PM_ERR_INVALID_ARG;
+    const CandOut none{nullptr, nullptr, nullptr, 0, 0, 0};
 #define PM_STATS_ARGS                                                                                              \
     inst->pi, dist, inst->n, (int32_t)inst->L, inst->stride, (int32_t)inst->W, (int32_t)inst->m, masks, pop,       \
-        reinterpret_cast<unsigned long long *>(gain), cap, reinterpret_cast<unsigned long long *>(loss), assign
+        reinterpret_cast<unsigned long long *>(gain), cap, reinterpret_cast<unsigned long long *>(loss), assign, none
     if (narrow && in_smem)
-        k_swap_stats<unsigned int, true><<<(unsigned)pop, 1024, smem, s>>>(PM_STATS_ARGS);
+        k_swap_stats<unsigned int, true, false><<<(unsigned)pop, 1024, smem, s>>>(PM_STATS_ARGS);
     else if (in_smem)
-        k_swap_stats<unsigned long long, true><<<(unsigned)pop, 1024, smem, s>>>(PM_STATS_ARGS);
+        k_swap_stats<unsigned long long, true, false><<<(unsigned)pop, 1024, smem, s>>>(PM_STATS_ARGS);
     else
-        k_swap_stats<unsigned long long, false><<<(unsigned)pop, 1024, smem, s>>>(PM_STATS_ARGS);
+        k_swap_stats<unsigned long long, false, false><<<(unsigned)pop, 1024, smem, s>>>(PM_STATS_ARGS);
 #undef PM_STATS_ARGS
     PM_CUDA(cudaGetLastError());
     return PM_OK;
@@ -2091,6 +2239,34 @@ pm_status pm_launch_candidates(const pm_instance *inst, const uint32_t *masks, i
     return PM_OK;
 }
 
+pm_status pm_launch_learned_candidates(const pm_instance *inst, const uint32_t *masks, int64_t pop, int64_t *gain,
+                                       int32_t *cap, int64_t *loss, int32_t *assign, const int64_t *costs, int T,
+                                       int32_t *moves, uint16_t *x, cudaStream_t s)
+{
+    if (pop <= 0)
+        return PM_OK;
+    const size_t bits = (size_t)pm_round_up(inst->W * 4, 16);
+    const bool narrow = (double)inst->n * (double)std::max(inst->max_d, 1) < 4294967295.0;
+    const size_t acc = (size_t)inst->m * (narrow ? 16 : 24);
+    const size_t smem = (size_t)pm_round_up(bits + acc, 16) + (size_t)pm_round_up(inst->p * 4, 16);
+    const int32_t *dist = inst->cum ? inst->delta : static_cast<const int32_t *>(inst->dsorted.ptr);
+    if (!dist || smem + 1024 > inst->smem_optin) {  // the two kernels, the statistics through global memory
+        PM_TRY(pm_launch_swap_stats(inst, masks, pop, gain, cap, loss, assign, s));
+        return pm_launch_candidates(inst, masks, pop, gain, cap, loss, assign, costs, T, moves, x, s);
+    }
+    const CandOut co{costs, moves, reinterpret_cast<__nv_bfloat16 *>(x), (int32_t)inst->p, T, inst->n};
+#define PM_STATS_ARGS                                                                                              \
+    inst->pi, dist, inst->n, (int32_t)inst->L, inst->stride, (int32_t)inst->W, (int32_t)inst->m, masks, pop,       \
+        nullptr, nullptr, nullptr, nullptr, co
+    if (narrow)
+        k_swap_stats<unsigned int, true, true><<<(unsigned)pop, 1024, smem, s>>>(PM_STATS_ARGS);
+    else
+        k_swap_stats<unsigned long long, true, true><<<(unsigned)pop, 1024, smem, s>>>(PM_STATS_ARGS);
+#undef PM_STATS_ARGS
+    PM_CUDA(cudaGetLastError());
+    return PM_OK;
+}
+
 int pm_mlp_in_width() { return kIn; }
 
 // Kernel attributes of the learned path for this instance (call outside stream capture).
@@ -2116,9 +2292,14 @@ pm_status pm_learn_prepare(const pm_instance *inst, cudaStream_t s)
     }
     const int cap = (int)(inst->smem_optin > 1024 ? inst->smem_optin - 1024 : inst->smem_optin);
     // the shared-memory accumulator variants (the global one holds only the bitset: at most 8 KB)
-    PM_CUDA(cudaFuncSetAttribute(k_swap_stats<unsigned int, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
-    PM_CUDA(cudaFuncSetAttribute(k_swap_stats<unsigned long long, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    PM_CUDA(cudaFuncSetAttribute(k_swap_stats<unsigned int, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  cap));
+    PM_CUDA(cudaFuncSetAttribute(k_swap_stats<unsigned long long, true, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+    PM_CUDA(cudaFuncSetAttribute(k_swap_stats<unsigned int, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 cap));
+    PM_CUDA(cudaFuncSetAttribute(k_swap_stats<unsigned long long, true, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
     PM_CUDA(cudaFuncSetAttribute(k_candidates, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
     return mlp_init_attrs();
 }
