@@ -2250,7 +2250,9 @@ pm_status pm_launch_learned_candidates(const pm_instance *inst, const uint32_t *
     const size_t acc = (size_t)inst->m * (narrow ? 16 : 24);
     const size_t smem = (size_t)pm_round_up(bits + acc, 16) + (size_t)pm_round_up(inst->p * 4, 16);
     const int32_t *dist = inst->cum ? inst->delta : static_cast<const int32_t *>(inst->dsorted.ptr);
-    if (!dist || smem + 1024 > inst->smem_optin) {  // the two kernels, the statistics through global memory
+    const char *env = std::getenv("PM_LEARN_FUSED");  // PM_LEARN_FUSED=0: always the two kernels (for comparison)
+    if (!dist || smem + 1024 > inst->smem_optin || (env && env[0] == '0')) {
+        // the two kernels, the statistics through global memory
         PM_TRY(pm_launch_swap_stats(inst, masks, pop, gain, cap, loss, assign, s));
         return pm_launch_candidates(inst, masks, pop, gain, cap, loss, assign, costs, T, moves, x, s);
     }

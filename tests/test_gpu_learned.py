@@ -346,3 +346,28 @@ def test_learned_ga_on_cumulative_tables_is_exact(pm):
     np.testing.assert_array_equal(costs, oracle.eval_direct(d, masks))
     assert all(len(s) == p for s in sets_from_masks(masks, 500))
     assert (np.diff(trace) <= 0).all()
+
+
+@pytest.mark.parametrize("cumulative,T", [(False, 4), (True, 8), (False, 3)])
+def test_learned_try_fused_candidates_equal_the_two_kernels(pm, monkeypatch, cumulative, T):
+    """The learned try takes its candidate moves in the statistics kernel's tail when the statistics fit in
+    shared memory; PM_LEARN_FUSED=0 (read when the GA captures its generation) runs the statistics and the
+    candidates as two kernels through global memory instead.  Same model, same seed: identical populations,
+    costs and traces, and every cost exact.  T = 8 with p close to m also covers fewer closed facilities than
+    candidates."""
+    d, p = gmm_instance(400, seed=13), (30 if T != 8 else 395)
+    inst = pm.Instance(d, p, cumulative=cumulative)
+    model = pm.Model(seed=7)  # untrained: deterministic scores, so any difference is the candidates'
+    runs = []
+    for fused in ("1", "0"):
+        monkeypatch.setenv("PM_LEARN_FUSED", fused)
+        ga = pm.GA(inst, seed=3, pop=128, deme=32, model=model, candidates=T)
+        trace = ga.step(3)
+        masks, costs = ga.population()
+        runs.append((trace, masks, costs))
+        ga.close()
+    monkeypatch.delenv("PM_LEARN_FUSED")
+    np.testing.assert_array_equal(runs[0][0], runs[1][0])
+    np.testing.assert_array_equal(runs[0][1], runs[1][1])
+    np.testing.assert_array_equal(runs[0][2], runs[1][2])
+    np.testing.assert_array_equal(runs[0][2], oracle.eval_direct(d, runs[0][1]))
