@@ -1000,8 +1000,9 @@ def run_batched(args):
 
 
 def batched_record(pm, torch, count, tables="delta", steps=50, warmup=5):
-    """`count` uneven instances (n = m log-uniform in [100, 5000], half graph, half Euclidean) evolved together, one generation per timed step (L2 flushed
-    between steps), with the roofline of one batched evaluation pass; the bench line of `--workload batchedN`."""
+    """`count` uneven instances (n = m log-uniform in [100, 5000], half graph, half Euclidean) evolved together,
+    one generation per timed step (L2 flushed between steps), with the roofline of one batched evaluation pass; the
+    bench line of `--workload batchedN`."""
     import numpy as np
 
     from paper_1610_10061_gb300.inputs import batched_instances
