@@ -85,12 +85,14 @@ def _load():
     lib.oracle_crossover_params.restype = None
     lib.oracle_swap_stats.argtypes = [P, P, I64, I64, I64, P, I64, I64, P, P, P, P]
     lib.oracle_ga_run.argtypes = [P, P, I64, I64, I64, U64, U32, I64, I64, ctypes.c_int32, ctypes.c_int32,
-                                  I64, I64, P, P, P, P, P, P, P, P, ctypes.c_int32, _INIT_FN]
+                                  I64, I64, P, P, P, P, P, P, P, P, ctypes.c_int32, _INIT_FN, _EXTRA_FN]
     _lib = lib
     return lib
 
 
 _INIT_FN = ctypes.CFUNCTYPE(None, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32))
+_EXTRA_FN = ctypes.CFUNCTYPE(ctypes.c_int64, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32),
+                             ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_ubyte))
 
 
 def _ptr(a):
@@ -326,11 +328,14 @@ class GAState:
 def ga_run(pi, delta, m: int, p: int, seed: int, P: int, D: int | None = None, gens: int = 1,
            xover_rounds: int | None = None, mut_tries: int | None = None, saturation: int = 0,
            state: GAState | None = None, record: bool = False, inst: int = 0, team: bool = False,
-           init: str = "floyd"):
+           init: str = "floyd", extra_try=None):
     """Run the reference GA for `gens` generations (Sections 3.1, 3.2.2, 4.5).
 
     team=True selects migration variant (ii) of Section 4.5 (all deme bests into deme 0).
     init="combinadic" draws fresh chromosomes as Section 4.1 does (oracle.combinadic), else Floyd sampling.
+    extra_try(gen, X, c, enhanced) -> evaluations: a try between the crossover and the mutation cycles (the
+    learned swap proposal, not in the paper) on the population X (P x W, writable), its costs c and the
+    mutation cycle's `enhanced` flags (see oracle.mlp.first_candidate_try).
 
     Returns (state, trace, pops, costs); pops/costs are per-generation copies
     of the population after mutation when record=True.
@@ -361,9 +366,19 @@ def ga_run(pi, delta, m: int, p: int, seed: int, P: int, D: int | None = None, g
         init_fn = _INIT_FN()
     else:
         raise ValueError("init is 'floyd' or 'combinadic'")
+    if extra_try is not None:
+        def extra(g, xp, cp, ep):
+            X = np.ctypeslib.as_array(xp, shape=(P, W))
+            c = np.ctypeslib.as_array(cp, shape=(P,))
+            e = np.ctypeslib.as_array(ep, shape=(P,))
+            return int(extra_try(int(g), X, c, e))
+
+        extra_fn = _EXTRA_FN(extra)
+    else:
+        extra_fn = _EXTRA_FN()
     rc = _load().oracle_ga_run(_ptr(pi), _ptr(delta), n, m, p, seed, inst, P, D, xover_rounds, mut_tries, gens,
                                saturation, _ptr(st.deme_best), _ptr(st.deme_cost), _ptr(st.best), _ptr(st.scalars),
-                               _ptr(pops), _ptr(costs), _ptr(trace), _ptr(ran), 1 if team else 0, init_fn)
+                               _ptr(pops), _ptr(costs), _ptr(trace), _ptr(ran), 1 if team else 0, init_fn, extra_fn)
     _check(rc, "ga_run")
     k = int(ran[0])
     trace = trace[:k]

@@ -222,3 +222,42 @@ def unflatten(v):
 
 
 N_PARAMS = F_PAD * HIDDEN + HIDDEN + HIDDEN * HIDDEN + HIDDEN + HIDDEN + 1
+
+
+# --------------------------------------------------------------------------
+# The learned try when every candidate scores the same (a model whose parameters are all zero)
+# --------------------------------------------------------------------------
+
+def first_candidate_try(pi, delta, m: int, p: int):
+    """The learned try of one generation (between the crossover and the mutation cycles) for a model that gives
+    every candidate move the same score, as an ``extra_try`` for ``oracle.ga_run``.
+
+    The library's learned try ranks the candidates of an individual as rows a * T + b (the a-th open facility in
+    ascending order, the b-th closed facility by gain descending, ties by lower id) and takes the lowest score,
+    ties to the lowest row; with equal scores that is row 0: close the lowest open facility, open the closed
+    facility of largest gain.  The child is evaluated exactly (one evaluation per individual) and replaces the
+    individual, marked as improved so the mutation cycle skips it, iff strictly cheaper."""
+    from . import eval_scan, swap_stats
+
+    def extra(gen, X, c, enhanced):
+        P = X.shape[0]
+        gain, _, _, _ = swap_stats(pi, delta, m, X)
+        child = X.copy()
+        for t in range(P):
+            bits = np.unpackbits(X[t].view(np.uint8), bitorder="little")[:m].astype(bool)
+            j = int(np.flatnonzero(bits)[0])
+            closed = np.flatnonzero(~bits)
+            # largest gain, then lowest id: argmax over (gain, -id) among the closed facilities
+            g = gain[t, closed]
+            k = int(closed[np.flatnonzero(g == g.max())[0]]) if closed.size else 0
+            child[t, j >> 5] &= np.uint32(~(1 << (j & 31)) & 0xFFFFFFFF)
+            child[t, k >> 5] |= np.uint32(1 << (k & 31))
+        cc = eval_scan(pi, delta, child)
+        for t in range(P):
+            if cc[t] < c[t]:
+                X[t] = child[t]
+                c[t] = cc[t]
+                enhanced[t] = 1
+        return P
+
+    return extra

@@ -450,11 +450,17 @@ static int ilog2_exact(int64_t v)
    big integers in oracle/combinadic.py): writes the W words of individual `unit`'s fresh bitset. */
 typedef void (*oracle_init_fn)(uint32_t gen, uint32_t unit, uint32_t *x);
 
+/* An extra try between the crossover cycle and the mutation cycle, supplied by the caller (the learned swap
+   proposal, which the paper does not have): it may replace individuals of X (P x W) and their costs c, marks
+   the replaced ones in `enhanced` (the mutation cycle then skips them, as it skips those a mutant improved)
+   and returns the number of evaluations it made. */
+typedef int64_t (*oracle_extra_try_fn)(uint32_t gen, uint32_t *X, int64_t *c, unsigned char *enhanced);
+
 int oracle_ga_run(const uint16_t *pi, const int32_t *delta, int64_t n, int64_t m, int64_t p, uint64_t seed,
                   uint32_t inst, int64_t P, int64_t D, int32_t xover_rounds, int32_t mut_tries, int64_t gens,
                   int64_t S, uint32_t *deme_best, int64_t *deme_cost, uint32_t *best, int64_t *scalars,
                   uint32_t *pop_out, int64_t *cost_out, int64_t *trace, int64_t *gens_run, int32_t team,
-                  oracle_init_fn init_fn)
+                  oracle_init_fn init_fn, oracle_extra_try_fn extra_fn)
 {
     int lgD = ilog2_exact(D);
     if (n < 1 || p < 1 || p >= m || D < 2 || lgD < 0 || P < D || P % D != 0 || xover_rounds < 0 || mut_tries < 0)
@@ -517,8 +523,10 @@ int oracle_ga_run(const uint16_t *pi, const int32_t *delta, int64_t n, int64_t m
                 }
             }
         }
-        /* Evolve step 5: mutation cycle, first strict improvement stops */
+        /* Evolve step 5: mutation cycle, first strict improvement stops; the caller's extra try comes first */
         memset(enhanced, 0, (size_t)P);
+        if (extra_fn)
+            evals += extra_fn(g, X, c, enhanced);
         for (int32_t q = 0; q < mut_tries; ++q) {
             for (int64_t t = 0; t < P; ++t) {
                 if (enhanced[t])

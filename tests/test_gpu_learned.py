@@ -371,3 +371,31 @@ def test_learned_try_fused_candidates_equal_the_two_kernels(pm, monkeypatch, cum
     np.testing.assert_array_equal(runs[0][1], runs[1][1])
     np.testing.assert_array_equal(runs[0][2], runs[1][2])
     np.testing.assert_array_equal(runs[0][2], oracle.eval_direct(d, runs[0][1]))
+
+
+@pytest.mark.parametrize("n,p,pop,deme,cumulative,fused", [(120, 9, 64, 32, False, "1"), (200, 20, 128, 64, True, "1"),
+                                                          (150, 12, 96, 32, False, "0")])
+def test_learned_ga_with_equal_scores_matches_oracle(pm, monkeypatch, n, p, pop, deme, cumulative, fused):
+    """The whole learned generation against the oracle GA: with every parameter zero the model scores every
+    candidate the same, so the learned try takes candidate 0 -- close the lowest open facility, open the closed
+    facility of largest gain -- evaluates the child exactly and keeps it iff strictly cheaper, and the mutation
+    cycle skips the individuals it improved (oracle.mlp.first_candidate_try).  Population, costs, best and
+    evaluations after every generation, for both table kinds and both candidate paths."""
+    monkeypatch.setenv("PM_LEARN_FUSED", fused)
+    d = gmm_instance(n, seed=13)
+    pi, de = oracle.tables(d, p)
+    st, otrace, opops, ocosts = oracle.ga_run(pi, de, n, p, seed=3, P=pop, D=deme, gens=3, record=True,
+                                              extra_try=mlp.first_candidate_try(pi, de, n, p))
+    inst = pm.Instance(d, p, cumulative=cumulative)
+    model = pm.Model(seed=0)
+    model.set_params(np.zeros(model.n_params, dtype=np.float32))
+    ga = pm.GA(inst, seed=3, pop=pop, deme=deme, model=model)
+    for g in range(3):
+        tr = ga.step(1)
+        assert tr[0] == otrace[g]
+        masks, costs = ga.population()
+        np.testing.assert_array_equal(masks, opops[g], err_msg=f"population after generation {g + 1}")
+        np.testing.assert_array_equal(costs, ocosts[g], err_msg=f"costs after generation {g + 1}")
+    bc, gr, ev, best = ga.result()
+    assert bc == st.best_cost and ev == st.evals and gr == 3
+    np.testing.assert_array_equal(best, st.best)

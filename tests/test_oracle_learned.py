@@ -166,3 +166,50 @@ def test_train_loop_reduces_the_loss_and_follows_adam_step_by_step():
     mlp.adam_step(q, g, st, 3e-3)
     loss2, _ = mlp.loss_and_grads(q, X[order[64:128]], t[order[64:128]], bf16=True)
     assert loss2 == losses[1]
+
+
+def test_first_candidate_try_by_brute_force():
+    """oracle.mlp.first_candidate_try against its definition written with the direct objective (O1) only: the
+    gain of opening closed facility k alone is O1(x) - O1(x + k); the child closes the lowest open facility and
+    opens the largest-gain closed one (lowest id on ties); it replaces the individual iff strictly cheaper."""
+    m, p = 40, 6
+    d = euclid_instance(m, seed=21)
+    pi, de = oracle.tables(d, p)
+    X = random_masks(24, m, p, seed=5)
+    c = oracle.eval_direct(d, X)
+    want_X, want_c, want_e = X.copy(), c.copy(), np.zeros(24, dtype=np.uint8)
+    for t in range(24):
+        s = sorted(sets_from_masks(X[t:t + 1], m)[0])
+        closed = [k for k in range(m) if k not in s]
+        drops = [c[t] - oracle.eval_direct(d, masks_from_sets([s + [k]], m))[0] for k in closed]
+        k = closed[int(np.argmax(drops))]  # first maximum: lowest id among equal gains
+        child = masks_from_sets([[j for j in s if j != s[0]] + [k]], m)
+        cc = oracle.eval_direct(d, child)[0]
+        if cc < c[t]:
+            want_X[t], want_c[t], want_e[t] = child[0], cc, 1
+    e = np.zeros(24, dtype=np.uint8)
+    try_ = mlp.first_candidate_try(pi, de, m, p)
+    assert try_(0, X, c, e) == 24
+    np.testing.assert_array_equal(X, want_X)
+    np.testing.assert_array_equal(c, want_c)
+    np.testing.assert_array_equal(e, want_e)
+
+
+def test_ga_extra_try_hook():
+    """A try between the crossover and mutation cycles: doing nothing leaves the GA as it was; the first-candidate
+    try keeps every cost exact, exactly p open facilities and a non-increasing best."""
+    m, p = 60, 7
+    d = graph_instance(m, 150, seed=8)
+    pi, de = oracle.tables(d, p)
+    a = oracle.ga_run(pi, de, m, p, seed=2, P=32, D=16, gens=4, record=True)
+    b = oracle.ga_run(pi, de, m, p, seed=2, P=32, D=16, gens=4, record=True, extra_try=lambda g, X, c, e: 0)
+    np.testing.assert_array_equal(a[2], b[2])
+    np.testing.assert_array_equal(a[1], b[1])
+    assert a[0].evals == b[0].evals
+    st, trace, pops, costs = oracle.ga_run(pi, de, m, p, seed=2, P=32, D=16, gens=4, record=True,
+                                           extra_try=mlp.first_candidate_try(pi, de, m, p))
+    for g in range(4):
+        np.testing.assert_array_equal(costs[g], oracle.eval_direct(d, pops[g]))
+        assert all(len(s) == p for s in sets_from_masks(pops[g], m))
+    assert (np.diff(trace) <= 0).all()
+    assert st.evals >= 4 * 32 * 2  # every generation: the initial evaluation and one learned child per individual
