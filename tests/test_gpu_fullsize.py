@@ -101,3 +101,29 @@ def test_learned_ga_gmm5000_full_size_costs_are_exact(pm):
         assert best == tr[-1] == _direct(d, best_mask) and gens == g + 1
         assert prev is None or best <= prev
         prev = best
+
+
+def test_learned_ga_gmm5000_equal_scores_matches_oracle(pm):
+    """The learned GA at the size bench.py times it (clustered n = m = 5000, p = 500, pop 1024 in demes of 256),
+    with an all-zero model so that the oracle can follow it (oracle.mlp.first_candidate_try): population, costs,
+    best and evaluations after each of two generations."""
+    from oracle import mlp
+    w = paper_shape_instance("gmm5000_p500")
+    d, p, pop = w["d"], w["p"], w["pop"]
+    pi, de = oracle.tables(d, p)
+    st, otrace, opops, ocosts = oracle.ga_run(pi, de, 5000, p, seed=4, P=pop, D=256, gens=2, record=True,
+                                              extra_try=mlp.first_candidate_try(pi, de, 5000, p))
+    inst = pm.Instance(d, p)
+    inst.tune(pop)
+    model = pm.Model(seed=0)
+    model.set_params(np.zeros(model.n_params, dtype=np.float32))
+    ga = pm.GA(inst, seed=4, pop=pop, deme=256, model=model)
+    for g in range(2):
+        tr = ga.step(1)
+        assert tr[0] == otrace[g]
+        masks, costs = ga.population()
+        np.testing.assert_array_equal(masks, opops[g], err_msg=f"population after generation {g + 1}")
+        np.testing.assert_array_equal(costs, ocosts[g], err_msg=f"costs after generation {g + 1}")
+    bc, gr, ev, best = ga.result()
+    assert bc == st.best_cost and ev == st.evals and gr == 2
+    np.testing.assert_array_equal(best, st.best)
